@@ -1,0 +1,671 @@
+"""Plain FP64 CPU oracle of the lattice kinetic scheme with grid-separated moving rigid bodies.
+
+TEST INFRASTRUCTURE ONLY.  This module is the independent checker of the CUDA path.  Only the tests,
+``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.
+It shares no code, table or helper with the CUDA library and never imports the product package.
+
+Every function follows one passage of "4D Topology optimization of moving rigid bodies in fluid flows"
+(Tanabe, Yaji, Ushijima), cited by section and equation label.  Arrays are indexed by spatial axis in
+math order: a scalar field has shape ``(nx, ny)`` or ``(nx, ny, nz)``; a vector field has a leading axis of
+length d.  Lattice units are used throughout (grid spacing and time step equal 1).  All indexing wraps
+periodically on every axis (wall planes are imposed on top, see ``lks_step``).
+
+The code is written to work unchanged on complex128 arrays, so that the tests can take exact
+directional derivatives by the complex-step method (the only real-valued decisions are the integer tap
+positions of the mapping kernel, taken from the real part).
+
+Pinned by the tests in ``tests/test_oracle_*.py``: lattice isotropy, the exact shear-wave decay factor,
+uniform Brinkman relaxation, Couette / Brinkman-channel steady states against a direct linear solve,
+mass and momentum conservation, mapping partition of unity / shift invariance / brute force / transpose,
+filter invariants and transposes, and the adjoint against complex-step JVPs and central finite
+differences.  The paper's own objective values (Sec. 4.1 table) depend on figure-only geometry:
+parity unpinned for that full-problem value only.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# ---------------------------------------------------------------------------------------------
+# Lattice velocity sets (Sec. 2.2, Fig. "Velocity sets").  The paper shows the weights only in a
+# figure; these are the standard D2Q9 / D3Q15 weights, pinned by the isotropy identities in the tests.
+# ---------------------------------------------------------------------------------------------
+
+
+def lattice(name: str):
+    """Return (c, w): integer velocities c[Q, d] and weights w[Q] of D2Q9 or D3Q15 (Sec. 2.2)."""
+    if name == "D2Q9":
+        c = [(0, 0)]
+        w = [4.0 / 9.0]
+        for v in [(1, 0), (0, 1), (-1, 0), (0, -1)]:
+            c.append(v)
+            w.append(1.0 / 9.0)
+        for v in [(1, 1), (-1, 1), (-1, -1), (1, -1)]:
+            c.append(v)
+            w.append(1.0 / 36.0)
+    elif name == "D3Q15":
+        c = [(0, 0, 0)]
+        w = [2.0 / 9.0]
+        for a in range(3):
+            for sgn in (1, -1):
+                v = [0, 0, 0]
+                v[a] = sgn
+                c.append(tuple(v))
+                w.append(1.0 / 9.0)
+        for sx in (1, -1):
+            for sy in (1, -1):
+                for sz in (1, -1):
+                    c.append((sx, sy, sz))
+                    w.append(1.0 / 72.0)
+    else:
+        raise ValueError(f"unknown lattice {name!r}")
+    return np.array(c, dtype=np.int64), np.array(w, dtype=np.float64)
+
+
+def viscosity_A(nu: float) -> float:
+    """A = 3/4 - (9/2) nu / dx with dx = 1 (Sec. 2.2, Eq. for A)."""
+    return 0.75 - 4.5 * nu
+
+
+# ---------------------------------------------------------------------------------------------
+# Problem description.  Plain data; built by the tests from the workload description.
+# ---------------------------------------------------------------------------------------------
+
+
+@dataclass
+class Problem:
+    lattice: str                      # "D2Q9" or "D3Q15"
+    shape: tuple                      # analysis grid (nx, ny[, nz])
+    periodic: tuple                   # per axis: True = periodic, False = wall planes at 0 and n-1
+    nu: float                         # lattice kinematic viscosity
+    design: tuple                     # inner design grid (ndx, ndy[, ndz])
+    margin: int = 2                   # fluid margin around the design grid (Sec. 2.3), gamma = 0 there
+    kappa_max: float = 1.0            # kappa_max^ref of Eq. kappa_ref
+    q: float = 0.1                    # convexity parameter q of Eq. kappa_ref
+    kernel: str = "linear"            # "linear" (hat, the configs) or "cosine" (Sec. 2.3 w(r))
+    base_center: tuple | None = None  # analysis coordinates of the design centre at zero offset
+    Nt: int = 10                      # number of time steps
+    K: int = 2                        # number of motion knots
+    R_t: float = 1.0                  # temporal filter radius in steps (Eq. chi_filtered)
+    filter_R: float = 0.0             # density filter radius in design cells (Eq. filtering); <= 1 is identity
+    beta: float = 0.0                 # Heaviside projection steepness (Eq. projection); 0 = identity
+    eta: float = 0.5                  # projection threshold
+    probe_lo: tuple = ()              # objective box O_target, inclusive lower corner
+    probe_hi: tuple = ()              # exclusive upper corner
+    direction: tuple = ()             # n of Eq. objective1
+    wall_velocity: dict = field(default_factory=dict)  # {(axis, side): vector}; side 0 = plane 0, 1 = plane n-1
+
+    @property
+    def d(self) -> int:
+        return len(self.shape)
+
+    @property
+    def ext(self) -> tuple:
+        """Design grid including the margin on both sides."""
+        return tuple(n + 2 * self.margin for n in self.design)
+
+    def center(self) -> np.ndarray:
+        if self.base_center is not None:
+            return np.asarray(self.base_center, dtype=np.float64)
+        return (np.asarray(self.shape, dtype=np.float64) - 1.0) / 2.0
+
+    def origin(self) -> np.ndarray:
+        """X0 - xi^G: analysis coordinate of design index 0 (incl. margin) at zero offset (Eq. rigid_body_position, theta = 0)."""
+        xi_g = (np.asarray(self.ext, dtype=np.float64) - 1.0) / 2.0
+        return self.center() - xi_g
+
+
+# ---------------------------------------------------------------------------------------------
+# LKS forward step (Sec. 2.2)
+# ---------------------------------------------------------------------------------------------
+
+
+def central_diff(f, axis):
+    """(f(x + e_axis) - f(x - e_axis)) / 2 with periodic wrap (the velocity gradient of the Inamuro equilibrium)."""
+    return (np.roll(f, -1, axis=axis) - np.roll(f, 1, axis=axis)) / 2.0
+
+
+def equilibrium(p, u, A, c, w):
+    """All f_i^eq(x) of the Inamuro equilibrium with the velocity-gradient term (Sec. 2.2, Eq. for f_i^eq).
+
+    f_i = w_i {3p + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u} + w_i A (du_b/dx_a + du_a/dx_b) c_a c_b.
+    """
+    d = u.shape[0]
+    uu = sum(u[a] * u[a] for a in range(d))
+    # S_ab = du_b/dx_a + du_a/dx_b
+    G = [[central_diff(u[b], a) for b in range(d)] for a in range(d)]  # G[a][b] = d u_b / d x_a
+    S = [[G[a][b] + G[b][a] for b in range(d)] for a in range(d)]
+    feq = []
+    for i in range(len(w)):
+        cu = sum(c[i, a] * u[a] for a in range(d))
+        grad = sum(S[a][b] * (c[i, a] * c[i, b]) for a in range(d) for b in range(d))
+        feq.append(w[i] * (3.0 * p + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu) + w[i] * A * grad)
+    return feq
+
+
+def stream_moments(feq, c):
+    """p*(x) = 1/3 sum_i f_i^eq(x - c_i), u*(x) = sum_i c_i f_i^eq(x - c_i) (Eqs. p_tmp, u_tmp), tau = 1 stream."""
+    d = c.shape[1]
+    axes = tuple(range(d))
+    pstar = 0.0
+    ustar = [0.0] * d
+    for i, f in enumerate(feq):
+        g = np.roll(f, shift=tuple(int(v) for v in c[i]), axis=axes)  # g(x) = f(x - c_i)
+        pstar = pstar + g / 3.0
+        for a in range(d):
+            if c[i, a] != 0:
+                ustar[a] = ustar[a] + c[i, a] * g
+    return pstar, np.stack([np.broadcast_to(v, feq[0].shape) for v in ustar])
+
+
+def wall_mask(prob: Problem):
+    """Boolean mask of wall nodes and the imposed wall velocity field (Sec. 2.2: p, u imposed directly).
+
+    Reading: the wall nodes are the first and last index planes of every non-periodic axis; u is set to
+    that plane's velocity (later axes win where planes meet); p is not overwritten.
+    """
+    d = prob.d
+    mask = np.zeros(prob.shape, dtype=bool)
+    uw = np.zeros((d,) + prob.shape)
+    for a in range(d):
+        if prob.periodic[a]:
+            continue
+        for side, idx in ((0, 0), (1, prob.shape[a] - 1)):
+            sl = [slice(None)] * d
+            sl[a] = idx
+            mask[tuple(sl)] = True
+            vel = prob.wall_velocity.get((a, side), (0.0,) * d)
+            for b in range(d):
+                uw[(b,) + tuple(sl)] = vel[b]
+    return mask, uw
+
+
+def lks_step(p, u, kappa, uS, A, c, w, mask, uw):
+    """One LKS step (n-1 -> n): Eqs. p_tmp, u_tmp, p and u with the implicit Brinkman update, then walls."""
+    feq = equilibrium(p, u, A, c, w)
+    pstar, ustar = stream_moments(feq, c)
+    unew = (ustar + kappa * uS) / (1.0 + kappa)
+    unew = np.where(mask, uw, unew)
+    return pstar, unew
+
+
+# ---------------------------------------------------------------------------------------------
+# Grid separation mapping (Sec. 2.3, Eqs. kappa, u_s, rigid_body_position, rigid_body_velocity)
+# ---------------------------------------------------------------------------------------------
+
+
+def kernel_halfwidth(kernel: str) -> int:
+    return 1 if kernel == "linear" else 2
+
+
+def w1(r, kernel):
+    """One-dimensional transfer weight w(r) (Sec. 2.3; 'linear' is the hat max(0, 1 - |r|) the configs ask for)."""
+    if kernel == "cosine":
+        return np.where(np.abs(np.real(r)) <= 2.0, 0.25 * (1.0 + np.cos(np.pi * r / 2.0)), 0.0)
+    return np.where(np.abs(np.real(r)) <= 1.0, 1.0 - np.sign(np.real(r)) * r, 0.0)
+
+
+def dw1(r, kernel):
+    """dw/dr on the tap pieces used by ``axis_taps`` (for the hat: -1 on [0, 1), +1 on [-1, 0))."""
+    if kernel == "cosine":
+        return np.where(np.abs(np.real(r)) <= 2.0, -(np.pi / 8.0) * np.sin(np.pi * r / 2.0), 0.0)
+    rr = np.real(r)
+    return np.where((rr > 0.0) & (rr <= 1.0), -1.0, np.where((rr > -1.0) & (rr <= 0.0), 1.0, 0.0))
+
+
+def fold(t, n, hw):
+    """Fold a local coordinate on a periodic axis into one period [-hw, n - hw)."""
+    shift = np.floor((np.real(t) + hw) / n) * n
+    return t - shift
+
+
+def axis_taps(x, o, n, ne, periodic, kernel):
+    """Taps of the rigidly shifted design grid along one axis.
+
+    For analysis nodes x (1-D integer array) and design-index origin o (analysis coordinate of design index 0),
+    the local coordinate is t = x - o.  Returns (j, wgt, dwgt_do, valid) of shape (len(x), 2*hw): the design
+    indices, their weights w(t - j), the derivatives of the weights with respect to o, and validity.
+    The tap window is the piece that contains t from the left (i0 = ceil(t) - 1), so the position derivative is
+    the one-sided derivative from the right in o (reading of the hat kernel at integer offsets).
+    """
+    hw = kernel_halfwidth(kernel)
+    t = x.astype(np.float64) - o if not np.iscomplexobj(o) else x - o
+    if periodic:
+        t = fold(t, n, hw)
+    i0 = np.ceil(np.real(t)).astype(np.int64) - 1
+    ks = np.arange(-(hw - 1), hw + 1)
+    j = i0[:, None] + ks[None, :]
+    r = t[:, None] - j
+    wgt = w1(r, kernel)
+    dwgt = -dw1(r, kernel)  # d w(t - j) / d o = -w'(r)
+    valid = (j >= 0) & (j < ne)
+    wgt = np.where(valid, wgt, 0.0)
+    dwgt = np.where(valid, dwgt, 0.0)
+    return np.clip(j, 0, ne - 1), wgt, dwgt, valid
+
+
+def map_gather(kref, o, prob: Problem, with_grad=False):
+    """kappa(x) = sum_j W(x - x^ref_j) kappa^ref_j and C(x) = sum_j W(x - x^ref_j) (Eqs. kappa, u_s) by taps.
+
+    x^ref_j = j + o for translation only (theta = 0) with unit design spacing.  Returns kappa, C and, with
+    with_grad, d kappa / d o_a and d C / d o_a for every axis a.
+    """
+    d = prob.d
+    taps = []
+    for a in range(d):
+        x = np.arange(prob.shape[a])
+        taps.append(axis_taps(x, o[a], prob.shape[a], prob.ext[a], prob.periodic[a], prob.kernel))
+    T = taps[0][0].shape[1]
+    kappa = 0.0
+    dk = [0.0] * d
+    for combo in np.ndindex(*([T] * d)):
+        # separable weight over axes, gathered design value
+        idx = []
+        wt = 1.0
+        for a in range(d):
+            sh = [1] * d
+            sh[a] = prob.shape[a]
+            idx.append(taps[a][0][:, combo[a]].reshape(sh))
+            wt = wt * taps[a][1][:, combo[a]].reshape(sh)
+        val = kref[tuple(np.broadcast_arrays(*idx))]
+        kappa = kappa + wt * val
+        if with_grad:
+            for a in range(d):
+                g = 1.0
+                for b in range(d):
+                    sh = [1] * d
+                    sh[b] = prob.shape[b]
+                    col = taps[b][2 if b == a else 1][:, combo[b]].reshape(sh)
+                    g = g * col
+                dk[a] = dk[a] + g * val
+    # C is separable: product over axes of the summed valid weights
+    C = 1.0
+    dC = [1.0] * d
+    for a in range(d):
+        sh = [1] * d
+        sh[a] = prob.shape[a]
+        s = taps[a][1].sum(axis=1).reshape(sh)
+        ds = taps[a][2].sum(axis=1).reshape(sh)
+        C = C * s
+        for b in range(d):
+            dC[b] = dC[b] * (ds if b == a else s)
+    kappa = np.broadcast_to(kappa, prob.shape)
+    C = np.broadcast_to(C, prob.shape)
+    if not with_grad:
+        return kappa, C
+    dk = [np.broadcast_to(v, prob.shape) for v in dk]
+    dC = [np.broadcast_to(v, prob.shape) for v in dC]
+    return kappa, C, dk, dC
+
+
+def map_gather_T(gk, o, prob: Problem):
+    """Transpose of the kappa mapping: g_j = sum_x W(x - x^ref_j) gk(x) (the scatter-add onto the design grid, Eq. dJdgamma)."""
+    d = prob.d
+    taps = []
+    for a in range(d):
+        x = np.arange(prob.shape[a])
+        taps.append(axis_taps(x, o[a], prob.shape[a], prob.ext[a], prob.periodic[a], prob.kernel))
+    T = taps[0][0].shape[1]
+    out = np.zeros(prob.ext, dtype=np.result_type(gk, o, np.float64))
+    for combo in np.ndindex(*([T] * d)):
+        idx = []
+        wt = 1.0
+        for a in range(d):
+            sh = [1] * d
+            sh[a] = prob.shape[a]
+            idx.append(taps[a][0][:, combo[a]].reshape(sh))
+            wt = wt * taps[a][1][:, combo[a]].reshape(sh)
+        np.add.at(out, tuple(np.broadcast_arrays(*idx)), np.broadcast_to(wt * gk, prob.shape))
+    return out
+
+
+def map_bruteforce(kref, o, prob: Problem):
+    """The literal Eqs. kappa, u_s: for every analysis node, sum W over every design node (incl. margin).
+
+    Periodic axes take the nearest periodic image of the displacement; on wall axes nothing is folded, so
+    contributions that land outside the grid are dropped.  O(N * N_d): tiny grids only.
+    """
+    d = prob.d
+    xs = np.stack(np.meshgrid(*[np.arange(n, dtype=np.float64) for n in prob.shape], indexing="ij"), axis=-1)
+    js = np.stack(np.meshgrid(*[np.arange(n, dtype=np.float64) for n in prob.ext], indexing="ij"), axis=-1)
+    X = xs.reshape(-1, d)
+    Jc = js.reshape(-1, d) + np.asarray(o)[None, :]
+    W = np.ones((X.shape[0], Jc.shape[0]))
+    for a in range(d):
+        r = X[:, a][:, None] - Jc[:, a][None, :]
+        if prob.periodic[a]:
+            n = prob.shape[a]
+            r = r - n * np.round(r / n)
+        W = W * w1(r, prob.kernel)
+    kappa = (W @ kref.reshape(-1)).reshape(prob.shape)
+    C = W.sum(axis=1).reshape(prob.shape)
+    return kappa, C
+
+
+# ---------------------------------------------------------------------------------------------
+# Shape parametrisation (Sec. 3.1, Eqs. filtering, projection; Sec. 2.3, Eq. kappa_ref)
+# ---------------------------------------------------------------------------------------------
+
+
+def filter_weights(shape, R):
+    """Dense matrix of cone weights w_s(x_i, x_j) = max(0, (R - |x_i - x_j|)/R) over the design grid (Eq. filtering)."""
+    pts = np.stack(np.meshgrid(*[np.arange(n, dtype=np.float64) for n in shape], indexing="ij"), -1).reshape(-1, len(shape))
+    dist = np.sqrt(((pts[:, None, :] - pts[None, :, :]) ** 2).sum(-1))
+    return np.maximum(0.0, (R - dist) / R)
+
+
+def density_filter(gamma, R):
+    """gamma~_i = sum_j w_s gamma_j / sum_j w_s, truncated normalisation at the edges (Eq. filtering)."""
+    if R <= 1.0:
+        return gamma.copy()
+    out = np.zeros_like(gamma)
+    r = int(math.floor(R))
+    shape = gamma.shape
+    norm = np.zeros(shape)
+    for off in np.ndindex(*([2 * r + 1] * gamma.ndim)):
+        dvec = np.array(off) - r
+        dist = math.sqrt(float((dvec * dvec).sum()))
+        wgt = max(0.0, (R - dist) / R)
+        if wgt == 0.0:
+            continue
+        src, dst = [], []
+        for a, dv in enumerate(dvec):
+            n = shape[a]
+            dst.append(slice(max(0, -dv), min(n, n - dv)))
+            src.append(slice(max(0, dv), min(n, n + dv)))
+        out[tuple(dst)] += wgt * gamma[tuple(src)]
+        norm[tuple(dst)] += wgt
+    return out / norm
+
+
+def density_filter_T(g, R):
+    """Transpose of ``density_filter``: dJ/dgamma_j = sum_i w_s(i, j) (dJ/dgamma~_i) / sum_k w_s(i, k)."""
+    if R <= 1.0:
+        return g.copy()
+    # row norms of the filter, then the transposed weighted sum
+    r = int(math.floor(R))
+    shape = g.shape
+    norm = np.zeros(shape)
+    for off in np.ndindex(*([2 * r + 1] * g.ndim)):
+        dvec = np.array(off) - r
+        wgt = max(0.0, (R - math.sqrt(float((dvec * dvec).sum()))) / R)
+        if wgt == 0.0:
+            continue
+        src, dst = [], []
+        for a, dv in enumerate(dvec):
+            n = shape[a]
+            dst.append(slice(max(0, -dv), min(n, n - dv)))
+            src.append(slice(max(0, dv), min(n, n + dv)))
+        norm[tuple(dst)] += wgt
+    h = g / norm
+    out = np.zeros_like(h)
+    for off in np.ndindex(*([2 * r + 1] * g.ndim)):
+        dvec = np.array(off) - r
+        wgt = max(0.0, (R - math.sqrt(float((dvec * dvec).sum()))) / R)
+        if wgt == 0.0:
+            continue
+        src, dst = [], []
+        for a, dv in enumerate(dvec):
+            n = shape[a]
+            dst.append(slice(max(0, -dv), min(n, n - dv)))
+            src.append(slice(max(0, dv), min(n, n + dv)))
+        # the forward sent gamma_j (src) to gamma~_i (dst); the transpose sends h_i back to j
+        out[tuple(src)] += wgt * h[tuple(dst)]
+    return out
+
+
+def projection(gt, beta, eta):
+    """Heaviside projection (Eq. projection); beta = 0 is the identity (its beta -> 0 limit)."""
+    if beta == 0.0:
+        return gt.copy()
+    den = np.tanh(beta * eta) + np.tanh(beta * (1.0 - eta))
+    return (np.tanh(beta * eta) + np.tanh(beta * (gt - eta))) / den
+
+
+def projection_deriv(gt, beta, eta):
+    """d gamma-bar / d gamma~ of Eq. projection."""
+    if beta == 0.0:
+        return np.ones_like(gt)
+    den = np.tanh(beta * eta) + np.tanh(beta * (1.0 - eta))
+    return beta / np.cosh(beta * (gt - eta)) ** 2 / den
+
+
+def kappa_ref(gb, kappa_max, q):
+    """kappa^ref = kappa_max q gamma / ((1 - gamma) + q) (Eq. kappa_ref)."""
+    return kappa_max * q * gb / ((1.0 - gb) + q)
+
+
+def kappa_ref_deriv(gb, kappa_max, q):
+    return kappa_max * q * (1.0 + q) / ((1.0 - gb) + q) ** 2
+
+
+def embed_margin(a, margin):
+    """Place the inner design array inside the extended grid with a zero (fluid) margin (Sec. 2.3)."""
+    return np.pad(a, margin, mode="constant")
+
+
+def strip_margin(a, margin):
+    sl = tuple(slice(margin, n - margin) for n in a.shape)
+    return a[sl]
+
+
+# ---------------------------------------------------------------------------------------------
+# Motion parametrisation (Sec. 2.4, Eqs. chi_filtered, x_g, u_g)
+# ---------------------------------------------------------------------------------------------
+
+
+def knot_times(K, Nt):
+    """Knot k sits at step k Nt / (K - 1) (reading of the knot representation of chi(t))."""
+    return np.arange(K, dtype=np.float64) * Nt / (K - 1)
+
+
+def temporal_filter_matrix(K, Nt, R_t):
+    """Normalised triangular weights of Eq. chi_filtered evaluated between knot times (truncated, non-periodic)."""
+    tk = knot_times(K, Nt)
+    W = np.maximum(0.0, (R_t - np.abs(tk[:, None] - tk[None, :])) / R_t)
+    return W / W.sum(axis=1, keepdims=True)
+
+
+def motion_filter(knots, Nt, R_t):
+    """Filtered knot positions chi~ (Eq. chi_filtered); knots has shape (K, d)."""
+    return temporal_filter_matrix(knots.shape[0], Nt, R_t) @ knots
+
+
+def motion_filter_T(g, Nt, R_t):
+    return temporal_filter_matrix(g.shape[0], Nt, R_t).T @ g
+
+
+def interp_matrix(K, Nt):
+    """Linear interpolation of knot values to every step n = 0..Nt (integer arithmetic for the segment index)."""
+    M = np.zeros((Nt + 1, K))
+    for n in range(Nt + 1):
+        num = n * (K - 1)
+        k = min(num // Nt, K - 2)
+        th = (num - k * Nt) / Nt
+        M[n, k] += 1.0 - th
+        M[n, k + 1] += th
+    return M
+
+
+def positions(knots, Nt, R_t):
+    """Per-step offsets s_n (n = 0..Nt) and velocities u^G_n = s_n - s_{n-1} (Eq. u_g, backward difference)."""
+    s = interp_matrix(knots.shape[0], Nt) @ motion_filter(knots, Nt, R_t)
+    uG = np.zeros_like(s)
+    uG[1:] = s[1:] - s[:-1]
+    uG[0] = uG[1]
+    return s, uG
+
+
+# ---------------------------------------------------------------------------------------------
+# Forward solve, objective and exact discrete adjoint (Sec. 2.2, 2.5, 2.6; Algorithm 1)
+# ---------------------------------------------------------------------------------------------
+
+
+def probe_weights(prob: Problem):
+    """phi(x) = n 1_O(x) / (Nt |O|): d J / d u_n(x) for every step n >= 1 (Eq. objective1 with phi_V = 0).
+
+    O excludes wall nodes.
+    """
+    mask, _ = wall_mask(prob)
+    box = np.zeros(prob.shape, dtype=bool)
+    box[tuple(slice(lo, hi) for lo, hi in zip(prob.probe_lo, prob.probe_hi))] = True
+    box &= ~mask
+    count = int(box.sum())
+    phi = np.zeros((prob.d,) + prob.shape)
+    for a in range(prob.d):
+        phi[a] = np.where(box, prob.direction[a], 0.0) / (prob.Nt * count)
+    return phi
+
+
+def initial_state(prob: Problem, dtype=np.float64):
+    """p = 1/3, u = 0 everywhere, wall nodes at their wall velocity (Sec. 4 initial conditions)."""
+    mask, uw = wall_mask(prob)
+    p = np.full(prob.shape, 1.0 / 3.0, dtype=dtype)
+    u = np.where(mask[None], uw, 0.0).astype(dtype)
+    return p, u
+
+
+def forward(prob: Problem, kref, s, uG, store=False, state0=None):
+    """Run Nt LKS steps (Algorithm 1, forward loop) and return J (Eq. objective1, phi = 0).
+
+    kref is the extended design array kappa^ref (margin included); s, uG are (Nt+1, d) offsets and velocities.
+    With store=True the list of states (p_n, u_n), n = 0..Nt, is returned too.
+    """
+    c, w = lattice(prob.lattice)
+    A = viscosity_A(prob.nu)
+    mask, uw = wall_mask(prob)
+    phi = probe_weights(prob)
+    o0 = prob.origin()
+    dtype = np.result_type(kref, s, uG, np.float64)
+    p, u = initial_state(prob, dtype) if state0 is None else state0
+    states = [(p, u)] if store else None
+    J = 0.0
+    for n in range(1, prob.Nt + 1):
+        o = o0 + s[n]
+        kappa, C = map_gather(kref, o, prob)
+        uS = np.stack([uG[n, a] * C for a in range(prob.d)])
+        p, u = lks_step(p, u, kappa, uS, A, c, w, mask, uw)
+        J = J + (phi * u).sum()
+        if store:
+            states.append((p, u))
+    return (J, states) if store else J
+
+
+def adjoint(prob: Problem, kref, s, uG, states):
+    """Exact discrete adjoint of ``forward`` (reverse sweep of Algorithm 1; discrete form of Eqs. ap_tmp-as).
+
+    Returns dJ/dkref (extended grid), dJ/ds_n and dJ/du^G_n for n = 0..Nt (row 0 is zero).
+    Per step n, going backward, with lam = dJ/d(p_n, u_n):
+      b3  u-bar* = lam_u / (1 + kappa) off the walls, 0 on them; p-bar* = lam_p;
+          kappa-bar = lam_u . (u^S - u_n) / (1 + kappa);  u^S-bar = lam_u kappa / (1 + kappa)
+      b1  F-bar_i(y) = p-bar*(y + c_i) / 3 + c_i . u-bar*(y + c_i); moments M0, M1, M2 with weights w_i
+      b2  lam_p(n-1) = 3 M0;  lam_u(n-1) = 3 M1 + 9 M2 u_{n-1} - 3 u_{n-1} M0
+                       + A sum_a [M2_a.(y - e_a) - M2_a.(y + e_a)]  (+ phi for n - 1 >= 1)
+      b4  dJ/dkref += M^T kappa-bar (transposed mapping)
+      b5  dJ/ds_n = sum_x kappa-bar dkappa/ds + (u^S-bar . u^G) dC/ds;  dJ/du^G_n = sum_x u^S-bar C
+    """
+    c, w = lattice(prob.lattice)
+    A = viscosity_A(prob.nu)
+    mask, _ = wall_mask(prob)
+    phi = probe_weights(prob)
+    d = prob.d
+    axes = tuple(range(d))
+    o0 = prob.origin()
+    dtype = np.result_type(kref, s, uG, np.float64)
+    lam_p = np.zeros(prob.shape, dtype=dtype)
+    lam_u = phi.astype(dtype)
+    g_kref = np.zeros(prob.ext, dtype=dtype)
+    g_s = np.zeros((prob.Nt + 1, d), dtype=dtype)
+    g_uG = np.zeros((prob.Nt + 1, d), dtype=dtype)
+    for n in range(prob.Nt, 0, -1):
+        o = o0 + s[n]
+        kappa, C, dk, dC = map_gather(kref, o, prob, with_grad=True)
+        u_n = states[n][1]
+        u_prev = states[n - 1][1]
+        uS = np.stack([uG[n, a] * C for a in range(d)])
+        # b3: Brinkman and wall adjoint, local sensitivities
+        ubar = np.where(mask[None], 0.0, lam_u / (1.0 + kappa))
+        pbar = lam_p
+        kbar = np.where(mask, 0.0, sum(lam_u[a] * (uS[a] - u_n[a]) for a in range(d)) / (1.0 + kappa))
+        uSbar = np.where(mask[None], 0.0, lam_u * kappa / (1.0 + kappa))
+        # b4, b5
+        g_kref = g_kref + map_gather_T(kbar, o, prob)
+        Cbar = sum(uSbar[a] * uG[n, a] for a in range(d))
+        for a in range(d):
+            g_s[n, a] = (kbar * dk[a]).sum() + (Cbar * dC[a]).sum()
+            g_uG[n, a] = (uSbar[a] * C).sum()
+        # b1: reverse stream and local moments
+        M0 = 0.0
+        M1 = [0.0] * d
+        M2 = [[0.0] * d for _ in range(d)]
+        for i in range(len(w)):
+            sh = tuple(-int(v) for v in c[i])  # g(y) = h(y + c_i)
+            Fb = np.roll(pbar, shift=sh, axis=axes) / 3.0
+            for a in range(d):
+                if c[i, a] != 0:
+                    Fb = Fb + c[i, a] * np.roll(ubar[a], shift=sh, axis=axes)
+            M0 = M0 + w[i] * Fb
+            for a in range(d):
+                M1[a] = M1[a] + w[i] * c[i, a] * Fb
+                for b in range(d):
+                    M2[a][b] = M2[a][b] + w[i] * c[i, a] * c[i, b] * Fb
+        # b2: adjoint of the equilibrium (pressure, quadratic and velocity-gradient terms)
+        new_p = 3.0 * M0
+        new_u = []
+        for b in range(d):
+            v = 3.0 * M1[b] - 3.0 * u_prev[b] * M0
+            for a in range(d):
+                v = v + 9.0 * M2[a][b] * u_prev[a]
+                v = v + A * (np.roll(M2[a][b], 1, axis=a) - np.roll(M2[a][b], -1, axis=a))
+            new_u.append(v)
+        lam_p = new_p
+        lam_u = np.stack(new_u)
+        if n - 1 >= 1:
+            lam_u = lam_u + phi
+    return g_kref, g_s, g_uG
+
+
+# ---------------------------------------------------------------------------------------------
+# Full problem: design variables -> J and gradients (Algorithm 1: filters, forward, adjoint, chain rule)
+# ---------------------------------------------------------------------------------------------
+
+
+def design_to_kref(prob: Problem, gamma):
+    """gamma -> gamma~ (filter) -> gamma-bar (projection) -> kappa^ref on the extended grid (Algorithm 1, first line)."""
+    gt = density_filter(gamma, prob.filter_R)
+    gb = projection(gt, prob.beta, prob.eta)
+    kr = kappa_ref(gb, prob.kappa_max, prob.q)
+    return embed_margin(kr, prob.margin), gt, gb
+
+
+def solve(prob: Problem, gamma, knots, store=False):
+    """J(gamma, knots) of the whole chain."""
+    kref, _, _ = design_to_kref(prob, gamma)
+    s, uG = positions(knots, prob.Nt, prob.R_t)
+    return forward(prob, kref, s, uG, store=store)
+
+
+def knot_gradient(prob: Problem, g_s, g_uG):
+    """Chain rule from per-step (dJ/ds_n, dJ/du^G_n) to the knots: difference^T, interpolation^T, filter^T."""
+    gs = g_s.copy()
+    gs[1:] += g_uG[1:]
+    gs[:-1] -= g_uG[1:]
+    # u^G_0 = u^G_1 is never used by a step, so g_uG[0] is zero
+    gf = interp_matrix(prob.K, prob.Nt).T @ gs
+    return motion_filter_T(gf, prob.Nt, prob.R_t)
+
+
+def gradient(prob: Problem, gamma, knots):
+    """Return J, dJ/dgamma (inner design grid), dJ/dknots (K, d)."""
+    kref, gt, gb = design_to_kref(prob, gamma)
+    s, uG = positions(knots, prob.Nt, prob.R_t)
+    J, states = forward(prob, kref, s, uG, store=True)
+    g_kref, g_s, g_uG = adjoint(prob, kref, s, uG, states)
+    g_kr = strip_margin(g_kref, prob.margin)
+    g_gb = g_kr * kappa_ref_deriv(gb, prob.kappa_max, prob.q)
+    g_gt = g_gb * projection_deriv(gt, prob.beta, prob.eta)
+    g_gamma = density_filter_T(g_gt, prob.filter_R)
+    g_knots = knot_gradient(prob, g_s, g_uG)
+    return J, g_gamma, g_knots

@@ -1,0 +1,77 @@
+"""Planted mistakes in the oracle (on the CPU) must make its pins fail.
+
+Each test patches one plausible error into the oracle and checks that the corresponding pin catches it,
+so a green pin run says something about the oracle's correctness.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.lks_oracle as L
+
+from test_oracle_lattice import shear_lambda
+from test_oracle_adjoint import tiny
+
+
+def shear_error(A_used, A_true, name="D2Q9"):
+    c, w = O.lattice(name)
+    shape = (3, 32)
+    k = 2 * np.pi / 32
+    prof = 0.01 * np.sin(k * np.arange(32))
+    u = np.zeros((2,) + shape)
+    u[0] = prof[None, :]
+    p = np.full(shape, 1 / 3)
+    mask = np.zeros(shape, bool)
+    for _ in range(200):
+        p, u = O.lks_step(p, u, 0.0, 0 * u, A_used, c, w, mask, 0 * u)
+    return np.max(np.abs(u[0, 0] - prof * shear_lambda(k, A_true) ** 200))
+
+
+def test_wrong_viscosity_coefficient_is_caught():
+    nu = 0.02
+    assert shear_error(O.viscosity_A(nu), O.viscosity_A(nu)) < 1e-15
+    assert shear_error(0.75 - 4.0 * nu, O.viscosity_A(nu)) > 1e-6
+
+
+def test_wrong_weight_is_caught():
+    c, w = O.lattice("D2Q9")
+    w2 = w.copy()
+    w2[5:] = 1.0 / 30.0
+    w2[0] = 1.0 - w2[1:].sum()
+    assert abs((w2 * c[:, 0] ** 2).sum() - 1 / 3) > 1e-3
+
+
+def test_forward_adjoint_mismatch_is_caught(monkeypatch):
+    P, gamma, knots = tiny("D2Q9", "linear", 50, Nt=8)
+    rng = np.random.default_rng(51)
+    vg = rng.standard_normal(gamma.shape)
+
+    def dot_gap():
+        J, gg, gk = O.gradient(P, gamma, knots)
+        h = 1e-30
+        jvp = np.imag(O.solve(P, gamma + 1j * h * vg, knots)) / h
+        return abs((gg * vg).sum() - jvp) / np.abs(gg * vg).sum()
+
+    assert dot_gap() < 1e-12
+    # a one-sided velocity gradient in the forward only (the adjoint keeps the central transpose)
+    monkeypatch.setattr(L, "central_diff", lambda f, axis: np.roll(f, -1, axis=axis) - f)
+    assert dot_gap() > 1e-6
+
+
+def test_dropped_brinkman_term_is_caught(monkeypatch):
+    # drop kappa u^S from Eq. u: the uniform relaxation closed form must fail
+    c, w = O.lattice("D2Q9")
+    shape = (4, 4)
+    u = np.zeros((2,) + shape)
+    p = np.full(shape, 1 / 3)
+    uS = np.full((2,) + shape, 0.05)
+    mask = np.zeros(shape, bool)
+    orig = L.lks_step
+
+    def bad(p, u, kappa, uS, A, c, w, mask, uw):
+        return orig(p, u, kappa, 0.0 * uS, A, c, w, mask, uw)
+
+    monkeypatch.setattr(L, "lks_step", bad)
+    p1, u1 = L.lks_step(p, u, 0.5, uS, 0.6, c, w, mask, 0 * u)
+    want = 0.05 + (0.0 - 0.05) / 1.5
+    assert abs(u1[0, 0, 0] - want) > 1e-3
