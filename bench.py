@@ -1,0 +1,277 @@
+#!/usr/bin/env python3
+"""Throughput of the fused forward + adjoint lattice-kinetic-scheme sweep (G node-steps/s, "GLUPS").
+
+One step = one lks_forward + one lks_adjoint of the whole workload (all steps of the hot path: filters,
+Nt forward LKS steps with the fused rigid-body mapping and objective, the checkpointed reverse sweep with
+recompute, the adjoint steps with shape/motion sensitivities, the chain rules).  value = nodes x Nt /
+(device time of one step), whole job (sum over ranks for --gpus N: independent replicas, weak scaling).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2608_01071_b300.workloads import draw_gamma, draw_knots, workload  # noqa: E402
+
+DEFAULT_WORKLOAD = "d2q9_512x256_fp32"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            v = [x.strip() for x in line.split(",")]
+            if len(v) < 9:
+                continue
+            try:
+                sm.append(float(v[1]))
+                smax.append(float(v[2]))
+            except ValueError:
+                continue
+            for nme, val in zip(names, v[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nme)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def node_count(w):
+    return int(np.prod(w["shape"]))
+
+
+def cpu_baseline(w, sample_steps=60):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: same grid, first `sample_steps` steps."""
+    import oracle as O  # test infrastructure: only this leg and --impl reference use it
+    from tests.helpers import oracle_problem
+
+    # shorter horizon: scale the motion amplitude with it so that body speeds stay those of the workload
+    ws = dict(w, Nt=sample_steps, K=min(w["K"], 6), R_t=max(1.0, sample_steps / 4), amp=w["amp"] * sample_steps / w["Nt"])
+    P = oracle_problem(ws)
+    gamma, knots = draw_gamma(ws), draw_knots(ws)
+    t0 = time.perf_counter()
+    O.gradient(P, gamma, knots)
+    dt = time.perf_counter() - t0
+    val = node_count(ws) * sample_steps / dt / 1e9
+    return {"value": val, "unit": "G node-steps/s (fwd+adj)", "cores": 1, "kind": "oracle",
+            "sample": f"{w['name']} grid, first {sample_steps} of {w['Nt']} steps, forward + exact adjoint, numpy FP64, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    sample_steps = 20
+    times = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(w, sample_steps)
+        if i >= args.warmup:
+            times.append(cb)
+    val = statistics.mean(t["value"] for t in times)
+    line = {"impl": "reference", "metric": "fwd+adjoint LKS GLUPS", "value": val, "unit": "G node-steps/s (fwd+adj)",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "grid": list(w["shape"]), "design": list(w["design"]), "Nt": w["Nt"],
+                       "sample_Nt": sample_steps},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": times[0]["sample"], "value": val,
+                             "unit": "G node-steps/s (fwd+adj)"},
+            "e2e": {"value": val, "unit": "G node-steps/s (fwd+adj)", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2608_01071_b300 import Solver
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl")
+
+    w = workload(args.workload)
+    D = len(w["shape"])
+    N = node_count(w)
+    solver = Solver.from_workload(w)
+    solver.set_timing(True)
+    gamma, knots = draw_gamma(w), draw_knots(w)
+    dev = torch.device("cuda", local)
+    d_gamma = torch.tensor(np.ascontiguousarray(gamma.T), device=dev)
+    d_knots = torch.tensor(knots, device=dev)
+    d_J = torch.empty((), dtype=torch.float64, device=dev)
+    d_dg = torch.empty_like(d_gamma)
+    d_dk = torch.empty_like(d_knots)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 2**20, dtype=torch.uint8, device=dev)  # > 126 MB L2
+
+    def step():
+        solver.forward_dev(d_gamma, d_knots, d_J, stream=stream)
+        solver.adjoint_dev(d_dg, d_dk, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    st_adj, st_rec, st_fwd, launches = [], [], [], 0
+    for i in range(args.steps):
+        flush.zero_()  # L2 flush between timed iterations (not inside the timed span)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        s = solver.stats()
+        st_adj.append((s["ms_adjoint_steps"], s["adjoint_steps"]))
+        st_rec.append((s["ms_recompute_steps"], s["recompute_steps"]))
+        st_fwd.append((s["ms_forward_steps"], s["forward_steps"]))
+        launches += s["kernel_launches"]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    t_dev = sum(ms) / 1e3
+    if dist:
+        t = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = float(t.item())
+    value = world * N * w["Nt"] * args.steps / t_dev / 1e9
+
+    # roofline of the dominant kernel (the adjoint step) from its live CUDA-event durations
+    s = 4 if w["precision"] == "fp32" else 8
+    Fbn = 1
+    hw = 1 if w["kernel"] == "linear" else 2
+    for a in range(D):
+        Fbn *= w["design"][a] + 2 * w["margin"] + 2 * hw - 1
+    adj_bytes = N * (2 * (D + 1) + D) * s + Fbn * (D + 1) * s
+    fwd_bytes = N * 2 * (D + 1) * s
+    adj_ms = sum(a for a, _ in st_adj) / max(1, sum(n for _, n in st_adj))
+    fwd_ms = sum(a for a, _ in st_fwd) / max(1, sum(n for _, n in st_fwd))
+    rec_ms = sum(a for a, _ in st_rec) / max(1, sum(n for _, n in st_rec))
+    peak, peak_kind = peaks()
+    adj_gbs = adj_bytes / (adj_ms * 1e-3) / 1e9
+    fwd_gbs = fwd_bytes / (fwd_ms * 1e-3) / 1e9
+
+    # end to end through the host-pointer C ABI (H2D of gamma and knots, D2H of J and both gradients)
+    e2e_times = []
+    for i in range(max(2, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        solver.forward(gamma, knots)
+        solver.adjoint()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e = world * N * w["Nt"] / statistics.mean(e2e_times) / 1e9
+    nd = int(np.prod(w["design"]))
+    h2d = nd * 8 + w["K"] * D * 8
+    d2h = 8 + nd * 8 + w["K"] * D * 8
+
+    if rank == 0:
+        line = {
+            "metric": "fwd+adjoint LKS GLUPS", "value": value, "unit": "G node-steps/s (fwd+adj)",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if w["precision"] == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "lattice": w["lattice"], "grid": list(w["shape"]), "design": list(w["design"]),
+                       "Nt": w["Nt"], "K": w["K"], "precision": w["precision"] + " state / f64 accumulators",
+                       "checkpointing": w["ckpt"], "parallelism": f"replicas{world}",
+                       "l2": "512 MB buffer written between timed steps; the 1.5 MB state is L2-resident within a step"},
+            "roofline": {"bound": "hbm", "kernel": "adj_step_kernel", "achieved": adj_gbs, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": adj_gbs / peak, "traffic": None,
+                         "bytes_per_launch": adj_bytes, "us_per_launch": adj_ms * 1e3,
+                         "fwd_step_kernel": {"achieved": fwd_gbs, "frac": fwd_gbs / peak, "us_per_launch": fwd_ms * 1e3,
+                                             "bytes_per_launch": fwd_bytes},
+                         "recompute_us_per_launch": rec_ms * 1e3},
+            "e2e": {"value": e2e, "unit": "G node-steps/s (fwd+adj)", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches * world),
+            "clocks": clk,
+            "wall_s": t_wall,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

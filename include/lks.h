@@ -1,0 +1,197 @@
+/*
+ * lks.h -- C ABI of the B300 lattice-kinetic-scheme solver with grid-separated moving rigid bodies
+ * and its exact discrete adjoint ("4D Topology optimization of moving rigid bodies in fluid flows",
+ * Tanabe, Yaji, Ushijima).
+ *
+ * Conventions for every entry point
+ *  - Lattice units: grid spacing and time step are 1.  Positions are offsets in analysis cells.
+ *  - Arrays are flat, x fastest: a field over an (nx, ny, nz) grid is indexed (z*ny + y)*nx + x;
+ *    a design array over (ndx, ndy, ndz) likewise.  Knot arrays are (K, d) row-major; per-step arrays
+ *    are (Nt+1, d) row-major.
+ *  - Entry points without the _dev suffix take HOST pointers and copy in and out themselves.
+ *    Entry points with the _dev suffix take DEVICE pointers of the current device and a cudaStream_t
+ *    passed as void* (NULL = the legacy default stream); they are asynchronous with respect to the host
+ *    unless stated otherwise.
+ *  - The library owns all of its device state (fields, checkpoints, history, reduction slots); it is
+ *    allocated in lks_create and freed in lks_destroy.  The caller owns every array it passes; no pointer
+ *    passed in is retained after the call returns.
+ *  - Every call returns an lks_status.  On error the outputs are left untouched and a message is
+ *    available from lks_last_error_string.  A context is not thread-safe: one host thread at a time.
+ */
+#ifndef LKS_H
+#define LKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LKS_ABI_VERSION 1
+
+typedef enum lks_status {
+    LKS_OK = 0,
+    LKS_EINVAL = -1,     /* bad parameters, sizes or pointers */
+    LKS_ENOMEM = -2,     /* a device or host allocation failed */
+    LKS_ECUDA = -3,      /* a CUDA runtime call failed (including "no device") */
+    LKS_ESTATE = -4,     /* call order violated (e.g. adjoint before forward) */
+    LKS_EUNSTABLE = -5,  /* non-finite velocity or |u| > u_crit seen during a forward sweep */
+    LKS_ETIMEOUT = -6    /* a bounded device-side wait expired */
+} lks_status;
+
+enum { LKS_D2Q9 = 9, LKS_D3Q15 = 15 };                         /* Sec. 2.2 velocity sets */
+enum { LKS_MAP_LINEAR = 0, LKS_MAP_COSINE = 1 };               /* Sec. 2.3 transfer kernel w(r) */
+enum { LKS_FP64 = 0, LKS_FP32 = 1 };                           /* state precision (accumulators FP64) */
+enum { LKS_CKPT_FULL = 0, LKS_CKPT_SQRT = 1, LKS_CKPT_REVOLVE = 2 };
+enum { LKS_MODE_JOINT = 0, LKS_MODE_SHAPE = 1, LKS_MODE_MOTION = 2 };
+
+/*
+ * Problem parameters (plain data, versioned by `size`).  Fill with lks_default_params, then set fields.
+ *
+ *  lattice        LKS_D2Q9 (2D) or LKS_D3Q15 (3D), Sec. 2.2.
+ *  n[3]           analysis grid; n[2] = 1 in 2D.
+ *  periodic[3]    1: periodic axis; 0: wall planes at index 0 and n-1 (u imposed, p streamed), Sec. 2.2.
+ *  wall_velocity  [axis][side][component] velocity of each wall plane (side 0 = index 0).
+ *  nu             lattice kinematic viscosity; A = 3/4 - 9 nu / 2 (Sec. 2.2).  Requires 0 < nu.
+ *  kappa_max, q   Eq. kappa_ref: kappa^ref = kappa_max q g / ((1 - g) + q).
+ *  nd[3]          inner design grid (nd[2] = 1 in 2D); margin: zero-kappa fluid margin per side (Sec. 2.3).
+ *  map_kernel     LKS_MAP_LINEAR (hat, w = max(0, 1-|r|)) or LKS_MAP_COSINE (Sec. 2.3 w(r), |r| <= 2).
+ *  base_center    analysis coordinates of the design-grid centre at zero offset; NaN = grid centre.
+ *  probe_lo/hi    objective box O_target [lo, hi) (wall nodes excluded); direction: n of Eq. objective1.
+ *  Nt, K          time steps and motion knots (knot k at step k Nt/(K-1)); K >= 2.
+ *  R_t            temporal filter radius in steps (Eq. chi_filtered), > 0.
+ *  filter_R       density filter radius in design cells (Eq. filtering); <= 1 means identity.
+ *  beta, eta      Heaviside projection (Eq. projection); beta = 0 means identity.
+ *  precision      LKS_FP64 (plain FP64 state) or LKS_FP32 (FP32 state/stencil, FP64 objective and
+ *                 sensitivity accumulation).
+ *  ckpt           LKS_CKPT_FULL (every state kept), LKS_CKPT_SQRT (checkpoints every ceil(sqrt Nt) steps),
+ *                 LKS_CKPT_REVOLVE (binomial schedule with ckpt_slots checkpoints, or as many as fit
+ *                 in ckpt_bytes when ckpt_slots = 0).
+ *  seg_len        recompute-segment length for REVOLVE (0 = automatic).
+ *  mode           which gradients lks_adjoint produces (the others are returned as zeros).
+ *  u_crit         stability limit on |u| checked every forward step (<= 0 disables); LKS_EUNSTABLE.
+ */
+typedef struct lks_params {
+    uint32_t size;
+    int32_t lattice;
+    int32_t n[3];
+    int32_t periodic[3];
+    double wall_velocity[3][2][3];
+    double nu;
+    double kappa_max;
+    double q;
+    int32_t nd[3];
+    int32_t margin;
+    int32_t map_kernel;
+    double base_center[3];
+    int32_t probe_lo[3];
+    int32_t probe_hi[3];
+    double direction[3];
+    int32_t Nt;
+    int32_t K;
+    double R_t;
+    double filter_R;
+    double beta;
+    double eta;
+    int32_t precision;
+    int32_t ckpt;
+    int32_t ckpt_slots;
+    int32_t seg_len;
+    int64_t ckpt_bytes;
+    int32_t mode;
+    double u_crit;
+} lks_params;
+
+typedef struct lks_ctx lks_ctx;
+
+/* Counters of the last forward / adjoint (for measurement). */
+typedef struct lks_stats {
+    int64_t forward_steps;     /* LKS steps run by the last lks_forward */
+    int64_t recompute_steps;   /* LKS steps re-run by the last lks_adjoint */
+    int64_t adjoint_steps;     /* adjoint steps run by the last lks_adjoint */
+    int64_t kernel_launches;   /* kernels launched by the last forward + adjoint pair */
+    int64_t device_bytes;      /* device memory held by the context */
+    int32_t ckpt_slots;        /* checkpoints in use */
+    int32_t seg_len;           /* recompute segment length */
+    /* With lks_set_timing(ctx, 1): device time (CUDA events on the launching stream) of the last call pair. */
+    double ms_forward_steps;   /* the Nt forward-step kernels of lks_forward */
+    double ms_recompute_steps; /* forward-step kernels re-run by lks_adjoint */
+    double ms_adjoint_steps;   /* the adjoint-step kernels */
+    double ms_total;           /* whole lks_forward + lks_adjoint device time */
+} lks_stats;
+
+/* Fill *p with defaults for a 2D D2Q9 problem (size set, base_center NaN, everything else valid). */
+int lks_default_params(lks_params* p);
+
+/* Validate *p, allocate all device state on the current device.  *out is set only on LKS_OK. */
+int lks_create(const lks_params* p, lks_ctx** out);
+
+/* Free a context (NULL is a no-op).  Waits for the context's outstanding work. */
+void lks_destroy(lks_ctx* ctx);
+
+/* Human-readable text of the last error on ctx (never NULL), and of a status code. */
+const char* lks_last_error_string(const lks_ctx* ctx);
+const char* lks_strerror(int status);
+
+/*
+ * Forward solve (Algorithm 1, filters and forward time loop; objective Eq. objective1 with phi = 0):
+ *   gamma[nd]      design variables on the inner design grid, in [0, 1];
+ *   pos_knots[K*d] body-centre offsets (cells) at the knots;
+ *   J              objective, the time-space mean of n.u over O_target.
+ * Keeps what the adjoint needs (checkpoints).  Host-pointer variant blocks until J is on the host.
+ */
+int lks_forward(lks_ctx* ctx, const double* gamma, const double* pos_knots, double* J);
+int lks_forward_dev(lks_ctx* ctx, const double* d_gamma, const double* d_pos_knots, double* d_J, void* stream);
+
+/*
+ * Adjoint solve (Algorithm 1, reverse loop; shape sensitivity Eq. dJdgamma, motion sensitivity Eq. dJdchi,
+ * as the exact discrete adjoint of the forward), then the chain rules through the filters:
+ *   dJ_dgamma[nd]     dJ/dgamma on the inner design grid;
+ *   dJ_dpos[K*d]      dJ/dpos_knots.
+ * Needs a preceding lks_forward on the same context (LKS_ESTATE otherwise).  With LKS_CKPT_REVOLVE the
+ * reverse sweep reuses the forward's checkpoint slots, so every lks_adjoint needs its own lks_forward.
+ */
+int lks_adjoint(lks_ctx* ctx, double* dJ_dgamma, double* dJ_dpos);
+int lks_adjoint_dev(lks_ctx* ctx, double* d_dJ_dgamma, double* d_dJ_dpos, void* stream);
+
+/* Density filter of Eq. filtering on the inner design grid (out = W gamma) and its transpose. */
+int lks_density_filter_dev(lks_ctx* ctx, const double* d_in, double* d_out, void* stream);
+int lks_density_filter_T_dev(lks_ctx* ctx, const double* d_in, double* d_out, void* stream);
+
+/* Heaviside projection of Eq. projection: out = P(in), dout = dP/din (either output may be NULL). */
+int lks_projection_dev(int64_t count, double beta, double eta, const double* d_in, double* d_out,
+                       double* d_dout, void* stream);
+
+/* Temporal motion filter of Eq. chi_filtered over the knots (K x d) and its transpose. */
+int lks_motion_filter_dev(lks_ctx* ctx, const double* d_knots, double* d_filtered, void* stream);
+int lks_motion_filter_T_dev(lks_ctx* ctx, const double* d_in, double* d_out, void* stream);
+
+/* Per-step offsets s[(Nt+1) x d] by linear interpolation of filtered knots and u^G_n = s_n - s_{n-1}
+ * (Eq. u_g as a backward difference; u^G_0 = u^G_1); and the transpose (s-bar, u^G-bar) -> knot-bar. */
+int lks_interp_positions_dev(lks_ctx* ctx, const double* d_filtered, double* d_s, double* d_uG, void* stream);
+int lks_interp_positions_T_dev(lks_ctx* ctx, const double* d_gs, const double* d_guG, double* d_out, void* stream);
+
+/* Final state (p_Nt, u_Nt) of the last forward, as FP64: p[N], u[d*N] (component-major). Synchronous. */
+int lks_get_state(lks_ctx* ctx, double* p, double* u);
+
+/* Per-step motion sensitivities of the last adjoint, dJ/ds_n and dJ/du^G_n, each (Nt+1) x d. Synchronous. */
+int lks_get_step_sensitivities(lks_ctx* ctx, double* dJ_ds, double* dJ_duG);
+
+/* Counters of the last forward / adjoint. */
+int lks_get_stats(const lks_ctx* ctx, lks_stats* out);
+
+/* Enable (1) or disable (0) CUDA-event timing of the step kernels.  When enabled, lks_adjoint[_dev]
+ * synchronizes its stream at the end to read the events. */
+int lks_set_timing(lks_ctx* ctx, int enable);
+
+/* Enable (1, the default) or disable (0) CUDA-graph replay of the forward and reverse sweeps.  With graphs
+ * on, the first lks_forward / lks_adjoint of a context capture their kernel sequence (all buffers belong to
+ * the context, so the sequence is fixed) and later calls replay it.  Results are identical either way.
+ * Changing the setting discards the captured graphs and requires a new lks_forward. */
+int lks_set_graphs(lks_ctx* ctx, int enable);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LKS_H */

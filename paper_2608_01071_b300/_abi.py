@@ -1,0 +1,114 @@
+"""ctypes declarations of the C ABI in include/lks.h (argument marshalling only).
+
+Loading fails loudly when the compiled library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblks.so")
+
+LKS_OK, LKS_EINVAL, LKS_ENOMEM, LKS_ECUDA, LKS_ESTATE, LKS_EUNSTABLE, LKS_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+LKS_D2Q9, LKS_D3Q15 = 9, 15
+LKS_MAP_LINEAR, LKS_MAP_COSINE = 0, 1
+LKS_FP64, LKS_FP32 = 0, 1
+LKS_CKPT_FULL, LKS_CKPT_SQRT, LKS_CKPT_REVOLVE = 0, 1, 2
+LKS_MODE_JOINT, LKS_MODE_SHAPE, LKS_MODE_MOTION = 0, 1, 2
+
+
+class lks_params(C.Structure):
+    _fields_ = [
+        ("size", C.c_uint32),
+        ("lattice", C.c_int32),
+        ("n", C.c_int32 * 3),
+        ("periodic", C.c_int32 * 3),
+        ("wall_velocity", ((C.c_double * 3) * 2) * 3),
+        ("nu", C.c_double),
+        ("kappa_max", C.c_double),
+        ("q", C.c_double),
+        ("nd", C.c_int32 * 3),
+        ("margin", C.c_int32),
+        ("map_kernel", C.c_int32),
+        ("base_center", C.c_double * 3),
+        ("probe_lo", C.c_int32 * 3),
+        ("probe_hi", C.c_int32 * 3),
+        ("direction", C.c_double * 3),
+        ("Nt", C.c_int32),
+        ("K", C.c_int32),
+        ("R_t", C.c_double),
+        ("filter_R", C.c_double),
+        ("beta", C.c_double),
+        ("eta", C.c_double),
+        ("precision", C.c_int32),
+        ("ckpt", C.c_int32),
+        ("ckpt_slots", C.c_int32),
+        ("seg_len", C.c_int32),
+        ("ckpt_bytes", C.c_int64),
+        ("mode", C.c_int32),
+        ("u_crit", C.c_double),
+    ]
+
+
+class lks_stats(C.Structure):
+    _fields_ = [
+        ("forward_steps", C.c_int64),
+        ("recompute_steps", C.c_int64),
+        ("adjoint_steps", C.c_int64),
+        ("kernel_launches", C.c_int64),
+        ("device_bytes", C.c_int64),
+        ("ckpt_slots", C.c_int32),
+        ("seg_len", C.c_int32),
+        ("ms_forward_steps", C.c_double),
+        ("ms_recompute_steps", C.c_double),
+        ("ms_adjoint_steps", C.c_double),
+        ("ms_total", C.c_double),
+    ]
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+
+# name -> (restype, argtypes)
+PROTOTYPES = {
+    "lks_default_params": (C.c_int, [C.POINTER(lks_params)]),
+    "lks_create": (C.c_int, [C.POINTER(lks_params), C.POINTER(_P)]),
+    "lks_destroy": (None, [_P]),
+    "lks_last_error_string": (C.c_char_p, [_P]),
+    "lks_strerror": (C.c_char_p, [C.c_int]),
+    "lks_forward": (C.c_int, [_P, _D, _D, _D]),
+    "lks_forward_dev": (C.c_int, [_P, _P, _P, _P, _P]),
+    "lks_adjoint": (C.c_int, [_P, _D, _D]),
+    "lks_adjoint_dev": (C.c_int, [_P, _P, _P, _P]),
+    "lks_density_filter_dev": (C.c_int, [_P, _P, _P, _P]),
+    "lks_density_filter_T_dev": (C.c_int, [_P, _P, _P, _P]),
+    "lks_projection_dev": (C.c_int, [C.c_int64, C.c_double, C.c_double, _P, _P, _P, _P]),
+    "lks_motion_filter_dev": (C.c_int, [_P, _P, _P, _P]),
+    "lks_motion_filter_T_dev": (C.c_int, [_P, _P, _P, _P]),
+    "lks_interp_positions_dev": (C.c_int, [_P, _P, _P, _P, _P]),
+    "lks_interp_positions_T_dev": (C.c_int, [_P, _P, _P, _P, _P]),
+    "lks_get_state": (C.c_int, [_P, _D, _D]),
+    "lks_get_step_sensitivities": (C.c_int, [_P, _D, _D]),
+    "lks_get_stats": (C.c_int, [_P, C.POINTER(lks_stats)]),
+    "lks_set_timing": (C.c_int, [_P, C.c_int]),
+    "lks_set_graphs": (C.c_int, [_P, C.c_int]),
+}
+
+_lib = None
+
+
+def load():
+    """Load liblks.so (built in-tree) and declare every prototype; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library {LIB_PATH} is missing: build it with `python -m paper_2608_01071_b300.build`")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in PROTOTYPES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib

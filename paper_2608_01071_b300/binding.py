@@ -1,0 +1,190 @@
+"""Python binding of the C ABI: one ``Solver`` per library context.  Argument marshalling only.
+
+Host arrays use the math index order [x, y(, z)]; they are passed to the library in its flat x-fastest
+order (``a.T`` in C order) and converted back on return.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import _abi
+
+_MAP = {"linear": _abi.LKS_MAP_LINEAR, "cosine": _abi.LKS_MAP_COSINE}
+_PREC = {"fp64": _abi.LKS_FP64, "fp32": _abi.LKS_FP32}
+_CKPT = {"full": _abi.LKS_CKPT_FULL, "sqrt": _abi.LKS_CKPT_SQRT, "revolve": _abi.LKS_CKPT_REVOLVE}
+_MODE = {"joint": _abi.LKS_MODE_JOINT, "shape": _abi.LKS_MODE_SHAPE, "motion": _abi.LKS_MODE_MOTION}
+
+
+class LKSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+def params_from_workload(w: dict) -> _abi.lks_params:
+    """Fill an lks_params from a workload description (plain data; see ``workloads``)."""
+    lib = _abi.load()
+    p = _abi.lks_params()
+    lib.lks_default_params(C.byref(p))
+    d = len(w["shape"])
+    p.lattice = _abi.LKS_D2Q9 if w["lattice"] == "D2Q9" else _abi.LKS_D3Q15
+    for a in range(3):
+        p.n[a] = w["shape"][a] if a < d else 1
+        p.periodic[a] = int(bool(w["periodic"][a])) if a < d else 1
+        p.nd[a] = w["design"][a] if a < d else 1
+        p.probe_lo[a] = w["probe_lo"][a] if a < d else 0
+        p.probe_hi[a] = w["probe_hi"][a] if a < d else 1
+        p.direction[a] = w["direction"][a] if a < d else 0.0
+        bc = w.get("base_center")
+        p.base_center[a] = bc[a] if (bc is not None and a < d) else math.nan
+    for (axis, side), vel in w.get("wall_velocity", {}).items():
+        for b in range(d):
+            p.wall_velocity[axis][side][b] = vel[b]
+    p.nu = w["nu"]
+    p.kappa_max = w["kappa_max"]
+    p.q = w["q"]
+    p.margin = w["margin"]
+    p.map_kernel = _MAP[w["kernel"]]
+    p.Nt = w["Nt"]
+    p.K = w["K"]
+    p.R_t = w["R_t"]
+    p.filter_R = w["filter_R"]
+    p.beta = w["beta"]
+    p.eta = w["eta"]
+    p.precision = _PREC[w["precision"]]
+    p.ckpt = _CKPT[w["ckpt"]]
+    p.ckpt_slots = w.get("ckpt_slots", 0)
+    p.seg_len = w.get("seg_len", 0)
+    p.ckpt_bytes = int(w.get("ckpt_bytes", 0))
+    p.mode = _MODE[w.get("mode", "joint")]
+    p.u_crit = w.get("u_crit", 0.3)
+    return p
+
+
+def _flat(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).T)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+class Solver:
+    """One library context (device state owned by the library)."""
+
+    def __init__(self, params: _abi.lks_params):
+        self.lib = _abi.load()
+        self.params = params
+        self.d = 2 if params.lattice == _abi.LKS_D2Q9 else 3
+        self.shape = tuple(params.n[a] for a in range(self.d))
+        self.design = tuple(params.nd[a] for a in range(self.d))
+        self.K = params.K
+        self.Nt = params.Nt
+        h = C.c_void_p()
+        rc = self.lib.lks_create(C.byref(params), C.byref(h))
+        if rc != 0:
+            raise LKSError(rc, self.lib.lks_last_error_string(None).decode())
+        self.h = h
+
+    @classmethod
+    def from_workload(cls, w: dict) -> "Solver":
+        return cls(params_from_workload(w))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lks_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise LKSError(rc, self.lib.lks_last_error_string(self.h).decode())
+
+    # host-pointer calls -------------------------------------------------------------------------
+    def forward(self, gamma, knots) -> float:
+        g = _flat(gamma)
+        k = np.ascontiguousarray(knots, dtype=np.float64)
+        J = C.c_double()
+        self._check(self.lib.lks_forward(self.h, _dptr(g), _dptr(k), C.byref(J)))
+        return J.value
+
+    def adjoint(self):
+        dg = np.zeros(self.design[::-1])
+        dk = np.zeros((self.K, self.d))
+        self._check(self.lib.lks_adjoint(self.h, _dptr(dg), _dptr(dk)))
+        return dg.T.copy(), dk
+
+    def state(self):
+        N = int(np.prod(self.shape))
+        p = np.zeros(N)
+        u = np.zeros(self.d * N)
+        self._check(self.lib.lks_get_state(self.h, _dptr(p), _dptr(u)))
+        p = p.reshape(self.shape[::-1]).T.copy()
+        u = np.stack([u[a * N:(a + 1) * N].reshape(self.shape[::-1]).T for a in range(self.d)])
+        return p, u
+
+    def step_sensitivities(self):
+        gs = np.zeros((self.Nt + 1, self.d))
+        gu = np.zeros((self.Nt + 1, self.d))
+        self._check(self.lib.lks_get_step_sensitivities(self.h, _dptr(gs), _dptr(gu)))
+        return gs, gu
+
+    def set_timing(self, on: bool):
+        self._check(self.lib.lks_set_timing(self.h, 1 if on else 0))
+
+    def set_graphs(self, on: bool):
+        self._check(self.lib.lks_set_graphs(self.h, 1 if on else 0))
+
+    def stats(self) -> dict:
+        s = _abi.lks_stats()
+        self._check(self.lib.lks_get_stats(self.h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    # device-pointer calls (torch tensors: contiguous float64 on the current device, flat x-fastest) ---
+    def forward_dev(self, d_gamma, d_knots, d_J, stream=None):
+        self._check(self.lib.lks_forward_dev(self.h, C.c_void_p(d_gamma.data_ptr()), C.c_void_p(d_knots.data_ptr()),
+                                             C.c_void_p(d_J.data_ptr()), _stream_ptr(stream)))
+
+    def adjoint_dev(self, d_dgamma, d_dknots, stream=None):
+        self._check(self.lib.lks_adjoint_dev(self.h, C.c_void_p(d_dgamma.data_ptr()) if d_dgamma is not None else None,
+                                             C.c_void_p(d_dknots.data_ptr()) if d_dknots is not None else None,
+                                             _stream_ptr(stream)))
+
+    def density_filter_dev(self, d_in, d_out, transpose=False, stream=None):
+        f = self.lib.lks_density_filter_T_dev if transpose else self.lib.lks_density_filter_dev
+        self._check(f(self.h, C.c_void_p(d_in.data_ptr()), C.c_void_p(d_out.data_ptr()), _stream_ptr(stream)))
+
+    def motion_filter_dev(self, d_in, d_out, transpose=False, stream=None):
+        f = self.lib.lks_motion_filter_T_dev if transpose else self.lib.lks_motion_filter_dev
+        self._check(f(self.h, C.c_void_p(d_in.data_ptr()), C.c_void_p(d_out.data_ptr()), _stream_ptr(stream)))
+
+    def interp_positions_dev(self, d_filt, d_s, d_uG, stream=None):
+        self._check(self.lib.lks_interp_positions_dev(self.h, C.c_void_p(d_filt.data_ptr()), C.c_void_p(d_s.data_ptr()),
+                                                      C.c_void_p(d_uG.data_ptr()), _stream_ptr(stream)))
+
+    def interp_positions_T_dev(self, d_gs, d_guG, d_out, stream=None):
+        self._check(self.lib.lks_interp_positions_T_dev(self.h, C.c_void_p(d_gs.data_ptr()), C.c_void_p(d_guG.data_ptr()),
+                                                        C.c_void_p(d_out.data_ptr()), _stream_ptr(stream)))
+
+
+def projection_dev(d_in, d_out, d_dout, beta, eta, stream=None):
+    lib = _abi.load()
+    rc = lib.lks_projection_dev(d_in.numel(), beta, eta, C.c_void_p(d_in.data_ptr()),
+                                C.c_void_p(d_out.data_ptr()) if d_out is not None else None,
+                                C.c_void_p(d_dout.data_ptr()) if d_dout is not None else None, _stream_ptr(stream))
+    if rc != 0:
+        raise LKSError(rc, lib.lks_strerror(rc).decode())

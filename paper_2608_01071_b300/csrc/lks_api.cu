@@ -1,0 +1,1158 @@
+// Host runtime of the LKS solver: parameter validation, device memory plan, checkpoint scheduling
+// (full storage, sqrt(N) segments, binomial "revolve" schedule) and the C ABI of include/lks.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/lks.h"
+#include "lks_common.cuh"
+#include "lks_prep_kernels.cuh"
+#include "lks_step_kernels.cuh"
+
+using namespace lks;
+
+namespace {
+
+struct LksError {
+    int code;
+    std::string msg;
+};
+
+#define LKS_CUDA(call)                                                                                   \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess)                                                                           \
+            throw LksError{LKS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};              \
+    } while (0)
+
+#define LKS_LAUNCHED()                                                                                   \
+    do {                                                                                                 \
+        cudaError_t e_ = cudaGetLastError();                                                             \
+        if (e_ != cudaSuccess) throw LksError{LKS_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)}; \
+    } while (0)
+
+inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------------------------------------------------
+// Typed engine: launches of the templated kernels for one (precision, dimension, kernel width).
+// ------------------------------------------------------------------------------------------------
+struct Engine {
+    virtual ~Engine() {}
+    virtual dim3 block() const = 0;
+    virtual void fwd(const Geom& g, dim3 grid, const void* in, void* out, const void* kref, const Pose* pose,
+                     double* jslot, unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) = 0;
+    virtual void adj(const Geom& g, dim3 grid, const void* lam_in, void* lam_out, const void* prev, const void* cur,
+                     const void* kref, const Pose* pose, void* kbar, double* mslot, int src, cudaStream_t s) = 0;
+    virtual void gather(const Geom& g, const Pose* poses, const void* kbar, int n_first, int nsteps,
+                        long long kstride, double* dkref, cudaStream_t s) = 0;
+    virtual void kappa_ref(const DesignGeom& dg, const double* gt, double* gb, double* k64, void* k, cudaStream_t s) = 0;
+    virtual void init_state(const Geom& g, void* st, cudaStream_t s) = 0;
+    virtual void init_adjoint(const Geom& g, void* lam, cudaStream_t s) = 0;
+    virtual void export_state(const Geom& g, const void* st, double* p, double* u, cudaStream_t s) = 0;
+};
+
+template <typename T, int D, int HW>
+struct EngineT : Engine {
+    static constexpr int TX = 32, TY = (D == 2) ? 8 : 4, TZ = (D == 2) ? 1 : 4;
+    using TL = Tile<D, TX, TY, TZ>;
+    static constexpr size_t smem_fwd = sizeof(T) * ((D + 1) * TL::S + (1 + NSym<D>::value) * TL::M);
+    static constexpr size_t smem_adj = sizeof(T) * ((D + 1) * TL::S + (1 + D + NSym<D>::value) * TL::M);
+
+    EngineT() {
+        LKS_CUDA(cudaFuncSetAttribute(fwd_step_kernel<T, D, HW, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem_fwd));
+        LKS_CUDA(cudaFuncSetAttribute(adj_step_kernel<T, D, HW, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem_adj));
+    }
+    dim3 block() const override { return dim3(TX, TY, TZ); }
+    void fwd(const Geom& g, dim3 grid, const void* in, void* out, const void* kref, const Pose* pose, double* jslot,
+             unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) override {
+        FwdArgs<T> a;
+        for (int i = 0; i < 3; ++i) {
+            a.jb_lo[i] = jlo[i];
+            a.jb_n[i] = jn[i];
+        }
+        a.in = (const T*)in;
+        a.out_p = (T*)out;
+        a.out_u = (T*)out + g.N;
+        a.kref = (const T*)kref;
+        a.pose = pose;
+        a.jslot = jslot;
+        a.flag = flag;
+        fwd_step_kernel<T, D, HW, TX, TY, TZ><<<grid, block(), smem_fwd, s>>>(g, a);
+        LKS_LAUNCHED();
+    }
+    void adj(const Geom& g, dim3 grid, const void* lam_in, void* lam_out, const void* prev, const void* cur,
+             const void* kref, const Pose* pose, void* kbar, double* mslot, int src, cudaStream_t s) override {
+        AdjArgs<T> a;
+        a.lam_in = (const T*)lam_in;
+        a.lam_out = (T*)lam_out;
+        a.u_prev = (const T*)prev + g.N;
+        a.u_cur = (const T*)cur + g.N;
+        a.kref = (const T*)kref;
+        a.pose = pose;
+        a.kbar = (T*)kbar;
+        a.mslot = mslot;
+        a.src = src;
+        adj_step_kernel<T, D, HW, TX, TY, TZ><<<grid, block(), smem_adj, s>>>(g, a);
+        LKS_LAUNCHED();
+    }
+    void gather(const Geom& g, const Pose* poses, const void* kbar, int n_first, int nsteps, long long kstride,
+                double* dkref, cudaStream_t s) override {
+        const long long nd = (long long)g.nde[0] * g.nde[1] * g.nde[2];
+        design_gather_kernel<T, D, HW><<<nblk(nd, 128), 128, 0, s>>>(g, poses, (const T*)kbar, n_first, nsteps, kstride, dkref);
+        LKS_LAUNCHED();
+    }
+    void kappa_ref(const DesignGeom& dg, const double* gt, double* gb, double* k64, void* k, cudaStream_t s) override {
+        const long long ne = (long long)dg.nde[0] * dg.nde[1] * dg.nde[2];
+        kappa_ref_kernel<T><<<nblk(ne, 256), 256, 0, s>>>(dg, gt, gb, k64, (T*)k);
+        LKS_LAUNCHED();
+    }
+    void init_state(const Geom& g, void* st, cudaStream_t s) override {
+        init_state_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, (T*)st);
+        LKS_LAUNCHED();
+    }
+    void init_adjoint(const Geom& g, void* lam, cudaStream_t s) override {
+        init_adjoint_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, (T*)lam);
+        LKS_LAUNCHED();
+    }
+    void export_state(const Geom& g, const void* st, double* p, double* u, cudaStream_t s) override {
+        export_state_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, (const T*)st, p, u);
+        LKS_LAUNCHED();
+    }
+};
+
+template <typename T, int D>
+Engine* make_engine_hw(int hw) {
+    if (hw == 1) return new EngineT<T, D, 1>();
+    return new EngineT<T, D, 2>();
+}
+
+Engine* make_engine(int precision, int D, int hw) {
+    if (precision == LKS_FP64) return D == 2 ? make_engine_hw<double, 2>(hw) : make_engine_hw<double, 3>(hw);
+    return D == 2 ? make_engine_hw<float, 2>(hw) : make_engine_hw<float, 3>(hw);
+}
+
+// Binomial coefficient C(c + r, c), saturating.
+long long binom_beta(int c, int r) {
+    long double v = 1.0L;
+    for (int i = 1; i <= c; ++i) {
+        v = v * (long double)(r + i) / (long double)i;
+        if (v > 1e15L) return (long long)1e15;
+    }
+    return (long long)(v + 0.5L);
+}
+
+// Position of the next checkpoint inside l segments with c free slots (binomial schedule).
+int binom_split(int l, int c) {
+    int r = 0;
+    while (binom_beta(c, r) < l) ++r;
+    long long lo = std::max<long long>(1, (long long)l - binom_beta(c - 1, r));
+    long long hi = std::min<long long>(l - 1, binom_beta(c, r - 1));
+    return (int)std::max(lo, hi);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// Context
+// ------------------------------------------------------------------------------------------------
+struct lks_ctx {
+    lks_params prm;
+    Geom g;
+    DesignGeom dg;
+    MotionGeom mg;
+    int D = 2, hw = 1, cosine = 0;
+    double o0[3] = {0, 0, 0};
+    size_t tsize = 8;
+    std::unique_ptr<Engine> eng;
+    dim3 grid, block;
+    int nblocks = 0;
+    long long nd = 0, nde = 0;
+    std::string err;
+    lks_stats stats;
+
+    // device memory
+    std::vector<void*> allocs;
+    double *d_gamma = nullptr, *d_gt = nullptr, *d_gb = nullptr, *d_kref64 = nullptr, *d_fnorm = nullptr,
+           *d_tmp = nullptr;
+    void* d_kref = nullptr;
+    double *d_knots = nullptr, *d_filt = nullptr, *d_s = nullptr, *d_uG = nullptr, *d_ktmp = nullptr;
+    double *d_out_g = nullptr, *d_out_k = nullptr;  // host-pointer adjoint staging
+    Pose* d_pose = nullptr;
+    double *d_gs = nullptr, *d_guG = nullptr, *d_dkref = nullptr, *d_jslot = nullptr, *d_jstep = nullptr,
+           *d_J = nullptr;
+    unsigned* d_flag = nullptr;
+    unsigned* h_flag = nullptr;  // pinned
+    cudaEvent_t ev_flag = nullptr;
+    void* d_kbar = nullptr;
+    double* d_mslot = nullptr;
+    size_t state_bytes = 0;
+    std::vector<void*> slot;  // checkpoint slots
+    std::vector<void*> hist;  // recompute history (index 0 unused)
+    void* pp[2] = {nullptr, nullptr};
+    void* tmp_state = nullptr;
+    void* fin = nullptr;
+    void* lam[2] = {nullptr, nullptr};
+
+    // schedule
+    int S = 1;             // boundary spacing (segment length)
+    int M = 1;             // number of segments
+    int Lmax = 1;          // longest segment (sensitivity buffer depth)
+    int free_slots = 0;    // REVOLVE: slots besides boundary 0
+    std::vector<int> chain;  // REVOLVE: boundaries stored by the forward sweep (after 0)
+    std::vector<int> slot_of;  // boundary -> slot index or -1
+    std::vector<int> slot_used;
+
+    bool have_forward = false;
+    long long launches = 0;
+    long long launches_fwd = 0, launches_adj = 0;
+
+    // CUDA graphs of the forward sweep and of the reverse sweep (captured once, replayed every call)
+    bool use_graphs = true;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gx_fwd = nullptr, gx_adj = nullptr;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> spans_fwd, spans_adj;
+
+    // optional CUDA-event timing of the step kernels
+    bool timing = false;
+    std::vector<cudaEvent_t> evpool;
+    size_t evnext = 0;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> spans;  // (kind, (start, end))
+    cudaEvent_t ev_all0 = nullptr, ev_end = nullptr;
+
+    int step_of(int m) const { return std::min(m * S, prm.Nt); }
+    void* state_ptr_stored(int m) const {  // state of boundary m if stored
+        if (m == M) return fin;
+        int si = slot_of[m];
+        return si >= 0 ? slot[si] : nullptr;
+    }
+    char* tptr(void* p, long long off) const { return (char*)p + off * (long long)tsize; }
+};
+
+namespace {
+
+void set_err(lks_ctx* c, const LksError& e) {
+    if (c) c->err = e.msg;
+}
+
+void* dalloc(lks_ctx* c, size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw LksError{LKS_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e)};
+    }
+    c->allocs.push_back(p);
+    c->stats.device_bytes += (int64_t)bytes;
+    return p;
+}
+
+void validate(const lks_params* p) {
+    auto bad = [](const std::string& m) { throw LksError{LKS_EINVAL, m}; };
+    if (!p) bad("params is NULL");
+    if (p->size != sizeof(lks_params)) bad("params.size does not match this library's lks_params");
+    if (p->lattice != LKS_D2Q9 && p->lattice != LKS_D3Q15) bad("lattice must be LKS_D2Q9 or LKS_D3Q15");
+    const int D = p->lattice == LKS_D2Q9 ? 2 : 3;
+    for (int a = 0; a < 3; ++a) {
+        if (a < D && (p->n[a] < 4 || p->n[a] > (1 << 20))) bad("grid extent out of range [4, 2^20]");
+        if (a >= D && p->n[a] != 1) bad("n[2] must be 1 for D2Q9");
+        if (a < D && (p->nd[a] < 1)) bad("design extent must be >= 1");
+        if (a >= D && p->nd[a] != 1) bad("nd[2] must be 1 for D2Q9");
+    }
+    long long N = (long long)p->n[0] * p->n[1] * p->n[2];
+    if (N > (1LL << 31)) bad("grid too large");
+    if (!(p->nu > 0.0) || !(p->nu < 1.0)) bad("nu must be in (0, 1)");
+    if (!(p->kappa_max >= 0.0) || !(p->q > 0.0)) bad("kappa_max >= 0 and q > 0 required");
+    if (p->margin < 0 || p->margin > 64) bad("margin out of range");
+    if (p->map_kernel != LKS_MAP_LINEAR && p->map_kernel != LKS_MAP_COSINE) bad("unknown map_kernel");
+    const int hw = p->map_kernel == LKS_MAP_LINEAR ? 1 : 2;
+    for (int a = 0; a < D; ++a) {
+        const int nde = p->nd[a] + 2 * p->margin;
+        if (p->periodic[a] && nde + 2 * hw > p->n[a])
+            bad("design grid plus kernel support must fit in one period of a periodic axis");
+        if (p->probe_lo[a] < 0 || p->probe_hi[a] > p->n[a] || p->probe_lo[a] >= p->probe_hi[a])
+            bad("probe box must satisfy 0 <= lo < hi <= n");
+    }
+    if (p->Nt < 1 || p->Nt > 10000000) bad("Nt out of range");
+    if (p->K < 2 || p->K > 1000000) bad("K must be >= 2");
+    if (!(p->R_t > 0.0)) bad("R_t must be > 0");
+    if (!(p->filter_R >= 0.0) || p->filter_R > 32.0) bad("filter_R out of range [0, 32]");
+    if (!(p->beta >= 0.0) || !(p->eta > 0.0 && p->eta < 1.0)) bad("beta >= 0 and 0 < eta < 1 required");
+    if (p->precision != LKS_FP64 && p->precision != LKS_FP32) bad("unknown precision");
+    if (p->ckpt < LKS_CKPT_FULL || p->ckpt > LKS_CKPT_REVOLVE) bad("unknown ckpt");
+    if (p->mode < LKS_MODE_JOINT || p->mode > LKS_MODE_MOTION) bad("unknown mode");
+    if (p->ckpt_slots < 0 || p->seg_len < 0 || p->ckpt_bytes < 0) bad("negative checkpoint setting");
+}
+
+void setup_geometry(lks_ctx* c) {
+    const lks_params& p = c->prm;
+    c->D = p.lattice == LKS_D2Q9 ? 2 : 3;
+    c->hw = p.map_kernel == LKS_MAP_LINEAR ? 1 : 2;
+    c->cosine = p.map_kernel == LKS_MAP_COSINE;
+    c->tsize = p.precision == LKS_FP64 ? 8 : 4;
+    Geom& g = c->g;
+    std::memset(&g, 0, sizeof(g));
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = p.n[a];
+        g.periodic[a] = a < c->D ? (p.periodic[a] ? 1 : 0) : 1;
+        g.nde[a] = a < c->D ? p.nd[a] + 2 * p.margin : 1;
+        g.Fb[a] = a < c->D ? g.nde[a] + 2 * c->hw - 1 : 1;
+        g.probe_lo[a] = a < c->D ? p.probe_lo[a] : 0;
+        g.probe_hi[a] = a < c->D ? p.probe_hi[a] : 1;
+        g.dir[a] = a < c->D ? p.direction[a] : 0.0;
+        for (int s = 0; s < 2; ++s)
+            for (int b = 0; b < 3; ++b) g.wall_u[a][s][b] = p.wall_velocity[a][s][b];
+    }
+    g.N = (long long)p.n[0] * p.n[1] * p.n[2];
+    g.hw = c->hw;
+    g.Fbn = (long long)g.Fb[0] * g.Fb[1] * g.Fb[2];
+    g.A = 0.75 - 4.5 * p.nu;
+    g.u_crit2 = p.u_crit > 0.0 ? p.u_crit * p.u_crit : 0.0;
+    // |O| counts probe nodes off the walls
+    long long cnt = 1;
+    for (int a = 0; a < c->D; ++a) {
+        int lo = p.probe_lo[a], hi = p.probe_hi[a];
+        if (!g.periodic[a]) {
+            lo = std::max(lo, 1);
+            hi = std::min(hi, p.n[a] - 1);
+        }
+        cnt *= std::max(0, hi - lo);
+    }
+    if (cnt <= 0) throw LksError{LKS_EINVAL, "probe box holds no fluid node"};
+    g.phi = 1.0 / ((double)p.Nt * (double)cnt);
+    for (int a = 0; a < c->D; ++a) {
+        const double center = std::isnan(p.base_center[a]) ? (p.n[a] - 1) / 2.0 : p.base_center[a];
+        c->o0[a] = center - (g.nde[a] - 1) / 2.0;
+    }
+    DesignGeom& dg = c->dg;
+    for (int a = 0; a < 3; ++a) {
+        dg.nd[a] = p.nd[a];
+        dg.nde[a] = g.nde[a];
+    }
+    dg.margin = p.margin;
+    dg.R = p.filter_R;
+    dg.beta = p.beta;
+    dg.eta = p.eta;
+    dg.kappa_max = p.kappa_max;
+    dg.q = p.q;
+    c->mg.K = p.K;
+    c->mg.d = c->D;
+    c->mg.Nt = p.Nt;
+    c->mg.R_t = p.R_t;
+    c->nd = (long long)p.nd[0] * p.nd[1] * p.nd[2];
+    c->nde = (long long)g.nde[0] * g.nde[1] * g.nde[2];
+}
+
+// Checkpoint layout: boundaries every S steps; FULL keeps every state, SQRT every ceil(sqrt Nt)-th,
+// REVOLVE keeps boundary 0 plus a binomial schedule over M segments of length S with free_slots slots.
+void plan_checkpoints(lks_ctx* c, size_t state_bytes) {
+    const lks_params& p = c->prm;
+    const int Nt = p.Nt;
+    if (p.ckpt == LKS_CKPT_FULL) {
+        c->S = 1;
+    } else if (p.seg_len > 0) {
+        c->S = std::min(p.seg_len, Nt);
+    } else {
+        c->S = std::max(1, (int)std::ceil(std::sqrt((double)Nt)));
+    }
+    c->M = (Nt + c->S - 1) / c->S;
+    c->Lmax = p.ckpt == LKS_CKPT_FULL ? std::min(Nt, 256) : c->S;
+    int nslots;
+    if (p.ckpt == LKS_CKPT_REVOLVE) {
+        int freec = p.ckpt_slots;
+        if (freec == 0) {
+            // budget: slots + history (S + 1) + 2 ping-pong + tmp + final + 2 adjoint states
+            long long fixed = (long long)(c->S + 1 + 2 + 1 + 1 + 2) * (long long)state_bytes;
+            long long avail = p.ckpt_bytes > 0 ? p.ckpt_bytes - fixed : 0;
+            freec = (int)std::max<long long>(1, avail / (long long)state_bytes - 1);
+        }
+        freec = std::max(1, std::min(freec, c->M - 1 > 0 ? c->M - 1 : 1));
+        c->free_slots = freec;
+        nslots = 1 + freec;
+        // right spine of the recursion: boundaries the forward sweep stores
+        c->chain.clear();
+        int a = 0, b = c->M, f = freec;
+        while (b - a > 1 && f > 0) {
+            int m = a + binom_split(b - a, f);
+            c->chain.push_back(m);
+            a = m;
+            --f;
+        }
+    } else {
+        // FULL: every state; SQRT: boundaries 0, S, 2S, ... below Nt
+        nslots = c->M;
+    }
+    c->slot_of.assign(c->M + 1, -1);
+    c->slot_used.assign(nslots, 0);
+    (void)nslots;
+}
+
+int njb_of(const lks_ctx* c);
+
+void allocate(lks_ctx* c) {
+    const lks_params& p = c->prm;
+    const int D = c->D;
+    const long long N = c->g.N;
+    const size_t ts = c->tsize;
+    c->state_bytes = (size_t)(D + 1) * N * ts;
+    plan_checkpoints(c, c->state_bytes);
+
+    c->d_gamma = (double*)dalloc(c, c->nd * 8);
+    c->d_gt = (double*)dalloc(c, c->nd * 8);
+    c->d_gb = (double*)dalloc(c, c->nd * 8);
+    c->d_fnorm = (double*)dalloc(c, c->nd * 8);
+    c->d_tmp = (double*)dalloc(c, c->nd * 8);
+    c->d_kref64 = (double*)dalloc(c, c->nde * 8);
+    c->d_kref = dalloc(c, c->nde * ts);
+    c->d_dkref = (double*)dalloc(c, c->nde * 8);
+    c->d_knots = (double*)dalloc(c, (size_t)p.K * D * 8);
+    c->d_filt = (double*)dalloc(c, (size_t)p.K * D * 8);
+    c->d_ktmp = (double*)dalloc(c, (size_t)p.K * D * 8);
+    c->d_s = (double*)dalloc(c, (size_t)(p.Nt + 1) * D * 8);
+    c->d_uG = (double*)dalloc(c, (size_t)(p.Nt + 1) * D * 8);
+    c->d_gs = (double*)dalloc(c, (size_t)(p.Nt + 1) * D * 8);
+    c->d_guG = (double*)dalloc(c, (size_t)(p.Nt + 1) * D * 8);
+    c->d_pose = (Pose*)dalloc(c, (size_t)(p.Nt + 1) * sizeof(Pose));
+    c->d_jslot = (double*)dalloc(c, (size_t)(p.Nt + 1) * njb_of(c) * 8);
+    c->d_out_g = (double*)dalloc(c, c->nd * 8);
+    c->d_out_k = (double*)dalloc(c, (size_t)p.K * D * 8);
+    c->d_jstep = (double*)dalloc(c, (size_t)(p.Nt + 1) * 8);
+    c->d_J = (double*)dalloc(c, 8);
+    c->d_flag = (unsigned*)dalloc(c, 16);
+    c->d_kbar = dalloc(c, (size_t)c->Lmax * c->g.Fbn * ts);
+    c->d_mslot = (double*)dalloc(c, (size_t)c->Lmax * c->nblocks * 2 * D * 8);
+
+    const size_t sb = c->state_bytes;
+    c->slot.resize(c->slot_used.size());
+    for (auto& s : c->slot) s = dalloc(c, sb);
+    c->hist.assign(c->S + 1, nullptr);
+    if (p.ckpt != LKS_CKPT_FULL)
+        for (int k = 1; k <= c->S; ++k) c->hist[k] = dalloc(c, sb);
+    c->pp[0] = dalloc(c, sb);
+    c->pp[1] = dalloc(c, sb);
+    c->tmp_state = dalloc(c, sb);
+    c->fin = dalloc(c, sb);
+    c->lam[0] = dalloc(c, sb);
+    c->lam[1] = dalloc(c, sb);
+    c->stats.ckpt_slots = (int32_t)c->slot.size();
+    c->stats.seg_len = c->S;
+
+    LKS_CUDA(cudaHostAlloc((void**)&c->h_flag, 16, cudaHostAllocDefault));
+    *c->h_flag = 0;
+    LKS_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    LKS_CUDA(cudaEventCreateWithFlags(&c->ev_flag, cudaEventDisableTiming));
+    LKS_CUDA(cudaMemset(c->d_jslot, 0, (size_t)(p.Nt + 1) * njb_of(c) * 8));
+    filter_norm_kernel<<<nblk(c->nd, 128), 128>>>(c->dg, c->d_fnorm);
+    LKS_LAUNCHED();
+    LKS_CUDA(cudaDeviceSynchronize());
+}
+
+cudaEvent_t next_event(lks_ctx* c) {
+    if (c->evnext == c->evpool.size()) return nullptr;  // pool exhausted: the span goes untimed
+    return c->evpool[c->evnext++];
+}
+
+// Mark the start of a timed span of one kind (0 forward steps, 1 recompute, 2 adjoint steps).
+cudaEvent_t span_begin(lks_ctx* c, cudaStream_t s) {
+    if (!c->timing) return nullptr;
+    cudaEvent_t e = next_event(c);
+    if (e) LKS_CUDA(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+    return e;
+}
+
+void span_end(lks_ctx* c, int kind, cudaEvent_t e0, cudaStream_t s) {
+    if (!c->timing || !e0) return;
+    cudaEvent_t e1 = next_event(c);
+    if (!e1) return;
+    LKS_CUDA(cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal));
+    c->spans.push_back({kind, {e0, e1}});
+}
+
+// Run `body(stream)` eagerly, or capture it once into a graph on the internal stream and replay it on s.
+template <typename F>
+void run_graph(lks_ctx* c, cudaGraphExec_t& gx, cudaStream_t s, F&& body) {
+    if (!c->use_graphs) {
+        body(s);
+        return;
+    }
+    if (!gx) {
+        LKS_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        try {
+            body(c->cap);
+        } catch (...) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(c->cap, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            throw;
+        }
+        cudaGraph_t g = nullptr;
+        LKS_CUDA(cudaStreamEndCapture(c->cap, &g));
+        cudaError_t e = cudaGraphInstantiate(&gx, g, 0);
+        cudaGraphDestroy(g);
+        LKS_CUDA(e);
+    }
+    LKS_CUDA(cudaGraphLaunch(gx, s));
+}
+
+void drop_graphs(lks_ctx* c) {
+    if (c->gx_fwd) cudaGraphExecDestroy(c->gx_fwd);
+    if (c->gx_adj) cudaGraphExecDestroy(c->gx_adj);
+    c->gx_fwd = c->gx_adj = nullptr;
+    c->evnext = 0;
+    c->spans_fwd.clear();
+    c->spans_adj.clear();
+}
+
+void free_all(lks_ctx* c) {
+    drop_graphs(c);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    c->cap = nullptr;
+    for (auto e : c->evpool) cudaEventDestroy(e);
+    c->evpool.clear();
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    if (c->h_flag) cudaFreeHost(c->h_flag);
+    c->h_flag = nullptr;
+    if (c->ev_flag) cudaEventDestroy(c->ev_flag);
+    c->ev_flag = nullptr;
+    if (c->ev_end) cudaEventDestroy(c->ev_end);
+    c->ev_end = nullptr;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Forward and reverse sweeps
+// ------------------------------------------------------------------------------------------------
+void prepare_design_and_motion(lks_ctx* c, cudaStream_t s) {
+    // a0: gamma -> gamma~ -> gamma-bar -> kappa^ref
+    density_filter_kernel<<<nblk(c->nd, 128), 128, 0, s>>>(c->dg, c->d_gamma, c->d_fnorm, c->d_gt, 0);
+    LKS_LAUNCHED();
+    c->eng->kappa_ref(c->dg, c->d_gt, c->d_gb, c->d_kref64, c->d_kref, s);
+    // a1: knots -> filtered -> s_n, u^G_n -> per-step pose
+    const int K = c->prm.K, D = c->D, Nt = c->prm.Nt;
+    motion_filter_kernel<<<nblk((long long)K * D, 128), 128, 0, s>>>(c->mg, c->d_knots, c->d_filt, 0);
+    LKS_LAUNCHED();
+    interp_kernel<<<nblk((long long)(Nt + 1) * D, 256), 256, 0, s>>>(c->mg, c->d_filt, c->d_s, c->d_uG);
+    LKS_LAUNCHED();
+    pose_kernel<<<nblk(Nt + 1, 128), 128, 0, s>>>(c->g, D, c->o0[0], c->o0[1], c->o0[2], c->cosine, Nt, c->d_s, c->d_uG,
+                                                  c->d_pose);
+    LKS_LAUNCHED();
+    c->launches += 5;
+}
+
+void fwd_step(lks_ctx* c, int n, const void* in, void* out, bool objective, cudaStream_t s);
+
+}  // namespace
+
+// probe-block window of the forward kernel's objective slots
+static void probe_blocks(const lks_ctx* c, int lo[3], int cnt[3]) {
+    const int T[3] = {(int)c->block.x, (int)c->block.y, (int)c->block.z};
+    const int G[3] = {(int)c->grid.x, (int)c->grid.y, (int)c->grid.z};
+    for (int a = 0; a < 3; ++a) {
+        if (a >= c->D) {
+            lo[a] = 0;
+            cnt[a] = 1;
+            continue;
+        }
+        int b0 = c->g.probe_lo[a] / T[a];
+        int b1 = (c->g.probe_hi[a] - 1) / T[a];
+        b1 = std::min(b1, G[a] - 1);
+        lo[a] = b0;
+        cnt[a] = b1 - b0 + 1;
+    }
+}
+
+namespace {
+
+int njb_of(const lks_ctx* c) {
+    int lo[3], cnt[3];
+    probe_blocks(c, lo, cnt);
+    return cnt[0] * cnt[1] * cnt[2];
+}
+
+void fwd_step(lks_ctx* c, int n, const void* in, void* out, bool objective, cudaStream_t s) {
+    int lo[3], cnt[3];
+    probe_blocks(c, lo, cnt);
+    const int njb = cnt[0] * cnt[1] * cnt[2];
+    c->eng->fwd(c->g, c->grid, in, out, c->d_kref, c->d_pose + n,
+                objective ? c->d_jslot + (long long)n * njb : nullptr, c->d_flag, lo, cnt, s);
+    c->launches++;
+}
+
+void forward_body(lks_ctx* c, cudaStream_t s);
+
+void run_forward(lks_ctx* c, cudaStream_t s) {
+    if (c->use_graphs && !c->gx_fwd) {
+        // a new forward capture starts a new timing-event layout; the reverse sweep is re-captured after it
+        drop_graphs(c);
+    }
+    run_graph(c, c->gx_fwd, s, [&](cudaStream_t cs) { forward_body(c, cs); });
+    LKS_CUDA(cudaEventRecord(c->ev_flag, s));
+    if (!c->use_graphs) c->spans_fwd = c->spans;
+    c->stats.forward_steps = c->prm.Nt;
+    c->have_forward = true;
+}
+
+void forward_body(lks_ctx* c, cudaStream_t s) {
+    const int Nt = c->prm.Nt;
+    c->launches = 0;
+    if (!c->use_graphs) c->evnext = 0;
+    c->spans.clear();
+    cudaEvent_t eall = span_begin(c, s);
+    c->ev_all0 = eall;
+    prepare_design_and_motion(c, s);
+    LKS_CUDA(cudaMemsetAsync(c->d_flag, 0, 4, s));
+    // boundary 0 lives in slot 0
+    std::fill(c->slot_of.begin(), c->slot_of.end(), -1);
+    std::fill(c->slot_used.begin(), c->slot_used.end(), 0);
+    c->slot_of[0] = 0;
+    c->slot_used[0] = 1;
+    std::vector<char> store(c->M + 1, 0);
+    if (c->prm.ckpt == LKS_CKPT_REVOLVE) {
+        for (int m : c->chain) store[m] = 1;
+    } else {
+        for (int m = 1; m < c->M; ++m) store[m] = 1;
+    }
+    c->eng->init_state(c->g, c->slot[0], s);
+    c->launches++;
+    const void* cur = c->slot[0];
+    int ppi = 0;
+    cudaEvent_t e0 = span_begin(c, s);
+    for (int n = 1; n <= Nt; ++n) {
+        void* out;
+        if (n == Nt) {
+            out = c->fin;
+        } else if (n % c->S == 0 && store[n / c->S]) {
+            const int m = n / c->S;
+            const int si = (int)(std::find(c->slot_used.begin(), c->slot_used.end(), 0) - c->slot_used.begin());
+            if (si >= (int)c->slot.size()) throw LksError{LKS_ESTATE, "internal: out of checkpoint slots"};
+            c->slot_used[si] = 1;
+            c->slot_of[m] = si;
+            out = c->slot[si];
+        } else {
+            out = c->pp[ppi];
+            ppi ^= 1;
+        }
+        fwd_step(c, n, cur, out, true, s);
+        cur = out;
+    }
+    span_end(c, 0, e0, s);
+    objective_reduce_kernel<<<1, 256, 0, s>>>(c->d_jslot, njb_of(c), Nt, c->g.phi, c->d_jstep, c->d_J);
+    LKS_LAUNCHED();
+    c->launches++;
+    LKS_CUDA(cudaMemcpyAsync(c->h_flag, c->d_flag, 4, cudaMemcpyDeviceToHost, s));
+    c->launches_fwd = c->launches;
+    c->spans_fwd = c->spans;
+}
+
+// Advance from the state at step n0 (pointer in) to step n1, writing the final state to out (out != in).
+void advance(lks_ctx* c, int n0, int n1, const void* in, void* out, cudaStream_t s) {
+    cudaEvent_t e0 = span_begin(c, s);
+    const void* cur = in;
+    int ppi = (in == c->pp[0]) ? 1 : 0;
+    for (int n = n0 + 1; n <= n1; ++n) {
+        void* dst = (n == n1) ? out : c->pp[ppi];
+        if (n != n1) ppi ^= 1;
+        fwd_step(c, n, cur, dst, false, s);
+        cur = dst;
+        c->stats.recompute_steps++;
+    }
+    span_end(c, 1, e0, s);
+}
+
+// Reverse one segment (steps a+1..b): rebuild the states a+1..b that are not stored, then run the adjoint
+// steps n = b..a+1 and fold the segment's local sensitivities into the design and motion gradients.
+void do_segment(lks_ctx* c, int a, int b, const void* start, const void* end, cudaStream_t s) {
+    const int L = b - a;
+    std::vector<const void*> st(L + 1, nullptr);
+    st[0] = start;
+    const bool full = c->prm.ckpt == LKS_CKPT_FULL;
+    cudaEvent_t er = full ? nullptr : span_begin(c, s);
+    for (int j = 1; j <= L; ++j) {
+        if (j == L && end != nullptr) {
+            st[j] = end;
+        } else if (full) {
+            const int m = a + j;  // every state is a stored boundary in FULL mode
+            st[j] = (m == c->prm.Nt) ? c->fin : c->slot[c->slot_of[m]];
+        } else {
+            fwd_step(c, a + j, st[j - 1], c->hist[j], false, s);
+            st[j] = c->hist[j];
+            c->stats.recompute_steps++;
+        }
+    }
+    span_end(c, 1, er, s);
+    const int mode = c->prm.mode;
+    const bool shape = mode != LKS_MODE_MOTION, motion = mode != LKS_MODE_SHAPE;
+    const long long kstride = c->g.Fbn;
+    cudaEvent_t ea = span_begin(c, s);
+    const long long mstride = (long long)c->nblocks * 2 * c->D;
+    for (int n = b; n > a; --n) {
+        const int j = n - a - 1;  // sensitivity slot of step n
+        void* kb = shape ? c->tptr(c->d_kbar, (long long)j * kstride) : nullptr;
+        double* ms = motion ? c->d_mslot + (long long)j * mstride : nullptr;
+        c->eng->adj(c->g, c->grid, c->lam[0], c->lam[1], st[n - 1 - a], st[n - a], c->d_kref, c->d_pose + n, kb, ms,
+                    n - 1 >= 1 ? 1 : 0, s);
+        std::swap(c->lam[0], c->lam[1]);
+        c->launches++;
+        c->stats.adjoint_steps++;
+    }
+    span_end(c, 2, ea, s);
+    if (shape) {
+        c->eng->gather(c->g, c->d_pose, c->d_kbar, a + 1, L, kstride, c->d_dkref, s);
+        c->launches++;
+    }
+    if (motion) {
+        if (c->D == 2)
+            motion_reduce_kernel<2><<<L, 32, 0, s>>>(c->g, c->block.x, c->block.y, c->block.z, c->grid.x, c->grid.y,
+                                                     c->grid.z, c->d_pose, c->d_mslot, mstride, a + 1, L, c->d_gs, c->d_guG);
+        else
+            motion_reduce_kernel<3><<<L, 32, 0, s>>>(c->g, c->block.x, c->block.y, c->block.z, c->grid.x, c->grid.y,
+                                                     c->grid.z, c->d_pose, c->d_mslot, mstride, a + 1, L, c->d_gs, c->d_guG);
+        LKS_LAUNCHED();
+        c->launches++;
+    }
+}
+
+int take_slot(lks_ctx* c) {
+    for (size_t i = 0; i < c->slot_used.size(); ++i)
+        if (!c->slot_used[i]) {
+            c->slot_used[i] = 1;
+            return (int)i;
+        }
+    throw LksError{LKS_ESTATE, "internal: out of checkpoint slots"};
+}
+
+// Binomial reverse sweep over segments [ma, mb) with the state of boundary ma at `ap` and `freec` free slots.
+void reverse_revolve(lks_ctx* c, int ma, int mb, int freec, const void* ap, cudaStream_t s) {
+    const int a = c->step_of(ma);
+    if (mb - ma == 1) {
+        do_segment(c, a, c->step_of(mb), ap, mb == c->M ? c->fin : nullptr, s);
+        return;
+    }
+    if (freec == 0) {
+        for (int m = mb - 1; m >= ma; --m) {
+            const void* sp = ap;
+            if (m > ma) {
+                advance(c, a, c->step_of(m), ap, c->tmp_state, s);
+                sp = c->tmp_state;
+            }
+            do_segment(c, c->step_of(m), c->step_of(m + 1), sp, m + 1 == c->M ? c->fin : nullptr, s);
+        }
+        return;
+    }
+    const int mm = ma + binom_split(mb - ma, freec);
+    int si = c->slot_of[mm];
+    if (si < 0) {
+        si = take_slot(c);
+        c->slot_of[mm] = si;
+        advance(c, a, c->step_of(mm), ap, c->slot[si], s);
+    }
+    reverse_revolve(c, mm, mb, freec - 1, c->slot[si], s);
+    c->slot_used[si] = 0;
+    c->slot_of[mm] = -1;
+    reverse_revolve(c, ma, mm, freec, ap, s);
+}
+
+void adjoint_body(lks_ctx* c, cudaStream_t s);
+
+void run_adjoint(lks_ctx* c, cudaStream_t s) {
+    if (!c->have_forward) throw LksError{LKS_ESTATE, "lks_adjoint needs a preceding lks_forward"};
+    LKS_CUDA(cudaEventSynchronize(c->ev_flag));
+    if (*c->h_flag) throw LksError{LKS_EUNSTABLE, "forward sweep unstable: non-finite velocity or |u| > u_crit"};
+    run_graph(c, c->gx_adj, s, [&](cudaStream_t cs) { adjoint_body(c, cs); });
+    if (!c->use_graphs) c->spans_adj = c->spans;
+    // the binomial schedule reuses the forward's checkpoint slots: a new forward must precede the next adjoint
+    if (c->prm.ckpt == LKS_CKPT_REVOLVE) c->have_forward = false;
+}
+
+void adjoint_body(lks_ctx* c, cudaStream_t s) {
+    const int Nt = c->prm.Nt, D = c->D, K = c->prm.K;
+    c->launches = 0;
+    c->spans.clear();
+    c->stats.recompute_steps = 0;
+    c->stats.adjoint_steps = 0;
+    LKS_CUDA(cudaMemsetAsync(c->d_dkref, 0, c->nde * 8, s));
+    LKS_CUDA(cudaMemsetAsync(c->d_gs, 0, (size_t)(Nt + 1) * D * 8, s));
+    LKS_CUDA(cudaMemsetAsync(c->d_guG, 0, (size_t)(Nt + 1) * D * 8, s));
+    c->eng->init_adjoint(c->g, c->lam[0], s);
+    c->launches++;
+    if (c->prm.ckpt == LKS_CKPT_REVOLVE) {
+        reverse_revolve(c, 0, c->M, c->free_slots, c->slot[0], s);
+    } else if (c->prm.ckpt == LKS_CKPT_FULL) {
+        for (int b = Nt; b > 0; b -= c->Lmax) {
+            const int a = std::max(0, b - c->Lmax);
+            do_segment(c, a, b, a == 0 ? c->slot[0] : c->slot[c->slot_of[a]], b == Nt ? c->fin : c->slot[c->slot_of[b]], s);
+        }
+    } else {
+        for (int m = c->M - 1; m >= 0; --m) {
+            const int a = c->step_of(m), b = c->step_of(m + 1);
+            do_segment(c, a, b, c->slot[c->slot_of[m]], m + 1 == c->M ? c->fin : c->slot[c->slot_of[m + 1]], s);
+        }
+    }
+    // b6: chain rules
+    design_chain_kernel<<<nblk(c->nd, 128), 128, 0, s>>>(c->dg, c->d_dkref, c->d_gt, c->d_gb, c->d_tmp);
+    LKS_LAUNCHED();
+    interp_T_kernel<<<nblk((long long)K * D, 64), 64, 0, s>>>(c->mg, c->d_gs, c->d_guG, c->d_ktmp);
+    LKS_LAUNCHED();
+    c->launches += 2;
+    c->launches_adj = c->launches;
+    c->spans_adj = c->spans;
+    (void)K;
+}
+
+// Final gradients into caller buffers (device pointers), honouring the gradient mode.
+void finish_adjoint(lks_ctx* c, double* dgamma, double* dpos, cudaStream_t s) {
+    const int K = c->prm.K, D = c->D;
+    c->launches = 0;
+    if (dgamma) {
+        if (c->prm.mode == LKS_MODE_MOTION) {
+            LKS_CUDA(cudaMemsetAsync(dgamma, 0, c->nd * 8, s));
+        } else {
+            density_filter_kernel<<<nblk(c->nd, 128), 128, 0, s>>>(c->dg, c->d_tmp, c->d_fnorm, dgamma, 1);
+            LKS_LAUNCHED();
+            c->launches++;
+        }
+    }
+    if (dpos) {
+        if (c->prm.mode == LKS_MODE_SHAPE) {
+            LKS_CUDA(cudaMemsetAsync(dpos, 0, (size_t)K * D * 8, s));
+        } else {
+            motion_filter_kernel<<<nblk((long long)K * D, 64), 64, 0, s>>>(c->mg, c->d_ktmp, dpos, 1);
+            LKS_LAUNCHED();
+            c->launches++;
+        }
+    }
+    c->stats.kernel_launches = c->launches_fwd + c->launches_adj + c->launches;
+    if (c->timing && c->ev_all0 && c->ev_end) {
+        LKS_CUDA(cudaEventRecord(c->ev_end, s));
+        LKS_CUDA(cudaEventSynchronize(c->ev_end));
+        double acc[3] = {0, 0, 0};
+        for (auto* v : {&c->spans_fwd, &c->spans_adj})
+            for (auto& sp : *v) {
+                float ms = 0.f;
+                LKS_CUDA(cudaEventElapsedTime(&ms, sp.second.first, sp.second.second));
+                acc[sp.first] += ms;
+            }
+        float tot = 0.f;
+        LKS_CUDA(cudaEventElapsedTime(&tot, c->ev_all0, c->ev_end));
+        c->stats.ms_forward_steps = acc[0];
+        c->stats.ms_recompute_steps = acc[1];
+        c->stats.ms_adjoint_steps = acc[2];
+        c->stats.ms_total = tot;
+    }
+}
+
+template <typename F>
+int guard(lks_ctx* c, F&& f) {
+    try {
+        f();
+        return LKS_OK;
+    } catch (const LksError& e) {
+        set_err(c, e);
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        if (c) c->err = "host allocation failed";
+        return LKS_ENOMEM;
+    } catch (...) {
+        if (c) c->err = "unexpected exception";
+        return LKS_ECUDA;
+    }
+}
+
+thread_local std::string g_create_err;
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------------
+extern "C" {
+
+int lks_default_params(lks_params* p) {
+    if (!p) return LKS_EINVAL;
+    std::memset(p, 0, sizeof(*p));
+    p->size = sizeof(lks_params);
+    p->lattice = LKS_D2Q9;
+    p->n[0] = 64;
+    p->n[1] = 32;
+    p->n[2] = 1;
+    p->periodic[0] = 1;
+    p->periodic[1] = 0;
+    p->periodic[2] = 1;
+    p->nu = 0.02;
+    p->kappa_max = 1.0;
+    p->q = 0.1;
+    p->nd[0] = 8;
+    p->nd[1] = 8;
+    p->nd[2] = 1;
+    p->margin = 2;
+    p->map_kernel = LKS_MAP_LINEAR;
+    for (int a = 0; a < 3; ++a) p->base_center[a] = std::nan("");
+    p->probe_lo[0] = 40;
+    p->probe_lo[1] = 8;
+    p->probe_lo[2] = 0;
+    p->probe_hi[0] = 56;
+    p->probe_hi[1] = 24;
+    p->probe_hi[2] = 1;
+    p->direction[0] = 1.0;
+    p->Nt = 100;
+    p->K = 10;
+    p->R_t = 25.0;
+    p->filter_R = 0.0;
+    p->beta = 0.0;
+    p->eta = 0.5;
+    p->precision = LKS_FP64;
+    p->ckpt = LKS_CKPT_FULL;
+    p->mode = LKS_MODE_JOINT;
+    p->u_crit = 0.3;
+    return LKS_OK;
+}
+
+const char* lks_strerror(int status) {
+    switch (status) {
+        case LKS_OK: return "ok";
+        case LKS_EINVAL: return "invalid argument";
+        case LKS_ENOMEM: return "out of memory";
+        case LKS_ECUDA: return "CUDA error";
+        case LKS_ESTATE: return "call order violated";
+        case LKS_EUNSTABLE: return "unstable forward sweep";
+        case LKS_ETIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+const char* lks_last_error_string(const lks_ctx* ctx) {
+    if (!ctx) return g_create_err.c_str();
+    return ctx->err.c_str();
+}
+
+int lks_create(const lks_params* p, lks_ctx** out) {
+    if (!out) return LKS_EINVAL;
+    lks_ctx* c = nullptr;
+    try {
+        validate(p);
+        c = new lks_ctx();
+        c->prm = *p;
+        std::memset(&c->stats, 0, sizeof(c->stats));
+        setup_geometry(c);
+        int ndev = 0;
+        LKS_CUDA(cudaGetDeviceCount(&ndev));
+        c->eng.reset(make_engine(p->precision, c->D, c->hw));
+        c->block = c->eng->block();
+        c->grid = dim3(nblk(p->n[0], c->block.x), nblk(p->n[1], c->block.y), nblk(p->n[2], c->block.z));
+        c->nblocks = (int)(c->grid.x * c->grid.y * c->grid.z);
+        allocate(c);
+        *out = c;
+        g_create_err.clear();
+        return LKS_OK;
+    } catch (const LksError& e) {
+        g_create_err = e.msg;
+        if (c) {
+            free_all(c);
+            delete c;
+        }
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        g_create_err = "host allocation failed";
+        if (c) {
+            free_all(c);
+            delete c;
+        }
+        return LKS_ENOMEM;
+    }
+}
+
+void lks_destroy(lks_ctx* ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    free_all(ctx);
+    delete ctx;
+}
+
+int lks_forward_dev(lks_ctx* c, const double* d_gamma, const double* d_pos, double* d_J, void* stream) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!d_gamma || !d_pos) throw LksError{LKS_EINVAL, "null input pointer"};
+        cudaStream_t s = (cudaStream_t)stream;
+        LKS_CUDA(cudaMemcpyAsync(c->d_gamma, d_gamma, c->nd * 8, cudaMemcpyDeviceToDevice, s));
+        LKS_CUDA(cudaMemcpyAsync(c->d_knots, d_pos, (size_t)c->prm.K * c->D * 8, cudaMemcpyDeviceToDevice, s));
+        c->have_forward = false;
+        run_forward(c, s);
+        if (d_J) LKS_CUDA(cudaMemcpyAsync(d_J, c->d_J, 8, cudaMemcpyDeviceToDevice, s));
+    });
+}
+
+int lks_forward(lks_ctx* c, const double* gamma, const double* pos, double* J) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!gamma || !pos || !J) throw LksError{LKS_EINVAL, "null pointer"};
+        cudaStream_t s = 0;
+        LKS_CUDA(cudaMemcpyAsync(c->d_gamma, gamma, c->nd * 8, cudaMemcpyHostToDevice, s));
+        LKS_CUDA(cudaMemcpyAsync(c->d_knots, pos, (size_t)c->prm.K * c->D * 8, cudaMemcpyHostToDevice, s));
+        c->have_forward = false;
+        run_forward(c, s);
+        double j = 0.0;
+        LKS_CUDA(cudaMemcpyAsync(&j, c->d_J, 8, cudaMemcpyDeviceToHost, s));
+        LKS_CUDA(cudaStreamSynchronize(s));
+        if (*c->h_flag) throw LksError{LKS_EUNSTABLE, "forward sweep unstable: non-finite velocity or |u| > u_crit"};
+        *J = j;
+    });
+}
+
+int lks_adjoint_dev(lks_ctx* c, double* d_dgamma, double* d_dpos, void* stream) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        cudaStream_t s = (cudaStream_t)stream;
+        run_adjoint(c, s);
+        finish_adjoint(c, d_dgamma, d_dpos, s);
+    });
+}
+
+int lks_adjoint(lks_ctx* c, double* dgamma, double* dpos) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!dgamma || !dpos) throw LksError{LKS_EINVAL, "null pointer"};
+        cudaStream_t s = 0;
+        run_adjoint(c, s);
+        finish_adjoint(c, c->d_out_g, c->d_out_k, s);
+        LKS_CUDA(cudaMemcpyAsync(dgamma, c->d_out_g, c->nd * 8, cudaMemcpyDeviceToHost, s));
+        LKS_CUDA(cudaMemcpyAsync(dpos, c->d_out_k, (size_t)c->prm.K * c->D * 8, cudaMemcpyDeviceToHost, s));
+        LKS_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int lks_density_filter_dev(lks_ctx* c, const double* in, double* out, void* stream) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!in || !out) throw LksError{LKS_EINVAL, "null pointer"};
+        density_filter_kernel<<<nblk(c->nd, 128), 128, 0, (cudaStream_t)stream>>>(c->dg, in, c->d_fnorm, out, 0);
+        LKS_LAUNCHED();
+    });
+}
+
+int lks_density_filter_T_dev(lks_ctx* c, const double* in, double* out, void* stream) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!in || !out) throw LksError{LKS_EINVAL, "null pointer"};
+        density_filter_kernel<<<nblk(c->nd, 128), 128, 0, (cudaStream_t)stream>>>(c->dg, in, c->d_fnorm, out, 1);
+        LKS_LAUNCHED();
+    });
+}
+
+int lks_projection_dev(int64_t count, double beta, double eta, const double* in, double* out, double* dout,
+                       void* stream) {
+    if (count < 0 || !in || !(beta >= 0.0) || !(eta > 0.0 && eta < 1.0)) return LKS_EINVAL;
+    if (count == 0) return LKS_OK;
+    projection_kernel<<<nblk(count, 256), 256, 0, (cudaStream_t)stream>>>(count, beta, eta, in, out, dout);
+    return cudaGetLastError() == cudaSuccess ? LKS_OK : LKS_ECUDA;
+}
+
+int lks_motion_filter_dev(lks_ctx* c, const double* in, double* out, void* stream) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!in || !out) throw LksError{LKS_EINVAL, "null pointer"};
+        motion_filter_kernel<<<nblk((long long)c->prm.K * c->D, 64), 64, 0, (cudaStream_t)stream>>>(c->mg, in, out, 0);
+        LKS_LAUNCHED();
+    });
+}
+
+int lks_motion_filter_T_dev(lks_ctx* c, const double* in, double* out, void* stream) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!in || !out) throw LksError{LKS_EINVAL, "null pointer"};
+        motion_filter_kernel<<<nblk((long long)c->prm.K * c->D, 64), 64, 0, (cudaStream_t)stream>>>(c->mg, in, out, 1);
+        LKS_LAUNCHED();
+    });
+}
+
+int lks_interp_positions_dev(lks_ctx* c, const double* filt, double* s_out, double* uG, void* stream) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!filt || !s_out || !uG) throw LksError{LKS_EINVAL, "null pointer"};
+        interp_kernel<<<nblk((long long)(c->prm.Nt + 1) * c->D, 256), 256, 0, (cudaStream_t)stream>>>(c->mg, filt, s_out, uG);
+        LKS_LAUNCHED();
+    });
+}
+
+int lks_interp_positions_T_dev(lks_ctx* c, const double* gs, const double* guG, double* out, void* stream) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!gs || !guG || !out) throw LksError{LKS_EINVAL, "null pointer"};
+        interp_T_kernel<<<nblk((long long)c->prm.K * c->D, 64), 64, 0, (cudaStream_t)stream>>>(c->mg, gs, guG, out);
+        LKS_LAUNCHED();
+    });
+}
+
+int lks_get_state(lks_ctx* c, double* p, double* u) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!p || !u) throw LksError{LKS_EINVAL, "null pointer"};
+        if (!c->have_forward) throw LksError{LKS_ESTATE, "no forward has run"};
+        const long long N = c->g.N;
+        double* dp = nullptr;
+        LKS_CUDA(cudaMalloc(&dp, (size_t)(c->D + 1) * N * 8));
+        c->eng->export_state(c->g, c->fin, dp, dp + N, 0);
+        cudaError_t e1 = cudaMemcpy(p, dp, N * 8, cudaMemcpyDeviceToHost);
+        cudaError_t e2 = cudaMemcpy(u, dp + N, (size_t)c->D * N * 8, cudaMemcpyDeviceToHost);
+        cudaFree(dp);
+        LKS_CUDA(e1);
+        LKS_CUDA(e2);
+    });
+}
+
+int lks_get_step_sensitivities(lks_ctx* c, double* gs, double* guG) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!gs || !guG) throw LksError{LKS_EINVAL, "null pointer"};
+        const size_t b = (size_t)(c->prm.Nt + 1) * c->D * 8;
+        LKS_CUDA(cudaDeviceSynchronize());
+        LKS_CUDA(cudaMemcpy(gs, c->d_gs, b, cudaMemcpyDeviceToHost));
+        LKS_CUDA(cudaMemcpy(guG, c->d_guG, b, cudaMemcpyDeviceToHost));
+    });
+}
+
+int lks_set_timing(lks_ctx* c, int enable) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        const bool on = enable != 0;
+        if (on == c->timing) return;
+        drop_graphs(c);
+        c->timing = on;
+        if (on && c->evpool.empty()) {
+            // two events per span: the forward sweep, and per segment a recompute and an adjoint span,
+            // plus binomial-schedule advances
+            const size_t need = 16 * (size_t)(c->M + 8) + 64;
+            for (size_t i = 0; i < need; ++i) {
+                cudaEvent_t e;
+                LKS_CUDA(cudaEventCreate(&e));
+                c->evpool.push_back(e);
+            }
+            LKS_CUDA(cudaEventCreate(&c->ev_end));
+        }
+    });
+}
+
+int lks_set_graphs(lks_ctx* c, int enable) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        drop_graphs(c);
+        c->use_graphs = enable != 0;
+        c->have_forward = false;
+    });
+}
+
+int lks_get_stats(const lks_ctx* c, lks_stats* out) {
+    if (!c || !out) return LKS_EINVAL;
+    *out = c->stats;
+    return LKS_OK;
+}
+
+}  // extern "C"

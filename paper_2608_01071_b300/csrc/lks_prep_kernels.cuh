@@ -1,0 +1,301 @@
+// Per-call preparation kernels (design and motion parametrisation) and their transposes.
+// All in FP64: they touch O(N_d + K + Nt) values once per call.
+#pragma once
+
+#include "lks_common.cuh"
+
+namespace lks {
+
+struct DesignGeom {
+    int nd[3];       // inner design grid
+    int margin;
+    int nde[3];      // extended grid
+    double R;        // density filter radius (<= 1: identity)
+    double beta, eta;
+    double kappa_max, q;
+};
+
+// Cone weight of Eq. filtering for an integer offset.
+__device__ __forceinline__ double cone_weight(int dx, int dy, int dz, double R) {
+    const double dist = sqrt((double)(dx * dx + dy * dy + dz * dz));
+    const double w = (R - dist) / R;
+    return w > 0.0 ? w : 0.0;
+}
+
+// Row sums sum_j w_s(i, j) over the design grid (truncated at the edges); static per context.
+__global__ void filter_norm_kernel(DesignGeom dg, double* __restrict__ norm) {
+    const long long n = (long long)dg.nd[0] * dg.nd[1] * dg.nd[2];
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int ix = i % dg.nd[0], iy = (i / dg.nd[0]) % dg.nd[1], iz = i / ((long long)dg.nd[0] * dg.nd[1]);
+    const int r = (int)floor(dg.R);
+    const int rz = dg.nd[2] > 1 ? r : 0;
+    double s = 0.0;
+    for (int dz = -rz; dz <= rz; ++dz)
+        for (int dy = -r; dy <= r; ++dy)
+            for (int dx = -r; dx <= r; ++dx) {
+                const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
+                if (jx < 0 || jx >= dg.nd[0] || jy < 0 || jy >= dg.nd[1] || jz < 0 || jz >= dg.nd[2]) continue;
+                s += cone_weight(dx, dy, dz, dg.R);
+            }
+    norm[i] = s;
+}
+
+// Eq. filtering (transpose = false): out_i = sum_j w_ij in_j / norm_i.
+// Transpose (transpose = true):      out_j = sum_i w_ij in_i / norm_i.
+__global__ void density_filter_kernel(DesignGeom dg, const double* __restrict__ in, const double* __restrict__ norm,
+                                      double* __restrict__ out, int transpose) {
+    const long long n = (long long)dg.nd[0] * dg.nd[1] * dg.nd[2];
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (dg.R <= 1.0) {
+        out[i] = in[i];
+        return;
+    }
+    const int ix = i % dg.nd[0], iy = (i / dg.nd[0]) % dg.nd[1], iz = i / ((long long)dg.nd[0] * dg.nd[1]);
+    const int r = (int)floor(dg.R);
+    const int rz = dg.nd[2] > 1 ? r : 0;
+    double s = 0.0;
+    for (int dz = -rz; dz <= rz; ++dz)
+        for (int dy = -r; dy <= r; ++dy)
+            for (int dx = -r; dx <= r; ++dx) {
+                const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
+                if (jx < 0 || jx >= dg.nd[0] || jy < 0 || jy >= dg.nd[1] || jz < 0 || jz >= dg.nd[2]) continue;
+                const double w = cone_weight(dx, dy, dz, dg.R);
+                if (w == 0.0) continue;
+                const long long j = jx + (long long)dg.nd[0] * (jy + (long long)dg.nd[1] * jz);
+                s += transpose ? w * in[j] / norm[j] : w * in[j];
+            }
+    out[i] = transpose ? s : s / norm[i];
+}
+
+// Eq. projection and its derivative; beta = 0 is the identity.
+__device__ __forceinline__ double proj(double x, double beta, double eta) {
+    if (beta == 0.0) return x;
+    return (tanh(beta * eta) + tanh(beta * (x - eta))) / (tanh(beta * eta) + tanh(beta * (1.0 - eta)));
+}
+__device__ __forceinline__ double proj_d(double x, double beta, double eta) {
+    if (beta == 0.0) return 1.0;
+    const double c = cosh(beta * (x - eta));
+    return beta / (c * c) / (tanh(beta * eta) + tanh(beta * (1.0 - eta)));
+}
+
+__global__ void projection_kernel(long long n, double beta, double eta, const double* __restrict__ in,
+                                  double* __restrict__ out, double* __restrict__ dout) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = in[i];
+    if (out) out[i] = proj(x, beta, eta);
+    if (dout) dout[i] = proj_d(x, beta, eta);
+}
+
+// gamma~ -> gamma-bar -> kappa^ref (Eq. kappa_ref) on the extended grid (zero margin), FP64 and state precision.
+template <typename T>
+__global__ void kappa_ref_kernel(DesignGeom dg, const double* __restrict__ gt, double* __restrict__ gb,
+                                 double* __restrict__ kref64, T* __restrict__ kref) {
+    const long long ne = (long long)dg.nde[0] * dg.nde[1] * dg.nde[2];
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const int ex = e % dg.nde[0], ey = (e / dg.nde[0]) % dg.nde[1], ez = e / ((long long)dg.nde[0] * dg.nde[1]);
+    const int m = dg.margin;
+    const int mz = dg.nd[2] > 1 ? m : 0;
+    const int ix = ex - m, iy = ey - m, iz = ez - mz;
+    double k = 0.0;
+    if (ix >= 0 && ix < dg.nd[0] && iy >= 0 && iy < dg.nd[1] && iz >= 0 && iz < dg.nd[2]) {
+        const long long i = ix + (long long)dg.nd[0] * (iy + (long long)dg.nd[1] * iz);
+        const double g = proj(gt[i], dg.beta, dg.eta);
+        gb[i] = g;
+        k = dg.kappa_max * dg.q * g / ((1.0 - g) + dg.q);
+    }
+    kref64[e] = k;
+    kref[e] = (T)k;
+}
+
+// Chain rule: dJ/dkappa^ref (extended grid) -> dJ/dgamma~ on the inner grid (kappa^ref' times projection').
+__global__ void design_chain_kernel(DesignGeom dg, const double* __restrict__ dkref, const double* __restrict__ gt,
+                                    const double* __restrict__ gb, double* __restrict__ out) {
+    const long long n = (long long)dg.nd[0] * dg.nd[1] * dg.nd[2];
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int ix = i % dg.nd[0], iy = (i / dg.nd[0]) % dg.nd[1], iz = i / ((long long)dg.nd[0] * dg.nd[1]);
+    const int m = dg.margin;
+    const int mz = dg.nd[2] > 1 ? m : 0;
+    const long long e = (ix + m) + (long long)dg.nde[0] * ((iy + m) + (long long)dg.nde[1] * (iz + mz));
+    const double g = gb[i];
+    const double den = (1.0 - g) + dg.q;
+    const double dk = dg.kappa_max * dg.q * (1.0 + dg.q) / (den * den);
+    out[i] = dkref[e] * dk * proj_d(gt[i], dg.beta, dg.eta);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Motion (Sec. 2.4): knots at t_k = k Nt / (K - 1); temporal filter of Eq. chi_filtered between knots;
+// linear interpolation to every step; u^G_n = s_n - s_{n-1}.
+// ------------------------------------------------------------------------------------------------
+struct MotionGeom {
+    int K, d, Nt;
+    double R_t;
+};
+
+__device__ __forceinline__ double tri_weight(int k, int m, const MotionGeom& mg) {
+    const double tk = (double)k * mg.Nt / (mg.K - 1), tm = (double)m * mg.Nt / (mg.K - 1);
+    const double w = (mg.R_t - fabs(tk - tm)) / mg.R_t;
+    return w > 0.0 ? w : 0.0;
+}
+
+// transpose = 0: out_k = sum_m w_km in_m / sum_m w_km.   transpose = 1: out_m = sum_k w_km in_k / sum_m' w_km'.
+__global__ void motion_filter_kernel(MotionGeom mg, const double* __restrict__ in, double* __restrict__ out, int transpose) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= mg.K * mg.d) return;
+    const int k = t / mg.d, a = t % mg.d;
+    double s = 0.0;
+    if (!transpose) {
+        double ws = 0.0;
+        for (int m = 0; m < mg.K; ++m) {
+            const double w = tri_weight(k, m, mg);
+            s += w * in[m * mg.d + a];
+            ws += w;
+        }
+        out[t] = s / ws;
+    } else {
+        for (int r = 0; r < mg.K; ++r) {
+            const double w = tri_weight(r, k, mg);
+            if (w == 0.0) continue;
+            double ws = 0.0;
+            for (int m = 0; m < mg.K; ++m) ws += tri_weight(r, m, mg);
+            s += w / ws * in[r * mg.d + a];
+        }
+        out[t] = s;
+    }
+}
+
+__device__ __forceinline__ void interp_coef(int n, const MotionGeom& mg, int& k, double& th) {
+    const long long num = (long long)n * (mg.K - 1);
+    k = (int)(num / mg.Nt);
+    if (k > mg.K - 2) k = mg.K - 2;
+    th = (double)(num - (long long)k * mg.Nt) / mg.Nt;
+}
+
+__global__ void interp_kernel(MotionGeom mg, const double* __restrict__ f, double* __restrict__ s, double* __restrict__ uG) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (mg.Nt + 1) * mg.d) return;
+    const int n = t / mg.d, a = t % mg.d;
+    int k;
+    double th;
+    interp_coef(n, mg, k, th);
+    const double sn = (1.0 - th) * f[k * mg.d + a] + th * f[(k + 1) * mg.d + a];
+    s[t] = sn;
+    // u^G_n = s_n - s_{n-1} (n >= 1), u^G_0 = u^G_1
+    const int n1 = n == 0 ? 1 : n;
+    int k1, k0;
+    double th1, th0;
+    interp_coef(n1, mg, k1, th1);
+    interp_coef(n1 - 1, mg, k0, th0);
+    const double s1 = (1.0 - th1) * f[k1 * mg.d + a] + th1 * f[(k1 + 1) * mg.d + a];
+    const double s0 = (1.0 - th0) * f[k0 * mg.d + a] + th0 * f[(k0 + 1) * mg.d + a];
+    uG[t] = s1 - s0;
+}
+
+// Transpose of interp_kernel: (s-bar, u^G-bar) -> filtered-knot bar.  u^G-bar_0 is ignored (u^G_0 drives no step).
+__global__ void interp_T_kernel(MotionGeom mg, const double* __restrict__ gs, const double* __restrict__ guG,
+                                double* __restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= mg.K * mg.d) return;
+    const int kk = t / mg.d, a = t % mg.d;
+    double acc = 0.0;
+    for (int n = 0; n <= mg.Nt; ++n) {
+        int k;
+        double th;
+        interp_coef(n, mg, k, th);
+        double c = 0.0;
+        if (k == kk) c += 1.0 - th;
+        if (k + 1 == kk) c += th;
+        if (c == 0.0) continue;
+        double g = gs[n * mg.d + a];
+        if (n >= 1) g += guG[n * mg.d + a];
+        if (n + 1 <= mg.Nt) g -= guG[(n + 1) * mg.d + a];
+        acc += c * g;
+    }
+    out[t] = acc;
+}
+
+// Per-step pose: offset o = o0 + s_n, box start and tap weights of the shifted design grid (Eq. rigid_body_position,
+// theta = 0; transfer kernel w of Sec. 2.3).  Tap k of a node reads design index j = b - 2 hw + 1 + k, with
+// r = t - j = hw - k - f for f = o - floor(o).
+__global__ void pose_kernel(Geom g, int D, double o0x, double o0y, double o0z, int cosine, int Nt,
+                            const double* __restrict__ s, const double* __restrict__ uG, Pose* __restrict__ poses) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n > Nt) return;
+    const double o0[3] = {o0x, o0y, o0z};
+    Pose P;
+    P.pad = 0;
+    for (int a = 0; a < 3; ++a) {
+        for (int k = 0; k < 4; ++k) {
+            P.w[a][k] = 0.0;
+            P.dw[a][k] = 0.0;
+        }
+        P.xs[a] = 0;
+        P.uG[a] = 0.0;
+        if (a >= D) continue;
+        const double o = o0[a] + s[n * D + a];
+        const double oi = floor(o);
+        const double f = o - oi;
+        int xs = (int)oi - g.hw + 1;
+        if (g.periodic[a]) xs = wrap(xs, g.n[a]);
+        P.xs[a] = xs;
+        P.uG[a] = uG[n * D + a];
+        for (int k = 0; k < 2 * g.hw; ++k) {
+            const double r = (double)(g.hw - k) - f;
+            if (cosine) {
+                P.w[a][k] = 0.25 * (1.0 + cos(3.141592653589793 * r / 2.0));
+                P.dw[a][k] = (3.141592653589793 / 8.0) * sin(3.141592653589793 * r / 2.0);
+            } else {
+                P.w[a][k] = k == 0 ? f : 1.0 - f;
+                P.dw[a][k] = k == 0 ? 1.0 : -1.0;
+            }
+        }
+    }
+    poses[n] = P;
+}
+
+// Initial state p' = 0 (p = 1/3), u = 0, wall nodes at their wall velocity.
+template <typename T, int D>
+__global__ void init_state_kernel(Geom g, T* __restrict__ st) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    int x[3] = {(int)(i % g.n[0]), (int)((i / g.n[0]) % g.n[1]), (int)(i / ((long long)g.n[0] * g.n[1]))};
+    T u[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) {
+        if (g.periodic[a]) continue;
+        int side = x[a] == 0 ? 0 : (x[a] == g.n[a] - 1 ? 1 : -1);
+        if (side >= 0)
+            for (int c = 0; c < D; ++c) u[c] = (T)g.wall_u[a][side][c];
+    }
+    st[i] = 0;
+    for (int c = 0; c < D; ++c) st[(1 + c) * g.N + i] = u[c];
+}
+
+// Adjoint terminal state: lambda_p = 0, lambda_u = phi (the objective's weight of the last step).
+template <typename T, int D>
+__global__ void init_adjoint_kernel(Geom g, T* __restrict__ lam) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    int x[3] = {(int)(i % g.n[0]), (int)((i / g.n[0]) % g.n[1]), (int)(i / ((long long)g.n[0] * g.n[1]))};
+    bool wall = false, probe = true;
+    for (int a = 0; a < D; ++a) {
+        if (!g.periodic[a] && (x[a] == 0 || x[a] == g.n[a] - 1)) wall = true;
+        probe = probe && x[a] >= g.probe_lo[a] && x[a] < g.probe_hi[a];
+    }
+    lam[i] = 0;
+    for (int c = 0; c < D; ++c) lam[(1 + c) * g.N + i] = (probe && !wall) ? (T)(g.dir[c] * g.phi) : (T)0;
+}
+
+// FP64 copy of a state (p = p' + 1/3) for the host.
+template <typename T, int D>
+__global__ void export_state_kernel(Geom g, const T* __restrict__ st, double* __restrict__ p, double* __restrict__ u) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    p[i] = (double)st[i] + 1.0 / 3.0;
+    for (int c = 0; c < D; ++c) u[c * g.N + i] = (double)st[(1 + c) * g.N + i];
+}
+
+}  // namespace lks

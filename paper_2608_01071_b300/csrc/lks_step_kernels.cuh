@@ -1,0 +1,670 @@
+// Forward LKS step, exact discrete adjoint step, transposed mapping and per-step reductions.
+//
+// Data layout in HBM (structure of arrays, x fastest): a "state" is D + 1 consecutive fields of N values,
+// field 0 the reduced pressure p' = p - 1/3 (the constant 1/3 streams through Eqs. p_tmp/u_tmp unchanged,
+// since sum_i w_i c_i = 0), fields 1..D the velocity components.  The adjoint state lambda = dJ/d(p, u)
+// uses the same layout.
+//
+// Both step kernels stage a (TX+4) x (TY+4) [x (TZ+4)] halo-2 tile in shared memory: the forward's
+// equilibrium at x - c_i needs the velocity gradient at x - c_i (radius 2), and the adjoint's transposed
+// gradient term needs M2 at z +- e_a of moments gathered from z + c_i (radius 2).
+#pragma once
+
+#include "lks_common.cuh"
+
+namespace lks {
+
+template <int D, int TX, int TY, int TZ>
+struct Tile {
+    static constexpr int SX = TX + 4, SY = TY + 4, SZ = (D == 3) ? TZ + 4 : 1;
+    static constexpr int S = SX * SY * SZ;  // halo-2 region
+    static constexpr int MX = TX + 2, MY = TY + 2, MZ = (D == 3) ? TZ + 2 : 1;
+    static constexpr int M = MX * MY * MZ;  // halo-1 region
+    static constexpr int NT = TX * TY * TZ;
+    static constexpr int KZ = (D == 3) ? 1 : 0;  // z offset flag
+};
+
+template <typename T>
+struct FwdArgs {
+    const T* in;        // state n-1
+    T* out_p;           // p' of state n
+    T* out_u;           // u of state n (component a at out_u + a N)
+    const T* kref;      // kappa^ref on the extended design grid
+    const Pose* pose;   // pose of step n
+    double* jslot;      // objective partials of step n, one per probe block (nullptr: not needed)
+    unsigned* flag;     // stability flag (bit 0)
+    int jb_lo[3];       // first block touching the probe box, per axis
+    int jb_n[3];        // number of blocks touching it, per axis
+};
+
+template <typename T>
+struct AdjArgs {
+    const T* lam_in;    // lambda_n
+    T* lam_out;         // lambda_{n-1}
+    const T* u_prev;    // u_{n-1} (component a at u_prev + a N)
+    const T* u_cur;     // u_n
+    const T* kref;
+    const Pose* pose;   // pose of step n
+    T* kbar;            // kappa-bar of step n on the footprint box (nullptr: no shape gradient)
+    double* mslot;      // 2D motion partials of every block for step n (nullptr: no motion gradient)
+    int src;            // 1: add the objective source phi (n - 1 >= 1)
+};
+
+// ------------------------------------------------------------------------------------------------
+// Small helpers
+// ------------------------------------------------------------------------------------------------
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    constexpr int NW = (NT + 31) / 32;
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (tid == 0) {
+#pragma unroll 1
+        for (int i = 0; i < NW; ++i) s += red[i];
+    }
+    return s;  // valid on thread 0
+}
+
+// Does the tile [x0, x0 + T) of an axis of length n touch the probe interval [lo, hi)?
+__device__ __host__ inline bool tile_hits_range(int x0, int T, int lo, int hi) {
+    return x0 < hi && x0 + T > lo;
+}
+
+// Does the tile [x0, x0 + T) touch the footprint box [xs, xs + Fb) (mod n on periodic axes)?
+__device__ __host__ inline bool tile_hits_box(int x0, int T, int n, int xs, int Fb, int periodic) {
+    int len = (n - x0 < T) ? n - x0 : T;
+    int b0 = x0 - xs;
+    if (periodic) {
+        if (b0 < 0) b0 += n;
+        return b0 < Fb || b0 + len - 1 >= n;
+    }
+    return b0 < Fb && b0 + len - 1 >= 0;
+}
+
+// Tap weights of one axis for a node with box coordinate b: tap k reads design index j = b - 2 HW + 1 + k.
+template <typename T, int HW>
+struct AxisTaps {
+    T w[2 * HW];
+    T dw[2 * HW];
+    int j0;  // design index of tap 0
+    int nde;
+};
+
+// kappa, C and (optionally) their offset derivatives at a node of the footprint box (Eqs. kappa, u_s).
+template <typename T, int D, int HW, bool GRAD>
+__device__ __forceinline__ void map_node(const Geom& g, const Pose& P, const T* __restrict__ kref, const int* b,
+                                         T& kap, T& C, T* dk, T* dC) {
+    constexpr int NTAP = 2 * HW;
+    T wt[D][NTAP], dwt[D][NTAP];
+    int j0[D];
+    T sa[D], dsa[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        j0[a] = b[a] - 2 * HW + 1;
+        sa[a] = 0;
+        dsa[a] = 0;
+#pragma unroll
+        for (int k = 0; k < NTAP; ++k) {
+            const int j = j0[a] + k;
+            const bool v = (j >= 0) && (j < g.nde[a]);
+            wt[a][k] = v ? (T)P.w[a][k] : (T)0;
+            dwt[a][k] = v ? (T)P.dw[a][k] : (T)0;
+            sa[a] += wt[a][k];
+            dsa[a] += dwt[a][k];
+        }
+    }
+    C = sa[0];
+#pragma unroll
+    for (int a = 1; a < D; ++a) C *= sa[a];
+    if (GRAD) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            T v = dsa[a];
+#pragma unroll
+            for (int c2 = 0; c2 < D; ++c2)
+                if (c2 != a) v *= sa[c2];
+            dC[a] = v;
+            dk[a] = 0;
+        }
+    }
+    kap = 0;
+    const long long sx = g.nde[0], sxy = (long long)g.nde[0] * g.nde[1];
+    if (D == 2) {
+#pragma unroll
+        for (int ky = 0; ky < NTAP; ++ky) {
+            const int jy = j0[1] + ky;
+            if (jy < 0 || jy >= g.nde[1]) continue;
+#pragma unroll
+            for (int kx = 0; kx < NTAP; ++kx) {
+                const int jx = j0[0] + kx;
+                if (jx < 0 || jx >= g.nde[0]) continue;
+                const T kr = kref[jx + sx * jy];
+                kap += wt[0][kx] * wt[1][ky] * kr;
+                if (GRAD) {
+                    dk[0] += dwt[0][kx] * wt[1][ky] * kr;
+                    dk[1] += wt[0][kx] * dwt[1][ky] * kr;
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int kz = 0; kz < NTAP; ++kz) {
+            const int jz = j0[D - 1] + kz;
+            if (jz < 0 || jz >= g.nde[D - 1]) continue;
+#pragma unroll
+            for (int ky = 0; ky < NTAP; ++ky) {
+                const int jy = j0[1] + ky;
+                if (jy < 0 || jy >= g.nde[1]) continue;
+#pragma unroll
+                for (int kx = 0; kx < NTAP; ++kx) {
+                    const int jx = j0[0] + kx;
+                    if (jx < 0 || jx >= g.nde[0]) continue;
+                    const T kr = kref[jx + sx * jy + sxy * jz];
+                    const T wyz = wt[1][ky] * wt[D - 1][kz];
+                    kap += wt[0][kx] * wyz * kr;
+                    if (GRAD) {
+                        dk[0] += dwt[0][kx] * wyz * kr;
+                        dk[1] += wt[0][kx] * dwt[1][ky] * wt[D - 1][kz] * kr;
+                        dk[D - 1] += wt[0][kx] * wt[1][ky] * dwt[D - 1][kz] * kr;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Wall test of a node; on a wall node writes the imposed velocity (later axes win where planes meet).
+template <typename T, int D>
+__device__ __forceinline__ bool wall_node(const Geom& g, const int* x, T* uw) {
+    bool wall = false;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        if (g.periodic[a]) continue;
+        int side = -1;
+        if (x[a] == 0) side = 0;
+        else if (x[a] == g.n[a] - 1) side = 1;
+        if (side >= 0) {
+            wall = true;
+#pragma unroll
+            for (int c2 = 0; c2 < D; ++c2) uw[c2] = (T)g.wall_u[a][side][c2];
+        }
+    }
+    return wall;
+}
+
+template <int D>
+__device__ __forceinline__ bool in_probe(const Geom& g, const int* x) {
+    bool in = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) in = in && x[a] >= g.probe_lo[a] && x[a] < g.probe_hi[a];
+    return in;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Forward step n-1 -> n (Sec. 2.2 Eqs. f_eq, p_tmp, u_tmp, p, u; Sec. 2.3 Eqs. kappa, u_s), fused with the
+// objective partial (Eq. objective1) and the stability check.
+// ------------------------------------------------------------------------------------------------
+template <typename T, int D, int HW, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(TX * TY * TZ) fwd_step_kernel(Geom g, FwdArgs<T> a) {
+    using L = Lattice<D>;
+    using TL = Tile<D, TX, TY, TZ>;
+    constexpr int NS = NSym<D>::value;
+    constexpr int S = TL::S, M = TL::M;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    T* sp = reinterpret_cast<T*>(smem_raw);  // p' on the halo-2 region
+    T* su = sp + S;                          // u_a on the halo-2 region
+    T* ms = su + D * S;                      // sigma = 3 p' - 3/2 |u|^2 on the halo-1 region
+    T* mt = ms + M;                          // T_ab = 9/2 u_a u_b + A S_ab on the halo-1 region
+
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long long N = g.N;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+    const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
+
+    // phase 1: load p', u with a halo of 2 (periodic wrap on every axis)
+    for (int l = tid; l < S; l += TL::NT) {
+        const int i = l % TL::SX, j = (l / TL::SX) % TL::SY, k = l / (TL::SX * TL::SY);
+        const int gx = wrap(x0 - 2 + i, nx), gy = wrap(y0 - 2 + j, ny);
+        const int gz = (D == 3) ? wrap(z0 - 2 + k, nz) : 0;
+        const long long gi = gx + (long long)nx * (gy + (long long)ny * gz);
+        sp[l] = a.in[gi];
+#pragma unroll
+        for (int c = 0; c < D; ++c) su[c * S + l] = a.in[(1 + c) * N + gi];
+    }
+    __syncthreads();
+
+    // phase 2: local moment fields on the halo-1 region
+    const T A = (T)g.A;
+    constexpr int st[3] = {1, TL::SX, TL::SX * TL::SY};
+    for (int l = tid; l < M; l += TL::NT) {
+        const int i = l % TL::MX, j = (l / TL::MX) % TL::MY, k = l / (TL::MX * TL::MY);
+        const int r = (i + 1) + TL::SX * ((j + 1) + TL::SY * (k + TL::KZ));
+        T u[D];
+        T uu = 0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            u[c] = su[c * S + r];
+            uu += u[c] * u[c];
+        }
+        ms[l] = (T)3 * sp[r] - (T)1.5 * uu;
+        // G[c][e] = d u_e / d x_c by central differences
+        T G[D][D];
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+            for (int e = 0; e < D; ++e) G[c][e] = (T)0.5 * (su[e * S + r + st[c]] - su[e * S + r - st[c]]);
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+            for (int e = c; e < D; ++e) mt[sym<D>(c, e) * M + l] = (T)4.5 * u[c] * u[e] + A * (G[c][e] + G[e][c]);
+    }
+    __syncthreads();
+
+    // phase 3: gather-stream p* = 1/3 sum_i f_i(x - c_i), u* = sum_i c_i f_i(x - c_i)
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+    int xg[3] = {x0 + tx, y0 + ty, (D == 3) ? z0 + tz : 0};
+    const bool active = xg[0] < nx && xg[1] < ny && (D == 2 || xg[2] < nz);
+    const int mc = (tx + 1) + TL::MX * ((ty + 1) + TL::MY * (tz + TL::KZ));
+    const int rc = (tx + 2) + TL::SX * ((ty + 2) + TL::SY * (tz + 2 * TL::KZ));
+    T accp = 0, accu[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) accu[c] = 0;
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q) {
+        int mo = mc, ro = rc;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const int mstride = (c == 0) ? 1 : (c == 1 ? TL::MX : TL::MX * TL::MY);
+            mo -= L::c(q, c) * mstride;
+            ro -= L::c(q, c) * st[c];
+        }
+        T f = ms[mo];
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            if (L::c(q, c) != 0) f += (T)(3 * L::c(q, c)) * su[c * S + ro];
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+            for (int e = c; e < D; ++e) {
+                const int cc = L::c(q, c) * L::c(q, e) * (c == e ? 1 : 2);
+                if (cc != 0) f += (T)cc * mt[sym<D>(c, e) * M + mo];
+            }
+        const T wf = (T)L::w(q) * f;
+        accp += wf;
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            if (L::c(q, c) != 0) accu[c] += (T)L::c(q, c) * wf;
+    }
+    const T pn = accp * (T)(1.0 / 3.0);
+    T un[D];
+    // Brinkman (Eq. u) with kappa and u^S = u^G C mapped from the design grid at this step's pose
+    const Pose& P = *a.pose;
+    int b[D];
+    bool inbox = active;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        b[c] = box_coord(xg[c], P.xs[c], g.Fb[c], g.n[c], g.periodic[c]);
+        inbox = inbox && b[c] >= 0;
+    }
+    T kap = 0, C = 0;
+    if (inbox) map_node<T, D, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
+    const T inv = (T)1 / ((T)1 + kap);
+#pragma unroll
+    for (int c = 0; c < D; ++c) un[c] = (accu[c] + kap * ((T)P.uG[c] * C)) * inv;
+    T uw[D];
+    const bool wall = wall_node<T, D>(g, xg, uw);
+    if (wall) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) un[c] = uw[c];
+    }
+    if (active) {
+        const long long gi = xg[0] + (long long)nx * (xg[1] + (long long)ny * xg[2]);
+        a.out_p[gi] = pn;
+#pragma unroll
+        for (int c = 0; c < D; ++c) a.out_u[c * N + gi] = un[c];
+        if (g.u_crit2 > 0.0 && !wall) {
+            double uu = 0.0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) uu += (double)un[c] * (double)un[c];
+            if (!(uu <= g.u_crit2)) atomicOr(a.flag, 1u);
+        }
+    }
+    // objective partial of this block (deterministic: fixed reduction order)
+    if (a.jslot != nullptr) {
+        const int bx = (int)blockIdx.x - a.jb_lo[0], by = (int)blockIdx.y - a.jb_lo[1], bz = (int)blockIdx.z - a.jb_lo[2];
+        const bool hit = bx >= 0 && bx < a.jb_n[0] && by >= 0 && by < a.jb_n[1] && bz >= 0 && bz < a.jb_n[2];
+        if (hit) {
+            double v = 0.0;
+            if (active && !wall && in_probe<D>(g, xg)) {
+#pragma unroll
+                for (int c = 0; c < D; ++c) v += g.dir[c] * (double)un[c];
+            }
+            const double s = block_sum<TL::NT>(v, red);
+            if (tid == 0) a.jslot[bx + a.jb_n[0] * (by + a.jb_n[1] * bz)] = s;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Adjoint step lambda_n -> lambda_{n-1}: the exact transpose of fwd_step_kernel (discrete form of the
+// ALKS moments, Eqs. ap_tmp-as), fused with the local shape and motion sensitivities (Eqs. dJdgamma,
+// dJdchi in discrete form):
+//   u-bar* = lam_u / (1 + kappa) (0 on walls), p-bar* = lam_p
+//   F-bar_i(y) = p-bar*(y + c_i)/3 + c_i . u-bar*(y + c_i);  M0, M1, M2 = sum_i w_i {1, c_i, c_i c_i} F-bar_i
+//   lam_p' = 3 M0;  lam_u'_b = 3 M1_b + 9 (M2 u)_b - 3 u_b M0 + A sum_a [M2_ab(z - e_a) - M2_ab(z + e_a)] + phi
+//   kappa-bar = lam_u . (u^S - u_n) / (1 + kappa),  u^S-bar = lam_u kappa / (1 + kappa)
+// ------------------------------------------------------------------------------------------------
+template <typename T, int D, int HW, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(TX * TY * TZ) adj_step_kernel(Geom g, AdjArgs<T> a) {
+    using L = Lattice<D>;
+    using TL = Tile<D, TX, TY, TZ>;
+    constexpr int NS = NSym<D>::value;
+    constexpr int S = TL::S, M = TL::M;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    T* sp = reinterpret_cast<T*>(smem_raw);  // p-bar* on the halo-2 region
+    T* su = sp + S;                          // u-bar* on the halo-2 region
+    T* m0 = su + D * S;                      // M0 on the halo-1 region
+    T* m1 = m0 + M;                          // M1_a
+    T* m2 = m1 + D * M;                      // M2_ab (packed symmetric)
+
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long long N = g.N;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+    const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
+    const Pose& P = *a.pose;
+
+    // phase 1: Brinkman and wall adjoint on the halo-2 region
+    for (int l = tid; l < S; l += TL::NT) {
+        const int i = l % TL::SX, j = (l / TL::SX) % TL::SY, k = l / (TL::SX * TL::SY);
+        int xg[3] = {wrap(x0 - 2 + i, nx), wrap(y0 - 2 + j, ny), (D == 3) ? wrap(z0 - 2 + k, nz) : 0};
+        const long long gi = xg[0] + (long long)nx * (xg[1] + (long long)ny * xg[2]);
+        sp[l] = a.lam_in[gi];
+        T uw[D];
+        if (wall_node<T, D>(g, xg, uw)) {
+#pragma unroll
+            for (int c = 0; c < D; ++c) su[c * S + l] = 0;
+        } else {
+            int b[D];
+            bool inbox = true;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                b[c] = box_coord(xg[c], P.xs[c], g.Fb[c], g.n[c], g.periodic[c]);
+                inbox = inbox && b[c] >= 0;
+            }
+            T kap = 0, C = 0;
+            if (inbox) map_node<T, D, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
+            const T inv = (T)1 / ((T)1 + kap);
+#pragma unroll
+            for (int c = 0; c < D; ++c) su[c * S + l] = a.lam_in[(1 + c) * N + gi] * inv;
+        }
+    }
+    __syncthreads();
+
+    // phase 2: reverse stream and local moments on the halo-1 region
+    constexpr int st[3] = {1, TL::SX, TL::SX * TL::SY};
+    for (int l = tid; l < M; l += TL::NT) {
+        const int i = l % TL::MX, j = (l / TL::MX) % TL::MY, k = l / (TL::MX * TL::MY);
+        const int r = (i + 1) + TL::SX * ((j + 1) + TL::SY * (k + TL::KZ));
+        T M0 = 0, M1[D], M2[NS];
+#pragma unroll
+        for (int c = 0; c < D; ++c) M1[c] = 0;
+#pragma unroll
+        for (int c = 0; c < NS; ++c) M2[c] = 0;
+#pragma unroll
+        for (int q = 0; q < L::Q; ++q) {
+            int ro = r;
+#pragma unroll
+            for (int c = 0; c < D; ++c) ro += L::c(q, c) * st[c];
+            T f = sp[ro] * (T)(1.0 / 3.0);
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                if (L::c(q, c) != 0) f += (T)L::c(q, c) * su[c * S + ro];
+            const T wf = (T)L::w(q) * f;
+            M0 += wf;
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                if (L::c(q, c) != 0) M1[c] += (T)L::c(q, c) * wf;
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+#pragma unroll
+                for (int e = c; e < D; ++e)
+                    if (L::c(q, c) * L::c(q, e) != 0) M2[sym<D>(c, e)] += (T)(L::c(q, c) * L::c(q, e)) * wf;
+        }
+        m0[l] = M0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) m1[c * M + l] = M1[c];
+#pragma unroll
+        for (int c = 0; c < NS; ++c) m2[c * M + l] = M2[c];
+    }
+    __syncthreads();
+
+    // phase 3: lambda_{n-1} at the interior nodes
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+    int xg[3] = {x0 + tx, y0 + ty, (D == 3) ? z0 + tz : 0};
+    const bool active = xg[0] < nx && xg[1] < ny && (D == 2 || xg[2] < nz);
+    const int mc = (tx + 1) + TL::MX * ((ty + 1) + TL::MY * (tz + TL::KZ));
+    const long long gi = active ? xg[0] + (long long)nx * (xg[1] + (long long)ny * xg[2]) : 0;
+    const T A = (T)g.A;
+    T uw[D];
+    const bool wall = wall_node<T, D>(g, xg, uw);
+    if (active) {
+        T u[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) u[c] = a.u_prev[c * N + gi];
+        const T M0 = m0[mc];
+        a.lam_out[gi] = (T)3 * M0;
+        const bool probe = a.src && !wall && in_probe<D>(g, xg);
+#pragma unroll
+        for (int e = 0; e < D; ++e) {
+            T v = (T)3 * m1[e * M + mc] - (T)3 * u[e] * M0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const int mstride = (c == 0) ? 1 : (c == 1 ? TL::MX : TL::MX * TL::MY);
+                const T* m2s = m2 + sym<D>(c, e) * M;
+                v += (T)9 * m2s[mc] * u[c];
+                v += A * (m2s[mc - mstride] - m2s[mc + mstride]);
+            }
+            if (probe) v += (T)(g.dir[e] * g.phi);
+            a.lam_out[(1 + e) * N + gi] = v;
+        }
+    }
+
+    // local sensitivities on the footprint box
+    int b[D];
+    bool inbox = active;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        b[c] = box_coord(xg[c], P.xs[c], g.Fb[c], g.n[c], g.periodic[c]);
+        inbox = inbox && b[c] >= 0;
+    }
+    double mv[2 * D];
+#pragma unroll
+    for (int c = 0; c < 2 * D; ++c) mv[c] = 0.0;
+    if (inbox) {
+        T kb = 0;
+        if (!wall) {
+            T kap, C, dk[D], dC[D];
+            map_node<T, D, HW, true>(g, P, a.kref, b, kap, C, dk, dC);
+            const T inv = (T)1 / ((T)1 + kap);
+            T usb[D];
+            T cbar = 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const T lu = a.lam_in[(1 + c) * N + gi];
+                const T uS = (T)P.uG[c] * C;
+                kb += lu * (uS - a.u_cur[c * N + gi]);
+                usb[c] = lu * kap * inv;
+                cbar += usb[c] * (T)P.uG[c];
+            }
+            kb *= inv;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                mv[c] = (double)kb * (double)dk[c] + (double)cbar * (double)dC[c];
+                mv[D + c] = (double)usb[c] * (double)C;
+            }
+        }
+        if (a.kbar != nullptr) {
+            long long bl = b[0] + (long long)g.Fb[0] * (b[1] + (D == 3 ? (long long)g.Fb[1] * b[D - 1] : 0));
+            a.kbar[bl] = kb;
+        }
+    }
+    if (a.mslot != nullptr) {
+        bool hit = true;
+        const int t0[3] = {x0, y0, z0};
+        const int tt[3] = {TX, TY, TZ};
+#pragma unroll
+        for (int c = 0; c < D; ++c) hit = hit && tile_hits_box(t0[c], tt[c], g.n[c], P.xs[c], g.Fb[c], g.periodic[c]);
+        if (hit) {
+            const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+#pragma unroll
+            for (int c = 0; c < 2 * D; ++c) {
+                const double s = block_sum<TL::NT>(mv[c], red);
+                if (tid == 0) a.mslot[(long long)blk * 2 * D + c] = s;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Transposed mapping onto the design grid (Eq. dJdgamma in discrete form):
+//   dJ/dkappa^ref_j += sum over the segment's steps n (fixed order) of sum_x W(x - x^ref_j(n)) kappa-bar_n(x).
+// One thread per extended design node; a gather from the per-step footprint buffers, so no atomics.
+// ------------------------------------------------------------------------------------------------
+template <typename T, int D, int HW>
+__global__ void design_gather_kernel(Geom g, const Pose* __restrict__ poses, const T* __restrict__ kbar,
+                                     int n_first, int nsteps, long long kstride, double* __restrict__ dkref) {
+    constexpr int NTAP = 2 * HW;
+    const long long nd = (long long)g.nde[0] * g.nde[1] * g.nde[2];
+    const long long jl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (jl >= nd) return;
+    int j[3] = {(int)(jl % g.nde[0]), (int)((jl / g.nde[0]) % g.nde[1]), (int)(jl / ((long long)g.nde[0] * g.nde[1]))};
+    // running FP64 sum in strict step order n = Nt..1 across calls, so that the segmentation of the
+    // reverse sweep (full storage, sqrt or binomial checkpoints) cannot change the rounding
+    double acc = dkref[jl];
+    for (int s = nsteps - 1; s >= 0; --s) {
+        const Pose& P = poses[n_first + s];
+        const T* kb = kbar + (long long)s * kstride;
+        // box coordinate of tap k: b = j + 2 HW - 1 - k; valid when its analysis node is on the grid
+        int bb[D][NTAP];
+        T ww[D][NTAP];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+#pragma unroll
+            for (int k = 0; k < NTAP; ++k) {
+                const int b = j[a] + 2 * HW - 1 - k;
+                bool ok = b >= 0 && b < g.Fb[a];
+                if (ok && !g.periodic[a]) {
+                    const int x = P.xs[a] + b;
+                    ok = x >= 0 && x < g.n[a];
+                }
+                bb[a][k] = ok ? b : -1;
+                ww[a][k] = (T)P.w[a][k];
+            }
+        }
+        T sum = 0;
+        if (D == 2) {
+#pragma unroll
+            for (int ky = 0; ky < NTAP; ++ky) {
+                if (bb[1][ky] < 0) continue;
+#pragma unroll
+                for (int kx = 0; kx < NTAP; ++kx) {
+                    if (bb[0][kx] < 0) continue;
+                    sum += ww[0][kx] * ww[1][ky] * kb[bb[0][kx] + (long long)g.Fb[0] * bb[1][ky]];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int kz = 0; kz < NTAP; ++kz) {
+                if (bb[D - 1][kz] < 0) continue;
+#pragma unroll
+                for (int ky = 0; ky < NTAP; ++ky) {
+                    if (bb[1][ky] < 0) continue;
+#pragma unroll
+                    for (int kx = 0; kx < NTAP; ++kx) {
+                        if (bb[0][kx] < 0) continue;
+                        sum += ww[0][kx] * ww[1][ky] * ww[D - 1][kz] *
+                               kb[bb[0][kx] + (long long)g.Fb[0] * (bb[1][ky] + (long long)g.Fb[1] * bb[D - 1][kz])];
+                    }
+                }
+            }
+        }
+        acc += (double)sum;
+    }
+    dkref[jl] = acc;
+}
+
+// Per-step motion sensitivities: sum of the per-block partials of the blocks that touch the footprint box,
+// in block order (one warp per step; deterministic).
+template <int D>
+__global__ void motion_reduce_kernel(Geom g, int TX, int TY, int TZ, int gx, int gy, int gz,
+                                     const Pose* __restrict__ poses, const double* __restrict__ mslot, long long mstride,
+                                     int n_first, int nsteps, double* __restrict__ gs, double* __restrict__ guG) {
+    const int s = blockIdx.x;
+    if (s >= nsteps) return;
+    const int n = n_first + s;
+    const Pose& P = poses[n];
+    const double* ms = mslot + (long long)s * mstride;
+    const int lane = threadIdx.x;
+    double acc[2 * D];
+#pragma unroll
+    for (int c = 0; c < 2 * D; ++c) acc[c] = 0.0;
+    const int nb = gx * gy * gz;
+    for (int blk = lane; blk < nb; blk += 32) {
+        const int bx = blk % gx, by = (blk / gx) % gy, bz = blk / (gx * gy);
+        bool hit = tile_hits_box(bx * TX, TX, g.n[0], P.xs[0], g.Fb[0], g.periodic[0]) &&
+                   tile_hits_box(by * TY, TY, g.n[1], P.xs[1], g.Fb[1], g.periodic[1]);
+        if (D == 3) hit = hit && tile_hits_box(bz * TZ, TZ, g.n[2], P.xs[2], g.Fb[2], g.periodic[2]);
+        if (!hit) continue;
+#pragma unroll
+        for (int c = 0; c < 2 * D; ++c) acc[c] += ms[(long long)blk * 2 * D + c];
+    }
+#pragma unroll
+    for (int c = 0; c < 2 * D; ++c) {
+        double v = acc[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        acc[c] = v;
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            gs[(long long)n * D + c] = acc[c];
+            guG[(long long)n * D + c] = acc[D + c];
+        }
+    }
+}
+
+// Objective: j_n = sum of the probe blocks' partials of step n (block order), then J = phi sum_n j_n
+// (Eq. objective1 with phi = 0 as a rectangle rule over n = 1..Nt).  Deterministic.
+__global__ void objective_reduce_kernel(const double* __restrict__ jslot, int njb, int Nt, double phi,
+                                        double* __restrict__ jstep, double* __restrict__ J) {
+    __shared__ double red[32];
+    const int tid = threadIdx.x;
+    double tot = 0.0;
+    for (int n = 1 + tid; n <= Nt; n += blockDim.x) {
+        const double* js = jslot + (long long)n * njb;
+        double v = 0.0;
+        for (int b = 0; b < njb; ++b) v += js[b];
+        jstep[n] = v;
+        tot += v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if ((tid & 31) == 0) red[tid >> 5] = tot;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) s += red[i];
+        *J = s * phi;
+    }
+}
+
+}  // namespace lks

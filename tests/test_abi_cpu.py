@@ -1,0 +1,58 @@
+"""C ABI checks that need no GPU: the library loads, exports every declared symbol, and validates input."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2608_01071_b300 import _abi
+from paper_2608_01071_b300.workloads import workload
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lks.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lks_[A-Za-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol():
+    lib = _abi.load()
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in _abi.PROTOTYPES, n
+
+
+def test_params_layout_matches():
+    lib = _abi.load()
+    p = _abi.lks_params()
+    assert lib.lks_default_params(C.byref(p)) == 0
+    assert p.size == C.sizeof(_abi.lks_params)
+
+
+def test_validation_errors_without_gpu():
+    from paper_2608_01071_b300.binding import params_from_workload
+    lib = _abi.load()
+    base = params_from_workload(workload("d2q9_96x48_fp64"))
+    h = C.c_void_p()
+    for mutate in [lambda p: setattr(p, "nu", -1.0), lambda p: setattr(p, "K", 1),
+                   lambda p: setattr(p, "lattice", 7), lambda p: setattr(p, "size", 12),
+                   lambda p: p.probe_hi.__setitem__(0, 500)]:
+        p = _abi.lks_params.from_buffer_copy(base)
+        mutate(p)
+        assert lib.lks_create(C.byref(p), C.byref(h)) == _abi.LKS_EINVAL
+        assert len(lib.lks_last_error_string(None)) > 0
+    assert lib.lks_strerror(-5) == b"unstable forward sweep"
+    assert lib.lks_forward(None, None, None, None) == _abi.LKS_EINVAL
+
+
+def test_design_too_large_for_period():
+    from paper_2608_01071_b300.binding import params_from_workload
+    lib = _abi.load()
+    p = params_from_workload(workload("d2q9_96x48_fp64"))
+    p.nd[0] = 94
+    h = C.c_void_p()
+    assert lib.lks_create(C.byref(p), C.byref(h)) == _abi.LKS_EINVAL

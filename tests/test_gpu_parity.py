@@ -1,0 +1,147 @@
+"""CUDA path vs the FP64 oracle on the same seeded inputs, through the C ABI.
+
+Tolerances: FP64 state path <= 1e-10 (fields: max error / max magnitude; J relative; gradients relative
+L2); FP32 state path: velocity <= 1e-4 max relative after the full horizon, gradients <= 1e-3 relative L2.
+"""
+import numpy as np
+import pytest
+
+from helpers import oracle_run, rel_l2, rel_max, tiny_workload
+from paper_2608_01071_b300 import Solver
+from paper_2608_01071_b300.workloads import draw_gamma, draw_knots, workload
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_run(w, gamma, knots):
+    s = Solver.from_workload(w)
+    J = s.forward(gamma, knots)
+    p, u = s.state()
+    dg, dk = s.adjoint()
+    gs, gu = s.step_sensitivities()
+    st = s.stats()
+    s.close()
+    return dict(J=J, dgamma=dg, dknots=dk, p=p, u=u, gs=gs, guG=gu, stats=st)
+
+
+def check(w, tol_f, tol_u, tol_g, ref=None):
+    gamma, knots = draw_gamma(w), draw_knots(w)
+    g = gpu_run(w, gamma, knots)
+    o = ref if ref is not None else oracle_run(w, gamma, knots)
+    assert abs(g["J"] - o["J"]) <= tol_f * abs(o["J"]), (g["J"], o["J"])
+    assert rel_max(g["p"], o["p"]) <= tol_f
+    assert rel_max(g["u"], o["u"]) <= tol_u
+    if w.get("mode", "joint") != "motion":
+        assert rel_l2(g["dgamma"], o["dgamma"]) <= tol_g
+    else:
+        assert np.all(g["dgamma"] == 0)
+    if w.get("mode", "joint") != "shape":
+        assert rel_l2(g["dknots"], o["dknots"]) <= tol_g
+    else:
+        assert np.all(g["dknots"] == 0)
+    return g, o
+
+
+def test_c1_fp64_full_size():
+    # 96x48 D2Q9, 400 steps, FP64, full storage (the small workload at its full size)
+    w = workload("d2q9_96x48_fp64")
+    g, o = check(w, 1e-10, 1e-10, 1e-10)
+    assert rel_l2(g["gs"][1:], o["gs"][1:]) <= 1e-10
+    assert g["stats"]["recompute_steps"] == 0
+
+
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q15"])
+@pytest.mark.parametrize("kernel", ["linear", "cosine"])
+def test_tiny_fp64(lattice, kernel):
+    check(tiny_workload(lattice, kernel=kernel), 1e-10, 1e-10, 1e-10)
+
+
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q15"])
+def test_tiny_fp32(lattice):
+    check(tiny_workload(lattice, precision="fp32"), 1e-5, 1e-4, 1e-3)
+
+
+@pytest.mark.parametrize("mode", ["shape", "motion"])
+def test_gradient_modes(mode):
+    check(tiny_workload("D2Q9", mode=mode), 1e-10, 1e-10, 1e-10)
+
+
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q15"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_checkpointing_bitwise(lattice, prec):
+    w = tiny_workload(lattice, precision=prec, Nt=47)
+    gamma, knots = draw_gamma(w), draw_knots(w)
+    runs = {}
+    for ck, extra in [("full", {}), ("sqrt", {}), ("revolve", dict(ckpt_slots=2, seg_len=3)),
+                      ("revolve1", dict(ckpt_slots=1, seg_len=5))]:
+        ww = dict(w, **extra)
+        ww["ckpt"] = "revolve" if ck == "revolve1" else ck
+        runs[ck] = gpu_run(ww, gamma, knots)
+    base = runs["full"]
+    for k, r in runs.items():
+        assert r["J"] == base["J"], k
+        assert np.array_equal(r["dgamma"], base["dgamma"]), k
+        assert np.array_equal(r["dknots"], base["dknots"]), k
+    assert runs["sqrt"]["stats"]["recompute_steps"] > 0
+    assert runs["revolve"]["stats"]["recompute_steps"] > runs["sqrt"]["stats"]["recompute_steps"]
+
+
+def test_deterministic_double_run():
+    w = tiny_workload("D2Q9", precision="fp32")
+    gamma, knots = draw_gamma(w), draw_knots(w)
+    a = gpu_run(w, gamma, knots)
+    b = gpu_run(w, gamma, knots)
+    assert a["J"] == b["J"]
+    assert np.array_equal(a["dgamma"], b["dgamma"]) and np.array_equal(a["dknots"], b["dknots"])
+
+
+def test_c2_full_grid_short_horizon_fp32():
+    # 512x256 D2Q9 in the launch configuration of the benchmark, horizon cut to 60 steps for the oracle;
+    # the motion amplitude is scaled with the horizon so that body speeds match the full workload's
+    # The probe box moves next to the body so that J and its gradient are not ~0 after 60 steps.
+    w = workload("d2q9_512x256_fp32", Nt=60, K=6, R_t=15.0, amp=32.0 * 60 / 4000, probe_lo=(300, 96),
+                 probe_hi=(340, 160))
+    check(w, 1e-5, 1e-4, 1e-3)
+
+
+def test_adjoint_before_forward_and_unstable():
+    from paper_2608_01071_b300.binding import LKSError
+    w = tiny_workload("D2Q9")
+    s = Solver.from_workload(w)
+    with pytest.raises(LKSError) as e:
+        s.adjoint()
+    assert e.value.code == -4
+    s.close()
+    s = Solver.from_workload(dict(w, u_crit=1e-9))
+    with pytest.raises(LKSError) as e:
+        s.forward(draw_gamma(w), draw_knots(w))
+    assert e.value.code == -5
+    s.close()
+
+
+@pytest.mark.parametrize("ckpt", ["sqrt", "revolve"])
+def test_graph_replay_matches_eager(ckpt):
+    w = tiny_workload("D2Q9", precision="fp32", ckpt=ckpt, ckpt_slots=2, seg_len=4)
+    gamma, knots = draw_gamma(w), draw_knots(w)
+    s = Solver.from_workload(w)
+    res = []
+    for graphs in (False, True, True):  # eager, capture, replay
+        s.set_graphs(graphs)
+        J = s.forward(gamma, knots)
+        dg, dk = s.adjoint()
+        res.append((J, dg, dk))
+    # a second pair on the captured graphs, with different inputs in between
+    s.forward(gamma * 0.5, knots + 0.3)
+    s.adjoint()
+    J = s.forward(gamma, knots)
+    dg, dk = s.adjoint()
+    res.append((J, dg, dk))
+    s.set_timing(True)
+    s.forward(gamma, knots)
+    s.adjoint()
+    st = s.stats()
+    s.close()
+    for r in res[1:]:
+        assert r[0] == res[0][0]
+        assert np.array_equal(r[1], res[0][1]) and np.array_equal(r[2], res[0][2])
+    assert st["ms_adjoint_steps"] > 0 and st["ms_forward_steps"] > 0 and st["ms_total"] > 0
