@@ -191,6 +191,28 @@ int lks_set_timing(lks_ctx* ctx, int enable);
  * Changing the setting discards the captured graphs and requires a new lks_forward. */
 int lks_set_graphs(lks_ctx* ctx, int enable);
 
+/*
+ * Density filter (same arithmetic as lks_density_filter_dev) that performs no memory allocation of any kind.
+ * The paper has no counterpart: it exists for callers that cannot call cudaMalloc or create a context,
+ * e.g. code that runs under a host framework owning the whole device memory pool, or code that must not
+ * take the latency or the failure modes of an allocation inside its loop.
+ *
+ *   nd[3]   design grid extents (nd[2] = 1 in 2D); nd[0]*nd[1]*nd[2] <= LKS_NOALLOC_FILTER_MAX, else LKS_EINVAL.
+ *   R       filter radius in design cells (<= 1: identity copy), 0 <= R <= 32.
+ *   d_in, d_out  device arrays of that many doubles (x fastest), owned by the caller; may not alias.
+ *
+ * Its scratch (the per-node weight sums) is a fixed file-scope device array of LKS_NOALLOC_FILTER_MAX
+ * doubles (8 MiB) that every GPU loading the library holds until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with the device current; make that
+ * first call before any stream capture on the device.  All calls share the array and each call overwrites
+ * the entries it uses, so calls whose kernels may overlap on the GPU (different streams without ordering)
+ * race and give undefined results: order them on one stream.  Asynchronous on `stream`.  Error text:
+ * lks_noalloc_last_error().
+ */
+#define LKS_NOALLOC_FILTER_MAX (1 << 20)
+int lks_density_filter_noalloc(const int32_t nd[3], double R, const double* d_in, double* d_out, void* stream);
+const char* lks_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

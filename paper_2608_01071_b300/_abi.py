@@ -93,6 +93,8 @@ PROTOTYPES = {
     "lks_get_stats": (C.c_int, [_P, C.POINTER(lks_stats)]),
     "lks_set_timing": (C.c_int, [_P, C.c_int]),
     "lks_set_graphs": (C.c_int, [_P, C.c_int]),
+    "lks_density_filter_noalloc": (C.c_int, [C.POINTER(C.c_int32), C.c_double, _P, _P, _P]),
+    "lks_noalloc_last_error": (C.c_char_p, []),
 }
 
 _lib = None

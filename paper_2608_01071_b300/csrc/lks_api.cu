@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1156,3 +1157,84 @@ int lks_get_stats(const lks_ctx* c, lks_stats* out) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// Density filter without any allocation.  Its only scratch (the per-node sum of filter weights) lives in
+// a fixed file-scope device array; every GPU that loads the library holds that array until the process
+// exits.  Host code must not pass the array's name to a kernel: on the host it names a stand-in object,
+// so the device address is looked up once per device with cudaGetSymbolAddress.
+// ------------------------------------------------------------------------------------------------
+static __device__ __align__(256) double g_noalloc_filter_norm[LKS_NOALLOC_FILTER_MAX];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+thread_local std::string g_noalloc_err;
+}  // namespace
+
+extern "C" int lks_density_filter_noalloc(const int32_t nd[3], double R, const double* d_in, double* d_out,
+                                          void* stream) {
+    if (!nd || !d_in || !d_out) {
+        g_noalloc_err = "null pointer";
+        return LKS_EINVAL;
+    }
+    long long n = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (nd[a] < 1) {
+            g_noalloc_err = "design extents must be >= 1";
+            return LKS_EINVAL;
+        }
+        n *= nd[a];
+    }
+    if (n > LKS_NOALLOC_FILTER_MAX) {
+        g_noalloc_err = "design grid of " + std::to_string(n) + " nodes exceeds LKS_NOALLOC_FILTER_MAX (" +
+                        std::to_string((long long)LKS_NOALLOC_FILTER_MAX) + ")";
+        return LKS_EINVAL;
+    }
+    if (!(R >= 0.0) || R > 32.0) {
+        g_noalloc_err = "filter radius out of range [0, 32]";
+        return LKS_EINVAL;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        g_noalloc_err = "no usable current CUDA device";
+        return LKS_ECUDA;
+    }
+    double* norm = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            // one-time set-up on this device (the device is current): the device address of the scratch array
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_filter_norm);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();
+                g_noalloc_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+                return LKS_ECUDA;
+            }
+            g_noalloc_ptr[dev] = (double*)p;
+        }
+        norm = g_noalloc_ptr[dev];
+    }
+    DesignGeom dg;
+    std::memset(&dg, 0, sizeof(dg));
+    for (int a = 0; a < 3; ++a) {
+        dg.nd[a] = nd[a];
+        dg.nde[a] = nd[a];
+    }
+    dg.R = R;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the norm kernel overwrites every entry the filter reads, so nothing needs clearing between calls
+    filter_norm_kernel<<<nblk(n, 128), 128, 0, s>>>(dg, norm);
+    density_filter_kernel<<<nblk(n, 128), 128, 0, s>>>(dg, d_in, norm, d_out, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_noalloc_err = std::string("kernel launch: ") + cudaGetErrorString(e);
+        return LKS_ECUDA;
+    }
+    return LKS_OK;
+}
+
+extern "C" const char* lks_noalloc_last_error(void) { return g_noalloc_err.c_str(); }
