@@ -40,10 +40,28 @@ struct LksError {
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Launch a step kernel with programmatic stream serialization (see pdl_wait_then_release).
+template <typename K, typename... Args>
+void launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
+    if (e != cudaSuccess) throw LksError{LKS_ECUDA, std::string("cudaLaunchKernelEx: ") + cudaGetErrorString(e)};
+}
+
 // ------------------------------------------------------------------------------------------------
 // Typed engine: launches of the templated kernels for one (precision, dimension, kernel width).
 // ------------------------------------------------------------------------------------------------
 struct Engine {
+    bool pdl = true;  // programmatic dependent launch of the step kernels
     virtual ~Engine() {}
     virtual dim3 block() const = 0;
     virtual void fwd(const Geom& g, dim3 grid, const void* in, void* out, const void* kref, const Pose* pose,
@@ -86,8 +104,9 @@ struct EngineT : Engine {
         a.pose = pose;
         a.jslot = jslot;
         a.flag = flag;
-        fwd_step_kernel<T, D, HW, TX, TY, TZ><<<grid, block(), smem_fwd, s>>>(g, a);
-        LKS_LAUNCHED();
+        for (int i = 0; i < 3; ++i) a.dir[i] = (T)g.dir[i];
+        a.u_crit2 = (T)g.u_crit2;
+        launch_pdl(fwd_step_kernel<T, D, HW, TX, TY, TZ>, grid, block(), smem_fwd, s, pdl, g, a);
     }
     void adj(const Geom& g, dim3 grid, const void* lam_in, void* lam_out, const void* prev, const void* cur,
              const void* kref, const Pose* pose, void* kbar, double* mslot, int src, cudaStream_t s) override {
@@ -101,8 +120,8 @@ struct EngineT : Engine {
         a.kbar = (T*)kbar;
         a.mslot = mslot;
         a.src = src;
-        adj_step_kernel<T, D, HW, TX, TY, TZ><<<grid, block(), smem_adj, s>>>(g, a);
-        LKS_LAUNCHED();
+        for (int i = 0; i < 3; ++i) a.phi_dir[i] = (T)(g.dir[i] * g.phi);
+        launch_pdl(adj_step_kernel<T, D, HW, TX, TY, TZ>, grid, block(), smem_adj, s, pdl, g, a);
     }
     void gather(const Geom& g, const Pose* poses, const void* kbar, int n_first, int nsteps, long long kstride,
                 double* dkref, cudaStream_t s) override {
@@ -186,6 +205,7 @@ struct lks_ctx {
     void* d_kref = nullptr;
     double *d_knots = nullptr, *d_filt = nullptr, *d_s = nullptr, *d_uG = nullptr, *d_ktmp = nullptr;
     double *d_out_g = nullptr, *d_out_k = nullptr;  // host-pointer adjoint staging
+    double* d_tnorm = nullptr;                        // temporal-filter row sums
     Pose* d_pose = nullptr;
     double *d_gs = nullptr, *d_guG = nullptr, *d_dkref = nullptr, *d_jslot = nullptr, *d_jstep = nullptr,
            *d_J = nullptr;
@@ -196,7 +216,10 @@ struct lks_ctx {
     double* d_mslot = nullptr;
     size_t state_bytes = 0;
     std::vector<void*> slot;  // checkpoint slots
-    std::vector<void*> hist;  // recompute history (index 0 unused)
+    std::vector<void*> hist[2];  // recompute history, two buffers (index 0 unused)
+    std::vector<const void*> seg_st[2];  // where the states of the segment in each buffer live
+    cudaStream_t side = nullptr, cap2 = nullptr;  // second stream for the recompute chain (eager / capture)
+    cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_adj[2] = {nullptr, nullptr}, ev_sync[2] = {nullptr, nullptr};
     void* pp[2] = {nullptr, nullptr};
     void* tmp_state = nullptr;
     void* fin = nullptr;
@@ -417,6 +440,7 @@ void allocate(lks_ctx* c) {
     c->d_knots = (double*)dalloc(c, (size_t)p.K * D * 8);
     c->d_filt = (double*)dalloc(c, (size_t)p.K * D * 8);
     c->d_ktmp = (double*)dalloc(c, (size_t)p.K * D * 8);
+    c->d_tnorm = (double*)dalloc(c, (size_t)p.K * 8);
     c->d_s = (double*)dalloc(c, (size_t)(p.Nt + 1) * D * 8);
     c->d_uG = (double*)dalloc(c, (size_t)(p.Nt + 1) * D * 8);
     c->d_gs = (double*)dalloc(c, (size_t)(p.Nt + 1) * D * 8);
@@ -434,9 +458,12 @@ void allocate(lks_ctx* c) {
     const size_t sb = c->state_bytes;
     c->slot.resize(c->slot_used.size());
     for (auto& s : c->slot) s = dalloc(c, sb);
-    c->hist.assign(c->S + 1, nullptr);
-    if (p.ckpt != LKS_CKPT_FULL)
-        for (int k = 1; k <= c->S; ++k) c->hist[k] = dalloc(c, sb);
+    for (int h = 0; h < 2; ++h) {
+        c->hist[h].assign(c->S + 1, nullptr);
+        // the second buffer serves the pipelined sqrt sweep only
+        if (p.ckpt != LKS_CKPT_FULL && (h == 0 || p.ckpt == LKS_CKPT_SQRT))
+            for (int k = 1; k <= c->S; ++k) c->hist[h][k] = dalloc(c, sb);
+    }
     c->pp[0] = dalloc(c, sb);
     c->pp[1] = dalloc(c, sb);
     c->tmp_state = dalloc(c, sb);
@@ -449,9 +476,18 @@ void allocate(lks_ctx* c) {
     LKS_CUDA(cudaHostAlloc((void**)&c->h_flag, 16, cudaHostAllocDefault));
     *c->h_flag = 0;
     LKS_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    LKS_CUDA(cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking));
+    LKS_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+        LKS_CUDA(cudaEventCreateWithFlags(&c->ev_rec[i], cudaEventDisableTiming));
+        LKS_CUDA(cudaEventCreateWithFlags(&c->ev_adj[i], cudaEventDisableTiming));
+        LKS_CUDA(cudaEventCreateWithFlags(&c->ev_sync[i], cudaEventDisableTiming));
+    }
     LKS_CUDA(cudaEventCreateWithFlags(&c->ev_flag, cudaEventDisableTiming));
     LKS_CUDA(cudaMemset(c->d_jslot, 0, (size_t)(p.Nt + 1) * njb_of(c) * 8));
     filter_norm_kernel<<<nblk(c->nd, 128), 128>>>(c->dg, c->d_fnorm);
+    LKS_LAUNCHED();
+    motion_norm_kernel<<<nblk(p.K, 128), 128>>>(c->mg, c->d_tnorm);
     LKS_LAUNCHED();
     LKS_CUDA(cudaDeviceSynchronize());
 }
@@ -516,7 +552,15 @@ void drop_graphs(lks_ctx* c) {
 void free_all(lks_ctx* c) {
     drop_graphs(c);
     if (c->cap) cudaStreamDestroy(c->cap);
-    c->cap = nullptr;
+    if (c->cap2) cudaStreamDestroy(c->cap2);
+    if (c->side) cudaStreamDestroy(c->side);
+    c->cap = c->cap2 = c->side = nullptr;
+    for (int i = 0; i < 2; ++i) {
+        if (c->ev_rec[i]) cudaEventDestroy(c->ev_rec[i]);
+        if (c->ev_adj[i]) cudaEventDestroy(c->ev_adj[i]);
+        if (c->ev_sync[i]) cudaEventDestroy(c->ev_sync[i]);
+        c->ev_rec[i] = c->ev_adj[i] = c->ev_sync[i] = nullptr;
+    }
     for (auto e : c->evpool) cudaEventDestroy(e);
     c->evpool.clear();
     for (void* p : c->allocs) cudaFree(p);
@@ -539,7 +583,7 @@ void prepare_design_and_motion(lks_ctx* c, cudaStream_t s) {
     c->eng->kappa_ref(c->dg, c->d_gt, c->d_gb, c->d_kref64, c->d_kref, s);
     // a1: knots -> filtered -> s_n, u^G_n -> per-step pose
     const int K = c->prm.K, D = c->D, Nt = c->prm.Nt;
-    motion_filter_kernel<<<nblk((long long)K * D, 128), 128, 0, s>>>(c->mg, c->d_knots, c->d_filt, 0);
+    motion_filter_kernel<<<nblk((long long)K * D, 128), 128, 0, s>>>(c->mg, c->d_knots, c->d_tnorm, c->d_filt, 0);
     LKS_LAUNCHED();
     interp_kernel<<<nblk((long long)(Nt + 1) * D, 256), 256, 0, s>>>(c->mg, c->d_filt, c->d_s, c->d_uG);
     LKS_LAUNCHED();
@@ -669,11 +713,12 @@ void advance(lks_ctx* c, int n0, int n1, const void* in, void* out, cudaStream_t
     span_end(c, 1, e0, s);
 }
 
-// Reverse one segment (steps a+1..b): rebuild the states a+1..b that are not stored, then run the adjoint
-// steps n = b..a+1 and fold the segment's local sensitivities into the design and motion gradients.
-void do_segment(lks_ctx* c, int a, int b, const void* start, const void* end, cudaStream_t s) {
+// Rebuild the states a+1..b of a segment that are not stored (into history buffer `buf`) and record where
+// every state a..b of the segment lives.
+void recompute_segment(lks_ctx* c, int a, int b, const void* start, const void* end, int buf, cudaStream_t s) {
     const int L = b - a;
-    std::vector<const void*> st(L + 1, nullptr);
+    std::vector<const void*>& st = c->seg_st[buf];
+    st.assign(L + 1, nullptr);
     st[0] = start;
     const bool full = c->prm.ckpt == LKS_CKPT_FULL;
     cudaEvent_t er = full ? nullptr : span_begin(c, s);
@@ -684,12 +729,20 @@ void do_segment(lks_ctx* c, int a, int b, const void* start, const void* end, cu
             const int m = a + j;  // every state is a stored boundary in FULL mode
             st[j] = (m == c->prm.Nt) ? c->fin : c->slot[c->slot_of[m]];
         } else {
-            fwd_step(c, a + j, st[j - 1], c->hist[j], false, s);
-            st[j] = c->hist[j];
+            fwd_step(c, a + j, st[j - 1], c->hist[buf][j], false, s);
+            st[j] = c->hist[buf][j];
             c->stats.recompute_steps++;
         }
     }
     span_end(c, 1, er, s);
+}
+
+// Adjoint steps n = b..a+1 of a segment whose states were laid out by recompute_segment(buf), then the
+// segment's local sensitivities folded into the design gradient (strict step order) and the per-step motion
+// gradients.
+void adjoint_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
+    const int L = b - a;
+    const std::vector<const void*>& st = c->seg_st[buf];
     const int mode = c->prm.mode;
     const bool shape = mode != LKS_MODE_MOTION, motion = mode != LKS_MODE_SHAPE;
     const long long kstride = c->g.Fbn;
@@ -720,6 +773,33 @@ void do_segment(lks_ctx* c, int a, int b, const void* start, const void* end, cu
         LKS_LAUNCHED();
         c->launches++;
     }
+}
+
+// Reverse one segment (steps a+1..b) on one stream.
+void do_segment(lks_ctx* c, int a, int b, const void* start, const void* end, cudaStream_t s) {
+    recompute_segment(c, a, b, start, end, 0, s);
+    adjoint_segment(c, a, b, 0, s);
+}
+
+// sqrt(N) reverse sweep with the recompute of segment m-1 overlapping the adjoint of segment m: the two
+// chains run on two streams (two history buffers); the adjoint chain waits for its segment's recompute, the
+// recompute chain waits until the adjoint two segments later has released the history buffer.
+void reverse_sqrt_pipelined(lks_ctx* c, cudaStream_t A, cudaStream_t B) {
+    LKS_CUDA(cudaEventRecord(c->ev_sync[0], A));
+    LKS_CUDA(cudaStreamWaitEvent(B, c->ev_sync[0], 0));
+    int idx = 0;
+    for (int m = c->M - 1; m >= 0; --m, ++idx) {
+        const int buf = idx & 1;
+        const int a = c->step_of(m), b = c->step_of(m + 1);
+        if (idx >= 2) LKS_CUDA(cudaStreamWaitEvent(B, c->ev_adj[buf], 0));
+        recompute_segment(c, a, b, c->slot[c->slot_of[m]], m + 1 == c->M ? c->fin : c->slot[c->slot_of[m + 1]], buf, B);
+        LKS_CUDA(cudaEventRecord(c->ev_rec[buf], B));
+        LKS_CUDA(cudaStreamWaitEvent(A, c->ev_rec[buf], 0));
+        adjoint_segment(c, a, b, buf, A);
+        LKS_CUDA(cudaEventRecord(c->ev_adj[buf], A));
+    }
+    LKS_CUDA(cudaEventRecord(c->ev_sync[1], B));
+    LKS_CUDA(cudaStreamWaitEvent(A, c->ev_sync[1], 0));
 }
 
 int take_slot(lks_ctx* c) {
@@ -793,10 +873,7 @@ void adjoint_body(lks_ctx* c, cudaStream_t s) {
             do_segment(c, a, b, a == 0 ? c->slot[0] : c->slot[c->slot_of[a]], b == Nt ? c->fin : c->slot[c->slot_of[b]], s);
         }
     } else {
-        for (int m = c->M - 1; m >= 0; --m) {
-            const int a = c->step_of(m), b = c->step_of(m + 1);
-            do_segment(c, a, b, c->slot[c->slot_of[m]], m + 1 == c->M ? c->fin : c->slot[c->slot_of[m + 1]], s);
-        }
+        reverse_sqrt_pipelined(c, s, s == c->cap ? c->cap2 : c->side);
     }
     // b6: chain rules
     design_chain_kernel<<<nblk(c->nd, 128), 128, 0, s>>>(c->dg, c->d_dkref, c->d_gt, c->d_gb, c->d_tmp);
@@ -826,7 +903,7 @@ void finish_adjoint(lks_ctx* c, double* dgamma, double* dpos, cudaStream_t s) {
         if (c->prm.mode == LKS_MODE_SHAPE) {
             LKS_CUDA(cudaMemsetAsync(dpos, 0, (size_t)K * D * 8, s));
         } else {
-            motion_filter_kernel<<<nblk((long long)K * D, 64), 64, 0, s>>>(c->mg, c->d_ktmp, dpos, 1);
+            motion_filter_kernel<<<nblk((long long)K * D, 64), 64, 0, s>>>(c->mg, c->d_ktmp, c->d_tnorm, dpos, 1);
             LKS_LAUNCHED();
             c->launches++;
         }
@@ -1060,7 +1137,7 @@ int lks_motion_filter_dev(lks_ctx* c, const double* in, double* out, void* strea
     if (!c) return LKS_EINVAL;
     return guard(c, [&] {
         if (!in || !out) throw LksError{LKS_EINVAL, "null pointer"};
-        motion_filter_kernel<<<nblk((long long)c->prm.K * c->D, 64), 64, 0, (cudaStream_t)stream>>>(c->mg, in, out, 0);
+        motion_filter_kernel<<<nblk((long long)c->prm.K * c->D, 64), 64, 0, (cudaStream_t)stream>>>(c->mg, in, c->d_tnorm, out, 0);
         LKS_LAUNCHED();
     });
 }
@@ -1069,7 +1146,7 @@ int lks_motion_filter_T_dev(lks_ctx* c, const double* in, double* out, void* str
     if (!c) return LKS_EINVAL;
     return guard(c, [&] {
         if (!in || !out) throw LksError{LKS_EINVAL, "null pointer"};
-        motion_filter_kernel<<<nblk((long long)c->prm.K * c->D, 64), 64, 0, (cudaStream_t)stream>>>(c->mg, in, out, 1);
+        motion_filter_kernel<<<nblk((long long)c->prm.K * c->D, 64), 64, 0, (cudaStream_t)stream>>>(c->mg, in, c->d_tnorm, out, 1);
         LKS_LAUNCHED();
     });
 }

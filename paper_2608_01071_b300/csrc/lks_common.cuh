@@ -84,7 +84,31 @@ struct Pose {
     double w[3][4];     // weight of tap k: design index j = b - 2 hw + 1 + k for box coordinate b
     double dw[3][4];    // d w / d offset
     double uG[3];
+    float wf[3][4];     // FP32 copies for the FP32 state path (no FP64 work per node)
+    float dwf[3][4];
+    float uGf[3];
+    float padf;
 };
+
+// Pose values in the state precision T.
+template <typename T>
+__device__ __forceinline__ T pose_w(const Pose& P, int a, int k);
+template <>
+__device__ __forceinline__ double pose_w<double>(const Pose& P, int a, int k) { return P.w[a][k]; }
+template <>
+__device__ __forceinline__ float pose_w<float>(const Pose& P, int a, int k) { return P.wf[a][k]; }
+template <typename T>
+__device__ __forceinline__ T pose_dw(const Pose& P, int a, int k);
+template <>
+__device__ __forceinline__ double pose_dw<double>(const Pose& P, int a, int k) { return P.dw[a][k]; }
+template <>
+__device__ __forceinline__ float pose_dw<float>(const Pose& P, int a, int k) { return P.dwf[a][k]; }
+template <typename T>
+__device__ __forceinline__ T pose_uG(const Pose& P, int a);
+template <>
+__device__ __forceinline__ double pose_uG<double>(const Pose& P, int a) { return P.uG[a]; }
+template <>
+__device__ __forceinline__ float pose_uG<float>(const Pose& P, int a) { return P.uGf[a]; }
 
 // Periodic wrap (no integer division: halo indices are at most a tile past the grid, so the loops run
 // zero or one time except on grids smaller than a tile).

@@ -142,30 +142,28 @@ __device__ __forceinline__ double tri_weight(int k, int m, const MotionGeom& mg)
     return w > 0.0 ? w : 0.0;
 }
 
-// transpose = 0: out_k = sum_m w_km in_m / sum_m w_km.   transpose = 1: out_m = sum_k w_km in_k / sum_m' w_km'.
-__global__ void motion_filter_kernel(MotionGeom mg, const double* __restrict__ in, double* __restrict__ out, int transpose) {
+// Row sums sum_m w_km of the temporal filter (static per context).
+__global__ void motion_norm_kernel(MotionGeom mg, double* __restrict__ norm) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= mg.K) return;
+    double ws = 0.0;
+    for (int m = 0; m < mg.K; ++m) ws += tri_weight(k, m, mg);
+    norm[k] = ws;
+}
+
+// transpose = 0: out_k = sum_m w_km in_m / norm_k.   transpose = 1: out_m = sum_k w_km in_k / norm_k.
+__global__ void motion_filter_kernel(MotionGeom mg, const double* __restrict__ in, const double* __restrict__ norm,
+                                     double* __restrict__ out, int transpose) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= mg.K * mg.d) return;
     const int k = t / mg.d, a = t % mg.d;
     double s = 0.0;
-    if (!transpose) {
-        double ws = 0.0;
-        for (int m = 0; m < mg.K; ++m) {
-            const double w = tri_weight(k, m, mg);
-            s += w * in[m * mg.d + a];
-            ws += w;
-        }
-        out[t] = s / ws;
-    } else {
-        for (int r = 0; r < mg.K; ++r) {
-            const double w = tri_weight(r, k, mg);
-            if (w == 0.0) continue;
-            double ws = 0.0;
-            for (int m = 0; m < mg.K; ++m) ws += tri_weight(r, m, mg);
-            s += w / ws * in[r * mg.d + a];
-        }
-        out[t] = s;
+    for (int m = 0; m < mg.K; ++m) {
+        const double w = tri_weight(k, m, mg);
+        if (w == 0.0) continue;
+        s += transpose ? w * in[m * mg.d + a] / norm[m] : w * in[m * mg.d + a];
     }
+    out[t] = transpose ? s : s / norm[k];
 }
 
 __device__ __forceinline__ void interp_coef(int n, const MotionGeom& mg, int& k, double& th) {
@@ -202,7 +200,10 @@ __global__ void interp_T_kernel(MotionGeom mg, const double* __restrict__ gs, co
     if (t >= mg.K * mg.d) return;
     const int kk = t / mg.d, a = t % mg.d;
     double acc = 0.0;
-    for (int n = 0; n <= mg.Nt; ++n) {
+    // only the steps of the two segments next to knot kk carry its weight
+    const int n0 = (int)(((long long)(kk > 0 ? kk - 1 : 0) * mg.Nt) / (mg.K - 1));
+    const int n1 = (int)min((long long)mg.Nt, ((long long)(kk + 1) * mg.Nt + mg.K - 2) / (mg.K - 1));
+    for (int n = n0; n <= n1; ++n) {
         int k;
         double th;
         interp_coef(n, mg, k, th);
@@ -254,6 +255,14 @@ __global__ void pose_kernel(Geom g, int D, double o0x, double o0y, double o0z, i
             }
         }
     }
+    for (int a = 0; a < 3; ++a) {
+        for (int k = 0; k < 4; ++k) {
+            P.wf[a][k] = (float)P.w[a][k];
+            P.dwf[a][k] = (float)P.dw[a][k];
+        }
+        P.uGf[a] = (float)P.uG[a];
+    }
+    P.padf = 0.f;
     poses[n] = P;
 }
 

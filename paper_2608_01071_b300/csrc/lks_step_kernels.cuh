@@ -35,6 +35,8 @@ struct FwdArgs {
     unsigned* flag;     // stability flag (bit 0)
     int jb_lo[3];       // first block touching the probe box, per axis
     int jb_n[3];        // number of blocks touching it, per axis
+    T dir[3];           // objective direction n in T
+    T u_crit2;          // squared stability limit in T (<= 0 disables)
 };
 
 template <typename T>
@@ -48,27 +50,47 @@ struct AdjArgs {
     T* kbar;            // kappa-bar of step n on the footprint box (nullptr: no shape gradient)
     double* mslot;      // 2D motion partials of every block for step n (nullptr: no motion gradient)
     int src;            // 1: add the objective source phi (n - 1 >= 1)
+    T phi_dir[3];       // objective source weight n_a / (Nt |O|) in T
 };
 
 // ------------------------------------------------------------------------------------------------
 // Small helpers
 // ------------------------------------------------------------------------------------------------
 
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+// Programmatic dependent launch: wait until the previous kernel in the stream has completed and its memory
+// is visible, then let the next kernel in the stream be scheduled while this one runs.  Both are no-ops
+// when the kernel was launched without the programmatic-serialization attribute.
+__device__ __forceinline__ void pdl_wait_then_release() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Sum of NV values over the block: warp shuffles in the state precision T, then the warp partials in FP64
+// (FP64 throughput is scarce on this part, so per-node work never touches it).  Result valid on thread 0.
+// Fixed reduction order, so the result is deterministic.  red must hold NV * (NT / 32) doubles.
+template <int NT, int NV, typename T>
+__device__ __forceinline__ void block_sum(T (&v)[NV], double (&out)[NV], double* red) {
     constexpr int NW = (NT + 31) / 32;
-    __syncthreads();
-    if ((tid & 31) == 0) red[tid >> 5] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (tid == 0) {
-#pragma unroll 1
-        for (int i = 0; i < NW; ++i) s += red[i];
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
     }
-    return s;  // valid on thread 0
+    if ((tid & 31) == 0) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) red[c * NW + (tid >> 5)] = (double)v[c];
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+            double s = 0.0;
+#pragma unroll 1
+            for (int i = 0; i < NW; ++i) s += red[c * NW + i];
+            out[c] = s;
+        }
+    }
 }
 
 // Does the tile [x0, x0 + T) of an axis of length n touch the probe interval [lo, hi)?
@@ -87,15 +109,6 @@ __device__ __host__ inline bool tile_hits_box(int x0, int T, int n, int xs, int 
     return b0 < Fb && b0 + len - 1 >= 0;
 }
 
-// Tap weights of one axis for a node with box coordinate b: tap k reads design index j = b - 2 HW + 1 + k.
-template <typename T, int HW>
-struct AxisTaps {
-    T w[2 * HW];
-    T dw[2 * HW];
-    int j0;  // design index of tap 0
-    int nde;
-};
-
 // kappa, C and (optionally) their offset derivatives at a node of the footprint box (Eqs. kappa, u_s).
 template <typename T, int D, int HW, bool GRAD>
 __device__ __forceinline__ void map_node(const Geom& g, const Pose& P, const T* __restrict__ kref, const int* b,
@@ -113,8 +126,8 @@ __device__ __forceinline__ void map_node(const Geom& g, const Pose& P, const T* 
         for (int k = 0; k < NTAP; ++k) {
             const int j = j0[a] + k;
             const bool v = (j >= 0) && (j < g.nde[a]);
-            wt[a][k] = v ? (T)P.w[a][k] : (T)0;
-            dwt[a][k] = v ? (T)P.dw[a][k] : (T)0;
+            wt[a][k] = v ? pose_w<T>(P, a, k) : (T)0;
+            dwt[a][k] = v ? pose_dw<T>(P, a, k) : (T)0;
             sa[a] += wt[a][k];
             dsa[a] += dwt[a][k];
         }
@@ -214,10 +227,9 @@ template <typename T, int D, int HW, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(TX * TY * TZ) fwd_step_kernel(Geom g, FwdArgs<T> a) {
     using L = Lattice<D>;
     using TL = Tile<D, TX, TY, TZ>;
-    constexpr int NS = NSym<D>::value;
     constexpr int S = TL::S, M = TL::M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[32];
+    __shared__ double red[(TX * TY * TZ + 31) / 32];
     T* sp = reinterpret_cast<T*>(smem_raw);  // p' on the halo-2 region
     T* su = sp + S;                          // u_a on the halo-2 region
     T* ms = su + D * S;                      // sigma = 3 p' - 3/2 |u|^2 on the halo-1 region
@@ -227,6 +239,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) fwd_step_kernel(Geom g, FwdArgs<
     const long long N = g.N;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
+    pdl_wait_then_release();
 
     // phase 1: load p', u with a halo of 2 (periodic wrap on every axis)
     for (int l = tid; l < S; l += TL::NT) {
@@ -317,7 +330,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) fwd_step_kernel(Geom g, FwdArgs<
     if (inbox) map_node<T, D, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
     const T inv = (T)1 / ((T)1 + kap);
 #pragma unroll
-    for (int c = 0; c < D; ++c) un[c] = (accu[c] + kap * ((T)P.uG[c] * C)) * inv;
+    for (int c = 0; c < D; ++c) un[c] = (accu[c] + kap * (pose_uG<T>(P, c) * C)) * inv;
     T uw[D];
     const bool wall = wall_node<T, D>(g, xg, uw);
     if (wall) {
@@ -329,11 +342,11 @@ __global__ void __launch_bounds__(TX * TY * TZ) fwd_step_kernel(Geom g, FwdArgs<
         a.out_p[gi] = pn;
 #pragma unroll
         for (int c = 0; c < D; ++c) a.out_u[c * N + gi] = un[c];
-        if (g.u_crit2 > 0.0 && !wall) {
-            double uu = 0.0;
+        if (a.u_crit2 > (T)0 && !wall) {
+            T uu = 0;
 #pragma unroll
-            for (int c = 0; c < D; ++c) uu += (double)un[c] * (double)un[c];
-            if (!(uu <= g.u_crit2)) atomicOr(a.flag, 1u);
+            for (int c = 0; c < D; ++c) uu += un[c] * un[c];
+            if (!(uu <= a.u_crit2)) atomicOr(a.flag, 1u);
         }
     }
     // objective partial of this block (deterministic: fixed reduction order)
@@ -341,13 +354,14 @@ __global__ void __launch_bounds__(TX * TY * TZ) fwd_step_kernel(Geom g, FwdArgs<
         const int bx = (int)blockIdx.x - a.jb_lo[0], by = (int)blockIdx.y - a.jb_lo[1], bz = (int)blockIdx.z - a.jb_lo[2];
         const bool hit = bx >= 0 && bx < a.jb_n[0] && by >= 0 && by < a.jb_n[1] && bz >= 0 && bz < a.jb_n[2];
         if (hit) {
-            double v = 0.0;
+            T v[1] = {0};
             if (active && !wall && in_probe<D>(g, xg)) {
 #pragma unroll
-                for (int c = 0; c < D; ++c) v += g.dir[c] * (double)un[c];
+                for (int c = 0; c < D; ++c) v[0] += a.dir[c] * un[c];
             }
-            const double s = block_sum<TL::NT>(v, red);
-            if (tid == 0) a.jslot[bx + a.jb_n[0] * (by + a.jb_n[1] * bz)] = s;
+            double s[1];
+            block_sum<TL::NT, 1, T>(v, s, red);
+            if (tid == 0) a.jslot[bx + a.jb_n[0] * (by + a.jb_n[1] * bz)] = s[0];
         }
     }
 }
@@ -368,7 +382,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) adj_step_kernel(Geom g, AdjArgs<
     constexpr int NS = NSym<D>::value;
     constexpr int S = TL::S, M = TL::M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[32];
+    __shared__ double red[2 * D * ((TX * TY * TZ + 31) / 32)];
     T* sp = reinterpret_cast<T*>(smem_raw);  // p-bar* on the halo-2 region
     T* su = sp + S;                          // u-bar* on the halo-2 region
     T* m0 = su + D * S;                      // M0 on the halo-1 region
@@ -380,6 +394,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) adj_step_kernel(Geom g, AdjArgs<
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
     const Pose& P = *a.pose;
+    pdl_wait_then_release();
 
     // phase 1: Brinkman and wall adjoint on the halo-2 region
     for (int l = tid; l < S; l += TL::NT) {
@@ -472,7 +487,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) adj_step_kernel(Geom g, AdjArgs<
                 v += (T)9 * m2s[mc] * u[c];
                 v += A * (m2s[mc - mstride] - m2s[mc + mstride]);
             }
-            if (probe) v += (T)(g.dir[e] * g.phi);
+            if (probe) v += a.phi_dir[e];
             a.lam_out[(1 + e) * N + gi] = v;
         }
     }
@@ -485,9 +500,9 @@ __global__ void __launch_bounds__(TX * TY * TZ) adj_step_kernel(Geom g, AdjArgs<
         b[c] = box_coord(xg[c], P.xs[c], g.Fb[c], g.n[c], g.periodic[c]);
         inbox = inbox && b[c] >= 0;
     }
-    double mv[2 * D];
+    T mv[2 * D];
 #pragma unroll
-    for (int c = 0; c < 2 * D; ++c) mv[c] = 0.0;
+    for (int c = 0; c < 2 * D; ++c) mv[c] = 0;
     if (inbox) {
         T kb = 0;
         if (!wall) {
@@ -499,16 +514,16 @@ __global__ void __launch_bounds__(TX * TY * TZ) adj_step_kernel(Geom g, AdjArgs<
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 const T lu = a.lam_in[(1 + c) * N + gi];
-                const T uS = (T)P.uG[c] * C;
+                const T uS = pose_uG<T>(P, c) * C;
                 kb += lu * (uS - a.u_cur[c * N + gi]);
                 usb[c] = lu * kap * inv;
-                cbar += usb[c] * (T)P.uG[c];
+                cbar += usb[c] * pose_uG<T>(P, c);
             }
             kb *= inv;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                mv[c] = (double)kb * (double)dk[c] + (double)cbar * (double)dC[c];
-                mv[D + c] = (double)usb[c] * (double)C;
+                mv[c] = kb * dk[c] + cbar * dC[c];
+                mv[D + c] = usb[c] * C;
             }
         }
         if (a.kbar != nullptr) {
@@ -524,10 +539,11 @@ __global__ void __launch_bounds__(TX * TY * TZ) adj_step_kernel(Geom g, AdjArgs<
         for (int c = 0; c < D; ++c) hit = hit && tile_hits_box(t0[c], tt[c], g.n[c], P.xs[c], g.Fb[c], g.periodic[c]);
         if (hit) {
             const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+            double s[2 * D];
+            block_sum<TL::NT, 2 * D, T>(mv, s, red);
+            if (tid == 0) {
 #pragma unroll
-            for (int c = 0; c < 2 * D; ++c) {
-                const double s = block_sum<TL::NT>(mv[c], red);
-                if (tid == 0) a.mslot[(long long)blk * 2 * D + c] = s;
+                for (int c = 0; c < 2 * D; ++c) a.mslot[(long long)blk * 2 * D + c] = s[c];
             }
         }
     }
@@ -566,7 +582,7 @@ __global__ void design_gather_kernel(Geom g, const Pose* __restrict__ poses, con
                     ok = x >= 0 && x < g.n[a];
                 }
                 bb[a][k] = ok ? b : -1;
-                ww[a][k] = (T)P.w[a][k];
+                ww[a][k] = pose_w<T>(P, a, k);
             }
         }
         T sum = 0;
