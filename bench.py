@@ -157,6 +157,7 @@ def run_ours(args):
     D = len(w["shape"])
     N = node_count(w)
     solver = Solver.from_workload(w)
+    st0 = solver.stats()
     solver.set_timing(True)
     gamma, knots = draw_gamma(w), draw_knots(w)
     dev = torch.device("cuda", local)
@@ -253,6 +254,7 @@ def run_ours(args):
                          "recompute_us_per_launch": rec_ms * 1e3},
             "e2e": {"value": e2e, "unit": "G node-steps/s (fwd+adj)", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches * world),
+            "tile_rows": [st0["tile_rows_fwd"], st0["tile_rows_adj"]],
             "clocks": clk,
             "wall_s": t_wall,
         }

@@ -71,6 +71,9 @@ enum { LKS_MODE_JOINT = 0, LKS_MODE_SHAPE = 1, LKS_MODE_MOTION = 2 };
  *  seg_len        recompute-segment length for REVOLVE (0 = automatic).
  *  mode           which gradients lks_adjoint produces (the others are returned as zeros).
  *  u_crit         stability limit on |u| checked every forward step (<= 0 disables); LKS_EUNSTABLE.
+ *  tile_rows      D2Q9 step kernels: 1 = shared-memory tiles of 32 x 8 nodes; 4, 8 or 16 (16: LKS_FP32 only) =
+ *                 warp-column kernels with that many grid rows per warp; 0 = autotune at lks_create (times
+ *                 every choice on the context's buffers; cached per process).
  */
 typedef struct lks_params {
     uint32_t size;
@@ -101,6 +104,7 @@ typedef struct lks_params {
     int64_t ckpt_bytes;
     int32_t mode;
     double u_crit;
+    int32_t tile_rows;
 } lks_params;
 
 typedef struct lks_ctx lks_ctx;
@@ -114,6 +118,8 @@ typedef struct lks_stats {
     int64_t device_bytes;      /* device memory held by the context */
     int32_t ckpt_slots;        /* checkpoints in use */
     int32_t seg_len;           /* recompute segment length */
+    int32_t tile_rows_fwd;     /* D2Q9: rows per warp chosen for the forward / adjoint step kernels */
+    int32_t tile_rows_adj;
     /* With lks_set_timing(ctx, 1): device time (CUDA events on the launching stream) of the last call pair. */
     double ms_forward_steps;   /* the Nt forward-step kernels of lks_forward */
     double ms_recompute_steps; /* forward-step kernels re-run by lks_adjoint */

@@ -48,6 +48,7 @@ class lks_params(C.Structure):
         ("ckpt_bytes", C.c_int64),
         ("mode", C.c_int32),
         ("u_crit", C.c_double),
+        ("tile_rows", C.c_int32),
     ]
 
 
@@ -60,6 +61,8 @@ class lks_stats(C.Structure):
         ("device_bytes", C.c_int64),
         ("ckpt_slots", C.c_int32),
         ("seg_len", C.c_int32),
+        ("tile_rows_fwd", C.c_int32),
+        ("tile_rows_adj", C.c_int32),
         ("ms_forward_steps", C.c_double),
         ("ms_recompute_steps", C.c_double),
         ("ms_adjoint_steps", C.c_double),

@@ -61,6 +61,7 @@ def params_from_workload(w: dict) -> _abi.lks_params:
     p.ckpt_bytes = int(w.get("ckpt_bytes", 0))
     p.mode = _MODE[w.get("mode", "joint")]
     p.u_crit = w.get("u_crit", 0.3)
+    p.tile_rows = w.get("tile_rows", 0)
     return p
 
 

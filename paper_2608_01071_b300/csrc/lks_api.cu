@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -15,6 +16,9 @@
 #include "lks_common.cuh"
 #include "lks_prep_kernels.cuh"
 #include "lks_step_kernels.cuh"
+#include "lks_step2d.cuh"
+#include <map>
+#include <tuple>
 
 using namespace lks;
 
@@ -62,12 +66,19 @@ void launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, bo
 // ------------------------------------------------------------------------------------------------
 struct Engine {
     bool pdl = true;  // programmatic dependent launch of the step kernels
+    dim3 fthreads, athreads;  // threads per block of the forward / adjoint step kernels
+    dim3 ftile, atile;        // analysis nodes covered per block
+    dim3 fgrid, agrid;
+    int rows_f = 0, rows_a = 0;  // D2Q9: rows per warp of the forward / adjoint kernels (0 elsewhere)
     virtual ~Engine() {}
-    virtual dim3 block() const = 0;
-    virtual void fwd(const Geom& g, dim3 grid, const void* in, void* out, const void* kref, const Pose* pose,
-                     double* jslot, unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) = 0;
-    virtual void adj(const Geom& g, dim3 grid, const void* lam_in, void* lam_out, const void* prev, const void* cur,
-                     const void* kref, const Pose* pose, void* kbar, double* mslot, int src, cudaStream_t s) = 0;
+    // D2Q9 only: choose the rows per warp (4, 8, 16 or 32) of the forward and adjoint step kernels
+    virtual bool set_rows(int rf, int ra, const Geom& g) { return false; }
+    virtual void fwd(const Geom& g, const void* in, void* out, const void* kref, const Pose* pose, double* jslot,
+                     unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) = 0;
+    virtual void adj(const Geom& g, const void* lam_in, void* lam_out, const void* prev, const void* cur,
+                     const void* kref, const Pose* pose, void* boxbuf, int src, cudaStream_t s) = 0;
+    virtual void sens(const Geom& g, const Pose* poses, const void* kref, const void* boxbuf, long long bstride,
+                      int n_first, int nsteps, void* kbar, double* mslot, cudaStream_t s) = 0;
     virtual void gather(const Geom& g, const Pose* poses, const void* kbar, int n_first, int nsteps,
                         long long kstride, double* dkref, cudaStream_t s) = 0;
     virtual void kappa_ref(const DesignGeom& dg, const double* gt, double* gb, double* k64, void* k, cudaStream_t s) = 0;
@@ -76,52 +87,51 @@ struct Engine {
     virtual void export_state(const Geom& g, const void* st, double* p, double* u, cudaStream_t s) = 0;
 };
 
-template <typename T, int D, int HW>
-struct EngineT : Engine {
-    static constexpr int TX = 32, TY = (D == 2) ? 8 : 4, TZ = (D == 2) ? 1 : 4;
-    using TL = Tile<D, TX, TY, TZ>;
-    static constexpr size_t smem_fwd = sizeof(T) * ((D + 1) * TL::S + (1 + NSym<D>::value) * TL::M);
-    static constexpr size_t smem_adj = sizeof(T) * ((D + 1) * TL::S + (1 + D + NSym<D>::value) * TL::M);
+template <typename T>
+FwdArgs<T> make_fwd_args(const Geom& g, const void* in, void* out, const void* kref, const Pose* pose, double* jslot,
+                         unsigned* flag, const int* jlo, const int* jn) {
+    FwdArgs<T> a;
+    for (int i = 0; i < 3; ++i) {
+        a.jb_lo[i] = jlo[i];
+        a.jb_n[i] = jn[i];
+        a.dir[i] = (T)g.dir[i];
+    }
+    a.in = (const T*)in;
+    a.out_p = (T*)out;
+    a.out_u = (T*)out + g.N;
+    a.kref = (const T*)kref;
+    a.pose = pose;
+    a.jslot = jslot;
+    a.flag = flag;
+    a.u_crit2 = (T)g.u_crit2;
+    return a;
+}
 
-    EngineT() {
-        LKS_CUDA(cudaFuncSetAttribute(fwd_step_kernel<T, D, HW, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem_fwd));
-        LKS_CUDA(cudaFuncSetAttribute(adj_step_kernel<T, D, HW, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem_adj));
-    }
-    dim3 block() const override { return dim3(TX, TY, TZ); }
-    void fwd(const Geom& g, dim3 grid, const void* in, void* out, const void* kref, const Pose* pose, double* jslot,
-             unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) override {
-        FwdArgs<T> a;
-        for (int i = 0; i < 3; ++i) {
-            a.jb_lo[i] = jlo[i];
-            a.jb_n[i] = jn[i];
-        }
-        a.in = (const T*)in;
-        a.out_p = (T*)out;
-        a.out_u = (T*)out + g.N;
-        a.kref = (const T*)kref;
-        a.pose = pose;
-        a.jslot = jslot;
-        a.flag = flag;
-        for (int i = 0; i < 3; ++i) a.dir[i] = (T)g.dir[i];
-        a.u_crit2 = (T)g.u_crit2;
-        launch_pdl(fwd_step_kernel<T, D, HW, TX, TY, TZ>, grid, block(), smem_fwd, s, pdl, g, a);
-    }
-    void adj(const Geom& g, dim3 grid, const void* lam_in, void* lam_out, const void* prev, const void* cur,
-             const void* kref, const Pose* pose, void* kbar, double* mslot, int src, cudaStream_t s) override {
-        AdjArgs<T> a;
-        a.lam_in = (const T*)lam_in;
-        a.lam_out = (T*)lam_out;
-        a.u_prev = (const T*)prev + g.N;
-        a.u_cur = (const T*)cur + g.N;
-        a.kref = (const T*)kref;
-        a.pose = pose;
-        a.kbar = (T*)kbar;
-        a.mslot = mslot;
-        a.src = src;
-        for (int i = 0; i < 3; ++i) a.phi_dir[i] = (T)(g.dir[i] * g.phi);
-        launch_pdl(adj_step_kernel<T, D, HW, TX, TY, TZ>, grid, block(), smem_adj, s, pdl, g, a);
+template <typename T>
+AdjArgs<T> make_adj_args(const Geom& g, const void* lam_in, void* lam_out, const void* prev, const void* cur,
+                         const void* kref, const Pose* pose, void* boxbuf, int src) {
+    AdjArgs<T> a;
+    a.lam_in = (const T*)lam_in;
+    a.lam_out = (T*)lam_out;
+    a.u_prev = (const T*)prev + g.N;
+    a.u_cur = (const T*)cur + g.N;
+    a.kref = (const T*)kref;
+    a.pose = pose;
+    a.boxbuf = (T*)boxbuf;
+    a.src = src;
+    for (int i = 0; i < 3; ++i) a.phi_dir[i] = (T)(g.dir[i] * g.phi);
+    return a;
+}
+
+// Shared pieces of both engines.
+template <typename T, int D, int HW>
+struct EngineCommon : Engine {
+    void sens(const Geom& g, const Pose* poses, const void* kref, const void* boxbuf, long long bstride, int n_first,
+              int nsteps, void* kbar, double* mslot, cudaStream_t s) override {
+        const dim3 grid(nblk(g.Fbn, 256), nsteps, 1);
+        adj_sens_kernel<T, D, HW><<<grid, 256, 0, s>>>(g, poses, (const T*)kref, (const T*)boxbuf, bstride, n_first,
+                                                       (T*)kbar, mslot);
+        LKS_LAUNCHED();
     }
     void gather(const Geom& g, const Pose* poses, const void* kbar, int n_first, int nsteps, long long kstride,
                 double* dkref, cudaStream_t s) override {
@@ -148,15 +158,106 @@ struct EngineT : Engine {
     }
 };
 
-template <typename T, int D>
-Engine* make_engine_hw(int hw) {
-    if (hw == 1) return new EngineT<T, D, 1>();
-    return new EngineT<T, D, 2>();
+// Generic shared-memory tile engine (used for D3Q15).
+template <typename T, int D, int HW>
+struct EngineT : EngineCommon<T, D, HW> {
+    static constexpr int TX = 32, TY = (D == 2) ? 8 : 4, TZ = (D == 2) ? 1 : 4;
+    using TL = Tile<D, TX, TY, TZ>;
+    static constexpr size_t smem_fwd = sizeof(T) * ((D + 1) * TL::S + (1 + NSym<D>::value) * TL::M);
+    static constexpr size_t smem_adj = sizeof(T) * ((D + 1) * TL::S + (1 + D + NSym<D>::value) * TL::M);
+
+    explicit EngineT(const Geom& g) {
+        LKS_CUDA(cudaFuncSetAttribute(fwd_step_kernel<T, D, HW, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem_fwd));
+        LKS_CUDA(cudaFuncSetAttribute(adj_step_kernel<T, D, HW, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem_adj));
+        this->fthreads = this->athreads = this->ftile = this->atile = dim3(TX, TY, TZ);
+        this->fgrid = this->agrid = dim3(nblk(g.n[0], TX), nblk(g.n[1], TY), nblk(g.n[2], TZ));
+    }
+    void fwd(const Geom& g, const void* in, void* out, const void* kref, const Pose* pose, double* jslot,
+             unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) override {
+        auto a = make_fwd_args<T>(g, in, out, kref, pose, jslot, flag, jlo, jn);
+        launch_pdl(fwd_step_kernel<T, D, HW, TX, TY, TZ>, this->fgrid, this->fthreads, smem_fwd, s, this->pdl, g, a);
+    }
+    void adj(const Geom& g, const void* lam_in, void* lam_out, const void* prev, const void* cur, const void* kref,
+             const Pose* pose, void* boxbuf, int src, cudaStream_t s) override {
+        auto a = make_adj_args<T>(g, lam_in, lam_out, prev, cur, kref, pose, boxbuf, src);
+        launch_pdl(adj_step_kernel<T, D, HW, TX, TY, TZ>, this->agrid, this->athreads, smem_adj, s, this->pdl, g, a);
+    }
+};
+
+// D2Q9 engine with two kernel families: rows = 1 selects the shared-memory tile kernels (32 x 8 nodes per block,
+// best on small grids where the launch is latency bound), rows = 4, 8, 16 the warp-column kernels with that many
+// rows per warp and WY = 4 warps per block (fewer instructions per node, for grids with many warps).
+template <typename T, int HW>
+struct Engine2D : EngineCommon<T, 2, HW> {
+    static constexpr int WY = 4;
+    using TL = Tile<2, 32, 8, 1>;
+    static constexpr size_t smem_fwd = sizeof(T) * (3 * TL::S + 4 * TL::M);
+    static constexpr size_t smem_adj = sizeof(T) * (3 * TL::S + 6 * TL::M);
+    explicit Engine2D(const Geom& g) { set_rows(1, 1, g); }
+    static void geom(int r, const Geom& g, dim3& th, dim3& tile, dim3& grid) {
+        if (r == 1) {
+            th = tile = dim3(32, 8, 1);
+            grid = dim3(nblk(g.n[0], 32), nblk(g.n[1], 8), 1);
+        } else {
+            th = dim3(32 * WY, 1, 1);
+            tile = dim3(kLanesOut, r * WY, 1);
+            grid = dim3(nblk(g.n[0], kLanesOut), nblk(g.n[1], r * WY), 1);
+        }
+    }
+    bool set_rows(int rf, int ra, const Geom& g) override {
+        // rows kept in registers grow with R: FP32 allows up to 16, FP64 up to 8 without spills
+        auto ok = [](int r) { return r == 1 || r == 4 || r == 8 || (r == 16 && sizeof(T) == 4); };
+        if (!ok(rf) || !ok(ra)) return false;
+        this->rows_f = rf;
+        this->rows_a = ra;
+        geom(rf, g, this->fthreads, this->ftile, this->fgrid);
+        geom(ra, g, this->athreads, this->atile, this->agrid);
+        return true;
+    }
+    template <int R>
+    void fwd_r(const Geom& g, FwdArgs<T> a, cudaStream_t s) {
+        launch_pdl(fwd2d_kernel<T, HW, R, WY>, this->fgrid, this->fthreads, 0, s, this->pdl, g, a);
+    }
+    template <int R>
+    void adj_r(const Geom& g, AdjArgs<T> a, cudaStream_t s) {
+        launch_pdl(adj2d_kernel<T, HW, R, WY>, this->agrid, this->athreads, 0, s, this->pdl, g, a);
+    }
+    void fwd(const Geom& g, const void* in, void* out, const void* kref, const Pose* pose, double* jslot,
+             unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) override {
+        auto a = make_fwd_args<T>(g, in, out, kref, pose, jslot, flag, jlo, jn);
+        switch (this->rows_f) {
+            case 1:
+                launch_pdl(fwd_step_kernel<T, 2, HW, 32, 8, 1>, this->fgrid, this->fthreads, smem_fwd, s, this->pdl, g, a);
+                break;
+            case 4: fwd_r<4>(g, a, s); break;
+            case 8: fwd_r<8>(g, a, s); break;
+            default: fwd_r<(sizeof(T) == 4 ? 16 : 8)>(g, a, s); break;
+        }
+    }
+    void adj(const Geom& g, const void* lam_in, void* lam_out, const void* prev, const void* cur, const void* kref,
+             const Pose* pose, void* boxbuf, int src, cudaStream_t s) override {
+        auto a = make_adj_args<T>(g, lam_in, lam_out, prev, cur, kref, pose, boxbuf, src);
+        switch (this->rows_a) {
+            case 1:
+                launch_pdl(adj_step_kernel<T, 2, HW, 32, 8, 1>, this->agrid, this->athreads, smem_adj, s, this->pdl, g, a);
+                break;
+            case 4: adj_r<4>(g, a, s); break;
+            case 8: adj_r<8>(g, a, s); break;
+            default: adj_r<(sizeof(T) == 4 ? 16 : 8)>(g, a, s); break;
+        }
+    }
+};
+
+template <typename T>
+Engine* make_engine_t(int D, int hw, const Geom& g) {
+    if (D == 2) return hw == 1 ? (Engine*)new Engine2D<T, 1>(g) : (Engine*)new Engine2D<T, 2>(g);
+    return hw == 1 ? (Engine*)new EngineT<T, 3, 1>(g) : (Engine*)new EngineT<T, 3, 2>(g);
 }
 
-Engine* make_engine(int precision, int D, int hw) {
-    if (precision == LKS_FP64) return D == 2 ? make_engine_hw<double, 2>(hw) : make_engine_hw<double, 3>(hw);
-    return D == 2 ? make_engine_hw<float, 2>(hw) : make_engine_hw<float, 3>(hw);
+Engine* make_engine(int precision, int D, int hw, const Geom& g) {
+    return precision == LKS_FP64 ? make_engine_t<double>(D, hw, g) : make_engine_t<float>(D, hw, g);
 }
 
 // Binomial coefficient C(c + r, c), saturating.
@@ -192,8 +293,8 @@ struct lks_ctx {
     double o0[3] = {0, 0, 0};
     size_t tsize = 8;
     std::unique_ptr<Engine> eng;
-    dim3 grid, block;
-    int nblocks = 0;
+    int max_ablocks = 0;  // most adjoint blocks over all tile choices (motion-slot stride)
+    int max_njb = 0;      // most probe blocks over all tile choices (objective-slot stride)
     long long nd = 0, nde = 0;
     std::string err;
     lks_stats stats;
@@ -214,12 +315,17 @@ struct lks_ctx {
     cudaEvent_t ev_flag = nullptr;
     void* d_kbar = nullptr;
     double* d_mslot = nullptr;
+    void* d_boxbuf = nullptr;   // two buffers of Lmax steps x 2D planes x Fbn (lam_u, u_n on the footprint box)
+    long long box_step = 0;     // elements per step in d_boxbuf
+    int nsb = 0;                // sensitivity blocks per step
     size_t state_bytes = 0;
     std::vector<void*> slot;  // checkpoint slots
     std::vector<void*> hist[2];  // recompute history, two buffers (index 0 unused)
     std::vector<const void*> seg_st[2];  // where the states of the segment in each buffer live
-    cudaStream_t side = nullptr, cap2 = nullptr;  // second stream for the recompute chain (eager / capture)
-    cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_adj[2] = {nullptr, nullptr}, ev_sync[2] = {nullptr, nullptr};
+    cudaStream_t side = nullptr, cap2 = nullptr;   // recompute chain (eager / capture)
+    cudaStream_t side2 = nullptr, cap3 = nullptr;  // sensitivity chain (eager / capture)
+    cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_adj[2] = {nullptr, nullptr}, ev_sens[2] = {nullptr, nullptr};
+    cudaEvent_t ev_sync[3] = {nullptr, nullptr, nullptr};
     void* pp[2] = {nullptr, nullptr};
     void* tmp_state = nullptr;
     void* fin = nullptr;
@@ -314,6 +420,9 @@ void validate(const lks_params* p) {
     if (p->ckpt < LKS_CKPT_FULL || p->ckpt > LKS_CKPT_REVOLVE) bad("unknown ckpt");
     if (p->mode < LKS_MODE_JOINT || p->mode > LKS_MODE_MOTION) bad("unknown mode");
     if (p->ckpt_slots < 0 || p->seg_len < 0 || p->ckpt_bytes < 0) bad("negative checkpoint setting");
+    if (p->tile_rows != 0 && p->tile_rows != 1 && p->tile_rows != 4 && p->tile_rows != 8 &&
+        !(p->tile_rows == 16 && p->precision == LKS_FP32))
+        bad("tile_rows must be 0 (autotune), 1 (shared-memory tiles), 4, 8, or 16 (FP32 only)");
 }
 
 void setup_geometry(lks_ctx* c) {
@@ -421,6 +530,89 @@ void plan_checkpoints(lks_ctx* c, size_t state_bytes) {
 
 int njb_of(const lks_ctx* c);
 
+// Size the slot strides for every tile choice the autotuner may make, then start from the default tiles.
+void choose_rows_initial(lks_ctx* c) {
+    c->max_ablocks = 0;
+    c->max_njb = 0;
+    const int cand[4] = {1, 4, 8, 16};
+    const int nc = c->D == 2 ? (c->tsize == 4 ? 4 : 3) : 1;
+    for (int i = 0; i < nc; ++i) {
+        if (c->D == 2) c->eng->set_rows(cand[i], cand[i], c->g);
+        const dim3 ag = c->eng->agrid;
+        c->max_ablocks = std::max(c->max_ablocks, (int)(ag.x * ag.y * ag.z));
+        c->max_njb = std::max(c->max_njb, njb_of(c));
+    }
+    const int r = c->prm.tile_rows > 0 ? c->prm.tile_rows : 1;
+    if (c->D == 2) c->eng->set_rows(r, r, c->g);
+}
+
+// Tile autotuner (D2Q9): time the forward and adjoint step kernels for every rows-per-warp choice on the
+// context's own buffers and keep the fastest of each.  Results are cached per (device, precision, kernel
+// width, grid) for the life of the process.
+void autotune_rows(lks_ctx* c) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> cache;
+    int dev = 0;
+    LKS_CUDA(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(dev, (int)c->tsize, c->hw, c->g.n[0], c->g.n[1]);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            c->eng->set_rows(it->second.first, it->second.second, c->g);
+            return;
+        }
+    }
+    cudaStream_t s = c->side;
+    LKS_CUDA(cudaMemsetAsync(c->d_pose, 0, sizeof(Pose), s));
+    LKS_CUDA(cudaMemsetAsync(c->lam[0], 0, c->state_bytes, s));
+    LKS_CUDA(cudaMemsetAsync(c->lam[1], 0, c->state_bytes, s));
+    c->eng->init_state(c->g, c->slot[0], s);
+    cudaEvent_t e0, e1;
+    LKS_CUDA(cudaEventCreate(&e0));
+    LKS_CUDA(cudaEventCreate(&e1));
+    const int cand[4] = {1, 4, 8, 16};
+    const int nc = c->tsize == 4 ? 4 : 3;
+    float best_f = 1e30f, best_a = 1e30f;
+    int rf = 1, ra = 1;
+    const int reps = 20;
+    const int jlo[3] = {0, 0, 0}, jn[3] = {1, 1, 1};
+    for (int ci = 0; ci < nc; ++ci) {
+        const int r = cand[ci];
+        c->eng->set_rows(r, r, c->g);
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int k = 0; k < 3 + reps; ++k) {
+                if (k == 3) LKS_CUDA(cudaEventRecord(e0, s));
+                if (pass == 0)
+                    c->eng->fwd(c->g, c->slot[0], c->pp[k & 1], c->d_kref, c->d_pose, nullptr, c->d_flag, jlo, jn, s);
+                else
+                    c->eng->adj(c->g, c->lam[k & 1], c->lam[(k + 1) & 1], c->slot[0], c->slot[0], c->d_kref, c->d_pose,
+                                c->d_boxbuf, 1, s);
+            }
+            LKS_CUDA(cudaEventRecord(e1, s));
+            LKS_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            LKS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (std::getenv("LKS_TUNE_VERBOSE"))
+                std::fprintf(stderr, "lks autotune %dx%d %s rows=%d: %.3f us/launch\n", c->g.n[0], c->g.n[1],
+                             pass == 0 ? "forward" : "adjoint", r, 1e3f * ms / reps);
+            if (pass == 0 && ms < best_f) {
+                best_f = ms;
+                rf = r;
+            }
+            if (pass == 1 && ms < best_a) {
+                best_a = ms;
+                ra = r;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->eng->set_rows(rf, ra, c->g);
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = std::make_pair(rf, ra);
+}
+
 void allocate(lks_ctx* c) {
     const lks_params& p = c->prm;
     const int D = c->D;
@@ -446,14 +638,17 @@ void allocate(lks_ctx* c) {
     c->d_gs = (double*)dalloc(c, (size_t)(p.Nt + 1) * D * 8);
     c->d_guG = (double*)dalloc(c, (size_t)(p.Nt + 1) * D * 8);
     c->d_pose = (Pose*)dalloc(c, (size_t)(p.Nt + 1) * sizeof(Pose));
-    c->d_jslot = (double*)dalloc(c, (size_t)(p.Nt + 1) * njb_of(c) * 8);
+    c->d_jslot = (double*)dalloc(c, (size_t)(p.Nt + 1) * c->max_njb * 8);
     c->d_out_g = (double*)dalloc(c, c->nd * 8);
     c->d_out_k = (double*)dalloc(c, (size_t)p.K * D * 8);
     c->d_jstep = (double*)dalloc(c, (size_t)(p.Nt + 1) * 8);
     c->d_J = (double*)dalloc(c, 8);
     c->d_flag = (unsigned*)dalloc(c, 16);
     c->d_kbar = dalloc(c, (size_t)c->Lmax * c->g.Fbn * ts);
-    c->d_mslot = (double*)dalloc(c, (size_t)c->Lmax * c->nblocks * 2 * D * 8);
+    c->nsb = (int)nblk(c->g.Fbn, 256);
+    c->d_mslot = (double*)dalloc(c, (size_t)c->Lmax * c->nsb * 2 * D * 8);
+    c->box_step = 2LL * D * c->g.Fbn;
+    c->d_boxbuf = dalloc(c, (size_t)2 * c->Lmax * c->box_step * ts);
 
     const size_t sb = c->state_bytes;
     c->slot.resize(c->slot_used.size());
@@ -477,14 +672,18 @@ void allocate(lks_ctx* c) {
     *c->h_flag = 0;
     LKS_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
     LKS_CUDA(cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking));
+    LKS_CUDA(cudaStreamCreateWithFlags(&c->cap3, cudaStreamNonBlocking));
     LKS_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    LKS_CUDA(cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking));
     for (int i = 0; i < 2; ++i) {
         LKS_CUDA(cudaEventCreateWithFlags(&c->ev_rec[i], cudaEventDisableTiming));
         LKS_CUDA(cudaEventCreateWithFlags(&c->ev_adj[i], cudaEventDisableTiming));
-        LKS_CUDA(cudaEventCreateWithFlags(&c->ev_sync[i], cudaEventDisableTiming));
+        LKS_CUDA(cudaEventCreateWithFlags(&c->ev_sens[i], cudaEventDisableTiming));
     }
+    for (int i = 0; i < 3; ++i) LKS_CUDA(cudaEventCreateWithFlags(&c->ev_sync[i], cudaEventDisableTiming));
     LKS_CUDA(cudaEventCreateWithFlags(&c->ev_flag, cudaEventDisableTiming));
-    LKS_CUDA(cudaMemset(c->d_jslot, 0, (size_t)(p.Nt + 1) * njb_of(c) * 8));
+    LKS_CUDA(cudaMemset(c->d_jslot, 0, (size_t)(p.Nt + 1) * c->max_njb * 8));
+    LKS_CUDA(cudaMemset(c->d_pose, 0, (size_t)(p.Nt + 1) * sizeof(Pose)));
     filter_norm_kernel<<<nblk(c->nd, 128), 128>>>(c->dg, c->d_fnorm);
     LKS_LAUNCHED();
     motion_norm_kernel<<<nblk(p.K, 128), 128>>>(c->mg, c->d_tnorm);
@@ -551,15 +750,19 @@ void drop_graphs(lks_ctx* c) {
 
 void free_all(lks_ctx* c) {
     drop_graphs(c);
-    if (c->cap) cudaStreamDestroy(c->cap);
-    if (c->cap2) cudaStreamDestroy(c->cap2);
-    if (c->side) cudaStreamDestroy(c->side);
-    c->cap = c->cap2 = c->side = nullptr;
+    for (cudaStream_t* st : {&c->cap, &c->cap2, &c->cap3, &c->side, &c->side2}) {
+        if (*st) cudaStreamDestroy(*st);
+        *st = nullptr;
+    }
     for (int i = 0; i < 2; ++i) {
-        if (c->ev_rec[i]) cudaEventDestroy(c->ev_rec[i]);
-        if (c->ev_adj[i]) cudaEventDestroy(c->ev_adj[i]);
+        for (cudaEvent_t* e : {&c->ev_rec[i], &c->ev_adj[i], &c->ev_sens[i]}) {
+            if (*e) cudaEventDestroy(*e);
+            *e = nullptr;
+        }
+    }
+    for (int i = 0; i < 3; ++i) {
         if (c->ev_sync[i]) cudaEventDestroy(c->ev_sync[i]);
-        c->ev_rec[i] = c->ev_adj[i] = c->ev_sync[i] = nullptr;
+        c->ev_sync[i] = nullptr;
     }
     for (auto e : c->evpool) cudaEventDestroy(e);
     c->evpool.clear();
@@ -599,8 +802,8 @@ void fwd_step(lks_ctx* c, int n, const void* in, void* out, bool objective, cuda
 
 // probe-block window of the forward kernel's objective slots
 static void probe_blocks(const lks_ctx* c, int lo[3], int cnt[3]) {
-    const int T[3] = {(int)c->block.x, (int)c->block.y, (int)c->block.z};
-    const int G[3] = {(int)c->grid.x, (int)c->grid.y, (int)c->grid.z};
+    const int T[3] = {(int)c->eng->ftile.x, (int)c->eng->ftile.y, (int)c->eng->ftile.z};
+    const int G[3] = {(int)c->eng->fgrid.x, (int)c->eng->fgrid.y, (int)c->eng->fgrid.z};
     for (int a = 0; a < 3; ++a) {
         if (a >= c->D) {
             lo[a] = 0;
@@ -627,7 +830,7 @@ void fwd_step(lks_ctx* c, int n, const void* in, void* out, bool objective, cuda
     int lo[3], cnt[3];
     probe_blocks(c, lo, cnt);
     const int njb = cnt[0] * cnt[1] * cnt[2];
-    c->eng->fwd(c->g, c->grid, in, out, c->d_kref, c->d_pose + n,
+    c->eng->fwd(c->g, in, out, c->d_kref, c->d_pose + n,
                 objective ? c->d_jslot + (long long)n * njb : nullptr, c->d_flag, lo, cnt, s);
     c->launches++;
 }
@@ -737,39 +940,42 @@ void recompute_segment(lks_ctx* c, int a, int b, const void* start, const void* 
     span_end(c, 1, er, s);
 }
 
-// Adjoint steps n = b..a+1 of a segment whose states were laid out by recompute_segment(buf), then the
-// segment's local sensitivities folded into the design gradient (strict step order) and the per-step motion
-// gradients.
+// Adjoint steps n = b..a+1 of a segment whose states were laid out by recompute_segment(buf); each step also
+// records lam_u and u_n on the footprint box into box buffer `buf` for sens_segment.
 void adjoint_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
-    const int L = b - a;
     const std::vector<const void*>& st = c->seg_st[buf];
-    const int mode = c->prm.mode;
-    const bool shape = mode != LKS_MODE_MOTION, motion = mode != LKS_MODE_SHAPE;
-    const long long kstride = c->g.Fbn;
     cudaEvent_t ea = span_begin(c, s);
-    const long long mstride = (long long)c->nblocks * 2 * c->D;
     for (int n = b; n > a; --n) {
-        const int j = n - a - 1;  // sensitivity slot of step n
-        void* kb = shape ? c->tptr(c->d_kbar, (long long)j * kstride) : nullptr;
-        double* ms = motion ? c->d_mslot + (long long)j * mstride : nullptr;
-        c->eng->adj(c->g, c->grid, c->lam[0], c->lam[1], st[n - 1 - a], st[n - a], c->d_kref, c->d_pose + n, kb, ms,
+        const int j = n - a - 1;  // box-buffer slot of step n
+        void* bb = c->tptr(c->d_boxbuf, ((long long)buf * c->Lmax + j) * c->box_step);
+        c->eng->adj(c->g, c->lam[0], c->lam[1], st[n - 1 - a], st[n - a], c->d_kref, c->d_pose + n, bb,
                     n - 1 >= 1 ? 1 : 0, s);
         std::swap(c->lam[0], c->lam[1]);
         c->launches++;
         c->stats.adjoint_steps++;
     }
     span_end(c, 2, ea, s);
+}
+
+// Local sensitivities of a segment's steps from box buffer `buf`, folded into the design gradient (strict step
+// order) and the per-step motion gradients.
+void sens_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
+    const int L = b - a;
+    const int mode = c->prm.mode;
+    const bool shape = mode != LKS_MODE_MOTION, motion = mode != LKS_MODE_SHAPE;
+    const void* bb = c->tptr(c->d_boxbuf, (long long)buf * c->Lmax * c->box_step);
+    c->eng->sens(c->g, c->d_pose, c->d_kref, bb, c->box_step, a + 1, L, shape ? c->d_kbar : nullptr,
+                 motion ? c->d_mslot : nullptr, s);
+    c->launches++;
     if (shape) {
-        c->eng->gather(c->g, c->d_pose, c->d_kbar, a + 1, L, kstride, c->d_dkref, s);
+        c->eng->gather(c->g, c->d_pose, c->d_kbar, a + 1, L, c->g.Fbn, c->d_dkref, s);
         c->launches++;
     }
     if (motion) {
         if (c->D == 2)
-            motion_reduce_kernel<2><<<L, 32, 0, s>>>(c->g, c->block.x, c->block.y, c->block.z, c->grid.x, c->grid.y,
-                                                     c->grid.z, c->d_pose, c->d_mslot, mstride, a + 1, L, c->d_gs, c->d_guG);
+            motion_reduce_kernel<2><<<L, 32, 0, s>>>(c->d_mslot, c->nsb, a + 1, L, c->d_gs, c->d_guG);
         else
-            motion_reduce_kernel<3><<<L, 32, 0, s>>>(c->g, c->block.x, c->block.y, c->block.z, c->grid.x, c->grid.y,
-                                                     c->grid.z, c->d_pose, c->d_mslot, mstride, a + 1, L, c->d_gs, c->d_guG);
+            motion_reduce_kernel<3><<<L, 32, 0, s>>>(c->d_mslot, c->nsb, a + 1, L, c->d_gs, c->d_guG);
         LKS_LAUNCHED();
         c->launches++;
     }
@@ -779,27 +985,35 @@ void adjoint_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
 void do_segment(lks_ctx* c, int a, int b, const void* start, const void* end, cudaStream_t s) {
     recompute_segment(c, a, b, start, end, 0, s);
     adjoint_segment(c, a, b, 0, s);
+    sens_segment(c, a, b, 0, s);
 }
 
-// sqrt(N) reverse sweep with the recompute of segment m-1 overlapping the adjoint of segment m: the two
-// chains run on two streams (two history buffers); the adjoint chain waits for its segment's recompute, the
-// recompute chain waits until the adjoint two segments later has released the history buffer.
-void reverse_sqrt_pipelined(lks_ctx* c, cudaStream_t A, cudaStream_t B) {
+// sqrt(N) reverse sweep as three concurrent chains: the recompute of segment m-1 (stream B) and the
+// sensitivities of segment m+1 (stream C) overlap the adjoint steps of segment m (stream A).  History and box
+// buffers are double-buffered; the events keep each buffer's producer and consumer in order.
+void reverse_sqrt_pipelined(lks_ctx* c, cudaStream_t A, cudaStream_t B, cudaStream_t Cs) {
     LKS_CUDA(cudaEventRecord(c->ev_sync[0], A));
     LKS_CUDA(cudaStreamWaitEvent(B, c->ev_sync[0], 0));
+    LKS_CUDA(cudaStreamWaitEvent(Cs, c->ev_sync[0], 0));
     int idx = 0;
     for (int m = c->M - 1; m >= 0; --m, ++idx) {
         const int buf = idx & 1;
         const int a = c->step_of(m), b = c->step_of(m + 1);
-        if (idx >= 2) LKS_CUDA(cudaStreamWaitEvent(B, c->ev_adj[buf], 0));
+        if (idx >= 2) LKS_CUDA(cudaStreamWaitEvent(B, c->ev_adj[buf], 0));  // history buffer released
         recompute_segment(c, a, b, c->slot[c->slot_of[m]], m + 1 == c->M ? c->fin : c->slot[c->slot_of[m + 1]], buf, B);
         LKS_CUDA(cudaEventRecord(c->ev_rec[buf], B));
         LKS_CUDA(cudaStreamWaitEvent(A, c->ev_rec[buf], 0));
+        if (idx >= 2) LKS_CUDA(cudaStreamWaitEvent(A, c->ev_sens[buf], 0));  // box buffer released
         adjoint_segment(c, a, b, buf, A);
         LKS_CUDA(cudaEventRecord(c->ev_adj[buf], A));
+        LKS_CUDA(cudaStreamWaitEvent(Cs, c->ev_adj[buf], 0));
+        sens_segment(c, a, b, buf, Cs);
+        LKS_CUDA(cudaEventRecord(c->ev_sens[buf], Cs));
     }
     LKS_CUDA(cudaEventRecord(c->ev_sync[1], B));
+    LKS_CUDA(cudaEventRecord(c->ev_sync[2], Cs));
     LKS_CUDA(cudaStreamWaitEvent(A, c->ev_sync[1], 0));
+    LKS_CUDA(cudaStreamWaitEvent(A, c->ev_sync[2], 0));
 }
 
 int take_slot(lks_ctx* c) {
@@ -873,7 +1087,8 @@ void adjoint_body(lks_ctx* c, cudaStream_t s) {
             do_segment(c, a, b, a == 0 ? c->slot[0] : c->slot[c->slot_of[a]], b == Nt ? c->fin : c->slot[c->slot_of[b]], s);
         }
     } else {
-        reverse_sqrt_pipelined(c, s, s == c->cap ? c->cap2 : c->side);
+        const bool cap = s == c->cap;
+        reverse_sqrt_pipelined(c, s, cap ? c->cap2 : c->side, cap ? c->cap3 : c->side2);
     }
     // b6: chain rules
     design_chain_kernel<<<nblk(c->nd, 128), 128, 0, s>>>(c->dg, c->d_dkref, c->d_gt, c->d_gb, c->d_tmp);
@@ -1023,11 +1238,12 @@ int lks_create(const lks_params* p, lks_ctx** out) {
         setup_geometry(c);
         int ndev = 0;
         LKS_CUDA(cudaGetDeviceCount(&ndev));
-        c->eng.reset(make_engine(p->precision, c->D, c->hw));
-        c->block = c->eng->block();
-        c->grid = dim3(nblk(p->n[0], c->block.x), nblk(p->n[1], c->block.y), nblk(p->n[2], c->block.z));
-        c->nblocks = (int)(c->grid.x * c->grid.y * c->grid.z);
+        c->eng.reset(make_engine(p->precision, c->D, c->hw, c->g));
+        choose_rows_initial(c);
         allocate(c);
+        if (c->D == 2 && p->tile_rows == 0) autotune_rows(c);
+        c->stats.tile_rows_fwd = c->eng->rows_f;
+        c->stats.tile_rows_adj = c->eng->rows_a;
         *out = c;
         g_create_err.clear();
         return LKS_OK;

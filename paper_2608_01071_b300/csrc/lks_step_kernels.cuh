@@ -47,8 +47,7 @@ struct AdjArgs {
     const T* u_cur;     // u_n
     const T* kref;
     const Pose* pose;   // pose of step n
-    T* kbar;            // kappa-bar of step n on the footprint box (nullptr: no shape gradient)
-    double* mslot;      // 2D motion partials of every block for step n (nullptr: no motion gradient)
+    T* boxbuf;          // footprint-box record of step n: lam_u (D planes, 0 on walls) then u_n (D planes)
     int src;            // 1: add the objective source phi (n - 1 >= 1)
     T phi_dir[3];       // objective source weight n_a / (Nt |O|) in T
 };
@@ -382,7 +381,6 @@ __global__ void __launch_bounds__(TX * TY * TZ) adj_step_kernel(Geom g, AdjArgs<
     constexpr int NS = NSym<D>::value;
     constexpr int S = TL::S, M = TL::M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[2 * D * ((TX * TY * TZ + 31) / 32)];
     T* sp = reinterpret_cast<T*>(smem_raw);  // p-bar* on the halo-2 region
     T* su = sp + S;                          // u-bar* on the halo-2 region
     T* m0 = su + D * S;                      // M0 on the halo-1 region
@@ -492,7 +490,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) adj_step_kernel(Geom g, AdjArgs<
         }
     }
 
-    // local sensitivities on the footprint box
+    // record lam_u and u_n on the footprint box for the segment's sensitivity pass (adj_sens_kernel)
     int b[D];
     bool inbox = active;
 #pragma unroll
@@ -500,51 +498,74 @@ __global__ void __launch_bounds__(TX * TY * TZ) adj_step_kernel(Geom g, AdjArgs<
         b[c] = box_coord(xg[c], P.xs[c], g.Fb[c], g.n[c], g.periodic[c]);
         inbox = inbox && b[c] >= 0;
     }
+    if (inbox) {
+        const long long bl = b[0] + (long long)g.Fb[0] * (b[1] + (D == 3 ? (long long)g.Fb[1] * b[D - 1] : 0));
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            a.boxbuf[c * g.Fbn + bl] = wall ? (T)0 : a.lam_in[(1 + c) * N + gi];
+            a.boxbuf[(D + c) * g.Fbn + bl] = a.u_cur[c * N + gi];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Local shape and motion sensitivities of a whole segment (Eqs. dJdgamma, dJdchi in discrete form), off the
+// adjoint's critical path: one thread per (footprint-box node, step).
+//   kappa-bar = lam_u . (u^S - u_n) / (1 + kappa),   u^S-bar = lam_u kappa / (1 + kappa)
+//   dJ/ds_a  += kappa-bar dkappa/ds_a + (u^S-bar . u^G) dC/ds_a,   dJ/du^G_a += u^S-bar_a C
+// kappa-bar goes to kbar[s][box node] (for design_gather_kernel); the motion terms are summed per block
+// (FP32 within a warp, FP64 across warps) into mslot[s][block][2D].
+// ------------------------------------------------------------------------------------------------
+template <typename T, int D, int HW>
+__global__ void __launch_bounds__(256) adj_sens_kernel(Geom g, const Pose* __restrict__ poses, const T* __restrict__ kref,
+                                                       const T* __restrict__ boxbuf, long long bstride, int n_first,
+                                                       T* __restrict__ kbar, double* __restrict__ mslot) {
+    __shared__ double red[2 * D * 8];
+    const int s = blockIdx.y;
+    const Pose& P = poses[n_first + s];
+    const long long bl = blockIdx.x * 256LL + threadIdx.x;
     T mv[2 * D];
 #pragma unroll
     for (int c = 0; c < 2 * D; ++c) mv[c] = 0;
-    if (inbox) {
-        T kb = 0;
-        if (!wall) {
+    if (bl < g.Fbn) {
+        int b[3] = {(int)(bl % g.Fb[0]), (int)((bl / g.Fb[0]) % g.Fb[1]), (int)(bl / ((long long)g.Fb[0] * g.Fb[1]))};
+        bool ingrid = true;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            if (!g.periodic[c]) {
+                const int x = P.xs[c] + b[c];
+                ingrid = ingrid && x >= 0 && x < g.n[c];
+            }
+        }
+        if (ingrid) {
+            const T* bb = boxbuf + (long long)s * bstride;
             T kap, C, dk[D], dC[D];
-            map_node<T, D, HW, true>(g, P, a.kref, b, kap, C, dk, dC);
+            map_node<T, D, HW, true>(g, P, kref, b, kap, C, dk, dC);
             const T inv = (T)1 / ((T)1 + kap);
-            T usb[D];
-            T cbar = 0;
+            T kb = 0, cbar = 0, usb[D];
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                const T lu = a.lam_in[(1 + c) * N + gi];
-                const T uS = pose_uG<T>(P, c) * C;
-                kb += lu * (uS - a.u_cur[c * N + gi]);
+                const T lu = bb[c * g.Fbn + bl];
+                const T uG = pose_uG<T>(P, c);
+                kb += lu * (uG * C - bb[(D + c) * g.Fbn + bl]);
                 usb[c] = lu * kap * inv;
-                cbar += usb[c] * pose_uG<T>(P, c);
+                cbar += usb[c] * uG;
             }
             kb *= inv;
+            if (kbar != nullptr) kbar[(long long)s * g.Fbn + bl] = kb;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 mv[c] = kb * dk[c] + cbar * dC[c];
                 mv[D + c] = usb[c] * C;
             }
         }
-        if (a.kbar != nullptr) {
-            long long bl = b[0] + (long long)g.Fb[0] * (b[1] + (D == 3 ? (long long)g.Fb[1] * b[D - 1] : 0));
-            a.kbar[bl] = kb;
-        }
     }
-    if (a.mslot != nullptr) {
-        bool hit = true;
-        const int t0[3] = {x0, y0, z0};
-        const int tt[3] = {TX, TY, TZ};
+    if (mslot != nullptr) {
+        double out[2 * D];
+        block_sum<256, 2 * D, T>(mv, out, red);
+        if (threadIdx.x == 0) {
 #pragma unroll
-        for (int c = 0; c < D; ++c) hit = hit && tile_hits_box(t0[c], tt[c], g.n[c], P.xs[c], g.Fb[c], g.periodic[c]);
-        if (hit) {
-            const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-            double s[2 * D];
-            block_sum<TL::NT, 2 * D, T>(mv, s, red);
-            if (tid == 0) {
-#pragma unroll
-                for (int c = 0; c < 2 * D; ++c) a.mslot[(long long)blk * 2 * D + c] = s[c];
-            }
+            for (int c = 0; c < 2 * D; ++c) mslot[((long long)s * gridDim.x + blockIdx.x) * 2 * D + c] = out[c];
         }
     }
 }
@@ -617,28 +638,20 @@ __global__ void design_gather_kernel(Geom g, const Pose* __restrict__ poses, con
     dkref[jl] = acc;
 }
 
-// Per-step motion sensitivities: sum of the per-block partials of the blocks that touch the footprint box,
-// in block order (one warp per step; deterministic).
+// Per-step motion sensitivities: the per-block partials of adj_sens_kernel summed in block order (one warp
+// per step; deterministic).
 template <int D>
-__global__ void motion_reduce_kernel(Geom g, int TX, int TY, int TZ, int gx, int gy, int gz,
-                                     const Pose* __restrict__ poses, const double* __restrict__ mslot, long long mstride,
-                                     int n_first, int nsteps, double* __restrict__ gs, double* __restrict__ guG) {
+__global__ void motion_reduce_kernel(const double* __restrict__ mslot, int nsb, int n_first, int nsteps,
+                                     double* __restrict__ gs, double* __restrict__ guG) {
     const int s = blockIdx.x;
     if (s >= nsteps) return;
     const int n = n_first + s;
-    const Pose& P = poses[n];
-    const double* ms = mslot + (long long)s * mstride;
+    const double* ms = mslot + (long long)s * nsb * 2 * D;
     const int lane = threadIdx.x;
     double acc[2 * D];
 #pragma unroll
     for (int c = 0; c < 2 * D; ++c) acc[c] = 0.0;
-    const int nb = gx * gy * gz;
-    for (int blk = lane; blk < nb; blk += 32) {
-        const int bx = blk % gx, by = (blk / gx) % gy, bz = blk / (gx * gy);
-        bool hit = tile_hits_box(bx * TX, TX, g.n[0], P.xs[0], g.Fb[0], g.periodic[0]) &&
-                   tile_hits_box(by * TY, TY, g.n[1], P.xs[1], g.Fb[1], g.periodic[1]);
-        if (D == 3) hit = hit && tile_hits_box(bz * TZ, TZ, g.n[2], P.xs[2], g.Fb[2], g.periodic[2]);
-        if (!hit) continue;
+    for (int blk = lane; blk < nsb; blk += 32) {
 #pragma unroll
         for (int c = 0; c < 2 * D; ++c) acc[c] += ms[(long long)blk * 2 * D + c];
     }

@@ -145,3 +145,13 @@ def test_graph_replay_matches_eager(ckpt):
         assert r[0] == res[0][0]
         assert np.array_equal(r[1], res[0][1]) and np.array_equal(r[2], res[0][2])
     assert st["ms_adjoint_steps"] > 0 and st["ms_forward_steps"] > 0 and st["ms_total"] > 0
+
+
+@pytest.mark.parametrize("rows,prec", [(1, "fp64"), (4, "fp64"), (8, "fp64"), (1, "fp32"), (4, "fp32"), (8, "fp32"),
+                                       (16, "fp32")])
+def test_d2q9_kernel_variants(rows, prec):
+    # every D2Q9 step-kernel family and rows-per-warp choice the tile autotuner may pick
+    tol = (1e-10, 1e-10, 1e-10) if prec == "fp64" else (1e-5, 1e-4, 1e-3)
+    w = tiny_workload("D2Q9", precision=prec, tile_rows=rows, shape=(93, 45), ckpt="sqrt")
+    g, _ = check(w, *tol)
+    assert g["stats"]["tile_rows_fwd"] == rows and g["stats"]["tile_rows_adj"] == rows
