@@ -267,10 +267,64 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """The batched parameter study: 32 uneven D2Q9 instances, forward + adjoint of all of them per step."""
+    import torch
+
+    from paper_2608_01071_b300 import Batch
+    from paper_2608_01071_b300.workloads import batched_study
+
+    ws = batched_study()
+    b = Batch(ws)
+    dev = torch.device("cuda", 0)
+    gam = [torch.tensor(np.ascontiguousarray(draw_gamma(w).T), device=dev) for w in ws]
+    kn = [torch.tensor(draw_knots(w), device=dev) for w in ws]
+    J = torch.empty(len(ws), dtype=torch.float64, device=dev)
+    dg = [torch.empty_like(g) for g in gam]
+    dk = [torch.empty_like(k) for k in kn]
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        b.forward_dev(gam, kn, J, stream=stream)
+        b.adjoint_dev(dg, dk, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    nodes = sum(int(np.prod(w["shape"])) for w in ws)
+    t = sum(ms) / 1e3
+    value = nodes * ws[0]["Nt"] * args.steps / t / 1e9
+    launches = sum(b.context_stats(i)["kernel_launches"] for i in range(len(ws)))
+    tiles = sorted({(tuple(w["shape"]), b.context_stats(i)["tile_rows_fwd"], b.context_stats(i)["tile_rows_adj"])
+                    for i, w in enumerate(ws)})
+    line = {"metric": "fwd+adjoint LKS GLUPS", "value": value, "unit": "G node-steps/s (fwd+adj)", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched_study_32xD2Q9", "instances": len(ws), "Nt": ws[0]["Nt"],
+                       "nodes_total": nodes, "modes": "11 shape / 11 motion / 10 joint",
+                       "tiles": [list(x[0]) + [x[1], x[2]] for x in tiles]},
+            "gpu_launches": launches * args.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched_study":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -178,6 +178,23 @@ int lks_motion_filter_T_dev(lks_ctx* ctx, const double* d_in, double* d_out, voi
 int lks_interp_positions_dev(lks_ctx* ctx, const double* d_filtered, double* d_s, double* d_uG, void* stream);
 int lks_interp_positions_T_dev(lks_ctx* ctx, const double* d_gs, const double* d_guG, double* d_out, void* stream);
 
+/*
+ * Batched parameter study: `count` independent problems (any mix of grid sizes, viscosities, gradient modes and
+ * designs, one common Nt) advanced together.  Every instance owns a context (its own autotuned tiles); the
+ * forward sweeps of all instances are captured into one CUDA graph, and so are their reverse sweeps, in which
+ * each instance's kernel chains are independent branches that the GPU runs concurrently.  Pointer arguments are
+ * arrays of `count` pointers (device pointers for _dev); d_J / J hold `count` values.  Errors name the
+ * failing instance in lks_batch_last_error.
+ */
+typedef struct lks_batch lks_batch;
+int lks_batch_create(int count, const lks_params* params, lks_batch** out);
+void lks_batch_destroy(lks_batch* b);
+lks_ctx* lks_batch_context(lks_batch* b, int index);
+const char* lks_batch_last_error(const lks_batch* b);
+int lks_batch_forward_dev(lks_batch* b, const double* const* d_gamma, const double* const* d_pos_knots, double* d_J,
+                          void* stream);
+int lks_batch_adjoint_dev(lks_batch* b, double* const* d_dJ_dgamma, double* const* d_dJ_dpos, void* stream);
+
 /* Final state (p_Nt, u_Nt) of the last forward, as FP64: p[N], u[d*N] (component-major). Synchronous. */
 int lks_get_state(lks_ctx* ctx, double* p, double* u);
 

@@ -4,6 +4,6 @@ The compute path is the CUDA library ``liblks.so`` (C ABI in ``include/lks.h``);
 marshals arguments.  ``Solver`` wraps one library context; ``LKSFunction`` exposes forward/adjoint to
 torch.autograd.
 """
-from .binding import LKSError, Solver, params_from_workload  # noqa: F401
+from .binding import Batch, LKSError, Solver, params_from_workload  # noqa: F401
 
-__all__ = ["Solver", "LKSError", "params_from_workload"]
+__all__ = ["Solver", "Batch", "LKSError", "params_from_workload"]

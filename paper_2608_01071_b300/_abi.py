@@ -96,6 +96,12 @@ PROTOTYPES = {
     "lks_get_stats": (C.c_int, [_P, C.POINTER(lks_stats)]),
     "lks_set_timing": (C.c_int, [_P, C.c_int]),
     "lks_set_graphs": (C.c_int, [_P, C.c_int]),
+    "lks_batch_create": (C.c_int, [C.c_int, C.POINTER(lks_params), C.POINTER(_P)]),
+    "lks_batch_destroy": (None, [_P]),
+    "lks_batch_context": (_P, [_P, C.c_int]),
+    "lks_batch_last_error": (C.c_char_p, [_P]),
+    "lks_batch_forward_dev": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), _P, _P]),
+    "lks_batch_adjoint_dev": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), _P]),
     "lks_density_filter_noalloc": (C.c_int, [C.POINTER(C.c_int32), C.c_double, _P, _P, _P]),
     "lks_noalloc_last_error": (C.c_char_p, []),
 }

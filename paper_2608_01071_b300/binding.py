@@ -189,3 +189,51 @@ def projection_dev(d_in, d_out, d_dout, beta, eta, stream=None):
                                 C.c_void_p(d_dout.data_ptr()) if d_dout is not None else None, _stream_ptr(stream))
     if rc != 0:
         raise LKSError(rc, lib.lks_strerror(rc).decode())
+
+
+class Batch:
+    """A batched parameter study (one library batch; every instance has its own context)."""
+
+    def __init__(self, workloads):
+        self.lib = _abi.load()
+        self.params = (_abi.lks_params * len(workloads))(*[params_from_workload(w) for w in workloads])
+        self.count = len(workloads)
+        h = C.c_void_p()
+        rc = self.lib.lks_batch_create(self.count, self.params, C.byref(h))
+        if rc != 0:
+            raise LKSError(rc, self.lib.lks_batch_last_error(None).decode())
+        self.h = h
+        self.d = [2 if p.lattice == _abi.LKS_D2Q9 else 3 for p in self.params]
+        self.K = [p.K for p in self.params]
+        self.design = [tuple(p.nd[a] for a in range(dd)) for p, dd in zip(self.params, self.d)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lks_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise LKSError(rc, self.lib.lks_batch_last_error(self.h).decode())
+
+    def context_stats(self, i) -> dict:
+        s = _abi.lks_stats()
+        rc = self.lib.lks_get_stats(self.lib.lks_batch_context(self.h, i), C.byref(s))
+        self._check(rc)
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def forward_dev(self, d_gammas, d_knots, d_J, stream=None):
+        ga = (C.c_void_p * self.count)(*[t.data_ptr() for t in d_gammas])
+        ka = (C.c_void_p * self.count)(*[t.data_ptr() for t in d_knots])
+        self._check(self.lib.lks_batch_forward_dev(self.h, ga, ka, C.c_void_p(d_J.data_ptr()), _stream_ptr(stream)))
+
+    def adjoint_dev(self, d_dgammas, d_dknots, stream=None):
+        ga = (C.c_void_p * self.count)(*[t.data_ptr() for t in d_dgammas])
+        ka = (C.c_void_p * self.count)(*[t.data_ptr() for t in d_dknots])
+        self._check(self.lib.lks_batch_adjoint_dev(self.h, ga, ka, _stream_ptr(stream)))

@@ -1531,3 +1531,163 @@ extern "C" int lks_density_filter_noalloc(const int32_t nd[3], double R, const d
 }
 
 extern "C" const char* lks_noalloc_last_error(void) { return g_noalloc_err.c_str(); }
+
+// ------------------------------------------------------------------------------------------------
+// Batched parameter study: one graph for the forward sweeps of all instances, one for their reverse sweeps.
+// ------------------------------------------------------------------------------------------------
+struct lks_batch {
+    std::vector<lks_ctx*> ctx;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraphExec_t gx_fwd = nullptr, gx_adj = nullptr;
+    std::string err;
+};
+
+namespace {
+
+template <typename F>
+void batch_graph(lks_batch* b, cudaGraphExec_t& gx, cudaStream_t s, F&& body) {
+    if (!gx) {
+        LKS_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        try {
+            LKS_CUDA(cudaEventRecord(b->ev, b->cap));
+            for (lks_ctx* c : b->ctx) LKS_CUDA(cudaStreamWaitEvent(c->cap, b->ev, 0));
+            for (lks_ctx* c : b->ctx) {
+                body(c, c->cap);
+                LKS_CUDA(cudaEventRecord(b->ev, c->cap));
+                LKS_CUDA(cudaStreamWaitEvent(b->cap, b->ev, 0));
+            }
+        } catch (...) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(b->cap, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            throw;
+        }
+        cudaGraph_t g = nullptr;
+        LKS_CUDA(cudaStreamEndCapture(b->cap, &g));
+        cudaError_t e = cudaGraphInstantiate(&gx, g, 0);
+        cudaGraphDestroy(g);
+        LKS_CUDA(e);
+    }
+    LKS_CUDA(cudaGraphLaunch(gx, s));
+}
+
+void batch_free(lks_batch* b) {
+    if (b->gx_fwd) cudaGraphExecDestroy(b->gx_fwd);
+    if (b->gx_adj) cudaGraphExecDestroy(b->gx_adj);
+    if (b->ev) cudaEventDestroy(b->ev);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (lks_ctx* c : b->ctx) lks_destroy(c);
+    b->ctx.clear();
+}
+
+template <typename F>
+int batch_guard(lks_batch* b, F&& f) {
+    try {
+        f();
+        return LKS_OK;
+    } catch (const LksError& e) {
+        b->err = e.msg;
+        return e.code;
+    } catch (...) {
+        b->err = "unexpected exception";
+        return LKS_ECUDA;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int lks_batch_create(int count, const lks_params* params, lks_batch** out) {
+    if (count < 1 || !params || !out) return LKS_EINVAL;
+    lks_batch* b = new lks_batch();
+    int rc = LKS_OK;
+    for (int i = 0; i < count && rc == LKS_OK; ++i) {
+        if (params[i].Nt != params[0].Nt) {
+            g_create_err = "all instances of a batch need the same Nt";
+            rc = LKS_EINVAL;
+            break;
+        }
+        lks_ctx* c = nullptr;
+        rc = lks_create(&params[i], &c);
+        if (rc == LKS_OK) {
+            c->use_graphs = false;  // the batch owns the graphs
+            b->ctx.push_back(c);
+        } else {
+            g_create_err = "instance " + std::to_string(i) + ": " + g_create_err;
+        }
+    }
+    if (rc == LKS_OK) {
+        if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+            g_create_err = "stream/event creation failed";
+            rc = LKS_ECUDA;
+        }
+    }
+    if (rc != LKS_OK) {
+        batch_free(b);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return LKS_OK;
+}
+
+void lks_batch_destroy(lks_batch* b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    batch_free(b);
+    delete b;
+}
+
+lks_ctx* lks_batch_context(lks_batch* b, int index) {
+    if (!b || index < 0 || index >= (int)b->ctx.size()) return nullptr;
+    return b->ctx[index];
+}
+
+const char* lks_batch_last_error(const lks_batch* b) { return b ? b->err.c_str() : g_create_err.c_str(); }
+
+int lks_batch_forward_dev(lks_batch* b, const double* const* d_gamma, const double* const* d_pos, double* d_J,
+                          void* stream) {
+    if (!b || !d_gamma || !d_pos) return LKS_EINVAL;
+    return batch_guard(b, [&] {
+        cudaStream_t s = (cudaStream_t)stream;
+        for (size_t i = 0; i < b->ctx.size(); ++i) {
+            lks_ctx* c = b->ctx[i];
+            if (!d_gamma[i] || !d_pos[i]) throw LksError{LKS_EINVAL, "null input pointer of instance " + std::to_string(i)};
+            LKS_CUDA(cudaMemcpyAsync(c->d_gamma, d_gamma[i], c->nd * 8, cudaMemcpyDeviceToDevice, s));
+            LKS_CUDA(cudaMemcpyAsync(c->d_knots, d_pos[i], (size_t)c->prm.K * c->D * 8, cudaMemcpyDeviceToDevice, s));
+        }
+        batch_graph(b, b->gx_fwd, s, [&](lks_ctx* c, cudaStream_t cs) { forward_body(c, cs); });
+        for (size_t i = 0; i < b->ctx.size(); ++i) {
+            lks_ctx* c = b->ctx[i];
+            LKS_CUDA(cudaEventRecord(c->ev_flag, s));
+            c->stats.forward_steps = c->prm.Nt;
+            c->have_forward = true;
+            if (d_J) LKS_CUDA(cudaMemcpyAsync(d_J + i, c->d_J, 8, cudaMemcpyDeviceToDevice, s));
+        }
+    });
+}
+
+int lks_batch_adjoint_dev(lks_batch* b, double* const* d_dgamma, double* const* d_dpos, void* stream) {
+    if (!b) return LKS_EINVAL;
+    return batch_guard(b, [&] {
+        cudaStream_t s = (cudaStream_t)stream;
+        for (size_t i = 0; i < b->ctx.size(); ++i) {
+            lks_ctx* c = b->ctx[i];
+            if (!c->have_forward) throw LksError{LKS_ESTATE, "lks_batch_adjoint needs a preceding lks_batch_forward"};
+            LKS_CUDA(cudaEventSynchronize(c->ev_flag));
+            if (*c->h_flag) throw LksError{LKS_EUNSTABLE, "instance " + std::to_string(i) + ": forward sweep unstable"};
+        }
+        batch_graph(b, b->gx_adj, s, [&](lks_ctx* c, cudaStream_t cs) { adjoint_body(c, cs); });
+        for (size_t i = 0; i < b->ctx.size(); ++i) {
+            lks_ctx* c = b->ctx[i];
+            finish_adjoint(c, d_dgamma ? d_dgamma[i] : nullptr, d_dpos ? d_dpos[i] : nullptr, s);
+            if (c->prm.ckpt == LKS_CKPT_REVOLVE) c->have_forward = false;
+        }
+    });
+}
+
+}  // extern "C"

@@ -40,12 +40,12 @@ WORKLOADS = {
         margin=2, kappa_max=1.0, q=0.1, kernel="linear", Nt=8000, K=200, R_t=2000.0, filter_R=1.5, beta=0.0,
         eta=0.5, probe_lo=(192, 48, 48), probe_hi=(224, 80, 80), direction=(1.0, 0.0, 0.0), precision="fp32",
         ckpt="revolve", ckpt_slots=0, ckpt_bytes=40 * 2**30, motion="sinusoids", amp=13.0, seed=3),
-    # HBM-sized 2D sizing run
+    # HBM-sized 2D sizing run; the amplitude is 4 cells so that the body speed (~amp 2 pi / Nt) stays ~0.05
     "d2q9_4096x4096_fp32": dict(
         lattice="D2Q9", shape=(4096, 4096), periodic=(True, False), nu=0.02, design=(1024, 1024), margin=2,
         kappa_max=1.0, q=0.1, kernel="linear", Nt=500, K=20, R_t=125.0, filter_R=0.0, beta=0.0, eta=0.5,
-        probe_lo=(3072, 1536), probe_hi=(3328, 2560), direction=(1.0, 0.0), precision="fp32", ckpt="sqrt",
-        ckpt_slots=0, motion="sine_noise", amp=64.0, seed=5),
+        probe_lo=(2600, 1536), probe_hi=(2856, 2560), direction=(1.0, 0.0), precision="fp32", ckpt="sqrt",
+        ckpt_slots=0, motion="sine_noise", amp=4.0, seed=5),
 }
 
 

@@ -155,3 +155,18 @@ def test_d2q9_kernel_variants(rows, prec):
     w = tiny_workload("D2Q9", precision=prec, tile_rows=rows, shape=(93, 45), ckpt="sqrt")
     g, _ = check(w, *tol)
     assert g["stats"]["tile_rows_fwd"] == rows and g["stats"]["tile_rows_adj"] == rows
+
+
+def test_3d_128x64x64_full_grid_revolve_fp32():
+    # the 128x64x64 D3Q15 workload at its full grid, 12 steps, binomial checkpoints (16 slots, short segments)
+    w = workload("d3q15_128x64x64_fp32", Nt=12, K=4, R_t=3.0, amp=16.0 * 12 / 2000, seg_len=2,
+                 probe_lo=(88, 20, 20), probe_hi=(100, 44, 44))
+    g, _ = check(w, 1e-5, 1e-4, 1e-3)
+    assert g["stats"]["recompute_steps"] > 0
+
+
+def test_3d_256x128x128_full_grid_budget_fp32():
+    # the 256x128x128 D3Q15 workload at its full grid, 4 steps, checkpoints sized from a 40 GB budget
+    w = workload("d3q15_256x128x128_fp32", Nt=4, K=3, R_t=1.0, amp=13.0 * 4 / 8000, seg_len=2,
+                 probe_lo=(176, 40, 40), probe_hi=(190, 88, 88))
+    check(w, 1e-5, 1e-4, 1e-3)
