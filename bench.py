@@ -37,6 +37,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nt", type=int, default=0, help="override the horizon (short runs for profiler captures)")
+    ap.add_argument("--tile-rows", type=int, default=0, help="force a D2Q9 kernel variant instead of autotuning")
     return ap.parse_args()
 
 
@@ -92,6 +94,22 @@ class Clocks:
         os.unlink(self.f.name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(value, dist, device):
+    """Largest value over all ranks (the job's time is the slowest rank's); identity without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, nodes, Nt, steps, seconds):
+    """Whole-job G node-steps/s of `world` replicas that each ran `steps` forward+adjoint passes."""
+    return world * nodes * Nt * steps / seconds / 1e9
 
 
 def node_count(w):
@@ -154,6 +172,11 @@ def run_ours(args):
         dist.init_process_group(backend="nccl")
 
     w = workload(args.workload)
+    if args.nt > 0:  # shorter horizon, same body speed
+        w = dict(w, Nt=args.nt, K=min(w["K"], max(2, args.nt // 4)), R_t=max(1.0, w["R_t"] * args.nt / w["Nt"]),
+                 amp=w["amp"] * args.nt / w["Nt"])
+    if args.tile_rows:
+        w = dict(w, tile_rows=args.tile_rows)
     D = len(w["shape"])
     N = node_count(w)
     solver = Solver.from_workload(w)
@@ -202,11 +225,8 @@ def run_ours(args):
     clk = clocks.stop()
     ms = [a.elapsed_time(b) for a, b in ev]
     t_dev = sum(ms) / 1e3
-    if dist:
-        t = torch.tensor([t_dev], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev = float(t.item())
-    value = world * N * w["Nt"] * args.steps / t_dev / 1e9
+    t_dev = max_over_ranks(t_dev, dist, dev)
+    value = job_throughput(world, N, w["Nt"], args.steps, t_dev)
 
     # roofline of the dominant kernel (the adjoint step) from its live CUDA-event durations
     s = 4 if w["precision"] == "fp32" else 8
