@@ -112,6 +112,29 @@ def job_throughput(world, nodes, Nt, steps, seconds):
     return world * nodes * Nt * steps / seconds / 1e9
 
 
+KERNEL_SOURCES = ["lks_common.cuh", "lks_step_kernels.cuh", "lks_step2d.cuh"]
+
+
+def captured_traffic(workload_name, kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of this workload, or None when the
+    kernel sources changed since that capture (or there is none)."""
+    import hashlib
+    import re
+
+    path = os.path.join(ROOT, "profiles", f"step_kernels_{workload_name}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"sha256 prefix `([0-9a-f]+)`", text)
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2608_01071_b300", "csrc", f), "rb").read())
+    if not m or h.hexdigest()[: len(m.group(1))] != m.group(1):
+        return None
+    m = re.search(rf"traffic_bytes_per_launch {kernel} (\d+)", text)
+    return int(m.group(1)) if m else None
+
+
 def node_count(w):
     return int(np.prod(w["shape"]))
 
@@ -266,11 +289,14 @@ def run_ours(args):
                        "Nt": w["Nt"], "K": w["K"], "precision": w["precision"] + " state / f64 accumulators",
                        "checkpointing": w["ckpt"], "parallelism": f"replicas{world}",
                        "l2": "512 MB buffer written between timed steps; the 1.5 MB state is L2-resident within a step"},
-            "roofline": {"bound": "hbm", "kernel": "adj_step_kernel", "achieved": adj_gbs, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": adj_gbs / peak, "traffic": None,
-                         "bytes_per_launch": adj_bytes, "us_per_launch": adj_ms * 1e3,
-                         "fwd_step_kernel": {"achieved": fwd_gbs, "frac": fwd_gbs / peak, "us_per_launch": fwd_ms * 1e3,
-                                             "bytes_per_launch": fwd_bytes},
+            "roofline": {"bound": "hbm", "kernel": "fwd_step_kernel", "achieved": fwd_gbs, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": fwd_gbs / peak,
+                         "traffic": captured_traffic(w["name"], "fwd_step_kernel") if st0["tile_rows_fwd"] == 1 else None,
+                         "bytes_per_launch": fwd_bytes, "us_per_launch": fwd_ms * 1e3,
+                         "adj_step_kernel": {"achieved": adj_gbs, "frac": adj_gbs / peak, "us_per_launch": adj_ms * 1e3,
+                                             "bytes_per_launch": adj_bytes,
+                                             "traffic": captured_traffic(w["name"], "adj_step_kernel")
+                                             if st0["tile_rows_adj"] == 1 else None},
                          "recompute_us_per_launch": rec_ms * 1e3},
             "e2e": {"value": e2e, "unit": "G node-steps/s (fwd+adj)", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches * world),

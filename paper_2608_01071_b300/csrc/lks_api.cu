@@ -17,6 +17,8 @@
 #include "lks_prep_kernels.cuh"
 #include "lks_step_kernels.cuh"
 #include "lks_step2d.cuh"
+#include "lks_step3d.cuh"
+#include "lks_step2r.cuh"
 #include <map>
 #include <tuple>
 
@@ -75,6 +77,10 @@ struct Engine {
     virtual bool set_rows(int rf, int ra, const Geom& g) { return false; }
     virtual void fwd(const Geom& g, const void* in, void* out, const void* kref, const Pose* pose, double* jslot,
                      unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) = 0;
+    // two-step forward launches (steps n and n+1 in one kernel); out2 == nullptr takes step n only
+    virtual bool fused2() const { return false; }
+    virtual void fwd2(const Geom& g, const void* in, void* out1, void* out2, const void* kref, const Pose* pose1,
+                      double* jslot1, double* jslot2, unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) {}
     virtual void adj(const Geom& g, const void* lam_in, void* lam_out, const void* prev, const void* cur,
                      const void* kref, const Pose* pose, void* boxbuf, int src, cudaStream_t s) = 0;
     virtual void sens(const Geom& g, const Pose* poses, const void* kref, const void* boxbuf, long long bstride,
@@ -158,48 +164,90 @@ struct EngineCommon : Engine {
     }
 };
 
-// Generic shared-memory tile engine (used for D3Q15).
-template <typename T, int D, int HW>
-struct EngineT : EngineCommon<T, D, HW> {
-    static constexpr int TX = 32, TY = (D == 2) ? 8 : 4, TZ = (D == 2) ? 1 : 4;
-    using TL = Tile<D, TX, TY, TZ>;
-    static constexpr size_t smem_fwd = sizeof(T) * ((D + 1) * TL::S + (1 + NSym<D>::value) * TL::M);
-    static constexpr size_t smem_adj = sizeof(T) * ((D + 1) * TL::S + (1 + D + NSym<D>::value) * TL::M);
+// D3Q15 engine: rows = 1 selects the generic shared-memory tile kernels (32 x 4 x 4 nodes per block);
+// rows = 8 or 16 the z-marching kernels with that many planes per block (32 x 8 columns).
+template <typename T, int HW>
+struct Engine3D : EngineCommon<T, 3, HW> {
+    static constexpr int TX = 32, TY = 4, TZ = 4;
+    using TL = Tile<3, TX, TY, TZ>;
+    static constexpr size_t smem_fwd = sizeof(T) * (4 * TL::S + 7 * TL::M);
+    static constexpr size_t smem_adj = sizeof(T) * (4 * TL::S + 10 * TL::M);
 
-    explicit EngineT(const Geom& g) {
-        LKS_CUDA(cudaFuncSetAttribute(fwd_step_kernel<T, D, HW, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    explicit Engine3D(const Geom& g) {
+        LKS_CUDA(cudaFuncSetAttribute(fwd_step_kernel<T, 3, HW, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem_fwd));
-        LKS_CUDA(cudaFuncSetAttribute(adj_step_kernel<T, D, HW, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        LKS_CUDA(cudaFuncSetAttribute(adj_step_kernel<T, 3, HW, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem_adj));
-        this->fthreads = this->athreads = this->ftile = this->atile = dim3(TX, TY, TZ);
-        this->fgrid = this->agrid = dim3(nblk(g.n[0], TX), nblk(g.n[1], TY), nblk(g.n[2], TZ));
+        LKS_CUDA(cudaFuncSetAttribute(fwd3d_kernel<T, HW, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3d_fwd<T>()));
+        LKS_CUDA(cudaFuncSetAttribute(fwd3d_kernel<T, HW, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3d_fwd<T>()));
+        LKS_CUDA(cudaFuncSetAttribute(adj3d_kernel<T, HW, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3d_adj<T>()));
+        LKS_CUDA(cudaFuncSetAttribute(adj3d_kernel<T, HW, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3d_adj<T>()));
+        set_rows(8, 8, g);
+    }
+    static void geom(int r, const Geom& g, dim3& th, dim3& tile, dim3& grid) {
+        if (r == 1) {
+            th = tile = dim3(TX, TY, TZ);
+            grid = dim3(nblk(g.n[0], TX), nblk(g.n[1], TY), nblk(g.n[2], TZ));
+        } else {
+            th = dim3(Reg3::TX, Reg3::TY, 1);
+            tile = dim3(Reg3::TX, Reg3::TY, r);
+            grid = dim3(nblk(g.n[0], Reg3::TX), nblk(g.n[1], Reg3::TY), nblk(g.n[2], r));
+        }
+    }
+    bool set_rows(int rf, int ra, const Geom& g) override {
+        auto ok = [](int r) { return r == 1 || r == 8 || r == 16; };
+        if (!ok(rf) || !ok(ra)) return false;
+        this->rows_f = rf;
+        this->rows_a = ra;
+        geom(rf, g, this->fthreads, this->ftile, this->fgrid);
+        geom(ra, g, this->athreads, this->atile, this->agrid);
+        return true;
     }
     void fwd(const Geom& g, const void* in, void* out, const void* kref, const Pose* pose, double* jslot,
              unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) override {
         auto a = make_fwd_args<T>(g, in, out, kref, pose, jslot, flag, jlo, jn);
-        launch_pdl(fwd_step_kernel<T, D, HW, TX, TY, TZ>, this->fgrid, this->fthreads, smem_fwd, s, this->pdl, g, a);
+        if (this->rows_f == 1)
+            launch_pdl(fwd_step_kernel<T, 3, HW, TX, TY, TZ>, this->fgrid, this->fthreads, smem_fwd, s, this->pdl, g, a);
+        else if (this->rows_f == 8)
+            launch_pdl(fwd3d_kernel<T, HW, 8>, this->fgrid, this->fthreads, smem3d_fwd<T>(), s, this->pdl, g, a);
+        else
+            launch_pdl(fwd3d_kernel<T, HW, 16>, this->fgrid, this->fthreads, smem3d_fwd<T>(), s, this->pdl, g, a);
     }
     void adj(const Geom& g, const void* lam_in, void* lam_out, const void* prev, const void* cur, const void* kref,
              const Pose* pose, void* boxbuf, int src, cudaStream_t s) override {
         auto a = make_adj_args<T>(g, lam_in, lam_out, prev, cur, kref, pose, boxbuf, src);
-        launch_pdl(adj_step_kernel<T, D, HW, TX, TY, TZ>, this->agrid, this->athreads, smem_adj, s, this->pdl, g, a);
+        if (this->rows_a == 1)
+            launch_pdl(adj_step_kernel<T, 3, HW, TX, TY, TZ>, this->agrid, this->athreads, smem_adj, s, this->pdl, g, a);
+        else if (this->rows_a == 8)
+            launch_pdl(adj3d_kernel<T, HW, 8>, this->agrid, this->athreads, smem3d_adj<T>(), s, this->pdl, g, a);
+        else
+            launch_pdl(adj3d_kernel<T, HW, 16>, this->agrid, this->athreads, smem3d_adj<T>(), s, this->pdl, g, a);
     }
 };
 
-// D2Q9 engine with two kernel families: rows = 1 selects the shared-memory tile kernels (32 x 8 nodes per block,
-// best on small grids where the launch is latency bound), rows = 4, 8, 16 the warp-column kernels with that many
-// rows per warp and WY = 4 warps per block (fewer instructions per node, for grids with many warps).
+// D2Q9 engine with two kernel families: rows = 1 or 2 select the row-tile kernels (blocks of 32 x 8 threads,
+// tiles 28 wide and 8 or 16 rows high; best on small grids, where launches are latency bound), rows = 4, 8, 16
+// the warp-column kernels with that many rows per warp and WY = 4 warps per block.
 template <typename T, int HW>
 struct Engine2D : EngineCommon<T, 2, HW> {
     static constexpr int WY = 4;
-    using TL = Tile<2, 32, 8, 1>;
-    static constexpr size_t smem_fwd = sizeof(T) * (3 * TL::S + 4 * TL::M);
-    static constexpr size_t smem_adj = sizeof(T) * (3 * TL::S + 6 * TL::M);
-    explicit Engine2D(const Geom& g) { set_rows(1, 1, g); }
+    explicit Engine2D(const Geom& g) {
+        LKS_CUDA(cudaFuncSetAttribute(fwd2r2_kernel<T, HW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r2_fwd<T>()));
+        LKS_CUDA(cudaFuncSetAttribute(fwd2r_kernel<T, HW, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_fwd<T, 1>()));
+        LKS_CUDA(cudaFuncSetAttribute(fwd2r_kernel<T, HW, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_fwd<T, 2>()));
+        LKS_CUDA(cudaFuncSetAttribute(adj2r_kernel<T, HW, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_adj<T, 1>()));
+        LKS_CUDA(cudaFuncSetAttribute(adj2r_kernel<T, HW, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_adj<T, 2>()));
+        set_rows(1, 1, g);
+    }
     static void geom(int r, const Geom& g, dim3& th, dim3& tile, dim3& grid) {
-        if (r == 1) {
-            th = tile = dim3(32, 8, 1);
-            grid = dim3(nblk(g.n[0], 32), nblk(g.n[1], 8), 1);
+        if (r == 3) {  // two-step fused row tiles
+            th = dim3(32, 8, 1);
+            tile = dim3(Fused2::TXO, Fused2::TY, 1);
+            grid = dim3(nblk(g.n[0], Fused2::TXO), nblk(g.n[1], Fused2::TY), 1);
+        } else if (r <= 2) {
+            th = dim3(32, 8, 1);
+            tile = dim3(28, 8 * r, 1);
+            grid = dim3(nblk(g.n[0], 28), nblk(g.n[1], 8 * r), 1);
         } else {
             th = dim3(32 * WY, 1, 1);
             tile = dim3(kLanesOut, r * WY, 1);
@@ -207,9 +255,9 @@ struct Engine2D : EngineCommon<T, 2, HW> {
         }
     }
     bool set_rows(int rf, int ra, const Geom& g) override {
-        // rows kept in registers grow with R: FP32 allows up to 16, FP64 up to 8 without spills
-        auto ok = [](int r) { return r == 1 || r == 4 || r == 8 || (r == 16 && sizeof(T) == 4); };
-        if (!ok(rf) || !ok(ra)) return false;
+        // rows kept in registers grow with R: FP32 allows up to 16, FP64 up to 8 without spills; 3 = fused forward
+        auto ok = [](int r) { return r == 1 || r == 2 || r == 4 || r == 8 || (r == 16 && sizeof(T) == 4); };
+        if (!(ok(rf) || rf == 3) || !ok(ra)) return false;
         this->rows_f = rf;
         this->rows_a = ra;
         geom(rf, g, this->fthreads, this->ftile, this->fgrid);
@@ -220,6 +268,14 @@ struct Engine2D : EngineCommon<T, 2, HW> {
     void fwd_r(const Geom& g, FwdArgs<T> a, cudaStream_t s) {
         launch_pdl(fwd2d_kernel<T, HW, R, WY>, this->fgrid, this->fthreads, 0, s, this->pdl, g, a);
     }
+    bool fused2() const override { return this->rows_f == 3; }
+    void fwd2(const Geom& g, const void* in, void* out1, void* out2, const void* kref, const Pose* pose1,
+              double* jslot1, double* jslot2, unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) override {
+        auto a1 = make_fwd_args<T>(g, in, out1, kref, pose1, jslot1, flag, jlo, jn);
+        auto a2 = make_fwd_args<T>(g, out1, out2 ? out2 : out1, kref, pose1 + 1, jslot2, flag, jlo, jn);
+        launch_pdl(fwd2r2_kernel<T, HW>, this->fgrid, this->fthreads, smem2r2_fwd<T>(), s, this->pdl, g, a1, a2,
+                   out2 ? 1 : 0);
+    }
     template <int R>
     void adj_r(const Geom& g, AdjArgs<T> a, cudaStream_t s) {
         launch_pdl(adj2d_kernel<T, HW, R, WY>, this->agrid, this->athreads, 0, s, this->pdl, g, a);
@@ -228,9 +284,11 @@ struct Engine2D : EngineCommon<T, 2, HW> {
              unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) override {
         auto a = make_fwd_args<T>(g, in, out, kref, pose, jslot, flag, jlo, jn);
         switch (this->rows_f) {
-            case 1:
-                launch_pdl(fwd_step_kernel<T, 2, HW, 32, 8, 1>, this->fgrid, this->fthreads, smem_fwd, s, this->pdl, g, a);
+            case 3:
+                launch_pdl(fwd2r2_kernel<T, HW>, this->fgrid, this->fthreads, smem2r2_fwd<T>(), s, this->pdl, g, a, a, 0);
                 break;
+            case 1: launch_pdl(fwd2r_kernel<T, HW, 1>, this->fgrid, this->fthreads, smem2r_fwd<T, 1>(), s, this->pdl, g, a); break;
+            case 2: launch_pdl(fwd2r_kernel<T, HW, 2>, this->fgrid, this->fthreads, smem2r_fwd<T, 2>(), s, this->pdl, g, a); break;
             case 4: fwd_r<4>(g, a, s); break;
             case 8: fwd_r<8>(g, a, s); break;
             default: fwd_r<(sizeof(T) == 4 ? 16 : 8)>(g, a, s); break;
@@ -240,9 +298,8 @@ struct Engine2D : EngineCommon<T, 2, HW> {
              const Pose* pose, void* boxbuf, int src, cudaStream_t s) override {
         auto a = make_adj_args<T>(g, lam_in, lam_out, prev, cur, kref, pose, boxbuf, src);
         switch (this->rows_a) {
-            case 1:
-                launch_pdl(adj_step_kernel<T, 2, HW, 32, 8, 1>, this->agrid, this->athreads, smem_adj, s, this->pdl, g, a);
-                break;
+            case 1: launch_pdl(adj2r_kernel<T, HW, 1>, this->agrid, this->athreads, smem2r_adj<T, 1>(), s, this->pdl, g, a); break;
+            case 2: launch_pdl(adj2r_kernel<T, HW, 2>, this->agrid, this->athreads, smem2r_adj<T, 2>(), s, this->pdl, g, a); break;
             case 4: adj_r<4>(g, a, s); break;
             case 8: adj_r<8>(g, a, s); break;
             default: adj_r<(sizeof(T) == 4 ? 16 : 8)>(g, a, s); break;
@@ -253,7 +310,7 @@ struct Engine2D : EngineCommon<T, 2, HW> {
 template <typename T>
 Engine* make_engine_t(int D, int hw, const Geom& g) {
     if (D == 2) return hw == 1 ? (Engine*)new Engine2D<T, 1>(g) : (Engine*)new Engine2D<T, 2>(g);
-    return hw == 1 ? (Engine*)new EngineT<T, 3, 1>(g) : (Engine*)new EngineT<T, 3, 2>(g);
+    return hw == 1 ? (Engine*)new Engine3D<T, 1>(g) : (Engine*)new Engine3D<T, 2>(g);
 }
 
 Engine* make_engine(int precision, int D, int hw, const Geom& g) {
@@ -326,7 +383,7 @@ struct lks_ctx {
     cudaStream_t side2 = nullptr, cap3 = nullptr;  // sensitivity chain (eager / capture)
     cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_adj[2] = {nullptr, nullptr}, ev_sens[2] = {nullptr, nullptr};
     cudaEvent_t ev_sync[3] = {nullptr, nullptr, nullptr};
-    void* pp[2] = {nullptr, nullptr};
+    void* pp[3] = {nullptr, nullptr, nullptr};
     void* tmp_state = nullptr;
     void* fin = nullptr;
     void* lam[2] = {nullptr, nullptr};
@@ -420,9 +477,11 @@ void validate(const lks_params* p) {
     if (p->ckpt < LKS_CKPT_FULL || p->ckpt > LKS_CKPT_REVOLVE) bad("unknown ckpt");
     if (p->mode < LKS_MODE_JOINT || p->mode > LKS_MODE_MOTION) bad("unknown mode");
     if (p->ckpt_slots < 0 || p->seg_len < 0 || p->ckpt_bytes < 0) bad("negative checkpoint setting");
-    if (p->tile_rows != 0 && p->tile_rows != 1 && p->tile_rows != 4 && p->tile_rows != 8 &&
-        !(p->tile_rows == 16 && p->precision == LKS_FP32))
-        bad("tile_rows must be 0 (autotune), 1 (shared-memory tiles), 4, 8, or 16 (FP32 only)");
+    if (D == 2 && p->tile_rows != 0 && p->tile_rows != 1 && p->tile_rows != 2 && p->tile_rows != 3 && p->tile_rows != 4 &&
+        p->tile_rows != 8 && !(p->tile_rows == 16 && p->precision == LKS_FP32))
+        bad("D2Q9 tile_rows must be 0 (autotune), 1 or 2 (row tiles), 3 (two-step row tiles), 4, 8, or 16 (FP32 only)");
+    if (D == 3 && p->tile_rows != 0 && p->tile_rows != 1 && p->tile_rows != 8 && p->tile_rows != 16)
+        bad("D3Q15 tile_rows must be 0 (autotune), 1 (shared-memory tiles), 8 or 16 (z planes per block)");
 }
 
 void setup_geometry(lks_ctx* c) {
@@ -534,16 +593,17 @@ int njb_of(const lks_ctx* c);
 void choose_rows_initial(lks_ctx* c) {
     c->max_ablocks = 0;
     c->max_njb = 0;
-    const int cand[4] = {1, 4, 8, 16};
-    const int nc = c->D == 2 ? (c->tsize == 4 ? 4 : 3) : 1;
+    const int cand2[6] = {1, 2, 4, 8, 16, 3}, cand3[3] = {1, 8, 16};
+    const int nc = c->D == 2 ? (c->tsize == 4 ? 6 : 5) : 3;
     for (int i = 0; i < nc; ++i) {
-        if (c->D == 2) c->eng->set_rows(cand[i], cand[i], c->g);
+        const int r = c->D == 2 ? (c->tsize == 4 ? cand2[i] : (i < 4 ? cand2[i] : 3)) : cand3[i];
+        c->eng->set_rows(r, r == 3 ? 1 : r, c->g);
         const dim3 ag = c->eng->agrid;
         c->max_ablocks = std::max(c->max_ablocks, (int)(ag.x * ag.y * ag.z));
         c->max_njb = std::max(c->max_njb, njb_of(c));
     }
-    const int r = c->prm.tile_rows > 0 ? c->prm.tile_rows : 1;
-    if (c->D == 2) c->eng->set_rows(r, r, c->g);
+    const int r = c->prm.tile_rows > 0 ? c->prm.tile_rows : (c->D == 2 ? 1 : 8);
+    c->eng->set_rows(r, r == 3 ? 1 : r, c->g);
 }
 
 // Tile autotuner (D2Q9): time the forward and adjoint step kernels for every rows-per-warp choice on the
@@ -554,7 +614,7 @@ void autotune_rows(lks_ctx* c) {
     static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> cache;
     int dev = 0;
     LKS_CUDA(cudaGetDevice(&dev));
-    const auto key = std::make_tuple(dev, (int)c->tsize, c->hw, c->g.n[0], c->g.n[1]);
+    const auto key = std::make_tuple(dev, (int)c->tsize, c->hw * 16 + c->D, c->g.n[0], c->g.n[1] * 65536 + c->g.n[2]);
     {
         std::lock_guard<std::mutex> lock(mu);
         auto it = cache.find(key);
@@ -571,19 +631,26 @@ void autotune_rows(lks_ctx* c) {
     cudaEvent_t e0, e1;
     LKS_CUDA(cudaEventCreate(&e0));
     LKS_CUDA(cudaEventCreate(&e1));
-    const int cand[4] = {1, 4, 8, 16};
-    const int nc = c->tsize == 4 ? 4 : 3;
+    // D2Q9: row tiles (1, 2), two-step fused row tiles (3, forward only), warp columns (4, 8, 16);
+    // D3Q15: z-marching blocks of 8 or 16 planes
+    const int cand2[6] = {1, 2, 3, 4, 8, 16}, cand3[2] = {8, 16};
+    const int* cand = c->D == 2 ? cand2 : cand3;
+    const int nc = c->D == 2 ? (c->tsize == 4 ? 6 : 5) : 2;
     float best_f = 1e30f, best_a = 1e30f;
-    int rf = 1, ra = 1;
+    int rf = cand[0], ra = cand[0];
     const int reps = 20;
     const int jlo[3] = {0, 0, 0}, jn[3] = {1, 1, 1};
     for (int ci = 0; ci < nc; ++ci) {
         const int r = cand[ci];
-        c->eng->set_rows(r, r, c->g);
+        c->eng->set_rows(r, r == 3 ? 1 : r, c->g);
         for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 1 && r == 3) continue;  // the fused variant is a forward kernel only
             for (int k = 0; k < 3 + reps; ++k) {
                 if (k == 3) LKS_CUDA(cudaEventRecord(e0, s));
-                if (pass == 0)
+                if (pass == 0 && r == 3)
+                    c->eng->fwd2(c->g, c->slot[0], c->pp[0], c->pp[1], c->d_kref, c->d_pose, nullptr, nullptr, c->d_flag,
+                                 jlo, jn, s);
+                else if (pass == 0)
                     c->eng->fwd(c->g, c->slot[0], c->pp[k & 1], c->d_kref, c->d_pose, nullptr, c->d_flag, jlo, jn, s);
                 else
                     c->eng->adj(c->g, c->lam[k & 1], c->lam[(k + 1) & 1], c->slot[0], c->slot[0], c->d_kref, c->d_pose,
@@ -593,8 +660,9 @@ void autotune_rows(lks_ctx* c) {
             LKS_CUDA(cudaEventSynchronize(e1));
             float ms = 0.f;
             LKS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (pass == 0 && r == 3) ms *= 0.5f;  // two steps per launch
             if (std::getenv("LKS_TUNE_VERBOSE"))
-                std::fprintf(stderr, "lks autotune %dx%d %s rows=%d: %.3f us/launch\n", c->g.n[0], c->g.n[1],
+                std::fprintf(stderr, "lks autotune %dx%dx%d %s rows=%d: %.3f us/step\n", c->g.n[0], c->g.n[1], c->g.n[2],
                              pass == 0 ? "forward" : "adjoint", r, 1e3f * ms / reps);
             if (pass == 0 && ms < best_f) {
                 best_f = ms;
@@ -661,6 +729,7 @@ void allocate(lks_ctx* c) {
     }
     c->pp[0] = dalloc(c, sb);
     c->pp[1] = dalloc(c, sb);
+    c->pp[2] = dalloc(c, sb);
     c->tmp_state = dalloc(c, sb);
     c->fin = dalloc(c, sb);
     c->lam[0] = dalloc(c, sb);
@@ -835,6 +904,54 @@ void fwd_step(lks_ctx* c, int n, const void* in, void* out, bool objective, cuda
     c->launches++;
 }
 
+// Two forward steps n, n+1 (or step n alone when out2 is null) in one fused launch.
+void fwd_pair(lks_ctx* c, int n, const void* in, void* out1, void* out2, bool objective, cudaStream_t s) {
+    int lo[3], cnt[3];
+    probe_blocks(c, lo, cnt);
+    const int njb = cnt[0] * cnt[1] * cnt[2];
+    c->eng->fwd2(c->g, in, out1, out2, c->d_kref, c->d_pose + n, objective ? c->d_jslot + (long long)n * njb : nullptr,
+                 objective && out2 ? c->d_jslot + (long long)(n + 1) * njb : nullptr, c->d_flag, lo, cnt, s);
+    c->launches++;
+}
+
+// Steps n0+1 .. n1 from the state at `in`; dst(n) names the buffer of state n (distinct from the state it is
+// computed from).  Pairs of steps go to one fused launch when the forward kernel supports it.
+template <typename Dst>
+const void* run_steps(lks_ctx* c, int n0, int n1, const void* in, Dst&& dst, bool objective, cudaStream_t s) {
+    const void* cur = in;
+    int n = n0 + 1;
+    while (n <= n1) {
+        if (c->eng->fused2()) {
+            const bool two = n + 1 <= n1;
+            void* o1 = dst(n);
+            void* o2 = two ? dst(n + 1) : nullptr;
+            fwd_pair(c, n, cur, o1, o2, objective, s);
+            cur = two ? o2 : o1;
+            n += two ? 2 : 1;
+        } else {
+            void* o = dst(n);
+            fwd_step(c, n, cur, o, objective, s);
+            cur = o;
+            ++n;
+        }
+    }
+    return cur;
+}
+
+// Round-robin over the three ping-pong buffers, never handing out `avoid` (the state being read).
+struct PingPong {
+    lks_ctx* c;
+    int i = 0;
+    void* next(const void* avoid) {
+        for (int k = 0; k < 3; ++k) {
+            void* p = c->pp[i];
+            i = (i + 1) % 3;
+            if (p != avoid) return p;
+        }
+        return nullptr;
+    }
+};
+
 void forward_body(lks_ctx* c, cudaStream_t s);
 
 void run_forward(lks_ctx* c, cudaStream_t s) {
@@ -871,27 +988,22 @@ void forward_body(lks_ctx* c, cudaStream_t s) {
     }
     c->eng->init_state(c->g, c->slot[0], s);
     c->launches++;
-    const void* cur = c->slot[0];
-    int ppi = 0;
+    PingPong pp{c};
     cudaEvent_t e0 = span_begin(c, s);
-    for (int n = 1; n <= Nt; ++n) {
-        void* out;
-        if (n == Nt) {
-            out = c->fin;
-        } else if (n % c->S == 0 && store[n / c->S]) {
+    // state n goes to the final buffer, its checkpoint slot, or a ping-pong buffer
+    auto dst = [&](int n) -> void* {
+        if (n == Nt) return c->fin;
+        if (n % c->S == 0 && store[n / c->S]) {
             const int m = n / c->S;
             const int si = (int)(std::find(c->slot_used.begin(), c->slot_used.end(), 0) - c->slot_used.begin());
             if (si >= (int)c->slot.size()) throw LksError{LKS_ESTATE, "internal: out of checkpoint slots"};
             c->slot_used[si] = 1;
             c->slot_of[m] = si;
-            out = c->slot[si];
-        } else {
-            out = c->pp[ppi];
-            ppi ^= 1;
+            return c->slot[si];
         }
-        fwd_step(c, n, cur, out, true, s);
-        cur = out;
-    }
+        return pp.next(nullptr);
+    };
+    run_steps(c, 0, Nt, c->slot[0], dst, true, s);
     span_end(c, 0, e0, s);
     objective_reduce_kernel<<<1, 256, 0, s>>>(c->d_jslot, njb_of(c), Nt, c->g.phi, c->d_jstep, c->d_J);
     LKS_LAUNCHED();
@@ -904,15 +1016,10 @@ void forward_body(lks_ctx* c, cudaStream_t s) {
 // Advance from the state at step n0 (pointer in) to step n1, writing the final state to out (out != in).
 void advance(lks_ctx* c, int n0, int n1, const void* in, void* out, cudaStream_t s) {
     cudaEvent_t e0 = span_begin(c, s);
-    const void* cur = in;
-    int ppi = (in == c->pp[0]) ? 1 : 0;
-    for (int n = n0 + 1; n <= n1; ++n) {
-        void* dst = (n == n1) ? out : c->pp[ppi];
-        if (n != n1) ppi ^= 1;
-        fwd_step(c, n, cur, dst, false, s);
-        cur = dst;
-        c->stats.recompute_steps++;
-    }
+    PingPong pp{c};
+    auto dst = [&](int n) -> void* { return n == n1 ? out : pp.next(in); };
+    run_steps(c, n0, n1, in, dst, false, s);
+    c->stats.recompute_steps += n1 - n0;
     span_end(c, 1, e0, s);
 }
 
@@ -925,16 +1032,20 @@ void recompute_segment(lks_ctx* c, int a, int b, const void* start, const void* 
     st[0] = start;
     const bool full = c->prm.ckpt == LKS_CKPT_FULL;
     cudaEvent_t er = full ? nullptr : span_begin(c, s);
-    for (int j = 1; j <= L; ++j) {
-        if (j == L && end != nullptr) {
-            st[j] = end;
-        } else if (full) {
+    if (full) {
+        for (int j = 1; j <= L; ++j) {
             const int m = a + j;  // every state is a stored boundary in FULL mode
-            st[j] = (m == c->prm.Nt) ? c->fin : c->slot[c->slot_of[m]];
-        } else {
-            fwd_step(c, a + j, st[j - 1], c->hist[buf][j], false, s);
-            st[j] = c->hist[buf][j];
-            c->stats.recompute_steps++;
+            st[j] = (j == L && end != nullptr) ? end : (m == c->prm.Nt) ? c->fin : c->slot[c->slot_of[m]];
+        }
+    } else {
+        // rebuild states a+1 .. last into the history (the segment end comes from its checkpoint when stored)
+        const int last = end != nullptr ? L - 1 : L;
+        for (int j = 1; j <= last; ++j) st[j] = c->hist[buf][j];
+        if (end != nullptr) st[L] = end;
+        if (last >= 1) {
+            auto dst = [&](int n) -> void* { return c->hist[buf][n - a]; };
+            run_steps(c, a, a + last, start, dst, false, s);
+            c->stats.recompute_steps += last;
         }
     }
     span_end(c, 1, er, s);
@@ -1241,7 +1352,7 @@ int lks_create(const lks_params* p, lks_ctx** out) {
         c->eng.reset(make_engine(p->precision, c->D, c->hw, c->g));
         choose_rows_initial(c);
         allocate(c);
-        if (c->D == 2 && p->tile_rows == 0) autotune_rows(c);
+        if (p->tile_rows == 0) autotune_rows(c);
         c->stats.tile_rows_fwd = c->eng->rows_f;
         c->stats.tile_rows_adj = c->eng->rows_a;
         *out = c;

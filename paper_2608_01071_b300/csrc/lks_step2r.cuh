@@ -1,0 +1,419 @@
+// D2Q9 forward and adjoint step kernels on row tiles.
+//
+// A block of 32 x 8 threads owns an output tile 28 nodes wide and TY = 8 * RPT rows high.  Shared memory holds
+// whole 32-lane rows (the tile plus a halo of 2 on each side), so every row is one coalesced warp load and a
+// lane's x-neighbours are the adjacent words of the same row.  The forward stages the nine weighted equilibrium
+// values w_i f_i of every node of the halo-1 region; the output node then reads the nine values that stream
+// into it (one per direction).  The adjoint stages the nine values G_i = p-bar*/3 + c_i . u-bar* of every node of
+// the halo-2 region, then the six local moments M0, M1, M2 of the halo-1 region.
+#pragma once
+
+#include "lks_common.cuh"
+#include "lks_step_kernels.cuh"
+
+namespace lks {
+
+template <int RPT>
+struct Row2 {
+    static constexpr int W = 32, TXO = 28, TR = 8;      // row width, output columns, thread rows
+    static constexpr int TY = TR * RPT;                  // output rows
+    static constexpr int RR = TY + 4;                    // raw rows (halo 2)
+    static constexpr int NT = W * TR;
+};
+
+template <typename T, int RPT>
+__host__ __device__ constexpr size_t smem2r_fwd() {
+    return sizeof(T) * (3 * Row2<RPT>::RR * 32 + 9 * Row2<RPT>::RR * 32);
+}
+template <typename T, int RPT>
+__host__ __device__ constexpr size_t smem2r_adj() {
+    return sizeof(T) * (9 * Row2<RPT>::RR * 32 + 6 * Row2<RPT>::RR * 32);
+}
+
+// Forward step n-1 -> n (Sec. 2.2 / 2.3), same arithmetic as fwd_step_kernel.
+template <typename T, int HW, int RPT>
+__global__ void __launch_bounds__(256) fwd2r_kernel(Geom g, FwdArgs<T> a) {
+    using RW = Row2<RPT>;
+    using L = Lattice<2>;
+    constexpr int RR = RW::RR;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[8];
+    T* sp = reinterpret_cast<T*>(smem_raw);  // [RR][32] p'
+    T* sx = sp + RR * 32;                    // u_x
+    T* sy = sx + RR * 32;                    // u_y
+    T* wf = sy + RR * 32;                    // [9][RR][32] weighted equilibrium values
+
+    const int lane = threadIdx.x, t = threadIdx.y, tid = lane + 32 * t;
+    const int nx = g.n[0], ny = g.n[1];
+    const int x0 = blockIdx.x * RW::TXO, y0 = blockIdx.y * RW::TY;
+    const int xo = x0 + lane - 2;
+    const int xl = wrap(xo, nx);
+    const T A = (T)g.A;
+    const Pose& P = *a.pose;
+    pdl_wait_then_release();
+
+    // phase 1: raw rows y0-2 .. y0+TY+1
+#pragma unroll
+    for (int r = t; r < RR; r += RW::TR) {
+        const int gi = wrap(y0 - 2 + r, ny) * nx + xl;
+        sp[r * 32 + lane] = a.in[gi];
+        sx[r * 32 + lane] = a.in[g.N + gi];
+        sy[r * 32 + lane] = a.in[2 * g.N + gi];
+    }
+    __syncthreads();
+    // phase 2: w_i f_i on rows 1 .. RR-2, lanes 1 .. 30
+    if (lane >= 1 && lane <= 30) {
+        for (int m = 1 + t; m < RR - 1; m += RW::TR) {
+            const int c = m * 32 + lane;
+            const T p = sp[c], ux = sx[c], uy = sy[c];
+            const T sig = (T)3 * p - (T)1.5 * (ux * ux + uy * uy);
+            const T Txx = (T)4.5 * ux * ux + A * (sx[c + 1] - sx[c - 1]);
+            const T Tyy = (T)4.5 * uy * uy + A * (sy[c + 32] - sy[c - 32]);
+            const T Txy = (T)4.5 * ux * uy + (T)0.5 * A * ((sy[c + 1] - sy[c - 1]) + (sx[c + 32] - sx[c - 32]));
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const int cx = L::c(q, 0), cy = L::c(q, 1);
+                T f = sig;
+                if (cx != 0) f += (T)(3 * cx) * ux + Txx;
+                if (cy != 0) f += (T)(3 * cy) * uy + Tyy;
+                if (cx * cy != 0) f += (T)(2 * cx * cy) * Txy;
+                wf[q * RR * 32 + c] = (T)L::w(q) * f;
+            }
+        }
+    }
+    __syncthreads();
+    // phase 3: outputs on rows 2 .. TY+1, lanes 2 .. 29
+    T jacc = 0;
+    bool unstable = false;
+    const bool lane_out = lane >= 2 && lane <= 29 && xo < nx;
+    const int bxc = box_coord(xo, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int o = 2 + t + RW::TR * k;
+        const int y = y0 - 2 + o;
+        if (!lane_out || y >= ny) continue;
+        const int c = o * 32 + lane;
+        T fq[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) fq[q] = wf[q * RR * 32 + c - L::c(q, 0) - 32 * L::c(q, 1)];
+        T accp = 0, ax = 0, ay = 0;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            accp += fq[q];
+            if (L::c(q, 0) != 0) ax += (T)L::c(q, 0) * fq[q];
+            if (L::c(q, 1) != 0) ay += (T)L::c(q, 1) * fq[q];
+        }
+        T un0 = ax, un1 = ay;
+        const int byc = box_coord(y, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
+        if (bxc >= 0 && byc >= 0) {
+            const int b[2] = {bxc, byc};
+            T kap, C;
+            map_node<T, 2, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
+            const T inv = (T)1 / ((T)1 + kap);
+            un0 = (ax + kap * (pose_uG<T>(P, 0) * C)) * inv;
+            un1 = (ay + kap * (pose_uG<T>(P, 1) * C)) * inv;
+        }
+        int xg[2] = {xo, y};
+        T uw[2];
+        const bool wall = wall_node<T, 2>(g, xg, uw);
+        if (wall) {
+            un0 = uw[0];
+            un1 = uw[1];
+        }
+        const long long go = (long long)y * nx + xo;
+        a.out_p[go] = accp * (T)(1.0 / 3.0);
+        a.out_u[go] = un0;
+        a.out_u[g.N + go] = un1;
+        if (!wall) {
+            if (a.u_crit2 > (T)0 && !(un0 * un0 + un1 * un1 <= a.u_crit2)) unstable = true;
+            if (in_probe<2>(g, xg)) jacc += a.dir[0] * un0 + a.dir[1] * un1;
+        }
+    }
+    if (unstable) atomicOr(a.flag, 1u);
+    if (a.jslot != nullptr) {
+        const int px = (int)blockIdx.x - a.jb_lo[0], py = (int)blockIdx.y - a.jb_lo[1];
+        if (px >= 0 && px < a.jb_n[0] && py >= 0 && py < a.jb_n[1]) {
+            T v[1] = {jacc};
+            double s[1];
+            block_sum<256, 1, T>(v, s, red);
+            if (tid == 0) a.jslot[px + a.jb_n[0] * py] = s[0];
+        }
+    }
+}
+
+// Adjoint step lambda_n -> lambda_{n-1} (same algebra as adj_step_kernel), recording lam_u and u_n on the
+// footprint box.
+template <typename T, int HW, int RPT>
+__global__ void __launch_bounds__(256) adj2r_kernel(Geom g, AdjArgs<T> a) {
+    using RW = Row2<RPT>;
+    using L = Lattice<2>;
+    constexpr int RR = RW::RR;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* gq = reinterpret_cast<T*>(smem_raw);  // [9][RR][32] G_i = p-bar*/3 + c_i . u-bar*
+    T* mo = gq + 9 * RR * 32;                // [6][RR][32] M0, M1x, M1y, M2xx, M2yy, M2xy
+
+    const int lane = threadIdx.x, t = threadIdx.y;
+    const int nx = g.n[0], ny = g.n[1];
+    const long long N = g.N;
+    const int x0 = blockIdx.x * RW::TXO, y0 = blockIdx.y * RW::TY;
+    const int xo = x0 + lane - 2;
+    const int xl = wrap(xo, nx);
+    const T A = (T)g.A;
+    const Pose& P = *a.pose;
+    const int bxl = box_coord(xl, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
+    pdl_wait_then_release();
+
+    // phase 1: G_i of the source nodes of rows y0-2 .. y0+TY+1 (Brinkman and wall adjoint folded in)
+#pragma unroll
+    for (int r = t; r < RR; r += RW::TR) {
+        const int yw = wrap(y0 - 2 + r, ny);
+        const int gi = yw * nx + xl;
+        const T lp = a.lam_in[gi];
+        T ux = a.lam_in[N + gi], uy = a.lam_in[2 * N + gi];
+        int xs[2] = {xl, yw};
+        T uw[2];
+        if (wall_node<T, 2>(g, xs, uw)) {
+            ux = 0;
+            uy = 0;
+        } else {
+            const int byl = box_coord(yw, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
+            if (bxl >= 0 && byl >= 0) {
+                const int b[2] = {bxl, byl};
+                T kap, C;
+                map_node<T, 2, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
+                const T inv = (T)1 / ((T)1 + kap);
+                ux *= inv;
+                uy *= inv;
+            }
+        }
+        const T p3 = lp * (T)(1.0 / 3.0);
+        const int c = r * 32 + lane;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            T v = p3;
+            if (L::c(q, 0) != 0) v += (T)L::c(q, 0) * ux;
+            if (L::c(q, 1) != 0) v += (T)L::c(q, 1) * uy;
+            gq[q * RR * 32 + c] = v;
+        }
+    }
+    __syncthreads();
+    // phase 2: moments of rows 1 .. RR-2, lanes 1 .. 30: M = sum_i w_i {1, c_i, c_i c_i} G_i(y + c_i)
+    if (lane >= 1 && lane <= 30) {
+        for (int m = 1 + t; m < RR - 1; m += RW::TR) {
+            const int c = m * 32 + lane;
+            T M0 = 0, M1x = 0, M1y = 0, Mxx = 0, Myy = 0, Mxy = 0;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const int cx = L::c(q, 0), cy = L::c(q, 1);
+                const T v = (T)L::w(q) * gq[q * RR * 32 + c + cx + 32 * cy];
+                M0 += v;
+                if (cx != 0) {
+                    M1x += (T)cx * v;
+                    Mxx += v;
+                }
+                if (cy != 0) {
+                    M1y += (T)cy * v;
+                    Myy += v;
+                }
+                if (cx * cy != 0) Mxy += (T)(cx * cy) * v;
+            }
+            mo[c] = M0;
+            mo[RR * 32 + c] = M1x;
+            mo[2 * RR * 32 + c] = M1y;
+            mo[3 * RR * 32 + c] = Mxx;
+            mo[4 * RR * 32 + c] = Myy;
+            mo[5 * RR * 32 + c] = Mxy;
+        }
+    }
+    __syncthreads();
+    // phase 3: lambda_{n-1} on rows 2 .. TY+1, lanes 2 .. 29
+    const bool lane_out = lane >= 2 && lane <= 29 && xo < nx;
+    const int bxc = box_coord(xo, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
+    const T* M0s = mo;
+    const T* M1xs = mo + RR * 32;
+    const T* M1ys = mo + 2 * RR * 32;
+    const T* Mxxs = mo + 3 * RR * 32;
+    const T* Myys = mo + 4 * RR * 32;
+    const T* Mxys = mo + 5 * RR * 32;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int o = 2 + t + RW::TR * k;
+        const int y = y0 - 2 + o;
+        if (!lane_out || y >= ny) continue;
+        const int c = o * 32 + lane;
+        const long long go = (long long)y * nx + xo;
+        const T u0 = a.u_prev[go], u1 = a.u_prev[N + go];
+        const T M0 = M0s[c], Mxx = Mxxs[c], Myy = Myys[c], Mxy = Mxys[c];
+        T vx = (T)3 * M1xs[c] - (T)3 * u0 * M0 + (T)9 * (Mxx * u0 + Mxy * u1) +
+               A * ((Mxxs[c - 1] - Mxxs[c + 1]) + (Mxys[c - 32] - Mxys[c + 32]));
+        T vy = (T)3 * M1ys[c] - (T)3 * u1 * M0 + (T)9 * (Mxy * u0 + Myy * u1) +
+               A * ((Mxys[c - 1] - Mxys[c + 1]) + (Myys[c - 32] - Myys[c + 32]));
+        int xg[2] = {xo, y};
+        T uw[2];
+        const bool wall = wall_node<T, 2>(g, xg, uw);
+        if (a.src && !wall && in_probe<2>(g, xg)) {
+            vx += a.phi_dir[0];
+            vy += a.phi_dir[1];
+        }
+        a.lam_out[go] = (T)3 * M0;
+        a.lam_out[N + go] = vx;
+        a.lam_out[2 * N + go] = vy;
+        const int byc = box_coord(y, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
+        if (bxc >= 0 && byc >= 0) {
+            const long long bl = bxc + (long long)g.Fb[0] * byc;
+            a.boxbuf[bl] = wall ? (T)0 : a.lam_in[N + go];
+            a.boxbuf[g.Fbn + bl] = wall ? (T)0 : a.lam_in[2 * N + go];
+            a.boxbuf[2 * g.Fbn + bl] = a.u_cur[go];
+            a.boxbuf[3 * g.Fbn + bl] = a.u_cur[N + go];
+        }
+    }
+}
+
+}  // namespace lks
+
+namespace lks {
+
+struct Fused2 {
+    static constexpr int TY = 8, RR = TY + 8, TXO = 24;
+};
+template <typename T>
+__host__ __device__ constexpr size_t smem2r2_fwd() {
+    return sizeof(T) * 12 * Fused2::RR * 32;
+}
+
+// Two forward steps n-1 -> n -> n+1 in one launch (D2Q9).  The tile is 24 columns wide (32-lane rows with a halo
+// of 4) and 8 rows high; step n is computed on the tile plus a halo of 2, kept in shared memory as the input of
+// step n+1, and written out for the tile itself.  The arithmetic per step is that of fwd2r_kernel.
+// With two = 0 only step n is taken (the last step of an odd run), on the same tile geometry.
+template <typename T, int HW>
+__global__ void __launch_bounds__(256) fwd2r2_kernel(Geom g, FwdArgs<T> a1, FwdArgs<T> a2, int two) {
+    using L = Lattice<2>;
+    constexpr int TY = Fused2::TY, RR = Fused2::RR, TXO = Fused2::TXO;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[8];
+    T* sp = reinterpret_cast<T*>(smem_raw);  // [RR][32] p', then step-n state in place
+    T* sx = sp + RR * 32;
+    T* sy = sx + RR * 32;
+    T* wf = sy + RR * 32;                    // [9][RR][32]
+
+    const int lane = threadIdx.x, t = threadIdx.y, tid = lane + 32 * t;
+    const int nx = g.n[0], ny = g.n[1];
+    const int x0 = blockIdx.x * TXO, y0 = blockIdx.y * TY;
+    const int xo = x0 + lane - 4;           // this lane's column (may lie outside [0, nx))
+    const int xl = wrap(xo, nx);
+    const T A = (T)g.A;
+    pdl_wait_then_release();
+
+#pragma unroll
+    for (int r = t; r < RR; r += 8) {
+        const int gi = wrap(y0 - 4 + r, ny) * nx + xl;
+        sp[r * 32 + lane] = a1.in[gi];
+        sx[r * 32 + lane] = a1.in[g.N + gi];
+        sy[r * 32 + lane] = a1.in[2 * g.N + gi];
+    }
+    __syncthreads();
+
+    auto equilibria = [&](int h) {  // w_i f_i on rows [h, RR-h), lanes [h, 32-h)
+        if (lane >= h && lane < 32 - h) {
+            for (int m = h + t; m < RR - h; m += 8) {
+                const int c = m * 32 + lane;
+                const T p = sp[c], ux = sx[c], uy = sy[c];
+                const T sig = (T)3 * p - (T)1.5 * (ux * ux + uy * uy);
+                const T Txx = (T)4.5 * ux * ux + A * (sx[c + 1] - sx[c - 1]);
+                const T Tyy = (T)4.5 * uy * uy + A * (sy[c + 32] - sy[c - 32]);
+                const T Txy = (T)4.5 * ux * uy + (T)0.5 * A * ((sy[c + 1] - sy[c - 1]) + (sx[c + 32] - sx[c - 32]));
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    const int cx = L::c(q, 0), cy = L::c(q, 1);
+                    T f = sig;
+                    if (cx != 0) f += (T)(3 * cx) * ux + Txx;
+                    if (cy != 0) f += (T)(3 * cy) * uy + Tyy;
+                    if (cx * cy != 0) f += (T)(2 * cx * cy) * Txy;
+                    wf[q * RR * 32 + c] = (T)L::w(q) * f;
+                }
+            }
+        }
+    };
+    // stream + Brinkman + walls of the nodes on rows [h, RR-h), lanes [h, 32-h); results to shared memory and,
+    // for the tile itself, to global memory (with the objective partial and the stability check)
+    T jacc1 = 0, jacc2 = 0;
+    bool unstable = false;
+    auto outputs = [&](int h, const FwdArgs<T>& a, T& jacc) {
+        const Pose& P = *a.pose;
+        const int bxc = box_coord(xl, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
+        const bool lane_in = lane >= h && lane < 32 - h;
+        const bool lane_tile = lane >= 4 && lane < 28 && xo < nx;
+        for (int o = h + t; o < RR - h; o += 8) {
+            if (!lane_in) continue;
+            const int c = o * 32 + lane;
+            const int yw = wrap(y0 - 4 + o, ny);
+            T fq[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) fq[q] = wf[q * RR * 32 + c - L::c(q, 0) - 32 * L::c(q, 1)];
+            T accp = 0, ax = 0, ay = 0;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                accp += fq[q];
+                if (L::c(q, 0) != 0) ax += (T)L::c(q, 0) * fq[q];
+                if (L::c(q, 1) != 0) ay += (T)L::c(q, 1) * fq[q];
+            }
+            T un0 = ax, un1 = ay;
+            const int byc = box_coord(yw, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
+            if (bxc >= 0 && byc >= 0) {
+                const int b[2] = {bxc, byc};
+                T kap, C;
+                map_node<T, 2, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
+                const T inv = (T)1 / ((T)1 + kap);
+                un0 = (ax + kap * (pose_uG<T>(P, 0) * C)) * inv;
+                un1 = (ay + kap * (pose_uG<T>(P, 1) * C)) * inv;
+            }
+            int xg[2] = {xl, yw};
+            T uw[2];
+            const bool wall = wall_node<T, 2>(g, xg, uw);
+            if (wall) {
+                un0 = uw[0];
+                un1 = uw[1];
+            }
+            const T pn = accp * (T)(1.0 / 3.0);
+            // results of this step become the next step's input (this phase reads only wf)
+            sp[c] = pn;
+            sx[c] = un0;
+            sy[c] = un1;
+            const int y = y0 - 4 + o;
+            if (lane_tile && o >= 4 && o < RR - 4 && y < ny) {
+                const long long go = (long long)y * nx + xo;
+                a.out_p[go] = pn;
+                a.out_u[go] = un0;
+                a.out_u[g.N + go] = un1;
+                if (!wall) {
+                    if (a.u_crit2 > (T)0 && !(un0 * un0 + un1 * un1 <= a.u_crit2)) unstable = true;
+                    if (in_probe<2>(g, xg)) jacc += a.dir[0] * un0 + a.dir[1] * un1;
+                }
+            }
+        }
+    };
+    equilibria(1);
+    __syncthreads();
+    outputs(2, a1, jacc1);
+    if (two) {
+        __syncthreads();
+        equilibria(3);
+        __syncthreads();
+        outputs(4, a2, jacc2);
+    }
+    if (unstable) atomicOr(a1.flag, 1u);
+    for (int s = 0; s < 1 + two; ++s) {
+        const FwdArgs<T>& a = s == 0 ? a1 : a2;
+        if (a.jslot == nullptr) continue;
+        const int px = (int)blockIdx.x - a.jb_lo[0], py = (int)blockIdx.y - a.jb_lo[1];
+        if (px >= 0 && px < a.jb_n[0] && py >= 0 && py < a.jb_n[1]) {
+            T v[1] = {s == 0 ? jacc1 : jacc2};
+            double sum[1];
+            __syncthreads();
+            block_sum<256, 1, T>(v, sum, red);
+            if (tid == 0) a.jslot[px + a.jb_n[0] * py] = sum[0];
+        }
+    }
+}
+
+}  // namespace lks

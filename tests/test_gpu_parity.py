@@ -147,14 +147,16 @@ def test_graph_replay_matches_eager(ckpt):
     assert st["ms_adjoint_steps"] > 0 and st["ms_forward_steps"] > 0 and st["ms_total"] > 0
 
 
-@pytest.mark.parametrize("rows,prec", [(1, "fp64"), (4, "fp64"), (8, "fp64"), (1, "fp32"), (4, "fp32"), (8, "fp32"),
-                                       (16, "fp32")])
-def test_d2q9_kernel_variants(rows, prec):
-    # every D2Q9 step-kernel family and rows-per-warp choice the tile autotuner may pick
+@pytest.mark.parametrize("rows,prec", [(1, "fp64"), (2, "fp64"), (3, "fp64"), (4, "fp64"), (8, "fp64"), (1, "fp32"),
+                                       (2, "fp32"), (3, "fp32"), (4, "fp32"), (8, "fp32"), (16, "fp32")])
+@pytest.mark.parametrize("nt", [60, 61])
+def test_d2q9_kernel_variants(rows, prec, nt):
+    # every D2Q9 step-kernel family and rows-per-warp choice the tile autotuner may pick; odd and even horizons
+    # (the two-step forward ends on a single step when Nt is odd)
     tol = (1e-10, 1e-10, 1e-10) if prec == "fp64" else (1e-5, 1e-4, 1e-3)
-    w = tiny_workload("D2Q9", precision=prec, tile_rows=rows, shape=(93, 45), ckpt="sqrt")
+    w = tiny_workload("D2Q9", precision=prec, tile_rows=rows, shape=(93, 45), ckpt="sqrt", Nt=nt)
     g, _ = check(w, *tol)
-    assert g["stats"]["tile_rows_fwd"] == rows and g["stats"]["tile_rows_adj"] == rows
+    assert g["stats"]["tile_rows_fwd"] == rows and g["stats"]["tile_rows_adj"] == (1 if rows == 3 else rows)
 
 
 def test_3d_128x64x64_full_grid_revolve_fp32():
@@ -170,3 +172,13 @@ def test_3d_256x128x128_full_grid_budget_fp32():
     w = workload("d3q15_256x128x128_fp32", Nt=4, K=3, R_t=1.0, amp=13.0 * 4 / 8000, seg_len=2,
                  probe_lo=(176, 40, 40), probe_hi=(190, 88, 88))
     check(w, 1e-5, 1e-4, 1e-3)
+
+
+@pytest.mark.parametrize("rows,prec,kernel", [(1, "fp64", "linear"), (8, "fp64", "linear"), (16, "fp64", "cosine"),
+                                              (8, "fp32", "linear"), (16, "fp32", "linear"), (8, "fp32", "cosine")])
+def test_d3q15_kernel_variants(rows, prec, kernel):
+    # every D3Q15 step-kernel family and planes-per-block choice, on a grid with ragged x, y and z tails
+    tol = (1e-10, 1e-10, 1e-10) if prec == "fp64" else (1e-5, 1e-4, 1e-3)
+    w = tiny_workload("D3Q15", precision=prec, tile_rows=rows, kernel=kernel, shape=(41, 21, 19), ckpt="sqrt")
+    g, _ = check(w, *tol)
+    assert g["stats"]["tile_rows_fwd"] == rows and g["stats"]["tile_rows_adj"] == rows
