@@ -73,7 +73,8 @@ enum { LKS_MODE_JOINT = 0, LKS_MODE_SHAPE = 1, LKS_MODE_MOTION = 2 };
  *  u_crit         stability limit on |u| checked every forward step (<= 0 disables); LKS_EUNSTABLE.
  *  tile_rows      step-kernel variant.  D2Q9: 1 or 2 = row tiles of 28 x 8 or 28 x 16 nodes staged in shared
  *                 memory; 3 = forward steps taken two per launch on 24 x 8 row tiles (adjoint on 28 x 8 row
- *                 tiles); 4, 8 or 16 (16: LKS_FP32 only) = warp-column kernels with that many grid rows per warp.  D3Q15: 1 = shared-memory tiles
+ *                 tiles); 4, 8 or 16 (16: LKS_FP32 only) = warp-column kernels with that many grid rows per warp;
+ *                 32 or 64 = vectorised warp columns (two columns per lane, even n[0] only) with that many rows.  D3Q15: 1 = shared-memory tiles
  *                 of 32 x 4 x 4 nodes; 8 or 16 = z-marching kernels with that many planes per block.
  *                 0 = autotune at lks_create (times every choice on the context's buffers; cached per process).
  */

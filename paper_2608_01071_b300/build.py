@@ -4,6 +4,7 @@ Usage: python -m paper_2608_01071_b300.build   (or build() from Python).
 """
 from __future__ import annotations
 
+import glob
 import os
 import subprocess
 import sys
@@ -11,8 +12,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", "lks_api.cu")]
-DEPS = [os.path.join(HERE, "csrc", f) for f in ("lks_common.cuh", "lks_prep_kernels.cuh", "lks_step_kernels.cuh")] + [
-    os.path.join(ROOT, "include", "lks.h")]
+DEPS = sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh"))) + [os.path.join(ROOT, "include", "lks.h")]
 LIB = os.path.join(HERE, "liblks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

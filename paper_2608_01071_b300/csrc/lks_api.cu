@@ -19,6 +19,7 @@
 #include "lks_step2d.cuh"
 #include "lks_step3d.cuh"
 #include "lks_step2r.cuh"
+#include "lks_step2v.cuh"
 #include <map>
 #include <tuple>
 
@@ -240,7 +241,11 @@ struct Engine2D : EngineCommon<T, 2, HW> {
         set_rows(1, 1, g);
     }
     static void geom(int r, const Geom& g, dim3& th, dim3& tile, dim3& grid) {
-        if (r == 3) {  // two-step fused row tiles
+        if (r >= 32) {  // vectorised warp columns, two columns per lane
+            th = dim3(32 * WY, 1, 1);
+            tile = dim3(kVecCols, r * WY, 1);
+            grid = dim3(nblk(g.n[0], kVecCols), nblk(g.n[1], r * WY), 1);
+        } else if (r == 3) {  // two-step fused row tiles
             th = dim3(32, 8, 1);
             tile = dim3(Fused2::TXO, Fused2::TY, 1);
             grid = dim3(nblk(g.n[0], Fused2::TXO), nblk(g.n[1], Fused2::TY), 1);
@@ -255,8 +260,12 @@ struct Engine2D : EngineCommon<T, 2, HW> {
         }
     }
     bool set_rows(int rf, int ra, const Geom& g) override {
-        // rows kept in registers grow with R: FP32 allows up to 16, FP64 up to 8 without spills; 3 = fused forward
-        auto ok = [](int r) { return r == 1 || r == 2 || r == 4 || r == 8 || (r == 16 && sizeof(T) == 4); };
+        // rows kept in registers grow with R: FP32 allows up to 16, FP64 up to 8 without spills; 3 = fused forward;
+        // 32 and 64 = vectorised warp columns (even x extent only)
+        const bool even = (g.n[0] % 2) == 0;
+        auto ok = [even](int r) {
+            return r == 1 || r == 2 || r == 4 || r == 8 || (r == 16 && sizeof(T) == 4) || ((r == 32 || r == 64) && even);
+        };
         if (!(ok(rf) || rf == 3) || !ok(ra)) return false;
         this->rows_f = rf;
         this->rows_a = ra;
@@ -291,6 +300,8 @@ struct Engine2D : EngineCommon<T, 2, HW> {
             case 2: launch_pdl(fwd2r_kernel<T, HW, 2>, this->fgrid, this->fthreads, smem2r_fwd<T, 2>(), s, this->pdl, g, a); break;
             case 4: fwd_r<4>(g, a, s); break;
             case 8: fwd_r<8>(g, a, s); break;
+            case 32: launch_pdl(fwd2v_kernel<T, HW, 32>, this->fgrid, this->fthreads, 0, s, this->pdl, g, a); break;
+            case 64: launch_pdl(fwd2v_kernel<T, HW, 64>, this->fgrid, this->fthreads, 0, s, this->pdl, g, a); break;
             default: fwd_r<(sizeof(T) == 4 ? 16 : 8)>(g, a, s); break;
         }
     }
@@ -302,6 +313,8 @@ struct Engine2D : EngineCommon<T, 2, HW> {
             case 2: launch_pdl(adj2r_kernel<T, HW, 2>, this->agrid, this->athreads, smem2r_adj<T, 2>(), s, this->pdl, g, a); break;
             case 4: adj_r<4>(g, a, s); break;
             case 8: adj_r<8>(g, a, s); break;
+            case 32: launch_pdl(adj2v_kernel<T, HW, 32>, this->agrid, this->athreads, 0, s, this->pdl, g, a); break;
+            case 64: launch_pdl(adj2v_kernel<T, HW, 64>, this->agrid, this->athreads, 0, s, this->pdl, g, a); break;
             default: adj_r<(sizeof(T) == 4 ? 16 : 8)>(g, a, s); break;
         }
     }
@@ -478,8 +491,10 @@ void validate(const lks_params* p) {
     if (p->mode < LKS_MODE_JOINT || p->mode > LKS_MODE_MOTION) bad("unknown mode");
     if (p->ckpt_slots < 0 || p->seg_len < 0 || p->ckpt_bytes < 0) bad("negative checkpoint setting");
     if (D == 2 && p->tile_rows != 0 && p->tile_rows != 1 && p->tile_rows != 2 && p->tile_rows != 3 && p->tile_rows != 4 &&
-        p->tile_rows != 8 && !(p->tile_rows == 16 && p->precision == LKS_FP32))
-        bad("D2Q9 tile_rows must be 0 (autotune), 1 or 2 (row tiles), 3 (two-step row tiles), 4, 8, or 16 (FP32 only)");
+        p->tile_rows != 8 && !(p->tile_rows == 16 && p->precision == LKS_FP32) &&
+        !((p->tile_rows == 32 || p->tile_rows == 64) && p->n[0] % 2 == 0))
+        bad("D2Q9 tile_rows must be 0 (autotune), 1 or 2 (row tiles), 3 (two-step row tiles), 4, 8, 16 (FP32) "
+            "or 32, 64 (even nx)");
     if (D == 3 && p->tile_rows != 0 && p->tile_rows != 1 && p->tile_rows != 8 && p->tile_rows != 16)
         bad("D3Q15 tile_rows must be 0 (autotune), 1 (shared-memory tiles), 8 or 16 (z planes per block)");
 }
@@ -593,11 +608,11 @@ int njb_of(const lks_ctx* c);
 void choose_rows_initial(lks_ctx* c) {
     c->max_ablocks = 0;
     c->max_njb = 0;
-    const int cand2[6] = {1, 2, 4, 8, 16, 3}, cand3[3] = {1, 8, 16};
-    const int nc = c->D == 2 ? (c->tsize == 4 ? 6 : 5) : 3;
+    const int cand2[8] = {1, 2, 3, 4, 8, 16, 32, 64}, cand3[3] = {1, 8, 16};
+    const int nc = c->D == 2 ? 8 : 3;
     for (int i = 0; i < nc; ++i) {
-        const int r = c->D == 2 ? (c->tsize == 4 ? cand2[i] : (i < 4 ? cand2[i] : 3)) : cand3[i];
-        c->eng->set_rows(r, r == 3 ? 1 : r, c->g);
+        const int r = c->D == 2 ? cand2[i] : cand3[i];
+        if (!c->eng->set_rows(r, r == 3 ? 1 : r, c->g)) continue;
         const dim3 ag = c->eng->agrid;
         c->max_ablocks = std::max(c->max_ablocks, (int)(ag.x * ag.y * ag.z));
         c->max_njb = std::max(c->max_njb, njb_of(c));
@@ -633,16 +648,16 @@ void autotune_rows(lks_ctx* c) {
     LKS_CUDA(cudaEventCreate(&e1));
     // D2Q9: row tiles (1, 2), two-step fused row tiles (3, forward only), warp columns (4, 8, 16);
     // D3Q15: z-marching blocks of 8 or 16 planes
-    const int cand2[6] = {1, 2, 3, 4, 8, 16}, cand3[2] = {8, 16};
+    const int cand2[8] = {1, 2, 3, 4, 8, 16, 32, 64}, cand3[2] = {8, 16};
     const int* cand = c->D == 2 ? cand2 : cand3;
-    const int nc = c->D == 2 ? (c->tsize == 4 ? 6 : 5) : 2;
+    const int nc = c->D == 2 ? 8 : 2;
     float best_f = 1e30f, best_a = 1e30f;
     int rf = cand[0], ra = cand[0];
     const int reps = 20;
     const int jlo[3] = {0, 0, 0}, jn[3] = {1, 1, 1};
     for (int ci = 0; ci < nc; ++ci) {
         const int r = cand[ci];
-        c->eng->set_rows(r, r == 3 ? 1 : r, c->g);
+        if (!c->eng->set_rows(r, r == 3 ? 1 : r, c->g)) continue;  // not available for this grid / precision
         for (int pass = 0; pass < 2; ++pass) {
             if (pass == 1 && r == 3) continue;  // the fused variant is a forward kernel only
             for (int k = 0; k < 3 + reps; ++k) {
