@@ -38,7 +38,8 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nt", type=int, default=0, help="override the horizon (short runs for profiler captures)")
-    ap.add_argument("--tile-rows", type=int, default=0, help="force a D2Q9 kernel variant instead of autotuning")
+    ap.add_argument("--tile-rows", default="", help="force step-kernel variants instead of autotuning: F or F,A "
+                    "(forward and adjoint tile_rows codes)")
     return ap.parse_args()
 
 
@@ -112,27 +113,53 @@ def job_throughput(world, nodes, Nt, steps, seconds):
     return world * nodes * Nt * steps / seconds / 1e9
 
 
-KERNEL_SOURCES = ["lks_common.cuh", "lks_step_kernels.cuh", "lks_step2d.cuh"]
+# Source files of the step kernels: the shared helpers, plus one file per kernel family.
+COMMON_SOURCES = ["lks_common.cuh", "lks_step_kernels.cuh"]
 
 
-def captured_traffic(workload_name, kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary of this workload, or None when the
-    kernel sources changed since that capture (or there is none)."""
+def kernel_variant(lattice, rows, kind):
+    """(name, source file, steps per launch) of the step kernel that a tile_rows code selects.
+
+    kind is "fwd" or "adj".  D2Q9: 1/2 row tiles, 3 the two-step fused forward, 4/8/16 warp columns,
+    32/64 vectorised warp columns.  D3Q15: 1 the generic shared-memory kernel, 8/16 z-marching."""
+    if lattice == "D3Q15":
+        if rows == 1:
+            return f"{kind}_step_kernel", "lks_step_kernels.cuh", 1
+        return f"{kind}3d_kernel<ZB={rows}>", "lks_step3d.cuh", 1
+    if rows == 3 and kind == "fwd":
+        return "fwd2r2_kernel", "lks_step2r.cuh", 2
+    if rows <= 2:
+        return f"{kind}2r_kernel<RPT={rows}>", "lks_step2r.cuh", 1
+    if rows >= 32:
+        return f"{kind}2v_kernel<R={rows}>", "lks_step2v.cuh", 1
+    return f"{kind}2d_kernel<R={rows}>", "lks_step2d.cuh", 1
+
+
+def source_sha(files):
     import hashlib
+
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2608_01071_b300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def captured_traffic(workload_name, kernel, source):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of this workload, or None when there is
+    no capture of that kernel or its sources changed since the capture.
+
+    The summary holds lines `traffic_bytes_per_launch <kernel> <bytes> src <sha256 prefix>`, the hash taken
+    over the shared step-kernel headers followed by the kernel's own header."""
     import re
 
     path = os.path.join(ROOT, "profiles", f"step_kernels_{workload_name}.md")
     if not os.path.exists(path):
         return None
-    text = open(path).read()
-    m = re.search(r"sha256 prefix `([0-9a-f]+)`", text)
-    h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2608_01071_b300", "csrc", f), "rb").read())
-    if not m or h.hexdigest()[: len(m.group(1))] != m.group(1):
-        return None
-    m = re.search(rf"traffic_bytes_per_launch {kernel} (\d+)", text)
-    return int(m.group(1)) if m else None
+    sha = source_sha(COMMON_SOURCES + [source])
+    for m in re.finditer(r"traffic_bytes_per_launch (\S+) (\d+) src ([0-9a-f]+)", open(path).read()):
+        if m.group(1) == kernel and sha.startswith(m.group(3)):
+            return int(m.group(2))
+    return None
 
 
 def node_count(w):
@@ -199,7 +226,8 @@ def run_ours(args):
         w = dict(w, Nt=args.nt, K=min(w["K"], max(2, args.nt // 4)), R_t=max(1.0, w["R_t"] * args.nt / w["Nt"]),
                  amp=w["amp"] * args.nt / w["Nt"])
     if args.tile_rows:
-        w = dict(w, tile_rows=args.tile_rows)
+        codes = [int(v) for v in args.tile_rows.split(",")]
+        w = dict(w, tile_rows=codes[0], tile_rows_adj=codes[1] if len(codes) > 1 else 0)
     D = len(w["shape"])
     N = node_count(w)
     solver = Solver.from_workload(w)
@@ -251,7 +279,9 @@ def run_ours(args):
     t_dev = max_over_ranks(t_dev, dist, dev)
     value = job_throughput(world, N, w["Nt"], args.steps, t_dev)
 
-    # roofline of the dominant kernel (the adjoint step) from its live CUDA-event durations
+    # roofline of the step kernels from their live CUDA-event durations (spans recorded on the launching
+    # streams); algorithmic bytes per node: forward reads and writes the (D+1)-component state, the adjoint reads
+    # and writes lambda and reads the stored velocity, and reads lambda once more over the design footprint box
     s = 4 if w["precision"] == "fp32" else 8
     Fbn = 1
     hw = 1 if w["kernel"] == "linear" else 2
@@ -259,12 +289,36 @@ def run_ours(args):
         Fbn *= w["design"][a] + 2 * w["margin"] + 2 * hw - 1
     adj_bytes = N * (2 * (D + 1) + D) * s + Fbn * (D + 1) * s
     fwd_bytes = N * 2 * (D + 1) * s
-    adj_ms = sum(a for a, _ in st_adj) / max(1, sum(n for _, n in st_adj))
-    fwd_ms = sum(a for a, _ in st_fwd) / max(1, sum(n for _, n in st_fwd))
+    n_adj = max(1, sum(n for _, n in st_adj))
+    n_fwd = max(1, sum(n for _, n in st_fwd) + sum(n for _, n in st_rec))
+    t_adj = sum(a for a, _ in st_adj)
+    t_fwd = sum(a for a, _ in st_fwd) + sum(a for a, _ in st_rec)
+    adj_ms, fwd_ms = t_adj / n_adj, t_fwd / n_fwd  # per step
     rec_ms = sum(a for a, _ in st_rec) / max(1, sum(n for _, n in st_rec))
     peak, peak_kind = peaks()
-    adj_gbs = adj_bytes / (adj_ms * 1e-3) / 1e9
-    fwd_gbs = fwd_bytes / (fwd_ms * 1e-3) / 1e9
+
+    def kernel_entry(kind, step_bytes, step_ms):
+        rows = st0["tile_rows_fwd" if kind == "fwd" else "tile_rows_adj"]
+        name, src, per_launch = kernel_variant(w["lattice"], rows, kind)
+        gbs = step_bytes / (step_ms * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": name, "achieved": gbs, "peak": peak, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": gbs / peak, "traffic": captured_traffic(w["name"], name, src),
+                "bytes_per_launch": step_bytes * per_launch, "us_per_launch": step_ms * per_launch * 1e3,
+                "steps_per_launch": per_launch}
+
+    k_fwd = kernel_entry("fwd", fwd_bytes, fwd_ms)
+    k_adj = kernel_entry("adj", adj_bytes, adj_ms)
+    tot = max(1e-30, t_fwd + t_adj)
+    # shares of the summed kernel spans (recompute overlaps the adjoint on its own stream, so these are shares of
+    # kernel time, not of wall time); forward launches are averaged over the forward sweep and the recomputation
+    k_fwd["share_of_kernel_time"], k_adj["share_of_kernel_time"] = t_fwd / tot, t_adj / tot
+    fwd_sweep_ms = sum(a for a, _ in st_fwd) / max(1, sum(n for _, n in st_fwd))
+    k_fwd["us_per_step_forward_sweep"], k_fwd["us_per_step_recompute"] = fwd_sweep_ms * 1e3, rec_ms * 1e3
+    roof, other = (k_fwd, k_adj) if t_fwd >= t_adj else (k_adj, k_fwd)
+    roof = dict(roof, other_kernel=other)
+    state_mb = N * (D + 1) * s / 2**20
+    l2_note = (f"512 MB buffer written between timed steps; the {state_mb:.1f} MB state "
+               + ("is larger than the 126 MB L2" if state_mb > 126 else "is L2-resident within a step"))
 
     # end to end through the host-pointer C ABI (H2D of gamma and knots, D2H of J and both gradients)
     e2e_times = []
@@ -288,16 +342,8 @@ def run_ours(args):
             "config": {"workload": w["name"], "lattice": w["lattice"], "grid": list(w["shape"]), "design": list(w["design"]),
                        "Nt": w["Nt"], "K": w["K"], "precision": w["precision"] + " state / f64 accumulators",
                        "checkpointing": w["ckpt"], "parallelism": f"replicas{world}",
-                       "l2": "512 MB buffer written between timed steps; the 1.5 MB state is L2-resident within a step"},
-            "roofline": {"bound": "hbm", "kernel": "fwd_step_kernel", "achieved": fwd_gbs, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": fwd_gbs / peak,
-                         "traffic": captured_traffic(w["name"], "fwd_step_kernel") if st0["tile_rows_fwd"] == 1 else None,
-                         "bytes_per_launch": fwd_bytes, "us_per_launch": fwd_ms * 1e3,
-                         "adj_step_kernel": {"achieved": adj_gbs, "frac": adj_gbs / peak, "us_per_launch": adj_ms * 1e3,
-                                             "bytes_per_launch": adj_bytes,
-                                             "traffic": captured_traffic(w["name"], "adj_step_kernel")
-                                             if st0["tile_rows_adj"] == 1 else None},
-                         "recompute_us_per_launch": rec_ms * 1e3},
+                       "l2": l2_note},
+            "roofline": roof,
             "e2e": {"value": e2e, "unit": "G node-steps/s (fwd+adj)", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches * world),
             "tile_rows": [st0["tile_rows_fwd"], st0["tile_rows_adj"]],

@@ -49,6 +49,7 @@ class lks_params(C.Structure):
         ("mode", C.c_int32),
         ("u_crit", C.c_double),
         ("tile_rows", C.c_int32),
+        ("tile_rows_adj", C.c_int32),
     ]
 
 

@@ -226,9 +226,11 @@ struct Engine3D : EngineCommon<T, 3, HW> {
     }
 };
 
-// D2Q9 engine with two kernel families: rows = 1 or 2 select the row-tile kernels (blocks of 32 x 8 threads,
-// tiles 28 wide and 8 or 16 rows high; best on small grids, where launches are latency bound), rows = 4, 8, 16
-// the warp-column kernels with that many rows per warp and WY = 4 warps per block.
+// D2Q9 engine with four kernel families: rows = 1 or 2 select the row-tile kernels (blocks of 32 x 8 threads,
+// tiles 28 wide and 8 or 16 rows high; best on small grids, where launches are latency bound), rows = 3 the
+// forward kernel that takes two steps per launch on 24 x 8 row tiles, rows = 4, 8, 16 the warp-column kernels
+// with that many rows per warp and WY = 4 warps per block, rows = 32, 64 the vectorised warp columns (two grid
+// columns per lane, 60 columns per warp).
 template <typename T, int HW>
 struct Engine2D : EngineCommon<T, 2, HW> {
     static constexpr int WY = 4;
@@ -490,13 +492,18 @@ void validate(const lks_params* p) {
     if (p->ckpt < LKS_CKPT_FULL || p->ckpt > LKS_CKPT_REVOLVE) bad("unknown ckpt");
     if (p->mode < LKS_MODE_JOINT || p->mode > LKS_MODE_MOTION) bad("unknown mode");
     if (p->ckpt_slots < 0 || p->seg_len < 0 || p->ckpt_bytes < 0) bad("negative checkpoint setting");
-    if (D == 2 && p->tile_rows != 0 && p->tile_rows != 1 && p->tile_rows != 2 && p->tile_rows != 3 && p->tile_rows != 4 &&
-        p->tile_rows != 8 && !(p->tile_rows == 16 && p->precision == LKS_FP32) &&
-        !((p->tile_rows == 32 || p->tile_rows == 64) && p->n[0] % 2 == 0))
-        bad("D2Q9 tile_rows must be 0 (autotune), 1 or 2 (row tiles), 3 (two-step row tiles), 4, 8, 16 (FP32) "
-            "or 32, 64 (even nx)");
-    if (D == 3 && p->tile_rows != 0 && p->tile_rows != 1 && p->tile_rows != 8 && p->tile_rows != 16)
-        bad("D3Q15 tile_rows must be 0 (autotune), 1 (shared-memory tiles), 8 or 16 (z planes per block)");
+    // a step-kernel variant code: the forward accepts 3 (two steps per launch), the adjoint does not
+    auto variant_ok = [&](int r, bool fwd) {
+        if (D == 3) return r == 1 || r == 8 || r == 16;
+        return r == 1 || r == 2 || (r == 3 && fwd) || r == 4 || r == 8 || (r == 16 && p->precision == LKS_FP32) ||
+               ((r == 32 || r == 64) && p->n[0] % 2 == 0);
+    };
+    if (p->tile_rows != 0 && !variant_ok(p->tile_rows, true))
+        bad(D == 2 ? "D2Q9 tile_rows must be 0 (autotune), 1 or 2 (row tiles), 3 (two-step row tiles), 4, 8, "
+                     "16 (FP32) or 32, 64 (even nx)"
+                   : "D3Q15 tile_rows must be 0 (autotune), 1 (shared-memory tiles), 8 or 16 (z planes per block)");
+    if (p->tile_rows_adj != 0 && (p->tile_rows == 0 || !variant_ok(p->tile_rows_adj, false)))
+        bad("tile_rows_adj must be 0, or a valid adjoint variant (tile_rows codes other than 3) with tile_rows != 0");
 }
 
 void setup_geometry(lks_ctx* c) {
@@ -618,7 +625,8 @@ void choose_rows_initial(lks_ctx* c) {
         c->max_njb = std::max(c->max_njb, njb_of(c));
     }
     const int r = c->prm.tile_rows > 0 ? c->prm.tile_rows : (c->D == 2 ? 1 : 8);
-    c->eng->set_rows(r, r == 3 ? 1 : r, c->g);
+    const int ra = c->prm.tile_rows_adj > 0 ? c->prm.tile_rows_adj : (r == 3 ? 1 : r);
+    if (!c->eng->set_rows(r, ra, c->g)) throw LksError{LKS_EINVAL, "step-kernel variant not available for this grid"};
 }
 
 // Tile autotuner (D2Q9): time the forward and adjoint step kernels for every rows-per-warp choice on the
@@ -653,32 +661,39 @@ void autotune_rows(lks_ctx* c) {
     const int nc = c->D == 2 ? 8 : 2;
     float best_f = 1e30f, best_a = 1e30f;
     int rf = cand[0], ra = cand[0];
-    const int reps = 20;
     const int jlo[3] = {0, 0, 0}, jn[3] = {1, 1, 1};
+    // ms per step of `reps` back-to-back launches of one variant after 3 untimed ones
+    auto time_variant = [&](int r, int pass, int reps) {
+        for (int k = 0; k < 3 + reps; ++k) {
+            if (k == 3) LKS_CUDA(cudaEventRecord(e0, s));
+            if (pass == 0 && r == 3)
+                c->eng->fwd2(c->g, c->slot[0], c->pp[0], c->pp[1], c->d_kref, c->d_pose, nullptr, nullptr, c->d_flag,
+                             jlo, jn, s);
+            else if (pass == 0)
+                c->eng->fwd(c->g, c->slot[0], c->pp[k & 1], c->d_kref, c->d_pose, nullptr, c->d_flag, jlo, jn, s);
+            else
+                c->eng->adj(c->g, c->lam[k & 1], c->lam[(k + 1) & 1], c->slot[0], c->slot[0], c->d_kref, c->d_pose,
+                            c->d_boxbuf, 1, s);
+        }
+        LKS_CUDA(cudaEventRecord(e1, s));
+        LKS_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        LKS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        return ms / (float)reps / (pass == 0 && r == 3 ? 2.f : 1.f);  // the fused variant takes two steps per launch
+    };
     for (int ci = 0; ci < nc; ++ci) {
         const int r = cand[ci];
         if (!c->eng->set_rows(r, r == 3 ? 1 : r, c->g)) continue;  // not available for this grid / precision
         for (int pass = 0; pass < 2; ++pass) {
             if (pass == 1 && r == 3) continue;  // the fused variant is a forward kernel only
-            for (int k = 0; k < 3 + reps; ++k) {
-                if (k == 3) LKS_CUDA(cudaEventRecord(e0, s));
-                if (pass == 0 && r == 3)
-                    c->eng->fwd2(c->g, c->slot[0], c->pp[0], c->pp[1], c->d_kref, c->d_pose, nullptr, nullptr, c->d_flag,
-                                 jlo, jn, s);
-                else if (pass == 0)
-                    c->eng->fwd(c->g, c->slot[0], c->pp[k & 1], c->d_kref, c->d_pose, nullptr, c->d_flag, jlo, jn, s);
-                else
-                    c->eng->adj(c->g, c->lam[k & 1], c->lam[(k + 1) & 1], c->slot[0], c->slot[0], c->d_kref, c->d_pose,
-                                c->d_boxbuf, 1, s);
-            }
-            LKS_CUDA(cudaEventRecord(e1, s));
-            LKS_CUDA(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            LKS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            if (pass == 0 && r == 3) ms *= 0.5f;  // two steps per launch
+            // size each measurement to about 1.5 ms of launches and keep the fastest of three
+            const float est = time_variant(r, pass, 10);
+            const int reps = std::max(10, std::min(2000, (int)(1.5f / std::max(est, 1e-4f))));
+            float ms = est;
+            for (int trial = 0; trial < 3; ++trial) ms = std::min(ms, time_variant(r, pass, reps));
             if (std::getenv("LKS_TUNE_VERBOSE"))
-                std::fprintf(stderr, "lks autotune %dx%dx%d %s rows=%d: %.3f us/step\n", c->g.n[0], c->g.n[1], c->g.n[2],
-                             pass == 0 ? "forward" : "adjoint", r, 1e3f * ms / reps);
+                std::fprintf(stderr, "lks autotune %dx%dx%d %s rows=%d: %.3f us/step (%d launches)\n", c->g.n[0],
+                             c->g.n[1], c->g.n[2], pass == 0 ? "forward" : "adjoint", r, 1e3f * ms, reps);
             if (pass == 0 && ms < best_f) {
                 best_f = ms;
                 rf = r;
