@@ -120,14 +120,18 @@ COMMON_SOURCES = ["lks_common.cuh", "lks_step_kernels.cuh"]
 def kernel_variant(lattice, rows, kind):
     """(name, source file, steps per launch) of the step kernel that a tile_rows code selects.
 
-    kind is "fwd" or "adj".  D2Q9: 1/2 row tiles, 3 the two-step fused forward, 4/8/16 warp columns,
-    32/64 vectorised warp columns.  D3Q15: 1 the generic shared-memory kernel, 8/16 z-marching."""
+    kind is "fwd" or "adj".  D2Q9: 1/2 row tiles, 3 two steps per launch on row tiles, 4/8/16 warp columns,
+    32/64 vectorised warp columns.  D3Q15: 1 the generic shared-memory kernel, 8/16 z-marching, 32/64/96
+    separable z-marching (planes x rows per block 16 x 8, 32 x 8, 16 x 16)."""
     if lattice == "D3Q15":
         if rows == 1:
             return f"{kind}_step_kernel", "lks_step_kernels.cuh", 1
+        if rows >= 32:
+            zb, ty = {32: (16, 8), 64: (32, 8), 96: (16, 16)}[rows]
+            return f"{kind}3s_kernel<ZB={zb},TY={ty}>", "lks_step3s.cuh", 1
         return f"{kind}3d_kernel<ZB={rows}>", "lks_step3d.cuh", 1
-    if rows == 3 and kind == "fwd":
-        return "fwd2r2_kernel", "lks_step2r.cuh", 2
+    if rows == 3:
+        return f"{kind}2r2_kernel", "lks_step2r.cuh", 2
     if rows <= 2:
         return f"{kind}2r_kernel<RPT={rows}>", "lks_step2r.cuh", 1
     if rows >= 32:
@@ -317,8 +321,9 @@ def run_ours(args):
     roof, other = (k_fwd, k_adj) if t_fwd >= t_adj else (k_adj, k_fwd)
     roof = dict(roof, other_kernel=other)
     state_mb = N * (D + 1) * s / 2**20
-    l2_note = (f"512 MB buffer written between timed steps; the {state_mb:.1f} MB state "
-               + ("is larger than the 126 MB L2" if state_mb > 126 else "is L2-resident within a step"))
+    # a step reads one state and writes another
+    l2_note = (f"512 MB buffer written between timed steps; a step touches two {state_mb:.1f} MB states, "
+               + ("more than the 126 MB L2" if 2 * state_mb > 126 else "which stay L2-resident"))
 
     # end to end through the host-pointer C ABI (H2D of gamma and knots, D2H of J and both gradients)
     e2e_times = []

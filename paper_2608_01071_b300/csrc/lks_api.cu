@@ -18,6 +18,7 @@
 #include "lks_step_kernels.cuh"
 #include "lks_step2d.cuh"
 #include "lks_step3d.cuh"
+#include "lks_step3s.cuh"
 #include "lks_step2r.cuh"
 #include "lks_step2v.cuh"
 #include <map>
@@ -47,7 +48,8 @@ struct LksError {
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// Launch a step kernel with programmatic stream serialization (see pdl_wait_then_release).
+// Launch a step kernel with programmatic stream serialization (see pdl_wait_then_release) and the priority of
+// its stream as a launch attribute, so that graph nodes captured from it keep that priority.
 template <typename K, typename... Args>
 void launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl, Args... args) {
     cudaLaunchConfig_t cfg = {};
@@ -55,11 +57,18 @@ void launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, bo
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    int prio = 0;
+    if (cudaStreamGetPriority(s, &prio) != cudaSuccess) {
+        cudaGetLastError();
+        prio = 0;
+    }
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = prio;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = pdl ? 1 : 0;
+    cfg.numAttrs = pdl ? 2 : 1;
     cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
     if (e != cudaSuccess) throw LksError{LKS_ECUDA, std::string("cudaLaunchKernelEx: ") + cudaGetErrorString(e)};
 }
@@ -72,10 +81,13 @@ struct Engine {
     dim3 fthreads, athreads;  // threads per block of the forward / adjoint step kernels
     dim3 ftile, atile;        // analysis nodes covered per block
     dim3 fgrid, agrid;
-    int rows_f = 0, rows_a = 0;  // D2Q9: rows per warp of the forward / adjoint kernels (0 elsewhere)
+    int rows_f = 0, rows_a = 0;  // step-kernel variant codes (tile_rows) of the forward / adjoint kernels
     virtual ~Engine() {}
-    // D2Q9 only: choose the rows per warp (4, 8, 16 or 32) of the forward and adjoint step kernels
-    virtual bool set_rows(int rf, int ra, const Geom& g) { return false; }
+    // choose the forward and adjoint step-kernel variants; false when one is not available for this grid
+    virtual bool set_rows(int rf, int ra, const Geom& g) = 0;
+    // variant codes the autotuner tries (some may be unavailable for a given grid)
+    virtual std::vector<int> fwd_codes() const = 0;
+    virtual std::vector<int> adj_codes() const = 0;
     virtual void fwd(const Geom& g, const void* in, void* out, const void* kref, const Pose* pose, double* jslot,
                      unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) = 0;
     // two-step forward launches (steps n and n+1 in one kernel); out2 == nullptr takes step n only
@@ -84,6 +96,12 @@ struct Engine {
                       double* jslot1, double* jslot2, unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) {}
     virtual void adj(const Geom& g, const void* lam_in, void* lam_out, const void* prev, const void* cur,
                      const void* kref, const Pose* pose, void* boxbuf, int src, cudaStream_t s) = 0;
+    // two-step adjoint launches: steps n (pose, boxbuf1, src1; states prev1 = n-1, cur1 = n) and n-1 (pose - 1,
+    // boxbuf2, src2; states prev2 = n-2, prev1) in one kernel
+    virtual bool fused_adj2() const { return false; }
+    virtual void adj2(const Geom& g, const void* lam_in, void* lam_out, const void* prev1, const void* cur1,
+                      const void* prev2, const void* kref, const Pose* pose, void* boxbuf1, int src1, void* boxbuf2,
+                      int src2, cudaStream_t s) {}
     virtual void sens(const Geom& g, const Pose* poses, const void* kref, const void* boxbuf, long long bstride,
                       int n_first, int nsteps, void* kbar, double* mslot, cudaStream_t s) = 0;
     virtual void gather(const Geom& g, const Pose* poses, const void* kbar, int n_first, int nsteps,
@@ -166,7 +184,9 @@ struct EngineCommon : Engine {
 };
 
 // D3Q15 engine: rows = 1 selects the generic shared-memory tile kernels (32 x 4 x 4 nodes per block);
-// rows = 8 or 16 the z-marching kernels with that many planes per block (32 x 8 columns).
+// rows = 8 or 16 the z-marching kernels with that many planes per block (32 x 8 columns); forward rows = 32,
+// 64 the separable z-marching kernels with 16 or 32 planes per block (32 x 8 columns), forward rows = 96 the
+// separable forward with 16 planes of 32 x 16 columns.
 template <typename T, int HW>
 struct Engine3D : EngineCommon<T, 3, HW> {
     static constexpr int TX = 32, TY = 4, TZ = 4;
@@ -183,12 +203,29 @@ struct Engine3D : EngineCommon<T, 3, HW> {
         LKS_CUDA(cudaFuncSetAttribute(fwd3d_kernel<T, HW, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3d_fwd<T>()));
         LKS_CUDA(cudaFuncSetAttribute(adj3d_kernel<T, HW, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3d_adj<T>()));
         LKS_CUDA(cudaFuncSetAttribute(adj3d_kernel<T, HW, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3d_adj<T>()));
+        LKS_CUDA(cudaFuncSetAttribute(fwd3s_kernel<T, HW, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem3s_fwd<T, 8>()));
+        LKS_CUDA(cudaFuncSetAttribute(fwd3s_kernel<T, HW, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem3s_fwd<T, 8>()));
+        LKS_CUDA(cudaFuncSetAttribute(fwd3s_kernel<T, HW, 16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem3s_fwd<T, 16>()));
+        LKS_CUDA(cudaFuncSetAttribute(adj3s_kernel<T, HW, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem3s_adj<T, 8>()));
+        LKS_CUDA(cudaFuncSetAttribute(adj3s_kernel<T, HW, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem3s_adj<T, 8>()));
         set_rows(8, 8, g);
     }
+    std::vector<int> fwd_codes() const override { return {1, 8, 16, 32, 64, 96}; }
+    std::vector<int> adj_codes() const override { return {1, 8, 16, 32, 64}; }
     static void geom(int r, const Geom& g, dim3& th, dim3& tile, dim3& grid) {
         if (r == 1) {
             th = tile = dim3(TX, TY, TZ);
             grid = dim3(nblk(g.n[0], TX), nblk(g.n[1], TY), nblk(g.n[2], TZ));
+        } else if (r >= 32) {  // separable forward: (planes, rows) per block
+            const int zb = r == 64 ? 32 : 16, ty = r == 96 ? 16 : 8;
+            th = dim3(32, ty, 1);
+            tile = dim3(32, ty, zb);
+            grid = dim3(nblk(g.n[0], 32), nblk(g.n[1], ty), nblk(g.n[2], zb));
         } else {
             th = dim3(Reg3::TX, Reg3::TY, 1);
             tile = dim3(Reg3::TX, Reg3::TY, r);
@@ -196,8 +233,9 @@ struct Engine3D : EngineCommon<T, 3, HW> {
         }
     }
     bool set_rows(int rf, int ra, const Geom& g) override {
-        auto ok = [](int r) { return r == 1 || r == 8 || r == 16; };
-        if (!ok(rf) || !ok(ra)) return false;
+        auto okf = [](int r) { return r == 1 || r == 8 || r == 16 || r == 32 || r == 64 || r == 96; };
+        auto oka = [](int r) { return r == 1 || r == 8 || r == 16 || r == 32 || r == 64; };
+        if (!okf(rf) || !oka(ra)) return false;
         this->rows_f = rf;
         this->rows_a = ra;
         geom(rf, g, this->fthreads, this->ftile, this->fgrid);
@@ -211,8 +249,14 @@ struct Engine3D : EngineCommon<T, 3, HW> {
             launch_pdl(fwd_step_kernel<T, 3, HW, TX, TY, TZ>, this->fgrid, this->fthreads, smem_fwd, s, this->pdl, g, a);
         else if (this->rows_f == 8)
             launch_pdl(fwd3d_kernel<T, HW, 8>, this->fgrid, this->fthreads, smem3d_fwd<T>(), s, this->pdl, g, a);
-        else
+        else if (this->rows_f == 16)
             launch_pdl(fwd3d_kernel<T, HW, 16>, this->fgrid, this->fthreads, smem3d_fwd<T>(), s, this->pdl, g, a);
+        else if (this->rows_f == 32)
+            launch_pdl(fwd3s_kernel<T, HW, 16, 8>, this->fgrid, this->fthreads, smem3s_fwd<T, 8>(), s, this->pdl, g, a);
+        else if (this->rows_f == 64)
+            launch_pdl(fwd3s_kernel<T, HW, 32, 8>, this->fgrid, this->fthreads, smem3s_fwd<T, 8>(), s, this->pdl, g, a);
+        else
+            launch_pdl(fwd3s_kernel<T, HW, 16, 16>, this->fgrid, this->fthreads, smem3s_fwd<T, 16>(), s, this->pdl, g, a);
     }
     void adj(const Geom& g, const void* lam_in, void* lam_out, const void* prev, const void* cur, const void* kref,
              const Pose* pose, void* boxbuf, int src, cudaStream_t s) override {
@@ -221,8 +265,12 @@ struct Engine3D : EngineCommon<T, 3, HW> {
             launch_pdl(adj_step_kernel<T, 3, HW, TX, TY, TZ>, this->agrid, this->athreads, smem_adj, s, this->pdl, g, a);
         else if (this->rows_a == 8)
             launch_pdl(adj3d_kernel<T, HW, 8>, this->agrid, this->athreads, smem3d_adj<T>(), s, this->pdl, g, a);
-        else
+        else if (this->rows_a == 16)
             launch_pdl(adj3d_kernel<T, HW, 16>, this->agrid, this->athreads, smem3d_adj<T>(), s, this->pdl, g, a);
+        else if (this->rows_a == 32)
+            launch_pdl(adj3s_kernel<T, HW, 16, 8>, this->agrid, this->athreads, smem3s_adj<T, 8>(), s, this->pdl, g, a);
+        else
+            launch_pdl(adj3s_kernel<T, HW, 32, 8>, this->agrid, this->athreads, smem3s_adj<T, 8>(), s, this->pdl, g, a);
     }
 };
 
@@ -236,6 +284,7 @@ struct Engine2D : EngineCommon<T, 2, HW> {
     static constexpr int WY = 4;
     explicit Engine2D(const Geom& g) {
         LKS_CUDA(cudaFuncSetAttribute(fwd2r2_kernel<T, HW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r2_fwd<T>()));
+        LKS_CUDA(cudaFuncSetAttribute(adj2r2_kernel<T, HW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r2_adj<T>()));
         LKS_CUDA(cudaFuncSetAttribute(fwd2r_kernel<T, HW, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_fwd<T, 1>()));
         LKS_CUDA(cudaFuncSetAttribute(fwd2r_kernel<T, HW, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_fwd<T, 2>()));
         LKS_CUDA(cudaFuncSetAttribute(adj2r_kernel<T, HW, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_adj<T, 1>()));
@@ -261,6 +310,8 @@ struct Engine2D : EngineCommon<T, 2, HW> {
             grid = dim3(nblk(g.n[0], kLanesOut), nblk(g.n[1], r * WY), 1);
         }
     }
+    std::vector<int> fwd_codes() const override { return {1, 2, 3, 4, 8, 16, 32, 64}; }
+    std::vector<int> adj_codes() const override { return {1, 2, 3, 4, 8, 16, 32, 64}; }
     bool set_rows(int rf, int ra, const Geom& g) override {
         // rows kept in registers grow with R: FP32 allows up to 16, FP64 up to 8 without spills; 3 = fused forward;
         // 32 and 64 = vectorised warp columns (even x extent only)
@@ -268,7 +319,7 @@ struct Engine2D : EngineCommon<T, 2, HW> {
         auto ok = [even](int r) {
             return r == 1 || r == 2 || r == 4 || r == 8 || (r == 16 && sizeof(T) == 4) || ((r == 32 || r == 64) && even);
         };
-        if (!(ok(rf) || rf == 3) || !ok(ra)) return false;
+        if (!(ok(rf) || rf == 3) || !(ok(ra) || ra == 3)) return false;
         this->rows_f = rf;
         this->rows_a = ra;
         geom(rf, g, this->fthreads, this->ftile, this->fgrid);
@@ -280,6 +331,10 @@ struct Engine2D : EngineCommon<T, 2, HW> {
         launch_pdl(fwd2d_kernel<T, HW, R, WY>, this->fgrid, this->fthreads, 0, s, this->pdl, g, a);
     }
     bool fused2() const override { return this->rows_f == 3; }
+    bool fused_adj2() const override { return this->rows_a == 3; }
+    void adj2(const Geom& g, const void* lam_in, void* lam_out, const void* prev1, const void* cur1, const void* prev2,
+              const void* kref, const Pose* pose, void* boxbuf1, int src1, void* boxbuf2, int src2,
+              cudaStream_t s) override;
     void fwd2(const Geom& g, const void* in, void* out1, void* out2, const void* kref, const Pose* pose1,
               double* jslot1, double* jslot2, unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) override {
         auto a1 = make_fwd_args<T>(g, in, out1, kref, pose1, jslot1, flag, jlo, jn);
@@ -311,6 +366,9 @@ struct Engine2D : EngineCommon<T, 2, HW> {
              const Pose* pose, void* boxbuf, int src, cudaStream_t s) override {
         auto a = make_adj_args<T>(g, lam_in, lam_out, prev, cur, kref, pose, boxbuf, src);
         switch (this->rows_a) {
+            case 3:
+                launch_pdl(adj2r2_kernel<T, HW>, this->agrid, this->athreads, smem2r2_adj<T>(), s, this->pdl, g, a, a, 0);
+                break;
             case 1: launch_pdl(adj2r_kernel<T, HW, 1>, this->agrid, this->athreads, smem2r_adj<T, 1>(), s, this->pdl, g, a); break;
             case 2: launch_pdl(adj2r_kernel<T, HW, 2>, this->agrid, this->athreads, smem2r_adj<T, 2>(), s, this->pdl, g, a); break;
             case 4: adj_r<4>(g, a, s); break;
@@ -321,6 +379,15 @@ struct Engine2D : EngineCommon<T, 2, HW> {
         }
     }
 };
+
+template <typename T, int HW>
+void Engine2D<T, HW>::adj2(const Geom& g, const void* lam_in, void* lam_out, const void* prev1, const void* cur1,
+                           const void* prev2, const void* kref, const Pose* pose, void* boxbuf1, int src1,
+                           void* boxbuf2, int src2, cudaStream_t s) {
+    auto a1 = make_adj_args<T>(g, lam_in, lam_out, prev1, cur1, kref, pose, boxbuf1, src1);
+    auto a2 = make_adj_args<T>(g, lam_in, lam_out, prev2, prev1, kref, pose - 1, boxbuf2, src2);
+    launch_pdl(adj2r2_kernel<T, HW>, this->agrid, this->athreads, smem2r2_adj<T>(), s, this->pdl, g, a1, a2, 1);
+}
 
 template <typename T>
 Engine* make_engine_t(int D, int hw, const Geom& g) {
@@ -494,16 +561,17 @@ void validate(const lks_params* p) {
     if (p->ckpt_slots < 0 || p->seg_len < 0 || p->ckpt_bytes < 0) bad("negative checkpoint setting");
     // a step-kernel variant code: the forward accepts 3 (two steps per launch), the adjoint does not
     auto variant_ok = [&](int r, bool fwd) {
-        if (D == 3) return r == 1 || r == 8 || r == 16;
-        return r == 1 || r == 2 || (r == 3 && fwd) || r == 4 || r == 8 || (r == 16 && p->precision == LKS_FP32) ||
+        if (D == 3) return r == 1 || r == 8 || r == 16 || r == 32 || r == 64 || (fwd && r == 96);
+        return r == 1 || r == 2 || r == 3 || r == 4 || r == 8 || (r == 16 && p->precision == LKS_FP32) ||
                ((r == 32 || r == 64) && p->n[0] % 2 == 0);
     };
     if (p->tile_rows != 0 && !variant_ok(p->tile_rows, true))
         bad(D == 2 ? "D2Q9 tile_rows must be 0 (autotune), 1 or 2 (row tiles), 3 (two-step row tiles), 4, 8, "
                      "16 (FP32) or 32, 64 (even nx)"
-                   : "D3Q15 tile_rows must be 0 (autotune), 1 (shared-memory tiles), 8 or 16 (z planes per block)");
+                   : "D3Q15 tile_rows must be 0 (autotune), 1 (shared-memory tiles), 8 or 16 (z planes per block), "
+                     "32, 64 (separable, 16 or 32 planes per block), 96 (separable forward, 16 x 16 columns)");
     if (p->tile_rows_adj != 0 && (p->tile_rows == 0 || !variant_ok(p->tile_rows_adj, false)))
-        bad("tile_rows_adj must be 0, or a valid adjoint variant (tile_rows codes other than 3) with tile_rows != 0");
+        bad("tile_rows_adj must be 0, or a valid adjoint variant with tile_rows != 0");
 }
 
 void setup_geometry(lks_ctx* c) {
@@ -615,17 +683,17 @@ int njb_of(const lks_ctx* c);
 void choose_rows_initial(lks_ctx* c) {
     c->max_ablocks = 0;
     c->max_njb = 0;
-    const int cand2[8] = {1, 2, 3, 4, 8, 16, 32, 64}, cand3[3] = {1, 8, 16};
-    const int nc = c->D == 2 ? 8 : 3;
-    for (int i = 0; i < nc; ++i) {
-        const int r = c->D == 2 ? cand2[i] : cand3[i];
-        if (!c->eng->set_rows(r, r == 3 ? 1 : r, c->g)) continue;
-        const dim3 ag = c->eng->agrid;
-        c->max_ablocks = std::max(c->max_ablocks, (int)(ag.x * ag.y * ag.z));
-        c->max_njb = std::max(c->max_njb, njb_of(c));
-    }
+    const std::vector<int> cf = c->eng->fwd_codes(), ca = c->eng->adj_codes();
+    for (int rf : cf)
+        for (int ra : ca) {
+            if (!c->eng->set_rows(rf, ra, c->g)) continue;
+            const dim3 ag = c->eng->agrid;
+            c->max_ablocks = std::max(c->max_ablocks, (int)(ag.x * ag.y * ag.z));
+            c->max_njb = std::max(c->max_njb, njb_of(c));
+        }
     const int r = c->prm.tile_rows > 0 ? c->prm.tile_rows : (c->D == 2 ? 1 : 8);
-    const int ra = c->prm.tile_rows_adj > 0 ? c->prm.tile_rows_adj : (r == 3 ? 1 : r);
+    int ra = c->prm.tile_rows_adj > 0 ? c->prm.tile_rows_adj : r;
+    if (c->prm.tile_rows_adj <= 0 && std::find(ca.begin(), ca.end(), ra) == ca.end()) ra = c->D == 2 ? 1 : 8;
     if (!c->eng->set_rows(r, ra, c->g)) throw LksError{LKS_EINVAL, "step-kernel variant not available for this grid"};
 }
 
@@ -647,30 +715,31 @@ void autotune_rows(lks_ctx* c) {
         }
     }
     cudaStream_t s = c->side;
-    LKS_CUDA(cudaMemsetAsync(c->d_pose, 0, sizeof(Pose), s));
+    LKS_CUDA(cudaMemsetAsync(c->d_pose, 0, 2 * sizeof(Pose), s));  // poses 0 and 1 (Nt >= 1)
     LKS_CUDA(cudaMemsetAsync(c->lam[0], 0, c->state_bytes, s));
     LKS_CUDA(cudaMemsetAsync(c->lam[1], 0, c->state_bytes, s));
     c->eng->init_state(c->g, c->slot[0], s);
     cudaEvent_t e0, e1;
     LKS_CUDA(cudaEventCreate(&e0));
     LKS_CUDA(cudaEventCreate(&e1));
-    // D2Q9: row tiles (1, 2), two-step fused row tiles (3, forward only), warp columns (4, 8, 16);
-    // D3Q15: z-marching blocks of 8 or 16 planes
-    const int cand2[8] = {1, 2, 3, 4, 8, 16, 32, 64}, cand3[2] = {8, 16};
-    const int* cand = c->D == 2 ? cand2 : cand3;
-    const int nc = c->D == 2 ? 8 : 2;
+    // every forward variant with the initial adjoint one, then every adjoint variant with the initial forward one
+    const std::vector<int> cf = c->eng->fwd_codes(), ca = c->eng->adj_codes();
+    const int rf0 = c->eng->rows_f, ra0 = c->eng->rows_a;
     float best_f = 1e30f, best_a = 1e30f;
-    int rf = cand[0], ra = cand[0];
+    int rf = rf0, ra = ra0;
     const int jlo[3] = {0, 0, 0}, jn[3] = {1, 1, 1};
     // ms per step of `reps` back-to-back launches of one variant after 3 untimed ones
     auto time_variant = [&](int r, int pass, int reps) {
         for (int k = 0; k < 3 + reps; ++k) {
             if (k == 3) LKS_CUDA(cudaEventRecord(e0, s));
-            if (pass == 0 && r == 3)
+            if (pass == 0 && c->eng->fused2())
                 c->eng->fwd2(c->g, c->slot[0], c->pp[0], c->pp[1], c->d_kref, c->d_pose, nullptr, nullptr, c->d_flag,
                              jlo, jn, s);
             else if (pass == 0)
                 c->eng->fwd(c->g, c->slot[0], c->pp[k & 1], c->d_kref, c->d_pose, nullptr, c->d_flag, jlo, jn, s);
+            else if (c->eng->fused_adj2())
+                c->eng->adj2(c->g, c->lam[k & 1], c->lam[(k + 1) & 1], c->slot[0], c->slot[0], c->slot[0], c->d_kref,
+                             c->d_pose + 1, c->d_boxbuf, 1, c->d_boxbuf, 1, s);
             else
                 c->eng->adj(c->g, c->lam[k & 1], c->lam[(k + 1) & 1], c->slot[0], c->slot[0], c->d_kref, c->d_pose,
                             c->d_boxbuf, 1, s);
@@ -679,13 +748,13 @@ void autotune_rows(lks_ctx* c) {
         LKS_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
         LKS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        return ms / (float)reps / (pass == 0 && r == 3 ? 2.f : 1.f);  // the fused variant takes two steps per launch
+        // the fused variant takes two steps per launch
+        return ms / (float)reps / ((pass == 0 ? c->eng->fused2() : c->eng->fused_adj2()) ? 2.f : 1.f);
     };
-    for (int ci = 0; ci < nc; ++ci) {
-        const int r = cand[ci];
-        if (!c->eng->set_rows(r, r == 3 ? 1 : r, c->g)) continue;  // not available for this grid / precision
-        for (int pass = 0; pass < 2; ++pass) {
-            if (pass == 1 && r == 3) continue;  // the fused variant is a forward kernel only
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int r : (pass == 0 ? cf : ca)) {
+            // not available for this grid / precision
+            if (!(pass == 0 ? c->eng->set_rows(r, ra0, c->g) : c->eng->set_rows(rf0, r, c->g))) continue;
             // size each measurement to about 1.5 ms of launches and keep the fastest of three
             const float est = time_variant(r, pass, 10);
             const int reps = std::max(10, std::min(2000, (int)(1.5f / std::max(est, 1e-4f))));
@@ -769,11 +838,15 @@ void allocate(lks_ctx* c) {
 
     LKS_CUDA(cudaHostAlloc((void**)&c->h_flag, 16, cudaHostAllocDefault));
     *c->h_flag = 0;
-    LKS_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
-    LKS_CUDA(cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking));
-    LKS_CUDA(cudaStreamCreateWithFlags(&c->cap3, cudaStreamNonBlocking));
-    LKS_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
-    LKS_CUDA(cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking));
+    // the reverse sweep's critical path (the adjoint chain on the capture stream) gets the highest priority; the
+    // recomputation and the sensitivity passes running beside it have slack and get the lowest
+    int prio_low = 0, prio_high = 0;
+    LKS_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+    LKS_CUDA(cudaStreamCreateWithPriority(&c->cap, cudaStreamNonBlocking, prio_high));
+    LKS_CUDA(cudaStreamCreateWithPriority(&c->cap2, cudaStreamNonBlocking, prio_low));
+    LKS_CUDA(cudaStreamCreateWithPriority(&c->cap3, cudaStreamNonBlocking, prio_low));
+    LKS_CUDA(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_low));
+    LKS_CUDA(cudaStreamCreateWithPriority(&c->side2, cudaStreamNonBlocking, prio_low));
     for (int i = 0; i < 2; ++i) {
         LKS_CUDA(cudaEventCreateWithFlags(&c->ev_rec[i], cudaEventDisableTiming));
         LKS_CUDA(cudaEventCreateWithFlags(&c->ev_adj[i], cudaEventDisableTiming));
@@ -831,7 +904,7 @@ void run_graph(lks_ctx* c, cudaGraphExec_t& gx, cudaStream_t s, F&& body) {
         }
         cudaGraph_t g = nullptr;
         LKS_CUDA(cudaStreamEndCapture(c->cap, &g));
-        cudaError_t e = cudaGraphInstantiate(&gx, g, 0);
+        cudaError_t e = cudaGraphInstantiate(&gx, g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
         LKS_CUDA(e);
     }
@@ -1086,14 +1159,23 @@ void recompute_segment(lks_ctx* c, int a, int b, const void* start, const void* 
 void adjoint_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
     const std::vector<const void*>& st = c->seg_st[buf];
     cudaEvent_t ea = span_begin(c, s);
-    for (int n = b; n > a; --n) {
+    for (int n = b; n > a;) {
         const int j = n - a - 1;  // box-buffer slot of step n
         void* bb = c->tptr(c->d_boxbuf, ((long long)buf * c->Lmax + j) * c->box_step);
-        c->eng->adj(c->g, c->lam[0], c->lam[1], st[n - 1 - a], st[n - a], c->d_kref, c->d_pose + n, bb,
-                    n - 1 >= 1 ? 1 : 0, s);
+        if (c->eng->fused_adj2() && n - 1 > a) {  // steps n and n-1 in one launch
+            void* bb2 = c->tptr(c->d_boxbuf, ((long long)buf * c->Lmax + j - 1) * c->box_step);
+            c->eng->adj2(c->g, c->lam[0], c->lam[1], st[n - 1 - a], st[n - a], st[n - 2 - a], c->d_kref,
+                         c->d_pose + n, bb, n - 1 >= 1 ? 1 : 0, bb2, n - 2 >= 1 ? 1 : 0, s);
+            c->stats.adjoint_steps += 2;
+            n -= 2;
+        } else {
+            c->eng->adj(c->g, c->lam[0], c->lam[1], st[n - 1 - a], st[n - a], c->d_kref, c->d_pose + n, bb,
+                        n - 1 >= 1 ? 1 : 0, s);
+            c->stats.adjoint_steps++;
+            n -= 1;
+        }
         std::swap(c->lam[0], c->lam[1]);
         c->launches++;
-        c->stats.adjoint_steps++;
     }
     span_end(c, 2, ea, s);
 }
@@ -1707,7 +1789,7 @@ void batch_graph(lks_batch* b, cudaGraphExec_t& gx, cudaStream_t s, F&& body) {
         }
         cudaGraph_t g = nullptr;
         LKS_CUDA(cudaStreamEndCapture(b->cap, &g));
-        cudaError_t e = cudaGraphInstantiate(&gx, g, 0);
+        cudaError_t e = cudaGraphInstantiate(&gx, g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
         LKS_CUDA(e);
     }
@@ -1760,8 +1842,13 @@ int lks_batch_create(int count, const lks_params* params, lks_batch** out) {
             g_create_err = "instance " + std::to_string(i) + ": " + g_create_err;
         }
     }
+    int prio_low = 0, prio_high = 0;
+    if (rc == LKS_OK && cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+        g_create_err = "cudaDeviceGetStreamPriorityRange failed";
+        rc = LKS_ECUDA;
+    }
     if (rc == LKS_OK) {
-        if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        if (cudaStreamCreateWithPriority(&b->cap, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
             cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
             g_create_err = "stream/event creation failed";
             rc = LKS_ECUDA;

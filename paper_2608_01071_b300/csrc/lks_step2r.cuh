@@ -416,4 +416,178 @@ __global__ void __launch_bounds__(256) fwd2r2_kernel(Geom g, FwdArgs<T> a1, FwdA
     }
 }
 
+template <typename T>
+__host__ __device__ constexpr size_t smem2r2_adj() {
+    return sizeof(T) * 18 * Fused2::RR * 32;
+}
+
+// Two adjoint steps lambda_n -> lambda_{n-1} -> lambda_{n-2} in one launch (D2Q9), on the tile geometry of
+// fwd2r2_kernel (24 x 8 outputs, 32-lane rows with a halo of 4).  Step n is computed on the tile plus a halo of
+// 2 and kept in shared memory as the input of step n-1; lambda_{n-1} never goes to global memory.  Each step
+// records lambda_u and u on the footprint box for the tile's own nodes.  The arithmetic per step is that of
+// adj2r_kernel.  With two = 0 only step n is taken and its result written out (the last step of an odd run).
+template <typename T, int HW>
+__global__ void __launch_bounds__(256) adj2r2_kernel(Geom g, AdjArgs<T> a1, AdjArgs<T> a2, int two) {
+    using L = Lattice<2>;
+    constexpr int RR = Fused2::RR, TXO = Fused2::TXO;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* gq = reinterpret_cast<T*>(smem_raw);  // [9][RR][32] G_i = p-bar*/3 + c_i . u-bar*
+    T* mo = gq + 9 * RR * 32;                // [6][RR][32] M0, M1x, M1y, M2xx, M2yy, M2xy
+    T* sl = mo + 6 * RR * 32;                // [3][RR][32] lambda_{n-1} (step n results)
+
+    const int lane = threadIdx.x, t = threadIdx.y;
+    const int nx = g.n[0], ny = g.n[1];
+    const long long N = g.N;
+    const int x0 = blockIdx.x * TXO, y0 = blockIdx.y * Fused2::TY;
+    const int xo = x0 + lane - 4;
+    const int xl = wrap(xo, nx);
+    const T A = (T)g.A;
+    const bool lane_tile = lane >= 4 && lane < 28 && xo < nx;
+    pdl_wait_then_release();
+
+    // G_i of rows [h, RR-h), lanes [h, 32-h) from lambda (global for step n, shared memory for step n-1)
+    auto stage = [&](int h, const AdjArgs<T>& a, bool from_smem) {
+        const Pose& P = *a.pose;
+        const int bxl = box_coord(xl, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
+        if (lane < h || lane >= 32 - h) return;
+        for (int r = h + t; r < RR - h; r += 8) {
+            const int yw = wrap(y0 - 4 + r, ny);
+            const int c = r * 32 + lane;
+            T lp, ux, uy;
+            if (from_smem) {
+                lp = sl[c];
+                ux = sl[RR * 32 + c];
+                uy = sl[2 * RR * 32 + c];
+            } else {
+                const long long gi = (long long)yw * nx + xl;
+                lp = a.lam_in[gi];
+                ux = a.lam_in[N + gi];
+                uy = a.lam_in[2 * N + gi];
+            }
+            int xs[2] = {xl, yw};
+            T uw[2];
+            if (wall_node<T, 2>(g, xs, uw)) {
+                ux = 0;
+                uy = 0;
+            } else {
+                const int byl = box_coord(yw, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
+                if (bxl >= 0 && byl >= 0) {
+                    const int b[2] = {bxl, byl};
+                    T kap, C;
+                    map_node<T, 2, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
+                    const T inv = (T)1 / ((T)1 + kap);
+                    ux *= inv;
+                    uy *= inv;
+                }
+            }
+            const T p3 = lp * (T)(1.0 / 3.0);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                T v = p3;
+                if (L::c(q, 0) != 0) v += (T)L::c(q, 0) * ux;
+                if (L::c(q, 1) != 0) v += (T)L::c(q, 1) * uy;
+                gq[q * RR * 32 + c] = v;
+            }
+        }
+    };
+    // moments of rows [h, RR-h), lanes [h, 32-h)
+    auto moments = [&](int h) {
+        if (lane < h || lane >= 32 - h) return;
+        for (int m = h + t; m < RR - h; m += 8) {
+            const int c = m * 32 + lane;
+            T M0 = 0, M1x = 0, M1y = 0, Mxx = 0, Myy = 0, Mxy = 0;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const int cx = L::c(q, 0), cy = L::c(q, 1);
+                const T v = (T)L::w(q) * gq[q * RR * 32 + c + cx + 32 * cy];
+                M0 += v;
+                if (cx != 0) {
+                    M1x += (T)cx * v;
+                    Mxx += v;
+                }
+                if (cy != 0) {
+                    M1y += (T)cy * v;
+                    Myy += v;
+                }
+                if (cx * cy != 0) Mxy += (T)(cx * cy) * v;
+            }
+            mo[c] = M0;
+            mo[RR * 32 + c] = M1x;
+            mo[2 * RR * 32 + c] = M1y;
+            mo[3 * RR * 32 + c] = Mxx;
+            mo[4 * RR * 32 + c] = Myy;
+            mo[5 * RR * 32 + c] = Mxy;
+        }
+    };
+    // lambda_{n-1} of rows [h, RR-h), lanes [h, 32-h): to shared memory (to_smem) and, for the tile's own nodes,
+    // to global memory (!to_smem); footprint-box records of the tile's own nodes
+    auto outputs = [&](int h, const AdjArgs<T>& a, bool to_smem, bool lam_smem) {
+        const Pose& P = *a.pose;
+        const int bxc = box_coord(xl, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
+        const T* M0s = mo;
+        const T* M1xs = mo + RR * 32;
+        const T* M1ys = mo + 2 * RR * 32;
+        const T* Mxxs = mo + 3 * RR * 32;
+        const T* Myys = mo + 4 * RR * 32;
+        const T* Mxys = mo + 5 * RR * 32;
+        if (lane < h || lane >= 32 - h) return;
+        for (int o = h + t; o < RR - h; o += 8) {
+            const int yw = wrap(y0 - 4 + o, ny);
+            const int c = o * 32 + lane;
+            const long long go = (long long)yw * nx + xl;
+            const T u0 = a.u_prev[go], u1 = a.u_prev[N + go];
+            const T M0 = M0s[c], Mxx = Mxxs[c], Myy = Myys[c], Mxy = Mxys[c];
+            T vx = (T)3 * M1xs[c] - (T)3 * u0 * M0 + (T)9 * (Mxx * u0 + Mxy * u1) +
+                   A * ((Mxxs[c - 1] - Mxxs[c + 1]) + (Mxys[c - 32] - Mxys[c + 32]));
+            T vy = (T)3 * M1ys[c] - (T)3 * u1 * M0 + (T)9 * (Mxy * u0 + Myy * u1) +
+                   A * ((Mxys[c - 1] - Mxys[c + 1]) + (Myys[c - 32] - Myys[c + 32]));
+            int xg[2] = {xl, yw};
+            T uw[2];
+            const bool wall = wall_node<T, 2>(g, xg, uw);
+            if (a.src && !wall && in_probe<2>(g, xg)) {
+                vx += a.phi_dir[0];
+                vy += a.phi_dir[1];
+            }
+            const bool own = lane_tile && o >= 4 && o < RR - 4 && y0 - 4 + o < ny;
+            if (own) {
+                // records of this step: lambda_n (the step's input) and u_n
+                const int byc = box_coord(yw, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
+                if (bxc >= 0 && byc >= 0) {
+                    const long long bl = bxc + (long long)g.Fb[0] * byc;
+                    const T lx = lam_smem ? sl[RR * 32 + c] : a.lam_in[N + go];
+                    const T ly = lam_smem ? sl[2 * RR * 32 + c] : a.lam_in[2 * N + go];
+                    a.boxbuf[bl] = wall ? (T)0 : lx;
+                    a.boxbuf[g.Fbn + bl] = wall ? (T)0 : ly;
+                    a.boxbuf[2 * g.Fbn + bl] = a.u_cur[go];
+                    a.boxbuf[3 * g.Fbn + bl] = a.u_cur[N + go];
+                }
+            }
+            if (to_smem) {
+                // step n-1 reads sl only in its staging, which follows a barrier; the records above read the
+                // step's own input, so sl is overwritten only in step n
+                sl[c] = (T)3 * M0;
+                sl[RR * 32 + c] = vx;
+                sl[2 * RR * 32 + c] = vy;
+            } else if (own) {
+                a.lam_out[go] = (T)3 * M0;
+                a.lam_out[N + go] = vx;
+                a.lam_out[2 * N + go] = vy;
+            }
+        }
+    };
+    stage(0, a1, false);
+    __syncthreads();
+    moments(1);
+    __syncthreads();
+    outputs(2, a1, two != 0, false);
+    if (two) {
+        __syncthreads();
+        stage(2, a2, true);
+        __syncthreads();
+        moments(3);
+        __syncthreads();
+        outputs(4, a2, false, true);
+    }
+}
+
 }  // namespace lks

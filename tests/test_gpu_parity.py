@@ -153,12 +153,22 @@ def test_graph_replay_matches_eager(ckpt):
 @pytest.mark.parametrize("nt", [60, 61])
 def test_d2q9_kernel_variants(rows, prec, nt):
     # every D2Q9 step-kernel family and rows-per-warp choice the tile autotuner may pick; odd and even horizons
-    # (the two-step forward ends on a single step when Nt is odd)
+    # (the two-step forward and adjoint end on a single step when a run or segment has odd length)
     tol = (1e-10, 1e-10, 1e-10) if prec == "fp64" else (1e-5, 1e-4, 1e-3)
     shape = (94, 45) if rows >= 32 else (93, 45)  # the vectorised kernels need an even x extent
     w = tiny_workload("D2Q9", precision=prec, tile_rows=rows, shape=shape, ckpt="sqrt", Nt=nt)
     g, _ = check(w, *tol)
-    assert g["stats"]["tile_rows_fwd"] == rows and g["stats"]["tile_rows_adj"] == (1 if rows == 3 else rows)
+    assert g["stats"]["tile_rows_fwd"] == rows and g["stats"]["tile_rows_adj"] == rows
+
+
+@pytest.mark.parametrize("fwd,adj", [(3, 1), (1, 3), (32, 3), (3, 4)])
+@pytest.mark.parametrize("ckpt", ["full", "revolve"])
+def test_d2q9_mixed_variants(fwd, adj, ckpt):
+    # forward and adjoint variants chosen independently; two-step adjoint launches across segment boundaries
+    w = tiny_workload("D2Q9", precision="fp64", tile_rows=fwd, tile_rows_adj=adj, shape=(94, 45), ckpt=ckpt,
+                      ckpt_slots=5 if ckpt == "revolve" else 0, Nt=47)
+    g, _ = check(w, 1e-10, 1e-10, 1e-10)
+    assert g["stats"]["tile_rows_fwd"] == fwd and g["stats"]["tile_rows_adj"] == adj
 
 
 def test_3d_128x64x64_full_grid_revolve_fp32():
@@ -177,10 +187,23 @@ def test_3d_256x128x128_full_grid_budget_fp32():
 
 
 @pytest.mark.parametrize("rows,prec,kernel", [(1, "fp64", "linear"), (8, "fp64", "linear"), (16, "fp64", "cosine"),
-                                              (8, "fp32", "linear"), (16, "fp32", "linear"), (8, "fp32", "cosine")])
+                                              (8, "fp32", "linear"), (16, "fp32", "linear"), (8, "fp32", "cosine"),
+                                              (32, "fp64", "linear"), (64, "fp64", "cosine"), (96, "fp64", "linear"),
+                                              (32, "fp32", "linear"), (64, "fp32", "linear"), (96, "fp32", "cosine")])
 def test_d3q15_kernel_variants(rows, prec, kernel):
     # every D3Q15 step-kernel family and planes-per-block choice, on a grid with ragged x, y and z tails
+    # (32, 64: the separable kernels with 16 or 32 planes per block; 96: the separable forward on 32 x 16 columns,
+    # paired with the 8-plane adjoint)
     tol = (1e-10, 1e-10, 1e-10) if prec == "fp64" else (1e-5, 1e-4, 1e-3)
     w = tiny_workload("D3Q15", precision=prec, tile_rows=rows, kernel=kernel, shape=(41, 21, 19), ckpt="sqrt")
     g, _ = check(w, *tol)
-    assert g["stats"]["tile_rows_fwd"] == rows and g["stats"]["tile_rows_adj"] == rows
+    assert g["stats"]["tile_rows_fwd"] == rows and g["stats"]["tile_rows_adj"] == (8 if rows == 96 else rows)
+
+
+@pytest.mark.parametrize("rows", [32, 64, 96])
+def test_d3q15_separable_forward_thin_grid(rows):
+    # fewer z planes than one block holds (the periodic wrap of the plane ring runs several times), x and y
+    # extents below one tile; forward and adjoint
+    w = tiny_workload("D3Q15", precision="fp64", tile_rows=rows, shape=(30, 13, 7), design=(6, 6, 4), ckpt="full",
+                      probe_lo=(20, 3, 2), probe_hi=(26, 9, 5), Nt=16)
+    check(w, 1e-10, 1e-10, 1e-10)
