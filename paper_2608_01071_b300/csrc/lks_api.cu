@@ -94,14 +94,18 @@ struct Engine {
     virtual bool fused2() const { return false; }
     virtual void fwd2(const Geom& g, const void* in, void* out1, void* out2, const void* kref, const Pose* pose1,
                       double* jslot1, double* jslot2, unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) {}
+    // fac: 1 / (1 + kappa) of the step on the footprint box (box_fac), or nullptr to evaluate the mapping
     virtual void adj(const Geom& g, const void* lam_in, void* lam_out, const void* prev, const void* cur,
-                     const void* kref, const Pose* pose, void* boxbuf, int src, cudaStream_t s) = 0;
+                     const void* kref, const Pose* pose, void* boxbuf, const void* fac, int src, cudaStream_t s) = 0;
     // two-step adjoint launches: steps n (pose, boxbuf1, src1; states prev1 = n-1, cur1 = n) and n-1 (pose - 1,
     // boxbuf2, src2; states prev2 = n-2, prev1) in one kernel
     virtual bool fused_adj2() const { return false; }
     virtual void adj2(const Geom& g, const void* lam_in, void* lam_out, const void* prev1, const void* cur1,
-                      const void* prev2, const void* kref, const Pose* pose, void* boxbuf1, int src1, void* boxbuf2,
-                      int src2, cudaStream_t s) {}
+                      const void* prev2, const void* kref, const Pose* pose, void* boxbuf1, const void* fac1, int src1,
+                      void* boxbuf2, const void* fac2, int src2, cudaStream_t s) {}
+    // 1 / (1 + kappa) on the footprint box for steps n_first .. n_first + nsteps - 1 (stride Fbn per step)
+    virtual void box_fac(const Geom& g, const Pose* poses, const void* kref, int n_first, int nsteps, void* out,
+                         cudaStream_t s) = 0;
     virtual void sens(const Geom& g, const Pose* poses, const void* kref, const void* boxbuf, long long bstride,
                       int n_first, int nsteps, void* kbar, double* mslot, cudaStream_t s) = 0;
     virtual void gather(const Geom& g, const Pose* poses, const void* kbar, int n_first, int nsteps,
@@ -134,7 +138,7 @@ FwdArgs<T> make_fwd_args(const Geom& g, const void* in, void* out, const void* k
 
 template <typename T>
 AdjArgs<T> make_adj_args(const Geom& g, const void* lam_in, void* lam_out, const void* prev, const void* cur,
-                         const void* kref, const Pose* pose, void* boxbuf, int src) {
+                         const void* kref, const Pose* pose, void* boxbuf, const void* fac, int src) {
     AdjArgs<T> a;
     a.lam_in = (const T*)lam_in;
     a.lam_out = (T*)lam_out;
@@ -143,6 +147,7 @@ AdjArgs<T> make_adj_args(const Geom& g, const void* lam_in, void* lam_out, const
     a.kref = (const T*)kref;
     a.pose = pose;
     a.boxbuf = (T*)boxbuf;
+    a.fac = (const T*)fac;
     a.src = src;
     for (int i = 0; i < 3; ++i) a.phi_dir[i] = (T)(g.dir[i] * g.phi);
     return a;
@@ -151,6 +156,12 @@ AdjArgs<T> make_adj_args(const Geom& g, const void* lam_in, void* lam_out, const
 // Shared pieces of both engines.
 template <typename T, int D, int HW>
 struct EngineCommon : Engine {
+    void box_fac(const Geom& g, const Pose* poses, const void* kref, int n_first, int nsteps, void* out,
+                 cudaStream_t s) override {
+        box_fac_kernel<T, D, HW><<<dim3(nblk(g.Fbn, 256), nsteps, 1), 256, 0, s>>>(g, poses, (const T*)kref, n_first,
+                                                                                 (T*)out);
+        LKS_LAUNCHED();
+    }
     void sens(const Geom& g, const Pose* poses, const void* kref, const void* boxbuf, long long bstride, int n_first,
               int nsteps, void* kbar, double* mslot, cudaStream_t s) override {
         const dim3 grid(nblk(g.Fbn, 256), nsteps, 1);
@@ -259,8 +270,8 @@ struct Engine3D : EngineCommon<T, 3, HW> {
             launch_pdl(fwd3s_kernel<T, HW, 16, 16>, this->fgrid, this->fthreads, smem3s_fwd<T, 16>(), s, this->pdl, g, a);
     }
     void adj(const Geom& g, const void* lam_in, void* lam_out, const void* prev, const void* cur, const void* kref,
-             const Pose* pose, void* boxbuf, int src, cudaStream_t s) override {
-        auto a = make_adj_args<T>(g, lam_in, lam_out, prev, cur, kref, pose, boxbuf, src);
+             const Pose* pose, void* boxbuf, const void* fac, int src, cudaStream_t s) override {
+        auto a = make_adj_args<T>(g, lam_in, lam_out, prev, cur, kref, pose, boxbuf, fac, src);
         if (this->rows_a == 1)
             launch_pdl(adj_step_kernel<T, 3, HW, TX, TY, TZ>, this->agrid, this->athreads, smem_adj, s, this->pdl, g, a);
         else if (this->rows_a == 8)
@@ -333,8 +344,8 @@ struct Engine2D : EngineCommon<T, 2, HW> {
     bool fused2() const override { return this->rows_f == 3; }
     bool fused_adj2() const override { return this->rows_a == 3; }
     void adj2(const Geom& g, const void* lam_in, void* lam_out, const void* prev1, const void* cur1, const void* prev2,
-              const void* kref, const Pose* pose, void* boxbuf1, int src1, void* boxbuf2, int src2,
-              cudaStream_t s) override;
+              const void* kref, const Pose* pose, void* boxbuf1, const void* fac1, int src1, void* boxbuf2,
+              const void* fac2, int src2, cudaStream_t s) override;
     void fwd2(const Geom& g, const void* in, void* out1, void* out2, const void* kref, const Pose* pose1,
               double* jslot1, double* jslot2, unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) override {
         auto a1 = make_fwd_args<T>(g, in, out1, kref, pose1, jslot1, flag, jlo, jn);
@@ -363,8 +374,8 @@ struct Engine2D : EngineCommon<T, 2, HW> {
         }
     }
     void adj(const Geom& g, const void* lam_in, void* lam_out, const void* prev, const void* cur, const void* kref,
-             const Pose* pose, void* boxbuf, int src, cudaStream_t s) override {
-        auto a = make_adj_args<T>(g, lam_in, lam_out, prev, cur, kref, pose, boxbuf, src);
+             const Pose* pose, void* boxbuf, const void* fac, int src, cudaStream_t s) override {
+        auto a = make_adj_args<T>(g, lam_in, lam_out, prev, cur, kref, pose, boxbuf, fac, src);
         switch (this->rows_a) {
             case 3:
                 launch_pdl(adj2r2_kernel<T, HW>, this->agrid, this->athreads, smem2r2_adj<T>(), s, this->pdl, g, a, a, 0);
@@ -382,10 +393,10 @@ struct Engine2D : EngineCommon<T, 2, HW> {
 
 template <typename T, int HW>
 void Engine2D<T, HW>::adj2(const Geom& g, const void* lam_in, void* lam_out, const void* prev1, const void* cur1,
-                           const void* prev2, const void* kref, const Pose* pose, void* boxbuf1, int src1,
-                           void* boxbuf2, int src2, cudaStream_t s) {
-    auto a1 = make_adj_args<T>(g, lam_in, lam_out, prev1, cur1, kref, pose, boxbuf1, src1);
-    auto a2 = make_adj_args<T>(g, lam_in, lam_out, prev2, prev1, kref, pose - 1, boxbuf2, src2);
+                           const void* prev2, const void* kref, const Pose* pose, void* boxbuf1, const void* fac1,
+                           int src1, void* boxbuf2, const void* fac2, int src2, cudaStream_t s) {
+    auto a1 = make_adj_args<T>(g, lam_in, lam_out, prev1, cur1, kref, pose, boxbuf1, fac1, src1);
+    auto a2 = make_adj_args<T>(g, lam_in, lam_out, prev2, prev1, kref, pose - 1, boxbuf2, fac2, src2);
     launch_pdl(adj2r2_kernel<T, HW>, this->agrid, this->athreads, smem2r2_adj<T>(), s, this->pdl, g, a1, a2, 1);
 }
 
@@ -456,6 +467,7 @@ struct lks_ctx {
     double* d_mslot = nullptr;
     void* d_boxbuf = nullptr;   // two buffers of Lmax steps x 2D planes x Fbn (lam_u, u_n on the footprint box)
     long long box_step = 0;     // elements per step in d_boxbuf
+    void* d_fac = nullptr;      // two buffers of Lmax steps x Fbn: 1 / (1 + kappa) on the footprint box
     int nsb = 0;                // sensitivity blocks per step
     size_t state_bytes = 0;
     std::vector<void*> slot;  // checkpoint slots
@@ -739,10 +751,10 @@ void autotune_rows(lks_ctx* c) {
                 c->eng->fwd(c->g, c->slot[0], c->pp[k & 1], c->d_kref, c->d_pose, nullptr, c->d_flag, jlo, jn, s);
             else if (c->eng->fused_adj2())
                 c->eng->adj2(c->g, c->lam[k & 1], c->lam[(k + 1) & 1], c->slot[0], c->slot[0], c->slot[0], c->d_kref,
-                             c->d_pose + 1, c->d_boxbuf, 1, c->d_boxbuf, 1, s);
+                             c->d_pose + 1, c->d_boxbuf, c->d_fac, 1, c->d_boxbuf, c->d_fac, 1, s);
             else
                 c->eng->adj(c->g, c->lam[k & 1], c->lam[(k + 1) & 1], c->slot[0], c->slot[0], c->d_kref, c->d_pose,
-                            c->d_boxbuf, 1, s);
+                            c->d_boxbuf, c->d_fac, 1, s);
         }
         LKS_CUDA(cudaEventRecord(e1, s));
         LKS_CUDA(cudaEventSynchronize(e1));
@@ -816,6 +828,8 @@ void allocate(lks_ctx* c) {
     c->d_mslot = (double*)dalloc(c, (size_t)c->Lmax * c->nsb * 2 * D * 8);
     c->box_step = 2LL * D * c->g.Fbn;
     c->d_boxbuf = dalloc(c, (size_t)2 * c->Lmax * c->box_step * ts);
+    c->d_fac = dalloc(c, (size_t)2 * c->Lmax * c->g.Fbn * ts);
+    LKS_CUDA(cudaMemset(c->d_fac, 0, (size_t)2 * c->Lmax * c->g.Fbn * ts));
 
     const size_t sb = c->state_bytes;
     c->slot.resize(c->slot_used.size());
@@ -1159,17 +1173,23 @@ void recompute_segment(lks_ctx* c, int a, int b, const void* start, const void* 
 void adjoint_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
     const std::vector<const void*>& st = c->seg_st[buf];
     cudaEvent_t ea = span_begin(c, s);
+    // 1 / (1 + kappa) on the footprint box for every step of the segment, in one launch
+    c->eng->box_fac(c->g, c->d_pose, c->d_kref, a + 1, b - a,
+                    c->tptr(c->d_fac, (long long)buf * c->Lmax * c->g.Fbn), s);
+    c->launches++;
     for (int n = b; n > a;) {
         const int j = n - a - 1;  // box-buffer slot of step n
         void* bb = c->tptr(c->d_boxbuf, ((long long)buf * c->Lmax + j) * c->box_step);
+        const void* fc = c->tptr(c->d_fac, ((long long)buf * c->Lmax + j) * c->g.Fbn);
         if (c->eng->fused_adj2() && n - 1 > a) {  // steps n and n-1 in one launch
             void* bb2 = c->tptr(c->d_boxbuf, ((long long)buf * c->Lmax + j - 1) * c->box_step);
+            const void* fc2 = c->tptr(c->d_fac, ((long long)buf * c->Lmax + j - 1) * c->g.Fbn);
             c->eng->adj2(c->g, c->lam[0], c->lam[1], st[n - 1 - a], st[n - a], st[n - 2 - a], c->d_kref,
-                         c->d_pose + n, bb, n - 1 >= 1 ? 1 : 0, bb2, n - 2 >= 1 ? 1 : 0, s);
+                         c->d_pose + n, bb, fc, n - 1 >= 1 ? 1 : 0, bb2, fc2, n - 2 >= 1 ? 1 : 0, s);
             c->stats.adjoint_steps += 2;
             n -= 2;
         } else {
-            c->eng->adj(c->g, c->lam[0], c->lam[1], st[n - 1 - a], st[n - a], c->d_kref, c->d_pose + n, bb,
+            c->eng->adj(c->g, c->lam[0], c->lam[1], st[n - 1 - a], st[n - a], c->d_kref, c->d_pose + n, bb, fc,
                         n - 1 >= 1 ? 1 : 0, s);
             c->stats.adjoint_steps++;
             n -= 1;

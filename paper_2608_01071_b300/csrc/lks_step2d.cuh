@@ -204,11 +204,7 @@ __global__ void __launch_bounds__(32 * WY) adj2d_kernel(Geom g, AdjArgs<T> a) {
                 int b[2];
                 b[0] = box_coord(xl, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
                 b[1] = box_coord(yw, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
-                if (b[0] >= 0 && b[1] >= 0) {
-                    T kap, C;
-                    map_node<T, 2, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
-                    fac[it] = (T)1 / ((T)1 + kap);
-                }
+                if (b[0] >= 0 && b[1] >= 0) fac[it] = adj_inv<T, 2, HW>(g, P, a.kref, a.fac, b);
             }
             yw = (yw + 1 == ny) ? 0 : yw + 1;
         }

@@ -179,9 +179,7 @@ __global__ void __launch_bounds__(256) adj2r_kernel(Geom g, AdjArgs<T> a) {
             const int byl = box_coord(yw, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
             if (bxl >= 0 && byl >= 0) {
                 const int b[2] = {bxl, byl};
-                T kap, C;
-                map_node<T, 2, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
-                const T inv = (T)1 / ((T)1 + kap);
+                const T inv = adj_inv<T, 2, HW>(g, P, a.kref, a.fac, b);
                 ux *= inv;
                 uy *= inv;
             }
@@ -473,9 +471,7 @@ __global__ void __launch_bounds__(256) adj2r2_kernel(Geom g, AdjArgs<T> a1, AdjA
                 const int byl = box_coord(yw, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
                 if (bxl >= 0 && byl >= 0) {
                     const int b[2] = {bxl, byl};
-                    T kap, C;
-                    map_node<T, 2, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
-                    const T inv = (T)1 / ((T)1 + kap);
+                    const T inv = adj_inv<T, 2, HW>(g, P, a.kref, a.fac, b);
                     ux *= inv;
                     uy *= inv;
                 }

@@ -228,9 +228,7 @@ __global__ void __launch_bounds__(128, 5) adj2v_kernel(Geom g, AdjArgs<T> a) {
         const int by = box_coord(yw, P.xs[1], g.Fb[1], ny, g.periodic[1]);
         if (bx < 0 || by < 0) return (T)1;
         const int b[2] = {bx, by};
-        T kap, C;
-        map_node<T, 2, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
-        return (T)1 / ((T)1 + kap);
+        return adj_inv<T, 2, HW>(g, P, a.kref, a.fac, b);
     };
     V pA, xA, yA, pB, xB, yB;
     load(y0 - 2, pA, xA, yA);

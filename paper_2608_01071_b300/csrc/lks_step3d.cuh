@@ -271,9 +271,7 @@ __global__ void __launch_bounds__(Reg3::NT) adj3d_kernel(Geom g, AdjArgs<T> a) {
                     fac = 0;
                 } else if (ebx[e] >= 0 && eby[e] >= 0 && bz >= 0) {
                     const int b[3] = {ebx[e], eby[e], bz};
-                    T kap, C;
-                    map_node<T, 3, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
-                    fac = (T)1 / ((T)1 + kap);
+                    fac = adj_inv<T, 3, HW>(g, P, a.kref, a.fac, b);
                 }
                 dst[l] = pre[e][0];
 #pragma unroll

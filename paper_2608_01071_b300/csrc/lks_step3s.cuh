@@ -350,7 +350,7 @@ __host__ __device__ constexpr size_t smem3s_adj() {
 }
 
 template <typename T, int HW, int ZB, int TY>
-__global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 2 : 1) adj3s_kernel(Geom g, AdjArgs<T> a) {
+__global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 3 : 1) adj3s_kernel(Geom g, AdjArgs<T> a) {
     using R = Sep3<TY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* raw = reinterpret_cast<T*>(smem_raw);  // [2 slots][p-bar*/3, u-bar*_x, u-bar*_y, u-bar*_z][NS]
@@ -426,9 +426,7 @@ __global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 2 : 1) adj3s_kernel(Ge
                     fac = 0;
                 } else if (ebx[e] >= 0 && eby[e] >= 0 && bz >= 0) {
                     const int b[3] = {ebx[e], eby[e], bz};
-                    T kap, C;
-                    map_node<T, 3, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
-                    fac = (T)1 / ((T)1 + kap);
+                    fac = adj_inv<T, 3, HW>(g, P, a.kref, a.fac, b);
                 }
                 dst[l] = pre[e][0] * (T)(1.0 / 3.0);
 #pragma unroll

@@ -48,6 +48,7 @@ struct AdjArgs {
     const T* kref;
     const Pose* pose;   // pose of step n
     T* boxbuf;          // footprint-box record of step n: lam_u (D planes, 0 on walls) then u_n (D planes)
+    const T* fac;       // 1 / (1 + kappa) of step n on the footprint box (box_fac_kernel), or nullptr
     int src;            // 1: add the objective source phi (n - 1 >= 1)
     T phi_dir[3];       // objective source weight n_a / (Nt |O|) in T
 };
@@ -189,6 +190,42 @@ __device__ __forceinline__ void map_node(const Geom& g, const Pose& P, const T* 
             }
         }
     }
+}
+
+// 1 / (1 + kappa) at footprint-box coordinates b for the adjoint's u-bar* = lam_u / (1 + kappa): read from the
+// step's precomputed box field when there is one, else evaluated here.
+template <typename T, int D, int HW>
+__device__ __forceinline__ T adj_inv(const Geom& g, const Pose& P, const T* __restrict__ kref, const T* __restrict__ fac,
+                                     const int* b) {
+    if (fac != nullptr) {
+        long long bl = b[D - 1];
+#pragma unroll
+        for (int c = D - 2; c >= 0; --c) bl = bl * g.Fb[c] + b[c];
+        return fac[bl];
+    }
+    T kap, C;
+    map_node<T, D, HW, false>(g, P, kref, b, kap, C, nullptr, nullptr);
+    return (T)1 / ((T)1 + kap);
+}
+
+// 1 / (1 + kappa) over the footprint box for steps n_first .. n_first + nsteps - 1 (one box field per step,
+// stride Fbn): the adjoint steps of a segment read it instead of evaluating the mapping at every staged node.
+template <typename T, int D, int HW>
+__global__ void __launch_bounds__(256) box_fac_kernel(Geom g, const Pose* __restrict__ poses,
+                                                      const T* __restrict__ kref, int n_first, T* __restrict__ fac) {
+    const long long bl = blockIdx.x * 256LL + threadIdx.x;
+    if (bl >= g.Fbn) return;
+    const int j = blockIdx.y;
+    int b[D];
+    long long r = bl;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        b[c] = (int)(r % g.Fb[c]);
+        r /= g.Fb[c];
+    }
+    T kap, C;
+    map_node<T, D, HW, false>(g, poses[n_first + j], kref, b, kap, C, nullptr, nullptr);
+    fac[j * g.Fbn + bl] = (T)1 / ((T)1 + kap);
 }
 
 // Wall test of a node; on a wall node writes the imposed velocity (later axes win where planes meet).
@@ -412,9 +449,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) adj_step_kernel(Geom g, AdjArgs<
                 b[c] = box_coord(xg[c], P.xs[c], g.Fb[c], g.n[c], g.periodic[c]);
                 inbox = inbox && b[c] >= 0;
             }
-            T kap = 0, C = 0;
-            if (inbox) map_node<T, D, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
-            const T inv = (T)1 / ((T)1 + kap);
+            const T inv = inbox ? adj_inv<T, D, HW>(g, P, a.kref, a.fac, b) : (T)1;
 #pragma unroll
             for (int c = 0; c < D; ++c) su[c * S + l] = a.lam_in[(1 + c) * N + gi] * inv;
         }
