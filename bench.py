@@ -319,7 +319,14 @@ def run_ours(args):
     fwd_sweep_ms = sum(a for a, _ in st_fwd) / max(1, sum(n for _, n in st_fwd))
     k_fwd["us_per_step_forward_sweep"], k_fwd["us_per_step_recompute"] = fwd_sweep_ms * 1e3, rec_ms * 1e3
     roof, other = (k_fwd, k_adj) if t_fwd >= t_adj else (k_adj, k_fwd)
-    roof = dict(roof, other_kernel=other)
+    # the whole path: algorithmic bytes of every forward, recompute and adjoint step over the device time
+    n_f = sum(n for _, n in st_fwd) + sum(n for _, n in st_rec)
+    path_bytes = n_f * fwd_bytes + sum(n for _, n in st_adj) * adj_bytes
+    path_gbs = path_bytes / t_dev / 1e9
+    roof = dict(roof, other_kernel=other,
+                path={"achieved": path_gbs, "frac": path_gbs / peak, "unit": "GB/s",
+                      "bytes_per_step": path_bytes / args.steps,
+                      "note": "algorithmic bytes of all step kernels (forward, recompute, adjoint) / device time"})
     state_mb = N * (D + 1) * s / 2**20
     # a step reads one state and writes another
     l2_note = (f"512 MB buffer written between timed steps; a step touches two {state_mb:.1f} MB states, "

@@ -366,9 +366,10 @@ __global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 3 : 1) adj3s_kernel(Ge
     const int xs2 = P.xs[2];
 
     // raw elements of this thread (halo-2 region): plane-invariant offsets, wall and footprint coordinates
+    // (einner: the element is one of the block's own columns, whose footprint records it writes)
     long long off[R::PER];
     int ebx[R::PER], eby[R::PER];
-    bool ewall[R::PER];
+    bool ewall[R::PER], einner[R::PER];
 #pragma unroll
     for (int e = 0; e < R::PER; ++e) {
         const int l = tid + e * R::NT;
@@ -378,6 +379,8 @@ __global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 3 : 1) adj3s_kernel(Ge
         ebx[e] = box_coord(ex, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
         eby[e] = box_coord(ey, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
         ewall[e] = (!g.periodic[0] && (ex == 0 || ex == nx - 1)) || (!g.periodic[1] && (ey == 0 || ey == ny - 1));
+        einner[e] = l < R::NS && i >= 2 && i < R::TX + 2 && j >= 2 && j < TY + 2 && x0 - 2 + i < nx && y0 - 2 + j < ny &&
+                    ebx[e] >= 0 && eby[e] >= 0;
     }
     // field nodes: 0 = own column, 1 = a node of the halo-1 ring (tid < NR)
     const bool has1 = tid < R::NR;
@@ -401,36 +404,45 @@ __global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 3 : 1) adj3s_kernel(Ge
     const bool probe_xy = xg >= g.probe_lo[0] && xg < g.probe_hi[0] && yg >= g.probe_lo[1] && yg < g.probe_hi[1];
     pdl_wait_then_release();
 
-    T pre[R::PER][4];
+    // lambda of a plane and, on the footprint box, its 1 / (1 + kappa), one plane ahead of use (this kernel
+    // requires the box field a.fac)
+    T pre[R::PER][4], pfac[R::PER];
     auto fetch = [&](int k) {
-        const long long base = plane * wrap(k, nz);
+        const int kz = wrap(k, nz);
+        const long long base = plane * kz;
+        const int bz = box_coord(kz, xs2, g.Fb[2], g.n[2], g.periodic[2]);
 #pragma unroll
         for (int e = 0; e < R::PER; ++e) {
             if (tid + e * R::NT < R::NS) {
 #pragma unroll
                 for (int f = 0; f < 4; ++f) pre[e][f] = a.lam_in[f * N + base + off[e]];
+                pfac[e] = 1;
+                if (ebx[e] >= 0 && eby[e] >= 0 && bz >= 0)
+                    pfac[e] = a.fac[ebx[e] + (long long)g.Fb[0] * (eby[e] + (long long)g.Fb[1] * bz)];
             }
         }
     };
-    // p-bar*/3 = lam_p / 3; u-bar* = lam_u / (1 + kappa), 0 on walls
+    // p-bar*/3 = lam_p / 3; u-bar* = lam_u / (1 + kappa), 0 on walls.  The lambda_u footprint records of the
+    // block's own nodes are written here, from the raw lambda in registers.
     auto store = [&](int k, T* dst) {
         const int kz = wrap(k, nz);
         const bool wz = !g.periodic[2] && (kz == 0 || kz == nz - 1);
+        const bool own_plane = k >= z0 && k < z0 + ZB && k < nz;
         const int bz = box_coord(kz, xs2, g.Fb[2], g.n[2], g.periodic[2]);
 #pragma unroll
         for (int e = 0; e < R::PER; ++e) {
             const int l = tid + e * R::NT;
             if (l < R::NS) {
-                T fac = 1;
-                if (ewall[e] || wz) {
-                    fac = 0;
-                } else if (ebx[e] >= 0 && eby[e] >= 0 && bz >= 0) {
-                    const int b[3] = {ebx[e], eby[e], bz};
-                    fac = adj_inv<T, 3, HW>(g, P, a.kref, a.fac, b);
-                }
+                const bool wall = ewall[e] || wz;
+                const T fac = wall ? (T)0 : pfac[e];
                 dst[l] = pre[e][0] * (T)(1.0 / 3.0);
 #pragma unroll
                 for (int f = 1; f < 4; ++f) dst[f * R::NS + l] = pre[e][f] * fac;
+                if (einner[e] && own_plane && bz >= 0) {
+                    const long long bl = ebx[e] + (long long)g.Fb[0] * (eby[e] + (long long)g.Fb[1] * bz);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) a.boxbuf[c * g.Fbn + bl] = wall ? (T)0 : pre[e][1 + c];
+                }
             }
         }
     };
@@ -451,6 +463,7 @@ __global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 3 : 1) adj3s_kernel(Ge
         for (int q = 0; q < 10; ++q) accC[s][q] = accN[s][q] = 0;
     T m0o = 0, m1o[3] = {0, 0, 0};  // own M0, M1 of the last completed plane
     T up0[3] = {0, 0, 0};           // u_{n-1} of the next output plane (prefetched)
+    T uc0[3] = {0, 0, 0};           // u_n of the next output plane on the footprint box (prefetched)
     int mslot = 0;                  // M2 ring slot of plane k - 1
 
 #pragma unroll 1
@@ -573,17 +586,18 @@ __global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 3 : 1) adj3s_kernel(Ge
             if (bz >= 0) {
                 const long long bl = bx + (long long)g.Fb[0] * (by + (long long)g.Fb[1] * bz);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    a.boxbuf[c * g.Fbn + bl] = wall ? (T)0 : a.lam_in[(1 + c) * N + gi];
-                    a.boxbuf[(3 + c) * g.Fbn + bl] = a.u_cur[c * N + gi];
-                }
+                for (int c = 0; c < 3; ++c) a.boxbuf[(3 + c) * g.Fbn + bl] = uc0[c];
             }
         }
-        // prefetch u_{n-1} of the next output plane
+        // prefetch u_{n-1} (and u_n on the footprint box) of the next output plane
         if (col && zo + 1 >= z0 && zo + 1 < z0 + ZB && zo + 1 < nz) {
             const long long gn = gcol + plane * (zo + 1);
 #pragma unroll
             for (int c = 0; c < 3; ++c) up0[c] = a.u_prev[c * N + gn];
+            if (colbox && box_coord(zo + 1, xs2, g.Fb[2], g.n[2], g.periodic[2]) >= 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) uc0[c] = a.u_cur[c * N + gn];
+            }
         }
         T* t = sk;
         sk = sn;
