@@ -468,6 +468,7 @@ struct lks_ctx {
     void* d_boxbuf = nullptr;   // two buffers of Lmax steps x 2D planes x Fbn (lam_u, u_n on the footprint box)
     long long box_step = 0;     // elements per step in d_boxbuf
     void* d_fac = nullptr;      // two buffers of Lmax steps x Fbn: 1 / (1 + kappa) on the footprint box
+    bool throughput = false;    // instance of a batch: tune for throughput (see create_ctx)
     int nsb = 0;                // sensitivity blocks per step
     size_t state_bytes = 0;
     std::vector<void*> slot;  // checkpoint slots
@@ -717,7 +718,8 @@ void autotune_rows(lks_ctx* c) {
     static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> cache;
     int dev = 0;
     LKS_CUDA(cudaGetDevice(&dev));
-    const auto key = std::make_tuple(dev, (int)c->tsize, c->hw * 16 + c->D, c->g.n[0], c->g.n[1] * 65536 + c->g.n[2]);
+    const auto key = std::make_tuple(dev, (int)c->tsize * 2 + (c->throughput ? 1 : 0), c->hw * 16 + c->D, c->g.n[0],
+                                     c->g.n[1] * 65536 + c->g.n[2]);
     {
         std::lock_guard<std::mutex> lock(mu);
         auto it = cache.find(key);
@@ -765,6 +767,7 @@ void autotune_rows(lks_ctx* c) {
     };
     for (int pass = 0; pass < 2; ++pass) {
         for (int r : (pass == 0 ? cf : ca)) {
+            if (c->throughput && c->D == 2 && r == 3) continue;  // two steps per launch: latency, not throughput
             // not available for this grid / precision
             if (!(pass == 0 ? c->eng->set_rows(r, ra0, c->g) : c->eng->set_rows(rf0, r, c->g))) continue;
             // size each measurement to about 1.5 ms of launches and keep the fastest of three
@@ -853,9 +856,11 @@ void allocate(lks_ctx* c) {
     LKS_CUDA(cudaHostAlloc((void**)&c->h_flag, 16, cudaHostAllocDefault));
     *c->h_flag = 0;
     // the reverse sweep's critical path (the adjoint chain on the capture stream) gets the highest priority; the
-    // recomputation and the sensitivity passes running beside it have slack and get the lowest
+    // recomputation and the sensitivity passes running beside it have slack and get the lowest.  Instances of a
+    // batch share the GPU with each other, so there all streams keep the default priority.
     int prio_low = 0, prio_high = 0;
     LKS_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+    if (c->throughput) prio_low = prio_high = 0;
     LKS_CUDA(cudaStreamCreateWithPriority(&c->cap, cudaStreamNonBlocking, prio_high));
     LKS_CUDA(cudaStreamCreateWithPriority(&c->cap2, cudaStreamNonBlocking, prio_low));
     LKS_CUDA(cudaStreamCreateWithPriority(&c->cap3, cudaStreamNonBlocking, prio_low));
@@ -1470,13 +1475,17 @@ const char* lks_last_error_string(const lks_ctx* ctx) {
     return ctx->err.c_str();
 }
 
-int lks_create(const lks_params* p, lks_ctx** out) {
+// A context; `throughput` (instances of a batch, which run concurrently) keeps the autotuner to variants that
+// take one step per launch: the two-step variants shorten a lone instance's critical path by recomputing a
+// halo, which costs throughput once many instances fill the GPU.
+static int create_ctx(const lks_params* p, bool throughput, lks_ctx** out) {
     if (!out) return LKS_EINVAL;
     lks_ctx* c = nullptr;
     try {
         validate(p);
         c = new lks_ctx();
         c->prm = *p;
+        c->throughput = throughput;
         std::memset(&c->stats, 0, sizeof(c->stats));
         setup_geometry(c);
         int ndev = 0;
@@ -1506,6 +1515,8 @@ int lks_create(const lks_params* p, lks_ctx** out) {
         return LKS_ENOMEM;
     }
 }
+
+int lks_create(const lks_params* p, lks_ctx** out) { return create_ctx(p, false, out); }
 
 void lks_destroy(lks_ctx* ctx) {
     if (!ctx) return;
@@ -1854,7 +1865,7 @@ int lks_batch_create(int count, const lks_params* params, lks_batch** out) {
             break;
         }
         lks_ctx* c = nullptr;
-        rc = lks_create(&params[i], &c);
+        rc = create_ctx(&params[i], true, &c);
         if (rc == LKS_OK) {
             c->use_graphs = false;  // the batch owns the graphs
             b->ctx.push_back(c);

@@ -26,6 +26,14 @@ def test_exports_every_declared_symbol():
         assert n in _abi.PROTOTYPES, n
 
 
+def test_exports_nothing_undeclared():
+    # the library's dynamic symbol table holds the declared C ABI and nothing else of its own
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", _abi.LIB_PATH], capture_output=True, text=True).stdout
+    names = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert names == set(declared_functions()), sorted(names ^ set(declared_functions()))
+
+
 def test_params_layout_matches():
     lib = _abi.load()
     p = _abi.lks_params()
