@@ -27,6 +27,25 @@ struct Vec2<double> {
     using type = double2;
 };
 
+// Arithmetic on (even, odd) column pairs: FP32 pairs use the packed FP32x2 instructions (one issue for both
+// columns, same rounding as the scalar ones; a - b is fma(b, -1, a)), FP64 pairs are component-wise.
+__device__ __forceinline__ float2 vmk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 vmk(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 vsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+template <typename T>
+__device__ __forceinline__ typename Vec2<T>::type vsplat(double a) {
+    return vmk((T)a, (T)a);
+}
+
 template <typename T>
 __device__ __forceinline__ T shfl_u(T v) {
     return __shfl_up_sync(0xffffffffu, v, 1);
@@ -57,7 +76,6 @@ __global__ void __launch_bounds__(128) fwd2v_kernel(Geom g, FwdArgs<T> a) {
     const int xl = wrap(xe, nx);          // even too, as nx is even
     const bool lane_out = lane >= 1 && lane <= 30 && xe < nx;
     const T A = (T)g.A;
-    const T W0 = (T)(2.0 / 3.0), W1 = (T)(1.0 / 6.0), third = (T)(1.0 / 3.0);
     const V* __restrict__ inP = reinterpret_cast<const V*>(a.in);
     const V* __restrict__ inX = reinterpret_cast<const V*>(a.in + g.N);
     const V* __restrict__ inY = reinterpret_cast<const V*>(a.in + 2 * g.N);
@@ -83,10 +101,11 @@ __global__ void __launch_bounds__(128) fwd2v_kernel(Geom g, FwdArgs<T> a) {
     load(y0 - 1, p1, x1v, y1v);
     load(y0, pA, xA, yA);
     load(y0 + 1, pB, xB, yB);
-    // output accumulators of rows m-1 (0), m (1), m+1 (2); e = even column, o = odd column
-    T aP0e = 0, aP0o = 0, aX0e = 0, aX0o = 0, aY0e = 0, aY0o = 0;
-    T aP1e = 0, aP1o = 0, aX1e = 0, aX1o = 0, aY1e = 0, aY1o = 0;
-    T aP2e = 0, aP2o = 0, aX2e = 0, aX2o = 0, aY2e = 0, aY2o = 0;
+    // output accumulators of rows m-1 (0), m (1), m+1 (2) as (even, odd) pairs: sum_i f_i, u*_x, u*_y
+    const V zero = vsplat<T>(0.0);
+    V aP0 = zero, aX0 = zero, aY0 = zero, aP1 = zero, aX1 = zero, aY1 = zero, aP2 = zero, aX2 = zero, aY2 = zero;
+    const V c3 = vsplat<T>(3.0), cm15 = vsplat<T>(-1.5), c45 = vsplat<T>(4.5), vA = vmk(A, A),
+            vhA = vmk((T)0.5 * A, (T)0.5 * A);
     T jacc = 0;
     bool unstable = false;
 
@@ -95,33 +114,32 @@ __global__ void __launch_bounds__(128) fwd2v_kernel(Geom g, FwdArgs<T> a) {
         p2 = pA; x2v = xA; y2v = yA;
         pA = pB; xA = xB; yA = yB;
         if (r + 2 <= y0 + R + 1) load(r + 2, pB, xB, yB);
-        // moment row m = r - 1 from rows r-2 (0), r-1 (1), r (2)
-        const T uxe = x1v.x, uxo = x1v.y, uye = y1v.x, uyo = y1v.y;
-        const T uxW = shfl_u(uxo), uxE = shfl_d(uxe), uyW = shfl_u(uyo), uyE = shfl_d(uye);
-        const T sige = (T)3 * p1.x - (T)1.5 * (uxe * uxe + uye * uye);
-        const T sigo = (T)3 * p1.y - (T)1.5 * (uxo * uxo + uyo * uyo);
-        const T Txxe = (T)4.5 * uxe * uxe + A * (uxo - uxW);
-        const T Txxo = (T)4.5 * uxo * uxo + A * (uxE - uxe);
-        const T Tyye = (T)4.5 * uye * uye + A * (y2v.x - y0v.x);
-        const T Tyyo = (T)4.5 * uyo * uyo + A * (y2v.y - y0v.y);
-        const T Txye = (T)4.5 * uxe * uye + (T)0.5 * A * ((uyo - uyW) + (x2v.x - x0v.x));
-        const T Txyo = (T)4.5 * uxo * uyo + (T)0.5 * A * ((uyE - uye) + (x2v.y - x0v.y));
+        // moment row m = r - 1 from rows r-2 (0), r-1 (1), r (2); the x-neighbours of the pair are
+        // (x - 1) = (previous lane's odd, even) and (x + 1) = (odd, next lane's even)
+        const V ux = x1v, uy = y1v;
+        const V uxL = vmk(shfl_u(ux.y), ux.x), uxR = vmk(ux.y, shfl_d(ux.x));
+        const V uyL = vmk(shfl_u(uy.y), uy.x), uyR = vmk(uy.y, shfl_d(uy.x));
+        const V uxx = vmul(ux, ux), uyy = vmul(uy, uy);
+        const V sig = vfma(cm15, vadd(uxx, uyy), vmul(c3, p1));
+        const V Txx = vfma(c45, uxx, vmul(vA, vsub(uxR, uxL)));
+        const V Tyy = vfma(c45, uyy, vmul(vA, vsub(y2v, y0v)));
+        const V Txy = vfma(c45, vmul(ux, uy), vmul(vhA, vadd(vsub(uyR, uyL), vsub(x2v, x0v))));
+        const V ux3 = vmul(c3, ux);
 #pragma unroll
         for (int cy = -1; cy <= 1; ++cy) {
-            const T be = sige + (T)(3 * cy) * uye + (T)(cy * cy) * Tyye;
-            const T bo = sigo + (T)(3 * cy) * uyo + (T)(cy * cy) * Tyyo;
-            const T gRe = be + (T)3 * uxe + Txxe + (T)(2 * cy) * Txye;  // (+1, cy) from the even column
-            const T gLe = be - (T)3 * uxe + Txxe - (T)(2 * cy) * Txye;  // (-1, cy)
-            const T gRo = bo + (T)3 * uxo + Txxo + (T)(2 * cy) * Txyo;
-            const T gLo = bo - (T)3 * uxo + Txxo - (T)(2 * cy) * Txyo;
-            const T inWe = shfl_u(gRo);  // into the even column from x - 1 (previous lane's odd column)
-            const T inEo = shfl_d(gLe);  // into the odd column from x + 1 (next lane's even column)
-            const T Wy = cy == 0 ? W0 : W1;
-            const T Se = Wy * (W1 * (inWe + gLo) + W0 * be), Xe = Wy * W1 * (inWe - gLo);
-            const T So = Wy * (W1 * (gRe + inEo) + W0 * bo), Xo = Wy * W1 * (gRe - inEo);
-            if (cy == -1) { aP0e += third * Se; aX0e += Xe; aY0e -= Se; aP0o += third * So; aX0o += Xo; aY0o -= So; }
-            if (cy == 0) { aP1e += third * Se; aX1e += Xe; aP1o += third * So; aX1o += Xo; }
-            if (cy == 1) { aP2e += third * Se; aX2e += Xe; aY2e += Se; aP2o += third * So; aX2o += Xo; aY2o += So; }
+            // b = sigma + 3 cy u_y + cy^2 T_yy; g(+-1, cy) = b +- 3 u_x + T_xx +- 2 cy T_xy
+            const V b = cy == 0 ? sig : vadd(vfma(vsplat<T>(3.0 * cy), uy, sig), Tyy);
+            const V cb = vadd(b, Txx);
+            const V gR = cy == 0 ? vadd(cb, ux3) : vfma(vsplat<T>(2.0 * cy), Txy, vadd(cb, ux3));
+            const V gL = cy == 0 ? vsub(cb, ux3) : vfma(vsplat<T>(-2.0 * cy), Txy, vsub(cb, ux3));
+            // streamed into the pair from x - 1 (gR of the left neighbours) and from x + 1 (gL of the right)
+            const V FL = vmk(shfl_u(gR.y), gR.x), FR = vmk(gL.y, shfl_d(gL.x));
+            const double Wy = cy == 0 ? 2.0 / 3.0 : 1.0 / 6.0;
+            const V S = vfma(vsplat<T>(Wy / 6.0), vadd(FL, FR), vmul(vsplat<T>(Wy * 2.0 / 3.0), b));
+            const V X = vmul(vsplat<T>(Wy / 6.0), vsub(FL, FR));
+            if (cy == -1) { aP0 = vadd(aP0, S); aX0 = vadd(aX0, X); aY0 = vsub(aY0, S); }
+            if (cy == 0) { aP1 = vadd(aP1, S); aX1 = vadd(aX1, X); }
+            if (cy == 1) { aP2 = vadd(aP2, S); aX2 = vadd(aX2, X); aY2 = vadd(aY2, S); }
         }
         // output row o = r - 2
         const int o = r - 2;
@@ -149,7 +167,7 @@ __global__ void __launch_bounds__(128) fwd2v_kernel(Geom g, FwdArgs<T> a) {
                     if (py && px) jacc += a.dir[0] * u0 + a.dir[1] * u1;
                 }
             };
-            T ue0 = aX0e, ue1 = aY0e, uo0 = aX0o, uo1 = aY0o;
+            T ue0 = aX0.x, ue1 = aY0.x, uo0 = aX0.y, uo1 = aY0.y;
             finish(ue0, ue1, bxe, wxe, pxe);
             finish(uo0, uo1, bxo, wxo, pxo);
             const int go = o * half + (xe >> 1);
@@ -157,7 +175,7 @@ __global__ void __launch_bounds__(128) fwd2v_kernel(Geom g, FwdArgs<T> a) {
             V* outX = reinterpret_cast<V*>(a.out_u);
             V* outY = reinterpret_cast<V*>(a.out_u + g.N);
             V vp, vx, vy;
-            vp.x = aP0e; vp.y = aP0o;
+            vp = vmul(vsplat<T>(1.0 / 3.0), aP0);
             vx.x = ue0; vx.y = uo0;
             vy.x = ue1; vy.y = uo1;
             outP[go] = vp;
@@ -166,9 +184,9 @@ __global__ void __launch_bounds__(128) fwd2v_kernel(Geom g, FwdArgs<T> a) {
         }
         p0 = p1; x0v = x1v; y0v = y1v;
         p1 = p2; x1v = x2v; y1v = y2v;
-        aP0e = aP1e; aP0o = aP1o; aX0e = aX1e; aX0o = aX1o; aY0e = aY1e; aY0o = aY1o;
-        aP1e = aP2e; aP1o = aP2o; aX1e = aX2e; aX1o = aX2o; aY1e = aY2e; aY1o = aY2o;
-        aP2e = 0; aP2o = 0; aX2e = 0; aX2o = 0; aY2e = 0; aY2o = 0;
+        aP0 = aP1; aX0 = aX1; aY0 = aY1;
+        aP1 = aP2; aX1 = aX2; aY1 = aY2;
+        aP2 = zero; aX2 = zero; aY2 = zero;
     }
     if (unstable) atomicOr(a.flag, 1u);
     if (a.jslot != nullptr) {
@@ -198,7 +216,6 @@ __global__ void __launch_bounds__(128, 5) adj2v_kernel(Geom g, AdjArgs<T> a) {
     const int xl = wrap(xe, nx);
     const bool lane_out = lane >= 1 && lane <= 30 && xe < nx;
     const T A = (T)g.A;
-    const T W0 = (T)(2.0 / 3.0), W1 = (T)(1.0 / 6.0), third = (T)(1.0 / 3.0);
     const V* __restrict__ lP = reinterpret_cast<const V*>(a.lam_in);
     const V* __restrict__ lX = reinterpret_cast<const V*>(a.lam_in + N);
     const V* __restrict__ lY = reinterpret_cast<const V*>(a.lam_in + 2 * N);
@@ -242,48 +259,46 @@ __global__ void __launch_bounds__(128, 5) adj2v_kernel(Geom g, AdjArgs<T> a) {
     V uxA, uyA, uxB, uyB;
     load_u(y0, uxA, uyA);
     load_u(y0 + 1, uxB, uyB);
-    // moment accumulators of rows r+1 (2), r (1), r-1 (0); completed rows r-2 (c), r-3 (p); e/o columns
-    T m0e0 = 0, m0o0 = 0, mxe0 = 0, mxo0 = 0, mye0 = 0, myo0 = 0, xxe0 = 0, xxo0 = 0, xye0 = 0, xyo0 = 0, yye0 = 0, yyo0 = 0;
-    T m0e1 = 0, m0o1 = 0, mxe1 = 0, mxo1 = 0, mye1 = 0, myo1 = 0, xxe1 = 0, xxo1 = 0, xye1 = 0, xyo1 = 0, yye1 = 0, yyo1 = 0;
-    T m0e2 = 0, m0o2 = 0, mxe2 = 0, mxo2 = 0, mye2 = 0, myo2 = 0, xxe2 = 0, xxo2 = 0, xye2 = 0, xyo2 = 0, yye2 = 0, yyo2 = 0;
-    T m0ec = 0, m0oc = 0, mxec = 0, mxoc = 0, myec = 0, myoc = 0, xxec = 0, xxoc = 0, xyec = 0, xyoc = 0, yyec = 0, yyoc = 0;
-    T xyep = 0, xyop = 0, yyep = 0, yyop = 0;
+    // moment accumulators as (even, odd) pairs: rows r-1 (0), r (1), r+1 (2); completed rows r-2 (c), r-3 (p)
+    const V zero = vsplat<T>(0.0);
+    V m00 = zero, mx0 = zero, my0 = zero, xx0 = zero, xy0 = zero, yy0 = zero;
+    V m01 = zero, mx1 = zero, my1 = zero, xx1 = zero, xy1 = zero, yy1 = zero;
+    V m02 = zero, mx2 = zero, my2 = zero, xx2 = zero, xy2 = zero, yy2 = zero;
+    V m0c = zero, mxc = zero, myc = zero, xxc = zero, xyc = zero, yyc = zero;
+    V xyp = zero, yyp = zero;
+    const V c3 = vsplat<T>(3.0), c9 = vsplat<T>(9.0), cm3 = vsplat<T>(-3.0), vA = vmk(A, A);
 
 #pragma unroll 1
     for (int r = y0 - 2; r <= y0 + R + 1; ++r) {
         const V lp = pA, lxv = xA, lyv = yA;
         pA = pB; xA = xB; yA = yB;
         if (r + 2 <= y0 + R + 1) load(r + 2, pB, xB, yB);
-        // source row r: p-bar* = lam_p, u-bar* = lam_u * factor
+        // source row r: p-bar*/3 = lam_p / 3, u-bar* = lam_u * factor
         const int yw = wrap(r, ny);
-        const T fe = factor(yw, sbxe, swxe), fo = factor(yw, sbxo, swxo);
-        const T pe = lp.x, po = lp.y, ue = lxv.x * fe, uo = lxv.y * fo, ve = lyv.x * fe, vo = lyv.y * fo;
-        // neighbours: x-1 of the even column is the previous lane's odd column, x+1 of the odd column the next
-        // lane's even column
-        const T pW = shfl_u(po), uW = shfl_u(uo), vW = shfl_u(vo);
-        const T pE = shfl_d(pe), uE = shfl_d(ue), vE = shfl_d(ve);
+        const V fac = vmk(factor(yw, sbxe, swxe), factor(yw, sbxo, swxo));
+        const V P3 = vmul(vsplat<T>(1.0 / 3.0), lp), U = vmul(lxv, fac), W = vmul(lyv, fac);
+        // sources x-1 of the pair (previous lane's odd, even) and x+1 (odd, next lane's even)
+        const V P3L = vmk(shfl_u(P3.y), P3.x), P3R = vmk(P3.y, shfl_d(P3.x));
+        const V UL = vmk(shfl_u(U.y), U.x), UR = vmk(U.y, shfl_d(U.x));
+        const V WL = vmk(shfl_u(W.y), W.x), WR = vmk(W.y, shfl_d(W.x));
+        const V FL0 = vsub(P3L, UL), FR0 = vadd(P3R, UR);  // F-bar of the sources at x-1, x+1 with c_y = 0
 #pragma unroll
         for (int cy = -1; cy <= 1; ++cy) {
-            // even column: sources x-1 (W), x (e), x+1 (o)
-            const T FLe = third * pW - uW + (T)cy * vW;
-            const T FCe = third * pe + (T)cy * ve;
-            const T FRe = third * po + uo + (T)cy * vo;
-            // odd column: sources x-1 (e), x (o), x+1 (E)
-            const T FLo = third * pe - ue + (T)cy * ve;
-            const T FCo = third * po + (T)cy * vo;
-            const T FRo = third * pE + uE + (T)cy * vE;
-            const T Wy = cy == 0 ? W0 : W1;
-            const T Se = Wy * (W1 * (FLe + FRe) + W0 * FCe), De = Wy * W1 * (FRe - FLe), Sxe = Wy * W1 * (FLe + FRe);
-            const T So = Wy * (W1 * (FLo + FRo) + W0 * FCo), Do = Wy * W1 * (FRo - FLo), Sxo = Wy * W1 * (FLo + FRo);
+            // F-bar_i(y) = p-bar*(y + c_i)/3 + c_i . u-bar*(y + c_i) for c = (-1, cy), (0, cy), (1, cy)
+            const V FL = cy == 0 ? FL0 : vfma(vsplat<T>(cy), WL, FL0);
+            const V FC = cy == 0 ? P3 : vfma(vsplat<T>(cy), W, P3);
+            const V FR = cy == 0 ? FR0 : vfma(vsplat<T>(cy), WR, FR0);
+            const double Wy = cy == 0 ? 2.0 / 3.0 : 1.0 / 6.0;
+            const V Sx = vmul(vsplat<T>(Wy / 6.0), vadd(FL, FR));
+            const V S = vfma(vsplat<T>(Wy * 2.0 / 3.0), FC, Sx), D = vmul(vsplat<T>(Wy / 6.0), vsub(FR, FL));
             if (cy == 1) {  // moment row r-1
-                m0e0 += Se; mxe0 += De; mye0 += Se; xxe0 += Sxe; xye0 += De; yye0 += Se;
-                m0o0 += So; mxo0 += Do; myo0 += So; xxo0 += Sxo; xyo0 += Do; yyo0 += So;
+                m00 = vadd(m00, S); mx0 = vadd(mx0, D); my0 = vadd(my0, S);
+                xx0 = vadd(xx0, Sx); xy0 = vadd(xy0, D); yy0 = vadd(yy0, S);
             } else if (cy == 0) {  // row r
-                m0e1 += Se; mxe1 += De; xxe1 += Sxe;
-                m0o1 += So; mxo1 += Do; xxo1 += Sxo;
+                m01 = vadd(m01, S); mx1 = vadd(mx1, D); xx1 = vadd(xx1, Sx);
             } else {  // row r+1
-                m0e2 += Se; mxe2 += De; mye2 -= Se; xxe2 += Sxe; xye2 -= De; yye2 += Se;
-                m0o2 += So; mxo2 += Do; myo2 -= So; xxo2 += Sxo; xyo2 -= Do; yyo2 += So;
+                m02 = vadd(m02, S); mx2 = vadd(mx2, D); my2 = vsub(my2, S);
+                xx2 = vadd(xx2, Sx); xy2 = vsub(xy2, D); yy2 = vadd(yy2, S);
             }
         }
         // lambda_{n-1} of row z = r - 2 from moment rows z-1 (p), z (c), z+1 (0)
@@ -293,39 +308,35 @@ __global__ void __launch_bounds__(128, 5) adj2v_kernel(Geom g, AdjArgs<T> a) {
             uxA = uxB;
             uyA = uyB;
             if (z + 2 <= y0 + R - 1) load_u(z + 2, uxB, uyB);
-            const T xxW = shfl_u(xxoc), xxE = shfl_d(xxec), xyW = shfl_u(xyoc), xyE = shfl_d(xyec);
+            const V xxL = vmk(shfl_u(xxc.y), xxc.x), xxR = vmk(xxc.y, shfl_d(xxc.x));
+            const V xyL = vmk(shfl_u(xyc.y), xyc.x), xyR = vmk(xyc.y, shfl_d(xyc.x));
             if (lane_out && z < ny) {
                 const int go = z * half + (xe >> 1);
-                T vxe = (T)3 * mxec - (T)3 * u0.x * m0ec + (T)9 * (xxec * u0.x + xyec * u1.x) +
-                        A * ((xxW - xxoc) + (xyep - xye0));
-                T vye = (T)3 * myec - (T)3 * u1.x * m0ec + (T)9 * (xyec * u0.x + yyec * u1.x) +
-                        A * ((xyW - xyoc) + (yyep - yye0));
-                T vxo = (T)3 * mxoc - (T)3 * u0.y * m0oc + (T)9 * (xxoc * u0.y + xyoc * u1.y) +
-                        A * ((xxec - xxE) + (xyop - xyo0));
-                T vyo = (T)3 * myoc - (T)3 * u1.y * m0oc + (T)9 * (xyoc * u0.y + yyoc * u1.y) +
-                        A * ((xyec - xyE) + (yyop - yyo0));
+                // lam_u' = 3 M1 - 3 u M0 + 9 M2 u + A sum_a [M2_a.(z - e_a) - M2_a.(z + e_a)]
+                V vx = vmul(c9, vfma(xyc, u1, vmul(xxc, u0)));
+                V vy = vmul(c9, vfma(yyc, u1, vmul(xyc, u0)));
+                vx = vfma(c3, mxc, vfma(vmul(cm3, u0), m0c, vx));
+                vy = vfma(c3, myc, vfma(vmul(cm3, u1), m0c, vy));
+                vx = vfma(vA, vadd(vsub(xxL, xxR), vsub(xyp, xy0)), vx);
+                vy = vfma(vA, vadd(vsub(xyL, xyR), vsub(yyp, yy0)), vy);
                 const int wy = wall_side(z, ny, g.periodic[1]);
                 const bool we = wy >= 0 || wall_side(xe, nx, g.periodic[0]) >= 0;
                 const bool wo = wy >= 0 || wall_side(xe + 1, nx, g.periodic[0]) >= 0;
                 const bool py = a.src && z >= g.probe_lo[1] && z < g.probe_hi[1];
                 if (py && pxe && !we) {
-                    vxe += a.phi_dir[0];
-                    vye += a.phi_dir[1];
+                    vx.x += a.phi_dir[0];
+                    vy.x += a.phi_dir[1];
                 }
                 if (py && pxo && !wo) {
-                    vxo += a.phi_dir[0];
-                    vyo += a.phi_dir[1];
+                    vx.y += a.phi_dir[0];
+                    vy.y += a.phi_dir[1];
                 }
                 V* oP = reinterpret_cast<V*>(a.lam_out);
                 V* oX = reinterpret_cast<V*>(a.lam_out + N);
                 V* oY = reinterpret_cast<V*>(a.lam_out + 2 * N);
-                V t;
-                t.x = (T)3 * m0ec; t.y = (T)3 * m0oc;
-                oP[go] = t;
-                t.x = vxe; t.y = vxo;
-                oX[go] = t;
-                t.x = vye; t.y = vyo;
-                oY[go] = t;
+                oP[go] = vmul(c3, m0c);
+                oX[go] = vx;
+                oY[go] = vy;
                 const int by = box_coord(z, P.xs[1], g.Fb[1], ny, g.periodic[1]);
                 if (by >= 0) {
                     for (int s = 0; s < 2; ++s) {
@@ -343,15 +354,11 @@ __global__ void __launch_bounds__(128, 5) adj2v_kernel(Geom g, AdjArgs<T> a) {
             }
         }
         // roll the moment rows
-        xyep = xyec; xyop = xyoc; yyep = yyec; yyop = yyoc;
-        m0ec = m0e0; m0oc = m0o0; mxec = mxe0; mxoc = mxo0; myec = mye0; myoc = myo0;
-        xxec = xxe0; xxoc = xxo0; xyec = xye0; xyoc = xyo0; yyec = yye0; yyoc = yyo0;
-        m0e0 = m0e1; m0o0 = m0o1; mxe0 = mxe1; mxo0 = mxo1; mye0 = mye1; myo0 = myo1;
-        xxe0 = xxe1; xxo0 = xxo1; xye0 = xye1; xyo0 = xyo1; yye0 = yye1; yyo0 = yyo1;
-        m0e1 = m0e2; m0o1 = m0o2; mxe1 = mxe2; mxo1 = mxo2; mye1 = mye2; myo1 = myo2;
-        xxe1 = xxe2; xxo1 = xxo2; xye1 = xye2; xyo1 = xyo2; yye1 = yye2; yyo1 = yyo2;
-        m0e2 = 0; m0o2 = 0; mxe2 = 0; mxo2 = 0; mye2 = 0; myo2 = 0;
-        xxe2 = 0; xxo2 = 0; xye2 = 0; xyo2 = 0; yye2 = 0; yyo2 = 0;
+        xyp = xyc; yyp = yyc;
+        m0c = m00; mxc = mx0; myc = my0; xxc = xx0; xyc = xy0; yyc = yy0;
+        m00 = m01; mx0 = mx1; my0 = my1; xx0 = xx1; xy0 = xy1; yy0 = yy1;
+        m01 = m02; mx1 = mx2; my1 = my2; xx1 = xx2; xy1 = xy2; yy1 = yy2;
+        m02 = zero; mx2 = zero; my2 = zero; xx2 = zero; xy2 = zero; yy2 = zero;
     }
 }
 
