@@ -48,8 +48,7 @@ struct LksError {
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// Launch a step kernel with programmatic stream serialization (see pdl_wait_then_release) and the priority of
-// its stream as a launch attribute, so that graph nodes captured from it keep that priority.
+// Launch a step kernel with programmatic stream serialization (see pdl_wait_then_release).
 template <typename K, typename... Args>
 void launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl, Args... args) {
     cudaLaunchConfig_t cfg = {};
@@ -57,18 +56,11 @@ void launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, bo
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    int prio = 0;
-    if (cudaStreamGetPriority(s, &prio) != cudaSuccess) {
-        cudaGetLastError();
-        prio = 0;
-    }
-    cudaLaunchAttribute attr[2];
-    attr[0].id = cudaLaunchAttributePriority;
-    attr[0].val.priority = prio;
-    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = pdl ? 2 : 1;
+    cfg.numAttrs = pdl ? 1 : 0;
     cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
     if (e != cudaSuccess) throw LksError{LKS_ECUDA, std::string("cudaLaunchKernelEx: ") + cudaGetErrorString(e)};
 }
@@ -855,17 +847,11 @@ void allocate(lks_ctx* c) {
 
     LKS_CUDA(cudaHostAlloc((void**)&c->h_flag, 16, cudaHostAllocDefault));
     *c->h_flag = 0;
-    // the reverse sweep's critical path (the adjoint chain on the capture stream) gets the highest priority; the
-    // recomputation and the sensitivity passes running beside it have slack and get the lowest.  Instances of a
-    // batch share the GPU with each other, so there all streams keep the default priority.
-    int prio_low = 0, prio_high = 0;
-    LKS_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
-    if (c->throughput) prio_low = prio_high = 0;
-    LKS_CUDA(cudaStreamCreateWithPriority(&c->cap, cudaStreamNonBlocking, prio_high));
-    LKS_CUDA(cudaStreamCreateWithPriority(&c->cap2, cudaStreamNonBlocking, prio_low));
-    LKS_CUDA(cudaStreamCreateWithPriority(&c->cap3, cudaStreamNonBlocking, prio_low));
-    LKS_CUDA(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_low));
-    LKS_CUDA(cudaStreamCreateWithPriority(&c->side2, cudaStreamNonBlocking, prio_low));
+    LKS_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    LKS_CUDA(cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking));
+    LKS_CUDA(cudaStreamCreateWithFlags(&c->cap3, cudaStreamNonBlocking));
+    LKS_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    LKS_CUDA(cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking));
     for (int i = 0; i < 2; ++i) {
         LKS_CUDA(cudaEventCreateWithFlags(&c->ev_rec[i], cudaEventDisableTiming));
         LKS_CUDA(cudaEventCreateWithFlags(&c->ev_adj[i], cudaEventDisableTiming));
@@ -923,7 +909,7 @@ void run_graph(lks_ctx* c, cudaGraphExec_t& gx, cudaStream_t s, F&& body) {
         }
         cudaGraph_t g = nullptr;
         LKS_CUDA(cudaStreamEndCapture(c->cap, &g));
-        cudaError_t e = cudaGraphInstantiate(&gx, g, cudaGraphInstantiateFlagUseNodePriority);
+        cudaError_t e = cudaGraphInstantiate(&gx, g, 0);
         cudaGraphDestroy(g);
         LKS_CUDA(e);
     }
@@ -1820,7 +1806,7 @@ void batch_graph(lks_batch* b, cudaGraphExec_t& gx, cudaStream_t s, F&& body) {
         }
         cudaGraph_t g = nullptr;
         LKS_CUDA(cudaStreamEndCapture(b->cap, &g));
-        cudaError_t e = cudaGraphInstantiate(&gx, g, cudaGraphInstantiateFlagUseNodePriority);
+        cudaError_t e = cudaGraphInstantiate(&gx, g, 0);
         cudaGraphDestroy(g);
         LKS_CUDA(e);
     }
@@ -1873,13 +1859,8 @@ int lks_batch_create(int count, const lks_params* params, lks_batch** out) {
             g_create_err = "instance " + std::to_string(i) + ": " + g_create_err;
         }
     }
-    int prio_low = 0, prio_high = 0;
-    if (rc == LKS_OK && cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
-        g_create_err = "cudaDeviceGetStreamPriorityRange failed";
-        rc = LKS_ECUDA;
-    }
     if (rc == LKS_OK) {
-        if (cudaStreamCreateWithPriority(&b->cap, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
+        if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
             g_create_err = "stream/event creation failed";
             rc = LKS_ECUDA;

@@ -50,6 +50,22 @@ __global__ void __launch_bounds__(256) fwd2r_kernel(Geom g, FwdArgs<T> a) {
     const int xl = wrap(xo, nx);
     const T A = (T)g.A;
     const Pose& P = *a.pose;
+    // kappa and C of this thread's output nodes depend only on the pose and the design, not on the previous
+    // step: evaluate them before waiting for it (programmatic dependent launch)
+    const bool lane_out = lane >= 2 && lane <= 29 && xo < nx;
+    const int bxc = box_coord(xo, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
+    T kapk[RPT], Ck[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int y = y0 + t + RW::TR * k;
+        const int byc = box_coord(y, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
+        kapk[k] = 0;
+        Ck[k] = 0;
+        if (lane_out && y < ny && bxc >= 0 && byc >= 0) {
+            const int b[2] = {bxc, byc};
+            map_node<T, 2, HW, false>(g, P, a.kref, b, kapk[k], Ck[k], nullptr, nullptr);
+        }
+    }
     pdl_wait_then_release();
 
     // phase 1: raw rows y0-2 .. y0+TY+1
@@ -85,8 +101,6 @@ __global__ void __launch_bounds__(256) fwd2r_kernel(Geom g, FwdArgs<T> a) {
     // phase 3: outputs on rows 2 .. TY+1, lanes 2 .. 29
     T jacc = 0;
     bool unstable = false;
-    const bool lane_out = lane >= 2 && lane <= 29 && xo < nx;
-    const int bxc = box_coord(xo, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
         const int o = 2 + t + RW::TR * k;
@@ -106,9 +120,7 @@ __global__ void __launch_bounds__(256) fwd2r_kernel(Geom g, FwdArgs<T> a) {
         T un0 = ax, un1 = ay;
         const int byc = box_coord(y, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
         if (bxc >= 0 && byc >= 0) {
-            const int b[2] = {bxc, byc};
-            T kap, C;
-            map_node<T, 2, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
+            const T kap = kapk[k], C = Ck[k];
             const T inv = (T)1 / ((T)1 + kap);
             un0 = (ax + kap * (pose_uG<T>(P, 0) * C)) * inv;
             un1 = (ay + kap * (pose_uG<T>(P, 1) * C)) * inv;
@@ -161,6 +173,25 @@ __global__ void __launch_bounds__(256) adj2r_kernel(Geom g, AdjArgs<T> a) {
     const T A = (T)g.A;
     const Pose& P = *a.pose;
     const int bxl = box_coord(xl, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
+    // u_{n-1} (and u_n on the footprint box) of this thread's output nodes come from the forward recomputation,
+    // complete before the previous step started: load them before waiting for it (programmatic dependent launch)
+    const bool lane_out = lane >= 2 && lane <= 29 && xo < nx;
+    const int bxc = box_coord(xo, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
+    T up0[RPT], up1[RPT], uc0[RPT], uc1[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int y = y0 + t + RW::TR * k;
+        up0[k] = up1[k] = uc0[k] = uc1[k] = 0;
+        if (lane_out && y < ny) {
+            const long long go = (long long)y * nx + xo;
+            up0[k] = a.u_prev[go];
+            up1[k] = a.u_prev[N + go];
+            if (bxc >= 0 && box_coord(y, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]) >= 0) {
+                uc0[k] = a.u_cur[go];
+                uc1[k] = a.u_cur[N + go];
+            }
+        }
+    }
     pdl_wait_then_release();
 
     // phase 1: G_i of the source nodes of rows y0-2 .. y0+TY+1 (Brinkman and wall adjoint folded in)
@@ -225,8 +256,6 @@ __global__ void __launch_bounds__(256) adj2r_kernel(Geom g, AdjArgs<T> a) {
     }
     __syncthreads();
     // phase 3: lambda_{n-1} on rows 2 .. TY+1, lanes 2 .. 29
-    const bool lane_out = lane >= 2 && lane <= 29 && xo < nx;
-    const int bxc = box_coord(xo, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
     const T* M0s = mo;
     const T* M1xs = mo + RR * 32;
     const T* M1ys = mo + 2 * RR * 32;
@@ -240,7 +269,7 @@ __global__ void __launch_bounds__(256) adj2r_kernel(Geom g, AdjArgs<T> a) {
         if (!lane_out || y >= ny) continue;
         const int c = o * 32 + lane;
         const long long go = (long long)y * nx + xo;
-        const T u0 = a.u_prev[go], u1 = a.u_prev[N + go];
+        const T u0 = up0[k], u1 = up1[k];
         const T M0 = M0s[c], Mxx = Mxxs[c], Myy = Myys[c], Mxy = Mxys[c];
         T vx = (T)3 * M1xs[c] - (T)3 * u0 * M0 + (T)9 * (Mxx * u0 + Mxy * u1) +
                A * ((Mxxs[c - 1] - Mxxs[c + 1]) + (Mxys[c - 32] - Mxys[c + 32]));
@@ -261,8 +290,8 @@ __global__ void __launch_bounds__(256) adj2r_kernel(Geom g, AdjArgs<T> a) {
             const long long bl = bxc + (long long)g.Fb[0] * byc;
             a.boxbuf[bl] = wall ? (T)0 : a.lam_in[N + go];
             a.boxbuf[g.Fbn + bl] = wall ? (T)0 : a.lam_in[2 * N + go];
-            a.boxbuf[2 * g.Fbn + bl] = a.u_cur[go];
-            a.boxbuf[3 * g.Fbn + bl] = a.u_cur[N + go];
+            a.boxbuf[2 * g.Fbn + bl] = uc0[k];
+            a.boxbuf[3 * g.Fbn + bl] = uc1[k];
         }
     }
 }
@@ -300,6 +329,25 @@ __global__ void __launch_bounds__(256) fwd2r2_kernel(Geom g, FwdArgs<T> a1, FwdA
     const int xo = x0 + lane - 4;           // this lane's column (may lie outside [0, nx))
     const int xl = wrap(xo, nx);
     const T A = (T)g.A;
+    // kappa and C of this thread's output nodes of both steps (rows h + t + 8 m, h = 2 for step n and 4 for step
+    // n+1) depend only on the poses and the design: evaluate them before waiting for the previous step
+    T kap1[2], C1[2], kap2[2], C2[2];
+    auto premap = [&](int h, const FwdArgs<T>& a, T* kk, T* cc, int nrow) {
+        const Pose& P = *a.pose;
+        const int bxc = box_coord(xl, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
+        for (int m = 0; m < nrow; ++m) {
+            const int o = h + t + 8 * m;
+            kk[m] = 0;
+            cc[m] = 0;
+            const int byc = box_coord(wrap(y0 - 4 + o, ny), P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
+            if (lane >= h && lane < 32 - h && o < RR - h && bxc >= 0 && byc >= 0) {
+                const int b[2] = {bxc, byc};
+                map_node<T, 2, HW, false>(g, P, a.kref, b, kk[m], cc[m], nullptr, nullptr);
+            }
+        }
+    };
+    premap(2, a1, kap1, C1, 2);
+    if (two) premap(4, a2, kap2, C2, 2);
     pdl_wait_then_release();
 
 #pragma unroll
@@ -336,13 +384,15 @@ __global__ void __launch_bounds__(256) fwd2r2_kernel(Geom g, FwdArgs<T> a1, FwdA
     // for the tile itself, to global memory (with the objective partial and the stability check)
     T jacc1 = 0, jacc2 = 0;
     bool unstable = false;
-    auto outputs = [&](int h, const FwdArgs<T>& a, T& jacc) {
+    auto outputs = [&](int h, const FwdArgs<T>& a, T& jacc, const T* kk, const T* cc) {
         const Pose& P = *a.pose;
         const int bxc = box_coord(xl, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
         const bool lane_in = lane >= h && lane < 32 - h;
         const bool lane_tile = lane >= 4 && lane < 28 && xo < nx;
-        for (int o = h + t; o < RR - h; o += 8) {
-            if (!lane_in) continue;
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int o = h + t + 8 * m;
+            if (o >= RR - h || !lane_in) continue;
             const int c = o * 32 + lane;
             const int yw = wrap(y0 - 4 + o, ny);
             T fq[9];
@@ -358,9 +408,7 @@ __global__ void __launch_bounds__(256) fwd2r2_kernel(Geom g, FwdArgs<T> a1, FwdA
             T un0 = ax, un1 = ay;
             const int byc = box_coord(yw, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
             if (bxc >= 0 && byc >= 0) {
-                const int b[2] = {bxc, byc};
-                T kap, C;
-                map_node<T, 2, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
+                const T kap = kk[m], C = cc[m];
                 const T inv = (T)1 / ((T)1 + kap);
                 un0 = (ax + kap * (pose_uG<T>(P, 0) * C)) * inv;
                 un1 = (ay + kap * (pose_uG<T>(P, 1) * C)) * inv;
@@ -392,12 +440,12 @@ __global__ void __launch_bounds__(256) fwd2r2_kernel(Geom g, FwdArgs<T> a1, FwdA
     };
     equilibria(1);
     __syncthreads();
-    outputs(2, a1, jacc1);
+    outputs(2, a1, jacc1, kap1, C1);
     if (two) {
         __syncthreads();
         equilibria(3);
         __syncthreads();
-        outputs(4, a2, jacc2);
+        outputs(4, a2, jacc2, kap2, C2);
     }
     if (unstable) atomicOr(a1.flag, 1u);
     for (int s = 0; s < 1 + two; ++s) {
