@@ -293,37 +293,46 @@ def run_ours(args):
         Fbn *= w["design"][a] + 2 * w["margin"] + 2 * hw - 1
     adj_bytes = N * (2 * (D + 1) + D) * s + Fbn * (D + 1) * s
     fwd_bytes = N * 2 * (D + 1) * s
-    n_adj = max(1, sum(n for _, n in st_adj))
-    n_fwd = max(1, sum(n for _, n in st_fwd) + sum(n for _, n in st_rec))
-    t_adj = sum(a for a, _ in st_adj)
-    t_fwd = sum(a for a, _ in st_fwd) + sum(a for a, _ in st_rec)
-    adj_ms, fwd_ms = t_adj / n_adj, t_fwd / n_fwd  # per step
-    rec_ms = sum(a for a, _ in st_rec) / max(1, sum(n for _, n in st_rec))
     peak, peak_kind = peaks()
+    # spans (ms) and launches-worth of steps per kind: the forward sweep, the recomputation, the adjoint steps
+    t_f, n_f = sum(a for a, _ in st_fwd), sum(n for _, n in st_fwd)
+    t_r, n_r = sum(a for a, _ in st_rec), sum(n for _, n in st_rec)
+    t_a, n_a = sum(a for a, _ in st_adj), sum(n for _, n in st_adj)
 
-    def kernel_entry(kind, step_bytes, step_ms):
-        rows = st0["tile_rows_fwd" if kind == "fwd" else "tile_rows_adj"]
+    def kernel_entry(kind, rows, step_bytes, t_ms, n_steps):
         name, src, per_launch = kernel_variant(w["lattice"], rows, kind)
-        gbs = step_bytes / (step_ms * 1e-3) / 1e9
+        step_ms = t_ms / max(1, n_steps)
+        gbs = step_bytes / (step_ms * 1e-3) / 1e9 if step_ms > 0 else 0.0
         return {"bound": "hbm", "kernel": name, "achieved": gbs, "peak": peak, "peak_kind": peak_kind,
                 "unit": "GB/s", "frac": gbs / peak, "traffic": captured_traffic(w["name"], name, src),
                 "bytes_per_launch": step_bytes * per_launch, "us_per_launch": step_ms * per_launch * 1e3,
-                "steps_per_launch": per_launch}
+                "steps_per_launch": per_launch, "_t": t_ms}
 
-    k_fwd = kernel_entry("fwd", fwd_bytes, fwd_ms)
-    k_adj = kernel_entry("adj", adj_bytes, adj_ms)
-    tot = max(1e-30, t_fwd + t_adj)
-    # shares of the summed kernel spans (recompute overlaps the adjoint on its own stream, so these are shares of
-    # kernel time, not of wall time); forward launches are averaged over the forward sweep and the recomputation
-    k_fwd["share_of_kernel_time"], k_adj["share_of_kernel_time"] = t_fwd / tot, t_adj / tot
-    fwd_sweep_ms = sum(a for a, _ in st_fwd) / max(1, sum(n for _, n in st_fwd))
-    k_fwd["us_per_step_forward_sweep"], k_fwd["us_per_step_recompute"] = fwd_sweep_ms * 1e3, rec_ms * 1e3
-    roof, other = (k_fwd, k_adj) if t_fwd >= t_adj else (k_adj, k_fwd)
+    # the forward-step kernel of the forward sweep and of the recomputation (one entry when they are the same
+    # variant: its launches averaged over both, the sweep and recompute means listed), and the adjoint kernel
+    entries = []
+    if st0["tile_rows_rec"] == st0["tile_rows_fwd"] or n_r == 0:
+        e = kernel_entry("fwd", st0["tile_rows_fwd"], fwd_bytes, t_f + t_r, n_f + n_r)
+        e["us_per_step_forward_sweep"] = 1e3 * t_f / max(1, n_f)
+        e["us_per_step_recompute"] = 1e3 * t_r / max(1, n_r)
+        entries.append(e)
+    else:
+        e = kernel_entry("fwd", st0["tile_rows_fwd"], fwd_bytes, t_f, n_f)
+        e["role"] = "forward sweep"
+        entries.append(e)
+        e = kernel_entry("fwd", st0["tile_rows_rec"], fwd_bytes, t_r, n_r)
+        e["role"] = "recomputation (beside the adjoint chain)"
+        entries.append(e)
+    entries.append(kernel_entry("adj", st0["tile_rows_adj"], adj_bytes, t_a, n_a))
+    tot = max(1e-30, sum(e["_t"] for e in entries))
+    for e in entries:
+        # shares of the summed kernel spans (recompute overlaps the adjoint on its own stream)
+        e["share_of_kernel_time"] = e.pop("_t") / tot
+    entries.sort(key=lambda e: -e["share_of_kernel_time"])
     # the whole path: algorithmic bytes of every forward, recompute and adjoint step over the device time
-    n_f = sum(n for _, n in st_fwd) + sum(n for _, n in st_rec)
-    path_bytes = n_f * fwd_bytes + sum(n for _, n in st_adj) * adj_bytes
+    path_bytes = (n_f + n_r) * fwd_bytes + n_a * adj_bytes
     path_gbs = path_bytes / t_dev / 1e9
-    roof = dict(roof, other_kernel=other,
+    roof = dict(entries[0], other_kernels=entries[1:],
                 path={"achieved": path_gbs, "frac": path_gbs / peak, "unit": "GB/s",
                       "bytes_per_step": path_bytes / args.steps,
                       "note": "algorithmic bytes of all step kernels (forward, recompute, adjoint) / device time"})
@@ -358,7 +367,8 @@ def run_ours(args):
             "roofline": roof,
             "e2e": {"value": e2e, "unit": "G node-steps/s (fwd+adj)", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches * world),
-            "tile_rows": [st0["tile_rows_fwd"], st0["tile_rows_adj"]],
+            "tile_rows": {"forward": st0["tile_rows_fwd"], "recompute": st0["tile_rows_rec"],
+                          "adjoint": st0["tile_rows_adj"]},
             "clocks": clk,
             "wall_s": t_wall,
         }

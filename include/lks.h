@@ -124,8 +124,10 @@ typedef struct lks_stats {
     int64_t device_bytes;      /* device memory held by the context */
     int32_t ckpt_slots;        /* checkpoints in use */
     int32_t seg_len;           /* recompute segment length */
-    int32_t tile_rows_fwd;     /* D2Q9: rows per warp chosen for the forward / adjoint step kernels */
-    int32_t tile_rows_adj;
+    int32_t tile_rows_fwd;     /* step-kernel variants (tile_rows codes) of the forward sweep, */
+    int32_t tile_rows_adj;     /* the adjoint steps */
+    int32_t tile_rows_rec;     /* and the recomputation in lks_adjoint */
+    int32_t reserved;
     /* With lks_set_timing(ctx, 1): device time (CUDA events on the launching stream) of the last call pair. */
     double ms_forward_steps;   /* the Nt forward-step kernels of lks_forward */
     double ms_recompute_steps; /* forward-step kernels re-run by lks_adjoint */

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -461,6 +462,10 @@ struct lks_ctx {
     long long box_step = 0;     // elements per step in d_boxbuf
     void* d_fac = nullptr;      // two buffers of Lmax steps x Fbn: 1 / (1 + kappa) on the footprint box
     bool throughput = false;    // instance of a batch: tune for throughput (see create_ctx)
+    // step-kernel variants of the forward sweep, the recomputation and the adjoint steps (see choose_variants)
+    int rows_fwd_sweep = 0, rows_rec = 0, rows_adj = 0;
+    // tuner results: fastest forward / adjoint variant overall and among those taking one step per launch
+    int tune_f_lat = 0, tune_f_one = 0, tune_a_lat = 0, tune_a_one = 0;
     int nsb = 0;                // sensitivity blocks per step
     size_t state_bytes = 0;
     std::vector<void*> slot;  // checkpoint slots
@@ -707,16 +712,18 @@ void choose_rows_initial(lks_ctx* c) {
 // width, grid) for the life of the process.
 void autotune_rows(lks_ctx* c) {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> cache;
+    static std::map<std::tuple<int, int, int, int, int>, std::array<int, 4>> cache;
     int dev = 0;
     LKS_CUDA(cudaGetDevice(&dev));
-    const auto key = std::make_tuple(dev, (int)c->tsize * 2 + (c->throughput ? 1 : 0), c->hw * 16 + c->D, c->g.n[0],
-                                     c->g.n[1] * 65536 + c->g.n[2]);
+    const auto key = std::make_tuple(dev, (int)c->tsize, c->hw * 16 + c->D, c->g.n[0], c->g.n[1] * 65536 + c->g.n[2]);
     {
         std::lock_guard<std::mutex> lock(mu);
         auto it = cache.find(key);
         if (it != cache.end()) {
-            c->eng->set_rows(it->second.first, it->second.second, c->g);
+            c->tune_f_lat = it->second[0];
+            c->tune_f_one = it->second[1];
+            c->tune_a_lat = it->second[2];
+            c->tune_a_one = it->second[3];
             return;
         }
     }
@@ -731,8 +738,9 @@ void autotune_rows(lks_ctx* c) {
     // every forward variant with the initial adjoint one, then every adjoint variant with the initial forward one
     const std::vector<int> cf = c->eng->fwd_codes(), ca = c->eng->adj_codes();
     const int rf0 = c->eng->rows_f, ra0 = c->eng->rows_a;
-    float best_f = 1e30f, best_a = 1e30f;
-    int rf = rf0, ra = ra0;
+    // fastest overall and fastest among the one-step variants, for each kernel
+    float best_f = 1e30f, best_a = 1e30f, best_f1 = 1e30f, best_a1 = 1e30f;
+    int rf = rf0, ra = ra0, rf1 = rf0, ra1 = ra0;
     const int jlo[3] = {0, 0, 0}, jn[3] = {1, 1, 1};
     // ms per step of `reps` back-to-back launches of one variant after 3 untimed ones
     auto time_variant = [&](int r, int pass, int reps) {
@@ -759,7 +767,6 @@ void autotune_rows(lks_ctx* c) {
     };
     for (int pass = 0; pass < 2; ++pass) {
         for (int r : (pass == 0 ? cf : ca)) {
-            if (c->throughput && c->D == 2 && r == 3) continue;  // two steps per launch: latency, not throughput
             // not available for this grid / precision
             if (!(pass == 0 ? c->eng->set_rows(r, ra0, c->g) : c->eng->set_rows(rf0, r, c->g))) continue;
             // size each measurement to about 1.5 ms of launches and keep the fastest of three
@@ -770,21 +777,55 @@ void autotune_rows(lks_ctx* c) {
             if (std::getenv("LKS_TUNE_VERBOSE"))
                 std::fprintf(stderr, "lks autotune %dx%dx%d %s rows=%d: %.3f us/step (%d launches)\n", c->g.n[0],
                              c->g.n[1], c->g.n[2], pass == 0 ? "forward" : "adjoint", r, 1e3f * ms, reps);
+            const bool one_step = (pass == 0 ? !c->eng->fused2() : !c->eng->fused_adj2());
             if (pass == 0 && ms < best_f) {
                 best_f = ms;
                 rf = r;
+            }
+            if (pass == 0 && one_step && ms < best_f1) {
+                best_f1 = ms;
+                rf1 = r;
             }
             if (pass == 1 && ms < best_a) {
                 best_a = ms;
                 ra = r;
             }
+            if (pass == 1 && one_step && ms < best_a1) {
+                best_a1 = ms;
+                ra1 = r;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->eng->set_rows(rf, ra, c->g);
+    c->tune_f_lat = rf;
+    c->tune_f_one = rf1;
+    c->tune_a_lat = ra;
+    c->tune_a_one = ra1;
     std::lock_guard<std::mutex> lock(mu);
-    cache[key] = std::make_pair(rf, ra);
+    cache[key] = {rf, rf1, ra, ra1};
+}
+
+// Variants of the three kinds of step launches.  The forward sweep is one chain, so it takes the fastest
+// variant.  In the pipelined sqrt(N) reverse sweep the recomputation and the adjoint chain run at the same time
+// and share the GPU, and in a batch all instances do: there the one-step variants win, because the two-step
+// ones recompute a halo (512x256: 13.6 against 13.0 G node-steps/s).  Binomial and full-storage reverse sweeps
+// run one chain and take the fastest variants.  Explicit tile_rows fix all of them.
+void choose_variants(lks_ctx* c) {
+    if (c->prm.tile_rows != 0) {
+        c->rows_fwd_sweep = c->rows_rec = c->eng->rows_f;
+        c->rows_adj = c->eng->rows_a;
+    } else {
+        const bool shared = c->throughput || c->prm.ckpt == LKS_CKPT_SQRT;
+        c->rows_fwd_sweep = c->throughput ? c->tune_f_one : c->tune_f_lat;
+        c->rows_rec = shared ? c->tune_f_one : c->tune_f_lat;
+        c->rows_adj = shared ? c->tune_a_one : c->tune_a_lat;
+    }
+    if (!c->eng->set_rows(c->rows_fwd_sweep, c->rows_adj, c->g) || !c->eng->set_rows(c->rows_rec, c->rows_adj, c->g))
+        throw LksError{LKS_EINVAL, "step-kernel variant not available for this grid"};
+    c->stats.tile_rows_fwd = c->rows_fwd_sweep;
+    c->stats.tile_rows_rec = c->rows_rec;
+    c->stats.tile_rows_adj = c->rows_adj;
 }
 
 void allocate(lks_ctx* c) {
@@ -1076,6 +1117,7 @@ void run_forward(lks_ctx* c, cudaStream_t s) {
 
 void forward_body(lks_ctx* c, cudaStream_t s) {
     const int Nt = c->prm.Nt;
+    c->eng->set_rows(c->rows_fwd_sweep, c->rows_adj, c->g);
     c->launches = 0;
     if (!c->use_graphs) c->evnext = 0;
     c->spans.clear();
@@ -1304,6 +1346,7 @@ void run_adjoint(lks_ctx* c, cudaStream_t s) {
 
 void adjoint_body(lks_ctx* c, cudaStream_t s) {
     const int Nt = c->prm.Nt, D = c->D, K = c->prm.K;
+    c->eng->set_rows(c->rows_rec, c->rows_adj, c->g);
     c->launches = 0;
     c->spans.clear();
     c->stats.recompute_steps = 0;
@@ -1480,8 +1523,7 @@ static int create_ctx(const lks_params* p, bool throughput, lks_ctx** out) {
         choose_rows_initial(c);
         allocate(c);
         if (p->tile_rows == 0) autotune_rows(c);
-        c->stats.tile_rows_fwd = c->eng->rows_f;
-        c->stats.tile_rows_adj = c->eng->rows_a;
+        choose_variants(c);
         *out = c;
         g_create_err.clear();
         return LKS_OK;

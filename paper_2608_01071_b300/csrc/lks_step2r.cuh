@@ -489,6 +489,32 @@ __global__ void __launch_bounds__(256) adj2r2_kernel(Geom g, AdjArgs<T> a1, AdjA
     const int xl = wrap(xo, nx);
     const T A = (T)g.A;
     const bool lane_tile = lane >= 4 && lane < 28 && xo < nx;
+    // u_{n-1} and u_n of this thread's output nodes of both steps (rows h + t + 8 m, h = 2 for step n and 4 for
+    // step n-1) come from the forward recomputation, complete before the previous launch started: load them
+    // before waiting for it (u_n only where a footprint record is written)
+    T up1[2][2], uc1[2][2], up2[2][2], uc2[2][2];
+    auto preload = [&](int h, const AdjArgs<T>& a, T (*up)[2], T (*uc)[2]) {
+        const Pose& P = *a.pose;
+        const int bxc = box_coord(xl, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int o = h + t + 8 * m;
+            up[m][0] = up[m][1] = uc[m][0] = uc[m][1] = 0;
+            if (lane >= h && lane < 32 - h && o < RR - h) {
+                const int yw = wrap(y0 - 4 + o, ny);
+                const long long go = (long long)yw * nx + xl;
+                up[m][0] = a.u_prev[go];
+                up[m][1] = a.u_prev[N + go];
+                const bool own = lane_tile && o >= 4 && o < RR - 4 && y0 - 4 + o < ny;
+                if (own && bxc >= 0 && box_coord(yw, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]) >= 0) {
+                    uc[m][0] = a.u_cur[go];
+                    uc[m][1] = a.u_cur[N + go];
+                }
+            }
+        }
+    };
+    preload(2, a1, up1, uc1);
+    if (two) preload(4, a2, up2, uc2);
     pdl_wait_then_release();
 
     // G_i of rows [h, RR-h), lanes [h, 32-h) from lambda (global for step n, shared memory for step n-1)
@@ -565,7 +591,7 @@ __global__ void __launch_bounds__(256) adj2r2_kernel(Geom g, AdjArgs<T> a1, AdjA
     };
     // lambda_{n-1} of rows [h, RR-h), lanes [h, 32-h): to shared memory (to_smem) and, for the tile's own nodes,
     // to global memory (!to_smem); footprint-box records of the tile's own nodes
-    auto outputs = [&](int h, const AdjArgs<T>& a, bool to_smem, bool lam_smem) {
+    auto outputs = [&](int h, const AdjArgs<T>& a, bool to_smem, bool lam_smem, const T (*up)[2], const T (*uc)[2]) {
         const Pose& P = *a.pose;
         const int bxc = box_coord(xl, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
         const T* M0s = mo;
@@ -575,11 +601,14 @@ __global__ void __launch_bounds__(256) adj2r2_kernel(Geom g, AdjArgs<T> a1, AdjA
         const T* Myys = mo + 4 * RR * 32;
         const T* Mxys = mo + 5 * RR * 32;
         if (lane < h || lane >= 32 - h) return;
-        for (int o = h + t; o < RR - h; o += 8) {
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int o = h + t + 8 * m;
+            if (o >= RR - h) continue;
             const int yw = wrap(y0 - 4 + o, ny);
             const int c = o * 32 + lane;
             const long long go = (long long)yw * nx + xl;
-            const T u0 = a.u_prev[go], u1 = a.u_prev[N + go];
+            const T u0 = up[m][0], u1 = up[m][1];
             const T M0 = M0s[c], Mxx = Mxxs[c], Myy = Myys[c], Mxy = Mxys[c];
             T vx = (T)3 * M1xs[c] - (T)3 * u0 * M0 + (T)9 * (Mxx * u0 + Mxy * u1) +
                    A * ((Mxxs[c - 1] - Mxxs[c + 1]) + (Mxys[c - 32] - Mxys[c + 32]));
@@ -602,8 +631,8 @@ __global__ void __launch_bounds__(256) adj2r2_kernel(Geom g, AdjArgs<T> a1, AdjA
                     const T ly = lam_smem ? sl[2 * RR * 32 + c] : a.lam_in[2 * N + go];
                     a.boxbuf[bl] = wall ? (T)0 : lx;
                     a.boxbuf[g.Fbn + bl] = wall ? (T)0 : ly;
-                    a.boxbuf[2 * g.Fbn + bl] = a.u_cur[go];
-                    a.boxbuf[3 * g.Fbn + bl] = a.u_cur[N + go];
+                    a.boxbuf[2 * g.Fbn + bl] = uc[m][0];
+                    a.boxbuf[3 * g.Fbn + bl] = uc[m][1];
                 }
             }
             if (to_smem) {
@@ -623,14 +652,14 @@ __global__ void __launch_bounds__(256) adj2r2_kernel(Geom g, AdjArgs<T> a1, AdjA
     __syncthreads();
     moments(1);
     __syncthreads();
-    outputs(2, a1, two != 0, false);
+    outputs(2, a1, two != 0, false, up1, uc1);
     if (two) {
         __syncthreads();
         stage(2, a2, true);
         __syncthreads();
         moments(3);
         __syncthreads();
-        outputs(4, a2, false, true);
+        outputs(4, a2, false, true, up2, uc2);
     }
 }
 
