@@ -38,8 +38,8 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nt", type=int, default=0, help="override the horizon (short runs for profiler captures)")
-    ap.add_argument("--tile-rows", default="", help="force step-kernel variants instead of autotuning: F or F,A "
-                    "(forward and adjoint tile_rows codes)")
+    ap.add_argument("--tile-rows", default="", help="force step-kernel variants instead of autotuning: F, F,A or "
+                    "F,A,R (tile_rows codes of the forward sweep, the adjoint and the recomputation)")
     return ap.parse_args()
 
 
@@ -231,7 +231,8 @@ def run_ours(args):
                  amp=w["amp"] * args.nt / w["Nt"])
     if args.tile_rows:
         codes = [int(v) for v in args.tile_rows.split(",")]
-        w = dict(w, tile_rows=codes[0], tile_rows_adj=codes[1] if len(codes) > 1 else 0)
+        w = dict(w, tile_rows=codes[0], tile_rows_adj=codes[1] if len(codes) > 1 else 0,
+                 tile_rows_rec=codes[2] if len(codes) > 2 else 0)
     D = len(w["shape"])
     N = node_count(w)
     solver = Solver.from_workload(w)

@@ -77,8 +77,9 @@ enum { LKS_MODE_JOINT = 0, LKS_MODE_SHAPE = 1, LKS_MODE_MOTION = 2 };
  *                 32 or 64 = vectorised warp columns (two columns per lane, even n[0] only) with that many rows.  D3Q15: 1 = shared-memory tiles
  *                 of 32 x 4 x 4 nodes; 8 or 16 = z-marching kernels with that many planes per block.
  *                 0 = autotune at lks_create (times every choice on the context's buffers; cached per process).
- *  tile_rows_adj  adjoint step-kernel variant when tile_rows != 0 (same codes, 3 excluded); 0 = tile_rows
- *                 (1 when tile_rows = 3).  Must be 0 when tile_rows = 0.
+ *  tile_rows_adj  adjoint step-kernel variant when tile_rows != 0 (same codes); 0 = tile_rows.
+ *  tile_rows_rec  forward variant of the recomputation in lks_adjoint when tile_rows != 0; 0 = tile_rows.
+ *                 tile_rows_adj and tile_rows_rec must be 0 when tile_rows = 0 (all three autotuned).
  */
 typedef struct lks_params {
     uint32_t size;
@@ -111,6 +112,7 @@ typedef struct lks_params {
     double u_crit;
     int32_t tile_rows;
     int32_t tile_rows_adj;
+    int32_t tile_rows_rec;
 } lks_params;
 
 typedef struct lks_ctx lks_ctx;

@@ -50,6 +50,7 @@ class lks_params(C.Structure):
         ("u_crit", C.c_double),
         ("tile_rows", C.c_int32),
         ("tile_rows_adj", C.c_int32),
+        ("tile_rows_rec", C.c_int32),
     ]
 
 

@@ -63,6 +63,7 @@ def params_from_workload(w: dict) -> _abi.lks_params:
     p.u_crit = w.get("u_crit", 0.3)
     p.tile_rows = w.get("tile_rows", 0)
     p.tile_rows_adj = w.get("tile_rows_adj", 0)
+    p.tile_rows_rec = w.get("tile_rows_rec", 0)
     return p
 
 

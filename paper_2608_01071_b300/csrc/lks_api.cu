@@ -464,7 +464,7 @@ struct lks_ctx {
     bool throughput = false;    // instance of a batch: tune for throughput (see create_ctx)
     // step-kernel variants of the forward sweep, the recomputation and the adjoint steps (see choose_variants)
     int rows_fwd_sweep = 0, rows_rec = 0, rows_adj = 0;
-    // tuner results: fastest forward / adjoint variant overall and among those taking one step per launch
+    // tuner results: fastest forward / adjoint variant alone, and the fastest one-step pair run side by side
     int tune_f_lat = 0, tune_f_one = 0, tune_a_lat = 0, tune_a_one = 0;
     int nsb = 0;                // sensitivity blocks per step
     size_t state_bytes = 0;
@@ -582,6 +582,8 @@ void validate(const lks_params* p) {
                      "32, 64 (separable, 16 or 32 planes per block), 96 (separable forward, 16 x 16 columns)");
     if (p->tile_rows_adj != 0 && (p->tile_rows == 0 || !variant_ok(p->tile_rows_adj, false)))
         bad("tile_rows_adj must be 0, or a valid adjoint variant with tile_rows != 0");
+    if (p->tile_rows_rec != 0 && (p->tile_rows == 0 || !variant_ok(p->tile_rows_rec, true)))
+        bad("tile_rows_rec must be 0, or a valid forward variant with tile_rows != 0");
 }
 
 void setup_geometry(lks_ctx* c) {
@@ -738,9 +740,10 @@ void autotune_rows(lks_ctx* c) {
     // every forward variant with the initial adjoint one, then every adjoint variant with the initial forward one
     const std::vector<int> cf = c->eng->fwd_codes(), ca = c->eng->adj_codes();
     const int rf0 = c->eng->rows_f, ra0 = c->eng->rows_a;
-    // fastest overall and fastest among the one-step variants, for each kernel
-    float best_f = 1e30f, best_a = 1e30f, best_f1 = 1e30f, best_a1 = 1e30f;
-    int rf = rf0, ra = ra0, rf1 = rf0, ra1 = ra0;
+    // fastest overall, for each kernel; the one-step variants' times are kept for the pair timing below
+    float best_f = 1e30f, best_a = 1e30f;
+    int rf = rf0, ra = ra0;
+    std::vector<std::pair<float, int>> one_f, one_a;
     const int jlo[3] = {0, 0, 0}, jn[3] = {1, 1, 1};
     // ms per step of `reps` back-to-back launches of one variant after 3 untimed ones
     auto time_variant = [&](int r, int pass, int reps) {
@@ -782,20 +785,61 @@ void autotune_rows(lks_ctx* c) {
                 best_f = ms;
                 rf = r;
             }
-            if (pass == 0 && one_step && ms < best_f1) {
-                best_f1 = ms;
-                rf1 = r;
-            }
             if (pass == 1 && ms < best_a) {
                 best_a = ms;
                 ra = r;
             }
-            if (pass == 1 && one_step && ms < best_a1) {
-                best_a1 = ms;
-                ra1 = r;
-            }
+            if (one_step) (pass == 0 ? one_f : one_a).push_back({ms, r});
         }
     }
+    // Chains that share the GPU (the recomputation beside the adjoint chain): time the three fastest one-step
+    // forward variants against the three fastest one-step adjoint variants, launched together on two streams,
+    // and keep the pair with the shortest time per step of both.  Isolated timings do not rank these well: on
+    // 512x256 the 16-row forward and adjoint tiles are faster alone and slower together.
+    std::sort(one_f.begin(), one_f.end());
+    std::sort(one_a.begin(), one_a.end());
+    if (one_f.size() > 3) one_f.resize(3);
+    if (one_a.size() > 3) one_a.resize(3);
+    cudaStream_t s2 = c->side2;
+    cudaEvent_t e2;
+    LKS_CUDA(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+    auto time_pair = [&](int reps) {
+        for (int k = 0; k < 3 + reps; ++k) {
+            if (k == 3) {
+                LKS_CUDA(cudaStreamSynchronize(s2));
+                LKS_CUDA(cudaEventRecord(e0, s));
+                LKS_CUDA(cudaStreamWaitEvent(s2, e0, 0));
+            }
+            c->eng->fwd(c->g, c->slot[0], c->pp[k & 1], c->d_kref, c->d_pose, nullptr, c->d_flag, jlo, jn, s2);
+            c->eng->adj(c->g, c->lam[k & 1], c->lam[(k + 1) & 1], c->slot[0], c->slot[0], c->d_kref, c->d_pose,
+                        c->d_boxbuf, c->d_fac, 1, s);
+        }
+        LKS_CUDA(cudaEventRecord(e2, s2));
+        LKS_CUDA(cudaStreamWaitEvent(s, e2, 0));
+        LKS_CUDA(cudaEventRecord(e1, s));
+        LKS_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        LKS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        return ms / (float)reps;
+    };
+    float best_pair = 1e30f;
+    int rf1 = one_f.empty() ? rf0 : one_f[0].second, ra1 = one_a.empty() ? ra0 : one_a[0].second;
+    for (const auto& f : one_f)
+        for (const auto& ad : one_a) {
+            if (!c->eng->set_rows(f.second, ad.second, c->g)) continue;
+            const int reps = std::max(10, std::min(2000, (int)(1.5f / std::max(f.first + ad.first, 1e-4f))));
+            float ms = 1e30f;
+            for (int trial = 0; trial < 3; ++trial) ms = std::min(ms, time_pair(reps));
+            if (std::getenv("LKS_TUNE_VERBOSE"))
+                std::fprintf(stderr, "lks autotune %dx%dx%d forward rows=%d beside adjoint rows=%d: %.3f us/step\n",
+                             c->g.n[0], c->g.n[1], c->g.n[2], f.second, ad.second, 1e3f * ms);
+            if (ms < best_pair) {
+                best_pair = ms;
+                rf1 = f.second;
+                ra1 = ad.second;
+            }
+        }
+    cudaEventDestroy(e2);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->tune_f_lat = rf;
@@ -808,12 +852,14 @@ void autotune_rows(lks_ctx* c) {
 
 // Variants of the three kinds of step launches.  The forward sweep is one chain, so it takes the fastest
 // variant.  In the pipelined sqrt(N) reverse sweep the recomputation and the adjoint chain run at the same time
-// and share the GPU, and in a batch all instances do: there the one-step variants win, because the two-step
-// ones recompute a halo (512x256: 13.6 against 13.0 G node-steps/s).  Binomial and full-storage reverse sweeps
-// run one chain and take the fastest variants.  Explicit tile_rows fix all of them.
+// and share the GPU, and in a batch all instances do: there the one-step pair timed side by side wins (two-step
+// launches recompute a halo; on 512x256 (two-step, two-step) gave 13.0 and the side-by-side pair of 8-row tiles
+// 15.0 G node-steps/s).  Binomial and full-storage reverse sweeps run one chain and take the fastest variants.
+// Explicit tile_rows fix all of them.
 void choose_variants(lks_ctx* c) {
     if (c->prm.tile_rows != 0) {
-        c->rows_fwd_sweep = c->rows_rec = c->eng->rows_f;
+        c->rows_fwd_sweep = c->eng->rows_f;
+        c->rows_rec = c->prm.tile_rows_rec != 0 ? c->prm.tile_rows_rec : c->eng->rows_f;
         c->rows_adj = c->eng->rows_a;
     } else {
         const bool shared = c->throughput || c->prm.ckpt == LKS_CKPT_SQRT;

@@ -51,6 +51,7 @@ def test_validation_errors_without_gpu():
                    lambda p: p.probe_hi.__setitem__(0, 500), lambda p: setattr(p, "tile_rows", 5),
                    lambda p: setattr(p, "tile_rows_adj", 4),  # adjoint variant without a forward one
                    lambda p: (setattr(p, "tile_rows", 4), setattr(p, "tile_rows_adj", 5)),  # no such variant
+                   lambda p: setattr(p, "tile_rows_rec", 4),  # recompute variant without a forward one
                    lambda p: (setattr(p, "tile_rows", 32), setattr(p, "n", (C.c_int32 * 3)(95, 48, 1)))]:
         p = _abi.lks_params.from_buffer_copy(base)
         mutate(p)

@@ -66,10 +66,15 @@ def test_gradient_modes(mode):
     check(tiny_workload("D2Q9", mode=mode), 1e-10, 1e-10, 1e-10)
 
 
-@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q15"])
+@pytest.mark.parametrize("lattice,rows", [("D2Q9", 1), ("D2Q9", 3), ("D3Q15", 32)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_checkpointing_bitwise(lattice, prec):
-    w = tiny_workload(lattice, precision=prec, Nt=47)
+def test_checkpointing_bitwise(lattice, rows, prec):
+    # with the step-kernel variants fixed, every checkpoint mode gives the same bits (the tuner may pick other
+    # variants for the pipelined sqrt sweep, whose results then differ at rounding level); rows = 3 pairs the
+    # two-step launches differently in every mode
+    if rows == 3 and prec == "fp64":
+        pytest.skip("covered in FP32")
+    w = tiny_workload(lattice, precision=prec, Nt=47, tile_rows=rows, **({"shape": (94, 45)} if rows != 32 else {}))
     gamma, knots = draw_gamma(w), draw_knots(w)
     runs = {}
     for ck, extra in [("full", {}), ("sqrt", {}), ("revolve", dict(ckpt_slots=2, seg_len=3)),
