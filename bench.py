@@ -170,22 +170,49 @@ def node_count(w):
     return int(np.prod(w["shape"]))
 
 
-def cpu_baseline(w, sample_steps=60):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload: same grid, first `sample_steps` steps."""
+def sample_workload(w, sample_steps):
+    """The workload's grid over its first `sample_steps` steps; the motion amplitude scales with the horizon so that
+    body speeds stay those of the workload."""
+    return dict(w, Nt=sample_steps, K=min(w["K"], 6), R_t=max(1.0, sample_steps / 4),
+                amp=w["amp"] * sample_steps / w["Nt"])
+
+
+def cpu_baseline(w, sample_steps=60, with_result=False):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: same grid, first `sample_steps` steps.
+    With `with_result`, also its (J, dJ/dgamma, dJ/dknots) for the gradient-error check."""
     import oracle as O  # test infrastructure: only this leg and --impl reference use it
     from tests.helpers import oracle_problem
 
-    # shorter horizon: scale the motion amplitude with it so that body speeds stay those of the workload
-    ws = dict(w, Nt=sample_steps, K=min(w["K"], 6), R_t=max(1.0, sample_steps / 4), amp=w["amp"] * sample_steps / w["Nt"])
+    ws = sample_workload(w, sample_steps)
     P = oracle_problem(ws)
     gamma, knots = draw_gamma(ws), draw_knots(ws)
     t0 = time.perf_counter()
-    O.gradient(P, gamma, knots)
+    res = O.gradient(P, gamma, knots)
     dt = time.perf_counter() - t0
     val = node_count(ws) * sample_steps / dt / 1e9
-    return {"value": val, "unit": "G node-steps/s (fwd+adj)", "cores": 1, "kind": "oracle",
-            "sample": f"{w['name']} grid, first {sample_steps} of {w['Nt']} steps, forward + exact adjoint, numpy FP64, "
-                      f"{dt:.1f} s"}
+    cb = {"value": val, "unit": "G node-steps/s (fwd+adj)", "cores": 1, "kind": "oracle",
+          "sample": f"{w['name']} grid, first {sample_steps} of {w['Nt']} steps, forward + exact adjoint, numpy FP64, "
+                    f"{dt:.1f} s"}
+    return (cb, res) if with_result else cb
+
+
+def gradient_error(w, oracle_result, sample_steps=60):
+    """The CUDA path's J and gradients on the oracle's sample against the oracle (gradients: relative L2; J: both
+    values and the absolute error, since over a short sample the flow may not yet reach the probe and J can be
+    near zero), beside the tolerance the gradients are held to."""
+    from paper_2608_01071_b300 import Solver
+
+    ws = sample_workload(w, sample_steps)
+    s = Solver.from_workload(ws)
+    J = s.forward(draw_gamma(ws), draw_knots(ws))
+    dg, dk = s.adjoint()
+    s.close()
+    Jo, dgo, dko = oracle_result
+    rl2 = lambda a, b: float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+    return {"sample": f"first {sample_steps} steps of the workload (the cpu_baseline sample)",
+            "J": {"oracle": Jo, "cuda": J, "abs_err": abs(J - Jo)},
+            "dgamma_rel_l2": rl2(dg, dgo), "dknots_rel_l2": rl2(dk, dko),
+            "tolerance": {"gradients_rel_l2": 1e-3 if w["precision"] == "fp32" else 1e-10}}
 
 
 def run_reference(args):
@@ -262,13 +289,15 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(args.steps)]
     st_adj, st_rec, st_fwd, launches = [], [], [], 0
     for i in range(args.steps):
         flush.zero_()  # L2 flush between timed iterations (not inside the timed span)
         ev[i][0].record(stream)
-        step()
+        solver.forward_dev(d_gamma, d_knots, d_J, stream=stream)
         ev[i][1].record(stream)
+        solver.adjoint_dev(d_dg, d_dk, stream=stream)
+        ev[i][2].record(stream)
         s = solver.stats()
         st_adj.append((s["ms_adjoint_steps"], s["adjoint_steps"]))
         st_rec.append((s["ms_recompute_steps"], s["recompute_steps"]))
@@ -279,10 +308,13 @@ def run_ours(args):
         dist.barrier()
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
-    ms = [a.elapsed_time(b) for a, b in ev]
+    ms = [a.elapsed_time(c) for a, _, c in ev]
     t_dev = sum(ms) / 1e3
     t_dev = max_over_ranks(t_dev, dist, dev)
     value = job_throughput(world, N, w["Nt"], args.steps, t_dev)
+    # forward-only and adjoint-only (the adjoint includes the recomputation and the chain rules)
+    t_fwd_call = max_over_ranks(sum(a.elapsed_time(b) for a, b, _ in ev) / 1e3, dist, dev)
+    t_adj_call = max_over_ranks(sum(b.elapsed_time(c) for _, b, c in ev) / 1e3, dist, dev)
 
     # roofline of the step kernels from their live CUDA-event durations (spans recorded on the launching
     # streams); algorithmic bytes per node: forward reads and writes the (D+1)-component state, the adjoint reads
@@ -370,11 +402,16 @@ def run_ours(args):
             "gpu_launches": int(launches * world),
             "tile_rows": {"forward": st0["tile_rows_fwd"], "recompute": st0["tile_rows_rec"],
                           "adjoint": st0["tile_rows_adj"]},
+            "forward_only": {"value": job_throughput(world, N, w["Nt"], args.steps, t_fwd_call),
+                             "unit": "G node-steps/s (lks_forward)"},
+            "adjoint_only": {"value": job_throughput(world, N, w["Nt"], args.steps, t_adj_call),
+                             "unit": "G node-steps/s (lks_adjoint, recomputation included)"},
             "clocks": clk,
             "wall_s": t_wall,
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(w)
+            line["cpu_baseline"], ores = cpu_baseline(w, with_result=True)
+            line["grad_error_vs_oracle"] = gradient_error(w, (ores[0], ores[1], ores[2]))
         print(json.dumps(line), flush=True)
     solver.close()
     if dist:
