@@ -205,8 +205,27 @@ int lks_batch_forward_dev(lks_batch* b, const double* const* d_gamma, const doub
                           void* stream);
 int lks_batch_adjoint_dev(lks_batch* b, double* const* d_dJ_dgamma, double* const* d_dJ_dpos, void* stream);
 
+/* Host-pointer variants of the five calls above (same kernels, same layouts; the arrays are host memory).  Each
+ * copies its inputs to device memory allocated for the call, runs the device variant on the default stream,
+ * copies the results back and frees the copies: synchronous, and not for callers that cannot allocate.
+ * lks_projection needs no context; either of out and dout may be NULL (not both). */
+int lks_density_filter(lks_ctx* ctx, const double* in, double* out);
+int lks_density_filter_T(lks_ctx* ctx, const double* in, double* out);
+int lks_projection(int64_t count, double beta, double eta, const double* in, double* out, double* dout);
+int lks_motion_filter(lks_ctx* ctx, const double* knots, double* filtered);
+int lks_motion_filter_T(lks_ctx* ctx, const double* in, double* out);
+int lks_interp_positions(lks_ctx* ctx, const double* filtered, double* s, double* uG);
+int lks_interp_positions_T(lks_ctx* ctx, const double* gs, const double* guG, double* out);
+
 /* Final state (p_Nt, u_Nt) of the last forward, as FP64: p[N], u[d*N] (component-major). Synchronous. */
 int lks_get_state(lks_ctx* ctx, double* p, double* u);
+
+/* Initial state (p_0, u_0) of every following lks_forward, host FP64 in the layout of lks_get_state (p is the
+ * pressure itself, not p - 1/3).  This is the warm start of the periodic approximation (Sec. 3.3): the final
+ * state of one optimisation iteration starts the next.  The values are used as given, wall nodes included.
+ * p = u = NULL restores the default (p = 1/3, u = 0, wall nodes at their wall velocity).  Discards captured
+ * graphs; the next lks_adjoint needs a new lks_forward.  Synchronous. */
+int lks_set_initial_state(lks_ctx* ctx, const double* p, const double* u);
 
 /* Per-step motion sensitivities of the last adjoint, dJ/ds_n and dJ/du^G_n, each (Nt+1) x d. Synchronous. */
 int lks_get_step_sensitivities(lks_ctx* ctx, double* dJ_ds, double* dJ_duG);

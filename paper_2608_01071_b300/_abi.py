@@ -96,6 +96,14 @@ PROTOTYPES = {
     "lks_interp_positions_dev": (C.c_int, [_P, _P, _P, _P, _P]),
     "lks_interp_positions_T_dev": (C.c_int, [_P, _P, _P, _P, _P]),
     "lks_get_state": (C.c_int, [_P, _D, _D]),
+    "lks_set_initial_state": (C.c_int, [_P, _D, _D]),
+    "lks_density_filter": (C.c_int, [_P, _D, _D]),
+    "lks_density_filter_T": (C.c_int, [_P, _D, _D]),
+    "lks_projection": (C.c_int, [C.c_int64, C.c_double, C.c_double, _D, _D, _D]),
+    "lks_motion_filter": (C.c_int, [_P, _D, _D]),
+    "lks_motion_filter_T": (C.c_int, [_P, _D, _D]),
+    "lks_interp_positions": (C.c_int, [_P, _D, _D, _D]),
+    "lks_interp_positions_T": (C.c_int, [_P, _D, _D, _D]),
     "lks_get_step_sensitivities": (C.c_int, [_P, _D, _D]),
     "lks_get_stats": (C.c_int, [_P, C.POINTER(lks_stats)]),
     "lks_set_timing": (C.c_int, [_P, C.c_int]),

@@ -140,6 +140,15 @@ class Solver:
         u = np.stack([u[a * N:(a + 1) * N].reshape(self.shape[::-1]).T for a in range(self.d)])
         return p, u
 
+    def set_initial_state(self, p=None, u=None):
+        """Initial state of the following forwards (arrays as returned by state()); None restores the default."""
+        if p is None and u is None:
+            self._check(self.lib.lks_set_initial_state(self.h, None, None))
+            return
+        pf = np.ascontiguousarray(np.asarray(p, dtype=np.float64).T).ravel()
+        uf = np.concatenate([np.ascontiguousarray(np.asarray(u[a], dtype=np.float64).T).ravel() for a in range(self.d)])
+        self._check(self.lib.lks_set_initial_state(self.h, _dptr(pf), _dptr(uf)))
+
     def step_sensitivities(self):
         gs = np.zeros((self.Nt + 1, self.d))
         gu = np.zeros((self.Nt + 1, self.d))
@@ -182,6 +191,51 @@ class Solver:
     def interp_positions_T_dev(self, d_gs, d_guG, d_out, stream=None):
         self._check(self.lib.lks_interp_positions_T_dev(self.h, C.c_void_p(d_gs.data_ptr()), C.c_void_p(d_guG.data_ptr()),
                                                         C.c_void_p(d_out.data_ptr()), _stream_ptr(stream)))
+
+
+    # host-array calls (numpy float64; design arrays flat x-fastest, knots and positions row-major) ---------
+    def _ptr(self, a):
+        return a.ctypes.data_as(C.POINTER(C.c_double))
+
+    def density_filter(self, x, transpose=False):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        out = np.empty_like(x)
+        f = self.lib.lks_density_filter_T if transpose else self.lib.lks_density_filter
+        self._check(f(self.h, self._ptr(x), self._ptr(out)))
+        return out
+
+    def motion_filter(self, x, transpose=False):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        out = np.empty_like(x)
+        f = self.lib.lks_motion_filter_T if transpose else self.lib.lks_motion_filter
+        self._check(f(self.h, self._ptr(x), self._ptr(out)))
+        return out
+
+    def interp_positions(self, filtered, Nt):
+        filtered = np.ascontiguousarray(filtered, dtype=np.float64)
+        s = np.empty((Nt + 1, filtered.shape[1]))
+        uG = np.empty_like(s)
+        self._check(self.lib.lks_interp_positions(self.h, self._ptr(filtered), self._ptr(s), self._ptr(uG)))
+        return s, uG
+
+    def interp_positions_T(self, gs, guG, K):
+        gs = np.ascontiguousarray(gs, dtype=np.float64)
+        guG = np.ascontiguousarray(guG, dtype=np.float64)
+        out = np.empty((K, gs.shape[1]))
+        self._check(self.lib.lks_interp_positions_T(self.h, self._ptr(gs), self._ptr(guG), self._ptr(out)))
+        return out
+
+
+def projection(x, beta, eta):
+    """Heaviside projection and its derivative of a host array (through the library's kernel)."""
+    lib = _abi.load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out, dout = np.empty_like(x), np.empty_like(x)
+    p = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    rc = lib.lks_projection(x.size, beta, eta, p(x), p(out), p(dout))
+    if rc != 0:
+        raise LKSError(rc, lib.lks_strerror(rc).decode())
+    return out, dout
 
 
 def projection_dev(d_in, d_out, d_dout, beta, eta, stream=None):

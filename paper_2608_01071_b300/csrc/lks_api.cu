@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <array>
+#include <initializer_list>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -105,6 +106,7 @@ struct Engine {
                         long long kstride, double* dkref, cudaStream_t s) = 0;
     virtual void kappa_ref(const DesignGeom& dg, const double* gt, double* gb, double* k64, void* k, cudaStream_t s) = 0;
     virtual void init_state(const Geom& g, void* st, cudaStream_t s) = 0;
+    virtual void import_state(const Geom& g, const double* p, const double* u, void* st, cudaStream_t s) = 0;
     virtual void init_adjoint(const Geom& g, void* lam, cudaStream_t s) = 0;
     virtual void export_state(const Geom& g, const void* st, double* p, double* u, cudaStream_t s) = 0;
 };
@@ -175,6 +177,10 @@ struct EngineCommon : Engine {
     }
     void init_state(const Geom& g, void* st, cudaStream_t s) override {
         init_state_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, (T*)st);
+        LKS_LAUNCHED();
+    }
+    void import_state(const Geom& g, const double* p, const double* u, void* st, cudaStream_t s) override {
+        import_state_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, p, u, (T*)st);
         LKS_LAUNCHED();
     }
     void init_adjoint(const Geom& g, void* lam, cudaStream_t s) override {
@@ -462,6 +468,8 @@ struct lks_ctx {
     long long box_step = 0;     // elements per step in d_boxbuf
     void* d_fac = nullptr;      // two buffers of Lmax steps x Fbn: 1 / (1 + kappa) on the footprint box
     bool throughput = false;    // instance of a batch: tune for throughput (see create_ctx)
+    void* d_init = nullptr;     // caller's initial state (lks_set_initial_state), in the state layout
+    bool custom_init = false;
     // step-kernel variants of the forward sweep, the recomputation and the adjoint steps (see choose_variants)
     int rows_fwd_sweep = 0, rows_rec = 0, rows_adj = 0;
     // tuner results: fastest forward / adjoint variant alone, and the fastest one-step pair run side by side
@@ -1182,7 +1190,10 @@ void forward_body(lks_ctx* c, cudaStream_t s) {
     } else {
         for (int m = 1; m < c->M; ++m) store[m] = 1;
     }
-    c->eng->init_state(c->g, c->slot[0], s);
+    if (c->custom_init)
+        LKS_CUDA(cudaMemcpyAsync(c->slot[0], c->d_init, c->state_bytes, cudaMemcpyDeviceToDevice, s));
+    else
+        c->eng->init_state(c->g, c->slot[0], s);
     c->launches++;
     PingPong pp{c};
     cudaEvent_t e0 = span_begin(c, s);
@@ -1490,6 +1501,48 @@ thread_local std::string g_create_err;
 // ------------------------------------------------------------------------------------------------
 // C ABI
 // ------------------------------------------------------------------------------------------------
+// Host-pointer variants of the filter calls: the same kernels on device copies made for the call (allocated and
+// freed here, on the legacy default stream), synchronous.
+namespace {
+struct DevScratch {
+    double* p = nullptr;
+    ~DevScratch() {
+        if (p) cudaFree(p);
+    }
+};
+// ins / outs: host arrays and their lengths; dev(inputs..., outputs...) runs the device variant on stream 0
+template <typename F>
+void host_roundtrip(std::initializer_list<std::pair<const double*, size_t>> ins,
+                    std::initializer_list<std::pair<double*, size_t>> outs, F&& dev) {
+    size_t total = 0;
+    for (const auto& a : ins) {
+        if (!a.first) throw LksError{LKS_EINVAL, "null pointer"};
+        total += a.second;
+    }
+    for (const auto& a : outs) {
+        if (!a.first) throw LksError{LKS_EINVAL, "null pointer"};
+        total += a.second;
+    }
+    DevScratch b;
+    LKS_CUDA(cudaMalloc(&b.p, std::max<size_t>(total, 1) * 8));
+    std::vector<double*> d;
+    double* q = b.p;
+    for (const auto& a : ins) {
+        LKS_CUDA(cudaMemcpy(q, a.first, a.second * 8, cudaMemcpyHostToDevice));
+        d.push_back(q);
+        q += a.second;
+    }
+    for (const auto& a : outs) {
+        d.push_back(q);
+        q += a.second;
+    }
+    const int rc = dev(d);
+    if (rc != LKS_OK) throw LksError{rc, "device call failed"};
+    size_t k = ins.size();
+    for (const auto& a : outs) LKS_CUDA(cudaMemcpy(a.first, d[k++], a.second * 8, cudaMemcpyDeviceToHost));
+}
+}  // namespace
+
 extern "C" {
 
 int lks_default_params(lks_params* p) {
@@ -1713,6 +1766,86 @@ int lks_interp_positions_T_dev(lks_ctx* c, const double* gs, const double* guG, 
     });
 }
 
+
+int lks_density_filter(lks_ctx* c, const double* in, double* out) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        host_roundtrip({{in, (size_t)c->nd}}, {{out, (size_t)c->nd}},
+                       [&](std::vector<double*>& d) { return lks_density_filter_dev(c, d[0], d[1], nullptr); });
+    });
+}
+
+int lks_density_filter_T(lks_ctx* c, const double* in, double* out) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        host_roundtrip({{in, (size_t)c->nd}}, {{out, (size_t)c->nd}},
+                       [&](std::vector<double*>& d) { return lks_density_filter_T_dev(c, d[0], d[1], nullptr); });
+    });
+}
+
+int lks_projection(int64_t count, double beta, double eta, const double* in, double* out, double* dout) {
+    if (count < 0 || !in || (!out && !dout)) return LKS_EINVAL;
+    if (count == 0) return LKS_OK;
+    try {
+        std::vector<double> unused;
+        double* o = out;
+        double* od = dout;
+        if (!o) {
+            unused.resize(count);
+            o = unused.data();
+        }
+        if (!od) {
+            if (unused.empty()) unused.resize(count);
+            od = unused.data();
+        }
+        host_roundtrip({{in, (size_t)count}}, {{o, (size_t)count}, {od, (size_t)count}}, [&](std::vector<double*>& d) {
+            return lks_projection_dev(count, beta, eta, d[0], d[1], d[2], nullptr);
+        });
+        return LKS_OK;
+    } catch (const LksError& e) {
+        return e.code;
+    } catch (...) {
+        return LKS_ENOMEM;
+    }
+}
+
+int lks_motion_filter(lks_ctx* c, const double* knots, double* filtered) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        const size_t n = (size_t)c->prm.K * c->D;
+        host_roundtrip({{knots, n}}, {{filtered, n}},
+                       [&](std::vector<double*>& d) { return lks_motion_filter_dev(c, d[0], d[1], nullptr); });
+    });
+}
+
+int lks_motion_filter_T(lks_ctx* c, const double* in, double* out) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        const size_t n = (size_t)c->prm.K * c->D;
+        host_roundtrip({{in, n}}, {{out, n}},
+                       [&](std::vector<double*>& d) { return lks_motion_filter_T_dev(c, d[0], d[1], nullptr); });
+    });
+}
+
+int lks_interp_positions(lks_ctx* c, const double* filtered, double* s, double* uG) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        const size_t nk = (size_t)c->prm.K * c->D, ns = (size_t)(c->prm.Nt + 1) * c->D;
+        host_roundtrip({{filtered, nk}}, {{s, ns}, {uG, ns}},
+                       [&](std::vector<double*>& d) { return lks_interp_positions_dev(c, d[0], d[1], d[2], nullptr); });
+    });
+}
+
+int lks_interp_positions_T(lks_ctx* c, const double* gs, const double* guG, double* out) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        const size_t nk = (size_t)c->prm.K * c->D, ns = (size_t)(c->prm.Nt + 1) * c->D;
+        host_roundtrip({{gs, ns}, {guG, ns}}, {{out, nk}}, [&](std::vector<double*>& d) {
+            return lks_interp_positions_T_dev(c, d[0], d[1], d[2], nullptr);
+        });
+    });
+}
+
 int lks_get_state(lks_ctx* c, double* p, double* u) {
     if (!c) return LKS_EINVAL;
     return guard(c, [&] {
@@ -1759,6 +1892,28 @@ int lks_set_timing(lks_ctx* c, int enable) {
             }
             LKS_CUDA(cudaEventCreate(&c->ev_end));
         }
+    });
+}
+
+int lks_set_initial_state(lks_ctx* c, const double* p, const double* u) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if ((p == nullptr) != (u == nullptr)) throw LksError{LKS_EINVAL, "p and u must both be given or both NULL"};
+        drop_graphs(c);  // the captured forward starts from the previous initial state
+        c->have_forward = false;
+        if (!p) {
+            c->custom_init = false;
+            return;
+        }
+        const long long N = c->g.N;
+        if (!c->d_init) c->d_init = dalloc(c, c->state_bytes);
+        DevScratch b;
+        LKS_CUDA(cudaMalloc(&b.p, (size_t)(c->D + 1) * N * 8));
+        LKS_CUDA(cudaMemcpy(b.p, p, N * 8, cudaMemcpyHostToDevice));
+        LKS_CUDA(cudaMemcpy(b.p + N, u, (size_t)c->D * N * 8, cudaMemcpyHostToDevice));
+        c->eng->import_state(c->g, b.p, b.p + N, c->d_init, 0);
+        LKS_CUDA(cudaDeviceSynchronize());
+        c->custom_init = true;
     });
 }
 

@@ -300,6 +300,14 @@ __global__ void init_adjoint_kernel(Geom g, T* __restrict__ lam) {
 
 // FP64 copy of a state (p = p' + 1/3) for the host.
 template <typename T, int D>
+__global__ void import_state_kernel(Geom g, const double* __restrict__ p, const double* __restrict__ u, T* __restrict__ st) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    st[i] = (T)(p[i] - 1.0 / 3.0);
+    for (int c = 0; c < D; ++c) st[(1 + c) * g.N + i] = (T)u[c * g.N + i];
+}
+
+template <typename T, int D>
 __global__ void export_state_kernel(Geom g, const T* __restrict__ st, double* __restrict__ p, double* __restrict__ u) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= g.N) return;

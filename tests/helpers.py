@@ -15,12 +15,13 @@ def oracle_problem(w, **kw):
     return P
 
 
-def oracle_run(w, gamma, knots):
-    """J, dJ/dgamma, dJ/dknots and the final state (p, u) from the oracle."""
+def oracle_run(w, gamma, knots, state0=None):
+    """J, dJ/dgamma, dJ/dknots and the final state (p, u) from the oracle (state0: initial (p, u), or the
+    default)."""
     P = oracle_problem(w)
     kref, gt, gb = O.design_to_kref(P, gamma)
     s, uG = O.positions(knots, P.Nt, P.R_t)
-    J, states = O.forward(P, kref, s, uG, store=True)
+    J, states = O.forward(P, kref, s, uG, store=True, state0=state0)
     g_kref, g_s, g_uG = O.adjoint(P, kref, s, uG, states)
     g_kr = O.strip_margin(g_kref, P.margin)
     g_gb = g_kr * O.kappa_ref_deriv(gb, P.kappa_max, P.q)
