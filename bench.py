@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nt", type=int, default=0, help="override the horizon (short runs for profiler captures)")
+    ap.add_argument("--optimize", type=int, default=0, help="also run this many projected-gradient optimisation "
+                    "iterations (gamma step 0.05, position step 0.5 cell, normalised) and report J and s/iteration")
     ap.add_argument("--tile-rows", default="", help="force step-kernel variants instead of autotuning: F, F,A or "
                     "F,A,R (tile_rows codes of the forward sweep, the adjoint and the recomputation)")
     return ap.parse_args()
@@ -409,6 +411,15 @@ def run_ours(args):
             "clocks": clk,
             "wall_s": t_wall,
         }
+        if args.optimize > 0:
+            from paper_2608_01071_b300.optimize import optimize
+
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, hist = optimize(solver, gamma, knots, iters=args.optimize, pos_bound=w["amp"])
+            dt = time.perf_counter() - t0
+            line["optimize"] = {"iters": args.optimize, "s_per_iter": dt / args.optimize, "J": hist,
+                                "gamma_step": 0.05, "pos_step_cells": 0.5, "pos_bound_cells": w["amp"]}
         if not args.no_cpu_baseline:
             line["cpu_baseline"], ores = cpu_baseline(w, with_result=True)
             line["grad_error_vs_oracle"] = gradient_error(w, (ores[0], ores[1], ores[2]))

@@ -179,6 +179,14 @@ int lks_density_filter_T_dev(lks_ctx* ctx, const double* d_in, double* d_out, vo
 int lks_projection_dev(int64_t count, double beta, double eta, const double* d_in, double* d_out,
                        double* d_dout, void* stream);
 
+/* One normalised projected-gradient step of an optimiser loop around lks_forward / lks_adjoint (the ascent step
+ * of the plain optimisation driver; Sec. 3 uses MMA, which is not part of this library):
+ *     x_i <- min(hi, max(lo, x_i + step * g_i / max_j |g_j|)),  i < count,
+ * with x left unchanged when g is zero everywhere.  Device pointers, on `stream`; lo <= hi and a finite step are
+ * required (LKS_EINVAL otherwise).  One block of the GPU does the work: meant for design grids and knot arrays. */
+int lks_gradient_step_dev(int64_t count, double step, const double* d_g, double* d_x, double lo, double hi,
+                          void* stream);
+
 /* Temporal motion filter of Eq. chi_filtered over the knots (K x d) and its transpose. */
 int lks_motion_filter_dev(lks_ctx* ctx, const double* d_knots, double* d_filtered, void* stream);
 int lks_motion_filter_T_dev(lks_ctx* ctx, const double* d_in, double* d_out, void* stream);

@@ -91,6 +91,7 @@ PROTOTYPES = {
     "lks_density_filter_dev": (C.c_int, [_P, _P, _P, _P]),
     "lks_density_filter_T_dev": (C.c_int, [_P, _P, _P, _P]),
     "lks_projection_dev": (C.c_int, [C.c_int64, C.c_double, C.c_double, _P, _P, _P, _P]),
+    "lks_gradient_step_dev": (C.c_int, [C.c_int64, C.c_double, _P, _P, C.c_double, C.c_double, _P]),
     "lks_motion_filter_dev": (C.c_int, [_P, _P, _P, _P]),
     "lks_motion_filter_T_dev": (C.c_int, [_P, _P, _P, _P]),
     "lks_interp_positions_dev": (C.c_int, [_P, _P, _P, _P, _P]),

@@ -1722,6 +1722,13 @@ int lks_density_filter_T_dev(lks_ctx* c, const double* in, double* out, void* st
     });
 }
 
+int lks_gradient_step_dev(int64_t count, double step, const double* g, double* x, double lo, double hi, void* stream) {
+    if (count < 0 || !g || !x || !(lo <= hi) || !std::isfinite(step)) return LKS_EINVAL;
+    if (count == 0) return LKS_OK;
+    gradient_step_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(count, step, g, x, lo, hi);
+    return cudaGetLastError() == cudaSuccess ? LKS_OK : LKS_ECUDA;
+}
+
 int lks_projection_dev(int64_t count, double beta, double eta, const double* in, double* out, double* dout,
                        void* stream) {
     if (count < 0 || !in || !(beta >= 0.0) || !(eta > 0.0 && eta < 1.0)) return LKS_EINVAL;

@@ -315,4 +315,30 @@ __global__ void export_state_kernel(Geom g, const T* __restrict__ st, double* __
     for (int c = 0; c < D; ++c) u[c * g.N + i] = (double)st[(1 + c) * g.N + i];
 }
 
+
+// One normalised projected-gradient step of the optimiser driver: x_i <- min(hi, max(lo, x_i + step g_i / max|g|))
+// (x unchanged where g = 0 everywhere).  A single block: the max-reduction, then the update, so that no scratch
+// memory is needed.  Launch with 1024 threads.
+__global__ void __launch_bounds__(1024) gradient_step_kernel(long long n, double step, const double* __restrict__ g,
+                                                             double* __restrict__ x, double lo, double hi) {
+    __shared__ double red[32];
+    double m = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(g[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) red[0] = m;
+    }
+    __syncthreads();
+    const double gmax = red[0];
+    if (!(gmax > 0.0)) return;
+    const double a = step / gmax;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) x[i] = fmin(hi, fmax(lo, x[i] + a * g[i]));
+}
+
 }  // namespace lks
