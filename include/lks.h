@@ -71,12 +71,17 @@ enum { LKS_MODE_JOINT = 0, LKS_MODE_SHAPE = 1, LKS_MODE_MOTION = 2 };
  *  seg_len        recompute-segment length for REVOLVE (0 = automatic).
  *  mode           which gradients lks_adjoint produces (the others are returned as zeros).
  *  u_crit         stability limit on |u| checked every forward step (<= 0 disables); LKS_EUNSTABLE.
- *  tile_rows      step-kernel variant.  D2Q9: 1 or 2 = row tiles of 28 x 8 or 28 x 16 nodes staged in shared
- *                 memory; 3 = forward steps taken two per launch on 24 x 8 row tiles (adjoint on 28 x 8 row
- *                 tiles); 4, 8 or 16 (16: LKS_FP32 only) = warp-column kernels with that many grid rows per warp;
- *                 32 or 64 = vectorised warp columns (two columns per lane, even n[0] only) with that many rows.  D3Q15: 1 = shared-memory tiles
- *                 of 32 x 4 x 4 nodes; 8 or 16 = z-marching kernels with that many planes per block.
- *                 0 = autotune at lks_create (times every choice on the context's buffers; cached per process).
+ *  tile_rows      step-kernel variant of the forward sweep.  D2Q9: 1 or 2 = row tiles of 28 x 8 or 28 x 16
+ *                 nodes staged in shared memory; 3 = two steps per launch on 24 x 8 row tiles; 4, 8 or 16 (16:
+ *                 LKS_FP32 only) = warp-column kernels with that many grid rows per warp; 32 or 64 = vectorised
+ *                 warp columns (two columns per lane, even n[0] only) with that many rows.  D3Q15: 1 =
+ *                 shared-memory tiles of 32 x 4 x 4 nodes; 8 or 16 = z-marching kernels with that many planes per
+ *                 block; 32 or 64 = separable z-marching kernels with 16 or 32 planes of 32 x 8 columns; 96 =
+ *                 separable forward with 16 planes of 32 x 16 columns (forward only).
+ *                 0 = autotune at lks_create: times every choice on the context's buffers, then the fastest
+ *                 one-step forward/adjoint pairs launched side by side; the forward sweep takes the fastest
+ *                 forward, the pipelined sqrt(N) sweep and batch instances the fastest side-by-side pair
+ *                 (cached per process; lks_get_stats reports the choices).
  *  tile_rows_adj  adjoint step-kernel variant when tile_rows != 0 (same codes); 0 = tile_rows.
  *  tile_rows_rec  forward variant of the recomputation in lks_adjoint when tile_rows != 0; 0 = tile_rows.
  *                 tile_rows_adj and tile_rows_rec must be 0 when tile_rows = 0 (all three autotuned).
