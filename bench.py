@@ -430,16 +430,40 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def shard_instances(sizes, rank, world):
+    """Instances of a study for one rank: largest first, each to the rank with the fewest nodes so far (ties to the
+    lower rank).  Every rank computes the same assignment; the shards partition the study."""
+    load = [0] * world
+    owner = [0] * len(sizes)
+    for i in sorted(range(len(sizes)), key=lambda i: (-sizes[i], i)):
+        r = min(range(world), key=lambda r: (load[r], r))
+        owner[i] = r
+        load[r] += sizes[i]
+    return [i for i in range(len(sizes)) if owner[i] == rank]
+
+
 def run_batched(args):
-    """The batched parameter study: 32 uneven D2Q9 instances, forward + adjoint of all of them per step."""
+    """The batched parameter study: 32 uneven D2Q9 instances, forward + adjoint of all of them per step.  Under
+    torchrun the instances are sharded over the ranks (independent problems: no collective on the data path), and
+    the throughput counts the whole study over the slowest rank's time."""
     import torch
 
     from paper_2608_01071_b300 import Batch
     from paper_2608_01071_b300.workloads import batched_study
 
-    ws = batched_study()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl")
+    study = batched_study()
+    nodes_all = sum(int(np.prod(w["shape"])) for w in study)
+    ws = [study[i] for i in shard_instances([int(np.prod(w["shape"])) for w in study], rank, world)]
     b = Batch(ws)
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", local)
     gam = [torch.tensor(np.ascontiguousarray(draw_gamma(w).T), device=dev) for w in ws]
     kn = [torch.tensor(draw_knots(w), device=dev) for w in ws]
     J = torch.empty(len(ws), dtype=torch.float64, device=dev)
@@ -454,8 +478,11 @@ def run_batched(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    clocks = Clocks(0)
+    clocks = Clocks(local)
     clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
     ms = []
     for _ in range(args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -464,22 +491,28 @@ def run_batched(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
+    if dist:
+        dist.barrier()
     clk = clocks.stop()
-    nodes = sum(int(np.prod(w["shape"])) for w in ws)
-    t = sum(ms) / 1e3
-    value = nodes * ws[0]["Nt"] * args.steps / t / 1e9
-    launches = sum(b.context_stats(i)["kernel_launches"] for i in range(len(ws)))
+    t = max_over_ranks(sum(ms) / 1e3, dist, dev)
+    value = nodes_all * study[0]["Nt"] * args.steps / t / 1e9
+    launches = max_over_ranks(sum(b.context_stats(i)["kernel_launches"] for i in range(len(ws))), dist, dev)
     tiles = sorted({(tuple(w["shape"]), b.context_stats(i)["tile_rows_fwd"], b.context_stats(i)["tile_rows_adj"])
                     for i, w in enumerate(ws)})
-    line = {"metric": "fwd+adjoint LKS GLUPS", "value": value, "unit": "G node-steps/s (fwd+adj)", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batched_study_32xD2Q9", "instances": len(ws), "Nt": ws[0]["Nt"],
-                       "nodes_total": nodes, "modes": "11 shape / 11 motion / 10 joint",
-                       "tiles": [list(x[0]) + [x[1], x[2]] for x in tiles]},
-            "gpu_launches": launches * args.steps, "clocks": clk}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        line = {"metric": "fwd+adjoint LKS GLUPS", "value": value, "unit": "G node-steps/s (fwd+adj)", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "batched_study_32xD2Q9", "instances": len(study), "Nt": study[0]["Nt"],
+                           "nodes_total": nodes_all, "modes": "11 shape / 11 motion / 10 joint",
+                           "parallelism": f"instances sharded over {world} GPU(s) by node count",
+                           "tiles": [list(x[0]) + [x[1], x[2]] for x in tiles]},
+                "gpu_launches": int(launches * args.steps * world), "clocks": clk}
+        print(json.dumps(line), flush=True)
     b.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def main():

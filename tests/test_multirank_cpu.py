@@ -52,3 +52,42 @@ def test_single_process_identity():
     import bench
 
     assert bench.max_over_ranks(3.25, None, "cpu") == 3.25
+
+
+def shard_worker(rank, world, port, q):
+    import sys
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import numpy as np
+
+    import bench
+    from paper_2608_01071_b300.workloads import batched_study
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    sizes = [int(np.prod(w["shape"])) for w in batched_study()]
+    mine = bench.shard_instances(sizes, rank, world)
+    got = [None] * world
+    dist.all_gather_object(got, mine)
+    q.put((rank, got, sizes))
+    dist.destroy_process_group()
+
+
+def test_two_rank_instance_sharding_gloo():
+    # the batched study split over two ranks: every rank derives the same partition, shards are disjoint, cover
+    # all instances, and their node counts differ by at most one instance's size
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=shard_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in range(2)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (_, got0, sizes), (_, got1, _) = res
+    assert got0 == got1
+    a, b = got0
+    assert not set(a) & set(b) and sorted(a + b) == list(range(len(sizes)))
+    la, lb = sum(sizes[i] for i in a), sum(sizes[i] for i in b)
+    assert abs(la - lb) <= max(sizes)
