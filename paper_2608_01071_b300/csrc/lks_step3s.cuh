@@ -12,8 +12,9 @@
 // node this needs 6 stored fields and 36 shared-memory reads, against 15 stored weighted equilibria and 15
 // reads in the direct form, and no equilibrium is evaluated on the halo more than once per plane.
 //
-// A block owns TX x TY columns and ZB planes; shared memory holds a ring of three raw planes (p', u on the
-// halo-2 region) and one plane of fields on the halo-1 region.  Each thread evaluates the fields of its own
+// A block owns TX x TY columns and ZB planes; shared memory holds a ring of five raw planes (p', u on the
+// halo-2 region, filled by asynchronous copies three planes ahead of use) and one plane of fields on the halo-1
+// region.  Each thread evaluates the fields of its own
 // column (kept in registers for the z recurrence) and at most one node of the halo-1 ring, carrying the
 // velocity of the planes below and at its node in registers so that only in-plane neighbours come from
 // shared memory.
@@ -36,7 +37,19 @@ struct Sep3 {
 
 template <typename T, int TY>
 __host__ __device__ constexpr size_t smem3s_fwd() {
-    return sizeof(T) * (3 * 4 * Sep3<TY>::NS + 6 * Sep3<TY>::NM);
+    return sizeof(T) * (5 * 4 * Sep3<TY>::NS + 6 * Sep3<TY>::NM);
+}
+
+// Asynchronous global-to-shared copy of one element (cp.async, completion tracked by commit groups).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // Halo-1 coordinates (i, j) of ring node r: row j = 0, row j = MY - 1, column i = 0, column i = MX - 1.
@@ -64,8 +77,8 @@ __global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 3 : 1) fwd3s_kernel(Ge
     using R = Sep3<TY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[R::NT / 32];
-    T* raw = reinterpret_cast<T*>(smem_raw);  // [3 slots][p, ux, uy, uz][NS]
-    T* fld = raw + 3 * 4 * R::NS;             // [Q, Txy, Txz, Tyz, phi_x, phi_y][NM]
+    T* raw = reinterpret_cast<T*>(smem_raw);  // [5 slots][p, ux, uy, uz][NS]
+    T* fld = raw + 5 * 4 * R::NS;             // [Q, Txy, Txz, Tyz, phi_x, phi_y][NM]
     T* fQ = fld;
     T* fXY = fld + R::NM;
     T* fXZ = fld + 2 * R::NM;
@@ -103,43 +116,35 @@ __global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 3 : 1) fwd3s_kernel(Ge
     }
     pdl_wait_then_release();
 
-    T pre[R::PER][4];
-    auto fetch = [&](int k) {
+    // raw planes arrive by asynchronous copies into a ring of five slots, three planes ahead of use (plane k in
+    // slot (k - z0 + 2) mod 5): no registers hold them in flight and no shared-memory stores are issued for them
+    auto slot_of = [&](int k) { return raw + ((k - z0 + 2) % 5) * 4 * R::NS; };
+    auto issue = [&](int k) {
+        T* dst = slot_of(k);
         const long long base = plane * wrap(k, nz);
-#pragma unroll
-        for (int e = 0; e < R::PER; ++e) {
-            if (tid + e * R::NT < R::NS) {
-#pragma unroll
-                for (int f = 0; f < 4; ++f) pre[e][f] = a.in[f * N + base + off[e]];
-            }
-        }
-    };
-    auto store = [&](int k) {
-        T* dst = raw + ring3(k) * 4 * R::NS;
 #pragma unroll
         for (int e = 0; e < R::PER; ++e) {
             const int l = tid + e * R::NT;
             if (l < R::NS) {
 #pragma unroll
-                for (int f = 0; f < 4; ++f) dst[f * R::NS + l] = pre[e][f];
+                for (int f = 0; f < 4; ++f) cp_async<sizeof(T)>(dst + f * R::NS + l, a.in + f * N + base + off[e]);
             }
         }
+        cp_async_commit();
     };
-    fetch(z0 - 2);
-    store(z0 - 2);
-    fetch(z0 - 1);
-    store(z0 - 1);
-    fetch(z0);
-    store(z0);
-    fetch(z0 + 1);
+    issue(z0 - 2);
+    issue(z0 - 1);
+    issue(z0);
+    issue(z0 + 1);
+    cp_async_wait<0>();
     __syncthreads();
 
     // velocity of the field nodes at the plane below (um) and at the plane (uc), and p' at the plane
     T um[2][3], uc[2][3], pc[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-        const T* rb = raw + ring3(z0 - 2) * 4 * R::NS + rrow[s];
-        const T* rc = raw + ring3(z0 - 1) * 4 * R::NS + rrow[s];
+        const T* rb = slot_of(z0 - 2) + rrow[s];
+        const T* rc = slot_of(z0 - 1) + rrow[s];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             um[s][c] = rb[(1 + c) * R::NS];
@@ -156,10 +161,6 @@ __global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 3 : 1) fwd3s_kernel(Ge
     const int xs2 = P.xs[2];
     const T uG0 = pose_uG<T>(P, 0), uG1 = pose_uG<T>(P, 1), uG2 = pose_uG<T>(P, 2);
     const bool colbox = col && bx >= 0 && by >= 0;
-    // ring slots of planes k, k + 1, k + 2 (k = z0 - 1 first), rotated every plane
-    T* sk = raw + ring3(z0 - 1) * 4 * R::NS;
-    T* sn = raw + ring3(z0) * 4 * R::NS;
-    T* sf = raw + ring3(z0 + 1) * 4 * R::NS;
     const T w0 = (T)(2.0 / 9.0), wf = (T)(1.0 / 9.0), wc = (T)(1.0 / 72.0), third = (T)(1.0 / 3.0);
     // partial streamed moments (p*, u*) of the plane below the current one and of the current plane
     T accM[4] = {0, 0, 0, 0}, accC[4] = {0, 0, 0, 0};
@@ -168,9 +169,17 @@ __global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 3 : 1) fwd3s_kernel(Ge
 
 #pragma unroll 1
     for (int k = z0 - 1; k <= z0 + ZB; ++k) {
+        // plane k + 3 into the slot of plane k - 2 (read last two iterations ago); plane k + 1 has arrived once
+        // at most the two newest copy groups are pending (empty groups keep the count at the end of the run)
+        if (k + 3 <= z0 + ZB + 1)
+            issue(k + 3);
+        else
+            cp_async_commit();
+        cp_async_wait<2>();
+        __syncthreads();
         // (A) fields of plane k at the field nodes
-        const T* rk = sk;
-        const T* rn = sn;
+        const T* rk = slot_of(k);
+        const T* rn = slot_of(k + 1);
         T sig0 = 0, phz0 = 0, uz0 = 0;
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
@@ -302,23 +311,6 @@ __global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 3 : 1) fwd3s_kernel(Ge
             accC[2] = dnY;
             accC[3] = dnZ;
         }
-        // next raw plane into the slot of plane k - 1 (no longer read), prefetch the one after
-        if (k + 2 <= z0 + ZB + 1) {
-#pragma unroll
-            for (int e = 0; e < R::PER; ++e) {
-                const int l = tid + e * R::NT;
-                if (l < R::NS) {
-#pragma unroll
-                    for (int f = 0; f < 4; ++f) sf[f * R::NS + l] = pre[e][f];
-                }
-            }
-        }
-        if (k + 3 <= z0 + ZB + 1) fetch(k + 3);
-        T* t = sk;
-        sk = sn;
-        sn = sf;
-        sf = t;
-        __syncthreads();
     }
     if (unstable) atomicOr(a.flag, 1u);
     if (a.jslot != nullptr) {
