@@ -95,6 +95,7 @@ class Problem:
     probe_lo: tuple = ()              # objective box O_target, inclusive lower corner
     probe_hi: tuple = ()              # exclusive upper corner
     direction: tuple = ()             # n of Eq. objective1
+    phi_var: float = 0.0              # phi of Eq. objective1: weight of the variance V in J1 = E - phi V
     wall_velocity: dict = field(default_factory=dict)  # {(axis, side): vector}; side 0 = plane 0, 1 = plane n-1
 
     @property
@@ -504,19 +505,38 @@ def positions(knots, Nt, R_t):
 
 
 def probe_weights(prob: Problem):
-    """phi(x) = n 1_O(x) / (Nt |O|): d J / d u_n(x) for every step n >= 1 (Eq. objective1 with phi_V = 0).
+    """phi(x) = n 1_O(x) / (Nt |O|): d E / d u_n(x) for every step n >= 1 (E of Eq. objective1).
 
     O excludes wall nodes.
     """
+    box = probe_mean_weights(prob)
+    phi = np.zeros((prob.d,) + prob.shape)
+    for a in range(prob.d):
+        phi[a] = box * prob.direction[a]
+    return phi
+
+
+def probe_mean_weights(prob: Problem):
+    """1_O(x) / (Nt |O|): the weight of one node and step in the space-time means of Eq. objective1."""
     mask, _ = wall_mask(prob)
     box = np.zeros(prob.shape, dtype=bool)
     box[tuple(slice(lo, hi) for lo, hi in zip(prob.probe_lo, prob.probe_hi))] = True
     box &= ~mask
     count = int(box.sum())
-    phi = np.zeros((prob.d,) + prob.shape)
-    for a in range(prob.d):
-        phi[a] = np.where(box, prob.direction[a], 0.0) / (prob.Nt * count)
-    return phi
+    return np.where(box, 1.0, 0.0) / (prob.Nt * count)
+
+
+def flow_along(prob: Problem, u):
+    """n . u at every node (the integrand of E in Eq. objective1)."""
+    return sum(prob.direction[a] * u[a] for a in range(prob.d))
+
+
+def objective_source(prob: Problem, phi, E, u):
+    """d J1 / d u_n(x) for J1 = E - phi_V V (Eq. objective1), V = S2 - E^2 with S2 the mean of (n.u)^2:
+    phi(x) [1 + 2 phi_V E - 2 phi_V n.u_n(x)].  E is the mean of the whole forward run."""
+    if prob.phi_var == 0.0:
+        return phi
+    return phi * (1.0 + 2.0 * prob.phi_var * E - 2.0 * prob.phi_var * flow_along(prob, u))
 
 
 def initial_state(prob: Problem, dtype=np.float64):
@@ -528,7 +548,10 @@ def initial_state(prob: Problem, dtype=np.float64):
 
 
 def forward(prob: Problem, kref, s, uG, store=False, state0=None):
-    """Run Nt LKS steps (Algorithm 1, forward loop) and return J (Eq. objective1, phi = 0).
+    """Run Nt LKS steps (Algorithm 1, forward loop) and return J1 = E - phi_V V (Eq. objective1).
+
+    E and S2 are rectangle-rule means over n = 1..Nt and the fluid nodes of O_target of n.u and (n.u)^2;
+    V = S2 - E^2.
 
     kref is the extended design array kappa^ref (margin included); s, uG are (Nt+1, d) offsets and velocities.
     With store=True the list of states (p_n, u_n), n = 0..Nt, is returned too.
@@ -537,19 +560,24 @@ def forward(prob: Problem, kref, s, uG, store=False, state0=None):
     A = viscosity_A(prob.nu)
     mask, uw = wall_mask(prob)
     phi = probe_weights(prob)
+    wO = probe_mean_weights(prob)
     o0 = prob.origin()
     dtype = np.result_type(kref, s, uG, np.float64)
     p, u = initial_state(prob, dtype) if state0 is None else state0
     states = [(p, u)] if store else None
-    J = 0.0
+    E = 0.0
+    S2 = 0.0
     for n in range(1, prob.Nt + 1):
         o = o0 + s[n]
         kappa, C = map_gather(kref, o, prob)
         uS = np.stack([uG[n, a] * C for a in range(prob.d)])
         p, u = lks_step(p, u, kappa, uS, A, c, w, mask, uw)
-        J = J + (phi * u).sum()
+        E = E + (phi * u).sum()
+        if prob.phi_var != 0.0:
+            S2 = S2 + (wO * flow_along(prob, u) ** 2).sum()
         if store:
             states.append((p, u))
+    J = E if prob.phi_var == 0.0 else E - prob.phi_var * (S2 - E * E)
     return (J, states) if store else J
 
 
@@ -562,20 +590,22 @@ def adjoint(prob: Problem, kref, s, uG, states):
           kappa-bar = lam_u . (u^S - u_n) / (1 + kappa);  u^S-bar = lam_u kappa / (1 + kappa)
       b1  F-bar_i(y) = p-bar*(y + c_i) / 3 + c_i . u-bar*(y + c_i); moments M0, M1, M2 with weights w_i
       b2  lam_p(n-1) = 3 M0;  lam_u(n-1) = 3 M1 + 9 M2 u_{n-1} - 3 u_{n-1} M0
-                       + A sum_a [M2_a.(y - e_a) - M2_a.(y + e_a)]  (+ phi for n - 1 >= 1)
+                       + A sum_a [M2_a.(y - e_a) - M2_a.(y + e_a)]  (+ dJ/du_{n-1} for n - 1 >= 1)
       b4  dJ/dkref += M^T kappa-bar (transposed mapping)
       b5  dJ/ds_n = sum_x kappa-bar dkappa/ds + (u^S-bar . u^G) dC/ds;  dJ/du^G_n = sum_x u^S-bar C
+    The objective's own source dJ/du_n (``objective_source``) uses the mean E of the stored forward run.
     """
     c, w = lattice(prob.lattice)
     A = viscosity_A(prob.nu)
     mask, _ = wall_mask(prob)
     phi = probe_weights(prob)
+    E = sum((phi * states[n][1]).sum() for n in range(1, prob.Nt + 1))
     d = prob.d
     axes = tuple(range(d))
     o0 = prob.origin()
     dtype = np.result_type(kref, s, uG, np.float64)
     lam_p = np.zeros(prob.shape, dtype=dtype)
-    lam_u = phi.astype(dtype)
+    lam_u = objective_source(prob, phi, E, states[prob.Nt][1]).astype(dtype)
     g_kref = np.zeros(prob.ext, dtype=dtype)
     g_s = np.zeros((prob.Nt + 1, d), dtype=dtype)
     g_uG = np.zeros((prob.Nt + 1, d), dtype=dtype)
@@ -623,7 +653,7 @@ def adjoint(prob: Problem, kref, s, uG, states):
         lam_p = new_p
         lam_u = np.stack(new_u)
         if n - 1 >= 1:
-            lam_u = lam_u + phi
+            lam_u = lam_u + objective_source(prob, phi, E, u_prev)
     return g_kref, g_s, g_uG
 
 

@@ -75,3 +75,27 @@ def test_dropped_brinkman_term_is_caught(monkeypatch):
     p1, u1 = L.lks_step(p, u, 0.5, uS, 0.6, c, w, mask, 0 * u)
     want = 0.05 + (0.0 - 0.05) / 1.5
     assert abs(u1[0, 0, 0] - want) > 1e-3
+
+
+@pytest.mark.parametrize("mistake", ["drop_mean", "sign"])
+def test_variance_source_mistake_is_caught(monkeypatch, mistake):
+    from test_oracle_adjoint import PHI_V
+
+    P, gamma, knots = tiny("D2Q9", "linear", 52, Nt=8, phi_var=PHI_V)
+    rng = np.random.default_rng(53)
+    vg = rng.standard_normal(gamma.shape)
+
+    def dot_gap():
+        J, gg, gk = O.gradient(P, gamma, knots)
+        h = 1e-30
+        jvp = np.imag(O.solve(P, gamma + 1j * h * vg, knots)) / h
+        return abs((gg * vg).sum() - jvp) / np.abs(gg * vg).sum()
+
+    assert dot_gap() < 1e-12
+    fa = L.flow_along
+    if mistake == "drop_mean":  # the 2 phi E term of dJ1/du left out
+        bad = lambda prob, phi, E, u: phi * (1.0 - 2.0 * prob.phi_var * fa(prob, u))
+    else:  # the variance term with the wrong sign
+        bad = lambda prob, phi, E, u: phi * (1.0 - 2.0 * prob.phi_var * E + 2.0 * prob.phi_var * fa(prob, u))
+    monkeypatch.setattr(L, "objective_source", bad)
+    assert dot_gap() > 1e-6
