@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--nt", type=int, default=0, help="override the horizon (short runs for profiler captures)")
     ap.add_argument("--optimize", type=int, default=0, help="also run this many projected-gradient optimisation "
                     "iterations (gamma step 0.05, position step 0.5 cell, normalised) and report J and s/iteration")
+    ap.add_argument("--phi-var", type=float, default=0.0, help="weight phi of the variance term of the objective "
+                    "(J1 = E - phi V); 0 = the mean E alone")
     ap.add_argument("--tile-rows", default="", help="force step-kernel variants instead of autotuning: F, F,A or "
                     "F,A,R (tile_rows codes of the forward sweep, the adjoint and the recomputation)")
     return ap.parse_args()
@@ -168,6 +170,11 @@ def captured_traffic(workload_name, kernel, source):
     return None
 
 
+def objective_name(w):
+    phi = w.get("phi_var", 0.0)
+    return "E (mean of n.u over the probe box)" if phi == 0.0 else f"E - {phi:g} V (mean and variance of n.u)"
+
+
 def node_count(w):
     return int(np.prod(w["shape"]))
 
@@ -221,7 +228,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = workload(args.workload)
+    w = dict(workload(args.workload), phi_var=args.phi_var)
     sample_steps = 20
     times = []
     for i in range(args.warmup + args.steps):
@@ -233,7 +240,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["name"], "grid": list(w["shape"]), "design": list(w["design"]), "Nt": w["Nt"],
-                       "sample_Nt": sample_steps},
+                       "sample_Nt": sample_steps, "objective": objective_name(w)},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": times[0]["sample"], "value": val,
                              "unit": "G node-steps/s (fwd+adj)"},
             "e2e": {"value": val, "unit": "G node-steps/s (fwd+adj)", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -254,7 +261,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group(backend="nccl")
 
-    w = workload(args.workload)
+    w = dict(workload(args.workload), phi_var=args.phi_var)
     if args.nt > 0:  # shorter horizon, same body speed
         w = dict(w, Nt=args.nt, K=min(w["K"], max(2, args.nt // 4)), R_t=max(1.0, w["R_t"] * args.nt / w["Nt"]),
                  amp=w["amp"] * args.nt / w["Nt"])
@@ -398,7 +405,7 @@ def run_ours(args):
             "config": {"workload": w["name"], "lattice": w["lattice"], "grid": list(w["shape"]), "design": list(w["design"]),
                        "Nt": w["Nt"], "K": w["K"], "precision": w["precision"] + " state / f64 accumulators",
                        "checkpointing": w["ckpt"], "parallelism": f"replicas{world}",
-                       "l2": l2_note},
+                       "objective": objective_name(w), "l2": l2_note},
             "roofline": roof,
             "e2e": {"value": e2e, "unit": "G node-steps/s (fwd+adj)", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches * world),

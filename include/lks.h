@@ -59,6 +59,9 @@ enum { LKS_MODE_JOINT = 0, LKS_MODE_SHAPE = 1, LKS_MODE_MOTION = 2 };
  *  map_kernel     LKS_MAP_LINEAR (hat, w = max(0, 1-|r|)) or LKS_MAP_COSINE (Sec. 2.3 w(r), |r| <= 2).
  *  base_center    analysis coordinates of the design-grid centre at zero offset; NaN = grid centre.
  *  probe_lo/hi    objective box O_target [lo, hi) (wall nodes excluded); direction: n of Eq. objective1.
+ *  phi_var        phi of Eq. objective1, the weight of the variance: J1 = E - phi_var V, with E and V the mean
+ *                 and variance of n.u over the fluid nodes of O_target and steps 1..Nt; 0 = the mean E alone.
+ *                 Any finite value.
  *  Nt, K          time steps and motion knots (knot k at step k Nt/(K-1)); K >= 2.
  *  R_t            temporal filter radius in steps (Eq. chi_filtered), > 0.
  *  filter_R       density filter radius in design cells (Eq. filtering); <= 1 means identity.
@@ -118,6 +121,7 @@ typedef struct lks_params {
     int32_t tile_rows;
     int32_t tile_rows_adj;
     int32_t tile_rows_rec;
+    double phi_var;
 } lks_params;
 
 typedef struct lks_ctx lks_ctx;
@@ -156,10 +160,11 @@ const char* lks_last_error_string(const lks_ctx* ctx);
 const char* lks_strerror(int status);
 
 /*
- * Forward solve (Algorithm 1, filters and forward time loop; objective Eq. objective1 with phi = 0):
+ * Forward solve (Algorithm 1, filters and forward time loop; objective Eq. objective1):
  *   gamma[nd]      design variables on the inner design grid, in [0, 1];
  *   pos_knots[K*d] body-centre offsets (cells) at the knots;
- *   J              objective, the time-space mean of n.u over O_target.
+ *   J              objective J1 = E - phi_var V: E the time-space mean of n.u over O_target, V its variance
+ *                  (rectangle rule over steps 1..Nt; FP64 accumulation of per-block partials in a fixed order).
  * Keeps what the adjoint needs (checkpoints).  Host-pointer variant blocks until J is on the host.
  */
 int lks_forward(lks_ctx* ctx, const double* gamma, const double* pos_knots, double* J);
@@ -242,6 +247,12 @@ int lks_set_initial_state(lks_ctx* ctx, const double* p, const double* u);
 
 /* Per-step motion sensitivities of the last adjoint, dJ/ds_n and dJ/du^G_n, each (Nt+1) x d. Synchronous. */
 int lks_get_step_sensitivities(lks_ctx* ctx, double* dJ_ds, double* dJ_duG);
+
+/* The two terms of Eq. objective1 for the last forward: *E the mean of n.u, *V its variance (both over the
+ * fluid nodes of O_target and steps 1..Nt), so that J = E - phi_var V.  The squares are summed only when
+ * phi_var != 0; with phi_var = 0, *V is NaN.  Synchronous.  LKS_ESTATE before the first forward; LKS_EINVAL for a
+ * NULL pointer. */
+int lks_get_objective_terms(lks_ctx* ctx, double* E, double* V);
 
 /* Counters of the last forward / adjoint. */
 int lks_get_stats(const lks_ctx* ctx, lks_stats* out);

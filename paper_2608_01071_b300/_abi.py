@@ -51,6 +51,7 @@ class lks_params(C.Structure):
         ("tile_rows", C.c_int32),
         ("tile_rows_adj", C.c_int32),
         ("tile_rows_rec", C.c_int32),
+        ("phi_var", C.c_double),
     ]
 
 
@@ -106,6 +107,7 @@ PROTOTYPES = {
     "lks_interp_positions": (C.c_int, [_P, _D, _D, _D]),
     "lks_interp_positions_T": (C.c_int, [_P, _D, _D, _D]),
     "lks_get_step_sensitivities": (C.c_int, [_P, _D, _D]),
+    "lks_get_objective_terms": (C.c_int, [_P, _D, _D]),
     "lks_get_stats": (C.c_int, [_P, C.POINTER(lks_stats)]),
     "lks_set_timing": (C.c_int, [_P, C.c_int]),
     "lks_set_graphs": (C.c_int, [_P, C.c_int]),

@@ -64,6 +64,7 @@ def params_from_workload(w: dict) -> _abi.lks_params:
     p.tile_rows = w.get("tile_rows", 0)
     p.tile_rows_adj = w.get("tile_rows_adj", 0)
     p.tile_rows_rec = w.get("tile_rows_rec", 0)
+    p.phi_var = w.get("phi_var", 0.0)
     return p
 
 
@@ -154,6 +155,12 @@ class Solver:
         gu = np.zeros((self.Nt + 1, self.d))
         self._check(self.lib.lks_get_step_sensitivities(self.h, _dptr(gs), _dptr(gu)))
         return gs, gu
+
+    def objective_terms(self):
+        """(E, V) of the last forward: mean and variance of n.u over O_target and the horizon (J = E - phi_var V)."""
+        E, V = C.c_double(), C.c_double()
+        self._check(self.lib.lks_get_objective_terms(self.h, C.byref(E), C.byref(V)))
+        return E.value, V.value
 
     def set_timing(self, on: bool):
         self._check(self.lib.lks_set_timing(self.h, 1 if on else 0))

@@ -107,7 +107,7 @@ struct Engine {
     virtual void kappa_ref(const DesignGeom& dg, const double* gt, double* gb, double* k64, void* k, cudaStream_t s) = 0;
     virtual void init_state(const Geom& g, void* st, cudaStream_t s) = 0;
     virtual void import_state(const Geom& g, const double* p, const double* u, void* st, cudaStream_t s) = 0;
-    virtual void init_adjoint(const Geom& g, void* lam, cudaStream_t s) = 0;
+    virtual void init_adjoint(const Geom& g, const void* fin, void* lam, cudaStream_t s) = 0;
     virtual void export_state(const Geom& g, const void* st, double* p, double* u, cudaStream_t s) = 0;
 };
 
@@ -126,6 +126,7 @@ FwdArgs<T> make_fwd_args(const Geom& g, const void* in, void* out, const void* k
     a.kref = (const T*)kref;
     a.pose = pose;
     a.jslot = jslot;
+    a.jsq = jslot != nullptr && g.jsq_off != 0 ? jslot + g.jsq_off : nullptr;
     a.flag = flag;
     a.u_crit2 = (T)g.u_crit2;
     return a;
@@ -144,7 +145,12 @@ AdjArgs<T> make_adj_args(const Geom& g, const void* lam_in, void* lam_out, const
     a.boxbuf = (T*)boxbuf;
     a.fac = (const T*)fac;
     a.src = src;
-    for (int i = 0; i < 3; ++i) a.phi_dir[i] = (T)(g.dir[i] * g.phi);
+    for (int i = 0; i < 3; ++i) {
+        a.phi_dir[i] = (T)(g.dir[i] * g.phi);
+        a.dir[i] = (T)g.dir[i];
+    }
+    a.src_c0 = g.phi_var != 0.0 ? g.obj + 3 : nullptr;
+    a.src_c1 = (T)(2.0 * g.phi_var);
     return a;
 }
 
@@ -183,8 +189,8 @@ struct EngineCommon : Engine {
         import_state_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, p, u, (T*)st);
         LKS_LAUNCHED();
     }
-    void init_adjoint(const Geom& g, void* lam, cudaStream_t s) override {
-        init_adjoint_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, (T*)lam);
+    void init_adjoint(const Geom& g, const void* fin, void* lam, cudaStream_t s) override {
+        init_adjoint_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, (const T*)fin + g.N, (T*)lam);
         LKS_LAUNCHED();
     }
     void export_state(const Geom& g, const void* st, double* p, double* u, cudaStream_t s) override {
@@ -293,7 +299,8 @@ template <typename T, int HW>
 struct Engine2D : EngineCommon<T, 2, HW> {
     static constexpr int WY = 4;
     explicit Engine2D(const Geom& g) {
-        LKS_CUDA(cudaFuncSetAttribute(fwd2r2_kernel<T, HW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r2_fwd<T>()));
+        LKS_CUDA(cudaFuncSetAttribute(fwd2r2_kernel<T, HW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r2_fwd<T>()));
+        LKS_CUDA(cudaFuncSetAttribute(fwd2r2_kernel<T, HW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r2_fwd<T>()));
         LKS_CUDA(cudaFuncSetAttribute(adj2r2_kernel<T, HW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r2_adj<T>()));
         LKS_CUDA(cudaFuncSetAttribute(fwd2r_kernel<T, HW, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_fwd<T, 1>()));
         LKS_CUDA(cudaFuncSetAttribute(fwd2r_kernel<T, HW, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_fwd<T, 2>()));
@@ -349,8 +356,17 @@ struct Engine2D : EngineCommon<T, 2, HW> {
               double* jslot1, double* jslot2, unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) override {
         auto a1 = make_fwd_args<T>(g, in, out1, kref, pose1, jslot1, flag, jlo, jn);
         auto a2 = make_fwd_args<T>(g, out1, out2 ? out2 : out1, kref, pose1 + 1, jslot2, flag, jlo, jn);
-        launch_pdl(fwd2r2_kernel<T, HW>, this->fgrid, this->fthreads, smem2r2_fwd<T>(), s, this->pdl, g, a1, a2,
-                   out2 ? 1 : 0);
+        fwd2r2(g, a1, a2, out2 ? 1 : 0, s);
+    }
+    // the squares of n.u are summed only when the objective has the variance term (a separate instantiation, so
+    // that the plain objective keeps the kernel's code unchanged)
+    void fwd2r2(const Geom& g, const FwdArgs<T>& a1, const FwdArgs<T>& a2, int two, cudaStream_t s) {
+        if (a1.jsq != nullptr)
+            launch_pdl(fwd2r2_kernel<T, HW, true>, this->fgrid, this->fthreads, smem2r2_fwd<T>(), s, this->pdl, g, a1,
+                       a2, two);
+        else
+            launch_pdl(fwd2r2_kernel<T, HW, false>, this->fgrid, this->fthreads, smem2r2_fwd<T>(), s, this->pdl, g, a1,
+                       a2, two);
     }
     template <int R>
     void adj_r(const Geom& g, AdjArgs<T> a, cudaStream_t s) {
@@ -361,7 +377,7 @@ struct Engine2D : EngineCommon<T, 2, HW> {
         auto a = make_fwd_args<T>(g, in, out, kref, pose, jslot, flag, jlo, jn);
         switch (this->rows_f) {
             case 3:
-                launch_pdl(fwd2r2_kernel<T, HW>, this->fgrid, this->fthreads, smem2r2_fwd<T>(), s, this->pdl, g, a, a, 0);
+                fwd2r2(g, a, a, 0, s);
                 break;
             case 1: launch_pdl(fwd2r_kernel<T, HW, 1>, this->fgrid, this->fthreads, smem2r_fwd<T, 1>(), s, this->pdl, g, a); break;
             case 2: launch_pdl(fwd2r_kernel<T, HW, 2>, this->fgrid, this->fthreads, smem2r_fwd<T, 2>(), s, this->pdl, g, a); break;
@@ -577,6 +593,7 @@ void validate(const lks_params* p) {
     if (p->ckpt < LKS_CKPT_FULL || p->ckpt > LKS_CKPT_REVOLVE) bad("unknown ckpt");
     if (p->mode < LKS_MODE_JOINT || p->mode > LKS_MODE_MOTION) bad("unknown mode");
     if (p->ckpt_slots < 0 || p->seg_len < 0 || p->ckpt_bytes < 0) bad("negative checkpoint setting");
+    if (!std::isfinite(p->phi_var)) bad("phi_var must be finite");
     // a step-kernel variant code: the forward accepts 3 (two steps per launch), the adjoint does not
     auto variant_ok = [&](int r, bool fwd) {
         if (D == 3) return r == 1 || r == 8 || r == 16 || r == 32 || r == 64 || (fwd && r == 96);
@@ -630,6 +647,7 @@ void setup_geometry(lks_ctx* c) {
     }
     if (cnt <= 0) throw LksError{LKS_EINVAL, "probe box holds no fluid node"};
     g.phi = 1.0 / ((double)p.Nt * (double)cnt);
+    g.phi_var = p.phi_var;
     for (int a = 0; a < c->D; ++a) {
         const double center = std::isnan(p.base_center[a]) ? (p.n[a] - 1) / 2.0 : p.base_center[a];
         c->o0[a] = center - (g.nde[a] - 1) / 2.0;
@@ -907,11 +925,15 @@ void allocate(lks_ctx* c) {
     c->d_gs = (double*)dalloc(c, (size_t)(p.Nt + 1) * D * 8);
     c->d_guG = (double*)dalloc(c, (size_t)(p.Nt + 1) * D * 8);
     c->d_pose = (Pose*)dalloc(c, (size_t)(p.Nt + 1) * sizeof(Pose));
-    c->d_jslot = (double*)dalloc(c, (size_t)(p.Nt + 1) * c->max_njb * 8);
+    // partials of n.u per step and probe block, then (with the variance term) their (n.u)^2 twins
+    const long long nslot = (long long)(p.Nt + 1) * c->max_njb;
+    c->g.jsq_off = p.phi_var != 0.0 ? nslot : 0;
+    c->d_jslot = (double*)dalloc(c, (size_t)2 * nslot * 8);
     c->d_out_g = (double*)dalloc(c, c->nd * 8);
     c->d_out_k = (double*)dalloc(c, (size_t)p.K * D * 8);
     c->d_jstep = (double*)dalloc(c, (size_t)(p.Nt + 1) * 8);
-    c->d_J = (double*)dalloc(c, 8);
+    c->d_J = (double*)dalloc(c, 4 * 8);  // J, E, V, 1 + 2 phi_var E
+    c->g.obj = c->d_J;
     c->d_flag = (unsigned*)dalloc(c, 16);
     c->d_kbar = dalloc(c, (size_t)c->Lmax * c->g.Fbn * ts);
     c->nsb = (int)nblk(c->g.Fbn, 256);
@@ -954,7 +976,8 @@ void allocate(lks_ctx* c) {
     }
     for (int i = 0; i < 3; ++i) LKS_CUDA(cudaEventCreateWithFlags(&c->ev_sync[i], cudaEventDisableTiming));
     LKS_CUDA(cudaEventCreateWithFlags(&c->ev_flag, cudaEventDisableTiming));
-    LKS_CUDA(cudaMemset(c->d_jslot, 0, (size_t)(p.Nt + 1) * c->max_njb * 8));
+    LKS_CUDA(cudaMemset(c->d_jslot, 0, (size_t)2 * nslot * 8));
+    LKS_CUDA(cudaMemset(c->d_J, 0, 4 * 8));
     LKS_CUDA(cudaMemset(c->d_pose, 0, (size_t)(p.Nt + 1) * sizeof(Pose)));
     filter_norm_kernel<<<nblk(c->nd, 128), 128>>>(c->dg, c->d_fnorm);
     LKS_LAUNCHED();
@@ -1212,7 +1235,8 @@ void forward_body(lks_ctx* c, cudaStream_t s) {
     };
     run_steps(c, 0, Nt, c->slot[0], dst, true, s);
     span_end(c, 0, e0, s);
-    objective_reduce_kernel<<<1, 256, 0, s>>>(c->d_jslot, njb_of(c), Nt, c->g.phi, c->d_jstep, c->d_J);
+    objective_reduce_kernel<<<1, 256, 0, s>>>(c->d_jslot, c->g.jsq_off, njb_of(c), Nt, c->g.phi, c->g.phi_var,
+                                              c->d_jstep, c->d_J);
     LKS_LAUNCHED();
     c->launches++;
     LKS_CUDA(cudaMemcpyAsync(c->h_flag, c->d_flag, 4, cudaMemcpyDeviceToHost, s));
@@ -1411,7 +1435,7 @@ void adjoint_body(lks_ctx* c, cudaStream_t s) {
     LKS_CUDA(cudaMemsetAsync(c->d_dkref, 0, c->nde * 8, s));
     LKS_CUDA(cudaMemsetAsync(c->d_gs, 0, (size_t)(Nt + 1) * D * 8, s));
     LKS_CUDA(cudaMemsetAsync(c->d_guG, 0, (size_t)(Nt + 1) * D * 8, s));
-    c->eng->init_adjoint(c->g, c->lam[0], s);
+    c->eng->init_adjoint(c->g, c->fin, c->lam[0], s);
     c->launches++;
     if (c->prm.ckpt == LKS_CKPT_REVOLVE) {
         reverse_revolve(c, 0, c->M, c->free_slots, c->slot[0], s);
@@ -1878,6 +1902,19 @@ int lks_get_step_sensitivities(lks_ctx* c, double* gs, double* guG) {
         LKS_CUDA(cudaDeviceSynchronize());
         LKS_CUDA(cudaMemcpy(gs, c->d_gs, b, cudaMemcpyDeviceToHost));
         LKS_CUDA(cudaMemcpy(guG, c->d_guG, b, cudaMemcpyDeviceToHost));
+    });
+}
+
+int lks_get_objective_terms(lks_ctx* c, double* E, double* V) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!E || !V) throw LksError{LKS_EINVAL, "null pointer"};
+        if (c->stats.forward_steps == 0) throw LksError{LKS_ESTATE, "no forward has run"};
+        double t[4];
+        LKS_CUDA(cudaDeviceSynchronize());
+        LKS_CUDA(cudaMemcpy(t, c->d_J, sizeof(t), cudaMemcpyDeviceToHost));
+        *E = t[1];
+        *V = t[2];
     });
 }
 

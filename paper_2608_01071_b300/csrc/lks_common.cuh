@@ -70,6 +70,9 @@ struct Geom {
     int probe_lo[3], probe_hi[3];
     double dir[3];      // objective direction n
     double phi;         // 1 / (Nt |O|): the objective's weight of one node-step
+    double phi_var;     // phi of Eq. objective1: weight of the variance V in J1 = E - phi V
+    long long jsq_off;  // from an objective slot (sum of n.u) to its twin (sum of (n.u)^2)
+    const double* obj;  // device objective terms of the last forward: J, E, V, 1 + 2 phi E
     double A;           // 3/4 - 9 nu / 2
     double wall_u[3][2][3];
     double u_crit2;     // squared stability limit (<= 0 disables)

@@ -283,9 +283,10 @@ __global__ void init_state_kernel(Geom g, T* __restrict__ st) {
     for (int c = 0; c < D; ++c) st[(1 + c) * g.N + i] = u[c];
 }
 
-// Adjoint terminal state: lambda_p = 0, lambda_u = phi (the objective's weight of the last step).
+// Adjoint terminal state: lambda_p = 0, lambda_u = dJ/du_Nt, the objective's source of the last step:
+// phi n at the probe nodes, times 1 + 2 phi_var E - 2 phi_var n.u_Nt when the variance term is on (Eq. objective1).
 template <typename T, int D>
-__global__ void init_adjoint_kernel(Geom g, T* __restrict__ lam) {
+__global__ void init_adjoint_kernel(Geom g, const T* __restrict__ u_fin, T* __restrict__ lam) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= g.N) return;
     int x[3] = {(int)(i % g.n[0]), (int)((i / g.n[0]) % g.n[1]), (int)(i / ((long long)g.n[0] * g.n[1]))};
@@ -294,8 +295,14 @@ __global__ void init_adjoint_kernel(Geom g, T* __restrict__ lam) {
         if (!g.periodic[a] && (x[a] == 0 || x[a] == g.n[a] - 1)) wall = true;
         probe = probe && x[a] >= g.probe_lo[a] && x[a] < g.probe_hi[a];
     }
+    T f = 1;
+    if (probe && !wall && g.phi_var != 0.0) {
+        T nu = 0;
+        for (int c = 0; c < D; ++c) nu += (T)g.dir[c] * u_fin[c * g.N + i];
+        f = (T)g.obj[3] - (T)(2.0 * g.phi_var) * nu;
+    }
     lam[i] = 0;
-    for (int c = 0; c < D; ++c) lam[(1 + c) * g.N + i] = (probe && !wall) ? (T)(g.dir[c] * g.phi) : (T)0;
+    for (int c = 0; c < D; ++c) lam[(1 + c) * g.N + i] = (probe && !wall) ? (T)(g.dir[c] * g.phi) * f : (T)0;
 }
 
 // FP64 copy of a state (p = p' + 1/3) for the host.

@@ -30,7 +30,7 @@ __device__ __forceinline__ double shfl_dn1(double v) { return __shfl_down_sync(0
 // ------------------------------------------------------------------------------------------------
 template <typename T, int HW, int R, int WY>
 __global__ void __launch_bounds__(32 * WY) fwd2d_kernel(Geom g, FwdArgs<T> a) {
-    __shared__ double red[WY];
+    __shared__ double red[2 * WY];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nx = g.n[0], ny = g.n[1];
     const int x0 = blockIdx.x * kLanesOut;
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(32 * WY) fwd2d_kernel(Geom g, FwdArgs<T> a) {
     // raw window (rows r-2, r-1, r) and output accumulators (rows m-1, m, m+1)
     T p0 = 0, p1 = 0, p2 = 0, ux0 = 0, ux1 = 0, ux2 = 0, uy0 = 0, uy1 = 0, uy2 = 0;
     T aP0 = 0, aP1 = 0, aP2 = 0, aX0 = 0, aX1 = 0, aX2 = 0, aY0 = 0, aY1 = 0, aY2 = 0;
-    T jacc = 0;
+    T jacc = 0, qacc = 0;
     bool unstable = false;
 #pragma unroll
     for (int it = 0; it < R + 4; ++it) {
@@ -128,7 +128,11 @@ __global__ void __launch_bounds__(32 * WY) fwd2d_kernel(Geom g, FwdArgs<T> a) {
             a.out_u[g.N + go] = un1;
             if (!wall) {
                 if (a.u_crit2 > (T)0 && !(un0 * un0 + un1 * un1 <= a.u_crit2)) unstable = true;
-                if (in_probe<2>(g, xg)) jacc += a.dir[0] * un0 + a.dir[1] * un1;
+                if (in_probe<2>(g, xg)) {
+                    const T nu = a.dir[0] * un0 + a.dir[1] * un1;
+                    jacc += nu;
+                    qacc += nu * nu;
+                }
             }
         }
         aP0 = aP1; aP1 = aP2; aP2 = 0;
@@ -139,10 +143,7 @@ __global__ void __launch_bounds__(32 * WY) fwd2d_kernel(Geom g, FwdArgs<T> a) {
     if (a.jslot != nullptr) {
         const int bx = (int)blockIdx.x - a.jb_lo[0], by = (int)blockIdx.y - a.jb_lo[1];
         if (bx >= 0 && bx < a.jb_n[0] && by >= 0 && by < a.jb_n[1]) {
-            T v[1] = {jacc};
-            double s[1];
-            block_sum<32 * WY, 1, T>(v, s, red);
-            if (threadIdx.x == 0) a.jslot[bx + a.jb_n[0] * by] = s[0];
+            store_probe_partials<32 * WY, T>(jacc, qacc, a.jslot, a.jsq, bx + a.jb_n[0] * by, red);
         }
     }
 }
@@ -260,8 +261,9 @@ __global__ void __launch_bounds__(32 * WY) adj2d_kernel(Geom g, AdjArgs<T> a) {
                 T uw[2];
                 const bool wall = wall_node<T, 2>(g, xg, uw);
                 if (a.src && !wall && in_probe<2>(g, xg)) {
-                    vx += a.phi_dir[0];
-                    vy += a.phi_dir[1];
+                    const T f = src_factor(a, a.dir[0] * u0 + a.dir[1] * u1);
+                    vx += a.phi_dir[0] * f;
+                    vy += a.phi_dir[1] * f;
                 }
                 a.lam_out[go] = (T)3 * m0_c;
                 a.lam_out[N + go] = vx;

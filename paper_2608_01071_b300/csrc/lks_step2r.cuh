@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256) fwd2r_kernel(Geom g, FwdArgs<T> a) {
     using L = Lattice<2>;
     constexpr int RR = RW::RR;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[8];
+    __shared__ double red[16];
     T* sp = reinterpret_cast<T*>(smem_raw);  // [RR][32] p'
     T* sx = sp + RR * 32;                    // u_x
     T* sy = sx + RR * 32;                    // u_y
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256) fwd2r_kernel(Geom g, FwdArgs<T> a) {
     }
     __syncthreads();
     // phase 3: outputs on rows 2 .. TY+1, lanes 2 .. 29
-    T jacc = 0;
+    T jacc = 0, qacc = 0;
     bool unstable = false;
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
@@ -138,18 +138,18 @@ __global__ void __launch_bounds__(256) fwd2r_kernel(Geom g, FwdArgs<T> a) {
         a.out_u[g.N + go] = un1;
         if (!wall) {
             if (a.u_crit2 > (T)0 && !(un0 * un0 + un1 * un1 <= a.u_crit2)) unstable = true;
-            if (in_probe<2>(g, xg)) jacc += a.dir[0] * un0 + a.dir[1] * un1;
+            if (in_probe<2>(g, xg)) {
+                const T nu = a.dir[0] * un0 + a.dir[1] * un1;
+                jacc += nu;
+                qacc += nu * nu;
+            }
         }
     }
     if (unstable) atomicOr(a.flag, 1u);
     if (a.jslot != nullptr) {
         const int px = (int)blockIdx.x - a.jb_lo[0], py = (int)blockIdx.y - a.jb_lo[1];
-        if (px >= 0 && px < a.jb_n[0] && py >= 0 && py < a.jb_n[1]) {
-            T v[1] = {jacc};
-            double s[1];
-            block_sum<256, 1, T>(v, s, red);
-            if (tid == 0) a.jslot[px + a.jb_n[0] * py] = s[0];
-        }
+        if (px >= 0 && px < a.jb_n[0] && py >= 0 && py < a.jb_n[1])
+            store_probe_partials<256, T>(jacc, qacc, a.jslot, a.jsq, px + a.jb_n[0] * py, red);
     }
 }
 
@@ -279,8 +279,9 @@ __global__ void __launch_bounds__(256) adj2r_kernel(Geom g, AdjArgs<T> a) {
         T uw[2];
         const bool wall = wall_node<T, 2>(g, xg, uw);
         if (a.src && !wall && in_probe<2>(g, xg)) {
-            vx += a.phi_dir[0];
-            vy += a.phi_dir[1];
+            const T f = src_factor(a, a.dir[0] * u0 + a.dir[1] * u1);
+            vx += a.phi_dir[0] * f;
+            vy += a.phi_dir[1] * f;
         }
         a.lam_out[go] = (T)3 * M0;
         a.lam_out[N + go] = vx;
@@ -312,12 +313,12 @@ __host__ __device__ constexpr size_t smem2r2_fwd() {
 // of 4) and 8 rows high; step n is computed on the tile plus a halo of 2, kept in shared memory as the input of
 // step n+1, and written out for the tile itself.  The arithmetic per step is that of fwd2r_kernel.
 // With two = 0 only step n is taken (the last step of an odd run), on the same tile geometry.
-template <typename T, int HW>
+template <typename T, int HW, bool SQ>
 __global__ void __launch_bounds__(256) fwd2r2_kernel(Geom g, FwdArgs<T> a1, FwdArgs<T> a2, int two) {
     using L = Lattice<2>;
     constexpr int TY = Fused2::TY, RR = Fused2::RR, TXO = Fused2::TXO;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[8];
+    __shared__ double red[SQ ? 16 : 8];
     T* sp = reinterpret_cast<T*>(smem_raw);  // [RR][32] p', then step-n state in place
     T* sx = sp + RR * 32;
     T* sy = sx + RR * 32;
@@ -382,9 +383,9 @@ __global__ void __launch_bounds__(256) fwd2r2_kernel(Geom g, FwdArgs<T> a1, FwdA
     };
     // stream + Brinkman + walls of the nodes on rows [h, RR-h), lanes [h, 32-h); results to shared memory and,
     // for the tile itself, to global memory (with the objective partial and the stability check)
-    T jacc1 = 0, jacc2 = 0;
+    T jacc1 = 0, jacc2 = 0, qacc1 = 0, qacc2 = 0;
     bool unstable = false;
-    auto outputs = [&](int h, const FwdArgs<T>& a, T& jacc, const T* kk, const T* cc) {
+    auto outputs = [&](int h, const FwdArgs<T>& a, T& jacc, T& qacc, const T* kk, const T* cc) {
         const Pose& P = *a.pose;
         const int bxc = box_coord(xl, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
         const bool lane_in = lane >= h && lane < 32 - h;
@@ -433,19 +434,23 @@ __global__ void __launch_bounds__(256) fwd2r2_kernel(Geom g, FwdArgs<T> a1, FwdA
                 a.out_u[g.N + go] = un1;
                 if (!wall) {
                     if (a.u_crit2 > (T)0 && !(un0 * un0 + un1 * un1 <= a.u_crit2)) unstable = true;
-                    if (in_probe<2>(g, xg)) jacc += a.dir[0] * un0 + a.dir[1] * un1;
+                    if (in_probe<2>(g, xg)) {
+                        const T nu = a.dir[0] * un0 + a.dir[1] * un1;
+                        jacc += nu;
+                        if constexpr (SQ) qacc += nu * nu;
+                    }
                 }
             }
         }
     };
     equilibria(1);
     __syncthreads();
-    outputs(2, a1, jacc1, kap1, C1);
+    outputs(2, a1, jacc1, qacc1, kap1, C1);
     if (two) {
         __syncthreads();
         equilibria(3);
         __syncthreads();
-        outputs(4, a2, jacc2, kap2, C2);
+        outputs(4, a2, jacc2, qacc2, kap2, C2);
     }
     if (unstable) atomicOr(a1.flag, 1u);
     for (int s = 0; s < 1 + two; ++s) {
@@ -453,11 +458,16 @@ __global__ void __launch_bounds__(256) fwd2r2_kernel(Geom g, FwdArgs<T> a1, FwdA
         if (a.jslot == nullptr) continue;
         const int px = (int)blockIdx.x - a.jb_lo[0], py = (int)blockIdx.y - a.jb_lo[1];
         if (px >= 0 && px < a.jb_n[0] && py >= 0 && py < a.jb_n[1]) {
-            T v[1] = {s == 0 ? jacc1 : jacc2};
-            double sum[1];
             __syncthreads();
-            block_sum<256, 1, T>(v, sum, red);
-            if (tid == 0) a.jslot[px + a.jb_n[0] * py] = sum[0];
+            if constexpr (SQ) {
+                store_probe_partials<256, T>(s == 0 ? jacc1 : jacc2, s == 0 ? qacc1 : qacc2, a.jslot, a.jsq,
+                                             px + a.jb_n[0] * py, red);
+            } else {
+                T v[1] = {s == 0 ? jacc1 : jacc2};
+                double sum[1];
+                block_sum<256, 1, T>(v, sum, red);
+                if (tid == 0) a.jslot[px + a.jb_n[0] * py] = sum[0];
+            }
         }
     }
 }
@@ -618,8 +628,9 @@ __global__ void __launch_bounds__(256) adj2r2_kernel(Geom g, AdjArgs<T> a1, AdjA
             T uw[2];
             const bool wall = wall_node<T, 2>(g, xg, uw);
             if (a.src && !wall && in_probe<2>(g, xg)) {
-                vx += a.phi_dir[0];
-                vy += a.phi_dir[1];
+                const T f = src_factor(a, a.dir[0] * u0 + a.dir[1] * u1);
+                vx += a.phi_dir[0] * f;
+                vy += a.phi_dir[1] * f;
             }
             const bool own = lane_tile && o >= 4 && o < RR - 4 && y0 - 4 + o < ny;
             if (own) {

@@ -64,10 +64,10 @@ __device__ __forceinline__ int wall_side(int x, int n, int periodic) {
 // Forward step n-1 -> n.
 // ------------------------------------------------------------------------------------------------
 template <typename T, int HW, int R>
-__global__ void __launch_bounds__(128) fwd2v_kernel(Geom g, FwdArgs<T> a) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (HW == 1 ? 7 : 5) : 4) fwd2v_kernel(Geom g, FwdArgs<T> a) {
     using V = typename Vec2<T>::type;
     constexpr int WY = 4;
-    __shared__ double red[WY];
+    __shared__ double red[2 * WY];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nx = g.n[0], ny = g.n[1];
     const int x0 = blockIdx.x * kVecCols;
@@ -106,7 +106,6 @@ __global__ void __launch_bounds__(128) fwd2v_kernel(Geom g, FwdArgs<T> a) {
     V aP0 = zero, aX0 = zero, aY0 = zero, aP1 = zero, aX1 = zero, aY1 = zero, aP2 = zero, aX2 = zero, aY2 = zero;
     const V c3 = vsplat<T>(3.0), cm15 = vsplat<T>(-1.5), c45 = vsplat<T>(4.5), vA = vmk(A, A),
             vhA = vmk((T)0.5 * A, (T)0.5 * A);
-    T jacc = 0;
     bool unstable = false;
 
 #pragma unroll 1
@@ -146,9 +145,8 @@ __global__ void __launch_bounds__(128) fwd2v_kernel(Geom g, FwdArgs<T> a) {
         if (o >= y0 && lane_out && o < ny) {
             const int wy = wall_side(o, ny, g.periodic[1]);
             const int by = box_coord(o, P.xs[1], g.Fb[1], ny, g.periodic[1]);
-            const bool py = o >= g.probe_lo[1] && o < g.probe_hi[1];
-            // Brinkman with the mapped kappa, walls, stability and objective for one column of the pair
-            auto finish = [&](T& u0, T& u1, int bx, int wx, bool px) {
+            // Brinkman with the mapped kappa, walls and stability for one column of the pair
+            auto finish = [&](T& u0, T& u1, int bx, int wx) {
                 if (bx >= 0 && by >= 0) {
                     const int b[2] = {bx, by};
                     T kap, C;
@@ -164,12 +162,11 @@ __global__ void __launch_bounds__(128) fwd2v_kernel(Geom g, FwdArgs<T> a) {
                     u1 = (T)g.wall_u[ax][side][1];
                 } else {
                     if (a.u_crit2 > (T)0 && !(u0 * u0 + u1 * u1 <= a.u_crit2)) unstable = true;
-                    if (py && px) jacc += a.dir[0] * u0 + a.dir[1] * u1;
                 }
             };
             T ue0 = aX0.x, ue1 = aY0.x, uo0 = aX0.y, uo1 = aY0.y;
-            finish(ue0, ue1, bxe, wxe, pxe);
-            finish(uo0, uo1, bxo, wxo, pxo);
+            finish(ue0, ue1, bxe, wxe);
+            finish(uo0, uo1, bxo, wxo);
             const int go = o * half + (xe >> 1);
             V* outP = reinterpret_cast<V*>(a.out_p);
             V* outX = reinterpret_cast<V*>(a.out_u);
@@ -192,10 +189,29 @@ __global__ void __launch_bounds__(128) fwd2v_kernel(Geom g, FwdArgs<T> a) {
     if (a.jslot != nullptr) {
         const int bx = (int)blockIdx.x - a.jb_lo[0], by = (int)blockIdx.y - a.jb_lo[1];
         if (bx >= 0 && bx < a.jb_n[0] && by >= 0 && by < a.jb_n[1]) {
-            T v[1] = {jacc};
-            double s[1];
-            block_sum<32 * WY, 1, T>(v, s, red);
-            if (threadIdx.x == 0) a.jslot[bx + a.jb_n[0] * by] = s[0];
+            // objective partials from this thread's own outputs, re-read after the march so that the march
+            // keeps no accumulators (same nodes and order: rows up, even column before odd)
+            T jacc = 0, qacc = 0;
+            if (lane_out) {
+                const V* oX = reinterpret_cast<const V*>(a.out_u);
+                const V* oY = reinterpret_cast<const V*>(a.out_u + g.N);
+                for (int o = max(y0, g.probe_lo[1]); o < min(min(y0 + R, ny), g.probe_hi[1]); ++o) {
+                    if (wall_side(o, ny, g.periodic[1]) >= 0) continue;
+                    const int go = o * half + (xe >> 1);
+                    const V ux = oX[go], uy = oY[go];
+                    if (pxe && wxe < 0) {
+                        const T nu = a.dir[0] * ux.x + a.dir[1] * uy.x;
+                        jacc += nu;
+                        qacc += nu * nu;
+                    }
+                    if (pxo && wxo < 0) {
+                        const T nu = a.dir[0] * ux.y + a.dir[1] * uy.y;
+                        jacc += nu;
+                        qacc += nu * nu;
+                    }
+                }
+            }
+            store_probe_partials<32 * WY, T>(jacc, qacc, a.jslot, a.jsq, bx + a.jb_n[0] * by, red);
         }
     }
 }
@@ -324,12 +340,14 @@ __global__ void __launch_bounds__(128, 5) adj2v_kernel(Geom g, AdjArgs<T> a) {
                 const bool wo = wy >= 0 || wall_side(xe + 1, nx, g.periodic[0]) >= 0;
                 const bool py = a.src && z >= g.probe_lo[1] && z < g.probe_hi[1];
                 if (py && pxe && !we) {
-                    vx.x += a.phi_dir[0];
-                    vy.x += a.phi_dir[1];
+                    const T f = src_factor(a, a.dir[0] * u0.x + a.dir[1] * u1.x);
+                    vx.x += a.phi_dir[0] * f;
+                    vy.x += a.phi_dir[1] * f;
                 }
                 if (py && pxo && !wo) {
-                    vx.y += a.phi_dir[0];
-                    vy.y += a.phi_dir[1];
+                    const T f = src_factor(a, a.dir[0] * u0.y + a.dir[1] * u1.y);
+                    vx.y += a.phi_dir[0] * f;
+                    vy.y += a.phi_dir[1] * f;
                 }
                 V* oP = reinterpret_cast<V*>(a.lam_out);
                 V* oX = reinterpret_cast<V*>(a.lam_out + N);

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(Reg3::NT) fwd3d_kernel(Geom g, FwdArgs<T> a) {
     using L = Lattice<3>;
     using R = Reg3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[R::NT / 32];
+    __shared__ double red[2 * (R::NT / 32)];
     T* raw = reinterpret_cast<T*>(smem_raw);  // [3 slots][4 fields][NS]
     T* wf = raw + 3 * 4 * R::NS;              // [3 slots][15][NM]
 
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(Reg3::NT) fwd3d_kernel(Geom g, FwdArgs<T> a) {
     const bool col = xg < nx && yg < ny;
     const int bx = box_coord(xg, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
     const int by = box_coord(yg, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
-    T jacc = 0;
+    T jacc = 0, qacc = 0;
     bool unstable = false;
 
     for (int k = z0 - 1; k <= z0 + ZB; ++k) {
@@ -191,7 +191,11 @@ __global__ void __launch_bounds__(Reg3::NT) fwd3d_kernel(Geom g, FwdArgs<T> a) {
             for (int c = 0; c < 3; ++c) a.out_u[c * N + gi] = un[c];
             if (!wall) {
                 if (a.u_crit2 > (T)0 && !(un[0] * un[0] + un[1] * un[1] + un[2] * un[2] <= a.u_crit2)) unstable = true;
-                if (in_probe<3>(g, xyz)) jacc += a.dir[0] * un[0] + a.dir[1] * un[1] + a.dir[2] * un[2];
+                if (in_probe<3>(g, xyz)) {
+                    const T nu = a.dir[0] * un[0] + a.dir[1] * un[1] + a.dir[2] * un[2];
+                    jacc += nu;
+                    qacc += nu * nu;
+                }
             }
         }
         // next raw plane into the slot of plane k - 1 (no longer read), prefetch the one after
@@ -203,10 +207,7 @@ __global__ void __launch_bounds__(Reg3::NT) fwd3d_kernel(Geom g, FwdArgs<T> a) {
     if (a.jslot != nullptr) {
         const int px = (int)blockIdx.x - a.jb_lo[0], py = (int)blockIdx.y - a.jb_lo[1], pz = (int)blockIdx.z - a.jb_lo[2];
         if (px >= 0 && px < a.jb_n[0] && py >= 0 && py < a.jb_n[1] && pz >= 0 && pz < a.jb_n[2]) {
-            T v[1] = {jacc};
-            double s[1];
-            block_sum<R::NT, 1, T>(v, s, red);
-            if (tid == 0) a.jslot[px + a.jb_n[0] * (py + a.jb_n[1] * pz)] = s[0];
+            store_probe_partials<R::NT, T>(jacc, qacc, a.jslot, a.jsq, px + a.jb_n[0] * (py + a.jb_n[1] * pz), red);
         }
     }
 }
@@ -345,6 +346,7 @@ __global__ void __launch_bounds__(Reg3::NT) adj3d_kernel(Geom g, AdjArgs<T> a) {
             T uw[3];
             const bool wall = wall_node<T, 3>(g, xyz, uw);
             const bool probe = a.src && !wall && in_probe<3>(g, xyz);
+            const T fsrc = probe ? src_factor(a, a.dir[0] * u[0] + a.dir[1] * u[1] + a.dir[2] * u[2]) : (T)1;
             a.lam_out[gi] = (T)3 * M0;
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(Reg3::NT) adj3d_kernel(Geom g, AdjArgs<T> a) {
                     if (c == 1) v += A * (Mc[f + m - R::MX] - Mc[f + m + R::MX]);
                     if (c == 2) v += A * (Mm[f + m] - Mp[f + m]);
                 }
-                if (probe) v += a.phi_dir[e];
+                if (probe) v += a.phi_dir[e] * fsrc;
                 a.lam_out[(1 + e) * N + gi] = v;
             }
             const int bz = box_coord(zo, P.xs[2], g.Fb[2], g.n[2], g.periodic[2]);

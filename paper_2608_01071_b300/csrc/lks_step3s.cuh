@@ -76,7 +76,7 @@ template <typename T, int HW, int ZB, int TY>
 __global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 3 : 1) fwd3s_kernel(Geom g, FwdArgs<T> a) {
     using R = Sep3<TY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[R::NT / 32];
+    __shared__ double red[2 * (R::NT / 32)];
     T* raw = reinterpret_cast<T*>(smem_raw);  // [5 slots][p, ux, uy, uz][NS]
     T* fld = raw + 5 * 4 * R::NS;             // [Q, Txy, Txz, Tyz, phi_x, phi_y][NM]
     T* fQ = fld;
@@ -164,7 +164,6 @@ __global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 3 : 1) fwd3s_kernel(Ge
     const T w0 = (T)(2.0 / 9.0), wf = (T)(1.0 / 9.0), wc = (T)(1.0 / 72.0), third = (T)(1.0 / 3.0);
     // partial streamed moments (p*, u*) of the plane below the current one and of the current plane
     T accM[4] = {0, 0, 0, 0}, accC[4] = {0, 0, 0, 0};
-    T jacc = 0;
     bool unstable = false;
 
 #pragma unroll 1
@@ -298,10 +297,8 @@ __global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 3 : 1) fwd3s_kernel(Ge
                 a.out_p[gi] = pn;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) a.out_u[c * N + gi] = un[c];
-                if (!wall) {
-                    if (a.u_crit2 > (T)0 && !(un[0] * un[0] + un[1] * un[1] + un[2] * un[2] <= a.u_crit2)) unstable = true;
-                    if (in_probe<3>(g, xyz)) jacc += a.dir[0] * un[0] + a.dir[1] * un[1] + a.dir[2] * un[2];
-                }
+                if (!wall && a.u_crit2 > (T)0 && !(un[0] * un[0] + un[1] * un[1] + un[2] * un[2] <= a.u_crit2))
+                    unstable = true;
             }
             // shift: plane k becomes the lower plane, plane k + 1 starts with this plane's emission
 #pragma unroll
@@ -316,10 +313,21 @@ __global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 3 : 1) fwd3s_kernel(Ge
     if (a.jslot != nullptr) {
         const int px = (int)blockIdx.x - a.jb_lo[0], py = (int)blockIdx.y - a.jb_lo[1], pz = (int)blockIdx.z - a.jb_lo[2];
         if (px >= 0 && px < a.jb_n[0] && py >= 0 && py < a.jb_n[1] && pz >= 0 && pz < a.jb_n[2]) {
-            T v[1] = {jacc};
-            double s[1];
-            block_sum<R::NT, 1, T>(v, s, red);
-            if (tid == 0) a.jslot[px + a.jb_n[0] * (py + a.jb_n[1] * pz)] = s[0];
+            // objective partials from this thread's own outputs, re-read after the march so that the march keeps
+            // no accumulators (same nodes, planes upward)
+            T jacc = 0, qacc = 0;
+            if (col) {
+                for (int zo = max(z0, g.probe_lo[2]); zo < min(min(z0 + ZB, nz), g.probe_hi[2]); ++zo) {
+                    int xyz[3] = {xg, yg, zo};
+                    T uw[3];
+                    if (!in_probe<3>(g, xyz) || wall_node<T, 3>(g, xyz, uw)) continue;
+                    const long long gi = xg + (long long)nx * yg + plane * zo;
+                    const T nu = a.dir[0] * a.out_u[gi] + a.dir[1] * a.out_u[N + gi] + a.dir[2] * a.out_u[2 * N + gi];
+                    jacc += nu;
+                    qacc += nu * nu;
+                }
+            }
+            store_probe_partials<R::NT, T>(jacc, qacc, a.jslot, a.jsq, px + a.jb_n[0] * (py + a.jb_n[1] * pz), red);
         }
     }
 }
@@ -566,14 +574,20 @@ __global__ void __launch_bounds__(Sep3<TY>::NT, TY == 8 ? 3 : 1) adj3s_kernel(Ge
             const bool probe = a.src && !wall && probe_xy && zo >= g.probe_lo[2] && zo < g.probe_hi[2];
             a.lam_out[gi] = (T)3 * M0o;
             const T M1[3] = {M1o0, M1o1, M1o2};
+            T v[3];
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
-                T v = (T)3 * M1[e] - (T)3 * u[e] * M0o + A * dA[e];
+                v[e] = (T)3 * M1[e] - (T)3 * u[e] * M0o + A * dA[e];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) v += (T)9 * m2[c][e] * u[c];
-                if (probe) v += a.phi_dir[e];
-                a.lam_out[(1 + e) * N + gi] = v;
+                for (int c = 0; c < 3; ++c) v[e] += (T)9 * m2[c][e] * u[c];
             }
+            if (probe) {
+                const T f = src_factor(a, a.dir[0] * u[0] + a.dir[1] * u[1] + a.dir[2] * u[2]);
+#pragma unroll
+                for (int e = 0; e < 3; ++e) v[e] += a.phi_dir[e] * f;
+            }
+#pragma unroll
+            for (int e = 0; e < 3; ++e) a.lam_out[(1 + e) * N + gi] = v[e];
             const int bz = colbox ? box_coord(zo, xs2, g.Fb[2], g.n[2], g.periodic[2]) : -1;
             if (bz >= 0) {
                 const long long bl = bx + (long long)g.Fb[0] * (by + (long long)g.Fb[1] * bz);

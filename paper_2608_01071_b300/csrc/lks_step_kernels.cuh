@@ -32,6 +32,7 @@ struct FwdArgs {
     const T* kref;      // kappa^ref on the extended design grid
     const Pose* pose;   // pose of step n
     double* jslot;      // objective partials of step n, one per probe block (nullptr: not needed)
+    double* jsq;        // their twins for (n.u)^2 (set with jslot)
     unsigned* flag;     // stability flag (bit 0)
     int jb_lo[3];       // first block touching the probe box, per axis
     int jb_n[3];        // number of blocks touching it, per axis
@@ -51,7 +52,17 @@ struct AdjArgs {
     const T* fac;       // 1 / (1 + kappa) of step n on the footprint box (box_fac_kernel), or nullptr
     int src;            // 1: add the objective source phi (n - 1 >= 1)
     T phi_dir[3];       // objective source weight n_a / (Nt |O|) in T
+    const double* src_c0;  // 1 + 2 phi E of the variance term (device, set by the objective reduction), or nullptr
+    T src_c1;           // 2 phi
+    T dir[3];           // objective direction n in T
 };
+
+// Factor f of the objective source dJ/du_{n-1} = phi_dir f at a probe node.  J1 = E - phi V (Eq. objective1),
+// V = S2 - E^2 with S2 the space-time mean of (n.u)^2, so f = 1 + 2 phi E - 2 phi n.u_{n-1}; f = 1 for phi = 0.
+template <typename T>
+__device__ __forceinline__ T src_factor(const AdjArgs<T>& a, T nu) {
+    return a.src_c0 == nullptr ? (T)1 : (T)(*a.src_c0) - a.src_c1 * nu;
+}
 
 // ------------------------------------------------------------------------------------------------
 // Small helpers
@@ -90,6 +101,28 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], double (&out)[NV], double*
             for (int i = 0; i < NW; ++i) s += red[c * NW + i];
             out[c] = s;
         }
+    }
+}
+
+// Objective partials of one probe block (Eq. objective1): the sums of n.u and, when jsq is set (the objective has
+// the variance term), of (n.u)^2 over its probe nodes, in the block's fixed reduction order.  red must hold
+// 2 * (NT / 32) doubles.
+template <int NT, typename T>
+__device__ __forceinline__ void store_probe_partials(T sum, T sq, double* jslot, double* jsq, long long b, double* red) {
+    const bool first = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z) == 0;
+    if (jsq == nullptr) {
+        T v[1] = {sum};
+        double s[1];
+        block_sum<NT, 1, T>(v, s, red);
+        if (first) jslot[b] = s[0];
+        return;
+    }
+    T v[2] = {sum, sq};
+    double s[2];
+    block_sum<NT, 2, T>(v, s, red);
+    if (first) {
+        jslot[b] = s[0];
+        jsq[b] = s[1];
     }
 }
 
@@ -265,7 +298,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) fwd_step_kernel(Geom g, FwdArgs<
     using TL = Tile<D, TX, TY, TZ>;
     constexpr int S = TL::S, M = TL::M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[(TX * TY * TZ + 31) / 32];
+    __shared__ double red[2 * ((TX * TY * TZ + 31) / 32)];
     T* sp = reinterpret_cast<T*>(smem_raw);  // p' on the halo-2 region
     T* su = sp + S;                          // u_a on the halo-2 region
     T* ms = su + D * S;                      // sigma = 3 p' - 3/2 |u|^2 on the halo-1 region
@@ -390,14 +423,12 @@ __global__ void __launch_bounds__(TX * TY * TZ) fwd_step_kernel(Geom g, FwdArgs<
         const int bx = (int)blockIdx.x - a.jb_lo[0], by = (int)blockIdx.y - a.jb_lo[1], bz = (int)blockIdx.z - a.jb_lo[2];
         const bool hit = bx >= 0 && bx < a.jb_n[0] && by >= 0 && by < a.jb_n[1] && bz >= 0 && bz < a.jb_n[2];
         if (hit) {
-            T v[1] = {0};
+            T nu = 0;
             if (active && !wall && in_probe<D>(g, xg)) {
 #pragma unroll
-                for (int c = 0; c < D; ++c) v[0] += a.dir[c] * un[c];
+                for (int c = 0; c < D; ++c) nu += a.dir[c] * un[c];
             }
-            double s[1];
-            block_sum<TL::NT, 1, T>(v, s, red);
-            if (tid == 0) a.jslot[bx + a.jb_n[0] * (by + a.jb_n[1] * bz)] = s[0];
+            store_probe_partials<TL::NT, T>(nu, nu * nu, a.jslot, a.jsq, bx + a.jb_n[0] * (by + a.jb_n[1] * bz), red);
         }
     }
 }
@@ -510,6 +541,10 @@ __global__ void __launch_bounds__(TX * TY * TZ) adj_step_kernel(Geom g, AdjArgs<
         const T M0 = m0[mc];
         a.lam_out[gi] = (T)3 * M0;
         const bool probe = a.src && !wall && in_probe<D>(g, xg);
+        T nu = 0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) nu += a.dir[c] * u[c];
+        const T f = probe ? src_factor(a, nu) : (T)1;
 #pragma unroll
         for (int e = 0; e < D; ++e) {
             T v = (T)3 * m1[e * M + mc] - (T)3 * u[e] * M0;
@@ -520,7 +555,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) adj_step_kernel(Geom g, AdjArgs<
                 v += (T)9 * m2s[mc] * u[c];
                 v += A * (m2s[mc - mstride] - m2s[mc + mstride]);
             }
-            if (probe) v += a.phi_dir[e];
+            if (probe) v += a.phi_dir[e] * f;
             a.lam_out[(1 + e) * N + gi] = v;
         }
     }
@@ -706,28 +741,48 @@ __global__ void motion_reduce_kernel(const double* __restrict__ mslot, int nsb, 
     }
 }
 
-// Objective: j_n = sum of the probe blocks' partials of step n (block order), then J = phi sum_n j_n
-// (Eq. objective1 with phi = 0 as a rectangle rule over n = 1..Nt).  Deterministic.
-__global__ void objective_reduce_kernel(const double* __restrict__ jslot, int njb, int Nt, double phi,
-                                        double* __restrict__ jstep, double* __restrict__ J) {
-    __shared__ double red[32];
+// Objective (Eq. objective1 as a rectangle rule over n = 1..Nt): j_n and q_n = the sums of the probe blocks'
+// partials of n.u and (n.u)^2 of step n (block order); E = phi sum_n j_n, S2 = phi sum_n q_n, V = S2 - E^2 and
+// J1 = E - phi_var V.  Writes obj = {J1, E, V, 1 + 2 phi_var E} (the last is the adjoint source's constant).
+// jsq_off = 0 (phi_var = 0): no squares were summed, J1 = E and V is NaN.  Deterministic.
+__global__ void objective_reduce_kernel(const double* __restrict__ jslot, long long jsq_off, int njb, int Nt,
+                                        double phi, double phi_var, double* __restrict__ jstep,
+                                        double* __restrict__ obj) {
+    __shared__ double red[2][32];
     const int tid = threadIdx.x;
-    double tot = 0.0;
+    double tot = 0.0, tsq = 0.0;
     for (int n = 1 + tid; n <= Nt; n += blockDim.x) {
         const double* js = jslot + (long long)n * njb;
-        double v = 0.0;
-        for (int b = 0; b < njb; ++b) v += js[b];
+        double v = 0.0, q = 0.0;
+        for (int b = 0; b < njb; ++b) {
+            v += js[b];
+            if (jsq_off != 0) q += js[jsq_off + b];
+        }
         jstep[n] = v;
         tot += v;
+        tsq += q;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    if ((tid & 31) == 0) red[tid >> 5] = tot;
+    for (int o = 16; o > 0; o >>= 1) {
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        tsq += __shfl_xor_sync(0xffffffffu, tsq, o);
+    }
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = tot;
+        red[1][tid >> 5] = tsq;
+    }
     __syncthreads();
     if (tid == 0) {
-        double s = 0.0;
-        for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) s += red[i];
-        *J = s * phi;
+        double s = 0.0, sq = 0.0;
+        for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) {
+            s += red[0][i];
+            sq += red[1][i];
+        }
+        const double E = s * phi, V = jsq_off != 0 ? sq * phi - E * E : __longlong_as_double(0x7ff8000000000000LL);  // quiet NaN
+        obj[0] = jsq_off != 0 ? E - phi_var * V : E;
+        obj[1] = E;
+        obj[2] = V;
+        obj[3] = 1.0 + 2.0 * phi_var * E;
     }
 }
 
