@@ -17,8 +17,10 @@ positions of the mapping kernel, taken from the real part).
 Pinned by the tests in ``tests/test_oracle_*.py``: lattice isotropy, the exact shear-wave decay factor,
 uniform Brinkman relaxation, Couette / Brinkman-channel steady states against a direct linear solve,
 mass and momentum conservation, mapping partition of unity / shift invariance / brute force / transpose,
-filter invariants and transposes, and the adjoint against complex-step JVPs and central finite
-differences.  The paper's own objective values (Sec. 4.1 table) depend on figure-only geometry:
+filter invariants and transposes, the adjoint against complex-step JVPs and central finite
+differences, the objective J1 against numpy's sample mean and variance, and the rotated-body mapping (quarter
+turns against ``numpy.rot90``, kept totals, the first moment turned by e^{i theta}, the rigid rotation's angular
+moment, complex-step derivatives, the adjoint with angle knots by complex step and central differences).  The paper's own objective values (Sec. 4.1 table) depend on figure-only geometry:
 parity unpinned for that full-problem value only.
 """
 from __future__ import annotations
@@ -89,6 +91,7 @@ class Problem:
     Nt: int = 10                      # number of time steps
     K: int = 2                        # number of motion knots
     R_t: float = 1.0                  # temporal filter radius in steps (Eq. chi_filtered)
+    R_w: float = 1.0                  # temporal filter radius of the rotation angle in steps (Eq. psi_filtered)
     filter_R: float = 0.0             # density filter radius in design cells (Eq. filtering); <= 1 is identity
     beta: float = 0.0                 # Heaviside projection steepness (Eq. projection); 0 = identity
     eta: float = 0.5                  # projection threshold
@@ -346,6 +349,124 @@ def map_bruteforce(kref, o, prob: Problem):
 
 
 # ---------------------------------------------------------------------------------------------
+# Rigid rotation about an axis parallel to z (Sec. 2.3, Eqs. rigid_body_position, rigid_body_velocity, kappa,
+# u_s; Sec. 2.5, the derivatives of x^ref and u^S,ref with respect to theta).  The rotated design lattice is no
+# longer aligned with the analysis axes, so these functions write the mapping out as a dense weight matrix
+# W[x, j] over every analysis node x and every node j of the extended design grid (tiny grids only).
+# ---------------------------------------------------------------------------------------------
+
+
+def rotation_matrix(theta):
+    """R(theta) of Eq. rigid_body_position (acts on the x-y components)."""
+    c, s = np.cos(theta), np.sin(theta)
+    return np.array([[c, -s], [s, c]])
+
+
+def rotation_matrix_d(theta):
+    """dR/dtheta: the matrix of Eq. rigid_body_velocity and of d x^ref / d theta."""
+    c, s = np.cos(theta), np.sin(theta)
+    return np.array([[-s, -c], [c, -s]])
+
+
+def rotation_matrix_dd(theta):
+    """d^2R/dtheta^2: the matrix of d u^S,ref / d theta (per unit omega)."""
+    c, s = np.cos(theta), np.sin(theta)
+    return np.array([[-c, s], [-s, -c]])
+
+
+def design_arms(prob: Problem):
+    """xi_j - xi^G for every node j of the extended design grid, shape (N_d, d), in the order of kref.reshape(-1)."""
+    js = np.stack(np.meshgrid(*[np.arange(n, dtype=np.float64) for n in prob.ext], indexing="ij"), axis=-1)
+    xi_g = (np.asarray(prob.ext, dtype=np.float64) - 1.0) / 2.0
+    return js.reshape(-1, prob.d) - xi_g[None, :]
+
+
+def rotated_reference(prob: Problem, o, theta):
+    """x^ref_j = R(theta)(xi_j - xi^G) + x^G (Eq. rigid_body_position) and d x^ref_j / d theta, shape (N_d, d).
+
+    o is the analysis coordinate of design index 0 at theta = 0 (so x^G = o + xi^G, and theta = 0 gives the
+    translated lattice x^ref_j = j + o).  In 3D the rotation turns x and y about an axis parallel to z.
+    """
+    arm = design_arms(prob)
+    xi_g = (np.asarray(prob.ext, dtype=np.float64) - 1.0) / 2.0
+    dtype = np.result_type(theta, np.asarray(o), np.float64)
+    xref = arm.astype(dtype)
+    xref[:, :2] = arm[:, :2] @ rotation_matrix(theta).T
+    xref = xref + (np.asarray(o) + xi_g)[None, :]
+    dxref = np.zeros_like(xref)
+    dxref[:, :2] = arm[:, :2] @ rotation_matrix_d(theta).T
+    return xref, dxref
+
+
+def weight_matrix(prob: Problem, xref):
+    """W[x, j] = prod_a w(x_a - x^ref_{j,a}) (the weight function of Eqs. kappa, u_s) and dW/dx^ref_{j,a}.
+
+    Periodic axes take the nearest periodic image of the displacement; on wall axes nothing is folded, so weight
+    that lands outside the grid is dropped (as in ``map_bruteforce``).  Derivatives use ``dw1``'s pieces.
+    """
+    d = prob.d
+    X = np.stack(np.meshgrid(*[np.arange(n, dtype=np.float64) for n in prob.shape], indexing="ij"),
+                 axis=-1).reshape(-1, d)
+    ws, dws = [], []
+    for a in range(d):
+        r = X[:, a][:, None] - xref[:, a][None, :]
+        if prob.periodic[a]:
+            n = prob.shape[a]
+            r = r - n * np.round(np.real(r) / n)
+        ws.append(w1(r, prob.kernel))
+        dws.append(dw1(r, prob.kernel))
+    W = ws[0]
+    for a in range(1, d):
+        W = W * ws[a]
+    dW = []
+    for a in range(d):
+        g = -dws[a]  # d w(x - x^ref) / d x^ref = -w'(r)
+        for b in range(d):
+            if b != a:
+                g = g * ws[b]
+        dW.append(g)
+    return W, dW
+
+
+def map_rotated(kref, o, theta, omega, uG, prob: Problem, with_grad=False):
+    """kappa(x) = sum_j W(x, x^ref_j) kappa^ref_j and u^S(x) = sum_j W(x, x^ref_j) u^S,ref_j (Eqs. kappa, u_s) for the
+    rotated pose, u^S,ref_j = R'(theta)(xi_j - xi^G) omega + u^G (Eq. rigid_body_velocity).
+
+    Returns kappa (shape), u^S (d, shape) and, with_grad, a dict of the derivatives with respect to o_a (= x^G_a),
+    theta, omega and u^G_a (the last is C = sum_j W, the same for every component), plus W itself.
+    """
+    d = prob.d
+    xref, dxref = rotated_reference(prob, o, theta)
+    W, dW = weight_matrix(prob, xref)
+    arm = design_arms(prob)
+    kr = kref.reshape(-1)
+    dtype = np.result_type(W, theta, omega, uG, np.float64)
+    vref = np.zeros((arm.shape[0], d), dtype=dtype)
+    vref[:, :2] = (arm[:, :2] @ rotation_matrix_d(theta).T) * omega
+    vref = vref + np.asarray(uG)[None, :]
+    shp = prob.shape
+    kappa = (W @ kr).reshape(shp)
+    uS = np.stack([(W @ vref[:, b]).reshape(shp) for b in range(d)])
+    if not with_grad:
+        return kappa, uS
+    dWdth = sum(dW[a] * dxref[:, a][None, :] for a in range(d))
+    dv_dth = np.zeros_like(vref)
+    dv_dth[:, :2] = (arm[:, :2] @ rotation_matrix_dd(theta).T) * omega
+    dv_dom = np.zeros_like(vref)
+    dv_dom[:, :2] = arm[:, :2] @ rotation_matrix_d(theta).T
+    G = {
+        "W": W,
+        "dk_do": [(dW[a] @ kr).reshape(shp) for a in range(d)],
+        "dk_dth": (dWdth @ kr).reshape(shp),
+        "duS_do": [[(dW[a] @ vref[:, b]).reshape(shp) for b in range(d)] for a in range(d)],
+        "duS_dth": [(dWdth @ vref[:, b] + W @ dv_dth[:, b]).reshape(shp) for b in range(d)],
+        "duS_dom": [(W @ dv_dom[:, b]).reshape(shp) for b in range(d)],
+        "C": W.sum(axis=1).reshape(shp),
+    }
+    return kappa, uS, G
+
+
+# ---------------------------------------------------------------------------------------------
 # Shape parametrisation (Sec. 3.1, Eqs. filtering, projection; Sec. 2.3, Eq. kappa_ref)
 # ---------------------------------------------------------------------------------------------
 
@@ -490,6 +611,16 @@ def interp_matrix(K, Nt):
     return M
 
 
+def angles(aknots, Nt, R_w):
+    """Per-step rotation angle theta_n and angular velocity omega_n = theta_n - theta_{n-1} (Eqs. psi_filtered, theta,
+    omega): the angle knots (radians, shape (K_w,)) are filtered and interpolated like the position knots."""
+    th = interp_matrix(len(aknots), Nt) @ motion_filter(np.asarray(aknots)[:, None], Nt, R_w)[:, 0]
+    om = np.zeros_like(th)
+    om[1:] = th[1:] - th[:-1]
+    om[0] = om[1]
+    return th, om
+
+
 def positions(knots, Nt, R_t):
     """Per-step offsets s_n (n = 0..Nt) and velocities u^G_n = s_n - s_{n-1} (Eq. u_g, backward difference)."""
     s = interp_matrix(knots.shape[0], Nt) @ motion_filter(knots, Nt, R_t)
@@ -547,13 +678,14 @@ def initial_state(prob: Problem, dtype=np.float64):
     return p, u
 
 
-def forward(prob: Problem, kref, s, uG, store=False, state0=None):
+def forward(prob: Problem, kref, s, uG, store=False, state0=None, rot=None):
     """Run Nt LKS steps (Algorithm 1, forward loop) and return J1 = E - phi_V V (Eq. objective1).
 
     E and S2 are rectangle-rule means over n = 1..Nt and the fluid nodes of O_target of n.u and (n.u)^2;
     V = S2 - E^2.
 
-    kref is the extended design array kappa^ref (margin included); s, uG are (Nt+1, d) offsets and velocities.
+    kref is the extended design array kappa^ref (margin included); s, uG are (Nt+1, d) offsets and velocities;
+    rot = (theta, omega), each (Nt+1,), turns the body (``map_rotated``); None keeps theta = 0 (``map_gather``).
     With store=True the list of states (p_n, u_n), n = 0..Nt, is returned too.
     """
     c, w = lattice(prob.lattice)
@@ -569,8 +701,11 @@ def forward(prob: Problem, kref, s, uG, store=False, state0=None):
     S2 = 0.0
     for n in range(1, prob.Nt + 1):
         o = o0 + s[n]
-        kappa, C = map_gather(kref, o, prob)
-        uS = np.stack([uG[n, a] * C for a in range(prob.d)])
+        if rot is None:
+            kappa, C = map_gather(kref, o, prob)
+            uS = np.stack([uG[n, a] * C for a in range(prob.d)])
+        else:
+            kappa, uS = map_rotated(kref, o, rot[0][n], rot[1][n], uG[n], prob)
         p, u = lks_step(p, u, kappa, uS, A, c, w, mask, uw)
         E = E + (phi * u).sum()
         if prob.phi_var != 0.0:
@@ -581,7 +716,7 @@ def forward(prob: Problem, kref, s, uG, store=False, state0=None):
     return (J, states) if store else J
 
 
-def adjoint(prob: Problem, kref, s, uG, states):
+def adjoint(prob: Problem, kref, s, uG, states, rot=None):
     """Exact discrete adjoint of ``forward`` (reverse sweep of Algorithm 1; discrete form of Eqs. ap_tmp-as).
 
     Returns dJ/dkref (extended grid), dJ/ds_n and dJ/du^G_n for n = 0..Nt (row 0 is zero).
@@ -594,6 +729,9 @@ def adjoint(prob: Problem, kref, s, uG, states):
       b4  dJ/dkref += M^T kappa-bar (transposed mapping)
       b5  dJ/ds_n = sum_x kappa-bar dkappa/ds + (u^S-bar . u^G) dC/ds;  dJ/du^G_n = sum_x u^S-bar C
     The objective's own source dJ/du_n (``objective_source``) uses the mean E of the stored forward run.
+    With rot = (theta, omega) (``forward``'s rotated pose) b4 and b5 go through the dense ``map_rotated``, and
+    dJ/dtheta_n = sum_x kappa-bar dkappa/dtheta + u^S-bar . du^S/dtheta, dJ/domega_n = sum_x u^S-bar . du^S/domega
+    are returned as two more (Nt+1,) arrays.
     """
     c, w = lattice(prob.lattice)
     A = viscosity_A(prob.nu)
@@ -609,23 +747,36 @@ def adjoint(prob: Problem, kref, s, uG, states):
     g_kref = np.zeros(prob.ext, dtype=dtype)
     g_s = np.zeros((prob.Nt + 1, d), dtype=dtype)
     g_uG = np.zeros((prob.Nt + 1, d), dtype=dtype)
+    g_th = np.zeros(prob.Nt + 1, dtype=dtype)
+    g_om = np.zeros(prob.Nt + 1, dtype=dtype)
     for n in range(prob.Nt, 0, -1):
         o = o0 + s[n]
-        kappa, C, dk, dC = map_gather(kref, o, prob, with_grad=True)
+        if rot is None:
+            kappa, C, dk, dC = map_gather(kref, o, prob, with_grad=True)
+            uS = np.stack([uG[n, a] * C for a in range(d)])
+        else:
+            kappa, uS, G = map_rotated(kref, o, rot[0][n], rot[1][n], uG[n], prob, with_grad=True)
         u_n = states[n][1]
         u_prev = states[n - 1][1]
-        uS = np.stack([uG[n, a] * C for a in range(d)])
         # b3: Brinkman and wall adjoint, local sensitivities
         ubar = np.where(mask[None], 0.0, lam_u / (1.0 + kappa))
         pbar = lam_p
         kbar = np.where(mask, 0.0, sum(lam_u[a] * (uS[a] - u_n[a]) for a in range(d)) / (1.0 + kappa))
         uSbar = np.where(mask[None], 0.0, lam_u * kappa / (1.0 + kappa))
         # b4, b5
-        g_kref = g_kref + map_gather_T(kbar, o, prob)
-        Cbar = sum(uSbar[a] * uG[n, a] for a in range(d))
-        for a in range(d):
-            g_s[n, a] = (kbar * dk[a]).sum() + (Cbar * dC[a]).sum()
-            g_uG[n, a] = (uSbar[a] * C).sum()
+        if rot is None:
+            g_kref = g_kref + map_gather_T(kbar, o, prob)
+            Cbar = sum(uSbar[a] * uG[n, a] for a in range(d))
+            for a in range(d):
+                g_s[n, a] = (kbar * dk[a]).sum() + (Cbar * dC[a]).sum()
+                g_uG[n, a] = (uSbar[a] * C).sum()
+        else:
+            g_kref = g_kref + (G["W"].T @ kbar.reshape(-1)).reshape(prob.ext)
+            for a in range(d):
+                g_s[n, a] = (kbar * G["dk_do"][a]).sum() + sum((uSbar[b] * G["duS_do"][a][b]).sum() for b in range(d))
+                g_uG[n, a] = (uSbar[a] * G["C"]).sum()
+            g_th[n] = (kbar * G["dk_dth"]).sum() + sum((uSbar[b] * G["duS_dth"][b]).sum() for b in range(d))
+            g_om[n] = sum((uSbar[b] * G["duS_dom"][b]).sum() for b in range(d))
         # b1: reverse stream and local moments
         M0 = 0.0
         M1 = [0.0] * d
@@ -654,6 +805,8 @@ def adjoint(prob: Problem, kref, s, uG, states):
         lam_u = np.stack(new_u)
         if n - 1 >= 1:
             lam_u = lam_u + objective_source(prob, phi, E, u_prev)
+    if rot is not None:
+        return g_kref, g_s, g_uG, g_th, g_om
     return g_kref, g_s, g_uG
 
 
@@ -670,11 +823,12 @@ def design_to_kref(prob: Problem, gamma):
     return embed_margin(kr, prob.margin), gt, gb
 
 
-def solve(prob: Problem, gamma, knots, store=False):
-    """J(gamma, knots) of the whole chain."""
+def solve(prob: Problem, gamma, knots, store=False, aknots=None):
+    """J(gamma, knots) of the whole chain; aknots (angle knots in radians) turn the body (Sec. 2.4)."""
     kref, _, _ = design_to_kref(prob, gamma)
     s, uG = positions(knots, prob.Nt, prob.R_t)
-    return forward(prob, kref, s, uG, store=store)
+    rot = None if aknots is None else angles(aknots, prob.Nt, prob.R_w)
+    return forward(prob, kref, s, uG, store=store, rot=rot)
 
 
 def knot_gradient(prob: Problem, g_s, g_uG):
@@ -687,15 +841,28 @@ def knot_gradient(prob: Problem, g_s, g_uG):
     return motion_filter_T(gf, prob.Nt, prob.R_t)
 
 
-def gradient(prob: Problem, gamma, knots):
-    """Return J, dJ/dgamma (inner design grid), dJ/dknots (K, d)."""
+def angle_gradient(prob: Problem, g_th, g_om, K_w):
+    """Chain rule from per-step (dJ/dtheta_n, dJ/domega_n) to the angle knots (the same steps as ``knot_gradient``)."""
+    gt = g_th.copy()
+    gt[1:] += g_om[1:]
+    gt[:-1] -= g_om[1:]
+    gf = interp_matrix(K_w, prob.Nt).T @ gt
+    return motion_filter_T(gf[:, None], prob.Nt, prob.R_w)[:, 0]
+
+
+def gradient(prob: Problem, gamma, knots, aknots=None):
+    """Return J, dJ/dgamma (inner design grid), dJ/dknots (K, d) and, with angle knots, dJ/daknots (K_w,)."""
     kref, gt, gb = design_to_kref(prob, gamma)
     s, uG = positions(knots, prob.Nt, prob.R_t)
-    J, states = forward(prob, kref, s, uG, store=True)
-    g_kref, g_s, g_uG = adjoint(prob, kref, s, uG, states)
+    rot = None if aknots is None else angles(aknots, prob.Nt, prob.R_w)
+    J, states = forward(prob, kref, s, uG, store=True, rot=rot)
+    res = adjoint(prob, kref, s, uG, states, rot=rot)
+    g_kref, g_s, g_uG = res[:3]
     g_kr = strip_margin(g_kref, prob.margin)
     g_gb = g_kr * kappa_ref_deriv(gb, prob.kappa_max, prob.q)
     g_gt = g_gb * projection_deriv(gt, prob.beta, prob.eta)
     g_gamma = density_filter_T(g_gt, prob.filter_R)
     g_knots = knot_gradient(prob, g_s, g_uG)
+    if rot is not None:
+        return J, g_gamma, g_knots, angle_gradient(prob, res[3], res[4], len(aknots))
     return J, g_gamma, g_knots

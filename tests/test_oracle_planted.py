@@ -99,3 +99,27 @@ def test_variance_source_mistake_is_caught(monkeypatch, mistake):
         bad = lambda prob, phi, E, u: phi * (1.0 - 2.0 * prob.phi_var * E + 2.0 * prob.phi_var * fa(prob, u))
     monkeypatch.setattr(L, "objective_source", bad)
     assert dot_gap() > 1e-6
+
+
+def test_rotation_mistakes_are_caught(monkeypatch):
+    # each plausible slip in the rotated mapping makes one of its pins fail (the pins pass unpatched)
+    import test_oracle_rotation as R
+
+    R.test_first_moment_turns_by_exp_i_theta(0.4)
+    R.test_mapped_velocity_is_a_rigid_rotation(0.7)
+    R.test_mapping_derivatives_match_complex_step("D2Q9", "linear")
+    rot, rot_d, rot_dd = L.rotation_matrix, L.rotation_matrix_d, L.rotation_matrix_dd
+    # the body turned the wrong way (R^T for R)
+    monkeypatch.setattr(L, "rotation_matrix", lambda th: rot(th).T)
+    with pytest.raises(AssertionError):
+        R.test_first_moment_turns_by_exp_i_theta(0.4)
+    monkeypatch.setattr(L, "rotation_matrix", rot)
+    # the rigid velocity with the wrong sense of rotation
+    monkeypatch.setattr(L, "rotation_matrix_d", lambda th: -rot_d(th))
+    with pytest.raises(AssertionError):
+        R.test_mapped_velocity_is_a_rigid_rotation(0.7)
+    monkeypatch.setattr(L, "rotation_matrix_d", rot_d)
+    # d u^S,ref / d theta dropped
+    monkeypatch.setattr(L, "rotation_matrix_dd", lambda th: 0.0 * rot_dd(th))
+    with pytest.raises(AssertionError):
+        R.test_mapping_derivatives_match_complex_step("D2Q9", "linear")
