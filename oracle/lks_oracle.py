@@ -20,7 +20,9 @@ mass and momentum conservation, mapping partition of unity / shift invariance / 
 filter invariants and transposes, the adjoint against complex-step JVPs and central finite
 differences, the objective J1 against numpy's sample mean and variance, and the rotated-body mapping (quarter
 turns against ``numpy.rot90``, kept totals, the first moment turned by e^{i theta}, the rigid rotation's angular
-moment, complex-step derivatives, the adjoint with angle knots by complex step and central differences).  The paper's own objective values (Sec. 4.1 table) depend on figure-only geometry:
+moment, complex-step derivatives, the adjoint with angle knots by complex step and central differences), and the
+oar objective J2 (uniform flow, fluid in rigid motion with the body, spinning and translating bodies in still
+fluid; its adjoint by complex step and central differences).  The paper's own objective values (Sec. 4.1 table) depend on figure-only geometry:
 parity unpinned for that full-problem value only.
 """
 from __future__ import annotations
@@ -99,6 +101,11 @@ class Problem:
     probe_hi: tuple = ()              # exclusive upper corner
     direction: tuple = ()             # n of Eq. objective1
     phi_var: float = 0.0              # phi of Eq. objective1: weight of the variance V in J1 = E - phi V
+    objective: str = "J1"             # "J1" (Eq. objective1) or "J2" (Eq. objective2, the oar)
+    w_D: float = 0.0                  # weights of F_D and T in J2 = F_L + w_D F_D + w_T T (Eq. objective2)
+    w_T: float = 0.0
+    drag_span: float = 1.0            # x_2^max - x_2^min of F_D (cells)
+    l_m: float = 1.0                  # moment arm l_m of T (cells)
     wall_velocity: dict = field(default_factory=dict)  # {(axis, side): vector}; side 0 = plane 0, 1 = plane n-1
 
     @property
@@ -670,6 +677,87 @@ def objective_source(prob: Problem, phi, E, u):
     return phi * (1.0 + 2.0 * prob.phi_var * E - 2.0 * prob.phi_var * flow_along(prob, u))
 
 
+def design_mask(prob: Problem):
+    """The inner design grid D inside the extended one (the margin is fluid and not part of D)."""
+    m = np.zeros(prob.ext, dtype=bool)
+    m[tuple(slice(prob.margin, prob.margin + n) for n in prob.design)] = True
+    return m
+
+
+def oar_force_weights(prob: Problem, r, omega, uG):
+    """g_{j,b} = d j2_n / d F_{j,b} for the Brinkman force density F_j = kappa^ref_j (u^ref_j - u^S,ref_j) of step n
+    (Eq. objective2 read as a rectangle rule over n = 1..Nt): F_L weighs F_1 by 1/(Nt |D|), w_D F_D weighs F_2 by
+    w_D u^G_2 / ((x_2^max - x_2^min) |D|), w_T T weighs e_3ab r_a F_b (r = x^ref - x^G) by w_T omega / (2 pi l_m |D|)."""
+    nD = float(np.prod(prob.design))
+    cL = 1.0 / (prob.Nt * nD)
+    cD = prob.w_D / (prob.drag_span * nD)
+    cT = prob.w_T / (2.0 * np.pi * prob.l_m * nD)
+    inD = design_mask(prob).reshape(-1)
+    g = np.zeros(r.shape, dtype=np.result_type(r, omega, uG, np.float64))
+    g[:, 0] = np.where(inD, cL - cT * omega * r[:, 1], 0.0)
+    g[:, 1] = np.where(inD, cD * uG[1] + cT * omega * r[:, 0], 0.0)
+    return g, cD, cT, inD
+
+
+def oar_terms(prob: Problem, kref, u, o, theta, omega, uG):
+    """(F_L, F_D, T) integrands of step n of Eq. objective2 (already divided by their normalisations): u^ref_j is the
+    transposed-mapped velocity sum_x W(x, x^ref_j) u(x), u^S,ref_j that of Eq. rigid_body_velocity."""
+    xref, _ = rotated_reference(prob, o, theta)
+    W, _ = weight_matrix(prob, xref)
+    arm = design_arms(prob)
+    d = prob.d
+    U = np.stack([W.T @ u[b].reshape(-1) for b in range(d)], axis=1)
+    v = np.zeros_like(U)
+    v[:, :2] = (arm[:, :2] @ rotation_matrix_d(theta).T) * omega
+    v = v + np.asarray(uG)[None, :]
+    F = kref.reshape(-1)[:, None] * (U - v)
+    r = xref - (np.asarray(o) + (np.asarray(prob.ext, dtype=np.float64) - 1.0) / 2.0)[None, :]
+    nD = float(np.prod(prob.design))
+    inD = design_mask(prob).reshape(-1)
+    FL = np.where(inD, F[:, 0], 0.0).sum() / (prob.Nt * nD)
+    FD = uG[1] * np.where(inD, F[:, 1], 0.0).sum() / (prob.drag_span * nD)
+    T = omega * np.where(inD, r[:, 0] * F[:, 1] - r[:, 1] * F[:, 0], 0.0).sum() / (2.0 * np.pi * prob.l_m * nD)
+    return FL, FD, T
+
+
+def oar_step(prob: Problem, kref, u, o, theta, omega, uG, with_grad=False):
+    """j2_n = F_L + w_D F_D + w_T T of step n (Eq. objective2) and, with_grad, its partial derivatives: dJ/du_n (the
+    adjoint source, (d,) + shape), dJ/dkref (explicit, extended grid), dJ/do (= dJ/dx^G), dJ/du^G, dJ/dtheta, dJ/domega."""
+    FL, FD, T = oar_terms(prob, kref, u, o, theta, omega, uG)
+    j2 = FL + prob.w_D * FD + prob.w_T * T
+    if not with_grad:
+        return j2
+    d = prob.d
+    xref, dxref = rotated_reference(prob, o, theta)
+    W, dW = weight_matrix(prob, xref)
+    arm = design_arms(prob)
+    kr = kref.reshape(-1)
+    U = np.stack([W.T @ u[b].reshape(-1) for b in range(d)], axis=1)
+    R1 = arm[:, :2] @ rotation_matrix_d(theta).T   # d u^S,ref / d omega (x-y components), also d r / d theta
+    R2 = arm[:, :2] @ rotation_matrix_dd(theta).T  # d^2 r / d theta^2
+    v = np.zeros_like(U)
+    v[:, :2] = R1 * omega
+    v = v + np.asarray(uG)[None, :]
+    F = kr[:, None] * (U - v)
+    r = xref - (np.asarray(o) + (np.asarray(prob.ext, dtype=np.float64) - 1.0) / 2.0)[None, :]
+    g, cD, cT, inD = oar_force_weights(prob, r, omega, uG)
+    gU = g * kr[:, None]           # d j2 / d u^ref_{j,b}
+    src = np.stack([(W @ gU[:, b]).reshape(prob.shape) for b in range(d)])
+    g_kref = (g * (U - v)).sum(axis=1).reshape(prob.ext)
+    gv = -gU                       # d j2 / d u^S,ref_{j,b}
+    g_uG = gv.sum(axis=0)
+    g_uG[1] = g_uG[1] + cD * np.where(inD, F[:, 1], 0.0).sum()
+    g_om = (gv[:, :2] * R1).sum() + cT * np.where(inD, r[:, 0] * F[:, 1] - r[:, 1] * F[:, 0], 0.0).sum()
+    g_th = (gv[:, :2] * R2).sum() * omega
+    # u^ref moves with x^ref
+    gx = np.stack([sum(gU[:, b] * (dW[a].T @ u[b].reshape(-1)) for b in range(d)) for a in range(d)], axis=1)
+    g_o = gx.sum(axis=0)
+    g_th = g_th + (gx * dxref).sum()
+    # the torque arm r = R(theta)(xi - xi^G)
+    g_th = g_th + (cT * omega * np.where(inD, F[:, 1] * dxref[:, 0] - F[:, 0] * dxref[:, 1], 0.0)).sum()
+    return j2, src, g_kref, g_o, g_uG, g_th, g_om
+
+
 def initial_state(prob: Problem, dtype=np.float64):
     """p = 1/3, u = 0 everywhere, wall nodes at their wall velocity (Sec. 4 initial conditions)."""
     mask, uw = wall_mask(prob)
@@ -679,7 +767,8 @@ def initial_state(prob: Problem, dtype=np.float64):
 
 
 def forward(prob: Problem, kref, s, uG, store=False, state0=None, rot=None):
-    """Run Nt LKS steps (Algorithm 1, forward loop) and return J1 = E - phi_V V (Eq. objective1).
+    """Run Nt LKS steps (Algorithm 1, forward loop) and return J1 = E - phi_V V (Eq. objective1), or J2 (Eq.
+    objective2, ``oar_step`` summed over n = 1..Nt) when prob.objective is "J2".
 
     E and S2 are rectangle-rule means over n = 1..Nt and the fluid nodes of O_target of n.u and (n.u)^2;
     V = S2 - E^2.
@@ -699,6 +788,7 @@ def forward(prob: Problem, kref, s, uG, store=False, state0=None, rot=None):
     states = [(p, u)] if store else None
     E = 0.0
     S2 = 0.0
+    J2 = 0.0
     for n in range(1, prob.Nt + 1):
         o = o0 + s[n]
         if rot is None:
@@ -707,12 +797,17 @@ def forward(prob: Problem, kref, s, uG, store=False, state0=None, rot=None):
         else:
             kappa, uS = map_rotated(kref, o, rot[0][n], rot[1][n], uG[n], prob)
         p, u = lks_step(p, u, kappa, uS, A, c, w, mask, uw)
+        if prob.objective == "J2":
+            th, om = (0.0, 0.0) if rot is None else (rot[0][n], rot[1][n])
+            J2 = J2 + oar_step(prob, kref, u, o, th, om, uG[n])
         E = E + (phi * u).sum()
         if prob.phi_var != 0.0:
             S2 = S2 + (wO * flow_along(prob, u) ** 2).sum()
         if store:
             states.append((p, u))
     J = E if prob.phi_var == 0.0 else E - prob.phi_var * (S2 - E * E)
+    if prob.objective == "J2":
+        J = J2
     return (J, states) if store else J
 
 
@@ -742,8 +837,18 @@ def adjoint(prob: Problem, kref, s, uG, states, rot=None):
     axes = tuple(range(d))
     o0 = prob.origin()
     dtype = np.result_type(kref, s, uG, np.float64)
+    oar = prob.objective == "J2"
+
+    def oar_at(m):
+        th, om = (0.0, 0.0) if rot is None else (rot[0][m], rot[1][m])
+        return oar_step(prob, kref, states[m][1], o0 + s[m], th, om, uG[m], with_grad=True)
+
     lam_p = np.zeros(prob.shape, dtype=dtype)
-    lam_u = objective_source(prob, phi, E, states[prob.Nt][1]).astype(dtype)
+    if oar:
+        src_next = oar_at(prob.Nt)
+        lam_u = src_next[1].astype(dtype)
+    else:
+        lam_u = objective_source(prob, phi, E, states[prob.Nt][1]).astype(dtype)
     g_kref = np.zeros(prob.ext, dtype=dtype)
     g_s = np.zeros((prob.Nt + 1, d), dtype=dtype)
     g_uG = np.zeros((prob.Nt + 1, d), dtype=dtype)
@@ -751,6 +856,14 @@ def adjoint(prob: Problem, kref, s, uG, states, rot=None):
     g_om = np.zeros(prob.Nt + 1, dtype=dtype)
     for n in range(prob.Nt, 0, -1):
         o = o0 + s[n]
+        if oar:
+            # explicit dependences of step n's oar integrand (its u_n source is already in lam_u)
+            _, _, gk2, go2, guG2, gth2, gom2 = src_next
+            g_kref = g_kref + gk2
+            g_s[n] = g_s[n] + go2
+            g_uG[n] = g_uG[n] + guG2
+            g_th[n] = g_th[n] + gth2
+            g_om[n] = g_om[n] + gom2
         if rot is None:
             kappa, C, dk, dC = map_gather(kref, o, prob, with_grad=True)
             uS = np.stack([uG[n, a] * C for a in range(d)])
@@ -768,15 +881,15 @@ def adjoint(prob: Problem, kref, s, uG, states, rot=None):
             g_kref = g_kref + map_gather_T(kbar, o, prob)
             Cbar = sum(uSbar[a] * uG[n, a] for a in range(d))
             for a in range(d):
-                g_s[n, a] = (kbar * dk[a]).sum() + (Cbar * dC[a]).sum()
-                g_uG[n, a] = (uSbar[a] * C).sum()
+                g_s[n, a] += (kbar * dk[a]).sum() + (Cbar * dC[a]).sum()
+                g_uG[n, a] += (uSbar[a] * C).sum()
         else:
             g_kref = g_kref + (G["W"].T @ kbar.reshape(-1)).reshape(prob.ext)
             for a in range(d):
-                g_s[n, a] = (kbar * G["dk_do"][a]).sum() + sum((uSbar[b] * G["duS_do"][a][b]).sum() for b in range(d))
-                g_uG[n, a] = (uSbar[a] * G["C"]).sum()
-            g_th[n] = (kbar * G["dk_dth"]).sum() + sum((uSbar[b] * G["duS_dth"][b]).sum() for b in range(d))
-            g_om[n] = sum((uSbar[b] * G["duS_dom"][b]).sum() for b in range(d))
+                g_s[n, a] += (kbar * G["dk_do"][a]).sum() + sum((uSbar[b] * G["duS_do"][a][b]).sum() for b in range(d))
+                g_uG[n, a] += (uSbar[a] * G["C"]).sum()
+            g_th[n] += (kbar * G["dk_dth"]).sum() + sum((uSbar[b] * G["duS_dth"][b]).sum() for b in range(d))
+            g_om[n] += sum((uSbar[b] * G["duS_dom"][b]).sum() for b in range(d))
         # b1: reverse stream and local moments
         M0 = 0.0
         M1 = [0.0] * d
@@ -804,7 +917,11 @@ def adjoint(prob: Problem, kref, s, uG, states, rot=None):
         lam_p = new_p
         lam_u = np.stack(new_u)
         if n - 1 >= 1:
-            lam_u = lam_u + objective_source(prob, phi, E, u_prev)
+            if oar:
+                src_next = oar_at(n - 1)
+                lam_u = lam_u + src_next[1]
+            else:
+                lam_u = lam_u + objective_source(prob, phi, E, u_prev)
     if rot is not None:
         return g_kref, g_s, g_uG, g_th, g_om
     return g_kref, g_s, g_uG
