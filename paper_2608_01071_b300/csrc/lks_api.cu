@@ -794,28 +794,38 @@ void autotune_rows(lks_ctx* c) {
         // the fused variant takes two steps per launch
         return ms / (float)reps / ((pass == 0 ? c->eng->fused2() : c->eng->fused_adj2()) ? 2.f : 1.f);
     };
+    // Each variant is first sized to about 1.5 ms of launches; then three rounds time every variant once per round
+    // and keep each one's fastest.  Rounds rather than back-to-back trials spread a drift of the clocks over all
+    // candidates instead of favouring the ones timed last.
     for (int pass = 0; pass < 2; ++pass) {
+        struct Cand { int r; int reps; float ms; bool one_step; };
+        std::vector<Cand> cands;
         for (int r : (pass == 0 ? cf : ca)) {
             // not available for this grid / precision
             if (!(pass == 0 ? c->eng->set_rows(r, ra0, c->g) : c->eng->set_rows(rf0, r, c->g))) continue;
-            // size each measurement to about 1.5 ms of launches and keep the fastest of three
             const float est = time_variant(r, pass, 10);
-            const int reps = std::max(10, std::min(2000, (int)(1.5f / std::max(est, 1e-4f))));
-            float ms = est;
-            for (int trial = 0; trial < 3; ++trial) ms = std::min(ms, time_variant(r, pass, reps));
+            cands.push_back({r, std::max(10, std::min(2000, (int)(1.5f / std::max(est, 1e-4f)))), est,
+                             pass == 0 ? !c->eng->fused2() : !c->eng->fused_adj2()});
+        }
+        for (int trial = 0; trial < 3; ++trial)
+            for (Cand& k : cands) {
+                if (!(pass == 0 ? c->eng->set_rows(k.r, ra0, c->g) : c->eng->set_rows(rf0, k.r, c->g)))
+                    throw LksError{LKS_ECUDA, "internal: tuner variant became unavailable"};
+                k.ms = std::min(k.ms, time_variant(k.r, pass, k.reps));
+            }
+        for (const Cand& k : cands) {
             if (std::getenv("LKS_TUNE_VERBOSE"))
                 std::fprintf(stderr, "lks autotune %dx%dx%d %s rows=%d: %.3f us/step (%d launches)\n", c->g.n[0],
-                             c->g.n[1], c->g.n[2], pass == 0 ? "forward" : "adjoint", r, 1e3f * ms, reps);
-            const bool one_step = (pass == 0 ? !c->eng->fused2() : !c->eng->fused_adj2());
-            if (pass == 0 && ms < best_f) {
-                best_f = ms;
-                rf = r;
+                             c->g.n[1], c->g.n[2], pass == 0 ? "forward" : "adjoint", k.r, 1e3f * k.ms, k.reps);
+            if (pass == 0 && k.ms < best_f) {
+                best_f = k.ms;
+                rf = k.r;
             }
-            if (pass == 1 && ms < best_a) {
-                best_a = ms;
-                ra = r;
+            if (pass == 1 && k.ms < best_a) {
+                best_a = k.ms;
+                ra = k.r;
             }
-            if (one_step) (pass == 0 ? one_f : one_a).push_back({ms, r});
+            if (k.one_step) (pass == 0 ? one_f : one_a).push_back({k.ms, k.r});
         }
     }
     // Chains that share the GPU (the recomputation beside the adjoint chain): time the three fastest one-step
@@ -850,21 +860,29 @@ void autotune_rows(lks_ctx* c) {
     };
     float best_pair = 1e30f;
     int rf1 = one_f.empty() ? rf0 : one_f[0].second, ra1 = one_a.empty() ? ra0 : one_a[0].second;
+    struct Pair { int f, a, reps; float ms; };
+    std::vector<Pair> pairs;
     for (const auto& f : one_f)
-        for (const auto& ad : one_a) {
-            if (!c->eng->set_rows(f.second, ad.second, c->g)) continue;
-            const int reps = std::max(10, std::min(2000, (int)(1.5f / std::max(f.first + ad.first, 1e-4f))));
-            float ms = 1e30f;
-            for (int trial = 0; trial < 3; ++trial) ms = std::min(ms, time_pair(reps));
-            if (std::getenv("LKS_TUNE_VERBOSE"))
-                std::fprintf(stderr, "lks autotune %dx%dx%d forward rows=%d beside adjoint rows=%d: %.3f us/step\n",
-                             c->g.n[0], c->g.n[1], c->g.n[2], f.second, ad.second, 1e3f * ms);
-            if (ms < best_pair) {
-                best_pair = ms;
-                rf1 = f.second;
-                ra1 = ad.second;
-            }
+        for (const auto& ad : one_a)
+            if (c->eng->set_rows(f.second, ad.second, c->g))
+                pairs.push_back({f.second, ad.second,
+                                 std::max(10, std::min(2000, (int)(1.5f / std::max(f.first + ad.first, 1e-4f)))), 1e30f});
+    // three rounds over all pairs, as for the single variants
+    for (int trial = 0; trial < 3; ++trial)
+        for (Pair& q : pairs) {
+            if (!c->eng->set_rows(q.f, q.a, c->g)) throw LksError{LKS_ECUDA, "internal: tuner pair became unavailable"};
+            q.ms = std::min(q.ms, time_pair(q.reps));
         }
+    for (const Pair& q : pairs) {
+        if (std::getenv("LKS_TUNE_VERBOSE"))
+            std::fprintf(stderr, "lks autotune %dx%dx%d forward rows=%d beside adjoint rows=%d: %.3f us/step\n",
+                         c->g.n[0], c->g.n[1], c->g.n[2], q.f, q.a, 1e3f * q.ms);
+        if (q.ms < best_pair) {
+            best_pair = q.ms;
+            rf1 = q.f;
+            ra1 = q.a;
+        }
+    }
     cudaEventDestroy(e2);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
