@@ -811,7 +811,7 @@ def forward(prob: Problem, kref, s, uG, store=False, state0=None, rot=None):
     return (J, states) if store else J
 
 
-def adjoint(prob: Problem, kref, s, uG, states, rot=None):
+def adjoint(prob: Problem, kref, s, uG, states, rot=None, terminal=None, lambda0=None):
     """Exact discrete adjoint of ``forward`` (reverse sweep of Algorithm 1; discrete form of Eqs. ap_tmp-as).
 
     Returns dJ/dkref (extended grid), dJ/ds_n and dJ/du^G_n for n = 0..Nt (row 0 is zero).
@@ -827,6 +827,8 @@ def adjoint(prob: Problem, kref, s, uG, states, rot=None):
     With rot = (theta, omega) (``forward``'s rotated pose) b4 and b5 go through the dense ``map_rotated``, and
     dJ/dtheta_n = sum_x kappa-bar dkappa/dtheta + u^S-bar . du^S/dtheta, dJ/domega_n = sum_x u^S-bar . du^S/domega
     are returned as two more (Nt+1,) arrays.
+    terminal = (lam_p, lam_u) is added to the terminal adjoint state (the periodic approximation of Sec. 3.3 passes
+    the previous iteration's lambda_0 there); with a list as lambda0, (lam_p, lam_u) at n = 0 is appended to it.
     """
     c, w = lattice(prob.lattice)
     A = viscosity_A(prob.nu)
@@ -849,6 +851,9 @@ def adjoint(prob: Problem, kref, s, uG, states, rot=None):
         lam_u = src_next[1].astype(dtype)
     else:
         lam_u = objective_source(prob, phi, E, states[prob.Nt][1]).astype(dtype)
+    if terminal is not None:
+        lam_p = lam_p + terminal[0]
+        lam_u = lam_u + terminal[1]
     g_kref = np.zeros(prob.ext, dtype=dtype)
     g_s = np.zeros((prob.Nt + 1, d), dtype=dtype)
     g_uG = np.zeros((prob.Nt + 1, d), dtype=dtype)
@@ -922,6 +927,8 @@ def adjoint(prob: Problem, kref, s, uG, states, rot=None):
                 lam_u = lam_u + src_next[1]
             else:
                 lam_u = lam_u + objective_source(prob, phi, E, u_prev)
+    if lambda0 is not None:
+        lambda0.append((lam_p, lam_u))
     if rot is not None:
         return g_kref, g_s, g_uG, g_th, g_om
     return g_kref, g_s, g_uG
@@ -930,6 +937,33 @@ def adjoint(prob: Problem, kref, s, uG, states, rot=None):
 # ---------------------------------------------------------------------------------------------
 # Full problem: design variables -> J and gradients (Algorithm 1: filters, forward, adjoint, chain rule)
 # ---------------------------------------------------------------------------------------------
+
+
+# ---------------------------------------------------------------------------------------------
+# Constraint functionals (Sec. 2.6, Eqs. constraint1, constraint2, constraint3)
+# ---------------------------------------------------------------------------------------------
+
+
+def solid_volume(gamma, V_max):
+    """G1 = sum_D gamma / (V_max |D|) - 1 and dG1/dgamma (Eq. constraint1; D the inner design grid)."""
+    n = gamma.size
+    return gamma.sum() / (V_max * n) - 1.0, np.full(gamma.shape, 1.0 / (V_max * n))
+
+
+def fluid_volume(gamma, V_max):
+    """G2 = sum_D (1 - gamma) / (V_max |D|) - 1 and dG2/dgamma (Eq. constraint2)."""
+    n = gamma.size
+    return (1.0 - gamma).sum() / (V_max * n) - 1.0, np.full(gamma.shape, -1.0 / (V_max * n))
+
+
+def angular_speed_bound(omega, omega_max, p):
+    """G3 = (sum_n (omega_n / omega_max)^p)^(1/p) - 1 over n = 1..Nt (Eq. constraint3, rectangle rule, unit step)
+    and dG3/domega_n (row 0 is zero: omega_0 enters no step)."""
+    r = omega[1:] / omega_max
+    S = (r ** p).sum()
+    g = np.zeros_like(omega)
+    g[1:] = S ** (1.0 / p - 1.0) * r ** (p - 1) / omega_max
+    return S ** (1.0 / p) - 1.0, g
 
 
 def design_to_kref(prob: Problem, gamma):

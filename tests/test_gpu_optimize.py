@@ -33,3 +33,20 @@ def test_optimize_increases_J():
     assert len(hist) == 5 and hist[-1] > hist[0]
     assert np.all((gamma >= 0.0) & (gamma <= 1.0)) and np.all(np.abs(knots) <= w["amp"])
     s.close()
+
+
+def test_algorithm1_on_the_cuda_solver_with_periodic_warm_start():
+    # beta continuation over two values with the solid-volume constraint, each forward started from the previous
+    # one's final state (Sec. 3.3); J and the gradients come from the CUDA library
+    from paper_2608_01071_b300.algorithm1 import Settings, SolverEvaluator, run
+
+    w = tiny_workload("D2Q9", precision="fp64", Nt=30)
+    ev = SolverEvaluator(w, periodic=True)
+    s = Settings(betas=(1.0, 4.0), n_opt=3, gamma_step=0.05, pos_step=0.3, pos_bound=w["amp"], V_max_solid=0.7,
+                 tol=0.0)
+    gamma, knots, h = run(ev, np.clip(draw_gamma(w), 0.0, 0.6), draw_knots(w), s)
+    ev.close()
+    assert h.beta == [1.0] * 3 + [4.0] * 3 and all(np.isfinite(h.J))
+    assert len(ev.solvers) == 0 and np.all((gamma >= 0.0) & (gamma <= 1.0))
+    # the warm start changes the forward: the second J of beta 1 differs from a cold start at the same design
+    assert h.J[1] != h.J[0]
