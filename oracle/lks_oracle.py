@@ -940,6 +940,97 @@ def adjoint(prob: Problem, kref, s, uG, states, rot=None, terminal=None, lambda0
 
 
 # ---------------------------------------------------------------------------------------------
+# The paper's continuous adjoint, the ALKS (Sec. 2.5, Eqs. ap_tmp-as), as an alternative to ``adjoint``
+# ---------------------------------------------------------------------------------------------
+
+
+def adjoint_alks(prob: Problem, kref, s, uG, states):
+    """Reverse sweep of the ALKS (Sec. 2.5) for J1 with phi_V = 0, and its sensitivities (Eqs. dJdgamma, dJdchi).
+
+    Adjoint moments (p~, u~, s~) at step n; going from n to n-1:
+      f~eq_i(z) = p~ + 3 c_ia (u~_a + 3 s~_ab u_b - p~ u_a) - A c_ia d_b(s~_ab + s~_ba), everything at node z and
+                  step n (u the state of step n, d_b the central difference);
+      p~*, u~*, s~* at node x and step n-1 = sum_i w_i {1, c_i, c_i c_i} f~eq_i(x + c_i)           (Eqs. ap_tmp-as_tmp)
+      sources at step n-1 (Eqs. ap-as): the Brinkman term -3 kappa c_ib u~_b makes u~ implicit, u~ (1 + kappa) =
+      u~* - sum_i w_i c_i dJ/df_i with dJ/df_i = c_i . n / (Nt |O|) on the probe nodes (its p~ and s~ moments vanish
+      by symmetry), so u~ = (u~* - n / (3 Nt |O|)) / (1 + kappa); u~ = 0 on wall nodes, where u is imposed.
+    The terminal state (step Nt) is the source alone.  The sensitivities are the ALKS forms: kappa-bar = 3 (u_n -
+    u^S_n) . u~_n and u^S-bar = -3 kappa_n u~_n, taken through the same transposed mapping and position derivatives as
+    in ``adjoint``.  Returns (dJ/dkref, dJ/ds_n, dJ/du^G_n) like ``adjoint``.
+    Readings: u in f~eq is the state at the same step and node as the adjoint moments; the walls are handled as in
+    the forward (u~ imposed to 0 there, p~ and s~ streamed).
+    """
+    c, w = lattice(prob.lattice)
+    A = viscosity_A(prob.nu)
+    mask, _ = wall_mask(prob)
+    phi = probe_weights(prob)
+    d = prob.d
+    axes = tuple(range(d))
+    o0 = prob.origin()
+    dtype = np.result_type(kref, s, uG, np.float64)
+
+    def brinkman(ustar_src, kappa):
+        return np.where(mask[None], 0.0, ustar_src / (1.0 + kappa))
+
+    kappa_n, C_n = map_gather(kref, o0 + s[prob.Nt], prob)
+    pt = np.zeros(prob.shape, dtype=dtype)
+    st = np.zeros((d, d) + prob.shape, dtype=dtype)
+    ut = brinkman(-phi / 3.0, kappa_n).astype(dtype)
+    g_kref = np.zeros(prob.ext, dtype=dtype)
+    g_s = np.zeros((prob.Nt + 1, d), dtype=dtype)
+    g_uG = np.zeros((prob.Nt + 1, d), dtype=dtype)
+    for n in range(prob.Nt, 0, -1):
+        o = o0 + s[n]
+        kappa, C, dk, dC = map_gather(kref, o, prob, with_grad=True)
+        u_n = states[n][1]
+        uS = np.stack([uG[n, a] * C for a in range(d)])
+        # sensitivities of step n (Eqs. dJdgamma, dJdchi in the notation of ``adjoint``)
+        kbar = np.where(mask, 0.0, 3.0 * sum((u_n[a] - uS[a]) * ut[a] for a in range(d)))
+        uSbar = np.where(mask[None], 0.0, -3.0 * kappa * ut)
+        g_kref = g_kref + map_gather_T(kbar, o, prob)
+        Cbar = sum(uSbar[a] * uG[n, a] for a in range(d))
+        for a in range(d):
+            g_s[n, a] = (kbar * dk[a]).sum() + (Cbar * dC[a]).sum()
+            g_uG[n, a] = (uSbar[a] * C).sum()
+        # f~eq at every node from the moments and the state of step n
+        div = [sum(central_diff(st[a][b] + st[b][a], b) for b in range(d)) for a in range(d)]
+        pstar = np.zeros_like(pt)
+        ustar = np.zeros_like(ut)
+        sstar = np.zeros_like(st)
+        for i in range(len(w)):
+            feq = pt.copy()
+            for a in range(d):
+                if c[i, a] != 0:
+                    inner = ut[a] + 3.0 * sum(st[a][b] * u_n[b] for b in range(d)) - pt * u_n[a]
+                    feq = feq + c[i, a] * (3.0 * inner - A * div[a])
+            g = np.roll(feq, shift=tuple(-int(v) for v in c[i]), axis=axes)  # value at x + c_i
+            pstar = pstar + w[i] * g
+            for a in range(d):
+                ustar[a] = ustar[a] + w[i] * c[i, a] * g
+                for b in range(d):
+                    sstar[a][b] = sstar[a][b] + w[i] * c[i, a] * c[i, b] * g
+        pt, st = pstar, sstar
+        if n - 1 >= 1:
+            kappa_m, _ = map_gather(kref, o0 + s[n - 1], prob)
+            ut = brinkman(ustar - phi / 3.0, kappa_m)
+        else:
+            ut = ustar
+    return g_kref, g_s, g_uG
+
+
+def gradient_alks(prob: Problem, gamma, knots):
+    """``gradient`` with the ALKS sweep in place of the exact discrete adjoint."""
+    kref, gt, gb = design_to_kref(prob, gamma)
+    s, uG = positions(knots, prob.Nt, prob.R_t)
+    J, states = forward(prob, kref, s, uG, store=True)
+    g_kref, g_s, g_uG = adjoint_alks(prob, kref, s, uG, states)
+    g_kr = strip_margin(g_kref, prob.margin)
+    g_gb = g_kr * kappa_ref_deriv(gb, prob.kappa_max, prob.q)
+    g_gt = g_gb * projection_deriv(gt, prob.beta, prob.eta)
+    return J, density_filter_T(g_gt, prob.filter_R), knot_gradient(prob, g_s, g_uG), g_s, g_uG
+
+
+# ---------------------------------------------------------------------------------------------
 # Constraint functionals (Sec. 2.6, Eqs. constraint1, constraint2, constraint3)
 # ---------------------------------------------------------------------------------------------
 
