@@ -1,5 +1,4 @@
 """torch.autograd.Function over the CUDA forward/adjoint, against the FP64 oracle."""
-import numpy as np
 import pytest
 
 from helpers import oracle_run, rel_l2, tiny_workload

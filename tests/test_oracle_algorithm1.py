@@ -8,7 +8,6 @@
   <L, (p_Nt, u_Nt)>, and its state at n = 0 is the gradient of J with respect to the initial state; both are checked
   against complex-step derivatives of the forward.
 """
-import dataclasses
 
 import numpy as np
 import pytest

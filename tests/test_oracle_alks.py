@@ -12,7 +12,6 @@ and finite differences.
   matching the "slight differences" reported against finite differences.
 """
 import numpy as np
-import pytest
 
 import oracle as O
 

@@ -4,7 +4,6 @@ Every check here is fixed by the mathematics of the scheme, not by the oracle it
 lattice isotropy, the exact shear-wave decay factor, the exact uniform Brinkman relaxation and
 the conservation of total pressure and momentum.
 """
-import itertools
 
 import numpy as np
 import pytest

@@ -11,7 +11,6 @@ Per-step integrands against what the mechanics fixes:
 - A body translating vertically in still fluid does the drag work -V^2 sum kappa^ref / ((x_2^max - x_2^min) |D|).
 The adjoint with J2 against complex-step JVPs and central differences, translating and rotating bodies.
 """
-import dataclasses
 
 import numpy as np
 import pytest

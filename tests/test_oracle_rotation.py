@@ -14,7 +14,6 @@ import numpy as np
 import pytest
 
 import oracle as O
-import oracle.lks_oracle as L
 
 
 def problem(name="D2Q9", kernel="linear", periodic=None, shape=None, design=None, **kw):
