@@ -52,13 +52,16 @@ def test_validation_errors_without_gpu():
                    lambda p: setattr(p, "tile_rows_adj", 4),  # adjoint variant without a forward one
                    lambda p: (setattr(p, "tile_rows", 4), setattr(p, "tile_rows_adj", 5)),  # no such variant
                    lambda p: setattr(p, "tile_rows_rec", 4),  # recompute variant without a forward one
-                   lambda p: (setattr(p, "tile_rows", 32), setattr(p, "n", (C.c_int32 * 3)(95, 48, 1)))]:
+                   lambda p: (setattr(p, "tile_rows", 32), setattr(p, "n", (C.c_int32 * 3)(95, 48, 1))),
+                   lambda p: setattr(p, "phi_var", float("nan")), lambda p: setattr(p, "phi_var", float("inf"))]:
         p = _abi.lks_params.from_buffer_copy(base)
         mutate(p)
         assert lib.lks_create(C.byref(p), C.byref(h)) == _abi.LKS_EINVAL
         assert len(lib.lks_last_error_string(None)) > 0
     assert lib.lks_strerror(-5) == b"unstable forward sweep"
     assert lib.lks_forward(None, None, None, None) == _abi.LKS_EINVAL
+    E, V = C.c_double(), C.c_double()
+    assert lib.lks_get_objective_terms(None, C.byref(E), C.byref(V)) == _abi.LKS_EINVAL
 
 
 def test_design_too_large_for_period():
