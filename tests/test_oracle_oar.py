@@ -160,3 +160,25 @@ def test_oar_mistakes_are_caught(monkeypatch):
                         else (lambda r: (r[0], r[1] / uG[1], r[2]))(orig(P, k, u, o, th, om, uG)))
     with pytest.raises(AssertionError):
         test_drag_work_of_a_body_translating_in_still_fluid()
+
+
+@pytest.mark.parametrize("name", ["D2Q9", "D3Q15"])
+@pytest.mark.parametrize("kernel", ["linear", "cosine"])
+def test_translating_oar_terms_from_the_mapped_kappa(name, kernel):
+    # without rotation, sum_j kappa^ref_j u^ref_j = sum_x kappa_n(x) u_n(x) exactly (both are sum_{x,j} W kappa^ref u),
+    # so F_L and F_D follow from the separable mapping of ``map_gather``, a different route from ``oar_terms``'
+    # dense transposed mapping
+    P = oar_problem(name, kernel, periodic=(True,) + (False,) * (2 if name == "D3Q15" else 1))
+    kref, o, _ = body(P, 5)
+    rng = np.random.default_rng(6)
+    u = rng.normal(0.0, 0.02, (P.d,) + P.shape)
+    uG = rng.normal(0.0, 0.01, P.d)
+    FL, FD, T = O.oar_terms(P, kref, u, o, 0.0, 0.0, uG)
+    kappa, _ = O.map_gather(kref, o, P)
+    K = kref.sum()
+    nD = np.prod(P.design)
+    want_L = ((kappa * u[0]).sum() - uG[0] * K) / (P.Nt * nD)
+    want_D = uG[1] * ((kappa * u[1]).sum() - uG[1] * K) / (P.drag_span * nD)
+    assert abs(FL - want_L) <= 1e-13 * (abs(want_L) + abs(uG[0] * K) / (P.Nt * nD))
+    assert abs(FD - want_D) <= 1e-13 * (abs(want_D) + abs(uG[1] ** 2 * K) / (P.drag_span * nD))
+    assert T == 0.0
