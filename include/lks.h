@@ -45,6 +45,7 @@ enum { LKS_MAP_LINEAR = 0, LKS_MAP_COSINE = 1 };               /* Sec. 2.3 trans
 enum { LKS_FP64 = 0, LKS_FP32 = 1 };                           /* state precision (accumulators FP64) */
 enum { LKS_CKPT_FULL = 0, LKS_CKPT_SQRT = 1, LKS_CKPT_REVOLVE = 2 };
 enum { LKS_MODE_JOINT = 0, LKS_MODE_SHAPE = 1, LKS_MODE_MOTION = 2 };
+enum { LKS_OBJ_FLOW = 0, LKS_OBJ_OAR = 1 };
 
 /*
  * Problem parameters (plain data, versioned by `size`).  Fill with lks_default_params, then set fields.
@@ -62,6 +63,12 @@ enum { LKS_MODE_JOINT = 0, LKS_MODE_SHAPE = 1, LKS_MODE_MOTION = 2 };
  *  phi_var        phi of Eq. objective1, the weight of the variance: J1 = E - phi_var V, with E and V the mean
  *                 and variance of n.u over the fluid nodes of O_target and steps 1..Nt; 0 = the mean E alone.
  *                 Any finite value.
+ *  objective      LKS_OBJ_FLOW: J1 of Eq. objective1 (probe box, direction, phi_var).  LKS_OBJ_OAR: J2 of Eq.
+ *                 objective2 for the translating body, J2 = F_L + w_D F_D, with F_L the mean over steps 1..Nt of
+ *                 sum_D kappa^ref (u^ref_x - u^G_x) / |D| and F_D the sum over steps of u^G_y sum_D kappa^ref
+ *                 (u^ref_y - u^G_y) / (drag_span |D|); u^ref is the velocity mapped back onto the design grid,
+ *                 D the inner design grid.  Without rotation the torque term T of Eq. objective2 is zero.
+ *  w_D, drag_span weight of F_D and x_2^max - x_2^min (cells, > 0) of Eq. objective2 (LKS_OBJ_OAR only).
  *  Nt, K          time steps and motion knots (knot k at step k Nt/(K-1)); K >= 2.
  *  R_t            temporal filter radius in steps (Eq. chi_filtered), > 0.
  *  filter_R       density filter radius in design cells (Eq. filtering); <= 1 means identity.
@@ -122,6 +129,10 @@ typedef struct lks_params {
     int32_t tile_rows_adj;
     int32_t tile_rows_rec;
     double phi_var;
+    int32_t objective;
+    int32_t reserved_obj;
+    double w_D;
+    double drag_span;
 } lks_params;
 
 typedef struct lks_ctx lks_ctx;

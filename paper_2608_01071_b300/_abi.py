@@ -16,6 +16,7 @@ LKS_MAP_LINEAR, LKS_MAP_COSINE = 0, 1
 LKS_FP64, LKS_FP32 = 0, 1
 LKS_CKPT_FULL, LKS_CKPT_SQRT, LKS_CKPT_REVOLVE = 0, 1, 2
 LKS_MODE_JOINT, LKS_MODE_SHAPE, LKS_MODE_MOTION = 0, 1, 2
+LKS_OBJ_FLOW, LKS_OBJ_OAR = 0, 1
 
 
 class lks_params(C.Structure):
@@ -52,6 +53,10 @@ class lks_params(C.Structure):
         ("tile_rows_adj", C.c_int32),
         ("tile_rows_rec", C.c_int32),
         ("phi_var", C.c_double),
+        ("objective", C.c_int32),
+        ("reserved_obj", C.c_int32),
+        ("w_D", C.c_double),
+        ("drag_span", C.c_double),
     ]
 
 

@@ -65,6 +65,9 @@ def params_from_workload(w: dict) -> _abi.lks_params:
     p.tile_rows_adj = w.get("tile_rows_adj", 0)
     p.tile_rows_rec = w.get("tile_rows_rec", 0)
     p.phi_var = w.get("phi_var", 0.0)
+    p.objective = _abi.LKS_OBJ_OAR if w.get("objective", "J1") == "J2" else _abi.LKS_OBJ_FLOW
+    p.w_D = w.get("w_D", 0.0)
+    p.drag_span = w.get("drag_span", 1.0)
     return p
 
 

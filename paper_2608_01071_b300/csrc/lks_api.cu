@@ -23,6 +23,7 @@
 #include "lks_step3s.cuh"
 #include "lks_step2r.cuh"
 #include "lks_step2v.cuh"
+#include "lks_oar.cuh"
 #include <map>
 #include <tuple>
 
@@ -107,7 +108,14 @@ struct Engine {
     virtual void kappa_ref(const DesignGeom& dg, const double* gt, double* gb, double* k64, void* k, cudaStream_t s) = 0;
     virtual void init_state(const Geom& g, void* st, cudaStream_t s) = 0;
     virtual void import_state(const Geom& g, const double* p, const double* u, void* st, cudaStream_t s) = 0;
-    virtual void init_adjoint(const Geom& g, const void* fin, void* lam, cudaStream_t s) = 0;
+    virtual void init_adjoint(const Geom& g, const void* fin, void* lam, int src, cudaStream_t s) = 0;
+    // objective J2 (translating body): per-block partials of sum_x kappa u of one step, and its adjoint source
+    virtual void oar_partial(const Geom& g, const Pose* pose, const void* kref, const void* st, double* slot,
+                             cudaStream_t s) = 0;
+    virtual void oar_source(const Geom& g, const OarGeom& o, const Pose* pose, const void* kref, void* lam,
+                            cudaStream_t s) = 0;
+    virtual void oar_sens(const Geom& g, const OarGeom& o, const Pose* poses, const void* kref, const void* boxbuf,
+                          long long bstride, int n_first, int nsteps, void* kbar, double* oms, cudaStream_t s) = 0;
     virtual void export_state(const Geom& g, const void* st, double* p, double* u, cudaStream_t s) = 0;
 };
 
@@ -189,12 +197,29 @@ struct EngineCommon : Engine {
         import_state_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, p, u, (T*)st);
         LKS_LAUNCHED();
     }
-    void init_adjoint(const Geom& g, const void* fin, void* lam, cudaStream_t s) override {
-        init_adjoint_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, (const T*)fin + g.N, (T*)lam);
+    void init_adjoint(const Geom& g, const void* fin, void* lam, int src, cudaStream_t s) override {
+        init_adjoint_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, (const T*)fin + g.N, (T*)lam, src);
         LKS_LAUNCHED();
     }
     void export_state(const Geom& g, const void* st, double* p, double* u, cudaStream_t s) override {
         export_state_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, (const T*)st, p, u);
+        LKS_LAUNCHED();
+    }
+    void oar_partial(const Geom& g, const Pose* pose, const void* kref, const void* st, double* slot,
+                     cudaStream_t s) override {
+        oar_partial_kernel<T, D, HW><<<nblk(g.Fbn, 256), 256, 0, s>>>(g, pose, (const T*)kref, (const T*)st, slot);
+        LKS_LAUNCHED();
+    }
+    void oar_source(const Geom& g, const OarGeom& o, const Pose* pose, const void* kref, void* lam,
+                    cudaStream_t s) override {
+        oar_source_kernel<T, D, HW><<<nblk(g.Fbn, 256), 256, 0, s>>>(g, o, pose, (const T*)kref, (T*)lam);
+        LKS_LAUNCHED();
+    }
+    void oar_sens(const Geom& g, const OarGeom& o, const Pose* poses, const void* kref, const void* boxbuf,
+                  long long bstride, int n_first, int nsteps, void* kbar, double* oms, cudaStream_t s) override {
+        const dim3 grid(nblk(g.Fbn, 256), nsteps, 1);
+        oar_sens_kernel<T, D, HW><<<grid, 256, 0, s>>>(g, o, poses, (const T*)kref, (const T*)boxbuf, bstride, n_first,
+                                                       (T*)kbar, oms);
         LKS_LAUNCHED();
     }
 };
@@ -460,6 +485,10 @@ struct lks_ctx {
     std::unique_ptr<Engine> eng;
     int max_ablocks = 0;  // most adjoint blocks over all tile choices (motion-slot stride)
     int max_njb = 0;      // most probe blocks over all tile choices (objective-slot stride)
+    bool oar = false;     // the objective is J2 of Eq. objective2 (translating body)
+    OarGeom ogeo{};
+    int nbox = 0;         // blocks of the footprint-box kernels (objective J2 slot stride)
+    double *d_oslot = nullptr, *d_oms = nullptr, *d_oar_guG = nullptr, *d_oar_dK = nullptr;
     long long nd = 0, nde = 0;
     std::string err;
     lks_stats stats;
@@ -594,6 +623,12 @@ void validate(const lks_params* p) {
     if (p->mode < LKS_MODE_JOINT || p->mode > LKS_MODE_MOTION) bad("unknown mode");
     if (p->ckpt_slots < 0 || p->seg_len < 0 || p->ckpt_bytes < 0) bad("negative checkpoint setting");
     if (!std::isfinite(p->phi_var)) bad("phi_var must be finite");
+    if (p->objective != LKS_OBJ_FLOW && p->objective != LKS_OBJ_OAR) bad("unknown objective");
+    if (p->objective == LKS_OBJ_OAR) {
+        if (!(p->drag_span > 0.0) || !std::isfinite(p->drag_span) || !std::isfinite(p->w_D))
+            bad("objective J2 needs drag_span > 0 and a finite w_D");
+        if (p->phi_var != 0.0) bad("phi_var belongs to objective J1");
+    }
     // a step-kernel variant code: the forward accepts 3 (two steps per launch), the adjoint does not
     auto variant_ok = [&](int r, bool fwd) {
         if (D == 3) return r == 1 || r == 8 || r == 16 || r == 32 || r == 64 || (fwd && r == 96);
@@ -648,6 +683,10 @@ void setup_geometry(lks_ctx* c) {
     if (cnt <= 0) throw LksError{LKS_EINVAL, "probe box holds no fluid node"};
     g.phi = 1.0 / ((double)p.Nt * (double)cnt);
     g.phi_var = p.phi_var;
+    const double nD = (double)p.nd[0] * p.nd[1] * p.nd[2];
+    c->oar = p.objective == LKS_OBJ_OAR;
+    c->ogeo.cL = 1.0 / ((double)p.Nt * nD);
+    c->ogeo.cD = c->oar ? p.w_D / (p.drag_span * nD) : 0.0;
     for (int a = 0; a < c->D; ++a) {
         const double center = std::isnan(p.base_center[a]) ? (p.n[a] - 1) / 2.0 : p.base_center[a];
         c->o0[a] = center - (g.nde[a] - 1) / 2.0;
@@ -952,6 +991,16 @@ void allocate(lks_ctx* c) {
     c->d_jstep = (double*)dalloc(c, (size_t)(p.Nt + 1) * 8);
     c->d_J = (double*)dalloc(c, 4 * 8);  // J, E, V, 1 + 2 phi_var E
     c->g.obj = c->d_J;
+    if (c->oar) {
+        c->nbox = (int)nblk(c->g.Fbn, 256);
+        c->d_oslot = (double*)dalloc(c, (size_t)(p.Nt + 1) * c->nbox * 2 * 8);
+        c->d_oms = (double*)dalloc(c, (size_t)(p.Nt + 1) * c->nbox * D * 8);
+        LKS_CUDA(cudaMemset(c->d_oms, 0, (size_t)(p.Nt + 1) * c->nbox * D * 8));
+        c->d_oar_guG = (double*)dalloc(c, (size_t)(p.Nt + 1) * D * 8);
+        c->d_oar_dK = (double*)dalloc(c, 8);
+        LKS_CUDA(cudaMemset(c->d_oslot, 0, (size_t)(p.Nt + 1) * c->nbox * 2 * 8));
+        LKS_CUDA(cudaMemset(c->d_oar_guG, 0, (size_t)(p.Nt + 1) * D * 8));
+    }
     c->d_flag = (unsigned*)dalloc(c, 16);
     c->d_kbar = dalloc(c, (size_t)c->Lmax * c->g.Fbn * ts);
     c->nsb = (int)nblk(c->g.Fbn, 256);
@@ -1158,6 +1207,12 @@ void fwd_pair(lks_ctx* c, int n, const void* in, void* out1, void* out2, bool ob
     c->launches++;
 }
 
+// Objective J2: the footprint partials of state n (read before its buffer is reused, in stream order).
+void oar_partial(lks_ctx* c, int n, const void* st, cudaStream_t s) {
+    c->eng->oar_partial(c->g, c->d_pose + n, c->d_kref, st, c->d_oslot + 2LL * n * c->nbox, s);
+    c->launches++;
+}
+
 // Steps n0+1 .. n1 from the state at `in`; dst(n) names the buffer of state n (distinct from the state it is
 // computed from).  Pairs of steps go to one fused launch when the forward kernel supports it.
 template <typename Dst>
@@ -1170,11 +1225,16 @@ const void* run_steps(lks_ctx* c, int n0, int n1, const void* in, Dst&& dst, boo
             void* o1 = dst(n);
             void* o2 = two ? dst(n + 1) : nullptr;
             fwd_pair(c, n, cur, o1, o2, objective, s);
+            if (objective && c->oar) {
+                oar_partial(c, n, o1, s);
+                if (two) oar_partial(c, n + 1, o2, s);
+            }
             cur = two ? o2 : o1;
             n += two ? 2 : 1;
         } else {
             void* o = dst(n);
             fwd_step(c, n, cur, o, objective, s);
+            if (objective && c->oar) oar_partial(c, n, o, s);
             cur = o;
             ++n;
         }
@@ -1257,6 +1317,12 @@ void forward_body(lks_ctx* c, cudaStream_t s) {
                                               c->d_jstep, c->d_J);
     LKS_LAUNCHED();
     c->launches++;
+    if (c->oar) {
+        oar_reduce_kernel<<<1, 256, 0, s>>>(c->ogeo, c->d_oslot, c->nbox, Nt, c->d_pose, c->d_kref64, (long long)c->nde,
+                                            c->D, c->d_J, c->d_oar_guG, c->d_oar_dK);
+        LKS_LAUNCHED();
+        c->launches++;
+    }
     LKS_CUDA(cudaMemcpyAsync(c->h_flag, c->d_flag, 4, cudaMemcpyDeviceToHost, s));
     c->launches_fwd = c->launches;
     c->spans_fwd = c->spans;
@@ -1313,7 +1379,12 @@ void adjoint_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
         const int j = n - a - 1;  // box-buffer slot of step n
         void* bb = c->tptr(c->d_boxbuf, ((long long)buf * c->Lmax + j) * c->box_step);
         const void* fc = c->tptr(c->d_fac, ((long long)buf * c->Lmax + j) * c->g.Fbn);
-        if (c->eng->fused_adj2() && n - 1 > a) {  // steps n and n-1 in one launch
+        // J2 adds the source of step n to lambda_n before the step reads it, so its steps go one per launch
+        if (c->oar) {
+            c->eng->oar_source(c->g, c->ogeo, c->d_pose + n, c->d_kref, c->lam[0], s);
+            c->launches++;
+        }
+        if (c->eng->fused_adj2() && n - 1 > a && !c->oar) {  // steps n and n-1 in one launch
             void* bb2 = c->tptr(c->d_boxbuf, ((long long)buf * c->Lmax + j - 1) * c->box_step);
             const void* fc2 = c->tptr(c->d_fac, ((long long)buf * c->Lmax + j - 1) * c->g.Fbn);
             c->eng->adj2(c->g, c->lam[0], c->lam[1], st[n - 1 - a], st[n - a], st[n - 2 - a], c->d_kref,
@@ -1322,7 +1393,7 @@ void adjoint_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
             n -= 2;
         } else {
             c->eng->adj(c->g, c->lam[0], c->lam[1], st[n - 1 - a], st[n - a], c->d_kref, c->d_pose + n, bb, fc,
-                        n - 1 >= 1 ? 1 : 0, s);
+                        n - 1 >= 1 && !c->oar ? 1 : 0, s);
             c->stats.adjoint_steps++;
             n -= 1;
         }
@@ -1342,6 +1413,11 @@ void sens_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
     c->eng->sens(c->g, c->d_pose, c->d_kref, bb, c->box_step, a + 1, L, shape ? c->d_kbar : nullptr,
                  motion ? c->d_mslot : nullptr, s);
     c->launches++;
+    if (c->oar) {
+        c->eng->oar_sens(c->g, c->ogeo, c->d_pose, c->d_kref, bb, c->box_step, a + 1, L, shape ? c->d_kbar : nullptr,
+                         c->d_oms, s);
+        c->launches++;
+    }
     if (shape) {
         c->eng->gather(c->g, c->d_pose, c->d_kbar, a + 1, L, c->g.Fbn, c->d_dkref, s);
         c->launches++;
@@ -1453,7 +1529,7 @@ void adjoint_body(lks_ctx* c, cudaStream_t s) {
     LKS_CUDA(cudaMemsetAsync(c->d_dkref, 0, c->nde * 8, s));
     LKS_CUDA(cudaMemsetAsync(c->d_gs, 0, (size_t)(Nt + 1) * D * 8, s));
     LKS_CUDA(cudaMemsetAsync(c->d_guG, 0, (size_t)(Nt + 1) * D * 8, s));
-    c->eng->init_adjoint(c->g, c->fin, c->lam[0], s);
+    c->eng->init_adjoint(c->g, c->fin, c->lam[0], c->oar ? 0 : 1, s);
     c->launches++;
     if (c->prm.ckpt == LKS_CKPT_REVOLVE) {
         reverse_revolve(c, 0, c->M, c->free_slots, c->slot[0], s);
@@ -1465,6 +1541,13 @@ void adjoint_body(lks_ctx* c, cudaStream_t s) {
     } else {
         const bool cap = s == c->cap;
         reverse_sqrt_pipelined(c, s, cap ? c->cap2 : c->side, cap ? c->cap3 : c->side2);
+    }
+    if (c->oar) {  // J2's position terms and its explicit dependences on u^G and kappa^ref
+        const long long nmax = std::max<long long>((long long)c->nde, (long long)Nt + 1);
+        oar_apply_kernel<<<nblk(nmax, 256), 256, 0, s>>>(Nt, D, c->nbox, c->d_oms, c->d_oar_guG, c->d_gs, c->d_guG,
+                                                         c->d_oar_dK, c->d_dkref, (long long)c->nde);
+        LKS_LAUNCHED();
+        c->launches++;
     }
     // b6: chain rules
     design_chain_kernel<<<nblk(c->nd, 128), 128, 0, s>>>(c->dg, c->d_dkref, c->d_gt, c->d_gb, c->d_tmp);

@@ -284,9 +284,10 @@ __global__ void init_state_kernel(Geom g, T* __restrict__ st) {
 }
 
 // Adjoint terminal state: lambda_p = 0, lambda_u = dJ/du_Nt, the objective's source of the last step:
-// phi n at the probe nodes, times 1 + 2 phi_var E - 2 phi_var n.u_Nt when the variance term is on (Eq. objective1).
+// phi n at the probe nodes, times 1 + 2 phi_var E - 2 phi_var n.u_Nt when the variance term is on (Eq. objective1);
+// zero when src = 0.
 template <typename T, int D>
-__global__ void init_adjoint_kernel(Geom g, const T* __restrict__ u_fin, T* __restrict__ lam) {
+__global__ void init_adjoint_kernel(Geom g, const T* __restrict__ u_fin, T* __restrict__ lam, int src) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= g.N) return;
     int x[3] = {(int)(i % g.n[0]), (int)((i / g.n[0]) % g.n[1]), (int)(i / ((long long)g.n[0] * g.n[1]))};
@@ -302,7 +303,8 @@ __global__ void init_adjoint_kernel(Geom g, const T* __restrict__ u_fin, T* __re
         f = (T)g.obj[3] - (T)(2.0 * g.phi_var) * nu;
     }
     lam[i] = 0;
-    for (int c = 0; c < D; ++c) lam[(1 + c) * g.N + i] = (probe && !wall) ? (T)(g.dir[c] * g.phi) * f : (T)0;
+    const bool on = src && probe && !wall;  // src = 0: the objective adds its sources elsewhere (J2)
+    for (int c = 0; c < D; ++c) lam[(1 + c) * g.N + i] = on ? (T)(g.dir[c] * g.phi) * f : (T)0;
 }
 
 // FP64 copy of a state (p = p' + 1/3) for the host.

@@ -11,7 +11,8 @@ def oracle_problem(w, **kw):
                   kernel=w["kernel"], Nt=w["Nt"], K=w["K"], R_t=w["R_t"], filter_R=w["filter_R"], beta=w["beta"],
                   eta=w["eta"], probe_lo=tuple(w["probe_lo"]), probe_hi=tuple(w["probe_hi"]),
                   direction=tuple(w["direction"]), base_center=w.get("base_center"),
-                  wall_velocity=dict(w.get("wall_velocity", {})), phi_var=w.get("phi_var", 0.0))
+                  wall_velocity=dict(w.get("wall_velocity", {})), phi_var=w.get("phi_var", 0.0),
+                  objective=w.get("objective", "J1"), w_D=w.get("w_D", 0.0), drag_span=w.get("drag_span", 1.0))
     return P
 
 

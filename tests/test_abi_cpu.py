@@ -53,7 +53,11 @@ def test_validation_errors_without_gpu():
                    lambda p: (setattr(p, "tile_rows", 4), setattr(p, "tile_rows_adj", 5)),  # no such variant
                    lambda p: setattr(p, "tile_rows_rec", 4),  # recompute variant without a forward one
                    lambda p: (setattr(p, "tile_rows", 32), setattr(p, "n", (C.c_int32 * 3)(95, 48, 1))),
-                   lambda p: setattr(p, "phi_var", float("nan")), lambda p: setattr(p, "phi_var", float("inf"))]:
+                   lambda p: setattr(p, "phi_var", float("nan")), lambda p: setattr(p, "phi_var", float("inf")),
+                   lambda p: setattr(p, "objective", 5),
+                   lambda p: (setattr(p, "objective", _abi.LKS_OBJ_OAR), setattr(p, "drag_span", 0.0)),
+                   lambda p: (setattr(p, "objective", _abi.LKS_OBJ_OAR), setattr(p, "drag_span", 9.0),
+                              setattr(p, "phi_var", 1.0))]:
         p = _abi.lks_params.from_buffer_copy(base)
         mutate(p)
         assert lib.lks_create(C.byref(p), C.byref(h)) == _abi.LKS_EINVAL
