@@ -261,8 +261,8 @@ int lks_get_step_sensitivities(lks_ctx* ctx, double* dJ_ds, double* dJ_duG);
 
 /* The two terms of Eq. objective1 for the last forward: *E the mean of n.u, *V its variance (both over the
  * fluid nodes of O_target and steps 1..Nt), so that J = E - phi_var V.  The squares are summed only when
- * phi_var != 0; with phi_var = 0, *V is NaN.  Synchronous.  LKS_ESTATE before the first forward; LKS_EINVAL for a
- * NULL pointer. */
+ * phi_var != 0; with phi_var = 0, *V is NaN.  With objective LKS_OBJ_OAR these are still the probe box's flow terms
+ * (J is J2).  Synchronous.  LKS_ESTATE before the first forward; LKS_EINVAL for a NULL pointer. */
 int lks_get_objective_terms(lks_ctx* ctx, double* E, double* V);
 
 /* Counters of the last forward / adjoint. */

@@ -89,3 +89,24 @@ def test_driver_on_the_oracle_raises_J_and_keeps_the_volume():
     assert h.beta == [1.0] * 4 + [4.0] * 4
     assert h.J[3] > h.J[0]  # ascent within the first beta
     assert max(G[0] for G in h.G) <= 0.05
+
+
+def test_fluid_volume_constraint_and_minimisation():
+    # minimise J = |gamma - T|^2 with T mostly solid while at least 70% of the design stays fluid (G2 <= 0)
+    rng = np.random.default_rng(2)
+    T = rng.uniform(0.5, 1.0, (5, 5))
+
+    class Bowl:
+        def objective(self, beta, gamma, knots):
+            self.g = gamma
+            return ((gamma - T) ** 2).sum()
+
+        def gradient(self):
+            return 2 * (self.g - T), np.zeros((2, 1))
+
+    s = Settings(betas=(1.0,), n_opt=400, maximize=False, gamma_step=0.01, V_max_fluid=0.7, tol=0.0)
+    gamma, _, h = run(Bowl(), np.full(T.shape, 0.9), np.zeros((2, 1)), s)
+    assert h.J[-1] < h.J[0]
+    # G2 = mean(1 - gamma) / 0.7 - 1 <= 0 requires mean(gamma) >= 0.3: not active here, since T already holds 75%
+    assert max(G[0] for G in h.G[-50:]) <= 0.0
+    assert np.max(np.abs(gamma - T)) <= 0.05
