@@ -14,7 +14,9 @@ The code is written to work unchanged on complex128 arrays, so that the tests ca
 directional derivatives by the complex-step method (the only real-valued decisions are the integer tap
 positions of the mapping kernel, taken from the real part).
 
-Pinned by the tests in ``tests/test_oracle_*.py``: lattice isotropy, the exact shear-wave decay factor,
+Pinned by the tests in ``tests/test_oracle_*.py``: lattice isotropy, the equilibrium's zeroth, first and second
+moments against their closed forms (the second moment's u_a u_b fixes the scale of the quadratic terms), the
+exact shear-wave decay factor,
 uniform Brinkman relaxation, Couette / Brinkman-channel steady states against a direct linear solve,
 mass and momentum conservation, mapping partition of unity / shift invariance / brute force / transpose,
 filter invariants and transposes, the adjoint against complex-step JVPs and central finite

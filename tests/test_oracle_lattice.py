@@ -150,3 +150,54 @@ def test_momentum_conservation_without_body_or_walls(name, shape):
     for _ in range(30):
         p, u = O.lks_step(p, u, 0.0, 0.0 * u, O.viscosity_A(0.03), c, w, mask, 0 * u)
         assert np.max(np.abs(u.reshape(d, -1).sum(1) - mom0)) < 1e-14
+
+
+def equilibrium_moment_gap(equilibrium, name, seed=5):
+    """Largest deviation of the equilibrium's moments from their closed forms (Sec. 2.2, Eq. for f_i^eq).
+
+    Derivation.  With f_i = w_i [3p + 3 c.u + (9/2)(c.u)^2 - (3/2) u.u + A c.S.c] and the lattice identities
+    sum_i w_i = 1, sum_i w_i c_a c_b = d_ab / 3, sum_i w_i c_a c_b c_g c_e = (d_ab d_ge + d_ag d_be + d_ae d_bg)/9
+    and vanishing odd moments (pinned by test_isotropy):
+      sum_i f_i       = 3p + (9/2)|u|^2/3 - (3/2)|u|^2 + A tr(S)/3              = 3p + A tr(S)/3,
+      sum_i c_a f_i   = u_a,
+      sum_i c_a c_b f_i = p d_ab + (9/2)(|u|^2 d_ab + 2 u_a u_b)/9 - (1/2)|u|^2 d_ab + A (tr(S) d_ab + 2 S_ab)/9
+                        = p d_ab + u_a u_b + A (tr(S) d_ab + 2 S_ab)/9.
+    The u_a u_b term is the Euler momentum flux of the Navier-Stokes-Brinkman model (Sec. 2.1); it fixes the
+    absolute scale of the quadratic terms, which the uniform fixed point (a ratio) and every linear pin (Couette,
+    shear wave, channel) leave free.  S_ab = du_b/dx_a + du_a/dx_b is taken from a velocity field linear in space,
+    u(x) = U + M x, whose central differences are exact away from the periodic seam: S = M + M^T at the interior
+    nodes, known without differencing anything.  p and U are random per case.
+    """
+    rng = np.random.default_rng(seed)
+    c, w = O.lattice(name)
+    d = c.shape[1]
+    shape = (7,) * d
+    worst = 0.0
+    for A in (0.0, O.viscosity_A(0.02), O.viscosity_A(0.005)):
+        U = rng.uniform(-0.1, 0.1, d)
+        M = rng.uniform(-0.01, 0.01, (d, d))  # u_b(x) = U_b + sum_a M[b, a] x_a, so du_b/dx_a = M[b, a]
+        X = np.meshgrid(*[np.arange(n, dtype=np.float64) for n in shape], indexing="ij")
+        u = np.stack([U[b] + sum(M[b, a] * X[a] for a in range(d)) for b in range(d)])
+        p = 1.0 / 3.0 + 0.02 * rng.standard_normal(shape)
+        feq = equilibrium(p, u, A, c, w)
+        S = M + M.T  # S[a, b] = du_b/dx_a + du_a/dx_b
+        inner = tuple(slice(1, n - 1) for n in shape)
+        f = [fi[inner] for fi in feq]
+        pi, ui = p[inner], u[(slice(None),) + inner]
+        m0 = sum(f)
+        worst = max(worst, np.max(np.abs(m0 - (3.0 * pi + A * np.trace(S) / 3.0))))
+        for a in range(d):
+            m1 = sum(c[i, a] * f[i] for i in range(len(w)))
+            worst = max(worst, np.max(np.abs(m1 - ui[a])))
+            for b in range(d):
+                m2 = sum(c[i, a] * c[i, b] * f[i] for i in range(len(w)))
+                want = pi * (a == b) + ui[a] * ui[b] + A * (np.trace(S) * (a == b) + 2.0 * S[a, b]) / 9.0
+                worst = max(worst, np.max(np.abs(m2 - want)))
+    return worst
+
+
+@pytest.mark.parametrize("name", ["D2Q9", "D3Q15"])
+def test_equilibrium_moments_closed_form(name):
+    # zeroth, first and second moments of f^eq against the closed forms derived from the isotropy identities;
+    # A = 0 isolates the quadratic terms, A != 0 adds the velocity-gradient term
+    assert equilibrium_moment_gap(O.equilibrium, name) < 1e-15

@@ -123,3 +123,34 @@ def test_rotation_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(L, "rotation_matrix_dd", lambda th: 0.0 * rot_dd(th))
     with pytest.raises(AssertionError):
         R.test_mapping_derivatives_match_complex_step("D2Q9", "linear")
+
+
+@pytest.mark.parametrize("name", ["D2Q9", "D3Q15"])
+def test_doubled_quadratic_terms_are_caught(name):
+    # both 1/2 factors of the quadratic terms dropped (9 (c.u)^2 - 3 u.u): the ratio 3 that the uniform fixed
+    # point checks is kept, the second moment's Euler flux u_a u_b doubles
+    from test_oracle_lattice import equilibrium_moment_gap
+
+    def doubled(p, u, A, c, w):
+        feq = O.equilibrium(p, u, A, c, w)
+        d = u.shape[0]
+        uu = sum(u[a] * u[a] for a in range(d))
+        out = []
+        for i in range(len(w)):
+            cu = sum(c[i, a] * u[a] for a in range(d))
+            out.append(feq[i] + w[i] * (4.5 * cu * cu - 1.5 * uu))
+        return out
+
+    assert equilibrium_moment_gap(O.equilibrium, name) < 1e-15
+    assert equilibrium_moment_gap(doubled, name) > 1e-4
+    # the fixed-point pin alone does not see it
+    rng = np.random.default_rng(1)
+    c, w = O.lattice(name)
+    shape = (5, 4) if name == "D2Q9" else (4, 3, 3)
+    d = len(shape)
+    p = np.full(shape, 1.0 / 3.0 + 0.01)
+    u = np.stack([np.full(shape, v) for v in rng.uniform(-0.05, 0.05, d)])
+    f = doubled(p, u, 0.5, c, w)
+    g = [np.roll(fi, shift=tuple(int(v) for v in c[i]), axis=tuple(range(d))) for i, fi in enumerate(f)]
+    ustar = sum(c[i, 0] * g[i] for i in range(len(w)))
+    assert np.max(np.abs(ustar - u[0])) < 1e-15
