@@ -16,6 +16,7 @@ _MAP = {"linear": _abi.LKS_MAP_LINEAR, "cosine": _abi.LKS_MAP_COSINE}
 _PREC = {"fp64": _abi.LKS_FP64, "fp32": _abi.LKS_FP32}
 _CKPT = {"full": _abi.LKS_CKPT_FULL, "sqrt": _abi.LKS_CKPT_SQRT, "revolve": _abi.LKS_CKPT_REVOLVE}
 _MODE = {"joint": _abi.LKS_MODE_JOINT, "shape": _abi.LKS_MODE_SHAPE, "motion": _abi.LKS_MODE_MOTION}
+_OBJ = {"J1": _abi.LKS_OBJ_FLOW, "J2": _abi.LKS_OBJ_OAR}
 
 
 class LKSError(RuntimeError):
@@ -65,7 +66,10 @@ def params_from_workload(w: dict) -> _abi.lks_params:
     p.tile_rows_adj = w.get("tile_rows_adj", 0)
     p.tile_rows_rec = w.get("tile_rows_rec", 0)
     p.phi_var = w.get("phi_var", 0.0)
-    p.objective = _abi.LKS_OBJ_OAR if w.get("objective", "J1") == "J2" else _abi.LKS_OBJ_FLOW
+    objective = w.get("objective", "J1")
+    if objective not in _OBJ:
+        raise ValueError(f"objective must be one of {sorted(_OBJ)}, not {objective!r}")
+    p.objective = _OBJ[objective]
     p.w_D = w.get("w_D", 0.0)
     p.drag_span = w.get("drag_span", 1.0)
     return p

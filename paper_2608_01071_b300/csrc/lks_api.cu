@@ -15,15 +15,7 @@
 #include <vector>
 
 #include "../../include/lks.h"
-#include "lks_common.cuh"
-#include "lks_prep_kernels.cuh"
-#include "lks_step_kernels.cuh"
-#include "lks_step2d.cuh"
-#include "lks_step3d.cuh"
-#include "lks_step3s.cuh"
-#include "lks_step2r.cuh"
-#include "lks_step2v.cuh"
-#include "lks_oar.cuh"
+#include "lks_engine.cuh"
 #include <map>
 #include <tuple>
 
@@ -31,423 +23,9 @@ using namespace lks;
 
 namespace {
 
-struct LksError {
-    int code;
-    std::string msg;
-};
-
-#define LKS_CUDA(call)                                                                                   \
-    do {                                                                                                 \
-        cudaError_t e_ = (call);                                                                         \
-        if (e_ != cudaSuccess)                                                                           \
-            throw LksError{LKS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};              \
-    } while (0)
-
-#define LKS_LAUNCHED()                                                                                   \
-    do {                                                                                                 \
-        cudaError_t e_ = cudaGetLastError();                                                             \
-        if (e_ != cudaSuccess) throw LksError{LKS_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)}; \
-    } while (0)
-
-inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
-
-// Launch a step kernel with programmatic stream serialization (see pdl_wait_then_release).
-template <typename K, typename... Args>
-void launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = pdl ? 1 : 0;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
-    if (e != cudaSuccess) throw LksError{LKS_ECUDA, std::string("cudaLaunchKernelEx: ") + cudaGetErrorString(e)};
-}
-
-// ------------------------------------------------------------------------------------------------
-// Typed engine: launches of the templated kernels for one (precision, dimension, kernel width).
-// ------------------------------------------------------------------------------------------------
-struct Engine {
-    bool pdl = true;  // programmatic dependent launch of the step kernels
-    dim3 fthreads, athreads;  // threads per block of the forward / adjoint step kernels
-    dim3 ftile, atile;        // analysis nodes covered per block
-    dim3 fgrid, agrid;
-    int rows_f = 0, rows_a = 0;  // step-kernel variant codes (tile_rows) of the forward / adjoint kernels
-    virtual ~Engine() {}
-    // choose the forward and adjoint step-kernel variants; false when one is not available for this grid
-    virtual bool set_rows(int rf, int ra, const Geom& g) = 0;
-    // variant codes the autotuner tries (some may be unavailable for a given grid)
-    virtual std::vector<int> fwd_codes() const = 0;
-    virtual std::vector<int> adj_codes() const = 0;
-    virtual void fwd(const Geom& g, const void* in, void* out, const void* kref, const Pose* pose, double* jslot,
-                     unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) = 0;
-    // two-step forward launches (steps n and n+1 in one kernel); out2 == nullptr takes step n only
-    virtual bool fused2() const { return false; }
-    virtual void fwd2(const Geom& g, const void* in, void* out1, void* out2, const void* kref, const Pose* pose1,
-                      double* jslot1, double* jslot2, unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) {}
-    // fac: 1 / (1 + kappa) of the step on the footprint box (box_fac), or nullptr to evaluate the mapping
-    virtual void adj(const Geom& g, const void* lam_in, void* lam_out, const void* prev, const void* cur,
-                     const void* kref, const Pose* pose, void* boxbuf, const void* fac, int src, cudaStream_t s) = 0;
-    // two-step adjoint launches: steps n (pose, boxbuf1, src1; states prev1 = n-1, cur1 = n) and n-1 (pose - 1,
-    // boxbuf2, src2; states prev2 = n-2, prev1) in one kernel
-    virtual bool fused_adj2() const { return false; }
-    virtual void adj2(const Geom& g, const void* lam_in, void* lam_out, const void* prev1, const void* cur1,
-                      const void* prev2, const void* kref, const Pose* pose, void* boxbuf1, const void* fac1, int src1,
-                      void* boxbuf2, const void* fac2, int src2, cudaStream_t s) {}
-    // 1 / (1 + kappa) on the footprint box for steps n_first .. n_first + nsteps - 1 (stride Fbn per step)
-    virtual void box_fac(const Geom& g, const Pose* poses, const void* kref, int n_first, int nsteps, void* out,
-                         cudaStream_t s) = 0;
-    virtual void sens(const Geom& g, const Pose* poses, const void* kref, const void* boxbuf, long long bstride,
-                      int n_first, int nsteps, void* kbar, double* mslot, cudaStream_t s) = 0;
-    virtual void gather(const Geom& g, const Pose* poses, const void* kbar, int n_first, int nsteps,
-                        long long kstride, double* dkref, cudaStream_t s) = 0;
-    virtual void kappa_ref(const DesignGeom& dg, const double* gt, double* gb, double* k64, void* k, cudaStream_t s) = 0;
-    virtual void init_state(const Geom& g, void* st, cudaStream_t s) = 0;
-    virtual void import_state(const Geom& g, const double* p, const double* u, void* st, cudaStream_t s) = 0;
-    virtual void init_adjoint(const Geom& g, const void* fin, void* lam, int src, cudaStream_t s) = 0;
-    // objective J2 (translating body): per-block partials of sum_x kappa u of one step, and its adjoint source
-    virtual void oar_partial(const Geom& g, const Pose* pose, const void* kref, const void* st, double* slot,
-                             cudaStream_t s) = 0;
-    virtual void oar_source(const Geom& g, const OarGeom& o, const Pose* pose, const void* kref, void* lam,
-                            cudaStream_t s) = 0;
-    virtual void oar_sens(const Geom& g, const OarGeom& o, const Pose* poses, const void* kref, const void* boxbuf,
-                          long long bstride, int n_first, int nsteps, void* kbar, double* oms, cudaStream_t s) = 0;
-    virtual void export_state(const Geom& g, const void* st, double* p, double* u, cudaStream_t s) = 0;
-};
-
-template <typename T>
-FwdArgs<T> make_fwd_args(const Geom& g, const void* in, void* out, const void* kref, const Pose* pose, double* jslot,
-                         unsigned* flag, const int* jlo, const int* jn) {
-    FwdArgs<T> a;
-    for (int i = 0; i < 3; ++i) {
-        a.jb_lo[i] = jlo[i];
-        a.jb_n[i] = jn[i];
-        a.dir[i] = (T)g.dir[i];
-    }
-    a.in = (const T*)in;
-    a.out_p = (T*)out;
-    a.out_u = (T*)out + g.N;
-    a.kref = (const T*)kref;
-    a.pose = pose;
-    a.jslot = jslot;
-    a.jsq = jslot != nullptr && g.jsq_off != 0 ? jslot + g.jsq_off : nullptr;
-    a.flag = flag;
-    a.u_crit2 = (T)g.u_crit2;
-    return a;
-}
-
-template <typename T>
-AdjArgs<T> make_adj_args(const Geom& g, const void* lam_in, void* lam_out, const void* prev, const void* cur,
-                         const void* kref, const Pose* pose, void* boxbuf, const void* fac, int src) {
-    AdjArgs<T> a;
-    a.lam_in = (const T*)lam_in;
-    a.lam_out = (T*)lam_out;
-    a.u_prev = (const T*)prev + g.N;
-    a.u_cur = (const T*)cur + g.N;
-    a.kref = (const T*)kref;
-    a.pose = pose;
-    a.boxbuf = (T*)boxbuf;
-    a.fac = (const T*)fac;
-    a.src = src;
-    for (int i = 0; i < 3; ++i) {
-        a.phi_dir[i] = (T)(g.dir[i] * g.phi);
-        a.dir[i] = (T)g.dir[i];
-    }
-    a.src_c0 = g.phi_var != 0.0 ? g.obj + 3 : nullptr;
-    a.src_c1 = (T)(2.0 * g.phi_var);
-    return a;
-}
-
-// Shared pieces of both engines.
-template <typename T, int D, int HW>
-struct EngineCommon : Engine {
-    void box_fac(const Geom& g, const Pose* poses, const void* kref, int n_first, int nsteps, void* out,
-                 cudaStream_t s) override {
-        box_fac_kernel<T, D, HW><<<dim3(nblk(g.Fbn, 256), nsteps, 1), 256, 0, s>>>(g, poses, (const T*)kref, n_first,
-                                                                                 (T*)out);
-        LKS_LAUNCHED();
-    }
-    void sens(const Geom& g, const Pose* poses, const void* kref, const void* boxbuf, long long bstride, int n_first,
-              int nsteps, void* kbar, double* mslot, cudaStream_t s) override {
-        const dim3 grid(nblk(g.Fbn, 256), nsteps, 1);
-        adj_sens_kernel<T, D, HW><<<grid, 256, 0, s>>>(g, poses, (const T*)kref, (const T*)boxbuf, bstride, n_first,
-                                                       (T*)kbar, mslot);
-        LKS_LAUNCHED();
-    }
-    void gather(const Geom& g, const Pose* poses, const void* kbar, int n_first, int nsteps, long long kstride,
-                double* dkref, cudaStream_t s) override {
-        const long long nd = (long long)g.nde[0] * g.nde[1] * g.nde[2];
-        design_gather_kernel<T, D, HW><<<nblk(nd, 128), 128, 0, s>>>(g, poses, (const T*)kbar, n_first, nsteps, kstride, dkref);
-        LKS_LAUNCHED();
-    }
-    void kappa_ref(const DesignGeom& dg, const double* gt, double* gb, double* k64, void* k, cudaStream_t s) override {
-        const long long ne = (long long)dg.nde[0] * dg.nde[1] * dg.nde[2];
-        kappa_ref_kernel<T><<<nblk(ne, 256), 256, 0, s>>>(dg, gt, gb, k64, (T*)k);
-        LKS_LAUNCHED();
-    }
-    void init_state(const Geom& g, void* st, cudaStream_t s) override {
-        init_state_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, (T*)st);
-        LKS_LAUNCHED();
-    }
-    void import_state(const Geom& g, const double* p, const double* u, void* st, cudaStream_t s) override {
-        import_state_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, p, u, (T*)st);
-        LKS_LAUNCHED();
-    }
-    void init_adjoint(const Geom& g, const void* fin, void* lam, int src, cudaStream_t s) override {
-        init_adjoint_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, (const T*)fin + g.N, (T*)lam, src);
-        LKS_LAUNCHED();
-    }
-    void export_state(const Geom& g, const void* st, double* p, double* u, cudaStream_t s) override {
-        export_state_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, (const T*)st, p, u);
-        LKS_LAUNCHED();
-    }
-    void oar_partial(const Geom& g, const Pose* pose, const void* kref, const void* st, double* slot,
-                     cudaStream_t s) override {
-        oar_partial_kernel<T, D, HW><<<nblk(g.Fbn, 256), 256, 0, s>>>(g, pose, (const T*)kref, (const T*)st, slot);
-        LKS_LAUNCHED();
-    }
-    void oar_source(const Geom& g, const OarGeom& o, const Pose* pose, const void* kref, void* lam,
-                    cudaStream_t s) override {
-        oar_source_kernel<T, D, HW><<<nblk(g.Fbn, 256), 256, 0, s>>>(g, o, pose, (const T*)kref, (T*)lam);
-        LKS_LAUNCHED();
-    }
-    void oar_sens(const Geom& g, const OarGeom& o, const Pose* poses, const void* kref, const void* boxbuf,
-                  long long bstride, int n_first, int nsteps, void* kbar, double* oms, cudaStream_t s) override {
-        const dim3 grid(nblk(g.Fbn, 256), nsteps, 1);
-        oar_sens_kernel<T, D, HW><<<grid, 256, 0, s>>>(g, o, poses, (const T*)kref, (const T*)boxbuf, bstride, n_first,
-                                                       (T*)kbar, oms);
-        LKS_LAUNCHED();
-    }
-};
-
-// D3Q15 engine: rows = 1 selects the generic shared-memory tile kernels (32 x 4 x 4 nodes per block);
-// rows = 8 or 16 the z-marching kernels with that many planes per block (32 x 8 columns); forward rows = 32,
-// 64 the separable z-marching kernels with 16 or 32 planes per block (32 x 8 columns), forward rows = 96 the
-// separable forward with 16 planes of 32 x 16 columns.
-template <typename T, int HW>
-struct Engine3D : EngineCommon<T, 3, HW> {
-    static constexpr int TX = 32, TY = 4, TZ = 4;
-    using TL = Tile<3, TX, TY, TZ>;
-    static constexpr size_t smem_fwd = sizeof(T) * (4 * TL::S + 7 * TL::M);
-    static constexpr size_t smem_adj = sizeof(T) * (4 * TL::S + 10 * TL::M);
-
-    explicit Engine3D(const Geom& g) {
-        LKS_CUDA(cudaFuncSetAttribute(fwd_step_kernel<T, 3, HW, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem_fwd));
-        LKS_CUDA(cudaFuncSetAttribute(adj_step_kernel<T, 3, HW, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem_adj));
-        LKS_CUDA(cudaFuncSetAttribute(fwd3d_kernel<T, HW, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3d_fwd<T>()));
-        LKS_CUDA(cudaFuncSetAttribute(fwd3d_kernel<T, HW, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3d_fwd<T>()));
-        LKS_CUDA(cudaFuncSetAttribute(adj3d_kernel<T, HW, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3d_adj<T>()));
-        LKS_CUDA(cudaFuncSetAttribute(adj3d_kernel<T, HW, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3d_adj<T>()));
-        LKS_CUDA(cudaFuncSetAttribute(fwd3s_kernel<T, HW, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem3s_fwd<T, 8>()));
-        LKS_CUDA(cudaFuncSetAttribute(fwd3s_kernel<T, HW, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem3s_fwd<T, 8>()));
-        LKS_CUDA(cudaFuncSetAttribute(fwd3s_kernel<T, HW, 16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem3s_fwd<T, 16>()));
-        LKS_CUDA(cudaFuncSetAttribute(adj3s_kernel<T, HW, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem3s_adj<T, 8>()));
-        LKS_CUDA(cudaFuncSetAttribute(adj3s_kernel<T, HW, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem3s_adj<T, 8>()));
-        set_rows(8, 8, g);
-    }
-    std::vector<int> fwd_codes() const override { return {1, 8, 16, 32, 64, 96}; }
-    std::vector<int> adj_codes() const override { return {1, 8, 16, 32, 64}; }
-    static void geom(int r, const Geom& g, dim3& th, dim3& tile, dim3& grid) {
-        if (r == 1) {
-            th = tile = dim3(TX, TY, TZ);
-            grid = dim3(nblk(g.n[0], TX), nblk(g.n[1], TY), nblk(g.n[2], TZ));
-        } else if (r >= 32) {  // separable forward: (planes, rows) per block
-            const int zb = r == 64 ? 32 : 16, ty = r == 96 ? 16 : 8;
-            th = dim3(32, ty, 1);
-            tile = dim3(32, ty, zb);
-            grid = dim3(nblk(g.n[0], 32), nblk(g.n[1], ty), nblk(g.n[2], zb));
-        } else {
-            th = dim3(Reg3::TX, Reg3::TY, 1);
-            tile = dim3(Reg3::TX, Reg3::TY, r);
-            grid = dim3(nblk(g.n[0], Reg3::TX), nblk(g.n[1], Reg3::TY), nblk(g.n[2], r));
-        }
-    }
-    bool set_rows(int rf, int ra, const Geom& g) override {
-        auto okf = [](int r) { return r == 1 || r == 8 || r == 16 || r == 32 || r == 64 || r == 96; };
-        auto oka = [](int r) { return r == 1 || r == 8 || r == 16 || r == 32 || r == 64; };
-        if (!okf(rf) || !oka(ra)) return false;
-        this->rows_f = rf;
-        this->rows_a = ra;
-        geom(rf, g, this->fthreads, this->ftile, this->fgrid);
-        geom(ra, g, this->athreads, this->atile, this->agrid);
-        return true;
-    }
-    void fwd(const Geom& g, const void* in, void* out, const void* kref, const Pose* pose, double* jslot,
-             unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) override {
-        auto a = make_fwd_args<T>(g, in, out, kref, pose, jslot, flag, jlo, jn);
-        if (this->rows_f == 1)
-            launch_pdl(fwd_step_kernel<T, 3, HW, TX, TY, TZ>, this->fgrid, this->fthreads, smem_fwd, s, this->pdl, g, a);
-        else if (this->rows_f == 8)
-            launch_pdl(fwd3d_kernel<T, HW, 8>, this->fgrid, this->fthreads, smem3d_fwd<T>(), s, this->pdl, g, a);
-        else if (this->rows_f == 16)
-            launch_pdl(fwd3d_kernel<T, HW, 16>, this->fgrid, this->fthreads, smem3d_fwd<T>(), s, this->pdl, g, a);
-        else if (this->rows_f == 32)
-            launch_pdl(fwd3s_kernel<T, HW, 16, 8>, this->fgrid, this->fthreads, smem3s_fwd<T, 8>(), s, this->pdl, g, a);
-        else if (this->rows_f == 64)
-            launch_pdl(fwd3s_kernel<T, HW, 32, 8>, this->fgrid, this->fthreads, smem3s_fwd<T, 8>(), s, this->pdl, g, a);
-        else
-            launch_pdl(fwd3s_kernel<T, HW, 16, 16>, this->fgrid, this->fthreads, smem3s_fwd<T, 16>(), s, this->pdl, g, a);
-    }
-    void adj(const Geom& g, const void* lam_in, void* lam_out, const void* prev, const void* cur, const void* kref,
-             const Pose* pose, void* boxbuf, const void* fac, int src, cudaStream_t s) override {
-        auto a = make_adj_args<T>(g, lam_in, lam_out, prev, cur, kref, pose, boxbuf, fac, src);
-        if (this->rows_a == 1)
-            launch_pdl(adj_step_kernel<T, 3, HW, TX, TY, TZ>, this->agrid, this->athreads, smem_adj, s, this->pdl, g, a);
-        else if (this->rows_a == 8)
-            launch_pdl(adj3d_kernel<T, HW, 8>, this->agrid, this->athreads, smem3d_adj<T>(), s, this->pdl, g, a);
-        else if (this->rows_a == 16)
-            launch_pdl(adj3d_kernel<T, HW, 16>, this->agrid, this->athreads, smem3d_adj<T>(), s, this->pdl, g, a);
-        else if (this->rows_a == 32)
-            launch_pdl(adj3s_kernel<T, HW, 16, 8>, this->agrid, this->athreads, smem3s_adj<T, 8>(), s, this->pdl, g, a);
-        else
-            launch_pdl(adj3s_kernel<T, HW, 32, 8>, this->agrid, this->athreads, smem3s_adj<T, 8>(), s, this->pdl, g, a);
-    }
-};
-
-// D2Q9 engine with four kernel families: rows = 1 or 2 select the row-tile kernels (blocks of 32 x 8 threads,
-// tiles 28 wide and 8 or 16 rows high; best on small grids, where launches are latency bound), rows = 3 the
-// forward kernel that takes two steps per launch on 24 x 8 row tiles, rows = 4, 8, 16 the warp-column kernels
-// with that many rows per warp and WY = 4 warps per block, rows = 32, 64 the vectorised warp columns (two grid
-// columns per lane, 60 columns per warp).
-template <typename T, int HW>
-struct Engine2D : EngineCommon<T, 2, HW> {
-    static constexpr int WY = 4;
-    explicit Engine2D(const Geom& g) {
-        LKS_CUDA(cudaFuncSetAttribute(fwd2r2_kernel<T, HW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r2_fwd<T>()));
-        LKS_CUDA(cudaFuncSetAttribute(fwd2r2_kernel<T, HW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r2_fwd<T>()));
-        LKS_CUDA(cudaFuncSetAttribute(adj2r2_kernel<T, HW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r2_adj<T>()));
-        LKS_CUDA(cudaFuncSetAttribute(fwd2r_kernel<T, HW, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_fwd<T, 1>()));
-        LKS_CUDA(cudaFuncSetAttribute(fwd2r_kernel<T, HW, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_fwd<T, 2>()));
-        LKS_CUDA(cudaFuncSetAttribute(adj2r_kernel<T, HW, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_adj<T, 1>()));
-        LKS_CUDA(cudaFuncSetAttribute(adj2r_kernel<T, HW, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_adj<T, 2>()));
-        set_rows(1, 1, g);
-    }
-    static void geom(int r, const Geom& g, dim3& th, dim3& tile, dim3& grid) {
-        if (r >= 32) {  // vectorised warp columns, two columns per lane
-            th = dim3(32 * WY, 1, 1);
-            tile = dim3(kVecCols, r * WY, 1);
-            grid = dim3(nblk(g.n[0], kVecCols), nblk(g.n[1], r * WY), 1);
-        } else if (r == 3) {  // two-step fused row tiles
-            th = dim3(32, 8, 1);
-            tile = dim3(Fused2::TXO, Fused2::TY, 1);
-            grid = dim3(nblk(g.n[0], Fused2::TXO), nblk(g.n[1], Fused2::TY), 1);
-        } else if (r <= 2) {
-            th = dim3(32, 8, 1);
-            tile = dim3(28, 8 * r, 1);
-            grid = dim3(nblk(g.n[0], 28), nblk(g.n[1], 8 * r), 1);
-        } else {
-            th = dim3(32 * WY, 1, 1);
-            tile = dim3(kLanesOut, r * WY, 1);
-            grid = dim3(nblk(g.n[0], kLanesOut), nblk(g.n[1], r * WY), 1);
-        }
-    }
-    std::vector<int> fwd_codes() const override { return {1, 2, 3, 4, 8, 16, 32, 64}; }
-    std::vector<int> adj_codes() const override { return {1, 2, 3, 4, 8, 16, 32, 64}; }
-    bool set_rows(int rf, int ra, const Geom& g) override {
-        // rows kept in registers grow with R: FP32 allows up to 16, FP64 up to 8 without spills; 3 = fused forward;
-        // 32 and 64 = vectorised warp columns (even x extent only)
-        const bool even = (g.n[0] % 2) == 0;
-        auto ok = [even](int r) {
-            return r == 1 || r == 2 || r == 4 || r == 8 || (r == 16 && sizeof(T) == 4) || ((r == 32 || r == 64) && even);
-        };
-        if (!(ok(rf) || rf == 3) || !(ok(ra) || ra == 3)) return false;
-        this->rows_f = rf;
-        this->rows_a = ra;
-        geom(rf, g, this->fthreads, this->ftile, this->fgrid);
-        geom(ra, g, this->athreads, this->atile, this->agrid);
-        return true;
-    }
-    template <int R>
-    void fwd_r(const Geom& g, FwdArgs<T> a, cudaStream_t s) {
-        launch_pdl(fwd2d_kernel<T, HW, R, WY>, this->fgrid, this->fthreads, 0, s, this->pdl, g, a);
-    }
-    bool fused2() const override { return this->rows_f == 3; }
-    bool fused_adj2() const override { return this->rows_a == 3; }
-    void adj2(const Geom& g, const void* lam_in, void* lam_out, const void* prev1, const void* cur1, const void* prev2,
-              const void* kref, const Pose* pose, void* boxbuf1, const void* fac1, int src1, void* boxbuf2,
-              const void* fac2, int src2, cudaStream_t s) override;
-    void fwd2(const Geom& g, const void* in, void* out1, void* out2, const void* kref, const Pose* pose1,
-              double* jslot1, double* jslot2, unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) override {
-        auto a1 = make_fwd_args<T>(g, in, out1, kref, pose1, jslot1, flag, jlo, jn);
-        auto a2 = make_fwd_args<T>(g, out1, out2 ? out2 : out1, kref, pose1 + 1, jslot2, flag, jlo, jn);
-        fwd2r2(g, a1, a2, out2 ? 1 : 0, s);
-    }
-    // the squares of n.u are summed only when the objective has the variance term (a separate instantiation, so
-    // that the plain objective keeps the kernel's code unchanged)
-    void fwd2r2(const Geom& g, const FwdArgs<T>& a1, const FwdArgs<T>& a2, int two, cudaStream_t s) {
-        if (a1.jsq != nullptr)
-            launch_pdl(fwd2r2_kernel<T, HW, true>, this->fgrid, this->fthreads, smem2r2_fwd<T>(), s, this->pdl, g, a1,
-                       a2, two);
-        else
-            launch_pdl(fwd2r2_kernel<T, HW, false>, this->fgrid, this->fthreads, smem2r2_fwd<T>(), s, this->pdl, g, a1,
-                       a2, two);
-    }
-    template <int R>
-    void adj_r(const Geom& g, AdjArgs<T> a, cudaStream_t s) {
-        launch_pdl(adj2d_kernel<T, HW, R, WY>, this->agrid, this->athreads, 0, s, this->pdl, g, a);
-    }
-    void fwd(const Geom& g, const void* in, void* out, const void* kref, const Pose* pose, double* jslot,
-             unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) override {
-        auto a = make_fwd_args<T>(g, in, out, kref, pose, jslot, flag, jlo, jn);
-        switch (this->rows_f) {
-            case 3:
-                fwd2r2(g, a, a, 0, s);
-                break;
-            case 1: launch_pdl(fwd2r_kernel<T, HW, 1>, this->fgrid, this->fthreads, smem2r_fwd<T, 1>(), s, this->pdl, g, a); break;
-            case 2: launch_pdl(fwd2r_kernel<T, HW, 2>, this->fgrid, this->fthreads, smem2r_fwd<T, 2>(), s, this->pdl, g, a); break;
-            case 4: fwd_r<4>(g, a, s); break;
-            case 8: fwd_r<8>(g, a, s); break;
-            case 32: launch_pdl(fwd2v_kernel<T, HW, 32>, this->fgrid, this->fthreads, 0, s, this->pdl, g, a); break;
-            case 64: launch_pdl(fwd2v_kernel<T, HW, 64>, this->fgrid, this->fthreads, 0, s, this->pdl, g, a); break;
-            default: fwd_r<(sizeof(T) == 4 ? 16 : 8)>(g, a, s); break;
-        }
-    }
-    void adj(const Geom& g, const void* lam_in, void* lam_out, const void* prev, const void* cur, const void* kref,
-             const Pose* pose, void* boxbuf, const void* fac, int src, cudaStream_t s) override {
-        auto a = make_adj_args<T>(g, lam_in, lam_out, prev, cur, kref, pose, boxbuf, fac, src);
-        switch (this->rows_a) {
-            case 3:
-                launch_pdl(adj2r2_kernel<T, HW>, this->agrid, this->athreads, smem2r2_adj<T>(), s, this->pdl, g, a, a, 0);
-                break;
-            case 1: launch_pdl(adj2r_kernel<T, HW, 1>, this->agrid, this->athreads, smem2r_adj<T, 1>(), s, this->pdl, g, a); break;
-            case 2: launch_pdl(adj2r_kernel<T, HW, 2>, this->agrid, this->athreads, smem2r_adj<T, 2>(), s, this->pdl, g, a); break;
-            case 4: adj_r<4>(g, a, s); break;
-            case 8: adj_r<8>(g, a, s); break;
-            case 32: launch_pdl(adj2v_kernel<T, HW, 32>, this->agrid, this->athreads, 0, s, this->pdl, g, a); break;
-            case 64: launch_pdl(adj2v_kernel<T, HW, 64>, this->agrid, this->athreads, 0, s, this->pdl, g, a); break;
-            default: adj_r<(sizeof(T) == 4 ? 16 : 8)>(g, a, s); break;
-        }
-    }
-};
-
-template <typename T, int HW>
-void Engine2D<T, HW>::adj2(const Geom& g, const void* lam_in, void* lam_out, const void* prev1, const void* cur1,
-                           const void* prev2, const void* kref, const Pose* pose, void* boxbuf1, const void* fac1,
-                           int src1, void* boxbuf2, const void* fac2, int src2, cudaStream_t s) {
-    auto a1 = make_adj_args<T>(g, lam_in, lam_out, prev1, cur1, kref, pose, boxbuf1, fac1, src1);
-    auto a2 = make_adj_args<T>(g, lam_in, lam_out, prev2, prev1, kref, pose - 1, boxbuf2, fac2, src2);
-    launch_pdl(adj2r2_kernel<T, HW>, this->agrid, this->athreads, smem2r2_adj<T>(), s, this->pdl, g, a1, a2, 1);
-}
-
-template <typename T>
-Engine* make_engine_t(int D, int hw, const Geom& g) {
-    if (D == 2) return hw == 1 ? (Engine*)new Engine2D<T, 1>(g) : (Engine*)new Engine2D<T, 2>(g);
-    return hw == 1 ? (Engine*)new Engine3D<T, 1>(g) : (Engine*)new Engine3D<T, 2>(g);
-}
-
 Engine* make_engine(int precision, int D, int hw, const Geom& g) {
-    return precision == LKS_FP64 ? make_engine_t<double>(D, hw, g) : make_engine_t<float>(D, hw, g);
+    if (D == 2) return precision == LKS_FP64 ? make_engine2d_f64(hw, g) : make_engine2d_f32(hw, g);
+    return precision == LKS_FP64 ? make_engine3d_f64(hw, g) : make_engine3d_f32(hw, g);
 }
 
 // Binomial coefficient C(c + r, c), saturating.
@@ -487,8 +65,10 @@ struct lks_ctx {
     int max_njb = 0;      // most probe blocks over all tile choices (objective-slot stride)
     bool oar = false;     // the objective is J2 of Eq. objective2 (translating body)
     OarGeom ogeo{};
-    int nbox = 0;         // blocks of the footprint-box kernels (objective J2 slot stride)
+    int nbox = 0;         // blocks of the footprint-box kernels (objective J2 scratch stride)
     double *d_oslot = nullptr, *d_oms = nullptr, *d_oar_guG = nullptr, *d_oar_dK = nullptr;
+    double *d_oscr = nullptr, *d_omsscr = nullptr;  // per-block partials of one step (J2 forward / sensitivities)
+    unsigned* d_otick = nullptr;                     // last-block tickets: [0] forward, [1 + s] sensitivity step s
     long long nd = 0, nde = 0;
     std::string err;
     lks_stats stats;
@@ -993,12 +573,17 @@ void allocate(lks_ctx* c) {
     c->g.obj = c->d_J;
     if (c->oar) {
         c->nbox = (int)nblk(c->g.Fbn, 256);
-        c->d_oslot = (double*)dalloc(c, (size_t)(p.Nt + 1) * c->nbox * 2 * 8);
-        c->d_oms = (double*)dalloc(c, (size_t)(p.Nt + 1) * c->nbox * D * 8);
-        LKS_CUDA(cudaMemset(c->d_oms, 0, (size_t)(p.Nt + 1) * c->nbox * D * 8));
+        // per-step sums only: the block partials of a launch live in scratch until its last block sums them
+        c->d_oslot = (double*)dalloc(c, (size_t)(p.Nt + 1) * 2 * 8);
+        c->d_oms = (double*)dalloc(c, (size_t)(p.Nt + 1) * D * 8);
+        LKS_CUDA(cudaMemset(c->d_oms, 0, (size_t)(p.Nt + 1) * D * 8));
+        c->d_oscr = (double*)dalloc(c, (size_t)c->nbox * 2 * 8);
+        c->d_omsscr = (double*)dalloc(c, (size_t)c->Lmax * c->nbox * D * 8);
+        c->d_otick = (unsigned*)dalloc(c, (size_t)(c->Lmax + 1) * sizeof(unsigned));
+        LKS_CUDA(cudaMemset(c->d_otick, 0, (size_t)(c->Lmax + 1) * sizeof(unsigned)));
         c->d_oar_guG = (double*)dalloc(c, (size_t)(p.Nt + 1) * D * 8);
         c->d_oar_dK = (double*)dalloc(c, 8);
-        LKS_CUDA(cudaMemset(c->d_oslot, 0, (size_t)(p.Nt + 1) * c->nbox * 2 * 8));
+        LKS_CUDA(cudaMemset(c->d_oslot, 0, (size_t)(p.Nt + 1) * 2 * 8));
         LKS_CUDA(cudaMemset(c->d_oar_guG, 0, (size_t)(p.Nt + 1) * D * 8));
     }
     c->d_flag = (unsigned*)dalloc(c, 16);
@@ -1209,7 +794,7 @@ void fwd_pair(lks_ctx* c, int n, const void* in, void* out1, void* out2, bool ob
 
 // Objective J2: the footprint partials of state n (read before its buffer is reused, in stream order).
 void oar_partial(lks_ctx* c, int n, const void* st, cudaStream_t s) {
-    c->eng->oar_partial(c->g, c->d_pose + n, c->d_kref, st, c->d_oslot + 2LL * n * c->nbox, s);
+    c->eng->oar_partial(c->g, c->d_pose + n, c->d_kref, st, c->d_oscr, c->d_otick, c->d_oslot + 2LL * n, s);
     c->launches++;
 }
 
@@ -1318,7 +903,7 @@ void forward_body(lks_ctx* c, cudaStream_t s) {
     LKS_LAUNCHED();
     c->launches++;
     if (c->oar) {
-        oar_reduce_kernel<<<1, 256, 0, s>>>(c->ogeo, c->d_oslot, c->nbox, Nt, c->d_pose, c->d_kref64, (long long)c->nde,
+        oar_reduce_kernel<<<1, 256, 0, s>>>(c->ogeo, c->d_oslot, Nt, c->d_pose, c->d_kref64, (long long)c->nde,
                                             c->D, c->d_J, c->d_oar_guG, c->d_oar_dK);
         LKS_LAUNCHED();
         c->launches++;
@@ -1415,7 +1000,7 @@ void sens_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
     c->launches++;
     if (c->oar) {
         c->eng->oar_sens(c->g, c->ogeo, c->d_pose, c->d_kref, bb, c->box_step, a + 1, L, shape ? c->d_kbar : nullptr,
-                         c->d_oms, s);
+                         c->d_omsscr, c->d_otick + 1, c->d_oms, s);
         c->launches++;
     }
     if (shape) {
@@ -1544,7 +1129,7 @@ void adjoint_body(lks_ctx* c, cudaStream_t s) {
     }
     if (c->oar) {  // J2's position terms and its explicit dependences on u^G and kappa^ref
         const long long nmax = std::max<long long>((long long)c->nde, (long long)Nt + 1);
-        oar_apply_kernel<<<nblk(nmax, 256), 256, 0, s>>>(Nt, D, c->nbox, c->d_oms, c->d_oar_guG, c->d_gs, c->d_guG,
+        oar_apply_kernel<<<nblk(nmax, 256), 256, 0, s>>>(Nt, D, c->d_oms, c->d_oar_guG, c->d_gs, c->d_guG,
                                                          c->d_oar_dK, c->d_dkref, (long long)c->nde);
         LKS_LAUNCHED();
         c->launches++;
@@ -2100,6 +1685,7 @@ extern "C" int lks_density_filter_noalloc(const int32_t nd[3], double R, const d
         g_noalloc_err = "null pointer";
         return LKS_EINVAL;
     }
+    // the product is checked after every factor: it stays below 2^20 * 2^31 before the check, so it cannot overflow
     long long n = 1;
     for (int a = 0; a < 3; ++a) {
         if (nd[a] < 1) {
@@ -2107,11 +1693,12 @@ extern "C" int lks_density_filter_noalloc(const int32_t nd[3], double R, const d
             return LKS_EINVAL;
         }
         n *= nd[a];
-    }
-    if (n > LKS_NOALLOC_FILTER_MAX) {
-        g_noalloc_err = "design grid of " + std::to_string(n) + " nodes exceeds LKS_NOALLOC_FILTER_MAX (" +
-                        std::to_string((long long)LKS_NOALLOC_FILTER_MAX) + ")";
-        return LKS_EINVAL;
+        if (n > LKS_NOALLOC_FILTER_MAX) {
+            g_noalloc_err = "design grid of " + std::to_string(nd[0]) + " x " + std::to_string(nd[1]) + " x " +
+                            std::to_string(nd[2]) + " nodes exceeds LKS_NOALLOC_FILTER_MAX (" +
+                            std::to_string((long long)LKS_NOALLOC_FILTER_MAX) + ")";
+            return LKS_EINVAL;
+        }
     }
     if (!(R >= 0.0) || R > 32.0) {
         g_noalloc_err = "filter radius out of range [0, 32]";

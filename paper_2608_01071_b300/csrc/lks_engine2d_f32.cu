@@ -1,0 +1,10 @@
+// Engine2D<float> instantiations (one translation unit per lattice and precision, compiled in parallel).
+#include "lks_engine2d.cuh"
+
+namespace lks {
+
+Engine* make_engine2d_f32(int hw, const Geom& g) {
+    return hw == 1 ? (Engine*)new Engine2D<float, 1>(g) : (Engine*)new Engine2D<float, 2>(g);
+}
+
+}  // namespace lks

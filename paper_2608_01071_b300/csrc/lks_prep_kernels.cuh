@@ -23,7 +23,7 @@ __device__ __forceinline__ double cone_weight(int dx, int dy, int dz, double R) 
 }
 
 // Row sums sum_j w_s(i, j) over the design grid (truncated at the edges); static per context.
-__global__ void filter_norm_kernel(DesignGeom dg, double* __restrict__ norm) {
+static __global__ void filter_norm_kernel(DesignGeom dg, double* __restrict__ norm) {
     const long long n = (long long)dg.nd[0] * dg.nd[1] * dg.nd[2];
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -43,7 +43,7 @@ __global__ void filter_norm_kernel(DesignGeom dg, double* __restrict__ norm) {
 
 // Eq. filtering (transpose = false): out_i = sum_j w_ij in_j / norm_i.
 // Transpose (transpose = true):      out_j = sum_i w_ij in_i / norm_i.
-__global__ void density_filter_kernel(DesignGeom dg, const double* __restrict__ in, const double* __restrict__ norm,
+static __global__ void density_filter_kernel(DesignGeom dg, const double* __restrict__ in, const double* __restrict__ norm,
                                       double* __restrict__ out, int transpose) {
     const long long n = (long long)dg.nd[0] * dg.nd[1] * dg.nd[2];
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -80,7 +80,7 @@ __device__ __forceinline__ double proj_d(double x, double beta, double eta) {
     return beta / (c * c) / (tanh(beta * eta) + tanh(beta * (1.0 - eta)));
 }
 
-__global__ void projection_kernel(long long n, double beta, double eta, const double* __restrict__ in,
+static __global__ void projection_kernel(long long n, double beta, double eta, const double* __restrict__ in,
                                   double* __restrict__ out, double* __restrict__ dout) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -112,7 +112,7 @@ __global__ void kappa_ref_kernel(DesignGeom dg, const double* __restrict__ gt, d
 }
 
 // Chain rule: dJ/dkappa^ref (extended grid) -> dJ/dgamma~ on the inner grid (kappa^ref' times projection').
-__global__ void design_chain_kernel(DesignGeom dg, const double* __restrict__ dkref, const double* __restrict__ gt,
+static __global__ void design_chain_kernel(DesignGeom dg, const double* __restrict__ dkref, const double* __restrict__ gt,
                                     const double* __restrict__ gb, double* __restrict__ out) {
     const long long n = (long long)dg.nd[0] * dg.nd[1] * dg.nd[2];
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -143,7 +143,7 @@ __device__ __forceinline__ double tri_weight(int k, int m, const MotionGeom& mg)
 }
 
 // Row sums sum_m w_km of the temporal filter (static per context).
-__global__ void motion_norm_kernel(MotionGeom mg, double* __restrict__ norm) {
+static __global__ void motion_norm_kernel(MotionGeom mg, double* __restrict__ norm) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= mg.K) return;
     double ws = 0.0;
@@ -152,7 +152,7 @@ __global__ void motion_norm_kernel(MotionGeom mg, double* __restrict__ norm) {
 }
 
 // transpose = 0: out_k = sum_m w_km in_m / norm_k.   transpose = 1: out_m = sum_k w_km in_k / norm_k.
-__global__ void motion_filter_kernel(MotionGeom mg, const double* __restrict__ in, const double* __restrict__ norm,
+static __global__ void motion_filter_kernel(MotionGeom mg, const double* __restrict__ in, const double* __restrict__ norm,
                                      double* __restrict__ out, int transpose) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= mg.K * mg.d) return;
@@ -173,7 +173,7 @@ __device__ __forceinline__ void interp_coef(int n, const MotionGeom& mg, int& k,
     th = (double)(num - (long long)k * mg.Nt) / mg.Nt;
 }
 
-__global__ void interp_kernel(MotionGeom mg, const double* __restrict__ f, double* __restrict__ s, double* __restrict__ uG) {
+static __global__ void interp_kernel(MotionGeom mg, const double* __restrict__ f, double* __restrict__ s, double* __restrict__ uG) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (mg.Nt + 1) * mg.d) return;
     const int n = t / mg.d, a = t % mg.d;
@@ -194,7 +194,7 @@ __global__ void interp_kernel(MotionGeom mg, const double* __restrict__ f, doubl
 }
 
 // Transpose of interp_kernel: (s-bar, u^G-bar) -> filtered-knot bar.  u^G-bar_0 is ignored (u^G_0 drives no step).
-__global__ void interp_T_kernel(MotionGeom mg, const double* __restrict__ gs, const double* __restrict__ guG,
+static __global__ void interp_T_kernel(MotionGeom mg, const double* __restrict__ gs, const double* __restrict__ guG,
                                 double* __restrict__ out) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= mg.K * mg.d) return;
@@ -222,7 +222,7 @@ __global__ void interp_T_kernel(MotionGeom mg, const double* __restrict__ gs, co
 // Per-step pose: offset o = o0 + s_n, box start and tap weights of the shifted design grid (Eq. rigid_body_position,
 // theta = 0; transfer kernel w of Sec. 2.3).  Tap k of a node reads design index j = b - 2 hw + 1 + k, with
 // r = t - j = hw - k - f for f = o - floor(o).
-__global__ void pose_kernel(Geom g, int D, double o0x, double o0y, double o0z, int cosine, int Nt,
+static __global__ void pose_kernel(Geom g, int D, double o0x, double o0y, double o0z, int cosine, int Nt,
                             const double* __restrict__ s, const double* __restrict__ uG, Pose* __restrict__ poses) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n > Nt) return;
@@ -328,7 +328,7 @@ __global__ void export_state_kernel(Geom g, const T* __restrict__ st, double* __
 // One normalised projected-gradient step of the optimiser driver: x_i <- min(hi, max(lo, x_i + step g_i / max|g|))
 // (x unchanged where g = 0 everywhere).  A single block: the max-reduction, then the update, so that no scratch
 // memory is needed.  Launch with 1024 threads.
-__global__ void __launch_bounds__(1024) gradient_step_kernel(long long n, double step, const double* __restrict__ g,
+static __global__ void __launch_bounds__(1024) gradient_step_kernel(long long n, double step, const double* __restrict__ g,
                                                              double* __restrict__ x, double lo, double hi) {
     __shared__ double red[32];
     double m = 0.0;

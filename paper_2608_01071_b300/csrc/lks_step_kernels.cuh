@@ -745,7 +745,7 @@ __global__ void motion_reduce_kernel(const double* __restrict__ mslot, int nsb, 
 // partials of n.u and (n.u)^2 of step n (block order); E = phi sum_n j_n, S2 = phi sum_n q_n, V = S2 - E^2 and
 // J1 = E - phi_var V.  Writes obj = {J1, E, V, 1 + 2 phi_var E} (the last is the adjoint source's constant).
 // jsq_off = 0 (phi_var = 0): no squares were summed, J1 = E and V is NaN.  Deterministic.
-__global__ void objective_reduce_kernel(const double* __restrict__ jslot, long long jsq_off, int njb, int Nt,
+static __global__ void objective_reduce_kernel(const double* __restrict__ jslot, long long jsq_off, int njb, int Nt,
                                         double phi, double phi_var, double* __restrict__ jstep,
                                         double* __restrict__ obj) {
     __shared__ double red[2][32];

@@ -75,3 +75,18 @@ def test_design_too_large_for_period():
     p.nd[0] = 94
     h = C.c_void_p()
     assert lib.lks_create(C.byref(p), C.byref(h)) == _abi.LKS_EINVAL
+
+
+def test_unknown_objective_is_rejected():
+    from paper_2608_01071_b300.binding import params_from_workload
+    with pytest.raises(ValueError):
+        params_from_workload(dict(workload("d2q9_96x48_fp64"), objective="J3"))
+
+
+def test_noalloc_rejects_oversize_before_any_device_call():
+    # the size check comes first, so it runs without a GPU; the pointers are never used on rejection
+    lib = _abi.load()
+    for shape in ((2048, 1024, 1), (1 << 21, 1 << 21, 1 << 22), (1 << 30, 1 << 30, 1 << 30), (0, 4, 4)):
+        nd = (C.c_int32 * 3)(*shape)
+        rc = lib.lks_density_filter_noalloc(nd, 2.0, C.c_void_p(16), C.c_void_p(16), None)
+        assert rc == _abi.LKS_EINVAL, shape

@@ -48,7 +48,9 @@ def test_noalloc_rejects_oversize():
 
     lib = _abi.load()
     x = torch.zeros(8, device="cuda", dtype=torch.float64)
-    nd = (C.c_int32 * 3)(2048, 1024, 1)
-    rc = lib.lks_density_filter_noalloc(nd, 2.0, C.c_void_p(x.data_ptr()), C.c_void_p(x.data_ptr()), None)
-    assert rc == _abi.LKS_EINVAL
-    assert b"exceeds" in lib.lks_noalloc_last_error()
+    # one node over the limit, and extents whose product overflows 64 bits if formed before the check
+    for shape in ((2048, 1024, 1), (1 << 21, 1 << 21, 1 << 22), (1 << 30, 1 << 30, 1 << 30)):
+        nd = (C.c_int32 * 3)(*shape)
+        rc = lib.lks_density_filter_noalloc(nd, 2.0, C.c_void_p(x.data_ptr()), C.c_void_p(x.data_ptr()), None)
+        assert rc == _abi.LKS_EINVAL, shape
+        assert b"exceeds" in lib.lks_noalloc_last_error()
