@@ -26,7 +26,10 @@ sys.path.insert(0, ROOT)
 
 from paper_2608_01071_b300.workloads import draw_gamma, draw_knots, workload  # noqa: E402
 
-DEFAULT_WORKLOAD = "d2q9_512x256_fp32"
+# the largest single-GPU configuration: D3Q15 on 256x128x128 (4.19 M nodes, 67 MB per FP32 state, HBM-bound),
+# 8000 steps, binomial checkpoints under a 40 GB budget
+DEFAULT_WORKLOAD = "d3q15_256x128x128_fp32"
+L2_BYTES = 126 * 2**20
 
 
 def parse():
@@ -37,6 +40,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-check", action="store_true", help="skip the plain FP64 GPU run (error of the FP32 path "
+                    "at the full horizon, and the FP64 path's own throughput)")
     ap.add_argument("--nt", type=int, default=0, help="override the horizon (short runs for profiler captures)")
     ap.add_argument("--optimize", type=int, default=0, help="also run this many projected-gradient optimisation "
                     "iterations (gamma step 0.05, position step 0.5 cell, normalised) and report J and s/iteration")
@@ -179,19 +184,31 @@ def node_count(w):
     return int(np.prod(w["shape"]))
 
 
+def sample_steps_for(w):
+    """Steps of the oracle's bounded sample: about 8 M node-steps (10-30 s of numpy FP64 on one core), 1 to 60."""
+    return int(max(1, min(60, 8e6 // node_count(w))))
+
+
 def sample_workload(w, sample_steps):
-    """The workload's grid over its first `sample_steps` steps; the motion amplitude scales with the horizon so that
-    body speeds stay those of the workload."""
-    return dict(w, Nt=sample_steps, K=min(w["K"], 6), R_t=max(1.0, sample_steps / 4),
-                amp=w["amp"] * sample_steps / w["Nt"])
+    """The workload's grid and seeded inputs over its first `sample_steps` steps.  The motion amplitude scales with the
+    horizon so that body speeds stay those of the workload, and the probe box straddles the body's downstream edge
+    (same cross-section as the workload's probe) so that J and its gradients are not zero after a few steps."""
+    d = len(w["shape"])
+    nde0 = w["design"][0] + 2 * w["margin"]
+    edge = int((w["shape"][0] - 1) / 2.0 + (nde0 - 1) / 2.0)
+    lo = (edge - 8,) + tuple(w["probe_lo"][1:d])
+    hi = (edge + 8,) + tuple(w["probe_hi"][1:d])
+    return dict(w, Nt=sample_steps, K=min(w["K"], max(2, min(6, sample_steps + 1))), R_t=max(1.0, sample_steps / 4),
+                amp=w["amp"] * sample_steps / w["Nt"], probe_lo=lo, probe_hi=hi)
 
 
-def cpu_baseline(w, sample_steps=60, with_result=False):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload: same grid, first `sample_steps` steps.
+def cpu_baseline(w, sample_steps=None, with_result=False):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload (see sample_workload).
     With `with_result`, also its (J, dJ/dgamma, dJ/dknots) for the gradient-error check."""
     import oracle as O  # test infrastructure: only this leg and --impl reference use it
     from tests.helpers import oracle_problem
 
+    sample_steps = sample_steps or sample_steps_for(w)
     ws = sample_workload(w, sample_steps)
     P = oracle_problem(ws)
     gamma, knots = draw_gamma(ws), draw_knots(ws)
@@ -200,17 +217,17 @@ def cpu_baseline(w, sample_steps=60, with_result=False):
     dt = time.perf_counter() - t0
     val = node_count(ws) * sample_steps / dt / 1e9
     cb = {"value": val, "unit": "G node-steps/s (fwd+adj)", "cores": 1, "kind": "oracle",
-          "sample": f"{w['name']} grid, first {sample_steps} of {w['Nt']} steps, forward + exact adjoint, numpy FP64, "
-                    f"{dt:.1f} s"}
+          "sample": f"{w['name']} grid and inputs, first {sample_steps} of {w['Nt']} steps, probe box at the body's "
+                    f"downstream edge, forward + exact adjoint + chain rules, numpy FP64, {dt:.1f} s"}
     return (cb, res) if with_result else cb
 
 
-def gradient_error(w, oracle_result, sample_steps=60):
-    """The CUDA path's J and gradients on the oracle's sample against the oracle (gradients: relative L2; J: both
-    values and the absolute error, since over a short sample the flow may not yet reach the probe and J can be
-    near zero), beside the tolerance the gradients are held to."""
+def gradient_error(w, oracle_result, sample_steps=None):
+    """The CUDA path's J and gradients on the oracle's sample against the oracle (relative errors), beside the
+    tolerance the gradients are held to."""
     from paper_2608_01071_b300 import Solver
 
+    sample_steps = sample_steps or sample_steps_for(w)
     ws = sample_workload(w, sample_steps)
     s = Solver.from_workload(ws)
     J = s.forward(draw_gamma(ws), draw_knots(ws))
@@ -218,10 +235,63 @@ def gradient_error(w, oracle_result, sample_steps=60):
     s.close()
     Jo, dgo, dko = oracle_result
     rl2 = lambda a, b: float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
-    return {"sample": f"first {sample_steps} steps of the workload (the cpu_baseline sample)",
-            "J": {"oracle": Jo, "cuda": J, "abs_err": abs(J - Jo)},
+    return {"sample": f"the cpu_baseline sample ({sample_steps} steps)",
+            "J": {"oracle": Jo, "cuda": J, "rel_err": abs(J - Jo) / max(abs(Jo), 1e-300)},
             "dgamma_rel_l2": rl2(dg, dgo), "dknots_rel_l2": rl2(dk, dko),
             "tolerance": {"gradients_rel_l2": 1e-3 if w["precision"] == "fp32" else 1e-10}}
+
+
+def fp64_comparison(w, gamma, knots, res32):
+    """The plain FP64 GPU path on the same inputs over the full horizon: its throughput (one forward + adjoint, CUDA
+    events on its stream) and the FP32 path's errors against it (J; final velocity, max relative; gradients,
+    relative L2)."""
+    import torch
+
+    from paper_2608_01071_b300 import Solver
+
+    w64 = dict(w, precision="fp64")
+    s = Solver.from_workload(w64)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    J = s.forward(gamma, knots)
+    dg, dk = s.adjoint()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    _, u = s.state()
+    st = s.stats()
+    s.close()
+    J32, u32, dg32, dk32 = res32
+    rl2 = lambda a, b: float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+    return {"fp64_value": node_count(w) * w["Nt"] / (ms * 1e-3) / 1e9, "unit": "G node-steps/s (fwd+adj, host-pointer "
+            "calls, copies included)", "fp64_tile_rows": [st["tile_rows_fwd"], st["tile_rows_rec"], st["tile_rows_adj"]],
+            "horizon": w["Nt"], "J": {"fp32": J32, "fp64": J, "rel_err": abs(J32 - J) / max(abs(J), 1e-300)},
+            "u_final_rel_max": float(np.max(np.abs(u32 - u)) / max(np.max(np.abs(u)), 1e-300)),
+            "dgamma_rel_l2": rl2(dg32, dg), "dknots_rel_l2": rl2(dk32, dk),
+            "tolerance": {"u_rel_max": 1e-4, "gradients_rel_l2": 1e-3}}
+
+
+def l2_copy_gbs(dev):
+    """Copy bandwidth of a 2 x 16 MB working set that stays in L2 (read + write bytes, torch copy, best of 5 runs of
+    200 copies, CUDA events): the roof of the step kernels on grids whose states fit in L2."""
+    import torch
+
+    a = torch.ones(4 * 2**20, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    best = 0.0
+    for _ in range(5):
+        for _ in range(20):
+            b.copy_(a)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(200):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2 * a.numel() * 4 * 200 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    return best
 
 
 def run_reference(args):
@@ -229,7 +299,7 @@ def run_reference(args):
     if rank != 0:
         return
     w = dict(workload(args.workload), phi_var=args.phi_var)
-    sample_steps = 20
+    sample_steps = sample_steps_for(w)
     times = []
     for i in range(args.warmup + args.steps):
         cb = cpu_baseline(w, sample_steps)
@@ -335,7 +405,15 @@ def run_ours(args):
         Fbn *= w["design"][a] + 2 * w["margin"] + 2 * hw - 1
     adj_bytes = N * (2 * (D + 1) + D) * s + Fbn * (D + 1) * s
     fwd_bytes = N * 2 * (D + 1) * s
-    peak, peak_kind = peaks()
+    # the roof follows the working set: a step reads one state and writes another; when both fit in L2 the step
+    # kernels never reach HBM and their roof is the measured L2 copy bandwidth
+    state_mb = N * (D + 1) * s / 2**20
+    l2_resident = 2 * N * (D + 1) * s <= L2_BYTES
+    if l2_resident:
+        bound, peak, peak_kind = "l2", l2_copy_gbs(dev), "measured L2 copy bandwidth (2 x 16 MB, torch copy)"
+    else:
+        bound = "hbm"
+        peak, peak_kind = peaks()
     # spans (ms) and launches-worth of steps per kind: the forward sweep, the recomputation, the adjoint steps
     t_f, n_f = sum(a for a, _ in st_fwd), sum(n for _, n in st_fwd)
     t_r, n_r = sum(a for a, _ in st_rec), sum(n for _, n in st_rec)
@@ -345,7 +423,7 @@ def run_ours(args):
         name, src, per_launch = kernel_variant(w["lattice"], rows, kind)
         step_ms = t_ms / max(1, n_steps)
         gbs = step_bytes / (step_ms * 1e-3) / 1e9 if step_ms > 0 else 0.0
-        return {"bound": "hbm", "kernel": name, "achieved": gbs, "peak": peak, "peak_kind": peak_kind,
+        return {"bound": bound, "kernel": name, "achieved": gbs, "peak": peak, "peak_kind": peak_kind,
                 "unit": "GB/s", "frac": gbs / peak, "traffic": captured_traffic(w["name"], name, src),
                 "bytes_per_launch": step_bytes * per_launch, "us_per_launch": step_ms * per_launch * 1e3,
                 "steps_per_launch": per_launch, "_t": t_ms}
@@ -378,19 +456,18 @@ def run_ours(args):
                 path={"achieved": path_gbs, "frac": path_gbs / peak, "unit": "GB/s",
                       "bytes_per_step": path_bytes / args.steps,
                       "note": "algorithmic bytes of all step kernels (forward, recompute, adjoint) / device time"})
-    state_mb = N * (D + 1) * s / 2**20
-    # a step reads one state and writes another
     l2_note = (f"512 MB buffer written between timed steps; a step touches two {state_mb:.1f} MB states, "
-               + ("more than the 126 MB L2" if 2 * state_mb > 126 else "which stay L2-resident"))
+               + ("more than the 126 MB L2" if not l2_resident else "which stay L2-resident"))
 
     # end to end through the host-pointer C ABI (H2D of gamma and knots, D2H of J and both gradients)
     e2e_times = []
     for i in range(max(2, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        solver.forward(gamma, knots)
-        solver.adjoint()
+        J32 = solver.forward(gamma, knots)
+        dg32, dk32 = solver.adjoint()
         e2e_times.append(time.perf_counter() - t0)
+    _, u32 = solver.state()  # final state of the last forward (the reverse sweep leaves it in place)
     e2e = world * N * w["Nt"] / statistics.mean(e2e_times) / 1e9
     nd = int(np.prod(w["design"]))
     h2d = nd * 8 + w["K"] * D * 8
@@ -427,6 +504,8 @@ def run_ours(args):
             dt = time.perf_counter() - t0
             line["optimize"] = {"iters": args.optimize, "s_per_iter": dt / args.optimize, "J": hist,
                                 "gamma_step": 0.05, "pos_step_cells": 0.5, "pos_bound_cells": w["amp"]}
+        if not args.no_fp64_check and w["precision"] == "fp32":
+            line["fp32_vs_fp64_gpu"] = fp64_comparison(w, gamma, knots, (J32, u32, dg32, dk32))
         if not args.no_cpu_baseline:
             line["cpu_baseline"], ores = cpu_baseline(w, with_result=True)
             line["grad_error_vs_oracle"] = gradient_error(w, (ores[0], ores[1], ores[2]))
