@@ -131,10 +131,13 @@ def kernel_variant(lattice, rows, kind):
 
     kind is "fwd" or "adj".  D2Q9: 1/2 row tiles, 3 two steps per launch on row tiles, 4/8/16 warp columns,
     32/64 vectorised warp columns.  D3Q15: 1 the generic shared-memory kernel, 8/16 z-marching, 32/64/96
-    separable z-marching (planes x rows per block 16 x 8, 32 x 8, 16 x 16)."""
+    separable z-marching (planes x rows per block 16 x 8, 32 x 8, 16 x 16), 128/160 plane-pair separable (16 or 32
+    planes per block)."""
     if lattice == "D3Q15":
         if rows == 1:
             return f"{kind}_step_kernel", "lks_step_kernels.cuh", 1
+        if rows >= 128:
+            return f"{kind}3p_kernel<ZB={16 if rows == 128 else 32}>", "lks_step3p.cuh", 1
         if rows >= 32:
             zb, ty = {32: (16, 8), 64: (32, 8), 96: (16, 16)}[rows]
             return f"{kind}3s_kernel<ZB={zb},TY={ty}>", "lks_step3s.cuh", 1
@@ -185,8 +188,8 @@ def node_count(w):
 
 
 def sample_steps_for(w):
-    """Steps of the oracle's bounded sample: about 8 M node-steps (10-30 s of numpy FP64 on one core), 1 to 60."""
-    return int(max(1, min(60, 8e6 // node_count(w))))
+    """Steps of the oracle's bounded sample: about 12 M node-steps (10-30 s of numpy FP64 on one core), 1 to 60."""
+    return int(max(1, min(60, 12e6 // node_count(w))))
 
 
 def sample_workload(w, sample_steps):
@@ -198,7 +201,7 @@ def sample_workload(w, sample_steps):
     edge = int((w["shape"][0] - 1) / 2.0 + (nde0 - 1) / 2.0)
     lo = (edge - 8,) + tuple(w["probe_lo"][1:d])
     hi = (edge + 8,) + tuple(w["probe_hi"][1:d])
-    return dict(w, Nt=sample_steps, K=min(w["K"], max(2, min(6, sample_steps + 1))), R_t=max(1.0, sample_steps / 4),
+    return dict(w, Nt=sample_steps, K=min(w["K"], 6), R_t=max(1.0, sample_steps / 4),
                 amp=w["amp"] * sample_steps / w["Nt"], probe_lo=lo, probe_hi=hi)
 
 

@@ -246,7 +246,8 @@ int lks_motion_filter_T(lks_ctx* ctx, const double* in, double* out);
 int lks_interp_positions(lks_ctx* ctx, const double* filtered, double* s, double* uG);
 int lks_interp_positions_T(lks_ctx* ctx, const double* gs, const double* guG, double* out);
 
-/* Final state (p_Nt, u_Nt) of the last forward, as FP64: p[N], u[d*N] (component-major). Synchronous. */
+/* Final state (p_Nt, u_Nt) of the last forward, as FP64: p[N], u[d*N] (component-major); still available after
+ * that forward's adjoint.  Synchronous.  LKS_ESTATE before the first forward. */
 int lks_get_state(lks_ctx* ctx, double* p, double* u);
 
 /* Initial state (p_0, u_0) of every following lks_forward, host FP64 in the layout of lks_get_state (p is the

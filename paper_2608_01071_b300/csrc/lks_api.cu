@@ -123,6 +123,7 @@ struct lks_ctx {
     std::vector<int> slot_used;
 
     bool have_forward = false;
+    bool have_final = false;  // the final-state buffer holds the last forward's state (the reverse sweeps never write it)
     long long launches = 0;
     long long launches_fwd = 0, launches_adj = 0;
 
@@ -211,7 +212,9 @@ void validate(const lks_params* p) {
     }
     // a step-kernel variant code: the forward accepts 3 (two steps per launch), the adjoint does not
     auto variant_ok = [&](int r, bool fwd) {
-        if (D == 3) return r == 1 || r == 8 || r == 16 || r == 32 || r == 64 || (fwd && r == 96);
+        if (D == 3)
+            return r == 1 || r == 8 || r == 16 || r == 32 || r == 64 || (fwd && r == 96) ||
+                   ((r == 128 || r == 160) && p->precision == LKS_FP32);
         return r == 1 || r == 2 || r == 3 || r == 4 || r == 8 || (r == 16 && p->precision == LKS_FP32) ||
                ((r == 32 || r == 64) && p->n[0] % 2 == 0);
     };
@@ -219,7 +222,8 @@ void validate(const lks_params* p) {
         bad(D == 2 ? "D2Q9 tile_rows must be 0 (autotune), 1 or 2 (row tiles), 3 (two-step row tiles), 4, 8, "
                      "16 (FP32) or 32, 64 (even nx)"
                    : "D3Q15 tile_rows must be 0 (autotune), 1 (shared-memory tiles), 8 or 16 (z planes per block), "
-                     "32, 64 (separable, 16 or 32 planes per block), 96 (separable forward, 16 x 16 columns)");
+                     "32, 64 (separable, 16 or 32 planes per block), 96 (separable forward, 16 x 16 columns), "
+                     "128, 160 (plane-pair separable kernels, FP32, 16 or 32 planes per block)");
     if (p->tile_rows_adj != 0 && (p->tile_rows == 0 || !variant_ok(p->tile_rows_adj, false)))
         bad("tile_rows_adj must be 0, or a valid adjoint variant with tile_rows != 0");
     if (p->tile_rows_rec != 0 && (p->tile_rows == 0 || !variant_ok(p->tile_rows_rec, true)))
@@ -853,6 +857,7 @@ void run_forward(lks_ctx* c, cudaStream_t s) {
     if (!c->use_graphs) c->spans_fwd = c->spans;
     c->stats.forward_steps = c->prm.Nt;
     c->have_forward = true;
+    c->have_final = true;
 }
 
 void forward_body(lks_ctx* c, cudaStream_t s) {
@@ -1369,7 +1374,7 @@ int lks_forward_dev(lks_ctx* c, const double* d_gamma, const double* d_pos, doub
         cudaStream_t s = (cudaStream_t)stream;
         LKS_CUDA(cudaMemcpyAsync(c->d_gamma, d_gamma, c->nd * 8, cudaMemcpyDeviceToDevice, s));
         LKS_CUDA(cudaMemcpyAsync(c->d_knots, d_pos, (size_t)c->prm.K * c->D * 8, cudaMemcpyDeviceToDevice, s));
-        c->have_forward = false;
+        c->have_forward = c->have_final = false;
         run_forward(c, s);
         if (d_J) LKS_CUDA(cudaMemcpyAsync(d_J, c->d_J, 8, cudaMemcpyDeviceToDevice, s));
     });
@@ -1382,7 +1387,7 @@ int lks_forward(lks_ctx* c, const double* gamma, const double* pos, double* J) {
         cudaStream_t s = 0;
         LKS_CUDA(cudaMemcpyAsync(c->d_gamma, gamma, c->nd * 8, cudaMemcpyHostToDevice, s));
         LKS_CUDA(cudaMemcpyAsync(c->d_knots, pos, (size_t)c->prm.K * c->D * 8, cudaMemcpyHostToDevice, s));
-        c->have_forward = false;
+        c->have_forward = c->have_final = false;
         run_forward(c, s);
         double j = 0.0;
         LKS_CUDA(cudaMemcpyAsync(&j, c->d_J, 8, cudaMemcpyDeviceToHost, s));
@@ -1567,7 +1572,7 @@ int lks_get_state(lks_ctx* c, double* p, double* u) {
     if (!c) return LKS_EINVAL;
     return guard(c, [&] {
         if (!p || !u) throw LksError{LKS_EINVAL, "null pointer"};
-        if (!c->have_forward) throw LksError{LKS_ESTATE, "no forward has run"};
+        if (!c->have_final) throw LksError{LKS_ESTATE, "no forward has run"};
         const long long N = c->g.N;
         double* dp = nullptr;
         LKS_CUDA(cudaMalloc(&dp, (size_t)(c->D + 1) * N * 8));

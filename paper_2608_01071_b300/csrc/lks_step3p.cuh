@@ -1,0 +1,822 @@
+// D3Q15 forward step on plane pairs with packed FP32x2 arithmetic (FP32 state only).
+//
+// Same separable algebra as fwd3s_kernel (the streamed moments of Eqs. p_tmp, u_tmp as sums and differences over the
+// in-plane diagonal neighbours of the fields Q = sigma + tr T, T_xy, T_xz, T_yz and u, plus the face terms), but a
+// block marches its columns two planes at a time: the fields of planes k and k+1 are computed together, one FP32x2
+// instruction for both, and stored interleaved in shared memory as float2, so that one 8-byte shared load feeds the
+// same stencil position of both planes.  Only the coupling along z between the planes of a pair and the neighbouring
+// pairs is done in scalar arithmetic (a few additions per node).  Raw planes (p', u) arrive by 16-byte asynchronous
+// copies (4-byte copies when n_x is not a multiple of 4) into a ring of three plane pairs, one pair ahead of use.
+//
+// Per iteration j the block holds the raw planes k-1 .. k+2 (k = z0 - 1 + 2j) and
+//   (A) evaluates the fields of planes k, k+1 on the halo-1 region (each thread its own column and at most one node
+//       of the halo-1 ring),
+//   (B) forms, for its own column, the in-plane sums and the emissions of planes k, k+1 to their z-neighbours, which
+//       completes the moments of planes k-1 and k; Brinkman (Eqs. p, u), walls and the stores follow.
+// Planes z0 - 1 .. z0 + ZB are evaluated for the ZB output planes z0 .. z0 + ZB - 1.
+#pragma once
+
+#include "lks_common.cuh"
+#include "lks_step_kernels.cuh"
+#include "lks_step3s.cuh"
+
+namespace lks {
+
+struct Pair3 {
+    static constexpr int TX = 32, TY = 8, NT = TX * TY;
+    static constexpr int RX = TX + 8, RY = TY + 4, RS = RX * RY;  // raw region: x0 - 4 .. x0 + TX + 3, y0 - 2 .. y0 + TY + 1
+    static constexpr int MX = TX + 2, MY = TY + 2, NM = MX * MY;  // halo-1 field region
+    static constexpr int NR = NM - NT;                            // halo-1 ring nodes
+    static constexpr int CPR = RX / 4;                            // 16-byte chunks per raw row
+    static constexpr int NCH = 4 * RY * CPR;                      // chunks of one raw plane (4 fields)
+    static constexpr int PERCH = (NCH + NT - 1) / NT;
+    static constexpr int NEL = 4 * RS;                            // elements of one raw plane
+    static constexpr int PEREL = (NEL + NT - 1) / NT;
+    static constexpr int NFLD = 9;  // float2 field arrays: Q, T_xy, T_xz, T_yz, P_x = sigma + T_xx, P_y, u_x, u_y, u_z
+    static_assert(NR <= NT, "one ring node per thread at most");
+    static_assert(Sep3<TY>::MX == MX && Sep3<TY>::MY == MY, "ring_node layout");
+};
+
+__host__ __device__ constexpr size_t smem3p_fwd() {
+    return sizeof(float) * 6 * 4 * Pair3::RS + sizeof(float2) * (Pair3::NFLD * Pair3::NM + 2 * Pair3::NT);
+}
+
+// Packed FP32x2 arithmetic (one instruction for both planes; rounding as the scalar instructions; a - b = fma(b, -1, a)).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// 16-byte asynchronous global-to-shared copy, cached in L2 only.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// Mapped kappa and C of Eqs. kappa and u_s along one analysis column of the footprint box, for the hat kernel.
+// The 2 x 2 x 2 design taps of a node factor into x, y and z weights.  The x-y part of design plane jz,
+//   K_xy(jz) = sum_{kx, ky} w_x[kx] w_y[ky] kappa^ref[jx0 + kx, jy0 + ky, jz],
+// is the same for every node of the column, and consecutive nodes share one of their two design planes: a window of
+// two K_xy values rolls upward, and each new plane adds one (four loads) instead of evaluating all eight taps.
+struct ColumnMapHat {
+    float wxy[4];  // products of the valid x and y tap weights (0 for a tap outside the design grid)
+    int off[4];    // design-grid offsets of the x-y taps (clamped into the grid where the weight is 0)
+    float cxy;     // sum of the valid x weights times the sum of the valid y weights
+    float win[2];  // K_xy of design planes jz0, jz0 + 1
+    int jz0;       // first design plane of the window (-2^30: empty)
+
+    __device__ __forceinline__ void init(const Geom& g, const Pose& P, int bx, int by) {
+        float wx[2], wy[2], sx = 0.f, sy = 0.f;
+        int ix[2], iy[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int jx = bx - 1 + k, jy = by - 1 + k;
+            const bool vx = jx >= 0 && jx < g.nde[0], vy = jy >= 0 && jy < g.nde[1];
+            wx[k] = vx ? P.wf[0][k] : 0.f;
+            wy[k] = vy ? P.wf[1][k] : 0.f;
+            ix[k] = vx ? jx : 0;
+            iy[k] = vy ? jy : 0;
+            sx += wx[k];
+            sy += wy[k];
+        }
+#pragma unroll
+        for (int l = 0; l < 2; ++l)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                wxy[k + 2 * l] = wx[k] * wy[l];
+                off[k + 2 * l] = ix[k] + g.nde[0] * iy[l];
+            }
+        cxy = sx * sy;
+        jz0 = -(1 << 30);
+    }
+    __device__ __forceinline__ float kxy(const Geom& g, const float* __restrict__ kref, int jz) const {
+        if (jz < 0 || jz >= g.nde[2]) return 0.f;
+        const float* kp = kref + (long long)g.nde[0] * g.nde[1] * jz;
+        float s = wxy[0] * kp[off[0]];
+#pragma unroll
+        for (int t = 1; t < 4; ++t) s += wxy[t] * kp[off[t]];
+        return s;
+    }
+    // kappa and C at box coordinate bz of the column
+    __device__ __forceinline__ void at(const Geom& g, const Pose& P, const float* __restrict__ kref, int bz, float& kap,
+                                       float& C) {
+        const int j0 = bz - 1;
+        if (j0 == jz0 + 1) {
+            win[0] = win[1];
+            win[1] = kxy(g, kref, j0 + 1);
+        } else if (j0 != jz0) {
+            win[0] = kxy(g, kref, j0);
+            win[1] = kxy(g, kref, j0 + 1);
+        }
+        jz0 = j0;
+        const bool v0 = j0 >= 0 && j0 < g.nde[2], v1 = j0 + 1 >= 0 && j0 + 1 < g.nde[2];
+        const float wz0 = v0 ? P.wf[2][0] : 0.f, wz1 = v1 ? P.wf[2][1] : 0.f;
+        kap = wz0 * win[0] + wz1 * win[1];
+        C = cxy * (wz0 + wz1);
+    }
+};
+
+// Forward step n-1 -> n (Sec. 2.2 / 2.3); same result as fwd_step_kernel up to the order of FP additions.
+// VEC4: n_x is a multiple of 4, so raw rows move in aligned 16-byte chunks that never straddle the periodic seam.
+template <int HW, int ZB, bool VEC4>
+__global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<float> a) {
+    using R = Pair3;
+    static_assert(ZB % 2 == 0, "planes come in pairs");
+    constexpr int NP = ZB / 2 + 1;  // iterations (field-plane pairs)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[2 * (R::NT / 32)];
+    float* raw = reinterpret_cast<float*>(smem_raw);                      // [6 planes][p', u_x, u_y, u_z][RS]
+    float2* fld = reinterpret_cast<float2*>(raw + 6 * 4 * R::RS);         // [NFLD][NM]
+    float2* fQ = fld;
+    float2* fXY = fld + R::NM;
+    float2* fXZ = fld + 2 * R::NM;
+    float2* fYZ = fld + 3 * R::NM;
+    float2* fPX = fld + 4 * R::NM;
+    float2* fPY = fld + 5 * R::NM;
+    float2* fUX = fld + 6 * R::NM;
+    float2* fUY = fld + 7 * R::NM;
+    float2* fUZ = fld + 8 * R::NM;
+    float2* fS0 = fld + 9 * R::NM;  // [NT]: sigma of the own column
+    float2* fZ0 = fS0 + R::NT;      // [NT]: sigma + T_zz of the own column
+
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long long N = g.N;
+    const long long plane = (long long)nx * ny;
+    const int x0 = blockIdx.x * R::TX, y0 = blockIdx.y * R::TY, z0 = blockIdx.z * ZB;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + R::TX * ty;
+    const float A = (float)g.A;
+    const Pose& P = *a.pose;
+
+    // plane-invariant copy descriptors of this thread's 16-byte chunks
+    long long goff[VEC4 ? R::PERCH : 1];
+    int soff[VEC4 ? R::PERCH : 1];
+    if (VEC4) {
+#pragma unroll
+        for (int q = 0; q < R::PERCH; ++q) {
+            const int e = tid + q * R::NT;
+            soff[q] = -1;
+            goff[q] = 0;
+            if (e < R::NCH) {
+                const int f = e / (R::RY * R::CPR), rem = e % (R::RY * R::CPR);
+                const int row = rem / R::CPR, cx = rem % R::CPR;
+                const int xw = wrap(x0 - 4 + 4 * cx, nx), yw = wrap(y0 - 2 + row, ny);
+                goff[q] = f * N + (long long)yw * nx + xw;
+                soff[q] = f * R::RS + row * R::RX + 4 * cx;
+            }
+        }
+    }
+    // raw plane k goes to ring slot (k - z0 + 2) mod 6
+    auto slot = [&](int k) -> float* { return raw + ((k - z0 + 2) % 6) * 4 * R::RS; };
+    auto issue = [&](int k) {
+        float* dst = slot(k);
+        const float* src = a.in + plane * wrap(k, nz);
+        if (VEC4) {
+#pragma unroll
+            for (int q = 0; q < R::PERCH; ++q)
+                if (soff[q] >= 0) cp_async16(dst + soff[q], src + goff[q]);
+        } else {
+#pragma unroll 1
+            for (int e = tid; e < R::NEL; e += R::NT) {
+                const int f = e / R::RS, rem = e % R::RS, row = rem / R::RX, col = rem % R::RX;
+                const long long go = f * N + (long long)wrap(y0 - 2 + row, ny) * nx + wrap(x0 - 4 + col, nx);
+                cp_async<4>(dst + e, src + go);
+            }
+        }
+    };
+    auto issue_pair = [&](int j) {  // raw planes z0 - 2 + 2j, z0 - 1 + 2j as one copy group
+        issue(z0 - 2 + 2 * j);
+        issue(z0 - 1 + 2 * j);
+        cp_async_commit();
+    };
+
+    // field nodes of this thread: 0 = own column, 1 = a node of the halo-1 ring (tid < NR)
+    const bool has1 = tid < R::NR;
+    int fi[2], fj[2];
+    fi[0] = tx + 1;
+    fj[0] = ty + 1;
+    ring_node<R::TY>(has1 ? tid : 0, fi[1], fj[1]);
+    int mrow[2], rrow[2];  // index in the halo-1 field region and in the raw region
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        mrow[s] = fi[s] + R::MX * fj[s];
+        rrow[s] = (fi[s] + 3) + R::RX * (fj[s] + 1);
+    }
+    const int xg = x0 + tx, yg = y0 + ty;
+    const bool col = xg < nx && yg < ny;
+    const int bx = box_coord(xg, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
+    const int by = box_coord(yg, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
+    const bool colbox = col && bx >= 0 && by >= 0;
+    const int xs2 = P.xs[2];
+    const float uG0 = P.uGf[0], uG1 = P.uGf[1], uG2 = P.uGf[2];
+    const float2 c3 = f2s(3.f), c2 = f2s(2.f), cA = f2s(A), chA = f2s(0.5f * A), c45 = f2s(4.5f), cm15 = f2s(-1.5f);
+    const float2 w0 = f2s(2.f / 9.f), wf = f2s(1.f / 9.f), wc = f2s(1.f / 72.f);
+
+    pdl_wait_then_release();
+    issue_pair(0);
+    issue_pair(1);
+
+    // moments carried between iterations: plane k-1 without its emission from plane k (accA), and the emission of
+    // plane k (the previous pair's second plane) to plane k+1 (dnB); components p*, u*_x, u*_y, u*_z
+    float accA[4] = {0.f, 0.f, 0.f, 0.f}, dnB[4] = {0.f, 0.f, 0.f, 0.f};
+    bool unstable = false;
+
+    // wall planes of the column's x and y (Sec. 2.2 reading: where wall planes meet, the later axis' velocity wins);
+    // the wall velocities are read only at wall nodes
+    int wxy_axis = -1, wxy_side = 0;
+    if (!g.periodic[0] && (xg == 0 || xg == nx - 1)) {
+        wxy_axis = 0;
+        wxy_side = xg == 0 ? 0 : 1;
+    }
+    if (!g.periodic[1] && (yg == 0 || yg == ny - 1)) {
+        wxy_axis = 1;
+        wxy_side = yg == 0 ? 0 : 1;
+    }
+    ColumnMapHat cmap;
+    if (HW == 1 && colbox) cmap.init(g, P, bx, by);
+    const long long gcol = xg + (long long)nx * yg;
+
+    // Brinkman, walls and stores of one completed output plane
+    auto emit = [&](int zo, float mp, float mx, float my, float mz) {
+        if (zo < z0 || zo >= z0 + ZB || zo >= nz || !col) return;
+        const float pn = mp * (1.f / 3.f);
+        float un[3] = {mx, my, mz};
+        const int bz = colbox ? box_coord(zo, xs2, g.Fb[2], g.n[2], g.periodic[2]) : -1;
+        if (bz >= 0) {
+            float kap, C;
+            if (HW == 1) {
+                cmap.at(g, P, a.kref, bz, kap, C);
+            } else {
+                const int b[3] = {bx, by, bz};
+                map_node<float, 3, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
+            }
+            const float inv = 1.f / (1.f + kap);
+            un[0] = (un[0] + kap * (uG0 * C)) * inv;
+            un[1] = (un[1] + kap * (uG1 * C)) * inv;
+            un[2] = (un[2] + kap * (uG2 * C)) * inv;
+        }
+        const int wz_side = g.periodic[2] ? -1 : (zo == 0 ? 0 : (zo == nz - 1 ? 1 : -1));
+        const bool wall = wxy_axis >= 0 || wz_side >= 0;
+        if (wall) {
+            const int ax = wz_side >= 0 ? 2 : wxy_axis, sd = wz_side >= 0 ? wz_side : wxy_side;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) un[c] = (float)g.wall_u[ax][sd][c];
+        }
+        const long long gi = gcol + plane * zo;
+        a.out_p[gi] = pn;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a.out_u[c * N + gi] = un[c];
+        if (!wall && a.u_crit2 > 0.f && !(un[0] * un[0] + un[1] * un[1] + un[2] * un[2] <= a.u_crit2)) unstable = true;
+    };
+
+#pragma unroll 1
+    for (int j = 0; j < NP; ++j) {
+        // raw pair j + 2 into the slots of pair j - 1 (read in phase A of the previous iteration, before its barrier);
+        // pair j + 1 has arrived once at most the newest group is pending
+        if (j + 2 <= NP)
+            issue_pair(j + 2);
+        else
+            cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const int k = z0 - 1 + 2 * j;
+        const float* pm = slot(k - 1);
+        const float* p0 = slot(k);
+        const float* p1 = slot(k + 1);
+        const float* p2 = slot(k + 2);
+        // (A) fields of planes k, k+1 at the field nodes
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (s == 1 && !has1) break;
+            const int r = rrow[s];
+            float2 U[3], Gx[3], Gy[3], Gz[3];  // twice the central differences of u_c along x, y, z
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float* a0 = p0 + (1 + c) * R::RS;
+                const float* a1 = p1 + (1 + c) * R::RS;
+                const float u0 = a0[r], u1 = a1[r];
+                U[c] = f2(u0, u1);
+                Gx[c] = f2sub(f2(a0[r + 1], a1[r + 1]), f2(a0[r - 1], a1[r - 1]));
+                Gy[c] = f2sub(f2(a0[r + R::RX], a1[r + R::RX]), f2(a0[r - R::RX], a1[r - R::RX]));
+                Gz[c] = f2sub(f2(u1, p2[(1 + c) * R::RS + r]), f2(pm[(1 + c) * R::RS + r], u0));
+            }
+            const float2 Pp = f2(p0[r], p1[r]);
+            const float2 uu = f2fma(U[2], U[2], f2fma(U[1], U[1], f2mul(U[0], U[0])));
+            const float2 sig = f2fma(c3, Pp, f2mul(cm15, uu));
+            const float2 Txx = f2fma(c45, f2mul(U[0], U[0]), f2mul(cA, Gx[0]));
+            const float2 Tyy = f2fma(c45, f2mul(U[1], U[1]), f2mul(cA, Gy[1]));
+            const float2 Tzz = f2fma(c45, f2mul(U[2], U[2]), f2mul(cA, Gz[2]));
+            const float2 Txy = f2fma(c45, f2mul(U[0], U[1]), f2mul(chA, f2add(Gx[1], Gy[0])));
+            const float2 Txz = f2fma(c45, f2mul(U[0], U[2]), f2mul(chA, f2add(Gx[2], Gz[0])));
+            const float2 Tyz = f2fma(c45, f2mul(U[1], U[2]), f2mul(chA, f2add(Gy[2], Gz[1])));
+            const int m = mrow[s];
+            const float2 px = f2add(sig, Txx), py = f2add(sig, Tyy);
+            fQ[m] = f2add(f2add(px, Tyy), Tzz);
+            fXY[m] = Txy;
+            fXZ[m] = Txz;
+            fYZ[m] = Tyz;
+            fPX[m] = px;
+            fPY[m] = py;
+            fUX[m] = U[0];
+            fUY[m] = U[1];
+            fUZ[m] = U[2];
+            if (s == 0) {  // sigma and sigma + T_zz of the own column, for (B)
+                fS0[tid] = sig;
+                fZ0[tid] = f2add(sig, Tzz);
+            }
+        }
+        __syncthreads();
+        // (B) in-plane sums and z emissions of planes k, k+1 along this thread's column
+        {
+            const int m = mrow[0];
+            // S/D products over the four diagonal in-plane neighbours (x-1, y-1), (x+1, y-1), (x-1, y+1), (x+1, y+1):
+            // S g = g(-1) + g(+1), D g = g(-1) - g(+1) along x (first letter) and y (second letter)
+            auto sd4 = [&](const float2* f, float2& SS, float2& DS, float2& SD, float2& DD) {
+                const float2 va = f[m - 1 - R::MX], vb = f[m + 1 - R::MX], vc = f[m - 1 + R::MX], vd = f[m + 1 + R::MX];
+                const float2 s1 = f2add(va, vb), s2 = f2add(vc, vd), d1 = f2sub(va, vb), d2 = f2sub(vc, vd);
+                SS = f2add(s1, s2);
+                SD = f2sub(s1, s2);
+                DS = f2add(d1, d2);
+                DD = f2sub(d1, d2);
+            };
+            // A1 = Q_SS + 3 (ux_DS + uy_SD) + 2 Txy_DD,  A2 = 3 uz_SS + 2 (Txz_DS + Tyz_SD),
+            // B1 = Q_DS + 3 (ux_SS + uy_DD) + 2 Txy_SD,  B2 = 3 uz_DS + 2 (Txz_SS + Tyz_DD),
+            // C1 = Q_SD + 3 (ux_DD + uy_SS) + 2 Txy_DS,  C2 = 3 uz_SD + 2 (Txz_DD + Tyz_SS),
+            // accumulated field by field so that only one field's products are live at a time
+            float2 A1, A2, B1, B2, C1, C2, SS, DS, SD, DD;
+            sd4(fQ, SS, DS, SD, DD);
+            A1 = SS;
+            B1 = DS;
+            C1 = SD;
+            sd4(fUX, SS, DS, SD, DD);
+            A1 = f2fma(c3, DS, A1);
+            B1 = f2fma(c3, SS, B1);
+            C1 = f2fma(c3, DD, C1);
+            sd4(fUY, SS, DS, SD, DD);
+            A1 = f2fma(c3, SD, A1);
+            B1 = f2fma(c3, DD, B1);
+            C1 = f2fma(c3, SS, C1);
+            sd4(fXY, SS, DS, SD, DD);
+            A1 = f2fma(c2, DD, A1);
+            B1 = f2fma(c2, SD, B1);
+            C1 = f2fma(c2, DS, C1);
+            sd4(fUZ, SS, DS, SD, DD);
+            A2 = f2mul(c3, SS);
+            B2 = f2mul(c3, DS);
+            C2 = f2mul(c3, SD);
+            sd4(fXZ, SS, DS, SD, DD);
+            A2 = f2fma(c2, DS, A2);
+            B2 = f2fma(c2, SS, B2);
+            C2 = f2fma(c2, DD, C2);
+            sd4(fYZ, SS, DS, SD, DD);
+            A2 = f2fma(c2, SD, A2);
+            B2 = f2fma(c2, DD, B2);
+            C2 = f2fma(c2, SS, C2);
+            // face terms: in-plane x and y, and z from the column's own fields
+            const float2 sig0 = fS0[tid], pz0 = fZ0[tid], uz0 = fUZ[m];
+            const float2 pxm = fPX[m - 1], pxp = fPX[m + 1], pym = fPY[m - R::MX], pyp = fPY[m + R::MX];
+            const float2 uxm = fUX[m - 1], uxp = fUX[m + 1], uym = fUY[m - R::MX], uyp = fUY[m + R::MX];
+            const float2 inP = f2fma(w0, sig0, f2mul(wf, f2add(f2add(f2add(pxm, pxp), f2add(pym, pyp)),
+                                                               f2mul(c3, f2add(f2sub(uxm, uxp), f2sub(uym, uyp))))));
+            const float2 inX = f2mul(wf, f2fma(c3, f2add(uxm, uxp), f2sub(pxm, pxp)));
+            const float2 inY = f2mul(wf, f2fma(c3, f2add(uym, uyp), f2sub(pym, pyp)));
+            const float2 fzd = f2mul(wf, f2fma(c3, uz0, pz0)), fzu = f2mul(wf, f2sub(pz0, f2mul(c3, uz0)));
+            // emissions to the plane above (dn: this plane is its z-1 neighbour) and below (up)
+            const float2 dnP = f2fma(wc, f2add(A1, A2), fzd);
+            const float2 dnX = f2mul(wc, f2add(B1, B2)), dnY = f2mul(wc, f2add(C1, C2));
+            const float2 upP = f2fma(wc, f2sub(A1, A2), fzu);
+            const float2 upX = f2mul(wc, f2sub(B1, B2)), upY = f2mul(wc, f2sub(C1, C2));
+            // plane k-1 gets the emission of plane k; plane k the one of plane k+1 (and the carried one of k-1)
+            const float oA0 = accA[0] + upP.x, oA1 = accA[1] + upX.x, oA2 = accA[2] + upY.x, oA3 = accA[3] - upP.x;
+            const float oB0 = (inP.x + dnB[0]) + upP.y, oB1 = (inX.x + dnB[1]) + upX.y, oB2 = (inY.x + dnB[2]) + upY.y,
+                        oB3 = dnB[3] - upP.y;
+            accA[0] = inP.y + dnP.x;
+            accA[1] = inX.y + dnX.x;
+            accA[2] = inY.y + dnY.x;
+            accA[3] = dnP.x;
+            dnB[0] = dnP.y;
+            dnB[1] = dnX.y;
+            dnB[2] = dnY.y;
+            dnB[3] = dnP.y;
+            emit(k - 1, oA0, oA1, oA2, oA3);
+            emit(k, oB0, oB1, oB2, oB3);
+        }
+    }
+    if (unstable) atomicOr(a.flag, 1u);
+    if (a.jslot != nullptr) {
+        const int px = (int)blockIdx.x - a.jb_lo[0], py = (int)blockIdx.y - a.jb_lo[1], pz = (int)blockIdx.z - a.jb_lo[2];
+        if (px >= 0 && px < a.jb_n[0] && py >= 0 && py < a.jb_n[1] && pz >= 0 && pz < a.jb_n[2]) {
+            // objective partials from this thread's own outputs, re-read after the march (planes upward)
+            float jacc = 0.f, qacc = 0.f;
+            if (col) {
+                for (int zo = max(z0, g.probe_lo[2]); zo < min(min(z0 + ZB, nz), g.probe_hi[2]); ++zo) {
+                    int xyz[3] = {xg, yg, zo};
+                    float uw[3];
+                    if (!in_probe<3>(g, xyz) || wall_node<float, 3>(g, xyz, uw)) continue;
+                    const long long gi = xg + (long long)nx * yg + plane * zo;
+                    const float nu = a.dir[0] * a.out_u[gi] + a.dir[1] * a.out_u[N + gi] + a.dir[2] * a.out_u[2 * N + gi];
+                    jacc += nu;
+                    qacc += nu * nu;
+                }
+            }
+            store_probe_partials<R::NT, float>(jacc, qacc, a.jslot, a.jsq, px + a.jb_n[0] * (py + a.jb_n[1] * pz), red);
+        }
+    }
+}
+
+
+// ------------------------------------------------------------------------------------------------
+// Adjoint step lambda_n -> lambda_{n-1} on plane pairs (packed FP32x2); the algebra of adj3s_kernel.
+//
+// With P = p-bar*/3 = lambda_p/3 and (X, Y, Z) = u-bar* = lambda_u/(1 + kappa) (0 on walls) staged on the halo-2
+// region as float2 pairs of planes (k, k+1), the local moments M0, M1, M2 of the planes are gathers from y + c_i that
+// factor into S g = g(+1) + g(-1) and D g = g(+1) - g(-1) products over the in-plane diagonal neighbours, plus the
+// face terms; a plane emits U = w (E + Z) to the plane below and L = w (E - Z) to the plane above.  A pair of raw
+// planes (k, k+1) therefore completes the moments of planes k-1 and k: one completed pair C_j per iteration, whose
+// M2 goes to shared memory on the halo-1 region (the A term needs its in-plane neighbours) and whose M0, M1 stay
+// with the own column.  The output pair is C_{j-1}, written one iteration later, when the M2 of the plane above it
+// is known: every step of the output is FP32x2 as well, with the M2 z-neighbours taken from the column itself.
+//
+// Iteration j: raw pair j (planes z0 - 2 + 2j, z0 - 1 + 2j) -> C_j (planes z0 - 3 + 2j, z0 - 2 + 2j);
+// output C_{j-1} (planes z0 - 5 + 2j, z0 - 4 + 2j) for j >= 2.  Raw lambda arrives by asynchronous copies one pair
+// ahead and is transformed into the staged pair one iteration ahead of use.
+// ------------------------------------------------------------------------------------------------
+struct PairA3 {
+    static constexpr int TX = 32, TY = 8, NT = TX * TY;
+    static constexpr int RX = TX + 8, RY = TY + 4, RS = RX * RY;  // raw lambda: x0 - 4 .. x0 + TX + 3, y0 - 2 .. y0 + TY + 1
+    static constexpr int SX = TX + 4, SY = TY + 4, NS = SX * SY;  // staged P, X, Y, Z (halo 2): x0 - 2 .. x0 + TX + 1
+    static constexpr int MX = TX + 2, MY = TY + 2, NM = MX * MY;  // moments (halo 1)
+    static constexpr int NR = NM - NT;
+    static constexpr int CPR = RX / 4, NCH = 4 * RY * CPR, PERCH = (NCH + NT - 1) / NT;
+    static constexpr int NEL = 4 * RS;
+    static constexpr int PERT = (NS + NT - 1) / NT;  // staged elements per thread
+    // per moment slot: M2 xx, yy, xy, xz, yz, zz over the halo-1 region, then M0, M1x, M1y, M1z of the own columns
+    static constexpr int SLOT = 6 * NM + 4 * NT;
+    static_assert(NR <= NT && PERT == 2, "layout");
+};
+
+__host__ __device__ constexpr size_t smem3p_adj() {
+    return sizeof(float) * 2 * 2 * 4 * PairA3::RS + sizeof(float2) * (2 * 4 * PairA3::NS + 2 * PairA3::SLOT);
+}
+
+template <int HW, int ZB, bool VEC4>
+__global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<float> a) {
+    using R = PairA3;
+    static_assert(ZB % 2 == 0, "planes come in pairs");
+    constexpr int NRP = ZB / 2 + 2;  // raw pairs
+    constexpr int NJ = ZB / 2 + 3;   // iterations: raw pairs 0 .. NRP - 1, outputs of C_1 .. C_{NRP - 1}
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* stg = reinterpret_cast<float*>(smem_raw);                  // [2 pair slots][2 planes][4 fields][RS]
+    float2* tl = reinterpret_cast<float2*>(stg + 2 * 2 * 4 * R::RS);  // [2 slots][P, X, Y, Z][NS]
+    float2* mom = tl + 2 * 4 * R::NS;                                 // [2 slots][SLOT]
+
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long long N = g.N;
+    const long long plane = (long long)nx * ny;
+    const int x0 = blockIdx.x * R::TX, y0 = blockIdx.y * R::TY, z0 = blockIdx.z * ZB;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + R::TX * ty;
+    const Pose& P = *a.pose;
+    const int xs2 = P.xs[2];
+    const bool zper = g.periodic[2] != 0;
+
+    // raw copies: plane-invariant descriptors of this thread's 16-byte chunks
+    long long goff[VEC4 ? R::PERCH : 1];
+    int soff[VEC4 ? R::PERCH : 1];
+    if (VEC4) {
+#pragma unroll
+        for (int q = 0; q < R::PERCH; ++q) {
+            const int e = tid + q * R::NT;
+            soff[q] = -1;
+            goff[q] = 0;
+            if (e < R::NCH) {
+                const int f = e / (R::RY * R::CPR), rem = e % (R::RY * R::CPR);
+                const int row = rem / R::CPR, cx = rem % R::CPR;
+                const int xw = wrap(x0 - 4 + 4 * cx, nx), yw = wrap(y0 - 2 + row, ny);
+                goff[q] = f * N + (long long)yw * nx + xw;
+                soff[q] = f * R::RS + row * R::RX + 4 * cx;
+            }
+        }
+    }
+    auto issue_plane = [&](float* dst, int k) {
+        const float* src = a.lam_in + plane * wrap(k, nz);
+        if (VEC4) {
+#pragma unroll
+            for (int q = 0; q < R::PERCH; ++q)
+                if (soff[q] >= 0) cp_async16(dst + soff[q], src + goff[q]);
+        } else {
+#pragma unroll 1
+            for (int e = tid; e < R::NEL; e += R::NT) {
+                const int f = e / R::RS, rem = e % R::RS, row = rem / R::RX, col = rem % R::RX;
+                const long long go = f * N + (long long)wrap(y0 - 2 + row, ny) * nx + wrap(x0 - 4 + col, nx);
+                cp_async<4>(dst + e, src + go);
+            }
+        }
+    };
+    auto issue_pair = [&](int jj) {  // raw pair jj into staging slot jj % 2
+        float* dst = stg + (jj & 1) * 2 * 4 * R::RS;
+        issue_plane(dst, z0 - 2 + 2 * jj);
+        issue_plane(dst + 4 * R::RS, z0 - 1 + 2 * jj);
+        cp_async_commit();
+    };
+
+    // staged elements of this thread (halo-2 region): wall and footprint coordinates, and whether the element is one
+    // of the block's own columns (whose lambda_u footprint records this block writes)
+    int ebx[R::PERT], eby[R::PERT];
+    bool ewall[R::PERT], einner[R::PERT];
+#pragma unroll
+    for (int q = 0; q < R::PERT; ++q) {
+        const int e = tid + q * R::NT;
+        const int i = e % R::SX, jr = e / R::SX;
+        const int ex = wrap(x0 - 2 + i, nx), ey = wrap(y0 - 2 + jr, ny);
+        ebx[q] = box_coord(ex, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
+        eby[q] = box_coord(ey, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
+        ewall[q] = (!g.periodic[0] && (ex == 0 || ex == nx - 1)) || (!g.periodic[1] && (ey == 0 || ey == ny - 1));
+        einner[q] = e < R::NS && i >= 2 && i < R::TX + 2 && jr >= 2 && jr < R::TY + 2 && x0 - 2 + i < nx &&
+                    y0 - 2 + jr < ny && ebx[q] >= 0 && eby[q] >= 0;
+    }
+    // transform raw pair jj (staging slot jj % 2) into staged slot jj % 2; lambda_u records of own footprint nodes
+    auto transform = [&](int jj) {
+        const float* s0 = stg + (jj & 1) * 2 * 4 * R::RS;
+        const float* s1 = s0 + 4 * R::RS;
+        float2* t = tl + (jj & 1) * 4 * R::NS;
+        const int q0 = z0 - 2 + 2 * jj;
+        int kz[2], bz[2];
+        bool wz[2], own[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            kz[h] = wrap(q0 + h, nz);
+            bz[h] = box_coord(kz[h], xs2, g.Fb[2], g.n[2], g.periodic[2]);
+            wz[h] = !zper && (kz[h] == 0 || kz[h] == nz - 1);
+            own[h] = q0 + h >= z0 && q0 + h < z0 + ZB && q0 + h < nz;
+        }
+#pragma unroll
+        for (int q = 0; q < R::PERT; ++q) {
+            const int e = tid + q * R::NT;
+            if (e >= R::NS) continue;
+            const int si = (e % R::SX + 2) + R::RX * (e / R::SX);
+            float fac[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                fac[h] = (ewall[q] || wz[h]) ? 0.f : 1.f;
+                if (fac[h] != 0.f && ebx[q] >= 0 && eby[q] >= 0 && bz[h] >= 0)
+                    fac[h] = a.fac[ebx[q] + (long long)g.Fb[0] * (eby[q] + (long long)g.Fb[1] * bz[h])];
+            }
+            t[e] = f2(s0[si] * (1.f / 3.f), s1[si] * (1.f / 3.f));
+#pragma unroll
+            for (int c = 1; c < 4; ++c) {
+                const float l0 = s0[c * R::RS + si], l1 = s1[c * R::RS + si];
+                t[c * R::NS + e] = f2(l0 * fac[0], l1 * fac[1]);
+                if (einner[q]) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (own[h] && bz[h] >= 0) {
+                            const long long bl = ebx[q] + (long long)g.Fb[0] * (eby[q] + (long long)g.Fb[1] * bz[h]);
+                            a.boxbuf[(c - 1) * g.Fbn + bl] = (ewall[q] || wz[h]) ? 0.f : (h == 0 ? l0 : l1);
+                        }
+                    }
+                }
+            }
+        }
+    };
+
+    // field nodes: 0 = own column, 1 = a node of the halo-1 ring (tid < NR)
+    const bool has1 = tid < R::NR;
+    int fi[2], fj[2];
+    fi[0] = tx + 1;
+    fj[0] = ty + 1;
+    ring_node<R::TY>(has1 ? tid : 0, fi[1], fj[1]);
+    int mrow[2], rrow[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        mrow[s] = fi[s] + R::MX * fj[s];
+        rrow[s] = (fi[s] + 1) + R::SX * (fj[s] + 1);
+    }
+    const int xg = x0 + tx, yg = y0 + ty;
+    const bool col = xg < nx && yg < ny;
+    const long long gcol = xg + (long long)nx * yg;
+    const int bx = box_coord(xg, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
+    const int by = box_coord(yg, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
+    const bool colbox = col && bx >= 0 && by >= 0;
+    const bool probe_xy = a.src && xg >= g.probe_lo[0] && xg < g.probe_hi[0] && yg >= g.probe_lo[1] && yg < g.probe_hi[1] &&
+                          !((!g.periodic[0] && (xg == 0 || xg == nx - 1)) || (!g.periodic[1] && (yg == 0 || yg == ny - 1)));
+    const float2 w0 = f2s(2.f / 9.f), wf = f2s(1.f / 9.f), wc = f2s(1.f / 72.f), c3 = f2s(3.f), c9 = f2s(9.f);
+    const float2 cA = f2s((float)g.A), cm3 = f2s(-3.f);
+
+    pdl_wait_then_release();
+    issue_pair(0);
+    cp_async_wait<0>();
+    __syncthreads();
+    transform(0);
+    issue_pair(1);
+
+    // partial moments of plane k+1 (in(k+1) + L(k)) and the distinct emission terms of plane k+1 to plane k+2, per
+    // field node (the ring node needs the M2 components only); z-neighbour M2 (xz, yz, zz) of the plane below the
+    // output pair
+    float cA0[10], cA1[5];
+    float cL0[5], cL1[4];
+#pragma unroll
+    for (int c = 0; c < 10; ++c) cA0[c] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) cA1[c] = cL0[c] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) cL1[c] = 0.f;
+    float zm[3] = {0.f, 0.f, 0.f};
+
+#pragma unroll 1
+    for (int j = 0; j < NJ; ++j) {
+        cp_async_wait<0>();  // raw pair j + 1 (this thread's copies)
+        __syncthreads();
+        if (j + 2 < NRP) issue_pair(j + 2);
+        if (j + 1 < NRP) transform(j + 1);
+        if (j < NRP) {
+            // (B) moments of planes k-1, k from raw pair j = (k, k+1), k = z0 - 2 + 2j
+            const float2* tP = tl + (j & 1) * 4 * R::NS;
+            const float2* tX = tP + R::NS;
+            const float2* tY = tP + 2 * R::NS;
+            const float2* tZ = tP + 3 * R::NS;
+            float2* ms = mom + (j & 1) * R::SLOT;
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                if (s == 1 && !has1) break;
+                const int r = rrow[s];
+                // S/D products over the diagonal neighbours; here D g = g(+1) - g(-1)
+                auto sd4 = [&](const float2* f, float2& SS, float2& DS, float2& SD, float2& DD) {
+                    const float2 va = f[r - 1 - R::SX], vb = f[r + 1 - R::SX], vc = f[r - 1 + R::SX], vd = f[r + 1 + R::SX];
+                    const float2 s1 = f2add(va, vb), s2 = f2add(vc, vd), d1 = f2sub(vb, va), d2 = f2sub(vd, vc);
+                    SS = f2add(s1, s2);
+                    SD = f2sub(s2, s1);
+                    DS = f2add(d1, d2);
+                    DD = f2sub(d2, d1);
+                };
+                float2 E0, E1, E2, E3, SS, DS, SD, DD;
+                sd4(tP, SS, DS, SD, DD);
+                E0 = SS;
+                E1 = DS;
+                E2 = SD;
+                E3 = DD;
+                sd4(tX, SS, DS, SD, DD);
+                E0 = f2add(E0, DS);
+                E1 = f2add(E1, SS);
+                E2 = f2add(E2, DD);
+                E3 = f2add(E3, SD);
+                sd4(tY, SS, DS, SD, DD);
+                E0 = f2add(E0, SD);
+                E1 = f2add(E1, DD);
+                E2 = f2add(E2, SS);
+                E3 = f2add(E3, DS);
+                sd4(tZ, SS, DS, SD, DD);
+                const float2 U0 = f2mul(wc, f2add(E0, SS)), U1 = f2mul(wc, f2add(E1, DS)), U2 = f2mul(wc, f2add(E2, SD)),
+                             U3 = f2mul(wc, f2add(E3, DD));
+                const float2 L0 = f2mul(wc, f2sub(E0, SS)), L1 = f2mul(wc, f2sub(E1, DS)), L2 = f2mul(wc, f2sub(E2, SD)),
+                             L3 = f2mul(wc, f2sub(E3, DD));
+                // faces: in-plane x and y; z from the node's own column
+                const float2 pxm = tP[r - 1], pxp = tP[r + 1], vxm = tX[r - 1], vxp = tX[r + 1];
+                const float2 pym = tP[r - R::SX], pyp = tP[r + R::SX], vym = tY[r - R::SX], vyp = tY[r + R::SX];
+                const float2 fx = f2mul(wf, f2add(f2add(pxp, pxm), f2sub(vxp, vxm)));
+                const float2 fy = f2mul(wf, f2add(f2add(pyp, pym), f2sub(vyp, vym)));
+                const int m = mrow[s];
+                if (s == 0) {
+                    const float2 pc = tP[r], vzc = tZ[r];
+                    const float2 zd = f2mul(wf, f2add(pc, vzc)), zu = f2mul(wf, f2sub(pc, vzc));
+                    const float2 in0 = f2fma(w0, pc, f2add(fx, fy));
+                    const float2 in1 = f2mul(wf, f2add(f2sub(pxp, pxm), f2add(vxp, vxm)));
+                    const float2 in2 = f2mul(wf, f2add(f2sub(pyp, pym), f2add(vyp, vym)));
+                    // contributions of the pair's planes: in-plane In, from the plane above Uc, from the plane below Lc
+                    // (components M0, M1x, M1y, M1z, M2xx, M2yy, M2zz, M2xy, M2xz, M2yz)
+                    const float2 Uz = f2add(U0, zd), Lz = f2add(L0, zu);
+                    const float2 In[10] = {in0, in1, in2, f2s(0.f), fx, fy, f2s(0.f), f2s(0.f), f2s(0.f), f2s(0.f)};
+                    const float2 Uc[10] = {Uz, U1, U2, Uz, U0, U0, Uz, U3, U1, U2};
+                    // Lc of the previous pair's second plane, from its distinct terms (L0, L1, L2, L3, L0 + zu)
+                    const float Lp[10] = {cL0[4], cL0[1], cL0[2], -cL0[4], cL0[0], cL0[0], cL0[4], cL0[3], -cL0[1], -cL0[2]};
+                    float2 Mc[10];
+#pragma unroll
+                    for (int c = 0; c < 10; ++c) {
+                        Mc[c].x = cA0[c] + Uc[c].x;
+                        Mc[c].y = (In[c].x + Lp[c]) + Uc[c].y;
+                    }
+                    // carries: plane k+1 without its emission from the next pair; the distinct L terms of plane k+1
+                    const float Lx[10] = {Lz.x, L1.x, L2.x, -Lz.x, L0.x, L0.x, Lz.x, L3.x, -L1.x, -L2.x};
+#pragma unroll
+                    for (int c = 0; c < 10; ++c) cA0[c] = In[c].y + Lx[c];
+                    cL0[0] = L0.y;
+                    cL0[1] = L1.y;
+                    cL0[2] = L2.y;
+                    cL0[3] = L3.y;
+                    cL0[4] = Lz.y;
+                    // completed pair: M2 on the halo-1 slot, M0 and M1 of the own column
+                    ms[m] = Mc[4];
+                    ms[R::NM + m] = Mc[5];
+                    ms[2 * R::NM + m] = Mc[7];
+                    ms[3 * R::NM + m] = Mc[8];
+                    ms[4 * R::NM + m] = Mc[9];
+                    ms[5 * R::NM + m] = Mc[6];
+                    float2* mo = ms + 6 * R::NM;
+                    mo[tid] = Mc[0];
+                    mo[R::NT + tid] = Mc[1];
+                    mo[2 * R::NT + tid] = Mc[2];
+                    mo[3 * R::NT + tid] = Mc[3];
+                } else {
+                    // the ring node needs the in-plane M2 components xx, yy, xy, xz, yz only
+                    const float2 In[5] = {fx, fy, f2s(0.f), f2s(0.f), f2s(0.f)};
+                    const float2 Uc[5] = {U0, U0, U3, U1, U2};
+                    const float Lp[5] = {cL1[0], cL1[0], cL1[3], -cL1[1], -cL1[2]};
+                    const float Lx[5] = {L0.x, L0.x, L3.x, -L1.x, -L2.x};
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) {
+                        float2 Mc;
+                        Mc.x = cA1[c] + Uc[c].x;
+                        Mc.y = (In[c].x + Lp[c]) + Uc[c].y;
+                        cA1[c] = In[c].y + Lx[c];
+                        ms[c * R::NM + m] = Mc;
+                    }
+                    cL1[0] = L0.y;
+                    cL1[1] = L1.y;
+                    cL1[2] = L2.y;
+                    cL1[3] = L3.y;
+                }
+            }
+        }
+        __syncthreads();
+        if (j >= 2) {
+            // (O) lambda_{n-1} of the pair C_{j-1} = planes (o0, o1) at the own column
+            const int o0 = z0 - 5 + 2 * j;
+            const float2* ms = mom + ((j - 1) & 1) * R::SLOT;  // C_{j-1}
+            const float2* mn = mom + (j & 1) * R::SLOT;        // C_j (its first plane is above the pair)
+            const int m = mrow[0];
+            const float2 Mxx = ms[m], Myy = ms[R::NM + m], Mxy = ms[2 * R::NM + m], Mxz = ms[3 * R::NM + m],
+                         Myz = ms[4 * R::NM + m], Mzz = ms[5 * R::NM + m];
+            const float2 M0 = ms[6 * R::NM + tid], M1x = ms[6 * R::NM + R::NT + tid], M1y = ms[6 * R::NM + 2 * R::NT + tid],
+                         M1z = ms[6 * R::NM + 3 * R::NT + tid];
+            // z-neighbours of the pair's planes: below (zm, .x), above (.y, C_j.x); C_j is empty on the last iteration
+            // (its plane lies past the block's planes and only feeds the discarded second lane)
+            const bool last = j >= NRP;
+            const float nxz = last ? 0.f : mn[3 * R::NM + m].x, nyz = last ? 0.f : mn[4 * R::NM + m].x,
+                        nzz = last ? 0.f : mn[5 * R::NM + m].x;
+            const float2 zxz = f2(zm[0] - Mxz.y, Mxz.x - nxz), zyz = f2(zm[1] - Myz.y, Myz.x - nyz),
+                         zzz = f2(zm[2] - Mzz.y, Mzz.x - nzz);
+            zm[0] = Mxz.y;
+            zm[1] = Myz.y;
+            zm[2] = Mzz.y;
+            // sum_a [M2_ab(y - e_a) - M2_ab(y + e_a)] for b = x, y, z
+            const float2 dAx = f2add(f2add(f2sub(ms[m - 1], ms[m + 1]), f2sub(ms[2 * R::NM + m - R::MX], ms[2 * R::NM + m + R::MX])), zxz);
+            const float2 dAy = f2add(f2add(f2sub(ms[2 * R::NM + m - 1], ms[2 * R::NM + m + 1]),
+                                           f2sub(ms[R::NM + m - R::MX], ms[R::NM + m + R::MX])), zyz);
+            const float2 dAz = f2add(f2add(f2sub(ms[3 * R::NM + m - 1], ms[3 * R::NM + m + 1]),
+                                           f2sub(ms[4 * R::NM + m - R::MX], ms[4 * R::NM + m + R::MX])), zzz);
+            bool ok[2];
+            float2 u[3] = {f2s(0.f), f2s(0.f), f2s(0.f)};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int zo = o0 + h;
+                ok[h] = col && zo >= z0 && zo < z0 + ZB && zo < nz;
+            }
+            const float* up = a.u_prev + gcol + plane * o0;
+            if (ok[0]) {
+                u[0].x = up[0];
+                u[1].x = up[N];
+                u[2].x = up[2 * N];
+            }
+            if (ok[1]) {
+                u[0].y = up[plane];
+                u[1].y = up[N + plane];
+                u[2].y = up[2 * N + plane];
+            }
+            // lambda_u = 3 M1 - 3 u M0 + 9 M2 u + A dA
+            const float2 m0u = f2mul(cm3, M0);
+            float2 v0 = f2fma(c3, M1x, f2fma(m0u, u[0], f2mul(cA, dAx)));
+            float2 v1 = f2fma(c3, M1y, f2fma(m0u, u[1], f2mul(cA, dAy)));
+            float2 v2 = f2fma(c3, M1z, f2fma(m0u, u[2], f2mul(cA, dAz)));
+            v0 = f2fma(c9, f2fma(Mxx, u[0], f2fma(Mxy, u[1], f2mul(Mxz, u[2]))), v0);
+            v1 = f2fma(c9, f2fma(Mxy, u[0], f2fma(Myy, u[1], f2mul(Myz, u[2]))), v1);
+            v2 = f2fma(c9, f2fma(Mxz, u[0], f2fma(Myz, u[1], f2mul(Mzz, u[2]))), v2);
+            const float2 lp = f2mul(c3, M0);
+            const float vx[2] = {v0.x, v0.y}, vy[2] = {v1.x, v1.y}, vz[2] = {v2.x, v2.y}, lpp[2] = {lp.x, lp.y};
+            const float ux[2] = {u[0].x, u[0].y}, uy[2] = {u[1].x, u[1].y}, uz[2] = {u[2].x, u[2].y};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!ok[h]) continue;
+                const int zo = o0 + h;
+                float v[3] = {vx[h], vy[h], vz[h]};
+                const bool wzo = !zper && (zo == 0 || zo == nz - 1);
+                if (probe_xy && !wzo && zo >= g.probe_lo[2] && zo < g.probe_hi[2]) {
+                    const float f = src_factor(a, a.dir[0] * ux[h] + a.dir[1] * uy[h] + a.dir[2] * uz[h]);
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) v[e] += a.phi_dir[e] * f;
+                }
+                const long long gi = gcol + plane * zo;
+                a.lam_out[gi] = lpp[h];
+#pragma unroll
+                for (int e = 0; e < 3; ++e) a.lam_out[(1 + e) * N + gi] = v[e];
+                const int bz = colbox ? box_coord(zo, xs2, g.Fb[2], g.n[2], g.periodic[2]) : -1;
+                if (bz >= 0) {
+                    const long long bl = bx + (long long)g.Fb[0] * (by + (long long)g.Fb[1] * bz);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) a.boxbuf[(3 + c) * g.Fbn + bl] = a.u_cur[c * N + gi];
+                }
+            }
+        }
+    }
+}
+
+}  // namespace lks

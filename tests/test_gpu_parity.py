@@ -176,6 +176,15 @@ def test_d2q9_mixed_variants(fwd, adj, ckpt):
     assert g["stats"]["tile_rows_fwd"] == fwd and g["stats"]["tile_rows_adj"] == adj
 
 
+@pytest.mark.parametrize("fwd,adj", [(128, 32), (32, 160), (160, 128)])
+def test_d3q15_mixed_variants(fwd, adj):
+    # plane-pair and separable kernels mixed between the forward sweep and the adjoint, binomial reverse sweep
+    w = tiny_workload("D3Q15", precision="fp32", tile_rows=fwd, tile_rows_adj=adj, shape=(44, 21, 19), ckpt="revolve",
+                      ckpt_slots=3, seg_len=4, Nt=23)
+    g, _ = check(w, 1e-5, 1e-4, 1e-3)
+    assert g["stats"]["tile_rows_fwd"] == fwd and g["stats"]["tile_rows_adj"] == adj
+
+
 def test_3d_128x64x64_full_grid_revolve_fp32():
     # the 128x64x64 D3Q15 workload at its full grid, 12 steps, binomial checkpoints (16 slots, short segments)
     w = workload("d3q15_128x64x64_fp32", Nt=12, K=4, R_t=3.0, amp=16.0 * 12 / 2000, seg_len=2,
@@ -194,21 +203,29 @@ def test_3d_256x128x128_full_grid_budget_fp32():
 @pytest.mark.parametrize("rows,prec,kernel", [(1, "fp64", "linear"), (8, "fp64", "linear"), (16, "fp64", "cosine"),
                                               (8, "fp32", "linear"), (16, "fp32", "linear"), (8, "fp32", "cosine"),
                                               (32, "fp64", "linear"), (64, "fp64", "cosine"), (96, "fp64", "linear"),
-                                              (32, "fp32", "linear"), (64, "fp32", "linear"), (96, "fp32", "cosine")])
-def test_d3q15_kernel_variants(rows, prec, kernel):
+                                              (32, "fp32", "linear"), (64, "fp32", "linear"), (96, "fp32", "cosine"),
+                                              (128, "fp32", "linear"), (160, "fp32", "cosine")])
+@pytest.mark.parametrize("nx", [41, 44])
+def test_d3q15_kernel_variants(rows, prec, kernel, nx):
     # every D3Q15 step-kernel family and planes-per-block choice, on a grid with ragged x, y and z tails
-    # (32, 64: the separable kernels with 16 or 32 planes per block; 96: the separable forward on 32 x 16 columns,
-    # paired with the 8-plane adjoint)
+    # (32, 64: the separable kernels with 16 or 32 planes per block; 96: the separable forward on 32 x 16 columns;
+    # 128, 160: the plane-pair forward and adjoint with 16 or 32 planes per block; the forward-only variant 96 runs
+    # with the 8-plane adjoint).  n_x = 44 moves the plane-pair kernels' raw rows in 16-byte chunks, n_x = 41 element
+    # by element.
+    if nx == 44 and rows < 128:
+        pytest.skip("the x extent changes the copy path of the plane-pair kernels only")
     tol = (1e-10, 1e-10, 1e-10) if prec == "fp64" else (1e-5, 1e-4, 1e-3)
-    w = tiny_workload("D3Q15", precision=prec, tile_rows=rows, kernel=kernel, shape=(41, 21, 19), ckpt="sqrt")
+    w = tiny_workload("D3Q15", precision=prec, tile_rows=rows, kernel=kernel, shape=(nx, 21, 19), ckpt="sqrt")
     g, _ = check(w, *tol)
     assert g["stats"]["tile_rows_fwd"] == rows and g["stats"]["tile_rows_adj"] == (8 if rows == 96 else rows)
 
 
-@pytest.mark.parametrize("rows", [32, 64, 96])
-def test_d3q15_separable_forward_thin_grid(rows):
+@pytest.mark.parametrize("rows,prec,nx", [(32, "fp64", 30), (64, "fp64", 30), (96, "fp64", 30), (128, "fp32", 30),
+                                          (160, "fp32", 32)])
+def test_d3q15_separable_forward_thin_grid(rows, prec, nx):
     # fewer z planes than one block holds (the periodic wrap of the plane ring runs several times), x and y
     # extents below one tile; forward and adjoint
-    w = tiny_workload("D3Q15", precision="fp64", tile_rows=rows, shape=(30, 13, 7), design=(6, 6, 4), ckpt="full",
+    tol = (1e-10, 1e-10, 1e-10) if prec == "fp64" else (1e-5, 1e-4, 1e-3)
+    w = tiny_workload("D3Q15", precision=prec, tile_rows=rows, shape=(nx, 13, 7), design=(6, 6, 4), ckpt="full",
                       probe_lo=(20, 3, 2), probe_hi=(26, 9, 5), Nt=16)
-    check(w, 1e-10, 1e-10, 1e-10)
+    check(w, *tol)
