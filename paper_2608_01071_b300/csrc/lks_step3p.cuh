@@ -522,59 +522,68 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
 
     // staged elements of this thread (halo-2 region): wall and footprint coordinates, and whether the element is one
     // of the block's own columns (whose lambda_u footprint records this block writes)
-    int ebx[R::PERT], eby[R::PERT];
+    int esi[R::PERT], ebl[R::PERT];  // staging index; footprint-box offset in the x-y plane (-1: off the box)
     bool ewall[R::PERT], einner[R::PERT];
 #pragma unroll
     for (int q = 0; q < R::PERT; ++q) {
         const int e = tid + q * R::NT;
         const int i = e % R::SX, jr = e / R::SX;
         const int ex = wrap(x0 - 2 + i, nx), ey = wrap(y0 - 2 + jr, ny);
-        ebx[q] = box_coord(ex, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
-        eby[q] = box_coord(ey, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
+        const int ebx = box_coord(ex, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
+        const int eby = box_coord(ey, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
+        esi[q] = (i + 2) + R::RX * jr;
+        ebl[q] = (e < R::NS && ebx >= 0 && eby >= 0) ? ebx + g.Fb[0] * eby : -1;
         ewall[q] = (!g.periodic[0] && (ex == 0 || ex == nx - 1)) || (!g.periodic[1] && (ey == 0 || ey == ny - 1));
         einner[q] = e < R::NS && i >= 2 && i < R::TX + 2 && jr >= 2 && jr < R::TY + 2 && x0 - 2 + i < nx &&
-                    y0 - 2 + jr < ny && ebx[q] >= 0 && eby[q] >= 0;
+                    y0 - 2 + jr < ny && ebl[q] >= 0;
     }
-    // transform raw pair jj (staging slot jj % 2) into staged slot jj % 2; lambda_u records of own footprint nodes
-    auto transform = [&](int jj) {
+    const long long fbxy = (long long)g.Fb[0] * g.Fb[1];
+    // 1 / (1 + kappa) of this thread's staged elements for the two planes of raw pair jj (1 off the footprint box,
+    // 0 on walls), read one iteration ahead of the transform
+    auto load_fac = [&](int jj, float (&fc)[R::PERT][2]) {
+        const int q0 = z0 - 2 + 2 * jj;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int kz = wrap(q0 + h, nz);
+            const int bz = box_coord(kz, xs2, g.Fb[2], g.n[2], g.periodic[2]);
+            const bool wz = !zper && (kz == 0 || kz == nz - 1);
+            const float* fz = a.fac + fbxy * bz;
+#pragma unroll
+            for (int q = 0; q < R::PERT; ++q) {
+                fc[q][h] = (ewall[q] || wz) ? 0.f : 1.f;
+                if (!(ewall[q] || wz) && ebl[q] >= 0 && bz >= 0) fc[q][h] = fz[ebl[q]];
+            }
+        }
+    };
+    // transform raw pair jj (staging slot jj % 2) into staged slot jj % 2 with the factors fc; lambda_u records of the
+    // own footprint nodes
+    auto transform = [&](int jj, const float (&fc)[R::PERT][2]) {
         const float* s0 = stg + (jj & 1) * 2 * 4 * R::RS;
         const float* s1 = s0 + 4 * R::RS;
         float2* t = tl + (jj & 1) * 4 * R::NS;
         const int q0 = z0 - 2 + 2 * jj;
-        int kz[2], bz[2];
-        bool wz[2], own[2];
+        long long bzo[2];  // box offset of the plane, or -1 when no record is written for it
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            kz[h] = wrap(q0 + h, nz);
-            bz[h] = box_coord(kz[h], xs2, g.Fb[2], g.n[2], g.periodic[2]);
-            wz[h] = !zper && (kz[h] == 0 || kz[h] == nz - 1);
-            own[h] = q0 + h >= z0 && q0 + h < z0 + ZB && q0 + h < nz;
+            const int kz = wrap(q0 + h, nz);
+            const int bz = box_coord(kz, xs2, g.Fb[2], g.n[2], g.periodic[2]);
+            const bool own = q0 + h >= z0 && q0 + h < z0 + ZB && q0 + h < nz;
+            bzo[h] = (own && bz >= 0) ? fbxy * bz : -1;
         }
 #pragma unroll
         for (int q = 0; q < R::PERT; ++q) {
             const int e = tid + q * R::NT;
             if (e >= R::NS) continue;
-            const int si = (e % R::SX + 2) + R::RX * (e / R::SX);
-            float fac[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                fac[h] = (ewall[q] || wz[h]) ? 0.f : 1.f;
-                if (fac[h] != 0.f && ebx[q] >= 0 && eby[q] >= 0 && bz[h] >= 0)
-                    fac[h] = a.fac[ebx[q] + (long long)g.Fb[0] * (eby[q] + (long long)g.Fb[1] * bz[h])];
-            }
+            const int si = esi[q];
             t[e] = f2(s0[si] * (1.f / 3.f), s1[si] * (1.f / 3.f));
 #pragma unroll
             for (int c = 1; c < 4; ++c) {
                 const float l0 = s0[c * R::RS + si], l1 = s1[c * R::RS + si];
-                t[c * R::NS + e] = f2(l0 * fac[0], l1 * fac[1]);
+                t[c * R::NS + e] = f2(l0 * fc[q][0], l1 * fc[q][1]);
                 if (einner[q]) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        if (own[h] && bz[h] >= 0) {
-                            const long long bl = ebx[q] + (long long)g.Fb[0] * (eby[q] + (long long)g.Fb[1] * bz[h]);
-                            a.boxbuf[(c - 1) * g.Fbn + bl] = (ewall[q] || wz[h]) ? 0.f : (h == 0 ? l0 : l1);
-                        }
-                    }
+                    // records of lambda_u on the box (0 on walls: the factor is 0 there)
+                    if (bzo[0] >= 0) a.boxbuf[(c - 1) * g.Fbn + bzo[0] + ebl[q]] = fc[q][0] == 0.f ? 0.f : l0;
+                    if (bzo[1] >= 0) a.boxbuf[(c - 1) * g.Fbn + bzo[1] + ebl[q]] = fc[q][1] == 0.f ? 0.f : l1;
                 }
             }
         }
@@ -604,11 +613,14 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
     const float2 cA = f2s((float)g.A), cm3 = f2s(-3.f);
 
     pdl_wait_then_release();
+    float fcur[R::PERT][2], fnext[R::PERT][2];
     issue_pair(0);
+    load_fac(0, fcur);
     cp_async_wait<0>();
     __syncthreads();
-    transform(0);
+    transform(0, fcur);
     issue_pair(1);
+    load_fac(1, fnext);
 
     // partial moments of plane k+1 (in(k+1) + L(k)) and the distinct emission terms of plane k+1 to plane k+2, per
     // field node (the ring node needs the M2 components only); z-neighbour M2 (xz, yz, zz) of the plane below the
@@ -625,10 +637,37 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
 
 #pragma unroll 1
     for (int j = 0; j < NJ; ++j) {
+        // u_{n-1} of this iteration's output pair (planes z0 - 5 + 2j, + 1), read ahead of the moments
+        const int o0 = z0 - 5 + 2 * j;
+        bool ok[2];
+        float2 u[3] = {f2s(0.f), f2s(0.f), f2s(0.f)};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) ok[h] = j >= 2 && col && o0 + h >= z0 && o0 + h < z0 + ZB && o0 + h < nz;
+        {
+            const float* up = a.u_prev + gcol + plane * o0;
+            if (ok[0]) {
+                u[0].x = up[0];
+                u[1].x = up[N];
+                u[2].x = up[2 * N];
+            }
+            if (ok[1]) {
+                u[0].y = up[plane];
+                u[1].y = up[N + plane];
+                u[2].y = up[2 * N + plane];
+            }
+        }
         cp_async_wait<0>();  // raw pair j + 1 (this thread's copies)
         __syncthreads();
-        if (j + 2 < NRP) issue_pair(j + 2);
-        if (j + 1 < NRP) transform(j + 1);
+#pragma unroll
+        for (int q = 0; q < R::PERT; ++q) {
+            fcur[q][0] = fnext[q][0];
+            fcur[q][1] = fnext[q][1];
+        }
+        if (j + 2 < NRP) {
+            issue_pair(j + 2);
+            load_fac(j + 2, fnext);
+        }
+        if (j + 1 < NRP) transform(j + 1, fcur);
         if (j < NRP) {
             // (B) moments of planes k-1, k from raw pair j = (k, k+1), k = z0 - 2 + 2j
             const float2* tP = tl + (j & 1) * 4 * R::NS;
@@ -739,8 +778,7 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
         }
         __syncthreads();
         if (j >= 2) {
-            // (O) lambda_{n-1} of the pair C_{j-1} = planes (o0, o1) at the own column
-            const int o0 = z0 - 5 + 2 * j;
+            // (O) lambda_{n-1} of the pair C_{j-1} = planes (o0, o0 + 1) at the own column
             const float2* ms = mom + ((j - 1) & 1) * R::SLOT;  // C_{j-1}
             const float2* mn = mom + (j & 1) * R::SLOT;        // C_j (its first plane is above the pair)
             const int m = mrow[0];
@@ -764,24 +802,6 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
                                            f2sub(ms[R::NM + m - R::MX], ms[R::NM + m + R::MX])), zyz);
             const float2 dAz = f2add(f2add(f2sub(ms[3 * R::NM + m - 1], ms[3 * R::NM + m + 1]),
                                            f2sub(ms[4 * R::NM + m - R::MX], ms[4 * R::NM + m + R::MX])), zzz);
-            bool ok[2];
-            float2 u[3] = {f2s(0.f), f2s(0.f), f2s(0.f)};
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int zo = o0 + h;
-                ok[h] = col && zo >= z0 && zo < z0 + ZB && zo < nz;
-            }
-            const float* up = a.u_prev + gcol + plane * o0;
-            if (ok[0]) {
-                u[0].x = up[0];
-                u[1].x = up[N];
-                u[2].x = up[2 * N];
-            }
-            if (ok[1]) {
-                u[0].y = up[plane];
-                u[1].y = up[N + plane];
-                u[2].y = up[2 * N + plane];
-            }
             // lambda_u = 3 M1 - 3 u M0 + 9 M2 u + A dA
             const float2 m0u = f2mul(cm3, M0);
             float2 v0 = f2fma(c3, M1x, f2fma(m0u, u[0], f2mul(cA, dAx)));
