@@ -89,6 +89,9 @@ struct Engine3D : EngineCommon<T, 3, HW> {
         auto okf = [](int r) { return r == 1 || r == 8 || r == 16 || r == 32 || r == 64 || r == 96 || (kPair && (r == 128 || r == 160)); };
         auto oka = [](int r) { return r == 1 || r == 8 || r == 16 || r == 32 || r == 64 || (kPair && (r == 128 || r == 160)); };
         if (!okf(rf) || !oka(ra)) return false;
+        // the plane-pair kernels index in 32 bits: every field offset c N + i and box offset c Fbn + b must fit
+        const bool small = 4 * g.N < (1LL << 31) && 6 * g.Fbn < (1LL << 31);
+        if (!small && (rf >= 128 || ra >= 128)) return false;
         this->rows_f = rf;
         this->rows_a = ra;
         geom(rf, g, this->fthreads, this->ftile, this->fgrid);

@@ -93,7 +93,7 @@ struct ColumnMapHat {
     }
     __device__ __forceinline__ float kxy(const Geom& g, const float* __restrict__ kref, int jz) const {
         if (jz < 0 || jz >= g.nde[2]) return 0.f;
-        const float* kp = kref + (long long)g.nde[0] * g.nde[1] * jz;
+        const float* kp = kref + g.nde[0] * g.nde[1] * jz;
         float s = wxy[0] * kp[off[0]];
 #pragma unroll
         for (int t = 1; t < 4; ++t) s += wxy[t] * kp[off[t]];
@@ -142,15 +142,15 @@ __global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<flo
     float2* fZ0 = fS0 + R::NT;      // [NT]: sigma + T_zz of the own column
 
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const long long N = g.N;
-    const long long plane = (long long)nx * ny;
+    const int N = (int)g.N;  // 32-bit indexing: these kernels run only when 4 N < 2^31
+    const int plane = nx * ny;
     const int x0 = blockIdx.x * R::TX, y0 = blockIdx.y * R::TY, z0 = blockIdx.z * ZB;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + R::TX * ty;
     const float A = (float)g.A;
     const Pose& P = *a.pose;
 
     // plane-invariant copy descriptors of this thread's 16-byte chunks
-    long long goff[VEC4 ? R::PERCH : 1];
+    int goff[VEC4 ? R::PERCH : 1];
     int soff[VEC4 ? R::PERCH : 1];
     if (VEC4) {
 #pragma unroll
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<flo
                 const int f = e / (R::RY * R::CPR), rem = e % (R::RY * R::CPR);
                 const int row = rem / R::CPR, cx = rem % R::CPR;
                 const int xw = wrap(x0 - 4 + 4 * cx, nx), yw = wrap(y0 - 2 + row, ny);
-                goff[q] = f * N + (long long)yw * nx + xw;
+                goff[q] = f * N + yw * nx + xw;
                 soff[q] = f * R::RS + row * R::RX + 4 * cx;
             }
         }
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<flo
 #pragma unroll 1
             for (int e = tid; e < R::NEL; e += R::NT) {
                 const int f = e / R::RS, rem = e % R::RS, row = rem / R::RX, col = rem % R::RX;
-                const long long go = f * N + (long long)wrap(y0 - 2 + row, ny) * nx + wrap(x0 - 4 + col, nx);
+                const int go = f * N + wrap(y0 - 2 + row, ny) * nx + wrap(x0 - 4 + col, nx);
                 cp_async<4>(dst + e, src + go);
             }
         }
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<flo
     }
     ColumnMapHat cmap;
     if (HW == 1 && colbox) cmap.init(g, P, bx, by);
-    const long long gcol = xg + (long long)nx * yg;
+    const int gcol = xg + nx * yg;
 
     // Brinkman, walls and stores of one completed output plane
     auto emit = [&](int zo, float mp, float mx, float my, float mz) {
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<flo
 #pragma unroll
             for (int c = 0; c < 3; ++c) un[c] = (float)g.wall_u[ax][sd][c];
         }
-        const long long gi = gcol + plane * zo;
+        const int gi = gcol + plane * zo;
         a.out_p[gi] = pn;
 #pragma unroll
         for (int c = 0; c < 3; ++c) a.out_u[c * N + gi] = un[c];
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<flo
                     int xyz[3] = {xg, yg, zo};
                     float uw[3];
                     if (!in_probe<3>(g, xyz) || wall_node<float, 3>(g, xyz, uw)) continue;
-                    const long long gi = xg + (long long)nx * yg + plane * zo;
+                    const int gi = xg + nx * yg + plane * zo;
                     const float nu = a.dir[0] * a.out_u[gi] + a.dir[1] * a.out_u[N + gi] + a.dir[2] * a.out_u[2 * N + gi];
                     jacc += nu;
                     qacc += nu * nu;
@@ -472,8 +472,8 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
     float2* mom = tl + 2 * 4 * R::NS;                                 // [2 slots][SLOT]
 
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const long long N = g.N;
-    const long long plane = (long long)nx * ny;
+    const int N = (int)g.N;  // 32-bit indexing: these kernels run only when 4 N < 2^31
+    const int plane = nx * ny;
     const int x0 = blockIdx.x * R::TX, y0 = blockIdx.y * R::TY, z0 = blockIdx.z * ZB;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + R::TX * ty;
     const Pose& P = *a.pose;
@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
     const bool zper = g.periodic[2] != 0;
 
     // raw copies: plane-invariant descriptors of this thread's 16-byte chunks
-    long long goff[VEC4 ? R::PERCH : 1];
+    int goff[VEC4 ? R::PERCH : 1];
     int soff[VEC4 ? R::PERCH : 1];
     if (VEC4) {
 #pragma unroll
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
                 const int f = e / (R::RY * R::CPR), rem = e % (R::RY * R::CPR);
                 const int row = rem / R::CPR, cx = rem % R::CPR;
                 const int xw = wrap(x0 - 4 + 4 * cx, nx), yw = wrap(y0 - 2 + row, ny);
-                goff[q] = f * N + (long long)yw * nx + xw;
+                goff[q] = f * N + yw * nx + xw;
                 soff[q] = f * R::RS + row * R::RX + 4 * cx;
             }
         }
@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
 #pragma unroll 1
             for (int e = tid; e < R::NEL; e += R::NT) {
                 const int f = e / R::RS, rem = e % R::RS, row = rem / R::RX, col = rem % R::RX;
-                const long long go = f * N + (long long)wrap(y0 - 2 + row, ny) * nx + wrap(x0 - 4 + col, nx);
+                const int go = f * N + wrap(y0 - 2 + row, ny) * nx + wrap(x0 - 4 + col, nx);
                 cp_async<4>(dst + e, src + go);
             }
         }
@@ -537,7 +537,8 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
         einner[q] = e < R::NS && i >= 2 && i < R::TX + 2 && jr >= 2 && jr < R::TY + 2 && x0 - 2 + i < nx &&
                     y0 - 2 + jr < ny && ebl[q] >= 0;
     }
-    const long long fbxy = (long long)g.Fb[0] * g.Fb[1];
+    const int fbxy = g.Fb[0] * g.Fb[1];
+    const int Fbn = (int)g.Fbn;
     // 1 / (1 + kappa) of this thread's staged elements for the two planes of raw pair jj (1 off the footprint box,
     // 0 on walls), read one iteration ahead of the transform
     auto load_fac = [&](int jj, float (&fc)[R::PERT][2]) {
@@ -562,7 +563,7 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
         const float* s1 = s0 + 4 * R::RS;
         float2* t = tl + (jj & 1) * 4 * R::NS;
         const int q0 = z0 - 2 + 2 * jj;
-        long long bzo[2];  // box offset of the plane, or -1 when no record is written for it
+        int bzo[2];  // box offset of the plane, or -1 when no record is written for it
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int kz = wrap(q0 + h, nz);
@@ -582,8 +583,8 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
                 t[c * R::NS + e] = f2(l0 * fc[q][0], l1 * fc[q][1]);
                 if (einner[q]) {
                     // records of lambda_u on the box (0 on walls: the factor is 0 there)
-                    if (bzo[0] >= 0) a.boxbuf[(c - 1) * g.Fbn + bzo[0] + ebl[q]] = fc[q][0] == 0.f ? 0.f : l0;
-                    if (bzo[1] >= 0) a.boxbuf[(c - 1) * g.Fbn + bzo[1] + ebl[q]] = fc[q][1] == 0.f ? 0.f : l1;
+                    if (bzo[0] >= 0) a.boxbuf[(c - 1) * Fbn + bzo[0] + ebl[q]] = fc[q][0] == 0.f ? 0.f : l0;
+                    if (bzo[1] >= 0) a.boxbuf[(c - 1) * Fbn + bzo[1] + ebl[q]] = fc[q][1] == 0.f ? 0.f : l1;
                 }
             }
         }
@@ -603,7 +604,7 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
     }
     const int xg = x0 + tx, yg = y0 + ty;
     const bool col = xg < nx && yg < ny;
-    const long long gcol = xg + (long long)nx * yg;
+    const int gcol = xg + nx * yg;
     const int bx = box_coord(xg, P.xs[0], g.Fb[0], g.n[0], g.periodic[0]);
     const int by = box_coord(yg, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
     const bool colbox = col && bx >= 0 && by >= 0;
@@ -622,17 +623,19 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
     issue_pair(1);
     load_fac(1, fnext);
 
-    // partial moments of plane k+1 (in(k+1) + L(k)) and the distinct emission terms of plane k+1 to plane k+2, per
-    // field node (the ring node needs the M2 components only); z-neighbour M2 (xz, yz, zz) of the plane below the
-    // output pair
-    float cA0[10], cA1[5];
-    float cL0[5], cL1[4];
+    // From the previous pair (planes k-2, k-1): its emissions to the plane above, as pairs of the distinct terms
+    // L0, L1, L2, L3, L0 + zu (own node; the ring node needs L0 .. L3), and the in-plane terms of its second plane
+    // (in0, in1, in2, fx, fy; the ring node fx, fy).  z-neighbour M2 (xz, yz, zz) of the plane below the output pair.
+    float2 pL0[5], pL1[4];
+    float pI0[5], pI1[2];
 #pragma unroll
-    for (int c = 0; c < 10; ++c) cA0[c] = 0.f;
+    for (int c = 0; c < 5; ++c) {
+        pL0[c] = f2s(0.f);
+        pI0[c] = 0.f;
+    }
 #pragma unroll
-    for (int c = 0; c < 5; ++c) cA1[c] = cL0[c] = 0.f;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) cL1[c] = 0.f;
+    for (int c = 0; c < 4; ++c) pL1[c] = f2s(0.f);
+    pI1[0] = pI1[1] = 0.f;
     float zm[3] = {0.f, 0.f, 0.f};
 
 #pragma unroll 1
@@ -721,28 +724,34 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
                     const float2 in0 = f2fma(w0, pc, f2add(fx, fy));
                     const float2 in1 = f2mul(wf, f2add(f2sub(pxp, pxm), f2add(vxp, vxm)));
                     const float2 in2 = f2mul(wf, f2add(f2sub(pyp, pym), f2add(vyp, vym)));
-                    // contributions of the pair's planes: in-plane In, from the plane above Uc, from the plane below Lc
+                    // completed pair (planes k-1, k): M = L(previous pair) + U(this pair) + in-plane terms, where the
+                    // first plane's in-plane terms come from the previous pair and the second's from this one
                     // (components M0, M1x, M1y, M1z, M2xx, M2yy, M2zz, M2xy, M2xz, M2yz)
                     const float2 Uz = f2add(U0, zd), Lz = f2add(L0, zu);
-                    const float2 In[10] = {in0, in1, in2, f2s(0.f), fx, fy, f2s(0.f), f2s(0.f), f2s(0.f), f2s(0.f)};
-                    const float2 Uc[10] = {Uz, U1, U2, Uz, U0, U0, Uz, U3, U1, U2};
-                    // Lc of the previous pair's second plane, from its distinct terms (L0, L1, L2, L3, L0 + zu)
-                    const float Lp[10] = {cL0[4], cL0[1], cL0[2], -cL0[4], cL0[0], cL0[0], cL0[4], cL0[3], -cL0[1], -cL0[2]};
                     float2 Mc[10];
+                    Mc[0] = f2add(pL0[4], Uz);
+                    Mc[1] = f2add(pL0[1], U1);
+                    Mc[2] = f2add(pL0[2], U2);
+                    Mc[3] = f2sub(Uz, pL0[4]);
+                    Mc[4] = f2add(pL0[0], U0);
+                    Mc[5] = f2add(pL0[0], U0);
+                    Mc[6] = f2add(pL0[4], Uz);
+                    Mc[7] = f2add(pL0[3], U3);
+                    Mc[8] = f2sub(U1, pL0[1]);
+                    Mc[9] = f2sub(U2, pL0[2]);
+                    const float2 In[5] = {in0, in1, in2, fx, fy};
+                    const int ic[5] = {0, 1, 2, 4, 5};
 #pragma unroll
-                    for (int c = 0; c < 10; ++c) {
-                        Mc[c].x = cA0[c] + Uc[c].x;
-                        Mc[c].y = (In[c].x + Lp[c]) + Uc[c].y;
+                    for (int t = 0; t < 5; ++t) {
+                        Mc[ic[t]].x += pI0[t];
+                        Mc[ic[t]].y += In[t].x;
+                        pI0[t] = In[t].y;
                     }
-                    // carries: plane k+1 without its emission from the next pair; the distinct L terms of plane k+1
-                    const float Lx[10] = {Lz.x, L1.x, L2.x, -Lz.x, L0.x, L0.x, Lz.x, L3.x, -L1.x, -L2.x};
-#pragma unroll
-                    for (int c = 0; c < 10; ++c) cA0[c] = In[c].y + Lx[c];
-                    cL0[0] = L0.y;
-                    cL0[1] = L1.y;
-                    cL0[2] = L2.y;
-                    cL0[3] = L3.y;
-                    cL0[4] = Lz.y;
+                    pL0[0] = L0;
+                    pL0[1] = L1;
+                    pL0[2] = L2;
+                    pL0[3] = L3;
+                    pL0[4] = Lz;
                     // completed pair: M2 on the halo-1 slot, M0 and M1 of the own column
                     ms[m] = Mc[4];
                     ms[R::NM + m] = Mc[5];
@@ -757,22 +766,24 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
                     mo[3 * R::NT + tid] = Mc[3];
                 } else {
                     // the ring node needs the in-plane M2 components xx, yy, xy, xz, yz only
-                    const float2 In[5] = {fx, fy, f2s(0.f), f2s(0.f), f2s(0.f)};
-                    const float2 Uc[5] = {U0, U0, U3, U1, U2};
-                    const float Lp[5] = {cL1[0], cL1[0], cL1[3], -cL1[1], -cL1[2]};
-                    const float Lx[5] = {L0.x, L0.x, L3.x, -L1.x, -L2.x};
+                    float2 Mc[5];
+                    Mc[0] = f2add(pL1[0], U0);
+                    Mc[1] = f2add(pL1[0], U0);
+                    Mc[2] = f2add(pL1[3], U3);
+                    Mc[3] = f2sub(U1, pL1[1]);
+                    Mc[4] = f2sub(U2, pL1[2]);
+                    Mc[0].x += pI1[0];
+                    Mc[0].y += fx.x;
+                    Mc[1].x += pI1[1];
+                    Mc[1].y += fy.x;
+                    pI1[0] = fx.y;
+                    pI1[1] = fy.y;
+                    pL1[0] = L0;
+                    pL1[1] = L1;
+                    pL1[2] = L2;
+                    pL1[3] = L3;
 #pragma unroll
-                    for (int c = 0; c < 5; ++c) {
-                        float2 Mc;
-                        Mc.x = cA1[c] + Uc[c].x;
-                        Mc.y = (In[c].x + Lp[c]) + Uc[c].y;
-                        cA1[c] = In[c].y + Lx[c];
-                        ms[c * R::NM + m] = Mc;
-                    }
-                    cL1[0] = L0.y;
-                    cL1[1] = L1.y;
-                    cL1[2] = L2.y;
-                    cL1[3] = L3.y;
+                    for (int c = 0; c < 5; ++c) ms[c * R::NM + m] = Mc[c];
                 }
             }
         }
@@ -824,15 +835,15 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
 #pragma unroll
                     for (int e = 0; e < 3; ++e) v[e] += a.phi_dir[e] * f;
                 }
-                const long long gi = gcol + plane * zo;
+                const int gi = gcol + plane * zo;
                 a.lam_out[gi] = lpp[h];
 #pragma unroll
                 for (int e = 0; e < 3; ++e) a.lam_out[(1 + e) * N + gi] = v[e];
                 const int bz = colbox ? box_coord(zo, xs2, g.Fb[2], g.n[2], g.periodic[2]) : -1;
                 if (bz >= 0) {
-                    const long long bl = bx + (long long)g.Fb[0] * (by + (long long)g.Fb[1] * bz);
+                    const int bl = bx + g.Fb[0] * (by + g.Fb[1] * bz);
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) a.boxbuf[(3 + c) * g.Fbn + bl] = a.u_cur[c * N + gi];
+                    for (int c = 0; c < 3; ++c) a.boxbuf[(3 + c) * Fbn + bl] = a.u_cur[c * N + gi];
                 }
             }
         }
