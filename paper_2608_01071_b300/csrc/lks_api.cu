@@ -383,6 +383,7 @@ void autotune_rows(lks_ctx* c) {
     LKS_CUDA(cudaMemsetAsync(c->lam[0], 0, c->state_bytes, s));
     LKS_CUDA(cudaMemsetAsync(c->lam[1], 0, c->state_bytes, s));
     c->eng->init_state(c->g, c->slot[0], s);
+    c->eng->init_state(c->g, c->pp[2], s);
     cudaEvent_t e0, e1;
     LKS_CUDA(cudaEventCreate(&e0));
     LKS_CUDA(cudaEventCreate(&e1));
@@ -406,8 +407,8 @@ void autotune_rows(lks_ctx* c) {
             else if (c->eng->fused_adj2())
                 c->eng->adj2(c->g, c->lam[k & 1], c->lam[(k + 1) & 1], c->slot[0], c->slot[0], c->slot[0], c->d_kref,
                              c->d_pose + 1, c->d_boxbuf, c->d_fac, 1, c->d_boxbuf, c->d_fac, 1, s);
-            else
-                c->eng->adj(c->g, c->lam[k & 1], c->lam[(k + 1) & 1], c->slot[0], c->slot[0], c->d_kref, c->d_pose,
+            else  // u_{n-1} and u_n from different buffers, as in the reverse sweep (the footprint records read u_n)
+                c->eng->adj(c->g, c->lam[k & 1], c->lam[(k + 1) & 1], c->slot[0], c->pp[2], c->d_kref, c->d_pose,
                             c->d_boxbuf, c->d_fac, 1, s);
         }
         LKS_CUDA(cudaEventRecord(e1, s));
@@ -470,7 +471,7 @@ void autotune_rows(lks_ctx* c) {
                 LKS_CUDA(cudaStreamWaitEvent(s2, e0, 0));
             }
             c->eng->fwd(c->g, c->slot[0], c->pp[k & 1], c->d_kref, c->d_pose, nullptr, c->d_flag, jlo, jn, s2);
-            c->eng->adj(c->g, c->lam[k & 1], c->lam[(k + 1) & 1], c->slot[0], c->slot[0], c->d_kref, c->d_pose,
+            c->eng->adj(c->g, c->lam[k & 1], c->lam[(k + 1) & 1], c->slot[0], c->pp[2], c->d_kref, c->d_pose,
                         c->d_boxbuf, c->d_fac, 1, s);
         }
         LKS_CUDA(cudaEventRecord(e2, s2));

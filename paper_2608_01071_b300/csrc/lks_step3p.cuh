@@ -640,14 +640,21 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
 
 #pragma unroll 1
     for (int j = 0; j < NJ; ++j) {
-        // u_{n-1} of this iteration's output pair (planes z0 - 5 + 2j, + 1), read ahead of the moments
+        // u_{n-1} of this iteration's output pair (planes z0 - 5 + 2j, + 1), and u_n there on the footprint box (for
+        // its records), read ahead of the moments
         const int o0 = z0 - 5 + 2 * j;
         bool ok[2];
-        float2 u[3] = {f2s(0.f), f2s(0.f), f2s(0.f)};
+        int bzo[2];
+        float2 u[3] = {f2s(0.f), f2s(0.f), f2s(0.f)}, uc[3] = {f2s(0.f), f2s(0.f), f2s(0.f)};
 #pragma unroll
-        for (int h = 0; h < 2; ++h) ok[h] = j >= 2 && col && o0 + h >= z0 && o0 + h < z0 + ZB && o0 + h < nz;
+        for (int h = 0; h < 2; ++h) {
+            ok[h] = j >= 2 && col && o0 + h >= z0 && o0 + h < z0 + ZB && o0 + h < nz;
+            bzo[h] = (ok[h] && colbox) ? box_coord(o0 + h, xs2, g.Fb[2], g.n[2], g.periodic[2]) : -1;
+        }
         {
-            const float* up = a.u_prev + gcol + plane * o0;
+            const int gi0 = gcol + plane * o0;
+            const float* up = a.u_prev + gi0;
+            const float* uq = a.u_cur + gi0;
             if (ok[0]) {
                 u[0].x = up[0];
                 u[1].x = up[N];
@@ -657,6 +664,16 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
                 u[0].y = up[plane];
                 u[1].y = up[N + plane];
                 u[2].y = up[2 * N + plane];
+            }
+            if (bzo[0] >= 0) {
+                uc[0].x = uq[0];
+                uc[1].x = uq[N];
+                uc[2].x = uq[2 * N];
+            }
+            if (bzo[1] >= 0) {
+                uc[0].y = uq[plane];
+                uc[1].y = uq[N + plane];
+                uc[2].y = uq[2 * N + plane];
             }
         }
         cp_async_wait<0>();  // raw pair j + 1 (this thread's copies)
@@ -824,6 +841,7 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
             const float2 lp = f2mul(c3, M0);
             const float vx[2] = {v0.x, v0.y}, vy[2] = {v1.x, v1.y}, vz[2] = {v2.x, v2.y}, lpp[2] = {lp.x, lp.y};
             const float ux[2] = {u[0].x, u[0].y}, uy[2] = {u[1].x, u[1].y}, uz[2] = {u[2].x, u[2].y};
+            const float cx[2] = {uc[0].x, uc[0].y}, cy[2] = {uc[1].x, uc[1].y}, cz[2] = {uc[2].x, uc[2].y};
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (!ok[h]) continue;
@@ -839,11 +857,11 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
                 a.lam_out[gi] = lpp[h];
 #pragma unroll
                 for (int e = 0; e < 3; ++e) a.lam_out[(1 + e) * N + gi] = v[e];
-                const int bz = colbox ? box_coord(zo, xs2, g.Fb[2], g.n[2], g.periodic[2]) : -1;
-                if (bz >= 0) {
-                    const int bl = bx + g.Fb[0] * (by + g.Fb[1] * bz);
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) a.boxbuf[(3 + c) * Fbn + bl] = a.u_cur[c * N + gi];
+                if (bzo[h] >= 0) {
+                    const int bl = bx + g.Fb[0] * (by + g.Fb[1] * bzo[h]);
+                    a.boxbuf[3 * Fbn + bl] = cx[h];
+                    a.boxbuf[4 * Fbn + bl] = cy[h];
+                    a.boxbuf[5 * Fbn + bl] = cz[h];
                 }
             }
         }
