@@ -28,7 +28,7 @@
 extern "C" {
 #endif
 
-#define LKS_ABI_VERSION 1
+#define LKS_ABI_VERSION 2
 
 typedef enum lks_status {
     LKS_OK = 0,
@@ -95,6 +95,13 @@ enum { LKS_OBJ_FLOW = 0, LKS_OBJ_OAR = 1 };
  *  tile_rows_adj  adjoint step-kernel variant when tile_rows != 0 (same codes); 0 = tile_rows.
  *  tile_rows_rec  forward variant of the recomputation in lks_adjoint when tile_rows != 0; 0 = tile_rows.
  *                 tile_rows_adj and tile_rows_rec must be 0 when tile_rows = 0 (all three autotuned).
+ *  K_w, R_w       rotating body (Sec. 2.3-2.5): K_w >= 2 angle knots (radians, lks_set_angle_knots; knot k at step
+ *                 k Nt/(K_w-1)) filtered with radius R_w steps (Eq. psi_filtered) and interpolated to theta_n, with
+ *                 omega_n = theta_n - theta_{n-1}; theta turns the x-y components of the body about an axis parallel
+ *                 to z through x^G (Eqs. rigid_body_position, rigid_body_velocity).  K_w = 0: translation only.  With a
+ *                 rotating body the forward sweep runs step-kernel variant 1 (tile_rows 0 or 1), the footprint box
+ *                 on x and y covers the design grid at any angle (it must fit in one period of a periodic axis), and
+ *                 the objective must be LKS_OBJ_FLOW.
  */
 typedef struct lks_params {
     uint32_t size;
@@ -133,6 +140,9 @@ typedef struct lks_params {
     int32_t reserved_obj;
     double w_D;
     double drag_span;
+    int32_t K_w;
+    int32_t reserved_rot;
+    double R_w;
 } lks_params;
 
 typedef struct lks_ctx lks_ctx;
@@ -182,12 +192,22 @@ int lks_forward(lks_ctx* ctx, const double* gamma, const double* pos_knots, doub
 int lks_forward_dev(lks_ctx* ctx, const double* d_gamma, const double* d_pos_knots, double* d_J, void* stream);
 
 /*
+ * Status of the last forward: waits for it to finish, then LKS_EUNSTABLE if it saw a non-finite velocity or |u| > u_crit
+ * (the check of lks_params.u_crit), LKS_OK otherwise; LKS_ESTATE before the first forward.  The _dev forward and
+ * adjoint calls do not wait for the forward, so this is where their callers learn of an unstable sweep.
+ */
+int lks_get_status(lks_ctx* ctx);
+
+/*
  * Adjoint solve (Algorithm 1, reverse loop; shape sensitivity Eq. dJdgamma, motion sensitivity Eq. dJdchi,
  * as the exact discrete adjoint of the forward), then the chain rules through the filters:
  *   dJ_dgamma[nd]     dJ/dgamma on the inner design grid;
  *   dJ_dpos[K*d]      dJ/dpos_knots.
  * Needs a preceding lks_forward on the same context (LKS_ESTATE otherwise).  With LKS_CKPT_REVOLVE the
  * reverse sweep reuses the forward's checkpoint slots, so every lks_adjoint needs its own lks_forward.
+ * If that forward was unstable, lks_adjoint returns LKS_EUNSTABLE with its outputs untouched, and lks_adjoint_dev,
+ * which does not wait for the forward (it is enqueued behind it on the stream), fills both outputs with NaN;
+ * lks_get_status reports the instability.
  */
 int lks_adjoint(lks_ctx* ctx, double* dJ_dgamma, double* dJ_dpos);
 int lks_adjoint_dev(lks_ctx* ctx, double* d_dJ_dgamma, double* d_dJ_dpos, void* stream);
@@ -256,6 +276,25 @@ int lks_get_state(lks_ctx* ctx, double* p, double* u);
  * p = u = NULL restores the default (p = 1/3, u = 0, wall nodes at their wall velocity).  Discards captured
  * graphs; the next lks_adjoint needs a new lks_forward.  Synchronous. */
 int lks_set_initial_state(lks_ctx* ctx, const double* p, const double* u);
+
+/* Terminal adjoint state of every following lks_adjoint: (lam_p, lam_u), host FP64 in the layout of lks_get_state
+ * (lam_p[N], lam_u[d*N]), is added to dJ/d(p_Nt, u_Nt) before the reverse sweep.  This is the adjoint half of the
+ * periodic approximation (Sec. 3.3): the adjoint state at n = 0 of one optimisation iteration (lks_get_adjoint_initial)
+ * ends the reverse sweep of the next, as the final flow state starts its forward sweep (lks_set_initial_state).
+ * lam_p = lam_u = NULL removes it.  Discards captured graphs; the next lks_adjoint needs a new lks_forward.
+ * Synchronous. */
+int lks_set_adjoint_terminal(lks_ctx* ctx, const double* lam_p, const double* lam_u);
+
+/* Adjoint state lambda_0 = dJ/d(p_0, u_0) of the last adjoint (the gradient of J with respect to the initial state),
+ * as FP64 in the layout of lks_get_state.  Waits for the device.  LKS_ESTATE before the first adjoint. */
+int lks_get_adjoint_initial(lks_ctx* ctx, double* lam_p, double* lam_u);
+
+/* Rotating body: the K_w angle knots (radians, host) of every following forward (all zero until set); LKS_EINVAL when
+ * the context has K_w = 0.  Synchronous.  dJ/d(angle knots) of the last adjoint, K_w values (zeros with
+ * LKS_MODE_SHAPE), and the per-step dJ/dtheta_n, dJ/domega_n ((Nt+1) values each).  Synchronous. */
+int lks_set_angle_knots(lks_ctx* ctx, const double* aknots);
+int lks_get_angle_gradient(lks_ctx* ctx, double* dJ_daknots);
+int lks_get_step_angle_sensitivities(lks_ctx* ctx, double* dJ_dtheta, double* dJ_domega);
 
 /* Per-step motion sensitivities of the last adjoint, dJ/ds_n and dJ/du^G_n, each (Nt+1) x d. Synchronous. */
 int lks_get_step_sensitivities(lks_ctx* ctx, double* dJ_ds, double* dJ_duG);

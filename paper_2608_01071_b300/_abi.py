@@ -57,6 +57,9 @@ class lks_params(C.Structure):
         ("reserved_obj", C.c_int32),
         ("w_D", C.c_double),
         ("drag_span", C.c_double),
+        ("K_w", C.c_int32),
+        ("reserved_rot", C.c_int32),
+        ("R_w", C.c_double),
     ]
 
 
@@ -104,6 +107,8 @@ PROTOTYPES = {
     "lks_interp_positions_T_dev": (C.c_int, [_P, _P, _P, _P, _P]),
     "lks_get_state": (C.c_int, [_P, _D, _D]),
     "lks_set_initial_state": (C.c_int, [_P, _D, _D]),
+    "lks_set_adjoint_terminal": (C.c_int, [_P, _D, _D]),
+    "lks_get_adjoint_initial": (C.c_int, [_P, _D, _D]),
     "lks_density_filter": (C.c_int, [_P, _D, _D]),
     "lks_density_filter_T": (C.c_int, [_P, _D, _D]),
     "lks_projection": (C.c_int, [C.c_int64, C.c_double, C.c_double, _D, _D, _D]),
@@ -114,6 +119,10 @@ PROTOTYPES = {
     "lks_get_step_sensitivities": (C.c_int, [_P, _D, _D]),
     "lks_get_objective_terms": (C.c_int, [_P, _D, _D]),
     "lks_get_stats": (C.c_int, [_P, C.POINTER(lks_stats)]),
+    "lks_get_status": (C.c_int, [_P]),
+    "lks_set_angle_knots": (C.c_int, [_P, _D]),
+    "lks_get_angle_gradient": (C.c_int, [_P, _D]),
+    "lks_get_step_angle_sensitivities": (C.c_int, [_P, _D, _D]),
     "lks_set_timing": (C.c_int, [_P, C.c_int]),
     "lks_set_graphs": (C.c_int, [_P, C.c_int]),
     "lks_batch_create": (C.c_int, [C.c_int, C.POINTER(lks_params), C.POINTER(_P)]),

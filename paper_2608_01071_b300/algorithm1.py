@@ -4,8 +4,9 @@
 - Stopping rule: after the forward solve of iteration k+1, stop this beta when |J^{k+1} - J^k| / |J^k| <= tol and
   every constraint G_j <= 0 holds (Sec. 3.2). As in Algorithm 1, the check comes before the adjoint solve.
 - Volume constraints G1 (solid) and G2 (fluid) of Eqs. constraint1-2, on the design variable gamma.
-- Periodic approximation of the state (Sec. 3.3): the final state of one forward solve starts the next
-  (``SolverEvaluator(periodic=True)``, through lks_get_state / lks_set_initial_state).
+- Periodic approximation (Sec. 3.3): the final state of one forward solve starts the next, and the adjoint state at
+  n = 0 of one reverse sweep ends the next (``SolverEvaluator(periodic=True)``, through lks_get_state /
+  lks_set_initial_state and lks_get_adjoint_initial / lks_set_adjoint_terminal).
 
 The paper updates the design with MMA, which is not part of this library. This driver takes normalised
 projected-gradient steps on an augmented Lagrangian of the inequality constraints instead.
@@ -123,14 +124,16 @@ def run(evaluator, gamma, knots, s: Settings = Settings(), callback=None):
 
 class SolverEvaluator:
     """Forward and adjoint solves through the CUDA library for ``run``: one context per beta, created on first use.
-    With periodic=True the final state of each forward solve is the initial state of the next (Sec. 3.3), across
-    betas too."""
+    With periodic=True (Sec. 3.3) the final state of each forward solve is the initial state of the next, and the
+    adjoint state at n = 0 of each reverse sweep is added to the terminal adjoint state of the next, across betas
+    too."""
 
     def __init__(self, workload: dict, periodic: bool = False):
         self.w = workload
         self.periodic = periodic
         self.solvers = {}
         self.state = None
+        self.lam0 = None
         self.current = None
 
     def objective(self, beta, gamma, knots):
@@ -141,6 +144,8 @@ class SolverEvaluator:
         s = self.solvers[beta]
         if self.periodic and self.state is not None:
             s.set_initial_state(*self.state)
+        if self.periodic and self.lam0 is not None:
+            s.set_adjoint_terminal(*self.lam0)
         J = s.forward(gamma, knots)
         if self.periodic:
             self.state = s.state()
@@ -148,7 +153,10 @@ class SolverEvaluator:
         return J
 
     def gradient(self):
-        return self.current.adjoint()
+        g = self.current.adjoint()
+        if self.periodic:
+            self.lam0 = self.current.adjoint_initial()
+        return g
 
     def close(self):
         for s in self.solvers.values():

@@ -72,6 +72,8 @@ def params_from_workload(w: dict) -> _abi.lks_params:
     p.objective = _OBJ[objective]
     p.w_D = w.get("w_D", 0.0)
     p.drag_span = w.get("drag_span", 1.0)
+    p.K_w = w.get("K_w", 0)
+    p.R_w = w.get("R_w", 1.0)
     return p
 
 
@@ -126,7 +128,26 @@ class Solver:
             raise LKSError(rc, self.lib.lks_last_error_string(self.h).decode())
 
     # host-pointer calls -------------------------------------------------------------------------
-    def forward(self, gamma, knots) -> float:
+    def set_angle_knots(self, aknots):
+        """Angle knots (radians, K_w values) of the rotating body for the following forwards."""
+        a = np.ascontiguousarray(aknots, dtype=np.float64)
+        self._check(self.lib.lks_set_angle_knots(self.h, _dptr(a)))
+
+    def angle_gradient(self):
+        """dJ/d(angle knots) of the last adjoint."""
+        out = np.zeros(self.params.K_w)
+        self._check(self.lib.lks_get_angle_gradient(self.h, _dptr(out)))
+        return out
+
+    def step_angle_sensitivities(self):
+        gth = np.zeros(self.Nt + 1)
+        gom = np.zeros(self.Nt + 1)
+        self._check(self.lib.lks_get_step_angle_sensitivities(self.h, _dptr(gth), _dptr(gom)))
+        return gth, gom
+
+    def forward(self, gamma, knots, aknots=None) -> float:
+        if aknots is not None:
+            self.set_angle_knots(aknots)
         g = _flat(gamma)
         k = np.ascontiguousarray(knots, dtype=np.float64)
         J = C.c_double()
@@ -157,6 +178,26 @@ class Solver:
         uf = np.concatenate([np.ascontiguousarray(np.asarray(u[a], dtype=np.float64).T).ravel() for a in range(self.d)])
         self._check(self.lib.lks_set_initial_state(self.h, _dptr(pf), _dptr(uf)))
 
+    def set_adjoint_terminal(self, lam_p=None, lam_u=None):
+        """Terminal adjoint state added before the following reverse sweeps (arrays as returned by
+        adjoint_initial()); None removes it."""
+        if lam_p is None and lam_u is None:
+            self._check(self.lib.lks_set_adjoint_terminal(self.h, None, None))
+            return
+        pf = np.ascontiguousarray(np.asarray(lam_p, dtype=np.float64).T).ravel()
+        uf = np.concatenate([np.ascontiguousarray(np.asarray(lam_u[a], dtype=np.float64).T).ravel() for a in range(self.d)])
+        self._check(self.lib.lks_set_adjoint_terminal(self.h, _dptr(pf), _dptr(uf)))
+
+    def adjoint_initial(self):
+        """lambda_0 = dJ/d(p_0, u_0) of the last adjoint, as (lam_p, lam_u) in the layout of state()."""
+        N = int(np.prod(self.shape))
+        p = np.zeros(N)
+        u = np.zeros(self.d * N)
+        self._check(self.lib.lks_get_adjoint_initial(self.h, _dptr(p), _dptr(u)))
+        p = p.reshape(self.shape[::-1]).T.copy()
+        u = np.stack([u[a * N:(a + 1) * N].reshape(self.shape[::-1]).T for a in range(self.d)])
+        return p, u
+
     def step_sensitivities(self):
         gs = np.zeros((self.Nt + 1, self.d))
         gu = np.zeros((self.Nt + 1, self.d))
@@ -168,6 +209,10 @@ class Solver:
         E, V = C.c_double(), C.c_double()
         self._check(self.lib.lks_get_objective_terms(self.h, C.byref(E), C.byref(V)))
         return E.value, V.value
+
+    def status(self):
+        """Waits for the last forward; raises LKSError (LKS_EUNSTABLE) if it was unstable."""
+        self._check(self.lib.lks_get_status(self.h))
 
     def set_timing(self, on: bool):
         self._check(self.lib.lks_set_timing(self.h, 1 if on else 0))

@@ -19,6 +19,8 @@
 #include <map>
 #include <tuple>
 
+#include <sys/stat.h>
+
 using namespace lks;
 
 namespace {
@@ -57,6 +59,9 @@ struct lks_ctx {
     Geom g;
     DesignGeom dg;
     MotionGeom mg;
+    MotionGeom mgw;       // rotating body: the angle knots' filter and interpolation (d = 1, radius R_w)
+    bool rot = false;     // the body rotates (K_w > 0)
+    double rb = 0.0;      // half extent of the rotating body's footprint box on x and y
     int D = 2, hw = 1, cosine = 0;
     double o0[3] = {0, 0, 0};
     size_t tsize = 8;
@@ -81,6 +86,11 @@ struct lks_ctx {
     double *d_knots = nullptr, *d_filt = nullptr, *d_s = nullptr, *d_uG = nullptr, *d_ktmp = nullptr;
     double *d_out_g = nullptr, *d_out_k = nullptr;  // host-pointer adjoint staging
     double* d_tnorm = nullptr;                        // temporal-filter row sums
+    // rotating body: angle knots, filtered knots and filter row sums, theta_n, omega_n, their sensitivities, the
+    // angle-knot gradient, and the step's kappa, u^S on the footprint box
+    double *d_aknots = nullptr, *d_afilt = nullptr, *d_anorm = nullptr, *d_theta = nullptr, *d_omega = nullptr,
+           *d_gth = nullptr, *d_gom = nullptr, *d_atmp = nullptr, *d_out_a = nullptr;
+    void* d_rotmap = nullptr;
     Pose* d_pose = nullptr;
     double *d_gs = nullptr, *d_guG = nullptr, *d_dkref = nullptr, *d_jslot = nullptr, *d_jstep = nullptr,
            *d_J = nullptr;
@@ -95,6 +105,9 @@ struct lks_ctx {
     bool throughput = false;    // instance of a batch: tune for throughput (see create_ctx)
     void* d_init = nullptr;     // caller's initial state (lks_set_initial_state), in the state layout
     bool custom_init = false;
+    void* d_lterm = nullptr;    // caller's terminal adjoint state (lks_set_adjoint_terminal), in the state layout
+    bool custom_lterm = false;
+    bool have_lambda0 = false;  // lam[0] holds lambda_0 of the last adjoint
     // step-kernel variants of the forward sweep, the recomputation and the adjoint steps (see choose_variants)
     int rows_fwd_sweep = 0, rows_rec = 0, rows_adj = 0;
     // tuner results: fastest forward / adjoint variant alone, and the fastest one-step pair run side by side
@@ -205,6 +218,13 @@ void validate(const lks_params* p) {
     if (p->ckpt_slots < 0 || p->seg_len < 0 || p->ckpt_bytes < 0) bad("negative checkpoint setting");
     if (!std::isfinite(p->phi_var)) bad("phi_var must be finite");
     if (p->objective != LKS_OBJ_FLOW && p->objective != LKS_OBJ_OAR) bad("unknown objective");
+    if (p->K_w != 0) {
+        if (p->K_w < 2 || p->K_w > 1000000) bad("K_w must be 0 (no rotation) or >= 2 angle knots");
+        if (!(p->R_w > 0.0)) bad("R_w must be > 0 with a rotating body");
+        if (p->objective != LKS_OBJ_FLOW) bad("a rotating body needs objective LKS_OBJ_FLOW (J2's torque term is not built)");
+        if (p->tile_rows > 1 || p->tile_rows_rec > 1)
+            bad("with a rotating body the forward sweep runs step-kernel variant 1 (tile_rows 0 or 1)");
+    }
     if (p->objective == LKS_OBJ_OAR) {
         if (!(p->drag_span > 0.0) || !std::isfinite(p->drag_span) || !std::isfinite(p->w_D))
             bad("objective J2 needs drag_span > 0 and a finite w_D");
@@ -290,6 +310,23 @@ void setup_geometry(lks_ctx* c) {
     c->mg.d = c->D;
     c->mg.Nt = p.Nt;
     c->mg.R_t = p.R_t;
+    c->rot = p.K_w > 0;
+    g.rot = c->rot ? 1 : 0;
+    if (c->rot) {
+        // footprint box on x and y: the design grid's circumscribed circle around x^G plus the kernel's half width
+        const double hx = 0.5 * (g.nde[0] - 1), hy = 0.5 * (g.nde[1] - 1);
+        c->rb = std::sqrt(hx * hx + hy * hy) + c->hw;
+        for (int a = 0; a < 2; ++a) {
+            g.Fb[a] = (int)std::ceil(2.0 * c->rb) + 2;
+            if (g.periodic[a] && g.Fb[a] > p.n[a])
+                throw LksError{LKS_EINVAL, "the rotating body's footprint must fit in one period of a periodic axis"};
+        }
+        g.Fbn = (long long)g.Fb[0] * g.Fb[1] * g.Fb[2];
+        c->mgw.K = p.K_w;
+        c->mgw.d = 1;
+        c->mgw.Nt = p.Nt;
+        c->mgw.R_t = p.R_w;
+    }
     c->nd = (long long)p.nd[0] * p.nd[1] * p.nd[2];
     c->nde = (long long)g.nde[0] * g.nde[1] * g.nde[2];
 }
@@ -352,7 +389,8 @@ void choose_rows_initial(lks_ctx* c) {
             c->max_ablocks = std::max(c->max_ablocks, (int)(ag.x * ag.y * ag.z));
             c->max_njb = std::max(c->max_njb, njb_of(c));
         }
-    const int r = c->prm.tile_rows > 0 ? c->prm.tile_rows : (c->D == 2 ? 1 : 8);
+    // a rotating body's forward runs variant 1 (the step kernel that reads the rotated footprint map)
+    const int r = c->prm.tile_rows > 0 ? c->prm.tile_rows : (c->D == 2 || c->rot ? 1 : 8);
     int ra = c->prm.tile_rows_adj > 0 ? c->prm.tile_rows_adj : r;
     if (c->prm.tile_rows_adj <= 0 && std::find(ca.begin(), ca.end(), ra) == ca.end()) ra = c->D == 2 ? 1 : 8;
     if (!c->eng->set_rows(r, ra, c->g)) throw LksError{LKS_EINVAL, "step-kernel variant not available for this grid"};
@@ -361,15 +399,83 @@ void choose_rows_initial(lks_ctx* c) {
 // Tile autotuner (D2Q9): time the forward and adjoint step kernels for every rows-per-warp choice on the
 // context's own buffers and keep the fastest of each.  Results are cached per (device, precision, kernel
 // width, grid) for the life of the process.
+// The tuner's choices decide which step kernels run, and the kernels of one lattice differ in the order of their FP
+// additions: two processes that tuned separately could return gradients that differ in the last bits.  The choices
+// are therefore also kept in a file, one line per (device model, precision, transfer kernel, lattice, grid), read
+// before tuning and appended after it, so that every process on a machine runs the same kernels.  The file is
+// $LKS_TUNE_FILE (an empty value: no file), else $XDG_CACHE_HOME/lks/tune.txt, else $HOME/.cache/lks/tune.txt.
+std::string tune_file_path() {
+    const char* f = std::getenv("LKS_TUNE_FILE");
+    if (f) return std::string(f);
+    std::string dir;
+    if (const char* x = std::getenv("XDG_CACHE_HOME"); x && *x)
+        dir = x;
+    else if (const char* h = std::getenv("HOME"); h && *h)
+        dir = std::string(h) + "/.cache";
+    else
+        return std::string();
+    mkdir(dir.c_str(), 0755);
+    dir += "/lks";
+    mkdir(dir.c_str(), 0755);
+    return dir + "/tune.txt";
+}
+
+std::string tune_key(const lks_ctx* c, int dev) {
+    cudaDeviceProp prop;
+    LKS_CUDA(cudaGetDeviceProperties(&prop, dev));
+    std::string name(prop.name);
+    for (char& ch : name)
+        if (ch == ' ' || ch == '\t') ch = '_';
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "v%d|%s|sm%d%d|t%d|hw%d|d%d|rot%d|%dx%dx%d", LKS_ABI_VERSION * 100 + 3, name.c_str(),
+                  prop.major, prop.minor, (int)c->tsize, c->hw, c->D, c->rot ? 1 : 0, c->g.n[0], c->g.n[1], c->g.n[2]);
+    return buf;
+}
+
+bool tune_file_read(const std::string& path, const std::string& key, std::array<int, 4>& out) {
+    if (path.empty()) return false;
+    FILE* f = std::fopen(path.c_str(), "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {  // the last matching line wins
+        char k[320];
+        int v[4];
+        if (std::sscanf(line, "%319s %d %d %d %d", k, &v[0], &v[1], &v[2], &v[3]) == 5 && key == k) {
+            out = {v[0], v[1], v[2], v[3]};
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void tune_file_append(const std::string& path, const std::string& key, const std::array<int, 4>& v) {
+    if (path.empty()) return;
+    FILE* f = std::fopen(path.c_str(), "a");
+    if (!f) return;  // a cache: the choices still hold for this process
+    std::fprintf(f, "%s %d %d %d %d\n", key.c_str(), v[0], v[1], v[2], v[3]);
+    std::fclose(f);
+}
+
 void autotune_rows(lks_ctx* c) {
     static std::mutex mu;
     static std::map<std::tuple<int, int, int, int, int>, std::array<int, 4>> cache;
     int dev = 0;
     LKS_CUDA(cudaGetDevice(&dev));
-    const auto key = std::make_tuple(dev, (int)c->tsize, c->hw * 16 + c->D, c->g.n[0], c->g.n[1] * 65536 + c->g.n[2]);
+    const auto key = std::make_tuple(dev, (int)c->tsize, c->hw * 16 + c->D + (c->rot ? 64 : 0), c->g.n[0],
+                                     c->g.n[1] * 65536 + c->g.n[2]);
+    const std::string fkey = tune_key(c, dev), fpath = tune_file_path();
     {
         std::lock_guard<std::mutex> lock(mu);
         auto it = cache.find(key);
+        std::array<int, 4> v;
+        if (it == cache.end() && tune_file_read(fpath, fkey, v)) {
+            // choices of an earlier process, kept only if this build still offers them on this grid
+            const int rf0 = c->eng->rows_f, ra0 = c->eng->rows_a;
+            if (c->eng->set_rows(v[0], v[2], c->g) && c->eng->set_rows(v[1], v[3], c->g)) it = cache.emplace(key, v).first;
+            c->eng->set_rows(rf0, ra0, c->g);
+        }
         if (it != cache.end()) {
             c->tune_f_lat = it->second[0];
             c->tune_f_one = it->second[1];
@@ -425,6 +531,7 @@ void autotune_rows(lks_ctx* c) {
         struct Cand { int r; int reps; float ms; bool one_step; };
         std::vector<Cand> cands;
         for (int r : (pass == 0 ? cf : ca)) {
+            if (pass == 0 && c->rot && r != 1) continue;  // a rotating body's forward runs variant 1
             // not available for this grid / precision
             if (!(pass == 0 ? c->eng->set_rows(r, ra0, c->g) : c->eng->set_rows(rf0, r, c->g))) continue;
             const float est = time_variant(r, pass, 10);
@@ -516,6 +623,7 @@ void autotune_rows(lks_ctx* c) {
     c->tune_a_one = ra1;
     std::lock_guard<std::mutex> lock(mu);
     cache[key] = {rf, rf1, ra, ra1};
+    tune_file_append(fpath, fkey, cache[key]);
 }
 
 // Variants of the three kinds of step launches.  The forward sweep is one chain, so it takes the fastest
@@ -549,6 +657,23 @@ void allocate(lks_ctx* c) {
     const size_t ts = c->tsize;
     c->state_bytes = (size_t)(D + 1) * N * ts;
     plan_checkpoints(c, c->state_bytes);
+    {
+        // the plan's large buffers (states, footprint-box records and factors, per-step slots) against the free
+        // device memory, before any of them is allocated
+        const long long S1 = (long long)c->S;
+        const long long hist = p.ckpt == LKS_CKPT_FULL ? 0 : (p.ckpt == LKS_CKPT_SQRT ? 2 * S1 : S1);
+        const long long states = (long long)c->slot_used.size() + hist + 7;
+        const long long Lmax = c->Lmax, Fbn = c->g.Fbn;
+        double need = (double)states * (double)c->state_bytes;
+        need += (double)Lmax * Fbn * ts * (2.0 * 2 * D + 2 + (c->rot ? 1 + D : 1));  // box records, factors, kappa-bar
+        need += (double)(p.Nt + 1) * (sizeof(Pose) + 8.0 * (4 * D + 2 * c->max_njb + 1));
+        size_t free_b = 0, total_b = 0;
+        LKS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        if (need > (double)free_b)
+            throw LksError{LKS_ENOMEM, "the checkpoint and state plan needs " + std::to_string((long long)(need / 1e6)) +
+                                           " MB of device memory, " + std::to_string((long long)(free_b / 1000000)) +
+                                           " MB are free"};
+    }
 
     c->d_gamma = (double*)dalloc(c, c->nd * 8);
     c->d_gt = (double*)dalloc(c, c->nd * 8);
@@ -592,9 +717,30 @@ void allocate(lks_ctx* c) {
         LKS_CUDA(cudaMemset(c->d_oar_guG, 0, (size_t)(p.Nt + 1) * D * 8));
     }
     c->d_flag = (unsigned*)dalloc(c, 16);
-    c->d_kbar = dalloc(c, (size_t)c->Lmax * c->g.Fbn * ts);
+    // kappa-bar per step (and u^S-bar with a rotating body); per-block motion partials per step (2 D values, and
+    // dJ/dtheta, dJ/domega with a rotating body)
+    c->d_kbar = dalloc(c, (size_t)c->Lmax * c->g.Fbn * ts * (c->rot ? 1 + D : 1));
     c->nsb = (int)nblk(c->g.Fbn, 256);
-    c->d_mslot = (double*)dalloc(c, (size_t)c->Lmax * c->nsb * 2 * D * 8);
+    c->d_mslot = (double*)dalloc(c, (size_t)c->Lmax * c->nsb * (2 * D + (c->rot ? 2 : 0)) * 8);
+    if (c->rot) {
+        const int Kw = p.K_w;
+        c->d_aknots = (double*)dalloc(c, (size_t)Kw * 8);
+        c->d_afilt = (double*)dalloc(c, (size_t)Kw * 8);
+        c->d_anorm = (double*)dalloc(c, (size_t)Kw * 8);
+        c->d_atmp = (double*)dalloc(c, (size_t)Kw * 8);
+        c->d_out_a = (double*)dalloc(c, (size_t)Kw * 8);
+        c->d_theta = (double*)dalloc(c, (size_t)(p.Nt + 1) * 8);
+        c->d_omega = (double*)dalloc(c, (size_t)(p.Nt + 1) * 8);
+        c->d_gth = (double*)dalloc(c, (size_t)(p.Nt + 1) * 8);
+        c->d_gom = (double*)dalloc(c, (size_t)(p.Nt + 1) * 8);
+        c->d_rotmap = dalloc(c, (size_t)(1 + D) * c->g.Fbn * ts);
+        c->g.rotmap = c->d_rotmap;
+        LKS_CUDA(cudaMemset(c->d_aknots, 0, (size_t)Kw * 8));
+        LKS_CUDA(cudaMemset(c->d_out_a, 0, (size_t)Kw * 8));
+        LKS_CUDA(cudaMemset(c->d_gth, 0, (size_t)(p.Nt + 1) * 8));
+        LKS_CUDA(cudaMemset(c->d_gom, 0, (size_t)(p.Nt + 1) * 8));
+        LKS_CUDA(cudaMemset(c->d_rotmap, 0, (size_t)(1 + D) * c->g.Fbn * ts));
+    }
     c->box_step = 2LL * D * c->g.Fbn;
     c->d_boxbuf = dalloc(c, (size_t)2 * c->Lmax * c->box_step * ts);
     c->d_fac = dalloc(c, (size_t)2 * c->Lmax * c->g.Fbn * ts);
@@ -640,6 +786,10 @@ void allocate(lks_ctx* c) {
     LKS_LAUNCHED();
     motion_norm_kernel<<<nblk(p.K, 128), 128>>>(c->mg, c->d_tnorm);
     LKS_LAUNCHED();
+    if (c->rot) {
+        motion_norm_kernel<<<nblk(p.K_w, 128), 128>>>(c->mgw, c->d_anorm);
+        LKS_LAUNCHED();
+    }
     LKS_CUDA(cudaDeviceSynchronize());
 }
 
@@ -742,7 +892,15 @@ void prepare_design_and_motion(lks_ctx* c, cudaStream_t s) {
     LKS_LAUNCHED();
     interp_kernel<<<nblk((long long)(Nt + 1) * D, 256), 256, 0, s>>>(c->mg, c->d_filt, c->d_s, c->d_uG);
     LKS_LAUNCHED();
+    if (c->rot) {  // angle knots -> filtered -> theta_n, omega_n = theta_n - theta_{n-1} (Eqs. psi_filtered, theta, omega)
+        motion_filter_kernel<<<nblk(c->prm.K_w, 128), 128, 0, s>>>(c->mgw, c->d_aknots, c->d_anorm, c->d_afilt, 0);
+        LKS_LAUNCHED();
+        interp_kernel<<<nblk(Nt + 1, 256), 256, 0, s>>>(c->mgw, c->d_afilt, c->d_theta, c->d_omega);
+        LKS_LAUNCHED();
+        c->launches += 2;
+    }
     pose_kernel<<<nblk(Nt + 1, 128), 128, 0, s>>>(c->g, D, c->o0[0], c->o0[1], c->o0[2], c->cosine, Nt, c->d_s, c->d_uG,
+                                                  c->rot ? c->d_theta : nullptr, c->rot ? c->d_omega : nullptr, c->rb,
                                                   c->d_pose);
     LKS_LAUNCHED();
     c->launches += 5;
@@ -779,6 +937,10 @@ int njb_of(const lks_ctx* c) {
 }
 
 void fwd_step(lks_ctx* c, int n, const void* in, void* out, bool objective, cudaStream_t s) {
+    if (c->rot) {  // kappa and u^S of step n on the footprint box, read by the step kernel
+        c->eng->rot_box_map(c->g, c->d_pose + n, c->d_kref, c->d_rotmap, s);
+        c->launches++;
+    }
     int lo[3], cnt[3];
     probe_blocks(c, lo, cnt);
     const int njb = cnt[0] * cnt[1] * cnt[2];
@@ -963,8 +1125,12 @@ void adjoint_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
     const std::vector<const void*>& st = c->seg_st[buf];
     cudaEvent_t ea = span_begin(c, s);
     // 1 / (1 + kappa) on the footprint box for every step of the segment, in one launch
-    c->eng->box_fac(c->g, c->d_pose, c->d_kref, a + 1, b - a,
-                    c->tptr(c->d_fac, (long long)buf * c->Lmax * c->g.Fbn), s);
+    if (c->rot)
+        c->eng->rot_box_fac(c->g, c->d_pose, c->d_kref, a + 1, b - a,
+                            c->tptr(c->d_fac, (long long)buf * c->Lmax * c->g.Fbn), s);
+    else
+        c->eng->box_fac(c->g, c->d_pose, c->d_kref, a + 1, b - a,
+                        c->tptr(c->d_fac, (long long)buf * c->Lmax * c->g.Fbn), s);
     c->launches++;
     for (int n = b; n > a;) {
         const int j = n - a - 1;  // box-buffer slot of step n
@@ -1001,6 +1167,28 @@ void sens_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
     const int mode = c->prm.mode;
     const bool shape = mode != LKS_MODE_MOTION, motion = mode != LKS_MODE_SHAPE;
     const void* bb = c->tptr(c->d_boxbuf, (long long)buf * c->Lmax * c->box_step);
+    if (c->rot) {
+        // rotating body: kappa-bar and u^S-bar per box node, the motion partials (position, u^G, theta, omega), the
+        // transposed mapping on the design side, and the per-step motion sums
+        const long long kst = (long long)(1 + c->D) * c->g.Fbn;
+        c->eng->rot_sens(c->g, c->d_pose, c->d_kref, bb, c->box_step, a + 1, L, c->d_kbar, c->d_mslot, s);
+        c->launches++;
+        if (shape) {
+            c->eng->rot_gather(c->g, c->d_pose, c->d_kbar, a + 1, L, kst, c->d_dkref, s);
+            c->launches++;
+        }
+        if (motion) {
+            if (c->D == 2)
+                rot_motion_reduce_kernel<2><<<L, 32, 0, s>>>(c->d_mslot, c->nsb, a + 1, L, c->d_gs, c->d_guG, c->d_gth,
+                                                            c->d_gom);
+            else
+                rot_motion_reduce_kernel<3><<<L, 32, 0, s>>>(c->d_mslot, c->nsb, a + 1, L, c->d_gs, c->d_guG, c->d_gth,
+                                                            c->d_gom);
+            LKS_LAUNCHED();
+            c->launches++;
+        }
+        return;
+    }
     c->eng->sens(c->g, c->d_pose, c->d_kref, bb, c->box_step, a + 1, L, shape ? c->d_kbar : nullptr,
                  motion ? c->d_mslot : nullptr, s);
     c->launches++;
@@ -1102,9 +1290,10 @@ void adjoint_body(lks_ctx* c, cudaStream_t s);
 
 void run_adjoint(lks_ctx* c, cudaStream_t s) {
     if (!c->have_forward) throw LksError{LKS_ESTATE, "lks_adjoint needs a preceding lks_forward"};
-    LKS_CUDA(cudaEventSynchronize(c->ev_flag));
-    if (*c->h_flag) throw LksError{LKS_EUNSTABLE, "forward sweep unstable: non-finite velocity or |u| > u_crit"};
+    // no wait for the forward's stability flag here: the reverse sweep is enqueued behind it, and an unstable forward
+    // is reported by lks_get_status, by lks_adjoint (host pointers) and as NaN gradients of lks_adjoint_dev
     run_graph(c, c->gx_adj, s, [&](cudaStream_t cs) { adjoint_body(c, cs); });
+    c->have_lambda0 = true;
     if (!c->use_graphs) c->spans_adj = c->spans;
     // the binomial schedule reuses the forward's checkpoint slots: a new forward must precede the next adjoint
     if (c->prm.ckpt == LKS_CKPT_REVOLVE) c->have_forward = false;
@@ -1120,8 +1309,16 @@ void adjoint_body(lks_ctx* c, cudaStream_t s) {
     LKS_CUDA(cudaMemsetAsync(c->d_dkref, 0, c->nde * 8, s));
     LKS_CUDA(cudaMemsetAsync(c->d_gs, 0, (size_t)(Nt + 1) * D * 8, s));
     LKS_CUDA(cudaMemsetAsync(c->d_guG, 0, (size_t)(Nt + 1) * D * 8, s));
+    if (c->rot) {
+        LKS_CUDA(cudaMemsetAsync(c->d_gth, 0, (size_t)(Nt + 1) * 8, s));
+        LKS_CUDA(cudaMemsetAsync(c->d_gom, 0, (size_t)(Nt + 1) * 8, s));
+    }
     c->eng->init_adjoint(c->g, c->fin, c->lam[0], c->oar ? 0 : 1, s);
     c->launches++;
+    if (c->custom_lterm) {  // the adjoint half of the periodic approximation (Sec. 3.3)
+        c->eng->add_state(c->g, c->lam[0], c->d_lterm, s);
+        c->launches++;
+    }
     if (c->prm.ckpt == LKS_CKPT_REVOLVE) {
         reverse_revolve(c, 0, c->M, c->free_slots, c->slot[0], s);
     } else if (c->prm.ckpt == LKS_CKPT_FULL) {
@@ -1146,6 +1343,18 @@ void adjoint_body(lks_ctx* c, cudaStream_t s) {
     interp_T_kernel<<<nblk((long long)K * D, 64), 64, 0, s>>>(c->mg, c->d_gs, c->d_guG, c->d_ktmp);
     LKS_LAUNCHED();
     c->launches += 2;
+    if (c->rot) {  // (dJ/dtheta_n, dJ/domega_n) -> difference^T, interpolation^T, filter^T -> dJ/d(angle knots)
+        const int Kw = c->prm.K_w;
+        if (c->prm.mode == LKS_MODE_SHAPE) {
+            LKS_CUDA(cudaMemsetAsync(c->d_out_a, 0, (size_t)Kw * 8, s));
+        } else {
+            interp_T_kernel<<<nblk(Kw, 64), 64, 0, s>>>(c->mgw, c->d_gth, c->d_gom, c->d_atmp);
+            LKS_LAUNCHED();
+            motion_filter_kernel<<<nblk(Kw, 64), 64, 0, s>>>(c->mgw, c->d_atmp, c->d_anorm, c->d_out_a, 1);
+            LKS_LAUNCHED();
+            c->launches += 2;
+        }
+    }
     c->launches_adj = c->launches;
     c->spans_adj = c->spans;
     (void)K;
@@ -1191,6 +1400,14 @@ void finish_adjoint(lks_ctx* c, double* dgamma, double* dpos, cudaStream_t s) {
         c->stats.ms_adjoint_steps = acc[2];
         c->stats.ms_total = tot;
     }
+}
+
+// NaN gradients on the device when the last forward raised the stability flag (asynchronous adjoint variants).
+void poison_if_unstable(lks_ctx* c, double* dgamma, double* dpos, cudaStream_t s) {
+    const long long nk = (long long)c->prm.K * c->D;
+    const long long n = std::max<long long>(c->nd, nk);
+    poison_unstable_kernel<<<nblk(n, 256), 256, 0, s>>>(c->d_flag, dgamma, c->nd, dpos, nk);
+    LKS_LAUNCHED();
 }
 
 template <typename F>
@@ -1404,6 +1621,7 @@ int lks_adjoint_dev(lks_ctx* c, double* d_dgamma, double* d_dpos, void* stream) 
         cudaStream_t s = (cudaStream_t)stream;
         run_adjoint(c, s);
         finish_adjoint(c, d_dgamma, d_dpos, s);
+        poison_if_unstable(c, d_dgamma, d_dpos, s);
     });
 }
 
@@ -1414,6 +1632,8 @@ int lks_adjoint(lks_ctx* c, double* dgamma, double* dpos) {
         cudaStream_t s = 0;
         run_adjoint(c, s);
         finish_adjoint(c, c->d_out_g, c->d_out_k, s);
+        LKS_CUDA(cudaStreamSynchronize(s));  // the forward's flag reached the host before its sweep ended
+        if (*c->h_flag) throw LksError{LKS_EUNSTABLE, "forward sweep unstable: non-finite velocity or |u| > u_crit"};
         LKS_CUDA(cudaMemcpyAsync(dgamma, c->d_out_g, c->nd * 8, cudaMemcpyDeviceToHost, s));
         LKS_CUDA(cudaMemcpyAsync(dpos, c->d_out_k, (size_t)c->prm.K * c->D * 8, cudaMemcpyDeviceToHost, s));
         LKS_CUDA(cudaStreamSynchronize(s));
@@ -1577,7 +1797,7 @@ int lks_get_state(lks_ctx* c, double* p, double* u) {
         const long long N = c->g.N;
         double* dp = nullptr;
         LKS_CUDA(cudaMalloc(&dp, (size_t)(c->D + 1) * N * 8));
-        c->eng->export_state(c->g, c->fin, dp, dp + N, 0);
+        c->eng->export_state(c->g, c->fin, dp, dp + N, 1.0 / 3.0, 0);
         cudaError_t e1 = cudaMemcpy(p, dp, N * 8, cudaMemcpyDeviceToHost);
         cudaError_t e2 = cudaMemcpy(u, dp + N, (size_t)c->D * N * 8, cudaMemcpyDeviceToHost);
         cudaFree(dp);
@@ -1647,9 +1867,77 @@ int lks_set_initial_state(lks_ctx* c, const double* p, const double* u) {
         LKS_CUDA(cudaMalloc(&b.p, (size_t)(c->D + 1) * N * 8));
         LKS_CUDA(cudaMemcpy(b.p, p, N * 8, cudaMemcpyHostToDevice));
         LKS_CUDA(cudaMemcpy(b.p + N, u, (size_t)c->D * N * 8, cudaMemcpyHostToDevice));
-        c->eng->import_state(c->g, b.p, b.p + N, c->d_init, 0);
+        c->eng->import_state(c->g, b.p, b.p + N, c->d_init, 1.0 / 3.0, 0);
         LKS_CUDA(cudaDeviceSynchronize());
         c->custom_init = true;
+    });
+}
+
+int lks_set_adjoint_terminal(lks_ctx* c, const double* lp, const double* lu) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if ((lp == nullptr) != (lu == nullptr)) throw LksError{LKS_EINVAL, "lam_p and lam_u must both be given or both NULL"};
+        drop_graphs(c);  // the captured reverse sweep starts from the previous terminal state
+        c->have_forward = false;
+        if (!lp) {
+            c->custom_lterm = false;
+            return;
+        }
+        const long long N = c->g.N;
+        if (!c->d_lterm) c->d_lterm = dalloc(c, c->state_bytes);
+        DevScratch b;
+        LKS_CUDA(cudaMalloc(&b.p, (size_t)(c->D + 1) * N * 8));
+        LKS_CUDA(cudaMemcpy(b.p, lp, N * 8, cudaMemcpyHostToDevice));
+        LKS_CUDA(cudaMemcpy(b.p + N, lu, (size_t)c->D * N * 8, cudaMemcpyHostToDevice));
+        c->eng->import_state(c->g, b.p, b.p + N, c->d_lterm, 0.0, 0);
+        LKS_CUDA(cudaDeviceSynchronize());
+        c->custom_lterm = true;
+    });
+}
+
+int lks_get_adjoint_initial(lks_ctx* c, double* lp, double* lu) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!lp || !lu) throw LksError{LKS_EINVAL, "null pointer"};
+        if (!c->have_lambda0) throw LksError{LKS_ESTATE, "no adjoint has run"};
+        const long long N = c->g.N;
+        DevScratch b;
+        LKS_CUDA(cudaMalloc(&b.p, (size_t)(c->D + 1) * N * 8));
+        LKS_CUDA(cudaDeviceSynchronize());
+        c->eng->export_state(c->g, c->lam[0], b.p, b.p + N, 0.0, 0);
+        LKS_CUDA(cudaMemcpy(lp, b.p, N * 8, cudaMemcpyDeviceToHost));
+        LKS_CUDA(cudaMemcpy(lu, b.p + N, (size_t)c->D * N * 8, cudaMemcpyDeviceToHost));
+    });
+}
+
+int lks_set_angle_knots(lks_ctx* c, const double* aknots) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!c->rot) throw LksError{LKS_EINVAL, "the context has no rotating body (K_w = 0)"};
+        if (!aknots) throw LksError{LKS_EINVAL, "null pointer"};
+        LKS_CUDA(cudaMemcpy(c->d_aknots, aknots, (size_t)c->prm.K_w * 8, cudaMemcpyHostToDevice));
+    });
+}
+
+int lks_get_angle_gradient(lks_ctx* c, double* out) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!c->rot) throw LksError{LKS_EINVAL, "the context has no rotating body (K_w = 0)"};
+        if (!out) throw LksError{LKS_EINVAL, "null pointer"};
+        if (!c->have_lambda0) throw LksError{LKS_ESTATE, "no adjoint has run"};
+        LKS_CUDA(cudaDeviceSynchronize());
+        LKS_CUDA(cudaMemcpy(out, c->d_out_a, (size_t)c->prm.K_w * 8, cudaMemcpyDeviceToHost));
+    });
+}
+
+int lks_get_step_angle_sensitivities(lks_ctx* c, double* gth, double* gom) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!c->rot) throw LksError{LKS_EINVAL, "the context has no rotating body (K_w = 0)"};
+        if (!gth || !gom) throw LksError{LKS_EINVAL, "null pointer"};
+        LKS_CUDA(cudaDeviceSynchronize());
+        LKS_CUDA(cudaMemcpy(gth, c->d_gth, (size_t)(c->prm.Nt + 1) * 8, cudaMemcpyDeviceToHost));
+        LKS_CUDA(cudaMemcpy(gom, c->d_gom, (size_t)(c->prm.Nt + 1) * 8, cudaMemcpyDeviceToHost));
     });
 }
 
@@ -1659,6 +1947,15 @@ int lks_set_graphs(lks_ctx* c, int enable) {
         drop_graphs(c);
         c->use_graphs = enable != 0;
         c->have_forward = false;
+    });
+}
+
+int lks_get_status(lks_ctx* c) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!c->have_final) throw LksError{LKS_ESTATE, "no forward has run"};
+        LKS_CUDA(cudaEventSynchronize(c->ev_flag));
+        if (*c->h_flag) throw LksError{LKS_EUNSTABLE, "forward sweep unstable: non-finite velocity or |u| > u_crit"};
     });
 }
 
@@ -1899,13 +2196,13 @@ int lks_batch_adjoint_dev(lks_batch* b, double* const* d_dgamma, double* const* 
         for (size_t i = 0; i < b->ctx.size(); ++i) {
             lks_ctx* c = b->ctx[i];
             if (!c->have_forward) throw LksError{LKS_ESTATE, "lks_batch_adjoint needs a preceding lks_batch_forward"};
-            LKS_CUDA(cudaEventSynchronize(c->ev_flag));
-            if (*c->h_flag) throw LksError{LKS_EUNSTABLE, "instance " + std::to_string(i) + ": forward sweep unstable"};
         }
         batch_graph(b, b->gx_adj, s, [&](lks_ctx* c, cudaStream_t cs) { adjoint_body(c, cs); });
         for (size_t i = 0; i < b->ctx.size(); ++i) {
             lks_ctx* c = b->ctx[i];
             finish_adjoint(c, d_dgamma ? d_dgamma[i] : nullptr, d_dpos ? d_dpos[i] : nullptr, s);
+            poison_if_unstable(c, d_dgamma ? d_dgamma[i] : nullptr, d_dpos ? d_dpos[i] : nullptr, s);
+            c->have_lambda0 = true;
             if (c->prm.ckpt == LKS_CKPT_REVOLVE) c->have_forward = false;
         }
     });

@@ -76,6 +76,9 @@ struct Geom {
     double A;           // 3/4 - 9 nu / 2
     double wall_u[3][2][3];
     double u_crit2;     // squared stability limit (<= 0 disables)
+    int rot;            // 1: the body also rotates (theta turns x-y about an axis parallel to z); the footprint box
+                        // on x and y then covers the design grid at any angle (lks_rot.cuh)
+    const void* rotmap; // rotating body: kappa, u^S_0 .. u^S_D-1 of the current step on the footprint box (forward)
 };
 
 // Per-step rigid-body pose (Eq. rigid_body_position with theta = 0) reduced to what the mapping needs:
@@ -91,6 +94,10 @@ struct Pose {
     float dwf[3][4];
     float uGf[3];
     float padf;
+    // rotating body (Eqs. rigid_body_position, rigid_body_velocity): theta, omega, (cos, sin) theta, and x^G - xs on
+    // x and y (the rotation centre relative to the footprint box start); theta = 0 without rotation
+    double th, om, cs[2], cg[2];
+    float thf, omf, csf[2], cgf[2];
 };
 
 // Pose values in the state precision T.

@@ -13,6 +13,7 @@
 #include "lks_prep_kernels.cuh"
 #include "lks_step_kernels.cuh"
 #include "lks_oar.cuh"
+#include "lks_rot.cuh"
 
 namespace lks {
 
@@ -92,7 +93,9 @@ struct Engine {
                         long long kstride, double* dkref, cudaStream_t s) = 0;
     virtual void kappa_ref(const DesignGeom& dg, const double* gt, double* gb, double* k64, void* k, cudaStream_t s) = 0;
     virtual void init_state(const Geom& g, void* st, cudaStream_t s) = 0;
-    virtual void import_state(const Geom& g, const double* p, const double* u, void* st, cudaStream_t s) = 0;
+    virtual void import_state(const Geom& g, const double* p, const double* u, void* st, double pshift,
+                              cudaStream_t s) = 0;
+    virtual void add_state(const Geom& g, void* dst, const void* src, cudaStream_t s) = 0;
     virtual void init_adjoint(const Geom& g, const void* fin, void* lam, int src, cudaStream_t s) = 0;
     // objective J2 (translating body): per-block partials of sum_x kappa u of one step, and its adjoint source
     virtual void oar_partial(const Geom& g, const Pose* pose, const void* kref, const void* st, double* scratch,
@@ -102,7 +105,17 @@ struct Engine {
     virtual void oar_sens(const Geom& g, const OarGeom& o, const Pose* poses, const void* kref, const void* boxbuf,
                           long long bstride, int n_first, int nsteps, void* kbar, double* scratch, unsigned* tickets,
                           double* oms, cudaStream_t s) = 0;
-    virtual void export_state(const Geom& g, const void* st, double* p, double* u, cudaStream_t s) = 0;
+    virtual void export_state(const Geom& g, const void* st, double* p, double* u, double pshift, cudaStream_t s) = 0;
+    // rotating body (lks_rot.cuh): kappa and u^S of one step on the footprint box; 1 / (1 + kappa) for a segment's
+    // steps; the local sensitivities of a segment (kappa-bar, u^S-bar per box node, per-block motion partials); the
+    // transposed mapping on the design side; the per-step motion sums
+    virtual void rot_box_map(const Geom& g, const Pose* pose, const void* kref, void* map, cudaStream_t s) = 0;
+    virtual void rot_box_fac(const Geom& g, const Pose* poses, const void* kref, int n_first, int nsteps, void* out,
+                             cudaStream_t s) = 0;
+    virtual void rot_sens(const Geom& g, const Pose* poses, const void* kref, const void* boxbuf, long long bstride,
+                          int n_first, int nsteps, void* kbar, double* mslot, cudaStream_t s) = 0;
+    virtual void rot_gather(const Geom& g, const Pose* poses, const void* kbar, int n_first, int nsteps,
+                            long long kstride, double* dkref, cudaStream_t s) = 0;
 };
 
 template <typename T>
@@ -179,16 +192,43 @@ struct EngineCommon : Engine {
         init_state_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, (T*)st);
         LKS_LAUNCHED();
     }
-    void import_state(const Geom& g, const double* p, const double* u, void* st, cudaStream_t s) override {
-        import_state_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, p, u, (T*)st);
+    void import_state(const Geom& g, const double* p, const double* u, void* st, double pshift,
+                      cudaStream_t s) override {
+        import_state_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, p, u, (T*)st, pshift);
+        LKS_LAUNCHED();
+    }
+    void add_state(const Geom& g, void* dst, const void* src, cudaStream_t s) override {
+        add_state_kernel<T, D><<<nblk((D + 1) * g.N, 256), 256, 0, s>>>(g, (T*)dst, (const T*)src);
         LKS_LAUNCHED();
     }
     void init_adjoint(const Geom& g, const void* fin, void* lam, int src, cudaStream_t s) override {
         init_adjoint_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, (const T*)fin + g.N, (T*)lam, src);
         LKS_LAUNCHED();
     }
-    void export_state(const Geom& g, const void* st, double* p, double* u, cudaStream_t s) override {
-        export_state_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, (const T*)st, p, u);
+    void export_state(const Geom& g, const void* st, double* p, double* u, double pshift, cudaStream_t s) override {
+        export_state_kernel<T, D><<<nblk(g.N, 256), 256, 0, s>>>(g, (const T*)st, p, u, pshift);
+        LKS_LAUNCHED();
+    }
+    void rot_box_map(const Geom& g, const Pose* pose, const void* kref, void* map, cudaStream_t s) override {
+        rot_box_map_kernel<T, D, HW><<<nblk(g.Fbn, 256), 256, 0, s>>>(g, pose, (const T*)kref, (T*)map);
+        LKS_LAUNCHED();
+    }
+    void rot_box_fac(const Geom& g, const Pose* poses, const void* kref, int n_first, int nsteps, void* out,
+                     cudaStream_t s) override {
+        rot_box_fac_kernel<T, D, HW><<<dim3(nblk(g.Fbn, 256), nsteps, 1), 256, 0, s>>>(g, poses, (const T*)kref, n_first,
+                                                                                     (T*)out);
+        LKS_LAUNCHED();
+    }
+    void rot_sens(const Geom& g, const Pose* poses, const void* kref, const void* boxbuf, long long bstride, int n_first,
+                  int nsteps, void* kbar, double* mslot, cudaStream_t s) override {
+        rot_sens_kernel<T, D, HW><<<dim3(nblk(g.Fbn, 256), nsteps, 1), 256, 0, s>>>(
+            g, poses, (const T*)kref, (const T*)boxbuf, bstride, n_first, (T*)kbar, mslot);
+        LKS_LAUNCHED();
+    }
+    void rot_gather(const Geom& g, const Pose* poses, const void* kbar, int n_first, int nsteps, long long kstride,
+                    double* dkref, cudaStream_t s) override {
+        const long long nd = (long long)g.nde[0] * g.nde[1] * g.nde[2];
+        rot_gather_kernel<T, D, HW><<<nblk(nd, 128), 128, 0, s>>>(g, poses, (const T*)kbar, n_first, nsteps, kstride, dkref);
         LKS_LAUNCHED();
     }
     void oar_partial(const Geom& g, const Pose* pose, const void* kref, const void* st, double* scratch,

@@ -222,8 +222,12 @@ static __global__ void interp_T_kernel(MotionGeom mg, const double* __restrict__
 // Per-step pose: offset o = o0 + s_n, box start and tap weights of the shifted design grid (Eq. rigid_body_position,
 // theta = 0; transfer kernel w of Sec. 2.3).  Tap k of a node reads design index j = b - 2 hw + 1 + k, with
 // r = t - j = hw - k - f for f = o - floor(o).
+// With a rotating body (g.rot), theta_n and omega_n come from `theta` and `omega`, and on x and y the footprint box
+// starts at floor(x^G - rb), rb the half extent of the box (the design grid's circumscribed radius plus the kernel's
+// half width), with cg = x^G - that start.
 static __global__ void pose_kernel(Geom g, int D, double o0x, double o0y, double o0z, int cosine, int Nt,
-                            const double* __restrict__ s, const double* __restrict__ uG, Pose* __restrict__ poses) {
+                            const double* __restrict__ s, const double* __restrict__ uG, const double* __restrict__ theta,
+                            const double* __restrict__ omega, double rb, Pose* __restrict__ poses) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n > Nt) return;
     const double o0[3] = {o0x, o0y, o0z};
@@ -255,6 +259,21 @@ static __global__ void pose_kernel(Geom g, int D, double o0x, double o0y, double
             }
         }
     }
+    P.th = theta != nullptr ? theta[n] : 0.0;
+    P.om = omega != nullptr ? omega[n] : 0.0;
+    P.cs[0] = cos(P.th);
+    P.cs[1] = sin(P.th);
+    P.cg[0] = P.cg[1] = 0.0;
+    if (g.rot) {
+        for (int a = 0; a < 2; ++a) {
+            const double xg = o0[a] + s[n * D + a] + 0.5 * (g.nde[a] - 1);
+            const double lo = floor(xg - rb);
+            P.cg[a] = xg - lo;
+            int xs = (int)lo;
+            if (g.periodic[a]) xs = wrap(xs, g.n[a]);
+            P.xs[a] = xs;
+        }
+    }
     for (int a = 0; a < 3; ++a) {
         for (int k = 0; k < 4; ++k) {
             P.wf[a][k] = (float)P.w[a][k];
@@ -263,6 +282,12 @@ static __global__ void pose_kernel(Geom g, int D, double o0x, double o0y, double
         P.uGf[a] = (float)P.uG[a];
     }
     P.padf = 0.f;
+    P.thf = (float)P.th;
+    P.omf = (float)P.om;
+    for (int a = 0; a < 2; ++a) {
+        P.csf[a] = (float)P.cs[a];
+        P.cgf[a] = (float)P.cg[a];
+    }
     poses[n] = P;
 }
 
@@ -307,25 +332,46 @@ __global__ void init_adjoint_kernel(Geom g, const T* __restrict__ u_fin, T* __re
     for (int c = 0; c < D; ++c) lam[(1 + c) * g.N + i] = on ? (T)(g.dir[c] * g.phi) * f : (T)0;
 }
 
-// FP64 copy of a state (p = p' + 1/3) for the host.
+// A state from FP64 host arrays and back: field 0 is stored as p - pshift (pshift = 1/3 for a flow state, whose
+// reduced pressure p' = p - 1/3 is kept; 0 for an adjoint state).
 template <typename T, int D>
-__global__ void import_state_kernel(Geom g, const double* __restrict__ p, const double* __restrict__ u, T* __restrict__ st) {
+__global__ void import_state_kernel(Geom g, const double* __restrict__ p, const double* __restrict__ u, T* __restrict__ st,
+                                    double pshift) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= g.N) return;
-    st[i] = (T)(p[i] - 1.0 / 3.0);
+    st[i] = (T)(p[i] - pshift);
     for (int c = 0; c < D; ++c) st[(1 + c) * g.N + i] = (T)u[c * g.N + i];
 }
 
 template <typename T, int D>
-__global__ void export_state_kernel(Geom g, const T* __restrict__ st, double* __restrict__ p, double* __restrict__ u) {
+__global__ void export_state_kernel(Geom g, const T* __restrict__ st, double* __restrict__ p, double* __restrict__ u,
+                                    double pshift) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= g.N) return;
-    p[i] = (double)st[i] + 1.0 / 3.0;
+    p[i] = (double)st[i] + pshift;
     for (int c = 0; c < D; ++c) u[c * g.N + i] = (double)st[(1 + c) * g.N + i];
+}
+
+// dst += src over all D + 1 fields of a state (the terminal adjoint state of the periodic approximation).
+template <typename T, int D>
+__global__ void add_state_kernel(Geom g, T* __restrict__ dst, const T* __restrict__ src) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (D + 1) * g.N) return;
+    dst[i] += src[i];
 }
 
 
 // One normalised projected-gradient step of the optimiser driver: x_i <- min(hi, max(lo, x_i + step g_i / max|g|))
+// NaN into the gradients when the forward sweep they come from raised the stability flag (bit 0 of *flag): the
+// asynchronous adjoint cannot return LKS_EUNSTABLE, so its outputs carry the failure instead.
+static __global__ void poison_unstable_kernel(const unsigned* __restrict__ flag, double* __restrict__ a, long long na,
+                                              double* __restrict__ b, long long nb) {
+    if ((*flag & 1u) == 0u) return;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (a != nullptr && i < na) a[i] = __longlong_as_double(0x7ff8000000000000LL);
+    if (b != nullptr && i < nb) b[i] = __longlong_as_double(0x7ff8000000000000LL);
+}
+
 // (x unchanged where g = 0 everywhere).  A single block: the max-reduction, then the update, so that no scratch
 // memory is needed.  Launch with 1024 threads.
 static __global__ void __launch_bounds__(1024) gradient_step_kernel(long long n, double step, const double* __restrict__ g,

@@ -61,12 +61,27 @@ __global__ void __launch_bounds__(256) fwd2r_kernel(Geom g, FwdArgs<T> a) {
         const int byc = box_coord(y, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
         kapk[k] = 0;
         Ck[k] = 0;
-        if (lane_out && y < ny && bxc >= 0 && byc >= 0) {
+        if (!g.rot && lane_out && y < ny && bxc >= 0 && byc >= 0) {
             const int b[2] = {bxc, byc};
             map_node<T, 2, HW, false>(g, P, a.kref, b, kapk[k], Ck[k], nullptr, nullptr);
         }
     }
     pdl_wait_then_release();
+    // rotating body: kappa and u^S from the footprint map that the previous kernel wrote (so only after the wait)
+    T uSk[RPT][2];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        uSk[k][0] = uSk[k][1] = 0;
+        const int y = y0 + t + RW::TR * k;
+        const int byc = box_coord(y, P.xs[1], g.Fb[1], g.n[1], g.periodic[1]);
+        if (g.rot && lane_out && y < ny && bxc >= 0 && byc >= 0) {
+            const T* map = (const T*)g.rotmap;
+            const long long bl = bxc + (long long)g.Fb[0] * byc;
+            kapk[k] = map[bl];
+            uSk[k][0] = map[g.Fbn + bl];
+            uSk[k][1] = map[2 * g.Fbn + bl];
+        }
+    }
 
     // phase 1: raw rows y0-2 .. y0+TY+1
 #pragma unroll
@@ -122,8 +137,9 @@ __global__ void __launch_bounds__(256) fwd2r_kernel(Geom g, FwdArgs<T> a) {
         if (bxc >= 0 && byc >= 0) {
             const T kap = kapk[k], C = Ck[k];
             const T inv = (T)1 / ((T)1 + kap);
-            un0 = (ax + kap * (pose_uG<T>(P, 0) * C)) * inv;
-            un1 = (ay + kap * (pose_uG<T>(P, 1) * C)) * inv;
+            const T us0 = g.rot ? uSk[k][0] : pose_uG<T>(P, 0) * C, us1 = g.rot ? uSk[k][1] : pose_uG<T>(P, 1) * C;
+            un0 = (ax + kap * us0) * inv;
+            un1 = (ay + kap * us1) * inv;
         }
         int xg[2] = {xo, y};
         T uw[2];

@@ -395,11 +395,27 @@ __global__ void __launch_bounds__(TX * TY * TZ) fwd_step_kernel(Geom g, FwdArgs<
         b[c] = box_coord(xg[c], P.xs[c], g.Fb[c], g.n[c], g.periodic[c]);
         inbox = inbox && b[c] >= 0;
     }
-    T kap = 0, C = 0;
-    if (inbox) map_node<T, D, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
+    T kap = 0, C = 0, uS[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) uS[c] = 0;
+    if (inbox) {
+        if (g.rot) {  // rotating body: kappa and u^S of this step on the footprint box (rot_box_map_kernel)
+            long long bl = b[D - 1];
+#pragma unroll
+            for (int c = D - 2; c >= 0; --c) bl = bl * g.Fb[c] + b[c];
+            const T* map = (const T*)g.rotmap;
+            kap = map[bl];
+#pragma unroll
+            for (int c = 0; c < D; ++c) uS[c] = map[(1 + c) * g.Fbn + bl];
+        } else {
+            map_node<T, D, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
+#pragma unroll
+            for (int c = 0; c < D; ++c) uS[c] = pose_uG<T>(P, c) * C;
+        }
+    }
     const T inv = (T)1 / ((T)1 + kap);
 #pragma unroll
-    for (int c = 0; c < D; ++c) un[c] = (accu[c] + kap * (pose_uG<T>(P, c) * C)) * inv;
+    for (int c = 0; c < D; ++c) un[c] = (accu[c] + kap * uS[c]) * inv;
     T uw[D];
     const bool wall = wall_node<T, D>(g, xg, uw);
     if (wall) {

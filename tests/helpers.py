@@ -12,24 +12,27 @@ def oracle_problem(w, **kw):
                   eta=w["eta"], probe_lo=tuple(w["probe_lo"]), probe_hi=tuple(w["probe_hi"]),
                   direction=tuple(w["direction"]), base_center=w.get("base_center"),
                   wall_velocity=dict(w.get("wall_velocity", {})), phi_var=w.get("phi_var", 0.0),
-                  objective=w.get("objective", "J1"), w_D=w.get("w_D", 0.0), drag_span=w.get("drag_span", 1.0))
+                  objective=w.get("objective", "J1"), w_D=w.get("w_D", 0.0), drag_span=w.get("drag_span", 1.0),
+                  R_w=w.get("R_w", 1.0))
     return P
 
 
-def oracle_run(w, gamma, knots, state0=None):
-    """J, dJ/dgamma, dJ/dknots and the final state (p, u) from the oracle (state0: initial (p, u), or the
-    default)."""
+def oracle_run(w, gamma, knots, state0=None, terminal=None):
+    """J, dJ/dgamma, dJ/dknots, the final state (p, u) and lambda_0 from the oracle (state0: initial (p, u), or the
+    default; terminal: (lam_p, lam_u) added to the terminal adjoint state)."""
     P = oracle_problem(w)
     kref, gt, gb = O.design_to_kref(P, gamma)
     s, uG = O.positions(knots, P.Nt, P.R_t)
     J, states = O.forward(P, kref, s, uG, store=True, state0=state0)
-    g_kref, g_s, g_uG = O.adjoint(P, kref, s, uG, states)
+    lam0 = []
+    g_kref, g_s, g_uG = O.adjoint(P, kref, s, uG, states, terminal=terminal, lambda0=lam0)
     g_kr = O.strip_margin(g_kref, P.margin)
     g_gb = g_kr * O.kappa_ref_deriv(gb, P.kappa_max, P.q)
     g_gt = g_gb * O.projection_deriv(gt, P.beta, P.eta)
     g_gamma = O.density_filter_T(g_gt, P.filter_R)
     g_knots = O.knot_gradient(P, g_s, g_uG)
-    return dict(J=J, dgamma=g_gamma, dknots=g_knots, p=states[-1][0], u=states[-1][1], gs=g_s, guG=g_uG)
+    return dict(J=J, dgamma=g_gamma, dknots=g_knots, p=states[-1][0], u=states[-1][1], gs=g_s, guG=g_uG,
+                lam0=lam0[0])
 
 
 def rel_max(a, b):
@@ -56,3 +59,20 @@ def tiny_workload(lattice="D2Q9", **over):
     w.update(over)
     w.setdefault("name", "tiny")
     return w
+
+
+def oracle_run_rot(w, gamma, knots, aknots):
+    """The oracle with a rotating body (angle knots aknots): J, dJ/dgamma, dJ/dknots, dJ/daknots, the final state and
+    the per-step dJ/dtheta_n, dJ/domega_n."""
+    P = oracle_problem(w)
+    kref, gt, gb = O.design_to_kref(P, gamma)
+    s, uG = O.positions(knots, P.Nt, P.R_t)
+    rot = O.angles(aknots, P.Nt, P.R_w)
+    J, states = O.forward(P, kref, s, uG, store=True, rot=rot)
+    g_kref, g_s, g_uG, g_th, g_om = O.adjoint(P, kref, s, uG, states, rot=rot)
+    g_kr = O.strip_margin(g_kref, P.margin)
+    g_gb = g_kr * O.kappa_ref_deriv(gb, P.kappa_max, P.q)
+    g_gt = g_gb * O.projection_deriv(gt, P.beta, P.eta)
+    return dict(J=J, dgamma=O.density_filter_T(g_gt, P.filter_R), dknots=O.knot_gradient(P, g_s, g_uG),
+                daknots=O.angle_gradient(P, g_th, g_om, len(aknots)), p=states[-1][0], u=states[-1][1], gth=g_th,
+                gom=g_om)
