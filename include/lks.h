@@ -295,6 +295,12 @@ int lks_get_adjoint_initial(lks_ctx* ctx, double* lam_p, double* lam_u);
 int lks_set_angle_knots(lks_ctx* ctx, const double* aknots);
 int lks_get_angle_gradient(lks_ctx* ctx, double* dJ_daknots);
 int lks_get_step_angle_sensitivities(lks_ctx* ctx, double* dJ_dtheta, double* dJ_domega);
+/* theta_n and omega_n = theta_n - theta_{n-1} of the last forward ((Nt+1) values each; Eqs. psi_filtered, theta,
+ * omega), and the transposed chain from per-step sensitivities (g_theta, g_omega, (Nt+1) each) to the K_w angle knots
+ * (difference^T, interpolation^T, filter^T): what an optimiser needs for a constraint on omega such as G3 of Eq.
+ * constraint3.  Host pointers, synchronous. */
+int lks_get_angles(lks_ctx* ctx, double* theta, double* omega);
+int lks_angles_T(lks_ctx* ctx, const double* g_theta, const double* g_omega, double* g_aknots);
 
 /* Per-step motion sensitivities of the last adjoint, dJ/ds_n and dJ/du^G_n, each (Nt+1) x d. Synchronous. */
 int lks_get_step_sensitivities(lks_ctx* ctx, double* dJ_ds, double* dJ_duG);

@@ -123,6 +123,8 @@ PROTOTYPES = {
     "lks_set_angle_knots": (C.c_int, [_P, _D]),
     "lks_get_angle_gradient": (C.c_int, [_P, _D]),
     "lks_get_step_angle_sensitivities": (C.c_int, [_P, _D, _D]),
+    "lks_get_angles": (C.c_int, [_P, _D, _D]),
+    "lks_angles_T": (C.c_int, [_P, _D, _D, _D]),
     "lks_set_timing": (C.c_int, [_P, C.c_int]),
     "lks_set_graphs": (C.c_int, [_P, C.c_int]),
     "lks_batch_create": (C.c_int, [C.c_int, C.POINTER(lks_params), C.POINTER(_P)]),

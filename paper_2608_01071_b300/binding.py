@@ -139,6 +139,21 @@ class Solver:
         self._check(self.lib.lks_get_angle_gradient(self.h, _dptr(out)))
         return out
 
+    def angles(self):
+        """(theta_n, omega_n), n = 0..Nt, of the last forward."""
+        th = np.zeros(self.Nt + 1)
+        om = np.zeros(self.Nt + 1)
+        self._check(self.lib.lks_get_angles(self.h, _dptr(th), _dptr(om)))
+        return th, om
+
+    def angles_T(self, g_theta, g_omega):
+        """Per-step sensitivities (g_theta, g_omega) -> gradient with respect to the angle knots."""
+        gt = np.ascontiguousarray(g_theta, dtype=np.float64)
+        go = np.ascontiguousarray(g_omega, dtype=np.float64)
+        out = np.zeros(self.params.K_w)
+        self._check(self.lib.lks_angles_T(self.h, _dptr(gt), _dptr(go), _dptr(out)))
+        return out
+
     def step_angle_sensitivities(self):
         gth = np.zeros(self.Nt + 1)
         gom = np.zeros(self.Nt + 1)

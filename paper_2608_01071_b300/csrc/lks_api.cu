@@ -1930,6 +1930,37 @@ int lks_get_angle_gradient(lks_ctx* c, double* out) {
     });
 }
 
+int lks_get_angles(lks_ctx* c, double* th, double* om) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!c->rot) throw LksError{LKS_EINVAL, "the context has no rotating body (K_w = 0)"};
+        if (!th || !om) throw LksError{LKS_EINVAL, "null pointer"};
+        if (!c->have_final) throw LksError{LKS_ESTATE, "no forward has run"};
+        LKS_CUDA(cudaDeviceSynchronize());
+        LKS_CUDA(cudaMemcpy(th, c->d_theta, (size_t)(c->prm.Nt + 1) * 8, cudaMemcpyDeviceToHost));
+        LKS_CUDA(cudaMemcpy(om, c->d_omega, (size_t)(c->prm.Nt + 1) * 8, cudaMemcpyDeviceToHost));
+    });
+}
+
+int lks_angles_T(lks_ctx* c, const double* gth, const double* gom, double* out) {
+    if (!c) return LKS_EINVAL;
+    return guard(c, [&] {
+        if (!c->rot) throw LksError{LKS_EINVAL, "the context has no rotating body (K_w = 0)"};
+        if (!gth || !gom || !out) throw LksError{LKS_EINVAL, "null pointer"};
+        const int Nt = c->prm.Nt, Kw = c->prm.K_w;
+        DevScratch b;
+        LKS_CUDA(cudaMalloc(&b.p, (size_t)(2 * (Nt + 1) + 2 * Kw) * 8));
+        double *dth = b.p, *dom = b.p + (Nt + 1), *dt = b.p + 2 * (Nt + 1), *dout = dt + Kw;
+        LKS_CUDA(cudaMemcpy(dth, gth, (size_t)(Nt + 1) * 8, cudaMemcpyHostToDevice));
+        LKS_CUDA(cudaMemcpy(dom, gom, (size_t)(Nt + 1) * 8, cudaMemcpyHostToDevice));
+        interp_T_kernel<<<nblk(Kw, 64), 64>>>(c->mgw, dth, dom, dt);
+        LKS_LAUNCHED();
+        motion_filter_kernel<<<nblk(Kw, 64), 64>>>(c->mgw, dt, c->d_anorm, dout, 1);
+        LKS_LAUNCHED();
+        LKS_CUDA(cudaMemcpy(out, dout, (size_t)Kw * 8, cudaMemcpyDeviceToHost));
+    });
+}
+
 int lks_get_step_angle_sensitivities(lks_ctx* c, double* gth, double* gom) {
     if (!c) return LKS_EINVAL;
     return guard(c, [&] {

@@ -120,3 +120,47 @@ def test_fluid_volume_constraint_and_minimisation():
     # the constrained minimiser of |gamma - T|^2 under mean(gamma) = 0.3 is T shifted by a constant
     shift = 0.3 - T.mean()
     assert np.max(np.abs(gamma - np.clip(T + shift, 0.0, 1.0))) <= 0.05
+
+
+def test_angular_speed_constraint_is_enforced():
+    # a model rotating body: omega_n = (M a)_n for angle knots a (M a fixed difference operator), J rewards fast
+    # rotation; G3 (Eq. constraint3) must end near its bound, and its gradient chain is the transpose of M
+    from paper_2608_01071_b300.algorithm1 import angular_speed_bound
+
+    Nt, Kw = 12, 4
+    rng = np.random.default_rng(5)
+    M = rng.uniform(0.0, 1.0, (Nt + 1, Kw)) / Kw
+    M[0] = 0.0
+
+    class Spinner:
+        def objective(self, beta, gamma, knots, aknots):
+            self.a = aknots
+            self.om = M @ aknots
+            return float(self.om[1:].sum())
+
+        def gradient(self):
+            return np.zeros((2, 2)), np.zeros((2, 1)), M[1:].sum(axis=0)
+
+        def angles(self):
+            return np.cumsum(self.om), self.om
+
+        def angles_T(self, g_theta, g_omega):
+            return M.T @ np.asarray(g_omega) + M.T @ np.cumsum(np.asarray(g_theta)[::-1])[::-1]
+
+    # G3 of a constant speed: (Nt |om/om_max|^p)^(1/p) - 1, and its gradient against central differences
+    om = np.full(Nt + 1, 0.02)
+    G3, g = angular_speed_bound(om, 0.01, 8.0)
+    assert abs(G3 - (Nt ** (1 / 8.0) * 2.0 - 1.0)) <= 1e-12
+    h = 1e-7
+    e = np.zeros(Nt + 1)
+    e[3] = h
+    fd = (angular_speed_bound(om + e, 0.01, 8.0)[0] - angular_speed_bound(om - e, 0.01, 8.0)[0]) / (2 * h)
+    assert abs(fd - g[3]) <= 1e-6 * abs(g[3])
+    s = Settings(betas=(1.0,), n_opt=300, omega_max=0.05, p_G3=8.0, ang_step=0.01, tol=0.0)
+    _, _, a, h = run(Spinner(), np.full((2, 2), 0.5), np.zeros((2, 1)), s, aknots=np.zeros(Kw))
+    G3s = [G[0] for G in h.G]
+    assert max(G3s) > 0.0  # the ascent reaches the bound
+    # then the multiplier holds omega at the bound: the first-order update settles into a small limit cycle around it
+    tail = G3s[-100:]
+    assert abs(np.mean(tail)) <= 0.05 and max(tail) <= 0.3
+    assert h.J[-1] > h.J[0]

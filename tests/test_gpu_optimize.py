@@ -50,3 +50,34 @@ def test_algorithm1_on_the_cuda_solver_with_periodic_warm_start():
     assert len(ev.solvers) == 0 and np.all((gamma >= 0.0) & (gamma <= 1.0))
     # the warm start changes the forward: the second J of beta 1 differs from a cold start at the same design
     assert h.J[1] != h.J[0]
+
+
+def test_angular_speed_constraint_from_the_library():
+    # G3 (Eq. constraint3) from the library's omega_n and its chain to the angle knots, against the oracle's
+    # angles and angle_gradient; then a few iterations of the driver with angle knots on the CUDA solver
+    import oracle as O
+    from helpers import oracle_problem, rel_l2, tiny_workload
+    from paper_2608_01071_b300.algorithm1 import Settings, SolverEvaluator, angular_speed_bound, run
+
+    w = tiny_workload("D2Q9", precision="fp64", Nt=24, K_w=5, R_w=8.0, probe_lo=(38, 10), probe_hi=(48, 27))
+    gamma, knots = draw_gamma(w), draw_knots(w)
+    aknots = 0.3 + np.random.default_rng(3).uniform(-0.03, 0.03, 5)
+    ev = SolverEvaluator(w)
+    ev.objective(1.0, gamma, knots, aknots)
+    th, om = ev.angles()
+    P = oracle_problem(w)
+    tho, omo = O.angles(aknots, P.Nt, P.R_w)
+    assert np.max(np.abs(th - tho)) <= 1e-13 and np.max(np.abs(om - omo)) <= 1e-13
+    G3, g = angular_speed_bound(om, 0.002, 8.0)
+    G3o, go = O.angular_speed_bound(omo, 0.002, 8.0)
+    assert abs(G3 - G3o) <= 1e-12 * abs(G3o)
+    da = ev.angles_T(np.zeros_like(g), g)
+    dao = O.angle_gradient(P, np.zeros_like(go), go, 5)
+    assert rel_l2(da, dao) <= 1e-12
+    ev.close()
+    s = Settings(betas=(1.0,), n_opt=4, omega_max=0.002, p_G3=8.0, ang_step=0.005, gamma_step=0.05, pos_step=0.2,
+                 pos_bound=2.0, tol=0.0)
+    ev = SolverEvaluator(w)
+    _, _, a, h = run(ev, gamma, knots, s, aknots=aknots)
+    ev.close()
+    assert len(h.J) == 4 and all(np.isfinite(h.J)) and len(h.G[0]) == 1
