@@ -46,6 +46,7 @@ enum { LKS_FP64 = 0, LKS_FP32 = 1 };                           /* state precisio
 enum { LKS_CKPT_FULL = 0, LKS_CKPT_SQRT = 1, LKS_CKPT_REVOLVE = 2 };
 enum { LKS_MODE_JOINT = 0, LKS_MODE_SHAPE = 1, LKS_MODE_MOTION = 2 };
 enum { LKS_OBJ_FLOW = 0, LKS_OBJ_OAR = 1 };
+enum { LKS_ADJ_DISCRETE = 0, LKS_ADJ_ALKS = 1 };                /* reverse sweep: exact discrete adjoint or Sec. 2.5 */
 
 /*
  * Problem parameters (plain data, versioned by `size`).  Fill with lks_default_params, then set fields.
@@ -102,6 +103,11 @@ enum { LKS_OBJ_FLOW = 0, LKS_OBJ_OAR = 1 };
  *                 rotating body the forward sweep runs step-kernel variant 1 (tile_rows 0 or 1), the footprint box
  *                 on x and y covers the design grid at any angle (it must fit in one period of a periodic axis), and
  *                 the objective must be LKS_OBJ_FLOW.
+ *  adjoint        LKS_ADJ_DISCRETE: the exact discrete adjoint of the forward sweep (the gradient of J as computed).
+ *                 LKS_ADJ_ALKS: the paper's continuous adjoint, the ALKS of Sec. 2.5 (Eqs. ap_tmp-as: adjoint moments
+ *                 p~, u~ and the symmetric s~ carried as state, explicit Brinkman source), an approximation of the
+ *                 gradient; objective LKS_OBJ_FLOW with phi_var = 0 and a translating body only, no adjoint terminal
+ *                 state.
  */
 typedef struct lks_params {
     uint32_t size;
@@ -141,7 +147,7 @@ typedef struct lks_params {
     double w_D;
     double drag_span;
     int32_t K_w;
-    int32_t reserved_rot;
+    int32_t adjoint;
     double R_w;
 } lks_params;
 

@@ -17,6 +17,7 @@ LKS_FP64, LKS_FP32 = 0, 1
 LKS_CKPT_FULL, LKS_CKPT_SQRT, LKS_CKPT_REVOLVE = 0, 1, 2
 LKS_MODE_JOINT, LKS_MODE_SHAPE, LKS_MODE_MOTION = 0, 1, 2
 LKS_OBJ_FLOW, LKS_OBJ_OAR = 0, 1
+LKS_ADJ_DISCRETE, LKS_ADJ_ALKS = 0, 1
 
 
 class lks_params(C.Structure):
@@ -58,7 +59,7 @@ class lks_params(C.Structure):
         ("w_D", C.c_double),
         ("drag_span", C.c_double),
         ("K_w", C.c_int32),
-        ("reserved_rot", C.c_int32),
+        ("adjoint", C.c_int32),
         ("R_w", C.c_double),
     ]
 

@@ -73,6 +73,10 @@ def params_from_workload(w: dict) -> _abi.lks_params:
     p.w_D = w.get("w_D", 0.0)
     p.drag_span = w.get("drag_span", 1.0)
     p.K_w = w.get("K_w", 0)
+    adj = w.get("adjoint", "discrete")
+    if adj not in ("discrete", "alks"):
+        raise ValueError(f"adjoint must be 'discrete' or 'alks', not {adj!r}")
+    p.adjoint = 1 if adj == "alks" else 0
     p.R_w = w.get("R_w", 1.0)
     return p
 

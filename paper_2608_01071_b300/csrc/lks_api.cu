@@ -61,6 +61,8 @@ struct lks_ctx {
     MotionGeom mg;
     MotionGeom mgw;       // rotating body: the angle knots' filter and interpolation (d = 1, radius R_w)
     bool rot = false;     // the body rotates (K_w > 0)
+    bool alks = false;    // the reverse sweep is the ALKS (lks_alks.cuh) instead of the exact discrete adjoint
+    void* alam[2] = {nullptr, nullptr};  // ALKS states (1 + D + D(D+1)/2 fields)
     double rb = 0.0;      // half extent of the rotating body's footprint box on x and y
     int D = 2, hw = 1, cosine = 0;
     double o0[3] = {0, 0, 0};
@@ -218,6 +220,9 @@ void validate(const lks_params* p) {
     if (p->ckpt_slots < 0 || p->seg_len < 0 || p->ckpt_bytes < 0) bad("negative checkpoint setting");
     if (!std::isfinite(p->phi_var)) bad("phi_var must be finite");
     if (p->objective != LKS_OBJ_FLOW && p->objective != LKS_OBJ_OAR) bad("unknown objective");
+    if (p->adjoint != LKS_ADJ_DISCRETE && p->adjoint != LKS_ADJ_ALKS) bad("unknown adjoint");
+    if (p->adjoint == LKS_ADJ_ALKS && (p->objective != LKS_OBJ_FLOW || p->phi_var != 0.0 || p->K_w != 0))
+        bad("the ALKS reverse sweep is built for objective LKS_OBJ_FLOW with phi_var = 0 and a translating body");
     if (p->K_w != 0) {
         if (p->K_w < 2 || p->K_w > 1000000) bad("K_w must be 0 (no rotation) or >= 2 angle knots");
         if (!(p->R_w > 0.0)) bad("R_w must be > 0 with a rotating body");
@@ -311,6 +316,7 @@ void setup_geometry(lks_ctx* c) {
     c->mg.Nt = p.Nt;
     c->mg.R_t = p.R_t;
     c->rot = p.K_w > 0;
+    c->alks = p.adjoint == LKS_ADJ_ALKS;
     g.rot = c->rot ? 1 : 0;
     if (c->rot) {
         // footprint box on x and y: the design grid's circumscribed circle around x^G plus the kernel's half width
@@ -762,6 +768,11 @@ void allocate(lks_ctx* c) {
     c->fin = dalloc(c, sb);
     c->lam[0] = dalloc(c, sb);
     c->lam[1] = dalloc(c, sb);
+    if (c->alks) {
+        const size_t ab = (size_t)(1 + D + D * (D + 1) / 2) * N * ts;
+        c->alam[0] = dalloc(c, ab);
+        c->alam[1] = dalloc(c, ab);
+    }
     c->stats.ckpt_slots = (int32_t)c->slot.size();
     c->stats.seg_len = c->S;
 
@@ -1121,9 +1132,23 @@ void recompute_segment(lks_ctx* c, int a, int b, const void* start, const void* 
 
 // Adjoint steps n = b..a+1 of a segment whose states were laid out by recompute_segment(buf); each step also
 // records lam_u and u_n on the footprint box into box buffer `buf` for sens_segment.
+void alks_launch(lks_ctx* c, bool init, const void* lam_in, void* lam_out, const void* cur, int n, void* boxbuf, int src,
+                 cudaStream_t s);
+
 void adjoint_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
     const std::vector<const void*>& st = c->seg_st[buf];
     cudaEvent_t ea = span_begin(c, s);
+    if (c->alks) {  // the ALKS: one step kernel per step, with the flow state of the same step
+        for (int n = b; n > a; --n) {
+            void* bb = c->tptr(c->d_boxbuf, ((long long)buf * c->Lmax + (n - a - 1)) * c->box_step);
+            alks_launch(c, false, c->alam[0], c->alam[1], st[n - a], n, bb, n - 1 >= 1 ? 1 : 0, s);
+            std::swap(c->alam[0], c->alam[1]);
+            c->stats.adjoint_steps++;
+            c->launches++;
+        }
+        span_end(c, 2, ea, s);
+        return;
+    }
     // 1 / (1 + kappa) on the footprint box for every step of the segment, in one launch
     if (c->rot)
         c->eng->rot_box_fac(c->g, c->d_pose, c->d_kref, a + 1, b - a,
@@ -1190,7 +1215,7 @@ void sens_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
         return;
     }
     c->eng->sens(c->g, c->d_pose, c->d_kref, bb, c->box_step, a + 1, L, shape ? c->d_kbar : nullptr,
-                 motion ? c->d_mslot : nullptr, s);
+                 motion ? c->d_mslot : nullptr, c->alks, s);
     c->launches++;
     if (c->oar) {
         c->eng->oar_sens(c->g, c->ogeo, c->d_pose, c->d_kref, bb, c->box_step, a + 1, L, shape ? c->d_kbar : nullptr,
@@ -1293,7 +1318,7 @@ void run_adjoint(lks_ctx* c, cudaStream_t s) {
     // no wait for the forward's stability flag here: the reverse sweep is enqueued behind it, and an unstable forward
     // is reported by lks_get_status, by lks_adjoint (host pointers) and as NaN gradients of lks_adjoint_dev
     run_graph(c, c->gx_adj, s, [&](cudaStream_t cs) { adjoint_body(c, cs); });
-    c->have_lambda0 = true;
+    c->have_lambda0 = !c->alks;  // the ALKS state at n = 0 is not the gradient with respect to the initial state
     if (!c->use_graphs) c->spans_adj = c->spans;
     // the binomial schedule reuses the forward's checkpoint slots: a new forward must precede the next adjoint
     if (c->prm.ckpt == LKS_CKPT_REVOLVE) c->have_forward = false;
@@ -1313,7 +1338,10 @@ void adjoint_body(lks_ctx* c, cudaStream_t s) {
         LKS_CUDA(cudaMemsetAsync(c->d_gth, 0, (size_t)(Nt + 1) * 8, s));
         LKS_CUDA(cudaMemsetAsync(c->d_gom, 0, (size_t)(Nt + 1) * 8, s));
     }
-    c->eng->init_adjoint(c->g, c->fin, c->lam[0], c->oar ? 0 : 1, s);
+    if (c->alks)
+        alks_launch(c, true, nullptr, c->alam[0], nullptr, Nt, nullptr, 1, s);
+    else
+        c->eng->init_adjoint(c->g, c->fin, c->lam[0], c->oar ? 0 : 1, s);
     c->launches++;
     if (c->custom_lterm) {  // the adjoint half of the periodic approximation (Sec. 3.3)
         c->eng->add_state(c->g, c->lam[0], c->d_lterm, s);
@@ -1399,6 +1427,36 @@ void finish_adjoint(lks_ctx* c, double* dgamma, double* dpos, cudaStream_t s) {
         c->stats.ms_recompute_steps = acc[1];
         c->stats.ms_adjoint_steps = acc[2];
         c->stats.ms_total = tot;
+    }
+}
+
+// Arguments of the ALKS kernels in the engine's state precision (lam_in, lam_out: ALKS states; cur: flow state n).
+template <typename T>
+AlksArgs<T> make_alks_args(const lks_ctx* c, const void* lam_in, void* lam_out, const void* cur, int n, void* boxbuf,
+                           int src) {
+    AlksArgs<T> a;
+    a.lam_in = (const T*)lam_in;
+    a.lam_out = (T*)lam_out;
+    a.u_cur = cur ? (const T*)cur + c->g.N : nullptr;
+    a.kref = (const T*)c->d_kref;
+    a.pose_n = c->d_pose + n;
+    a.pose_m = c->d_pose + (n > 0 ? n - 1 : 0);
+    a.boxbuf = (T*)boxbuf;
+    a.src = src;
+    for (int i = 0; i < 3; ++i) a.phi_dir3[i] = (T)(c->g.dir[i] * c->g.phi / 3.0);
+    return a;
+}
+
+void alks_launch(lks_ctx* c, bool init, const void* lam_in, void* lam_out, const void* cur, int n, void* boxbuf, int src,
+                 cudaStream_t s) {
+    if (c->tsize == 4) {
+        const AlksArgs<float> a = make_alks_args<float>(c, lam_in, lam_out, cur, n, boxbuf, src);
+        if (init) c->eng->alks_init(c->g, c->d_pose + n, c->d_kref, lam_out, &a, s);
+        else c->eng->alks_step(c->g, &a, s);
+    } else {
+        const AlksArgs<double> a = make_alks_args<double>(c, lam_in, lam_out, cur, n, boxbuf, src);
+        if (init) c->eng->alks_init(c->g, c->d_pose + n, c->d_kref, lam_out, &a, s);
+        else c->eng->alks_step(c->g, &a, s);
     }
 }
 
@@ -1877,6 +1935,7 @@ int lks_set_adjoint_terminal(lks_ctx* c, const double* lp, const double* lu) {
     if (!c) return LKS_EINVAL;
     return guard(c, [&] {
         if ((lp == nullptr) != (lu == nullptr)) throw LksError{LKS_EINVAL, "lam_p and lam_u must both be given or both NULL"};
+        if (c->alks && lp) throw LksError{LKS_EINVAL, "the ALKS reverse sweep takes no terminal adjoint state"};
         drop_graphs(c);  // the captured reverse sweep starts from the previous terminal state
         c->have_forward = false;
         if (!lp) {

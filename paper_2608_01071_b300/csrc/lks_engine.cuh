@@ -14,6 +14,7 @@
 #include "lks_step_kernels.cuh"
 #include "lks_oar.cuh"
 #include "lks_rot.cuh"
+#include "lks_alks.cuh"
 
 namespace lks {
 
@@ -88,7 +89,12 @@ struct Engine {
     virtual void box_fac(const Geom& g, const Pose* poses, const void* kref, int n_first, int nsteps, void* out,
                          cudaStream_t s) = 0;
     virtual void sens(const Geom& g, const Pose* poses, const void* kref, const void* boxbuf, long long bstride,
-                      int n_first, int nsteps, void* kbar, double* mslot, cudaStream_t s) = 0;
+                      int n_first, int nsteps, void* kbar, double* mslot, bool alks, cudaStream_t s) = 0;
+    // the ALKS reverse sweep (lks_alks.cuh): terminal state and one step; the pointers of AlksArgs are in the state
+    // precision of the engine
+    virtual void alks_init(const Geom& g, const Pose* pose, const void* kref, void* lam, const void* args,
+                           cudaStream_t s) = 0;
+    virtual void alks_step(const Geom& g, const void* args, cudaStream_t s) = 0;
     virtual void gather(const Geom& g, const Pose* poses, const void* kbar, int n_first, int nsteps,
                         long long kstride, double* dkref, cudaStream_t s) = 0;
     virtual void kappa_ref(const DesignGeom& dg, const double* gt, double* gb, double* k64, void* k, cudaStream_t s) = 0;
@@ -171,11 +177,37 @@ struct EngineCommon : Engine {
         LKS_LAUNCHED();
     }
     void sens(const Geom& g, const Pose* poses, const void* kref, const void* boxbuf, long long bstride, int n_first,
-              int nsteps, void* kbar, double* mslot, cudaStream_t s) override {
+              int nsteps, void* kbar, double* mslot, bool alks, cudaStream_t s) override {
         const dim3 grid(nblk(g.Fbn, 256), nsteps, 1);
-        adj_sens_kernel<T, D, HW><<<grid, 256, 0, s>>>(g, poses, (const T*)kref, (const T*)boxbuf, bstride, n_first,
-                                                       (T*)kbar, mslot);
+        if (alks)
+            adj_sens_kernel<T, D, HW, true><<<grid, 256, 0, s>>>(g, poses, (const T*)kref, (const T*)boxbuf, bstride,
+                                                                 n_first, (T*)kbar, mslot);
+        else
+            adj_sens_kernel<T, D, HW><<<grid, 256, 0, s>>>(g, poses, (const T*)kref, (const T*)boxbuf, bstride, n_first,
+                                                           (T*)kbar, mslot);
         LKS_LAUNCHED();
+    }
+    // ALKS tiles: 32 x 8 nodes in 2D, 32 x 4 x 4 in 3D
+    static constexpr int ATX = 32, ATY = D == 2 ? 8 : 4, ATZ = D == 2 ? 1 : 4;
+    static constexpr size_t alks_smem() {
+        using TL = Tile<D, ATX, ATY, ATZ>;
+        return sizeof(T) * (AlksState<D>::NS * TL::S + (1 + D) * TL::M);
+    }
+    void alks_init(const Geom& g, const Pose* pose, const void* kref, void* lam, const void* args,
+                   cudaStream_t s) override {
+        alks_init_kernel<T, D, HW><<<nblk(g.N, 256), 256, 0, s>>>(g, pose, (const T*)kref, (T*)lam,
+                                                                  *(const AlksArgs<T>*)args);
+        LKS_LAUNCHED();
+    }
+    // called by the engines' constructors (the tiles' shared memory exceeds the default limit)
+    void alks_attr() {
+        LKS_CUDA(cudaFuncSetAttribute(alks_step_kernel<T, D, HW, ATX, ATY, ATZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)alks_smem()));
+    }
+    void alks_step(const Geom& g, const void* args, cudaStream_t s) override {
+        const dim3 grid(nblk(g.n[0], ATX), nblk(g.n[1], ATY), nblk(g.n[2], ATZ));
+        launch_pdl(alks_step_kernel<T, D, HW, ATX, ATY, ATZ>, grid, dim3(ATX, ATY, ATZ), alks_smem(), s, this->pdl, g,
+                   *(const AlksArgs<T>*)args);
     }
     void gather(const Geom& g, const Pose* poses, const void* kbar, int n_first, int nsteps, long long kstride,
                 double* dkref, cudaStream_t s) override {

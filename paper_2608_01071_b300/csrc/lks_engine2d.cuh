@@ -24,6 +24,7 @@ struct Engine2D : EngineCommon<T, 2, HW> {
         LKS_CUDA(cudaFuncSetAttribute(fwd2r_kernel<T, HW, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_fwd<T, 2>()));
         LKS_CUDA(cudaFuncSetAttribute(adj2r_kernel<T, HW, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_adj<T, 1>()));
         LKS_CUDA(cudaFuncSetAttribute(adj2r_kernel<T, HW, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_adj<T, 2>()));
+        this->alks_attr();
         set_rows(1, 1, g);
     }
     static void geom(int r, const Geom& g, dim3& th, dim3& tile, dim3& grid) {

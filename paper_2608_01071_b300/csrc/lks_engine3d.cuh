@@ -53,6 +53,7 @@ struct Engine3D : EngineCommon<T, 3, HW> {
             LKS_CUDA(cudaFuncSetAttribute(adj3p_kernel<HW, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa));
             LKS_CUDA(cudaFuncSetAttribute(adj3p_kernel<HW, 32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa));
         }
+        this->alks_attr();
         set_rows(8, 8, g);
     }
     // the plane-pair kernels exist for the FP32 state only

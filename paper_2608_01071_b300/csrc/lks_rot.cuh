@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(256) rot_sens_kernel(Geom g, const Pose* __res
 }
 
 // Transposed mapping on the design side (b4): dJ/dkappa^ref_j += sum_x W(x, x^ref_j(n)) kappa-bar_n(x), over the
-// steps of a segment in order (fixed summation order, no atomics).  The nodes x around x^ref_j are the 2 hw taps per
+// steps of a segment (fixed summation order, no atomics).  The nodes x around x^ref_j are the 2 hw taps per
 // axis in box coordinates: x-y around cg + R arm_j, z the translation taps.
 template <typename T, int D, int HW>
 __global__ void rot_gather_kernel(Geom g, const Pose* __restrict__ poses, const T* __restrict__ kbar, int n_first,
@@ -296,8 +296,10 @@ __global__ void rot_gather_kernel(Geom g, const Pose* __restrict__ poses, const 
     if (j >= nde) return;
     const int jx = (int)(j % g.nde[0]), jy = (int)((j / g.nde[0]) % g.nde[1]), jz = (int)(j / ((long long)g.nde[0] * g.nde[1]));
     const T ax = (T)jx - (T)(0.5 * (g.nde[0] - 1)), ay = (T)jy - (T)(0.5 * (g.nde[1] - 1));
+    // running FP64 sum in strict step order n = Nt..1 across calls, as in design_gather_kernel, so that the
+    // segmentation of the reverse sweep cannot change the rounding
     double acc = dkref[j];
-    for (int st = 0; st < nsteps; ++st) {
+    for (int st = nsteps - 1; st >= 0; --st) {
         const Pose& P = poses[n_first + st];
         const T c = pose_cos<T>(P), s = pose_sin<T>(P);
         const T cx = pose_cg<T>(P, 0) + (c * ax - s * ay), cy = pose_cg<T>(P, 1) + (s * ax + c * ay);

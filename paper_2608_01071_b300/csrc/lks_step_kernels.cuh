@@ -602,7 +602,9 @@ __global__ void __launch_bounds__(TX * TY * TZ) adj_step_kernel(Geom g, AdjArgs<
 // kappa-bar goes to kbar[s][box node] (for design_gather_kernel); the motion terms are summed per block
 // (FP32 within a warp, FP64 across warps) into mslot[s][block][2D].
 // ------------------------------------------------------------------------------------------------
-template <typename T, int D, int HW>
+// With ALKS set the records hold the ALKS adjoint velocity u~ (lks_alks.cuh) and the sensitivities are its forms
+// kappa-bar = 3 (u_n - u^S) . u~, u^S-bar = -3 kappa u~.
+template <typename T, int D, int HW, bool ALKS = false>
 __global__ void __launch_bounds__(256) adj_sens_kernel(Geom g, const Pose* __restrict__ poses, const T* __restrict__ kref,
                                                        const T* __restrict__ boxbuf, long long bstride, int n_first,
                                                        T* __restrict__ kbar, double* __restrict__ mslot) {
@@ -633,11 +635,16 @@ __global__ void __launch_bounds__(256) adj_sens_kernel(Geom g, const Pose* __res
             for (int c = 0; c < D; ++c) {
                 const T lu = bb[c * g.Fbn + bl];
                 const T uG = pose_uG<T>(P, c);
-                kb += lu * (uG * C - bb[(D + c) * g.Fbn + bl]);
-                usb[c] = lu * kap * inv;
+                if (ALKS) {
+                    kb += lu * (bb[(D + c) * g.Fbn + bl] - uG * C);
+                    usb[c] = (T)-3 * kap * lu;
+                } else {
+                    kb += lu * (uG * C - bb[(D + c) * g.Fbn + bl]);
+                    usb[c] = lu * kap * inv;
+                }
                 cbar += usb[c] * uG;
             }
-            kb *= inv;
+            kb *= ALKS ? (T)3 : inv;
             if (kbar != nullptr) kbar[(long long)s * g.Fbn + bl] = kb;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
