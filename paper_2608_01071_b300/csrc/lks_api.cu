@@ -433,7 +433,7 @@ std::string tune_key(const lks_ctx* c, int dev) {
     for (char& ch : name)
         if (ch == ' ' || ch == '\t') ch = '_';
     char buf[256];
-    std::snprintf(buf, sizeof(buf), "v%d|%s|sm%d%d|t%d|hw%d|d%d|rot%d|%dx%dx%d", LKS_ABI_VERSION * 100 + 3, name.c_str(),
+    std::snprintf(buf, sizeof(buf), "v%d|%s|sm%d%d|t%d|hw%d|d%d|rot%d|%dx%dx%d", LKS_ABI_VERSION * 100 + 4, name.c_str(),
                   prop.major, prop.minor, (int)c->tsize, c->hw, c->D, c->rot ? 1 : 0, c->g.n[0], c->g.n[1], c->g.n[2]);
     return buf;
 }

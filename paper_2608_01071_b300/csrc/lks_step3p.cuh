@@ -1,17 +1,23 @@
 // D3Q15 forward step on plane pairs with packed FP32x2 arithmetic (FP32 state only).
 //
-// Same separable algebra as fwd3s_kernel (the streamed moments of Eqs. p_tmp, u_tmp as sums and differences over the
-// in-plane diagonal neighbours of the fields Q = sigma + tr T, T_xy, T_xz, T_yz and u, plus the face terms), but a
-// block marches its columns two planes at a time: the fields of planes k and k+1 are computed together, one FP32x2
-// instruction for both, and stored interleaved in shared memory as float2, so that one 8-byte shared load feeds the
-// same stencil position of both planes.  Only the coupling along z between the planes of a pair and the neighbouring
-// pairs is done in scalar arithmetic (a few additions per node).  Raw planes (p', u) arrive by 16-byte asynchronous
-// copies (4-byte copies when n_x is not a multiple of 4) into a ring of three plane pairs, one pair ahead of use.
+// The streamed moments of Eqs. p_tmp, u_tmp gather f_i^eq(x - c_i).  For the eight diagonal directions
+// c = (sx, sy, sz) the equilibrium at a node splits into an in-plane part and a z part,
+//   f^eq_c = w_c [F(sx, sy) + sz G(sx, sy)],  F = Q + 3 (sx u_x + sy u_y) + 2 sx sy T_xy,  G = 3 u_z + 2 (sx T_xz + sy T_yz)
+// (Q = sigma + tr T), and for the in-plane faces f^eq_(sx,0,0) = w_f (P_x + 3 sx u_x) (P_x = sigma + T_xx), likewise
+// in y.  Each node therefore evaluates, once, the value it emits to each in-plane diagonal neighbour, for the plane
+// above and below (H+-(sx, sy) = w_c (F +- G), eight values) and to its four in-plane face neighbours (four values);
+// a receiving node sums one value from each neighbour, with the signs of c for the momentum.  A block marches its
+// columns two planes at a time: these values for planes k and k+1 are computed together, one FP32x2 instruction for
+// both, and stored interleaved in shared memory as float2, so that one 8-byte shared load feeds the same stencil
+// position of both planes.  Only the coupling along z between the planes of a pair and the neighbouring pairs is done
+// in scalar arithmetic (a few additions per node).  Raw planes (p', u) arrive by 16-byte asynchronous copies (4-byte
+// copies when n_x is not a multiple of 4) into a ring of two plane pairs; the next pair is fetched while the
+// current one is being summed.
 //
 // Per iteration j the block holds the raw planes k-1 .. k+2 (k = z0 - 1 + 2j) and
-//   (A) evaluates the fields of planes k, k+1 on the halo-1 region (each thread its own column and at most one node
-//       of the halo-1 ring),
-//   (B) forms, for its own column, the in-plane sums and the emissions of planes k, k+1 to their z-neighbours, which
+//   (A) evaluates the emitted values of planes k, k+1 on the halo-1 region (each thread its own column and at most
+//       one node of the halo-1 ring),
+//   (B) sums, for its own column, the in-plane values and the emissions of planes k, k+1 to their z-neighbours, which
 //       completes the moments of planes k-1 and k; Brinkman (Eqs. p, u), walls and the stores follow.
 // Planes z0 - 1 .. z0 + ZB are evaluated for the ZB output planes z0 .. z0 + ZB - 1.
 #pragma once
@@ -32,13 +38,13 @@ struct Pair3 {
     static constexpr int PERCH = (NCH + NT - 1) / NT;
     static constexpr int NEL = 4 * RS;                            // elements of one raw plane
     static constexpr int PEREL = (NEL + NT - 1) / NT;
-    static constexpr int NFLD = 9;  // float2 field arrays: Q, T_xy, T_xz, T_yz, P_x = sigma + T_xx, P_y, u_x, u_y, u_z
+    static constexpr int NFLD = 12;  // float2 arrays: H+(sx, sy), H-(sx, sy) for the four (sx, sy), then E_x+, E_x-, E_y+, E_y-
     static_assert(NR <= NT, "one ring node per thread at most");
     static_assert(Sep3<TY>::MX == MX && Sep3<TY>::MY == MY, "ring_node layout");
 };
 
 __host__ __device__ constexpr size_t smem3p_fwd() {
-    return sizeof(float) * 6 * 4 * Pair3::RS + sizeof(float2) * (Pair3::NFLD * Pair3::NM + 2 * Pair3::NT);
+    return sizeof(float) * 4 * 4 * Pair3::RS + sizeof(float2) * Pair3::NFLD * Pair3::NM;
 }
 
 // Packed FP32x2 arithmetic (one instruction for both planes; rounding as the scalar instructions; a - b = fma(b, -1, a)).
@@ -127,19 +133,15 @@ __global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<flo
     constexpr int NP = ZB / 2 + 1;  // iterations (field-plane pairs)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[2 * (R::NT / 32)];
-    float* raw = reinterpret_cast<float*>(smem_raw);                      // [6 planes][p', u_x, u_y, u_z][RS]
-    float2* fld = reinterpret_cast<float2*>(raw + 6 * 4 * R::RS);         // [NFLD][NM]
-    float2* fQ = fld;
-    float2* fXY = fld + R::NM;
-    float2* fXZ = fld + 2 * R::NM;
-    float2* fYZ = fld + 3 * R::NM;
-    float2* fPX = fld + 4 * R::NM;
-    float2* fPY = fld + 5 * R::NM;
-    float2* fUX = fld + 6 * R::NM;
-    float2* fUY = fld + 7 * R::NM;
-    float2* fUZ = fld + 8 * R::NM;
-    float2* fS0 = fld + 9 * R::NM;  // [NT]: sigma of the own column
-    float2* fZ0 = fS0 + R::NT;      // [NT]: sigma + T_zz of the own column
+    float* raw = reinterpret_cast<float*>(smem_raw);                      // [4 planes][p', u_x, u_y, u_z][RS]
+    float2* fld = reinterpret_cast<float2*>(raw + 4 * 4 * R::RS);         // [NFLD][NM]
+    // emitted values: hp[s] = H+ and hm[s] = H- for (sx, sy) = (+,+), (-,+), (+,-), (-,-) (s = 0 .. 3), i.e. for the
+    // receivers at (x + 1, y + 1), (x - 1, y + 1), (x + 1, y - 1), (x - 1, y - 1); ex[0] = E_x+ (receiver x + 1),
+    // ex[1] = E_x- (receiver x - 1), ey likewise in y
+    float2* hp = fld;
+    float2* hm = fld + 4 * R::NM;
+    float2* ex = fld + 8 * R::NM;
+    float2* ey = fld + 10 * R::NM;
 
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int N = (int)g.N;  // 32-bit indexing: these kernels run only when 4 N < 2^31
@@ -167,8 +169,8 @@ __global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<flo
             }
         }
     }
-    // raw plane k goes to ring slot (k - z0 + 2) mod 6
-    auto slot = [&](int k) -> float* { return raw + ((k - z0 + 2) % 6) * 4 * R::RS; };
+    // raw plane k goes to ring slot (k - z0 + 2) mod 4
+    auto slot = [&](int k) -> float* { return raw + ((k - z0 + 2) & 3) * 4 * R::RS; };
     auto issue = [&](int k) {
         float* dst = slot(k);
         const float* src = a.in + plane * wrap(k, nz);
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<flo
     const bool colbox = col && bx >= 0 && by >= 0;
     const int xs2 = P.xs[2];
     const float uG0 = P.uGf[0], uG1 = P.uGf[1], uG2 = P.uGf[2];
-    const float2 c3 = f2s(3.f), c2 = f2s(2.f), cA = f2s(A), chA = f2s(0.5f * A), c45 = f2s(4.5f), cm15 = f2s(-1.5f);
+    const float2 c3 = f2s(3.f), c9 = f2s(9.f), cA = f2s(A), c45 = f2s(4.5f), cm15 = f2s(-1.5f);
     const float2 w0 = f2s(2.f / 9.f), wf = f2s(1.f / 9.f), wc = f2s(1.f / 72.f);
 
     pdl_wait_then_release();
@@ -221,6 +223,8 @@ __global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<flo
     // plane k (the previous pair's second plane) to plane k+1 (dnB); components p*, u*_x, u*_y, u*_z
     float accA[4] = {0.f, 0.f, 0.f, 0.f}, dnB[4] = {0.f, 0.f, 0.f, 0.f};
     bool unstable = false;
+    // own-column values of the current pair, kept from (A) for (B): sigma, sigma + T_zz, 3 u_z
+    float2 sig0 = f2s(0.f), pz0 = f2s(0.f), uz0 = f2s(0.f);
 
     // wall planes of the column's x and y (Sec. 2.2 reading: where wall planes meet, the later axis' velocity wins);
     // the wall velocities are read only at wall nodes
@@ -272,20 +276,14 @@ __global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<flo
 
 #pragma unroll 1
     for (int j = 0; j < NP; ++j) {
-        // raw pair j + 2 into the slots of pair j - 1 (read in phase A of the previous iteration, before its barrier);
-        // pair j + 1 has arrived once at most the newest group is pending
-        if (j + 2 <= NP)
-            issue_pair(j + 2);
-        else
-            cp_async_commit();
-        cp_async_wait<1>();
+        cp_async_wait<0>();  // raw pair j + 1 (this thread's copies; pair j arrived one iteration earlier)
         __syncthreads();
         const int k = z0 - 1 + 2 * j;
         const float* pm = slot(k - 1);
         const float* p0 = slot(k);
         const float* p1 = slot(k + 1);
         const float* p2 = slot(k + 2);
-        // (A) fields of planes k, k+1 at the field nodes
+        // (A) emitted values of planes k, k+1 at the field nodes
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             if (s == 1 && !has1) break;
@@ -307,86 +305,61 @@ __global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<flo
             const float2 Txx = f2fma(c45, f2mul(U[0], U[0]), f2mul(cA, Gx[0]));
             const float2 Tyy = f2fma(c45, f2mul(U[1], U[1]), f2mul(cA, Gy[1]));
             const float2 Tzz = f2fma(c45, f2mul(U[2], U[2]), f2mul(cA, Gz[2]));
-            const float2 Txy = f2fma(c45, f2mul(U[0], U[1]), f2mul(chA, f2add(Gx[1], Gy[0])));
-            const float2 Txz = f2fma(c45, f2mul(U[0], U[2]), f2mul(chA, f2add(Gx[2], Gz[0])));
-            const float2 Tyz = f2fma(c45, f2mul(U[1], U[2]), f2mul(chA, f2add(Gy[2], Gz[1])));
-            const int m = mrow[s];
+            // twice the off-diagonal T
+            const float2 Txy2 = f2fma(c9, f2mul(U[0], U[1]), f2mul(cA, f2add(Gx[1], Gy[0])));
+            const float2 Txz2 = f2fma(c9, f2mul(U[0], U[2]), f2mul(cA, f2add(Gx[2], Gz[0])));
+            const float2 Tyz2 = f2fma(c9, f2mul(U[1], U[2]), f2mul(cA, f2add(Gy[2], Gz[1])));
             const float2 px = f2add(sig, Txx), py = f2add(sig, Tyy);
-            fQ[m] = f2add(f2add(px, Tyy), Tzz);
-            fXY[m] = Txy;
-            fXZ[m] = Txz;
-            fYZ[m] = Tyz;
-            fPX[m] = px;
-            fPY[m] = py;
-            fUX[m] = U[0];
-            fUY[m] = U[1];
-            fUZ[m] = U[2];
-            if (s == 0) {  // sigma and sigma + T_zz of the own column, for (B)
-                fS0[tid] = sig;
-                fZ0[tid] = f2add(sig, Tzz);
+            const float2 Q = f2add(f2add(px, Tyy), Tzz);
+            // F(sx, sy) = Q + 3 (sx u_x + sy u_y) + 2 sx sy T_xy,  G(sx, sy) = 3 u_z + 2 (sx T_xz + sy T_yz)
+            const float2 t1 = f2add(Q, Txy2), t2 = f2sub(Q, Txy2);
+            const float2 v1 = f2mul(c3, f2add(U[0], U[1])), v2 = f2mul(c3, f2sub(U[0], U[1]));
+            const float2 uz3 = f2mul(c3, U[2]);
+            const float2 g1 = f2add(Txz2, Tyz2), g2 = f2sub(Txz2, Tyz2);
+            const float2 F[4] = {f2add(t1, v1), f2sub(t2, v2), f2add(t2, v2), f2sub(t1, v1)};
+            const float2 G[4] = {f2add(uz3, g1), f2sub(uz3, g2), f2add(uz3, g2), f2sub(uz3, g1)};
+            const int m = mrow[s];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                hp[q * R::NM + m] = f2mul(wc, f2add(F[q], G[q]));
+                hm[q * R::NM + m] = f2mul(wc, f2sub(F[q], G[q]));
+            }
+            const float2 ux3 = f2mul(c3, U[0]), uy3 = f2mul(c3, U[1]);
+            ex[m] = f2mul(wf, f2add(px, ux3));
+            ex[R::NM + m] = f2mul(wf, f2sub(px, ux3));
+            ey[m] = f2mul(wf, f2add(py, uy3));
+            ey[R::NM + m] = f2mul(wf, f2sub(py, uy3));
+            if (s == 0) {  // the own column, for (B)
+                sig0 = sig;
+                pz0 = f2add(sig, Tzz);
+                uz0 = uz3;
             }
         }
         __syncthreads();
-        // (B) in-plane sums and z emissions of planes k, k+1 along this thread's column
+        // raw pair j + 2 into the slots of pair j, read for the last time in (A) above
+        if (j + 2 <= NP) issue_pair(j + 2);
+        // (B) sums of the emitted values at this thread's column
         {
             const int m = mrow[0];
-            // S/D products over the four diagonal in-plane neighbours (x-1, y-1), (x+1, y-1), (x-1, y+1), (x+1, y+1):
-            // S g = g(-1) + g(+1), D g = g(-1) - g(+1) along x (first letter) and y (second letter)
-            auto sd4 = [&](const float2* f, float2& SS, float2& DS, float2& SD, float2& DD) {
-                const float2 va = f[m - 1 - R::MX], vb = f[m + 1 - R::MX], vc = f[m - 1 + R::MX], vd = f[m + 1 + R::MX];
-                const float2 s1 = f2add(va, vb), s2 = f2add(vc, vd), d1 = f2sub(va, vb), d2 = f2sub(vc, vd);
-                SS = f2add(s1, s2);
-                SD = f2sub(s1, s2);
-                DS = f2add(d1, d2);
-                DD = f2sub(d1, d2);
+            // receivers at (x, y) take H(+,+) from (x-1, y-1), H(-,+) from (x+1, y-1), H(+,-) from (x-1, y+1) and
+            // H(-,-) from (x+1, y+1): sum, and the x and y first moments with the signs of c
+            auto gather = [&](const float2* h, float2& S, float2& Dx, float2& Dy) {
+                const float2 va = h[m - 1 - R::MX], vb = h[R::NM + m + 1 - R::MX], vc = h[2 * R::NM + m - 1 + R::MX],
+                             vd = h[3 * R::NM + m + 1 + R::MX];
+                const float2 s1 = f2add(va, vb), s2 = f2add(vc, vd);
+                S = f2add(s1, s2);
+                Dy = f2sub(s1, s2);
+                Dx = f2add(f2sub(va, vb), f2sub(vc, vd));
             };
-            // A1 = Q_SS + 3 (ux_DS + uy_SD) + 2 Txy_DD,  A2 = 3 uz_SS + 2 (Txz_DS + Tyz_SD),
-            // B1 = Q_DS + 3 (ux_SS + uy_DD) + 2 Txy_SD,  B2 = 3 uz_DS + 2 (Txz_SS + Tyz_DD),
-            // C1 = Q_SD + 3 (ux_DD + uy_SS) + 2 Txy_DS,  C2 = 3 uz_SD + 2 (Txz_DD + Tyz_SS),
-            // accumulated field by field so that only one field's products are live at a time
-            float2 A1, A2, B1, B2, C1, C2, SS, DS, SD, DD;
-            sd4(fQ, SS, DS, SD, DD);
-            A1 = SS;
-            B1 = DS;
-            C1 = SD;
-            sd4(fUX, SS, DS, SD, DD);
-            A1 = f2fma(c3, DS, A1);
-            B1 = f2fma(c3, SS, B1);
-            C1 = f2fma(c3, DD, C1);
-            sd4(fUY, SS, DS, SD, DD);
-            A1 = f2fma(c3, SD, A1);
-            B1 = f2fma(c3, DD, B1);
-            C1 = f2fma(c3, SS, C1);
-            sd4(fXY, SS, DS, SD, DD);
-            A1 = f2fma(c2, DD, A1);
-            B1 = f2fma(c2, SD, B1);
-            C1 = f2fma(c2, DS, C1);
-            sd4(fUZ, SS, DS, SD, DD);
-            A2 = f2mul(c3, SS);
-            B2 = f2mul(c3, DS);
-            C2 = f2mul(c3, SD);
-            sd4(fXZ, SS, DS, SD, DD);
-            A2 = f2fma(c2, DS, A2);
-            B2 = f2fma(c2, SS, B2);
-            C2 = f2fma(c2, DD, C2);
-            sd4(fYZ, SS, DS, SD, DD);
-            A2 = f2fma(c2, SD, A2);
-            B2 = f2fma(c2, DD, B2);
-            C2 = f2fma(c2, SS, C2);
-            // face terms: in-plane x and y, and z from the column's own fields
-            const float2 sig0 = fS0[tid], pz0 = fZ0[tid], uz0 = fUZ[m];
-            const float2 pxm = fPX[m - 1], pxp = fPX[m + 1], pym = fPY[m - R::MX], pyp = fPY[m + R::MX];
-            const float2 uxm = fUX[m - 1], uxp = fUX[m + 1], uym = fUY[m - R::MX], uyp = fUY[m + R::MX];
-            const float2 inP = f2fma(w0, sig0, f2mul(wf, f2add(f2add(f2add(pxm, pxp), f2add(pym, pyp)),
-                                                               f2mul(c3, f2add(f2sub(uxm, uxp), f2sub(uym, uyp))))));
-            const float2 inX = f2mul(wf, f2fma(c3, f2add(uxm, uxp), f2sub(pxm, pxp)));
-            const float2 inY = f2mul(wf, f2fma(c3, f2add(uym, uyp), f2sub(pym, pyp)));
-            const float2 fzd = f2mul(wf, f2fma(c3, uz0, pz0)), fzu = f2mul(wf, f2sub(pz0, f2mul(c3, uz0)));
-            // emissions to the plane above (dn: this plane is its z-1 neighbour) and below (up)
-            const float2 dnP = f2fma(wc, f2add(A1, A2), fzd);
-            const float2 dnX = f2mul(wc, f2add(B1, B2)), dnY = f2mul(wc, f2add(C1, C2));
-            const float2 upP = f2fma(wc, f2sub(A1, A2), fzu);
-            const float2 upX = f2mul(wc, f2sub(B1, B2)), upY = f2mul(wc, f2sub(C1, C2));
+            float2 dnP, dnX, dnY, upP, upX, upY;
+            gather(hp, dnP, dnX, dnY);
+            gather(hm, upP, upX, upY);
+            const float2 exm = ex[m - 1], exp_ = ex[R::NM + m + 1], eym = ey[m - R::MX], eyp = ey[R::NM + m + R::MX];
+            const float2 inP = f2fma(w0, sig0, f2add(f2add(exm, exp_), f2add(eym, eyp)));
+            const float2 inX = f2sub(exm, exp_), inY = f2sub(eym, eyp);
+            // z faces from the column's own values
+            dnP = f2add(dnP, f2mul(wf, f2add(pz0, uz0)));
+            upP = f2add(upP, f2mul(wf, f2sub(pz0, uz0)));
             // plane k-1 gets the emission of plane k; plane k the one of plane k+1 (and the carried one of k-1)
             const float oA0 = accA[0] + upP.x, oA1 = accA[1] + upX.x, oA2 = accA[2] + upY.x, oA3 = accA[3] - upP.x;
             const float oB0 = (inP.x + dnB[0]) + upP.y, oB1 = (inX.x + dnB[1]) + upX.y, oB2 = (inY.x + dnB[2]) + upY.y,
