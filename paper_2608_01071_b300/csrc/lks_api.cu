@@ -25,6 +25,9 @@ using namespace lks;
 
 namespace {
 
+// chunks of one step's per-block motion partials summed in parallel before the per-step sums (motion_chunk_kernel)
+constexpr int kMotionChunks = 32;
+
 Engine* make_engine(int precision, int D, int hw, const Geom& g) {
     if (D == 2) return precision == LKS_FP64 ? make_engine2d_f64(hw, g) : make_engine2d_f32(hw, g);
     return precision == LKS_FP64 ? make_engine3d_f64(hw, g) : make_engine3d_f32(hw, g);
@@ -101,6 +104,7 @@ struct lks_ctx {
     cudaEvent_t ev_flag = nullptr;
     void* d_kbar = nullptr;
     double* d_mslot = nullptr;
+    double* d_mpart = nullptr;  // Lmax steps x kMotionChunks chunk sums of d_mslot
     void* d_boxbuf = nullptr;   // two buffers of Lmax steps x 2D planes x Fbn (lam_u, u_n on the footprint box)
     long long box_step = 0;     // elements per step in d_boxbuf
     void* d_fac = nullptr;      // two buffers of Lmax steps x Fbn: 1 / (1 + kappa) on the footprint box
@@ -335,6 +339,9 @@ void setup_geometry(lks_ctx* c) {
     }
     c->nd = (long long)p.nd[0] * p.nd[1] * p.nd[2];
     c->nde = (long long)g.nde[0] * g.nde[1] * g.nde[2];
+    // the mapping and sensitivity kernels index the design grid and the footprint-box records in 32 bits
+    if (c->nde >= (1LL << 31) || 6 * g.Fbn >= (1LL << 31))
+        throw LksError{LKS_EINVAL, "design grid or footprint box too large (2^31 design nodes, 2^31 / 6 box nodes)"};
 }
 
 // Checkpoint layout: boundaries every S steps; FULL keeps every state, SQRT every ceil(sqrt Nt)-th,
@@ -728,6 +735,7 @@ void allocate(lks_ctx* c) {
     c->d_kbar = dalloc(c, (size_t)c->Lmax * c->g.Fbn * ts * (c->rot ? 1 + D : 1));
     c->nsb = (int)nblk(c->g.Fbn, 256);
     c->d_mslot = (double*)dalloc(c, (size_t)c->Lmax * c->nsb * (2 * D + (c->rot ? 2 : 0)) * 8);
+    c->d_mpart = (double*)dalloc(c, (size_t)c->Lmax * kMotionChunks * (2 * D + (c->rot ? 2 : 0)) * 8);
     if (c->rot) {
         const int Kw = p.K_w;
         c->d_aknots = (double*)dalloc(c, (size_t)Kw * 8);
@@ -1203,14 +1211,18 @@ void sens_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
             c->launches++;
         }
         if (motion) {
-            if (c->D == 2)
-                rot_motion_reduce_kernel<2><<<L, 32, 0, s>>>(c->d_mslot, c->nsb, a + 1, L, c->d_gs, c->d_guG, c->d_gth,
-                                                            c->d_gom);
-            else
-                rot_motion_reduce_kernel<3><<<L, 32, 0, s>>>(c->d_mslot, c->nsb, a + 1, L, c->d_gs, c->d_guG, c->d_gth,
-                                                            c->d_gom);
+            const dim3 cg(L, kMotionChunks);
+            if (c->D == 2) {
+                motion_chunk_kernel<6><<<cg, 128, 0, s>>>(c->d_mslot, c->nsb, kMotionChunks, c->d_mpart);
+                rot_motion_reduce_kernel<2><<<L, 32, 0, s>>>(c->d_mpart, kMotionChunks, a + 1, L, c->d_gs, c->d_guG,
+                                                            c->d_gth, c->d_gom);
+            } else {
+                motion_chunk_kernel<8><<<cg, 128, 0, s>>>(c->d_mslot, c->nsb, kMotionChunks, c->d_mpart);
+                rot_motion_reduce_kernel<3><<<L, 32, 0, s>>>(c->d_mpart, kMotionChunks, a + 1, L, c->d_gs, c->d_guG,
+                                                            c->d_gth, c->d_gom);
+            }
             LKS_LAUNCHED();
-            c->launches++;
+            c->launches += 2;
         }
         return;
     }
@@ -1227,12 +1239,16 @@ void sens_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
         c->launches++;
     }
     if (motion) {
-        if (c->D == 2)
-            motion_reduce_kernel<2><<<L, 32, 0, s>>>(c->d_mslot, c->nsb, a + 1, L, c->d_gs, c->d_guG);
-        else
-            motion_reduce_kernel<3><<<L, 32, 0, s>>>(c->d_mslot, c->nsb, a + 1, L, c->d_gs, c->d_guG);
+        const dim3 cg(L, kMotionChunks);
+        if (c->D == 2) {
+            motion_chunk_kernel<4><<<cg, 128, 0, s>>>(c->d_mslot, c->nsb, kMotionChunks, c->d_mpart);
+            motion_reduce_kernel<2><<<L, 32, 0, s>>>(c->d_mpart, kMotionChunks, a + 1, L, c->d_gs, c->d_guG);
+        } else {
+            motion_chunk_kernel<6><<<cg, 128, 0, s>>>(c->d_mslot, c->nsb, kMotionChunks, c->d_mpart);
+            motion_reduce_kernel<3><<<L, 32, 0, s>>>(c->d_mpart, kMotionChunks, a + 1, L, c->d_gs, c->d_guG);
+        }
         LKS_LAUNCHED();
-        c->launches++;
+        c->launches += 2;
     }
 }
 

@@ -165,12 +165,8 @@ __device__ __forceinline__ void rot_uS(const Pose& P, const RotSums<T, D>& S, T*
 // Box node bl -> box coordinates b and the analysis node index (-1 outside the grid on a wall axis).
 template <int D>
 __device__ __forceinline__ long long rot_box_node(const Geom& g, const Pose& P, long long bl, int* b) {
-    long long r = bl, gi = 0, stride = 1;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        b[a] = (int)(r % g.Fb[a]);
-        r /= g.Fb[a];
-    }
+    long long gi = 0, stride = 1;
+    box_unflatten<D>(g, bl, b);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         int v = P.xs[a] + b[a];

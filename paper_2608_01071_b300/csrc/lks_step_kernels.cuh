@@ -76,13 +76,16 @@ __device__ __forceinline__ void pdl_wait_then_release() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Sum of NV values over the block: warp shuffles in the state precision T, then the warp partials in FP64
-// (FP64 throughput is scarce on this part, so per-node work never touches it).  Result valid on thread 0.
-// Fixed reduction order, so the result is deterministic.  red must hold NV * (NT / 32) doubles.
+// Sum of NV values over the block in the state precision T (warp shuffles, then the warp partials in warp order on
+// thread 0); the block total is returned in FP64, in which the callers sum over blocks.  FP64 throughput is scarce
+// on this part (a few FP64 instructions per block already take a visible share of a sensitivity pass), so
+// per-node and per-warp work never touches it.  Result valid on thread 0.  Fixed reduction order, so the result
+// is deterministic.  red must hold NV * (NT / 32) doubles.
 template <int NT, int NV, typename T>
 __device__ __forceinline__ void block_sum(T (&v)[NV], double (&out)[NV], double* red) {
     constexpr int NW = (NT + 31) / 32;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    T* rt = reinterpret_cast<T*>(red);
 #pragma unroll
     for (int c = 0; c < NV; ++c) {
 #pragma unroll
@@ -90,16 +93,16 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], double (&out)[NV], double*
     }
     if ((tid & 31) == 0) {
 #pragma unroll
-        for (int c = 0; c < NV; ++c) red[c * NW + (tid >> 5)] = (double)v[c];
+        for (int c = 0; c < NV; ++c) rt[c * NW + (tid >> 5)] = v[c];
     }
     __syncthreads();
     if (tid == 0) {
 #pragma unroll
         for (int c = 0; c < NV; ++c) {
-            double s = 0.0;
-#pragma unroll 1
-            for (int i = 0; i < NW; ++i) s += red[c * NW + i];
-            out[c] = s;
+            T s = 0;
+#pragma unroll
+            for (int i = 0; i < NW; ++i) s += rt[c * NW + i];
+            out[c] = (double)s;
         }
     }
 }
@@ -180,7 +183,7 @@ __device__ __forceinline__ void map_node(const Geom& g, const Pose& P, const T* 
         }
     }
     kap = 0;
-    const long long sx = g.nde[0], sxy = (long long)g.nde[0] * g.nde[1];
+    const int sx = g.nde[0], sxy = g.nde[0] * g.nde[1];  // the extended design grid holds fewer than 2^31 nodes
     if (D == 2) {
 #pragma unroll
         for (int ky = 0; ky < NTAP; ++ky) {
@@ -241,6 +244,23 @@ __device__ __forceinline__ T adj_inv(const Geom& g, const Pose& P, const T* __re
     return (T)1 / ((T)1 + kap);
 }
 
+// Box coordinates of the flat footprint-box index bl (x fastest), in 32-bit arithmetic: the box holds fewer than
+// 2^31 / 6 nodes (checked at context creation).
+template <int D>
+__device__ __forceinline__ void box_unflatten(const Geom& g, long long bl, int* b) {
+    const unsigned u = (unsigned)bl, F0 = (unsigned)g.Fb[0];
+    const unsigned q = u / F0;
+    b[0] = (int)(u - q * F0);
+    if (D == 2) {
+        b[1] = (int)q;
+        b[2] = 0;
+    } else {
+        const unsigned F1 = (unsigned)g.Fb[1], q2 = q / F1;
+        b[1] = (int)(q - q2 * F1);
+        b[2] = (int)q2;
+    }
+}
+
 // 1 / (1 + kappa) over the footprint box for steps n_first .. n_first + nsteps - 1 (one box field per step,
 // stride Fbn): the adjoint steps of a segment read it instead of evaluating the mapping at every staged node.
 template <typename T, int D, int HW>
@@ -249,13 +269,8 @@ __global__ void __launch_bounds__(256) box_fac_kernel(Geom g, const Pose* __rest
     const long long bl = blockIdx.x * 256LL + threadIdx.x;
     if (bl >= g.Fbn) return;
     const int j = blockIdx.y;
-    int b[D];
-    long long r = bl;
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-        b[c] = (int)(r % g.Fb[c]);
-        r /= g.Fb[c];
-    }
+    int b[3];
+    box_unflatten<D>(g, bl, b);
     T kap, C;
     map_node<T, D, HW, false>(g, poses[n_first + j], kref, b, kap, C, nullptr, nullptr);
     fac[j * g.Fbn + bl] = (T)1 / ((T)1 + kap);
@@ -616,7 +631,8 @@ __global__ void __launch_bounds__(256) adj_sens_kernel(Geom g, const Pose* __res
 #pragma unroll
     for (int c = 0; c < 2 * D; ++c) mv[c] = 0;
     if (bl < g.Fbn) {
-        int b[3] = {(int)(bl % g.Fb[0]), (int)((bl / g.Fb[0]) % g.Fb[1]), (int)(bl / ((long long)g.Fb[0] * g.Fb[1]))};
+        int b[3];
+        box_unflatten<D>(g, bl, b);
         bool ingrid = true;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
@@ -672,30 +688,35 @@ template <typename T, int D, int HW>
 __global__ void design_gather_kernel(Geom g, const Pose* __restrict__ poses, const T* __restrict__ kbar,
                                      int n_first, int nsteps, long long kstride, double* __restrict__ dkref) {
     constexpr int NTAP = 2 * HW;
-    const long long nd = (long long)g.nde[0] * g.nde[1] * g.nde[2];
-    const long long jl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int nd = g.nde[0] * g.nde[1] * g.nde[2];  // fewer than 2^31 (checked at context creation)
+    const int jl = blockIdx.x * blockDim.x + threadIdx.x;
     if (jl >= nd) return;
-    int j[3] = {(int)(jl % g.nde[0]), (int)((jl / g.nde[0]) % g.nde[1]), (int)(jl / ((long long)g.nde[0] * g.nde[1]))};
+    const int j[3] = {jl % g.nde[0], (jl / g.nde[0]) % g.nde[1], jl / (g.nde[0] * g.nde[1])};
+    // box coordinate of tap k along axis a, b = j + 2 HW - 1 - k, and its flat-offset term (-1: off the box); both
+    // are the same at every step, only the grid test of non-periodic axes depends on the pose
+    const int bst[3] = {1, g.Fb[0], g.Fb[0] * g.Fb[1]};
+    int bc[D][NTAP], bo[D][NTAP];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int k = 0; k < NTAP; ++k) {
+            const int b = j[a] + 2 * HW - 1 - k;
+            bc[a][k] = b;
+            bo[a][k] = (b >= 0 && b < g.Fb[a]) ? b * bst[a] : -1;
+        }
     // running FP64 sum in strict step order n = Nt..1 across calls, so that the segmentation of the
     // reverse sweep (full storage, sqrt or binomial checkpoints) cannot change the rounding
     double acc = dkref[jl];
     for (int s = nsteps - 1; s >= 0; --s) {
         const Pose& P = poses[n_first + s];
         const T* kb = kbar + (long long)s * kstride;
-        // box coordinate of tap k: b = j + 2 HW - 1 - k; valid when its analysis node is on the grid
-        int bb[D][NTAP];
+        bool ok[D][NTAP];
         T ww[D][NTAP];
 #pragma unroll
         for (int a = 0; a < D; ++a) {
 #pragma unroll
             for (int k = 0; k < NTAP; ++k) {
-                const int b = j[a] + 2 * HW - 1 - k;
-                bool ok = b >= 0 && b < g.Fb[a];
-                if (ok && !g.periodic[a]) {
-                    const int x = P.xs[a] + b;
-                    ok = x >= 0 && x < g.n[a];
-                }
-                bb[a][k] = ok ? b : -1;
+                ok[a][k] = bo[a][k] >= 0 && (g.periodic[a] || (unsigned)(P.xs[a] + bc[a][k]) < (unsigned)g.n[a]);
                 ww[a][k] = pose_w<T>(P, a, k);
             }
         }
@@ -703,25 +724,24 @@ __global__ void design_gather_kernel(Geom g, const Pose* __restrict__ poses, con
         if (D == 2) {
 #pragma unroll
             for (int ky = 0; ky < NTAP; ++ky) {
-                if (bb[1][ky] < 0) continue;
+                if (!ok[1][ky]) continue;
 #pragma unroll
                 for (int kx = 0; kx < NTAP; ++kx) {
-                    if (bb[0][kx] < 0) continue;
-                    sum += ww[0][kx] * ww[1][ky] * kb[bb[0][kx] + (long long)g.Fb[0] * bb[1][ky]];
+                    if (!ok[0][kx]) continue;
+                    sum += ww[0][kx] * ww[1][ky] * kb[bo[0][kx] + bo[1][ky]];
                 }
             }
         } else {
 #pragma unroll
             for (int kz = 0; kz < NTAP; ++kz) {
-                if (bb[D - 1][kz] < 0) continue;
+                if (!ok[D - 1][kz]) continue;
 #pragma unroll
                 for (int ky = 0; ky < NTAP; ++ky) {
-                    if (bb[1][ky] < 0) continue;
+                    if (!ok[1][ky]) continue;
 #pragma unroll
                     for (int kx = 0; kx < NTAP; ++kx) {
-                        if (bb[0][kx] < 0) continue;
-                        sum += ww[0][kx] * ww[1][ky] * ww[D - 1][kz] *
-                               kb[bb[0][kx] + (long long)g.Fb[0] * (bb[1][ky] + (long long)g.Fb[1] * bb[D - 1][kz])];
+                        if (!ok[0][kx]) continue;
+                        sum += ww[0][kx] * ww[1][ky] * ww[D - 1][kz] * kb[bo[0][kx] + bo[1][ky] + bo[D - 1][kz]];
                     }
                 }
             }
@@ -731,7 +751,39 @@ __global__ void design_gather_kernel(Geom g, const Pose* __restrict__ poses, con
     dkref[jl] = acc;
 }
 
-// Per-step motion sensitivities: the per-block partials of adj_sens_kernel summed in block order (one warp
+// First stage of the per-step motion sums: chunk ch of step s's per-block partials (blocks [nsb ch / nch,
+// nsb (ch + 1) / nch)), summed in a fixed order (strided over the threads, then a pairwise tree) into
+// mpart[s][ch][NV].  The per-step kernels below then sum the nch chunk partials in chunk order; spreading the FP64
+// additions over nsteps x nch blocks keeps them off a single SM.
+template <int NV>
+__global__ void __launch_bounds__(128) motion_chunk_kernel(const double* __restrict__ mslot, int nsb, int nch,
+                                                          double* __restrict__ mpart) {
+    __shared__ double red[NV][128];
+    const int st = blockIdx.x, ch = blockIdx.y, t = threadIdx.x;
+    const long long lo = (long long)nsb * ch / nch, hi = (long long)nsb * (ch + 1) / nch;
+    const double* ms = mslot + (long long)st * nsb * NV;
+    double acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+    for (long long b = lo + t; b < hi; b += 128) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] += ms[b * NV + q];
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) red[q][t] = acc[q];
+    __syncthreads();
+#pragma unroll
+    for (int w = 64; w > 0; w >>= 1) {
+        if (t < w) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) red[q][t] += red[q][t + w];
+        }
+        __syncthreads();
+    }
+    if (t < NV) mpart[((long long)st * nch + ch) * NV + t] = red[t][0];
+}
+
+// Per-step motion sensitivities: the partials (the chunk sums of motion_chunk_kernel) summed in order (one warp
 // per step; deterministic).
 template <int D>
 __global__ void motion_reduce_kernel(const double* __restrict__ mslot, int nsb, int n_first, int nsteps,
