@@ -131,13 +131,14 @@ def kernel_variant(lattice, rows, kind):
 
     kind is "fwd" or "adj".  D2Q9: 1/2 row tiles, 3 two steps per launch on row tiles, 4/8/16 warp columns,
     32/64 vectorised warp columns.  D3Q15: 1 the generic shared-memory kernel, 8/16 z-marching, 32/64/96
-    separable z-marching (planes x rows per block 16 x 8, 32 x 8, 16 x 16), 128/160 plane-pair separable (16 or 32
-    planes per block)."""
+    separable z-marching (planes x rows per block 16 x 8, 32 x 8, 16 x 16), 128/160/192 plane-pair separable
+    (16, 32 or 64 planes per block; 192 adjoint only)."""
     if lattice == "D3Q15":
         if rows == 1:
             return f"{kind}_step_kernel", "lks_step_kernels.cuh", 1
         if rows >= 128:
-            return f"{kind}3p_kernel<ZB={16 if rows == 128 else 32}>", "lks_step3p.cuh", 1
+            zb = {128: 16, 160: 32, 192: 64}[rows]
+            return f"{kind}3p_kernel<ZB={zb}>", "lks_step3p.cuh", 1
         if rows >= 32:
             zb, ty = {32: (16, 8), 64: (32, 8), 96: (16, 16)}[rows]
             return f"{kind}3s_kernel<ZB={zb},TY={ty}>", "lks_step3s.cuh", 1

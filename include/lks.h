@@ -88,7 +88,9 @@ enum { LKS_ADJ_DISCRETE = 0, LKS_ADJ_ALKS = 1 };                /* reverse sweep
  *                 warp columns (two columns per lane, even n[0] only) with that many rows.  D3Q15: 1 =
  *                 shared-memory tiles of 32 x 4 x 4 nodes; 8 or 16 = z-marching kernels with that many planes per
  *                 block; 32 or 64 = separable z-marching kernels with 16 or 32 planes of 32 x 8 columns; 96 =
- *                 separable forward with 16 planes of 32 x 16 columns (forward only).
+ *                 separable forward with 16 planes of 32 x 16 columns (forward only); LKS_FP32 only: 128 or 160 =
+ *                 plane-pair kernels (two planes per FP32x2 instruction) with 16 or 32 planes of 32 x 8 columns
+ *                 per block, 192 = the plane-pair adjoint with 64 planes (tile_rows_adj only).
  *                 0 = autotune at lks_create: times every choice on the context's buffers, then the fastest
  *                 one-step forward/adjoint pairs launched side by side; the forward sweep takes the fastest
  *                 forward, the pipelined sqrt(N) sweep and batch instances the fastest side-by-side pair

@@ -243,7 +243,7 @@ void validate(const lks_params* p) {
     auto variant_ok = [&](int r, bool fwd) {
         if (D == 3)
             return r == 1 || r == 8 || r == 16 || r == 32 || r == 64 || (fwd && r == 96) ||
-                   ((r == 128 || r == 160) && p->precision == LKS_FP32);
+                   ((r == 128 || r == 160 || (!fwd && r == 192)) && p->precision == LKS_FP32);
         return r == 1 || r == 2 || r == 3 || r == 4 || r == 8 || (r == 16 && p->precision == LKS_FP32) ||
                ((r == 32 || r == 64) && p->n[0] % 2 == 0);
     };
@@ -254,7 +254,8 @@ void validate(const lks_params* p) {
                      "32, 64 (separable, 16 or 32 planes per block), 96 (separable forward, 16 x 16 columns), "
                      "128, 160 (plane-pair separable kernels, FP32, 16 or 32 planes per block)");
     if (p->tile_rows_adj != 0 && (p->tile_rows == 0 || !variant_ok(p->tile_rows_adj, false)))
-        bad("tile_rows_adj must be 0, or a valid adjoint variant with tile_rows != 0");
+        bad("tile_rows_adj must be 0, or a valid adjoint variant with tile_rows != 0 (D3Q15 FP32 also 192: plane-pair "
+            "adjoint with 64 planes per block)");
     if (p->tile_rows_rec != 0 && (p->tile_rows == 0 || !variant_ok(p->tile_rows_rec, true)))
         bad("tile_rows_rec must be 0, or a valid forward variant with tile_rows != 0");
 }

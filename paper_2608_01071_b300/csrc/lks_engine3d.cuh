@@ -14,7 +14,8 @@ namespace lks {
 // rows = 8 or 16 the z-marching kernels with that many planes per block (32 x 8 columns); forward rows = 32,
 // 64 the separable z-marching kernels with 16 or 32 planes per block (32 x 8 columns), forward rows = 96 the
 // separable forward with 16 planes of 32 x 16 columns; FP32 rows = 128, 160 the plane-pair separable kernels (packed
-// FP32x2, forward and adjoint) with 16 or 32 planes per block (32 x 8 columns).
+// FP32x2, forward and adjoint) with 16 or 32 planes per block (32 x 8 columns), adjoint rows = 192 the plane-pair
+// adjoint with 64 planes.
 template <typename T, int HW>
 struct Engine3D : EngineCommon<T, 3, HW> {
     static constexpr int TX = 32, TY = 4, TZ = 4;
@@ -42,36 +43,49 @@ struct Engine3D : EngineCommon<T, 3, HW> {
         LKS_CUDA(cudaFuncSetAttribute(adj3s_kernel<T, HW, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem3s_adj<T, 8>()));
         if constexpr (kPair) {
-            const int sm = (int)smem3p_fwd();
-            LKS_CUDA(cudaFuncSetAttribute(fwd3p_kernel<HW, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-            LKS_CUDA(cudaFuncSetAttribute(fwd3p_kernel<HW, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-            LKS_CUDA(cudaFuncSetAttribute(fwd3p_kernel<HW, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-            LKS_CUDA(cudaFuncSetAttribute(fwd3p_kernel<HW, 32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-            const int sa = (int)smem3p_adj();
-            LKS_CUDA(cudaFuncSetAttribute(adj3p_kernel<HW, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa));
-            LKS_CUDA(cudaFuncSetAttribute(adj3p_kernel<HW, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa));
-            LKS_CUDA(cudaFuncSetAttribute(adj3p_kernel<HW, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa));
-            LKS_CUDA(cudaFuncSetAttribute(adj3p_kernel<HW, 32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa));
+            const int sm = (int)smem3p_fwd(), sa = (int)smem3p_adj();
+            for (bool v4 : {true, false}) {
+                LKS_CUDA(cudaFuncSetAttribute(fwd3p_fn<16>(v4), cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+                LKS_CUDA(cudaFuncSetAttribute(fwd3p_fn<32>(v4), cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+                LKS_CUDA(cudaFuncSetAttribute(adj3p_fn<16>(v4), cudaFuncAttributeMaxDynamicSharedMemorySize, sa));
+                LKS_CUDA(cudaFuncSetAttribute(adj3p_fn<32>(v4), cudaFuncAttributeMaxDynamicSharedMemorySize, sa));
+                LKS_CUDA(cudaFuncSetAttribute(adj3p_fn<64>(v4), cudaFuncAttributeMaxDynamicSharedMemorySize, sa));
+            }
         }
         this->alks_attr();
         set_rows(8, 8, g);
     }
     // the plane-pair kernels exist for the FP32 state only
     static constexpr bool kPair = std::is_same<T, float>::value;
+    // planes per block of the plane-pair codes (0: not a plane-pair code of that kernel)
+    static int pair_zb(int r, bool adj) {
+        if (r == 128) return 16;
+        if (r == 160) return 32;
+        if (adj && r == 192) return 64;
+        return 0;
+    }
+    template <int ZB>
+    static void (*fwd3p_fn(bool v4))(Geom, FwdArgs<float>) {
+        return v4 ? fwd3p_kernel<HW, ZB, true> : fwd3p_kernel<HW, ZB, false>;
+    }
+    template <int ZB>
+    static void (*adj3p_fn(bool v4))(Geom, AdjArgs<float>) {
+        return v4 ? adj3p_kernel<HW, ZB, true> : adj3p_kernel<HW, ZB, false>;
+    }
     std::vector<int> fwd_codes() const override {
         if (kPair) return {1, 8, 16, 32, 64, 96, 128, 160};
         return {1, 8, 16, 32, 64, 96};
     }
     std::vector<int> adj_codes() const override {
-        if (kPair) return {1, 8, 16, 32, 64, 128, 160};
+        if (kPair) return {1, 8, 16, 32, 64, 128, 160, 192};
         return {1, 8, 16, 32, 64};
     }
-    static void geom(int r, const Geom& g, dim3& th, dim3& tile, dim3& grid) {
+    static void geom(int r, bool adj, const Geom& g, dim3& th, dim3& tile, dim3& grid) {
         if (r == 1) {
             th = tile = dim3(TX, TY, TZ);
             grid = dim3(nblk(g.n[0], TX), nblk(g.n[1], TY), nblk(g.n[2], TZ));
-        } else if (r >= 128) {  // plane-pair separable forward: 16 or 32 planes of 32 x 8 columns
-            const int zb = r == 160 ? 32 : 16;
+        } else if (r >= 128) {  // plane-pair kernels: pair_zb planes of 32 x 8 columns
+            const int zb = pair_zb(r, adj);
             th = dim3(Pair3::TX, Pair3::TY, 1);
             tile = dim3(Pair3::TX, Pair3::TY, zb);
             grid = dim3(nblk(g.n[0], Pair3::TX), nblk(g.n[1], Pair3::TY), nblk(g.n[2], zb));
@@ -87,16 +101,16 @@ struct Engine3D : EngineCommon<T, 3, HW> {
         }
     }
     bool set_rows(int rf, int ra, const Geom& g) override {
-        auto okf = [](int r) { return r == 1 || r == 8 || r == 16 || r == 32 || r == 64 || r == 96 || (kPair && (r == 128 || r == 160)); };
-        auto oka = [](int r) { return r == 1 || r == 8 || r == 16 || r == 32 || r == 64 || (kPair && (r == 128 || r == 160)); };
+        auto okf = [](int r) { return r == 1 || r == 8 || r == 16 || r == 32 || r == 64 || r == 96 || (kPair && pair_zb(r, false) > 0); };
+        auto oka = [](int r) { return r == 1 || r == 8 || r == 16 || r == 32 || r == 64 || (kPair && pair_zb(r, true) > 0); };
         if (!okf(rf) || !oka(ra)) return false;
         // the plane-pair kernels index in 32 bits: every field offset c N + i and box offset c Fbn + b must fit
         const bool small = 4 * g.N < (1LL << 31) && 6 * g.Fbn < (1LL << 31);
         if (!small && (rf >= 128 || ra >= 128)) return false;
         this->rows_f = rf;
         this->rows_a = ra;
-        geom(rf, g, this->fthreads, this->ftile, this->fgrid);
-        geom(ra, g, this->athreads, this->atile, this->agrid);
+        geom(rf, false, g, this->fthreads, this->ftile, this->fgrid);
+        geom(ra, true, g, this->athreads, this->atile, this->agrid);
         return true;
     }
     void fwd(const Geom& g, const void* in, void* out, const void* kref, const Pose* pose, double* jslot,
@@ -116,12 +130,10 @@ struct Engine3D : EngineCommon<T, 3, HW> {
             launch_pdl(fwd3s_kernel<T, HW, 16, 16>, this->fgrid, this->fthreads, smem3s_fwd<T, 16>(), s, this->pdl, g, a);
         else if constexpr (kPair) {
             const bool v4 = g.n[0] % 4 == 0;
-            if (this->rows_f == 128)
-                launch_pdl(v4 ? fwd3p_kernel<HW, 16, true> : fwd3p_kernel<HW, 16, false>, this->fgrid, this->fthreads,
-                           smem3p_fwd(), s, this->pdl, g, a);
-            else
-                launch_pdl(v4 ? fwd3p_kernel<HW, 32, true> : fwd3p_kernel<HW, 32, false>, this->fgrid, this->fthreads,
-                           smem3p_fwd(), s, this->pdl, g, a);
+            switch (pair_zb(this->rows_f, false)) {
+                case 16: launch_pdl(fwd3p_fn<16>(v4), this->fgrid, this->fthreads, smem3p_fwd(), s, this->pdl, g, a); break;
+                default: launch_pdl(fwd3p_fn<32>(v4), this->fgrid, this->fthreads, smem3p_fwd(), s, this->pdl, g, a); break;
+            }
         }
     }
     void adj(const Geom& g, const void* lam_in, void* lam_out, const void* prev, const void* cur, const void* kref,
@@ -139,12 +151,11 @@ struct Engine3D : EngineCommon<T, 3, HW> {
             launch_pdl(adj3s_kernel<T, HW, 32, 8>, this->agrid, this->athreads, smem3s_adj<T, 8>(), s, this->pdl, g, a);
         else if constexpr (kPair) {
             const bool v4 = g.n[0] % 4 == 0;
-            if (this->rows_a == 128)
-                launch_pdl(v4 ? adj3p_kernel<HW, 16, true> : adj3p_kernel<HW, 16, false>, this->agrid, this->athreads,
-                           smem3p_adj(), s, this->pdl, g, a);
-            else
-                launch_pdl(v4 ? adj3p_kernel<HW, 32, true> : adj3p_kernel<HW, 32, false>, this->agrid, this->athreads,
-                           smem3p_adj(), s, this->pdl, g, a);
+            switch (pair_zb(this->rows_a, true)) {
+                case 16: launch_pdl(adj3p_fn<16>(v4), this->agrid, this->athreads, smem3p_adj(), s, this->pdl, g, a); break;
+                case 64: launch_pdl(adj3p_fn<64>(v4), this->agrid, this->athreads, smem3p_adj(), s, this->pdl, g, a); break;
+                default: launch_pdl(adj3p_fn<32>(v4), this->agrid, this->athreads, smem3p_adj(), s, this->pdl, g, a); break;
+            }
         }
     }
 };

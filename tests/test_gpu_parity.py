@@ -176,13 +176,21 @@ def test_d2q9_mixed_variants(fwd, adj, ckpt):
     assert g["stats"]["tile_rows_fwd"] == fwd and g["stats"]["tile_rows_adj"] == adj
 
 
-@pytest.mark.parametrize("fwd,adj", [(128, 32), (32, 160), (160, 128)])
+@pytest.mark.parametrize("fwd,adj", [(128, 32), (32, 160), (160, 128), (128, 192), (32, 192)])
 def test_d3q15_mixed_variants(fwd, adj):
     # plane-pair and separable kernels mixed between the forward sweep and the adjoint, binomial reverse sweep
     w = tiny_workload("D3Q15", precision="fp32", tile_rows=fwd, tile_rows_adj=adj, shape=(44, 21, 19), ckpt="revolve",
                       ckpt_slots=3, seg_len=4, Nt=23)
     g, _ = check(w, 1e-5, 1e-4, 1e-3)
     assert g["stats"]["tile_rows_fwd"] == fwd and g["stats"]["tile_rows_adj"] == adj
+
+
+def test_d3q15_adjoint_64_planes_several_blocks():
+    # the 64-plane plane-pair adjoint on 136 planes: three z blocks, the last one ragged (8 planes), z walls
+    w = tiny_workload("D3Q15", precision="fp32", tile_rows=128, tile_rows_adj=192, shape=(44, 13, 136),
+                      design=(8, 6, 40), probe_lo=(30, 3, 60), probe_hi=(36, 10, 90), ckpt="sqrt", Nt=12)
+    g, _ = check(w, 1e-5, 1e-4, 1e-3)
+    assert g["stats"]["tile_rows_adj"] == 192
 
 
 def test_3d_128x64x64_full_grid_revolve_fp32():
