@@ -220,7 +220,9 @@ int lks_get_status(lks_ctx* ctx);
 int lks_adjoint(lks_ctx* ctx, double* dJ_dgamma, double* dJ_dpos);
 int lks_adjoint_dev(lks_ctx* ctx, double* d_dJ_dgamma, double* d_dJ_dpos, void* stream);
 
-/* Density filter of Eq. filtering on the inner design grid (out = W gamma) and its transpose. */
+/* Density filter of Eq. filtering on the inner design grid (out = W gamma) and its transpose.  The transpose stages
+ * its input divided by the row sums in a buffer of the context: transposes on one context that may overlap on the
+ * GPU (different streams without ordering) race; order them on one stream. */
 int lks_density_filter_dev(lks_ctx* ctx, const double* d_in, double* d_out, void* stream);
 int lks_density_filter_T_dev(lks_ctx* ctx, const double* d_in, double* d_out, void* stream);
 

@@ -85,6 +85,7 @@ struct lks_ctx {
 
     // device memory
     std::vector<void*> allocs;
+    double* d_fscr = nullptr;  // nd: the transposed filter's input divided by the row sums
     double *d_gamma = nullptr, *d_gt = nullptr, *d_gb = nullptr, *d_kref64 = nullptr, *d_fnorm = nullptr,
            *d_tmp = nullptr;
     void* d_kref = nullptr;
@@ -693,6 +694,7 @@ void allocate(lks_ctx* c) {
     c->d_gt = (double*)dalloc(c, c->nd * 8);
     c->d_gb = (double*)dalloc(c, c->nd * 8);
     c->d_fnorm = (double*)dalloc(c, c->nd * 8);
+    c->d_fscr = (double*)dalloc(c, c->nd * 8);
     c->d_tmp = (double*)dalloc(c, c->nd * 8);
     c->d_kref64 = (double*)dalloc(c, c->nde * 8);
     c->d_kref = dalloc(c, c->nde * ts);
@@ -734,7 +736,7 @@ void allocate(lks_ctx* c) {
     // kappa-bar per step (and u^S-bar with a rotating body); per-block motion partials per step (2 D values, and
     // dJ/dtheta, dJ/domega with a rotating body)
     c->d_kbar = dalloc(c, (size_t)c->Lmax * c->g.Fbn * ts * (c->rot ? 1 + D : 1));
-    c->nsb = (int)nblk(c->g.Fbn, 256);
+    c->nsb = (int)nblk(c->g.Fbn, c->rot ? 256 : 256 * kSensNPT);  // blocks per step of rot_sens / adj_sens
     c->d_mslot = (double*)dalloc(c, (size_t)c->Lmax * c->nsb * (2 * D + (c->rot ? 2 : 0)) * 8);
     c->d_mpart = (double*)dalloc(c, (size_t)c->Lmax * kMotionChunks * (2 * D + (c->rot ? 2 : 0)) * 8);
     if (c->rot) {
@@ -802,7 +804,7 @@ void allocate(lks_ctx* c) {
     LKS_CUDA(cudaMemset(c->d_jslot, 0, (size_t)2 * nslot * 8));
     LKS_CUDA(cudaMemset(c->d_J, 0, 4 * 8));
     LKS_CUDA(cudaMemset(c->d_pose, 0, (size_t)(p.Nt + 1) * sizeof(Pose)));
-    filter_norm_kernel<<<nblk(c->nd, 128), 128>>>(c->dg, c->d_fnorm);
+    filter_norm_kernel<<<nblk(c->nd, 128), 128, cone_table_bytes(c->dg.R)>>>(c->dg, c->d_fnorm);
     LKS_LAUNCHED();
     motion_norm_kernel<<<nblk(p.K, 128), 128>>>(c->mg, c->d_tnorm);
     LKS_LAUNCHED();
@@ -903,7 +905,8 @@ void free_all(lks_ctx* c) {
 // ------------------------------------------------------------------------------------------------
 void prepare_design_and_motion(lks_ctx* c, cudaStream_t s) {
     // a0: gamma -> gamma~ -> gamma-bar -> kappa^ref
-    density_filter_kernel<<<nblk(c->nd, 128), 128, 0, s>>>(c->dg, c->d_gamma, c->d_fnorm, c->d_gt, 0);
+    density_filter_kernel<<<nblk(c->nd, 128), 128, cone_table_bytes(c->dg.R), s>>>(c->dg, c->d_gamma, c->d_fnorm,
+                                                                                c->d_gt, 0);
     LKS_LAUNCHED();
     c->eng->kappa_ref(c->dg, c->d_gt, c->d_gb, c->d_kref64, c->d_kref, s);
     // a1: knots -> filtered -> s_n, u^G_n -> per-step pose
@@ -1405,6 +1408,18 @@ void adjoint_body(lks_ctx* c, cudaStream_t s) {
     (void)K;
 }
 
+// Transposed density filter: in / norm into the context's scratch, then the weighted sums (identity for R <= 1).
+void filter_T(lks_ctx* c, const double* in, double* out, cudaStream_t s) {
+    const double* src = in;
+    if (c->dg.R > 1.0) {
+        filter_scale_kernel<<<nblk(c->nd, 256), 256, 0, s>>>(c->nd, in, c->d_fnorm, c->d_fscr);
+        LKS_LAUNCHED();
+        src = c->d_fscr;
+    }
+    density_filter_kernel<<<nblk(c->nd, 128), 128, cone_table_bytes(c->dg.R), s>>>(c->dg, src, c->d_fnorm, out, 1);
+    LKS_LAUNCHED();
+}
+
 // Final gradients into caller buffers (device pointers), honouring the gradient mode.
 void finish_adjoint(lks_ctx* c, double* dgamma, double* dpos, cudaStream_t s) {
     const int K = c->prm.K, D = c->D;
@@ -1413,9 +1428,8 @@ void finish_adjoint(lks_ctx* c, double* dgamma, double* dpos, cudaStream_t s) {
         if (c->prm.mode == LKS_MODE_MOTION) {
             LKS_CUDA(cudaMemsetAsync(dgamma, 0, c->nd * 8, s));
         } else {
-            density_filter_kernel<<<nblk(c->nd, 128), 128, 0, s>>>(c->dg, c->d_tmp, c->d_fnorm, dgamma, 1);
-            LKS_LAUNCHED();
-            c->launches++;
+            filter_T(c, c->d_tmp, dgamma, s);
+            c->launches += 2;
         }
     }
     if (dpos) {
@@ -1719,7 +1733,8 @@ int lks_density_filter_dev(lks_ctx* c, const double* in, double* out, void* stre
     if (!c) return LKS_EINVAL;
     return guard(c, [&] {
         if (!in || !out) throw LksError{LKS_EINVAL, "null pointer"};
-        density_filter_kernel<<<nblk(c->nd, 128), 128, 0, (cudaStream_t)stream>>>(c->dg, in, c->d_fnorm, out, 0);
+        density_filter_kernel<<<nblk(c->nd, 128), 128, cone_table_bytes(c->dg.R), (cudaStream_t)stream>>>(
+            c->dg, in, c->d_fnorm, out, 0);
         LKS_LAUNCHED();
     });
 }
@@ -1728,8 +1743,7 @@ int lks_density_filter_T_dev(lks_ctx* c, const double* in, double* out, void* st
     if (!c) return LKS_EINVAL;
     return guard(c, [&] {
         if (!in || !out) throw LksError{LKS_EINVAL, "null pointer"};
-        density_filter_kernel<<<nblk(c->nd, 128), 128, 0, (cudaStream_t)stream>>>(c->dg, in, c->d_fnorm, out, 1);
-        LKS_LAUNCHED();
+        filter_T(c, in, out, (cudaStream_t)stream);
     });
 }
 
@@ -2145,8 +2159,8 @@ extern "C" int lks_density_filter_noalloc(const int32_t nd[3], double R, const d
     dg.R = R;
     cudaStream_t s = (cudaStream_t)stream;
     // the norm kernel overwrites every entry the filter reads, so nothing needs clearing between calls
-    filter_norm_kernel<<<nblk(n, 128), 128, 0, s>>>(dg, norm);
-    density_filter_kernel<<<nblk(n, 128), 128, 0, s>>>(dg, d_in, norm, d_out, 0);
+    filter_norm_kernel<<<nblk(n, 128), 128, cone_table_bytes(R), s>>>(dg, norm);
+    density_filter_kernel<<<nblk(n, 128), 128, cone_table_bytes(R), s>>>(dg, d_in, norm, d_out, 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         g_noalloc_err = std::string("kernel launch: ") + cudaGetErrorString(e);

@@ -178,7 +178,7 @@ struct EngineCommon : Engine {
     }
     void sens(const Geom& g, const Pose* poses, const void* kref, const void* boxbuf, long long bstride, int n_first,
               int nsteps, void* kbar, double* mslot, bool alks, cudaStream_t s) override {
-        const dim3 grid(nblk(g.Fbn, 256), nsteps, 1);
+        const dim3 grid(nblk(g.Fbn, 256 * kSensNPT), nsteps, 1);
         if (alks)
             adj_sens_kernel<T, D, HW, true><<<grid, 256, 0, s>>>(g, poses, (const T*)kref, (const T*)boxbuf, bstride,
                                                                  n_first, (T*)kbar, mslot);

@@ -15,20 +15,31 @@ struct DesignGeom {
     double kappa_max, q;
 };
 
-// Cone weight of Eq. filtering for an integer offset.
-__device__ __forceinline__ double cone_weight(int dx, int dy, int dz, double R) {
-    const double dist = sqrt((double)(dx * dx + dy * dy + dz * dz));
-    const double w = (R - dist) / R;
-    return w > 0.0 ? w : 0.0;
+// Cone weights of Eq. filtering, w = max(0, (R - |d|) / R) for an integer offset d, tabulated by |d|^2 = 0 .. 3 r^2
+// (r = floor R <= 32: at most 3073 entries) in shared memory: one square root per entry and block instead of one per
+// tap, the FP64 square root being costly on this part.  Every thread of the block must call it.
+__device__ __forceinline__ void cone_table(double R, int r, double* sh) {
+    const int n = 3 * r * r + 1;
+    for (int d2 = threadIdx.x; d2 < n; d2 += blockDim.x) {
+        const double w = (R - sqrt((double)d2)) / R;
+        sh[d2] = w > 0.0 ? w : 0.0;
+    }
+    __syncthreads();
+}
+inline size_t cone_table_bytes(double R) {
+    const int r = (int)floor(R);
+    return sizeof(double) * (3 * r * r + 1);
 }
 
 // Row sums sum_j w_s(i, j) over the design grid (truncated at the edges); static per context.
 static __global__ void filter_norm_kernel(DesignGeom dg, double* __restrict__ norm) {
+    extern __shared__ double cw[];
+    const int r = (int)floor(dg.R);
+    cone_table(dg.R, r, cw);
     const long long n = (long long)dg.nd[0] * dg.nd[1] * dg.nd[2];
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int ix = i % dg.nd[0], iy = (i / dg.nd[0]) % dg.nd[1], iz = i / ((long long)dg.nd[0] * dg.nd[1]);
-    const int r = (int)floor(dg.R);
     const int rz = dg.nd[2] > 1 ? r : 0;
     double s = 0.0;
     for (int dz = -rz; dz <= rz; ++dz)
@@ -36,24 +47,27 @@ static __global__ void filter_norm_kernel(DesignGeom dg, double* __restrict__ no
             for (int dx = -r; dx <= r; ++dx) {
                 const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
                 if (jx < 0 || jx >= dg.nd[0] || jy < 0 || jy >= dg.nd[1] || jz < 0 || jz >= dg.nd[2]) continue;
-                s += cone_weight(dx, dy, dz, dg.R);
+                s += cw[dx * dx + dy * dy + dz * dz];
             }
     norm[i] = s;
 }
 
 // Eq. filtering (transpose = false): out_i = sum_j w_ij in_j / norm_i.
-// Transpose (transpose = true):      out_j = sum_i w_ij in_i / norm_i.
+// Transpose (transpose = true):      out_j = sum_i w_ij in_i / norm_i, with `in` already divided by norm
+// (filter_scale_kernel), so that no tap divides.  R <= 1 is the identity in both directions.
 static __global__ void density_filter_kernel(DesignGeom dg, const double* __restrict__ in, const double* __restrict__ norm,
-                                      double* __restrict__ out, int transpose) {
+                                             double* __restrict__ out, int transpose) {
+    extern __shared__ double cw[];
     const long long n = (long long)dg.nd[0] * dg.nd[1] * dg.nd[2];
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (dg.R <= 1.0) {
-        out[i] = in[i];
+    if (dg.R <= 1.0) {  // identity (the transposed call then gets its input unscaled)
+        if (i < n) out[i] = in[i];
         return;
     }
-    const int ix = i % dg.nd[0], iy = (i / dg.nd[0]) % dg.nd[1], iz = i / ((long long)dg.nd[0] * dg.nd[1]);
     const int r = (int)floor(dg.R);
+    cone_table(dg.R, r, cw);
+    if (i >= n) return;
+    const int ix = i % dg.nd[0], iy = (i / dg.nd[0]) % dg.nd[1], iz = i / ((long long)dg.nd[0] * dg.nd[1]);
     const int rz = dg.nd[2] > 1 ? r : 0;
     double s = 0.0;
     for (int dz = -rz; dz <= rz; ++dz)
@@ -61,12 +75,19 @@ static __global__ void density_filter_kernel(DesignGeom dg, const double* __rest
             for (int dx = -r; dx <= r; ++dx) {
                 const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
                 if (jx < 0 || jx >= dg.nd[0] || jy < 0 || jy >= dg.nd[1] || jz < 0 || jz >= dg.nd[2]) continue;
-                const double w = cone_weight(dx, dy, dz, dg.R);
+                const double w = cw[dx * dx + dy * dy + dz * dz];
                 if (w == 0.0) continue;
                 const long long j = jx + (long long)dg.nd[0] * (jy + (long long)dg.nd[1] * jz);
-                s += transpose ? w * in[j] / norm[j] : w * in[j];
+                s += w * in[j];
             }
     out[i] = transpose ? s : s / norm[i];
+}
+
+// in / norm, the input of the transposed filter.
+static __global__ void filter_scale_kernel(long long n, const double* __restrict__ in, const double* __restrict__ norm,
+                                           double* __restrict__ out) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i] / norm[i];
 }
 
 // Eq. projection and its derivative; beta = 0 is the identity.

@@ -619,6 +619,10 @@ __global__ void __launch_bounds__(TX * TY * TZ) adj_step_kernel(Geom g, AdjArgs<
 // ------------------------------------------------------------------------------------------------
 // With ALKS set the records hold the ALKS adjoint velocity u~ (lks_alks.cuh) and the sensitivities are its forms
 // kappa-bar = 3 (u_n - u^S) . u~, u^S-bar = -3 kappa u~.
+// Footprint-box nodes per thread of adj_sens_kernel (block b covers nodes 256 kSensNPT b .. 256 kSensNPT (b + 1) - 1,
+// coalesced per sweep): the block's motion partials are reduced once for all of them.
+constexpr int kSensNPT = 4;
+
 template <typename T, int D, int HW, bool ALKS = false>
 __global__ void __launch_bounds__(256) adj_sens_kernel(Geom g, const Pose* __restrict__ poses, const T* __restrict__ kref,
                                                        const T* __restrict__ boxbuf, long long bstride, int n_first,
@@ -626,11 +630,13 @@ __global__ void __launch_bounds__(256) adj_sens_kernel(Geom g, const Pose* __res
     __shared__ double red[2 * D * 8];
     const int s = blockIdx.y;
     const Pose& P = poses[n_first + s];
-    const long long bl = blockIdx.x * 256LL + threadIdx.x;
     T mv[2 * D];
 #pragma unroll
     for (int c = 0; c < 2 * D; ++c) mv[c] = 0;
-    if (bl < g.Fbn) {
+#pragma unroll 1
+    for (int k = 0; k < kSensNPT; ++k) {
+        const long long bl = (blockIdx.x * (long long)kSensNPT + k) * 256 + threadIdx.x;
+        if (bl >= g.Fbn) break;
         int b[3];
         box_unflatten<D>(g, bl, b);
         bool ingrid = true;
@@ -664,8 +670,8 @@ __global__ void __launch_bounds__(256) adj_sens_kernel(Geom g, const Pose* __res
             if (kbar != nullptr) kbar[(long long)s * g.Fbn + bl] = kb;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                mv[c] = kb * dk[c] + cbar * dC[c];
-                mv[D + c] = usb[c] * C;
+                mv[c] += kb * dk[c] + cbar * dC[c];
+                mv[D + c] += usb[c] * C;
             }
         }
     }
