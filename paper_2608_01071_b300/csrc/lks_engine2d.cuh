@@ -51,9 +51,11 @@ struct Engine2D : EngineCommon<T, 2, HW> {
     bool set_rows(int rf, int ra, const Geom& g) override {
         // rows kept in registers grow with R: FP32 allows up to 16, FP64 up to 8 without spills; 3 = fused forward;
         // 32 and 64 = vectorised warp columns (even x extent only)
-        const bool even = (g.n[0] % 2) == 0;
-        auto ok = [even](int r) {
-            return r == 1 || r == 2 || r == 4 || r == 8 || (r == 16 && sizeof(T) == 4) || ((r == 32 || r == 64) && even);
+        // (the vectorised adjoint indexes in 32 bits: 3 N must fit)
+        const bool even = (g.n[0] % 2) == 0, small = 3 * g.N < (1LL << 31);
+        auto ok = [even, small](int r) {
+            return r == 1 || r == 2 || r == 4 || r == 8 || (r == 16 && sizeof(T) == 4) ||
+                   ((r == 32 || r == 64) && even && small);
         };
         if (!(ok(rf) || rf == 3) || !(ok(ra) || ra == 3)) return false;
         this->rows_f = rf;

@@ -218,14 +218,18 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (HW == 1 ? 7 : 5) : 4) f
 
 // ------------------------------------------------------------------------------------------------
 // Adjoint step lambda_n -> lambda_{n-1}, recording lam_u and u_n on the footprint box.
+// The rows' uniform work (wrap, wall test, footprint row) is done once per row; a source row arrives two rows
+// ahead of use together with its 1/(1 + kappa) factors, and the output row's u_{n-1} (and u_n on footprint rows)
+// two rows ahead as well; the raw lam_u of the output row, for its footprint record, is kept from its source pass.
+// Indices are 32-bit (offered when 3 N and 4 F_b fit).
 // ------------------------------------------------------------------------------------------------
 template <typename T, int HW, int R>
-__global__ void __launch_bounds__(128, 5) adj2v_kernel(Geom g, AdjArgs<T> a) {
+__global__ void __launch_bounds__(128, 4) adj2v_kernel(Geom g, AdjArgs<T> a) {
     using V = typename Vec2<T>::type;
     constexpr int WY = 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nx = g.n[0], ny = g.n[1];
-    const long long N = g.N;
+    const int N = (int)g.N, Fbn = (int)g.Fbn, Fb0 = g.Fb[0];
     const int x0 = blockIdx.x * kVecCols;
     const int y0 = (blockIdx.y * WY + warp) * R;
     const int xe = x0 - 2 + 2 * lane;
@@ -237,46 +241,76 @@ __global__ void __launch_bounds__(128, 5) adj2v_kernel(Geom g, AdjArgs<T> a) {
     const V* __restrict__ lY = reinterpret_cast<const V*>(a.lam_in + 2 * N);
     const V* __restrict__ upX = reinterpret_cast<const V*>(a.u_prev);
     const V* __restrict__ upY = reinterpret_cast<const V*>(a.u_prev + N);
+    const V* __restrict__ ucX = reinterpret_cast<const V*>(a.u_cur);
+    const V* __restrict__ ucY = reinterpret_cast<const V*>(a.u_cur + N);
     const Pose& P = *a.pose;
     const int half = nx >> 1;
     // per-lane invariants: source columns (wrapped) and output columns
     const int sbxe = box_coord(xl, P.xs[0], g.Fb[0], nx, g.periodic[0]);
     const int sbxo = box_coord(xl + 1, P.xs[0], g.Fb[0], nx, g.periodic[0]);
-    const int swxe = wall_side(xl, nx, g.periodic[0]), swxo = wall_side(xl + 1, nx, g.periodic[0]);
+    const bool swxe = wall_side(xl, nx, g.periodic[0]) >= 0, swxo = wall_side(xl + 1, nx, g.periodic[0]) >= 0;
     const int bxe = box_coord(xe, P.xs[0], g.Fb[0], nx, g.periodic[0]);
     const int bxo = box_coord(xe + 1, P.xs[0], g.Fb[0], nx, g.periodic[0]);
+    const bool wxe = wall_side(xe, nx, g.periodic[0]) >= 0, wxo = wall_side(xe + 1, nx, g.periodic[0]) >= 0;
     const bool pxe = xe >= g.probe_lo[0] && xe < g.probe_hi[0];
     const bool pxo = xe + 1 >= g.probe_lo[0] && xe + 1 < g.probe_hi[0];
+    const T one = (T)1, zr = (T)0;
     pdl_wait_then_release();
 
-    auto load = [&](int r, V& p, V& ux, V& uy) {
-        const int gi = wrap(r, ny) * half + (xl >> 1);
+    // source row r: raw lambda and the factor pair 1/(1 + kappa) off the walls, 0 on them
+    auto load = [&](int r, V& p, V& ux, V& uy, V& fc) {
+        const int yw = wrap(r, ny);
+        const int gi = yw * half + (xl >> 1);
         p = lP[gi];
         ux = lX[gi];
         uy = lY[gi];
+        T fe = one, fo = one;
+        if (wall_side(yw, ny, g.periodic[1]) >= 0) {
+            fe = fo = zr;
+        } else {
+            const int by = box_coord(yw, P.xs[1], g.Fb[1], ny, g.periodic[1]);
+            if (by >= 0) {
+                if (a.fac != nullptr) {
+                    const T* fr = a.fac + by * Fb0;
+                    if (sbxe >= 0) fe = fr[sbxe];
+                    if (sbxo >= 0) fo = fr[sbxo];
+                } else {
+                    if (sbxe >= 0) {
+                        const int b[2] = {sbxe, by};
+                        fe = adj_inv<T, 2, HW>(g, P, a.kref, nullptr, b);
+                    }
+                    if (sbxo >= 0) {
+                        const int b[2] = {sbxo, by};
+                        fo = adj_inv<T, 2, HW>(g, P, a.kref, nullptr, b);
+                    }
+                }
+            }
+            if (swxe) fe = zr;
+            if (swxo) fo = zr;
+        }
+        fc = vmk(fe, fo);
     };
-    // Brinkman / wall adjoint factor of a source node: 1/(1 + kappa) off the walls, 0 on them
-    auto factor = [&](int yw, int bx, int wx) -> T {
-        if (wx >= 0 || wall_side(yw, ny, g.periodic[1]) >= 0) return (T)0;
-        const int by = box_coord(yw, P.xs[1], g.Fb[1], ny, g.periodic[1]);
-        if (bx < 0 || by < 0) return (T)1;
-        const int b[2] = {bx, by};
-        return adj_inv<T, 2, HW>(g, P, a.kref, a.fac, b);
-    };
-    V pA, xA, yA, pB, xB, yB;
-    load(y0 - 2, pA, xA, yA);
-    load(y0 - 1, pB, xB, yB);
-    // u_{n-1} of the output rows, two rows ahead (row z is consumed at iteration r = z + 2)
-    auto load_u = [&](int z, V& u0, V& u1) {
-        const int gz = (lane_out && z < ny) ? z * half + (xe >> 1) : 0;
+    V pA, xA, yA, fA, pB, xB, yB, fB;
+    load(y0 - 2, pA, xA, yA, fA);
+    load(y0 - 1, pB, xB, yB, fB);
+    // output row z: u_{n-1}, and u_n on footprint rows (for the records); two rows ahead of use
+    auto load_u = [&](int z, V& u0, V& u1, V& c0, V& c1) {
+        const bool ok = lane_out && z < ny;
+        const int gz = ok ? z * half + (xe >> 1) : 0;
         u0 = upX[gz];
         u1 = upY[gz];
+        if (ok && box_coord(z, P.xs[1], g.Fb[1], ny, g.periodic[1]) >= 0 && (bxe >= 0 || bxo >= 0)) {
+            c0 = ucX[gz];
+            c1 = ucY[gz];
+        }
     };
-    V uxA, uyA, uxB, uyB;
-    load_u(y0, uxA, uyA);
-    load_u(y0 + 1, uxB, uyB);
-    // moment accumulators as (even, odd) pairs: rows r-1 (0), r (1), r+1 (2); completed rows r-2 (c), r-3 (p)
     const V zero = vsplat<T>(0.0);
+    V uxA, uyA, cxA = zero, cyA = zero, uxB, uyB, cxB = zero, cyB = zero;
+    load_u(y0, uxA, uyA, cxA, cyA);
+    load_u(y0 + 1, uxB, uyB, cxB, cyB);
+    // raw lam_u of the source rows r-1 and r-2 (the output row's footprint record)
+    V rx1 = zero, ry1 = zero, rx2 = zero, ry2 = zero;
+    // moment accumulators as (even, odd) pairs: rows r-1 (0), r (1), r+1 (2); completed rows r-2 (c), r-3 (p)
     V m00 = zero, mx0 = zero, my0 = zero, xx0 = zero, xy0 = zero, yy0 = zero;
     V m01 = zero, mx1 = zero, my1 = zero, xx1 = zero, xy1 = zero, yy1 = zero;
     V m02 = zero, mx2 = zero, my2 = zero, xx2 = zero, xy2 = zero, yy2 = zero;
@@ -286,12 +320,10 @@ __global__ void __launch_bounds__(128, 5) adj2v_kernel(Geom g, AdjArgs<T> a) {
 
 #pragma unroll 1
     for (int r = y0 - 2; r <= y0 + R + 1; ++r) {
-        const V lp = pA, lxv = xA, lyv = yA;
-        pA = pB; xA = xB; yA = yB;
-        if (r + 2 <= y0 + R + 1) load(r + 2, pB, xB, yB);
+        const V lp = pA, lxv = xA, lyv = yA, fac = fA;
+        pA = pB; xA = xB; yA = yB; fA = fB;
+        if (r + 2 <= y0 + R + 1) load(r + 2, pB, xB, yB, fB);
         // source row r: p-bar*/3 = lam_p / 3, u-bar* = lam_u * factor
-        const int yw = wrap(r, ny);
-        const V fac = vmk(factor(yw, sbxe, swxe), factor(yw, sbxo, swxo));
         const V P3 = vmul(vsplat<T>(1.0 / 3.0), lp), U = vmul(lxv, fac), W = vmul(lyv, fac);
         // sources x-1 of the pair (previous lane's odd, even) and x+1 (odd, next lane's even)
         const V P3L = vmk(shfl_u(P3.y), P3.x), P3R = vmk(P3.y, shfl_d(P3.x));
@@ -320,10 +352,9 @@ __global__ void __launch_bounds__(128, 5) adj2v_kernel(Geom g, AdjArgs<T> a) {
         // lambda_{n-1} of row z = r - 2 from moment rows z-1 (p), z (c), z+1 (0)
         const int z = r - 2;
         if (z >= y0) {
-            const V u0 = uxA, u1 = uyA;
-            uxA = uxB;
-            uyA = uyB;
-            if (z + 2 <= y0 + R - 1) load_u(z + 2, uxB, uyB);
+            const V u0 = uxA, u1 = uyA, c0 = cxA, c1 = cyA;
+            uxA = uxB; uyA = uyB; cxA = cxB; cyA = cyB;
+            if (z + 2 <= y0 + R - 1) load_u(z + 2, uxB, uyB, cxB, cyB);
             const V xxL = vmk(shfl_u(xxc.y), xxc.x), xxR = vmk(xxc.y, shfl_d(xxc.x));
             const V xyL = vmk(shfl_u(xyc.y), xyc.x), xyR = vmk(xyc.y, shfl_d(xyc.x));
             if (lane_out && z < ny) {
@@ -335,19 +366,19 @@ __global__ void __launch_bounds__(128, 5) adj2v_kernel(Geom g, AdjArgs<T> a) {
                 vy = vfma(c3, myc, vfma(vmul(cm3, u1), m0c, vy));
                 vx = vfma(vA, vadd(vsub(xxL, xxR), vsub(xyp, xy0)), vx);
                 vy = vfma(vA, vadd(vsub(xyL, xyR), vsub(yyp, yy0)), vy);
-                const int wy = wall_side(z, ny, g.periodic[1]);
-                const bool we = wy >= 0 || wall_side(xe, nx, g.periodic[0]) >= 0;
-                const bool wo = wy >= 0 || wall_side(xe + 1, nx, g.periodic[0]) >= 0;
-                const bool py = a.src && z >= g.probe_lo[1] && z < g.probe_hi[1];
-                if (py && pxe && !we) {
-                    const T f = src_factor(a, a.dir[0] * u0.x + a.dir[1] * u1.x);
-                    vx.x += a.phi_dir[0] * f;
-                    vy.x += a.phi_dir[1] * f;
-                }
-                if (py && pxo && !wo) {
-                    const T f = src_factor(a, a.dir[0] * u0.y + a.dir[1] * u1.y);
-                    vx.y += a.phi_dir[0] * f;
-                    vy.y += a.phi_dir[1] * f;
+                const bool wy = wall_side(z, ny, g.periodic[1]) >= 0;
+                const bool we = wy || wxe, wo = wy || wxo;
+                if (a.src && z >= g.probe_lo[1] && z < g.probe_hi[1]) {
+                    if (pxe && !we) {
+                        const T f = src_factor(a, a.dir[0] * u0.x + a.dir[1] * u1.x);
+                        vx.x += a.phi_dir[0] * f;
+                        vy.x += a.phi_dir[1] * f;
+                    }
+                    if (pxo && !wo) {
+                        const T f = src_factor(a, a.dir[0] * u0.y + a.dir[1] * u1.y);
+                        vx.y += a.phi_dir[0] * f;
+                        vy.y += a.phi_dir[1] * f;
+                    }
                 }
                 V* oP = reinterpret_cast<V*>(a.lam_out);
                 V* oX = reinterpret_cast<V*>(a.lam_out + N);
@@ -357,21 +388,25 @@ __global__ void __launch_bounds__(128, 5) adj2v_kernel(Geom g, AdjArgs<T> a) {
                 oY[go] = vy;
                 const int by = box_coord(z, P.xs[1], g.Fb[1], ny, g.periodic[1]);
                 if (by >= 0) {
-                    for (int s = 0; s < 2; ++s) {
-                        const int bx = s == 0 ? bxe : bxo;
-                        if (bx < 0) continue;
-                        const bool w = s == 0 ? we : wo;
-                        const long long bl = bx + (long long)g.Fb[0] * by;
-                        const long long gi = (long long)z * nx + xe + s;
-                        a.boxbuf[bl] = w ? (T)0 : a.lam_in[N + gi];
-                        a.boxbuf[g.Fbn + bl] = w ? (T)0 : a.lam_in[2 * N + gi];
-                        a.boxbuf[2 * g.Fbn + bl] = a.u_cur[gi];
-                        a.boxbuf[3 * g.Fbn + bl] = a.u_cur[N + gi];
+                    // records: raw lam_u of row z (0 on walls) and u_n
+                    const int bl = by * Fb0;
+                    if (bxe >= 0) {
+                        a.boxbuf[bl + bxe] = we ? zr : rx2.x;
+                        a.boxbuf[Fbn + bl + bxe] = we ? zr : ry2.x;
+                        a.boxbuf[2 * Fbn + bl + bxe] = c0.x;
+                        a.boxbuf[3 * Fbn + bl + bxe] = c1.x;
+                    }
+                    if (bxo >= 0) {
+                        a.boxbuf[bl + bxo] = wo ? zr : rx2.y;
+                        a.boxbuf[Fbn + bl + bxo] = wo ? zr : ry2.y;
+                        a.boxbuf[2 * Fbn + bl + bxo] = c0.y;
+                        a.boxbuf[3 * Fbn + bl + bxo] = c1.y;
                     }
                 }
             }
         }
-        // roll the moment rows
+        // roll the raw lam_u rows and the moment rows
+        rx2 = rx1; ry2 = ry1; rx1 = lxv; ry1 = lyv;
         xyp = xyc; yyp = yyc;
         m0c = m00; mxc = mx0; myc = my0; xxc = xx0; xyc = xy0; yyc = yy0;
         m00 = m01; mx0 = mx1; my0 = my1; xx0 = xx1; xy0 = xy1; yy0 = yy1;
