@@ -28,7 +28,7 @@
 extern "C" {
 #endif
 
-#define LKS_ABI_VERSION 2
+#define LKS_ABI_VERSION 3
 
 typedef enum lks_status {
     LKS_OK = 0,
@@ -65,11 +65,14 @@ enum { LKS_ADJ_DISCRETE = 0, LKS_ADJ_ALKS = 1 };                /* reverse sweep
  *                 and variance of n.u over the fluid nodes of O_target and steps 1..Nt; 0 = the mean E alone.
  *                 Any finite value.
  *  objective      LKS_OBJ_FLOW: J1 of Eq. objective1 (probe box, direction, phi_var).  LKS_OBJ_OAR: J2 of Eq.
- *                 objective2 for the translating body, J2 = F_L + w_D F_D, with F_L the mean over steps 1..Nt of
- *                 sum_D kappa^ref (u^ref_x - u^G_x) / |D| and F_D the sum over steps of u^G_y sum_D kappa^ref
- *                 (u^ref_y - u^G_y) / (drag_span |D|); u^ref is the velocity mapped back onto the design grid,
- *                 D the inner design grid.  Without rotation the torque term T of Eq. objective2 is zero.
+ *                 objective2, J2 = F_L + w_D F_D + w_T T, with F_L the mean over steps 1..Nt of
+ *                 sum_D F_x / |D|, F_D the sum over steps of u^G_y sum_D F_y / (drag_span |D|) and T the sum
+ *                 over steps of omega sum_D (r_x F_y - r_y F_x) / (2 pi l_m |D|), where F = kappa^ref (u^ref -
+ *                 u^S,ref) is the Brinkman force density on the design grid, u^ref the velocity mapped back onto
+ *                 it, r = x^ref - x^G the arm and D the inner design grid.  Without rotation (K_w = 0) T is zero.
  *  w_D, drag_span weight of F_D and x_2^max - x_2^min (cells, > 0) of Eq. objective2 (LKS_OBJ_OAR only).
+ *  w_T, l_m       weight of T and the moment arm l_m (cells, > 0) of Eq. objective2 (LKS_OBJ_OAR with a rotating
+ *                 body; ignored without rotation).
  *  Nt, K          time steps and motion knots (knot k at step k Nt/(K-1)); K >= 2.
  *  R_t            temporal filter radius in steps (Eq. chi_filtered), > 0.
  *  filter_R       density filter radius in design cells (Eq. filtering); <= 1 means identity.
@@ -151,6 +154,8 @@ typedef struct lks_params {
     int32_t K_w;
     int32_t adjoint;
     double R_w;
+    double w_T;
+    double l_m;
 } lks_params;
 
 typedef struct lks_ctx lks_ctx;

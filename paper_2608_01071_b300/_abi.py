@@ -61,6 +61,8 @@ class lks_params(C.Structure):
         ("K_w", C.c_int32),
         ("adjoint", C.c_int32),
         ("R_w", C.c_double),
+        ("w_T", C.c_double),
+        ("l_m", C.c_double),
     ]
 
 

@@ -72,6 +72,8 @@ def params_from_workload(w: dict) -> _abi.lks_params:
     p.objective = _OBJ[objective]
     p.w_D = w.get("w_D", 0.0)
     p.drag_span = w.get("drag_span", 1.0)
+    p.w_T = w.get("w_T", 0.0)
+    p.l_m = w.get("l_m", 1.0)
     p.K_w = w.get("K_w", 0)
     adj = w.get("adjoint", "discrete")
     if adj not in ("discrete", "alks"):

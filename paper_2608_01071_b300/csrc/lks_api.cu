@@ -77,8 +77,12 @@ struct lks_ctx {
     OarGeom ogeo{};
     int nbox = 0;         // blocks of the footprint-box kernels (objective J2 scratch stride)
     double *d_oslot = nullptr, *d_oms = nullptr, *d_oar_guG = nullptr, *d_oar_dK = nullptr;
+    // J2 with a rotating body: compensated d j2 / d kappa^ref (state precision, nde each), K / M1 / I, per-step
+    // d/dtheta and d/domega, and the scratch of the constants' last-block sum
+    void *d_okh = nullptr, *d_okl = nullptr;
+    double *d_ocst = nullptr, *d_ocscr = nullptr, *d_oar_gth = nullptr, *d_oar_gom = nullptr;
     double *d_oscr = nullptr, *d_omsscr = nullptr;  // per-block partials of one step (J2 forward / sensitivities)
-    unsigned* d_otick = nullptr;                     // last-block tickets: [0] forward, [1 + s] sensitivity step s
+    unsigned* d_otick = nullptr;  // last-block tickets: [0] forward, [1 + s] sensitivity step s, [Lmax + 1] constants
     long long nd = 0, nde = 0;
     std::string err;
     lks_stats stats;
@@ -231,7 +235,8 @@ void validate(const lks_params* p) {
     if (p->K_w != 0) {
         if (p->K_w < 2 || p->K_w > 1000000) bad("K_w must be 0 (no rotation) or >= 2 angle knots");
         if (!(p->R_w > 0.0)) bad("R_w must be > 0 with a rotating body");
-        if (p->objective != LKS_OBJ_FLOW) bad("a rotating body needs objective LKS_OBJ_FLOW (J2's torque term is not built)");
+        if (p->objective == LKS_OBJ_OAR && (!(p->l_m > 0.0) || !std::isfinite(p->l_m) || !std::isfinite(p->w_T)))
+            bad("J2 with a rotating body needs l_m > 0 and a finite w_T");
         if (p->tile_rows > 1 || p->tile_rows_rec > 1)
             bad("with a rotating body the forward sweep runs step-kernel variant 1 (tile_rows 0 or 1)");
     }
@@ -302,6 +307,7 @@ void setup_geometry(lks_ctx* c) {
     c->oar = p.objective == LKS_OBJ_OAR;
     c->ogeo.cL = 1.0 / ((double)p.Nt * nD);
     c->ogeo.cD = c->oar ? p.w_D / (p.drag_span * nD) : 0.0;
+    c->ogeo.cT = c->oar && p.K_w > 0 ? p.w_T / (2.0 * M_PI * p.l_m * nD) : 0.0;
     for (int a = 0; a < c->D; ++a) {
         const double center = std::isnan(p.base_center[a]) ? (p.n[a] - 1) / 2.0 : p.base_center[a];
         c->o0[a] = center - (g.nde[a] - 1) / 2.0;
@@ -719,17 +725,29 @@ void allocate(lks_ctx* c) {
     c->g.obj = c->d_J;
     if (c->oar) {
         c->nbox = (int)nblk(c->g.Fbn, 256);
+        const int onv = c->rot ? kOarRotNV : 2;  // per-step sums
+        const long long ndb = nblk(c->nde, 256);
         // per-step sums only: the block partials of a launch live in scratch until its last block sums them
-        c->d_oslot = (double*)dalloc(c, (size_t)(p.Nt + 1) * 2 * 8);
+        c->d_oslot = (double*)dalloc(c, (size_t)(p.Nt + 1) * onv * 8);
         c->d_oms = (double*)dalloc(c, (size_t)(p.Nt + 1) * D * 8);
         LKS_CUDA(cudaMemset(c->d_oms, 0, (size_t)(p.Nt + 1) * D * 8));
-        c->d_oscr = (double*)dalloc(c, (size_t)c->nbox * 2 * 8);
+        c->d_oscr = (double*)dalloc(c, (size_t)std::max<long long>((long long)c->nbox * 2, c->rot ? ndb * onv : 0) * 8);
+        if (c->rot) {
+            c->d_okh = dalloc(c, (size_t)c->nde * ts);
+            c->d_okl = dalloc(c, (size_t)c->nde * ts);
+            c->d_ocst = (double*)dalloc(c, 4 * 8);
+            c->d_ocscr = (double*)dalloc(c, (size_t)ndb * 4 * 8);
+            c->d_oar_gth = (double*)dalloc(c, (size_t)(p.Nt + 1) * 8);
+            c->d_oar_gom = (double*)dalloc(c, (size_t)(p.Nt + 1) * 8);
+            LKS_CUDA(cudaMemset(c->d_oar_gth, 0, (size_t)(p.Nt + 1) * 8));
+            LKS_CUDA(cudaMemset(c->d_oar_gom, 0, (size_t)(p.Nt + 1) * 8));
+        }
         c->d_omsscr = (double*)dalloc(c, (size_t)c->Lmax * c->nbox * D * 8);
-        c->d_otick = (unsigned*)dalloc(c, (size_t)(c->Lmax + 1) * sizeof(unsigned));
-        LKS_CUDA(cudaMemset(c->d_otick, 0, (size_t)(c->Lmax + 1) * sizeof(unsigned)));
+        c->d_otick = (unsigned*)dalloc(c, (size_t)(c->Lmax + 2) * sizeof(unsigned));
+        LKS_CUDA(cudaMemset(c->d_otick, 0, (size_t)(c->Lmax + 2) * sizeof(unsigned)));
         c->d_oar_guG = (double*)dalloc(c, (size_t)(p.Nt + 1) * D * 8);
         c->d_oar_dK = (double*)dalloc(c, 8);
-        LKS_CUDA(cudaMemset(c->d_oslot, 0, (size_t)(p.Nt + 1) * 2 * 8));
+        LKS_CUDA(cudaMemset(c->d_oslot, 0, (size_t)(p.Nt + 1) * onv * 8));
         LKS_CUDA(cudaMemset(c->d_oar_guG, 0, (size_t)(p.Nt + 1) * D * 8));
     }
     c->d_flag = (unsigned*)dalloc(c, 16);
@@ -984,6 +1002,12 @@ void fwd_pair(lks_ctx* c, int n, const void* in, void* out1, void* out2, bool ob
 
 // Objective J2: the footprint partials of state n (read before its buffer is reused, in stream order).
 void oar_partial(lks_ctx* c, int n, const void* st, cudaStream_t s) {
+    if (c->rot) {
+        c->eng->oar_rot_partial(c->g, c->ogeo, c->d_pose + n, c->d_kref, st, c->d_okh, c->d_okl, c->d_oscr,
+                                c->d_otick, c->d_oslot + (long long)kOarRotNV * n, s);
+        c->launches++;
+        return;
+    }
     c->eng->oar_partial(c->g, c->d_pose + n, c->d_kref, st, c->d_oscr, c->d_otick, c->d_oslot + 2LL * n, s);
     c->launches++;
 }
@@ -1072,6 +1096,14 @@ void forward_body(lks_ctx* c, cudaStream_t s) {
     else
         c->eng->init_state(c->g, c->slot[0], s);
     c->launches++;
+    if (c->oar && c->rot) {  // J2 with a rotating body: clear the per-node accumulation, K / M1 / I of kappa^ref
+        LKS_CUDA(cudaMemsetAsync(c->d_okh, 0, (size_t)c->nde * c->tsize, s));
+        LKS_CUDA(cudaMemsetAsync(c->d_okl, 0, (size_t)c->nde * c->tsize, s));
+        oar_rot_const_kernel<<<nblk(c->nde, 256), 256, 0, s>>>(c->d_kref64, c->g.nde[0], c->g.nde[1], c->g.nde[2],
+                                                               c->d_ocscr, c->d_otick + c->Lmax + 1, c->d_ocst);
+        LKS_LAUNCHED();
+        c->launches++;
+    }
     PingPong pp{c};
     cudaEvent_t e0 = span_begin(c, s);
     // state n goes to the final buffer, its checkpoint slot, or a ping-pong buffer
@@ -1093,7 +1125,12 @@ void forward_body(lks_ctx* c, cudaStream_t s) {
                                               c->d_jstep, c->d_J);
     LKS_LAUNCHED();
     c->launches++;
-    if (c->oar) {
+    if (c->oar && c->rot) {
+        oar_rot_reduce_kernel<<<1, 256, 0, s>>>(c->ogeo, c->d_oslot, Nt, c->d_pose, c->d_ocst, c->D, c->d_J, c->d_oms,
+                                                c->d_oar_guG, c->d_oar_gth, c->d_oar_gom);
+        LKS_LAUNCHED();
+        c->launches++;
+    } else if (c->oar) {
         oar_reduce_kernel<<<1, 256, 0, s>>>(c->ogeo, c->d_oslot, Nt, c->d_pose, c->d_kref64, (long long)c->nde,
                                             c->D, c->d_J, c->d_oar_guG, c->d_oar_dK);
         LKS_LAUNCHED();
@@ -1175,7 +1212,10 @@ void adjoint_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
         const void* fc = c->tptr(c->d_fac, ((long long)buf * c->Lmax + j) * c->g.Fbn);
         // J2 adds the source of step n to lambda_n before the step reads it, so its steps go one per launch
         if (c->oar) {
-            c->eng->oar_source(c->g, c->ogeo, c->d_pose + n, c->d_kref, c->lam[0], s);
+            if (c->rot)
+                c->eng->oar_rot_source(c->g, c->ogeo, c->d_pose + n, c->d_kref, c->lam[0], s);
+            else
+                c->eng->oar_source(c->g, c->ogeo, c->d_pose + n, c->d_kref, c->lam[0], s);
             c->launches++;
         }
         if (c->eng->fused_adj2() && n - 1 > a && !c->oar) {  // steps n and n-1 in one launch
@@ -1378,10 +1418,19 @@ void adjoint_body(lks_ctx* c, cudaStream_t s) {
         const bool cap = s == c->cap;
         reverse_sqrt_pipelined(c, s, cap ? c->cap2 : c->side, cap ? c->cap3 : c->side2);
     }
-    if (c->oar) {  // J2's position terms and its explicit dependences on u^G and kappa^ref
+    if (c->oar) {  // J2's position terms and its explicit dependences on u^G and kappa^ref (and theta, omega)
         const long long nmax = std::max<long long>((long long)c->nde, (long long)Nt + 1);
-        oar_apply_kernel<<<nblk(nmax, 256), 256, 0, s>>>(Nt, D, c->d_oms, c->d_oar_guG, c->d_gs, c->d_guG,
-                                                         c->d_oar_dK, c->d_dkref, (long long)c->nde);
+        if (c->rot && c->tsize == 4)
+            oar_rot_apply_kernel<float><<<nblk(nmax, 256), 256, 0, s>>>(
+                Nt, D, c->d_oms, c->d_oar_guG, c->d_oar_gth, c->d_oar_gom, (const float*)c->d_okh,
+                (const float*)c->d_okl, c->d_gs, c->d_guG, c->d_gth, c->d_gom, c->d_dkref, (long long)c->nde);
+        else if (c->rot)
+            oar_rot_apply_kernel<double><<<nblk(nmax, 256), 256, 0, s>>>(
+                Nt, D, c->d_oms, c->d_oar_guG, c->d_oar_gth, c->d_oar_gom, (const double*)c->d_okh,
+                (const double*)c->d_okl, c->d_gs, c->d_guG, c->d_gth, c->d_gom, c->d_dkref, (long long)c->nde);
+        else
+            oar_apply_kernel<<<nblk(nmax, 256), 256, 0, s>>>(Nt, D, c->d_oms, c->d_oar_guG, c->d_gs, c->d_guG,
+                                                             c->d_oar_dK, c->d_dkref, (long long)c->nde);
         LKS_LAUNCHED();
         c->launches++;
     }
@@ -1604,6 +1653,7 @@ int lks_default_params(lks_params* p) {
     p->ckpt = LKS_CKPT_FULL;
     p->mode = LKS_MODE_JOINT;
     p->u_crit = 0.3;
+    p->l_m = 1.0;
     return LKS_OK;
 }
 

@@ -14,6 +14,7 @@
 #include "lks_step_kernels.cuh"
 #include "lks_oar.cuh"
 #include "lks_rot.cuh"
+#include "lks_oar_rot.cuh"
 #include "lks_alks.cuh"
 
 namespace lks {
@@ -111,6 +112,12 @@ struct Engine {
     virtual void oar_sens(const Geom& g, const OarGeom& o, const Pose* poses, const void* kref, const void* boxbuf,
                           long long bstride, int n_first, int nsteps, void* kbar, double* scratch, unsigned* tickets,
                           double* oms, cudaStream_t s) = 0;
+    // objective J2 with a rotating body (lks_oar_rot.cuh): the per-step design-side sums and the compensated
+    // d j2 / d kappa^ref accumulation (kh, kl: state precision, extended design grid); the adjoint source
+    virtual void oar_rot_partial(const Geom& g, const OarGeom& o, const Pose* pose, const void* kref, const void* st,
+                                 void* kh, void* kl, double* scratch, unsigned* ticket, double* slot, cudaStream_t s) = 0;
+    virtual void oar_rot_source(const Geom& g, const OarGeom& o, const Pose* pose, const void* kref, void* lam,
+                                cudaStream_t s) = 0;
     virtual void export_state(const Geom& g, const void* st, double* p, double* u, double pshift, cudaStream_t s) = 0;
     // rotating body (lks_rot.cuh): kappa and u^S of one step on the footprint box; 1 / (1 + kappa) for a segment's
     // steps; the local sensitivities of a segment (kappa-bar, u^S-bar per box node, per-block motion partials); the
@@ -267,6 +274,18 @@ struct EngineCommon : Engine {
                      unsigned* ticket, double* slot, cudaStream_t s) override {
         oar_partial_kernel<T, D, HW><<<nblk(g.Fbn, 256), 256, 0, s>>>(g, pose, (const T*)kref, (const T*)st, scratch,
                                                                      ticket, slot);
+        LKS_LAUNCHED();
+    }
+    void oar_rot_partial(const Geom& g, const OarGeom& o, const Pose* pose, const void* kref, const void* st, void* kh,
+                         void* kl, double* scratch, unsigned* ticket, double* slot, cudaStream_t s) override {
+        const long long nd = (long long)g.nde[0] * g.nde[1] * g.nde[2];
+        oar_rot_partial_kernel<T, D, HW><<<nblk(nd, 256), 256, 0, s>>>(g, o, pose, (const T*)kref, (const T*)st, (T*)kh,
+                                                                       (T*)kl, scratch, ticket, slot);
+        LKS_LAUNCHED();
+    }
+    void oar_rot_source(const Geom& g, const OarGeom& o, const Pose* pose, const void* kref, void* lam,
+                        cudaStream_t s) override {
+        oar_rot_source_kernel<T, D, HW><<<nblk(g.Fbn, 256), 256, 0, s>>>(g, o, pose, (const T*)kref, (T*)lam);
         LKS_LAUNCHED();
     }
     void oar_source(const Geom& g, const OarGeom& o, const Pose* pose, const void* kref, void* lam,

@@ -1,4 +1,5 @@
-// Objective J2 of Eq. objective2 (the oar) for a translating body, and its adjoint pieces.
+// Objective J2 of Eq. objective2 (the oar) for a translating body, and its adjoint pieces (a rotating body:
+// lks_oar_rot.cuh).
 //
 // Without rotation x^ref_j = j + o_n, so the design-grid integral sum_j kappa^ref_j u^ref_{j,b}, with u^ref_j the
 // velocity mapped back onto node j (sum_x W(x - x^ref_j) u(x)), equals sum_x kappa_n(x) u_{n,b}(x): both are the sum
@@ -26,15 +27,14 @@ namespace lks {
 struct OarGeom {
     double cL;  // 1 / (Nt |D|): weight of sum_x kappa u_x in F_L
     double cD;  // w_D / (drag_span |D|): weight of u^G_y sum_x kappa u_y in w_D F_D
+    double cT;  // w_T / (2 pi l_m |D|): weight of omega sum_j r_j x F_j in w_T T (rotating body only)
 };
 
 // Analysis node of footprint-box node bl of a pose: its box coordinates b, grid coordinates x and node index, or
 // -1 outside the grid (wall axes; periodic axes fold into one period, the box being shorter than a period).
 template <int D>
 __device__ __forceinline__ long long oar_box_node(const Geom& g, const Pose& P, long long bl, int (&b)[3], int (&x)[3]) {
-    b[0] = (int)(bl % g.Fb[0]);
-    b[1] = (int)((bl / g.Fb[0]) % g.Fb[1]);
-    b[2] = (int)(bl / ((long long)g.Fb[0] * g.Fb[1]));
+    box_unflatten<D>(g, bl, b);
     long long gi = 0, stride = 1;
     x[2] = 0;
 #pragma unroll

@@ -13,7 +13,7 @@ def oracle_problem(w, **kw):
                   direction=tuple(w["direction"]), base_center=w.get("base_center"),
                   wall_velocity=dict(w.get("wall_velocity", {})), phi_var=w.get("phi_var", 0.0),
                   objective=w.get("objective", "J1"), w_D=w.get("w_D", 0.0), drag_span=w.get("drag_span", 1.0),
-                  R_w=w.get("R_w", 1.0))
+                  w_T=w.get("w_T", 0.0), l_m=w.get("l_m", 1.0), R_w=w.get("R_w", 1.0))
     return P
 
 

@@ -102,6 +102,37 @@ def test_zero_angle_equals_translation():
     assert rel_l2(g["dgamma"], dg0) <= 1e-12 and rel_l2(g["dknots"], dk0) <= 1e-12
 
 
+OAR_ROT = dict(objective="J2", w_D=0.3, drag_span=9.0, w_T=0.7, l_m=5.0)
+
+
+@pytest.mark.parametrize("lattice,kernel,prec", [("D2Q9", "linear", "fp64"), ("D2Q9", "cosine", "fp64"),
+                                                 ("D3Q15", "linear", "fp64"), ("D2Q9", "linear", "fp32"),
+                                                 ("D3Q15", "linear", "fp32")])
+def test_rotating_oar_matches_oracle(lattice, kernel, prec):
+    # objective J2 with the torque term (Eq. objective2): force, drag work and torque work on the design grid of a
+    # rotating body, and their adjoint source and explicit derivatives (kappa^ref, position, u^G, theta, omega)
+    nt = 24 if lattice == "D2Q9" else 12
+    w = rot_workload(lattice, kernel=kernel, precision=prec, Nt=nt, **OAR_ROT)
+    g, o = check(w)
+    assert abs(o["J"]) > 0 and np.abs(o["daknots"]).max() > 0
+
+
+@pytest.mark.parametrize("ckpt", ["sqrt", "revolve"])
+def test_rotating_oar_checkpointed(ckpt):
+    w = rot_workload("D2Q9", precision="fp64", Nt=21, ckpt=ckpt, ckpt_slots=2, seg_len=4, **OAR_ROT)
+    g, _ = check(w)
+    assert g["stats"]["recompute_steps"] > 0
+
+
+def test_rotating_oar_torque_term_counts():
+    # the same run with and without the torque weight: the torque term's share is visible in J
+    w0 = rot_workload("D2Q9", precision="fp64", Nt=20, **dict(OAR_ROT, w_T=0.0))
+    w1 = rot_workload("D2Q9", precision="fp64", Nt=20, **OAR_ROT)
+    g0, _ = check(w0)
+    g1, _ = check(w1)
+    assert abs(g1["J"] - g0["J"]) > 1e-6 * abs(g0["J"])
+
+
 def test_rotating_body_across_periodic_seam():
     w = rot_workload("D2Q9", precision="fp64", Nt=20, base_center=(3.0, 18.0), probe_lo=(8, 10), probe_hi=(18, 27))
     check(w)
