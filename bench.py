@@ -448,6 +448,12 @@ def run_ours(args):
         e["role"] = "recomputation (beside the adjoint chain)"
         entries.append(e)
     entries.append(kernel_entry("adj", st0["tile_rows_adj"], adj_bytes, t_a, n_a))
+    if st0.get("pipelined"):
+        # the recomputation and the adjoint steps run at the same time on two streams: their live launch durations
+        # include the sharing, so their fractions understate each kernel alone; the path fraction measures the whole
+        for e in entries:
+            if e.get("role") != "forward sweep":
+                e["concurrent"] = "the recomputation and the adjoint chain share the GPU (two streams)"
     tot = max(1e-30, sum(e["_t"] for e in entries))
     for e in entries:
         # shares of the summed kernel spans (recompute overlaps the adjoint on its own stream)

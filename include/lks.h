@@ -81,7 +81,9 @@ enum { LKS_ADJ_DISCRETE = 0, LKS_ADJ_ALKS = 1 };                /* reverse sweep
  *                 sensitivity accumulation).
  *  ckpt           LKS_CKPT_FULL (every state kept), LKS_CKPT_SQRT (checkpoints every ceil(sqrt Nt) steps),
  *                 LKS_CKPT_REVOLVE (binomial schedule with ckpt_slots checkpoints, or as many as fit
- *                 in ckpt_bytes when ckpt_slots = 0).
+ *                 in ckpt_bytes when ckpt_slots = 0).  When the slots hold every segment boundary (and, under a
+ *                 byte budget, a second recompute history fits too) the schedule is the sqrt one, and the reverse
+ *                 sweep is pipelined like LKS_CKPT_SQRT's.
  *  seg_len        recompute-segment length for REVOLVE (0 = automatic).
  *  mode           which gradients lks_adjoint produces (the others are returned as zeros).
  *  u_crit         stability limit on |u| checked every forward step (<= 0 disables); LKS_EUNSTABLE.
@@ -172,7 +174,7 @@ typedef struct lks_stats {
     int32_t tile_rows_fwd;     /* step-kernel variants (tile_rows codes) of the forward sweep, */
     int32_t tile_rows_adj;     /* the adjoint steps */
     int32_t tile_rows_rec;     /* and the recomputation in lks_adjoint */
-    int32_t reserved;
+    int32_t pipelined;         /* 1: the reverse sweep runs the recomputation beside the adjoint chain */
     /* With lks_set_timing(ctx, 1): device time (CUDA events on the launching stream) of the last call pair. */
     double ms_forward_steps;   /* the Nt forward-step kernels of lks_forward */
     double ms_recompute_steps; /* forward-step kernels re-run by lks_adjoint */

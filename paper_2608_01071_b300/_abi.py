@@ -78,7 +78,7 @@ class lks_stats(C.Structure):
         ("tile_rows_fwd", C.c_int32),
         ("tile_rows_adj", C.c_int32),
         ("tile_rows_rec", C.c_int32),
-        ("reserved", C.c_int32),
+        ("pipelined", C.c_int32),
         ("ms_forward_steps", C.c_double),
         ("ms_recompute_steps", C.c_double),
         ("ms_adjoint_steps", C.c_double),

@@ -142,6 +142,9 @@ struct lks_ctx {
     int M = 1;             // number of segments
     int Lmax = 1;          // longest segment (sensitivity buffer depth)
     int free_slots = 0;    // REVOLVE: slots besides boundary 0
+    // the reverse sweep pipelines recomputation, adjoint and sensitivities on three streams with two history buffers:
+    // SQRT, and REVOLVE when the slots hold every segment boundary (the binomial schedule is then the sqrt one)
+    bool pipelined = false;
     std::vector<int> chain;  // REVOLVE: boundaries stored by the forward sweep (after 0)
     std::vector<int> slot_of;  // boundary -> slot index or -1
     std::vector<int> slot_used;
@@ -375,6 +378,8 @@ void plan_checkpoints(lks_ctx* c, size_t state_bytes) {
             long long avail = p.ckpt_bytes > 0 ? p.ckpt_bytes - fixed : 0;
             freec = (int)std::max<long long>(1, avail / (long long)state_bytes - 1);
         }
+        // every boundary fits, and (under a byte budget) so does a second history buffer: pipeline the sweep
+        c->pipelined = c->M > 1 && freec >= c->M - 1 && (p.ckpt_slots > 0 || freec >= c->M - 1 + c->S);
         freec = std::max(1, std::min(freec, c->M - 1 > 0 ? c->M - 1 : 1));
         c->free_slots = freec;
         nslots = 1 + freec;
@@ -390,6 +395,7 @@ void plan_checkpoints(lks_ctx* c, size_t state_bytes) {
     } else {
         // FULL: every state; SQRT: boundaries 0, S, 2S, ... below Nt
         nslots = c->M;
+        c->pipelined = p.ckpt == LKS_CKPT_SQRT;
     }
     c->slot_of.assign(c->M + 1, -1);
     c->slot_used.assign(nslots, 0);
@@ -651,7 +657,8 @@ void autotune_rows(lks_ctx* c) {
 // variant.  In the pipelined sqrt(N) reverse sweep the recomputation and the adjoint chain run at the same time
 // and share the GPU, and in a batch all instances do: there the one-step pair timed side by side wins (two-step
 // launches recompute a halo; on 512x256 (two-step, two-step) gave 13.0 and the side-by-side pair of 8-row tiles
-// 15.0 G node-steps/s).  Binomial and full-storage reverse sweeps run one chain and take the fastest variants.
+// 15.0 G node-steps/s).  A binomial schedule whose slots hold every segment boundary is the sqrt layout and is
+// pipelined the same way; other binomial and full-storage reverse sweeps run one chain and take the fastest variants.
 // Explicit tile_rows fix all of them.
 void choose_variants(lks_ctx* c) {
     if (c->prm.tile_rows != 0) {
@@ -659,7 +666,7 @@ void choose_variants(lks_ctx* c) {
         c->rows_rec = c->prm.tile_rows_rec != 0 ? c->prm.tile_rows_rec : c->eng->rows_f;
         c->rows_adj = c->eng->rows_a;
     } else {
-        const bool shared = c->throughput || c->prm.ckpt == LKS_CKPT_SQRT;
+        const bool shared = c->throughput || c->pipelined;
         c->rows_fwd_sweep = c->throughput ? c->tune_f_one : c->tune_f_lat;
         c->rows_rec = shared ? c->tune_f_one : c->tune_f_lat;
         c->rows_adj = shared ? c->tune_a_one : c->tune_a_lat;
@@ -682,7 +689,7 @@ void allocate(lks_ctx* c) {
         // the plan's large buffers (states, footprint-box records and factors, per-step slots) against the free
         // device memory, before any of them is allocated
         const long long S1 = (long long)c->S;
-        const long long hist = p.ckpt == LKS_CKPT_FULL ? 0 : (p.ckpt == LKS_CKPT_SQRT ? 2 * S1 : S1);
+        const long long hist = p.ckpt == LKS_CKPT_FULL ? 0 : (c->pipelined ? 2 * S1 : S1);
         const long long states = (long long)c->slot_used.size() + hist + 7;
         const long long Lmax = c->Lmax, Fbn = c->g.Fbn;
         double need = (double)states * (double)c->state_bytes;
@@ -786,8 +793,8 @@ void allocate(lks_ctx* c) {
     for (auto& s : c->slot) s = dalloc(c, sb);
     for (int h = 0; h < 2; ++h) {
         c->hist[h].assign(c->S + 1, nullptr);
-        // the second buffer serves the pipelined sqrt sweep only
-        if (p.ckpt != LKS_CKPT_FULL && (h == 0 || p.ckpt == LKS_CKPT_SQRT))
+        // the second buffer serves the pipelined sweep only
+        if (p.ckpt != LKS_CKPT_FULL && (h == 0 || c->pipelined))
             for (int k = 1; k <= c->S; ++k) c->hist[h][k] = dalloc(c, sb);
     }
     c->pp[0] = dalloc(c, sb);
@@ -804,6 +811,7 @@ void allocate(lks_ctx* c) {
     }
     c->stats.ckpt_slots = (int32_t)c->slot.size();
     c->stats.seg_len = c->S;
+    c->stats.pipelined = c->pipelined ? 1 : 0;
 
     LKS_CUDA(cudaHostAlloc((void**)&c->h_flag, 16, cudaHostAllocDefault));
     *c->h_flag = 0;
@@ -1407,7 +1415,7 @@ void adjoint_body(lks_ctx* c, cudaStream_t s) {
         c->eng->add_state(c->g, c->lam[0], c->d_lterm, s);
         c->launches++;
     }
-    if (c->prm.ckpt == LKS_CKPT_REVOLVE) {
+    if (c->prm.ckpt == LKS_CKPT_REVOLVE && !c->pipelined) {
         reverse_revolve(c, 0, c->M, c->free_slots, c->slot[0], s);
     } else if (c->prm.ckpt == LKS_CKPT_FULL) {
         for (int b = Nt; b > 0; b -= c->Lmax) {

@@ -77,10 +77,11 @@ def test_checkpointing_bitwise(lattice, rows, prec):
     w = tiny_workload(lattice, precision=prec, Nt=47, tile_rows=rows, **({"shape": (94, 45)} if rows != 32 else {}))
     gamma, knots = draw_gamma(w), draw_knots(w)
     runs = {}
+    # revolve_all: slots for every segment boundary, so the binomial sweep runs pipelined like the sqrt one
     for ck, extra in [("full", {}), ("sqrt", {}), ("revolve", dict(ckpt_slots=2, seg_len=3)),
-                      ("revolve1", dict(ckpt_slots=1, seg_len=5))]:
+                      ("revolve1", dict(ckpt_slots=1, seg_len=5)), ("revolve_all", dict(ckpt_slots=100, seg_len=5))]:
         ww = dict(w, **extra)
-        ww["ckpt"] = "revolve" if ck == "revolve1" else ck
+        ww["ckpt"] = "revolve" if ck.startswith("revolve") else ck
         runs[ck] = gpu_run(ww, gamma, knots)
     base = runs["full"]
     for k, r in runs.items():
@@ -89,6 +90,8 @@ def test_checkpointing_bitwise(lattice, rows, prec):
         assert np.array_equal(r["dknots"], base["dknots"]), k
     assert runs["sqrt"]["stats"]["recompute_steps"] > 0
     assert runs["revolve"]["stats"]["recompute_steps"] > runs["sqrt"]["stats"]["recompute_steps"]
+    assert runs["sqrt"]["stats"]["pipelined"] == 1 and runs["revolve_all"]["stats"]["pipelined"] == 1
+    assert runs["revolve"]["stats"]["pipelined"] == 0 and runs["full"]["stats"]["pipelined"] == 0
 
 
 def test_deterministic_double_run():
