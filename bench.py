@@ -47,6 +47,8 @@ def parse():
                     "iterations (gamma step 0.05, position step 0.5 cell, normalised) and report J and s/iteration")
     ap.add_argument("--phi-var", type=float, default=0.0, help="weight phi of the variance term of the objective "
                     "(J1 = E - phi V); 0 = the mean E alone")
+    ap.add_argument("--objective", choices=["J1", "J2"], default="J1", help="J1 (Eq. objective1, the workload's "
+                    "probe box) or J2 (Eq. objective2, the oar: F_L + 0.3 F_D with drag_span = the design's y extent)")
     ap.add_argument("--tile-rows", default="", help="force step-kernel variants instead of autotuning: F, F,A or "
                     "F,A,R (tile_rows codes of the forward sweep, the adjoint and the recomputation)")
     return ap.parse_args()
@@ -180,8 +182,18 @@ def captured_traffic(workload_name, kernel, source):
 
 
 def objective_name(w):
+    if w.get("objective", "J1") == "J2":
+        return f"J2 = F_L + {w['w_D']:g} F_D (the Brinkman force on the design grid)"
     phi = w.get("phi_var", 0.0)
     return "E (mean of n.u over the probe box)" if phi == 0.0 else f"E - {phi:g} V (mean and variance of n.u)"
+
+
+def bench_workload(args):
+    """The named workload with the command line's objective settings."""
+    w = dict(workload(args.workload), phi_var=args.phi_var)
+    if args.objective == "J2":
+        w = dict(w, objective="J2", phi_var=0.0, w_D=0.3, drag_span=float(w["design"][1]))
+    return w
 
 
 def node_count(w):
@@ -302,7 +314,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = dict(workload(args.workload), phi_var=args.phi_var)
+    w = bench_workload(args)
     sample_steps = sample_steps_for(w)
     times = []
     for i in range(args.warmup + args.steps):
@@ -335,7 +347,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group(backend="nccl")
 
-    w = dict(workload(args.workload), phi_var=args.phi_var)
+    w = bench_workload(args)
     if args.nt > 0:  # shorter horizon, same body speed
         w = dict(w, Nt=args.nt, K=min(w["K"], max(2, args.nt // 4)), R_t=max(1.0, w["R_t"] * args.nt / w["Nt"]),
                  amp=w["amp"] * args.nt / w["Nt"])
