@@ -24,6 +24,8 @@ struct Engine2D : EngineCommon<T, 2, HW> {
         LKS_CUDA(cudaFuncSetAttribute(fwd2r_kernel<T, HW, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_fwd<T, 2>()));
         LKS_CUDA(cudaFuncSetAttribute(adj2r_kernel<T, HW, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_adj<T, 1>()));
         LKS_CUDA(cudaFuncSetAttribute(adj2r_kernel<T, HW, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2r_adj<T, 2>()));
+        LKS_CUDA(cudaFuncSetAttribute(adj2v_kernel<T, HW, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Adj2vRing<T>::bytes()));
+        LKS_CUDA(cudaFuncSetAttribute(adj2v_kernel<T, HW, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Adj2vRing<T>::bytes()));
         this->alks_attr();
         set_rows(1, 1, g);
     }
@@ -120,8 +122,8 @@ struct Engine2D : EngineCommon<T, 2, HW> {
             case 2: launch_pdl(adj2r_kernel<T, HW, 2>, this->agrid, this->athreads, smem2r_adj<T, 2>(), s, this->pdl, g, a); break;
             case 4: adj_r<4>(g, a, s); break;
             case 8: adj_r<8>(g, a, s); break;
-            case 32: launch_pdl(adj2v_kernel<T, HW, 32>, this->agrid, this->athreads, 0, s, this->pdl, g, a); break;
-            case 64: launch_pdl(adj2v_kernel<T, HW, 64>, this->agrid, this->athreads, 0, s, this->pdl, g, a); break;
+            case 32: launch_pdl(adj2v_kernel<T, HW, 32>, this->agrid, this->athreads, Adj2vRing<T>::bytes(), s, this->pdl, g, a); break;
+            case 64: launch_pdl(adj2v_kernel<T, HW, 64>, this->agrid, this->athreads, Adj2vRing<T>::bytes(), s, this->pdl, g, a); break;
             default: adj_r<(sizeof(T) == 4 ? 16 : 8)>(g, a, s); break;
         }
     }

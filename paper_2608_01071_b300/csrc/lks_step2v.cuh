@@ -218,16 +218,33 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (HW == 1 ? 7 : 5) : 4) f
 
 // ------------------------------------------------------------------------------------------------
 // Adjoint step lambda_n -> lambda_{n-1}, recording lam_u and u_n on the footprint box.
-// The rows' uniform work (wrap, wall test, footprint row) is done once per row; a source row arrives two rows
-// ahead of use together with its 1/(1 + kappa) factors, and the output row's u_{n-1} (and u_n on footprint rows)
-// two rows ahead as well; the raw lam_u of the output row, for its footprint record, is kept from its source pass.
-// Indices are 32-bit (offered when 3 N and 4 F_b fit).
+// Each lane fetches its own data (its column pair of the source row's lambda, the source row's 1/(1 + kappa) on
+// footprint rows, u_{n-1} and on footprint rows u_n of the output row) by asynchronous copies into a per-warp ring of
+// Adj2vRing::DEPTH rows in shared memory, DEPTH - 1 rows ahead of use, so that many rows are in flight without holding
+// them in registers; a lane reads back only what it copied, so the ring needs no barrier.  The row's
+// uniform work (wrap, wall test, footprint row) is done once per row.  Indices are 32-bit (offered when 3 N and
+// 4 F_b fit).
 // ------------------------------------------------------------------------------------------------
+template <typename T>
+struct Adj2vRing {
+    static constexpr int WY = 4;                               // warps per block
+    static constexpr int DEPTH = sizeof(T) == 4 ? 6 : 3;       // rows per warp ring
+    using V = typename Vec2<T>::type;
+    // per row and lane: lambda p, x, y and u_{n-1} x, y, u_n x, y (V each), then the factor pair (T each)
+    static constexpr size_t ROW_V = 7 * 32, ROW_T = 2 * 32;
+    static constexpr size_t bytes() { return (size_t)WY * DEPTH * (ROW_V * sizeof(V) + ROW_T * sizeof(T)); }
+};
+
 template <typename T, int HW, int R>
 __global__ void __launch_bounds__(128, 4) adj2v_kernel(Geom g, AdjArgs<T> a) {
     using V = typename Vec2<T>::type;
-    constexpr int WY = 4;
+    using RG = Adj2vRing<T>;
+    constexpr int WY = RG::WY, DEPTH = RG::DEPTH;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    V* rv = reinterpret_cast<V*>(smem_raw) + (size_t)warp * DEPTH * RG::ROW_V;                  // [DEPTH][7][32]
+    T* rt = reinterpret_cast<T*>(reinterpret_cast<V*>(smem_raw) + (size_t)WY * DEPTH * RG::ROW_V) +
+            (size_t)warp * DEPTH * RG::ROW_T;                                                      // [DEPTH][2][32]
     const int nx = g.n[0], ny = g.n[1];
     const int N = (int)g.N, Fbn = (int)g.Fbn, Fb0 = g.Fb[0];
     const int x0 = blockIdx.x * kVecCols;
@@ -255,75 +272,93 @@ __global__ void __launch_bounds__(128, 4) adj2v_kernel(Geom g, AdjArgs<T> a) {
     const bool pxe = xe >= g.probe_lo[0] && xe < g.probe_hi[0];
     const bool pxo = xe + 1 >= g.probe_lo[0] && xe + 1 < g.probe_hi[0];
     const T one = (T)1, zr = (T)0;
+    const int NRW = R + 4;  // source rows y0 - 2 .. y0 + R + 1; row t is source row y0 - 2 + t, output row y0 - 4 + t
     pdl_wait_then_release();
 
-    // source row r: raw lambda and the factor pair 1/(1 + kappa) off the walls, 0 on them
-    auto load = [&](int r, V& p, V& ux, V& uy, V& fc) {
-        const int yw = wrap(r, ny);
-        const int gi = yw * half + (xl >> 1);
-        p = lP[gi];
-        ux = lX[gi];
-        uy = lY[gi];
-        T fe = one, fo = one;
-        if (wall_side(yw, ny, g.periodic[1]) >= 0) {
-            fe = fo = zr;
-        } else {
-            const int by = box_coord(yw, P.xs[1], g.Fb[1], ny, g.periodic[1]);
-            if (by >= 0) {
-                if (a.fac != nullptr) {
+    // copy group t: source row r = y0 - 2 + t (lambda; factors on footprint rows) and output row z = r - 2 (u_{n-1};
+    // u_n on footprint rows), into ring slot t mod DEPTH
+    auto issue = [&](int t) {
+        if (t < NRW) {
+            V* sv = rv + (t % DEPTH) * RG::ROW_V;
+            T* st = rt + (t % DEPTH) * RG::ROW_T;
+            const int yw = wrap(y0 - 2 + t, ny);
+            const int gi = yw * half + (xl >> 1);
+            cp_async<sizeof(V)>(sv + lane, lP + gi);
+            cp_async<sizeof(V)>(sv + 32 + lane, lX + gi);
+            cp_async<sizeof(V)>(sv + 64 + lane, lY + gi);
+            if (a.fac != nullptr && wall_side(yw, ny, g.periodic[1]) < 0) {
+                const int by = box_coord(yw, P.xs[1], g.Fb[1], ny, g.periodic[1]);
+                if (by >= 0) {
                     const T* fr = a.fac + by * Fb0;
-                    if (sbxe >= 0) fe = fr[sbxe];
-                    if (sbxo >= 0) fo = fr[sbxo];
-                } else {
-                    if (sbxe >= 0) {
-                        const int b[2] = {sbxe, by};
-                        fe = adj_inv<T, 2, HW>(g, P, a.kref, nullptr, b);
-                    }
-                    if (sbxo >= 0) {
-                        const int b[2] = {sbxo, by};
-                        fo = adj_inv<T, 2, HW>(g, P, a.kref, nullptr, b);
-                    }
+                    if (sbxe >= 0) cp_async<sizeof(T)>(st + lane, fr + sbxe);
+                    if (sbxo >= 0) cp_async<sizeof(T)>(st + 32 + lane, fr + sbxo);
                 }
             }
-            if (swxe) fe = zr;
-            if (swxo) fo = zr;
+            const int z = y0 - 4 + t;
+            if (t >= 4 && lane_out && z < ny && z < y0 + R) {
+                const int gz = z * half + (xe >> 1);
+                cp_async<sizeof(V)>(sv + 96 + lane, upX + gz);
+                cp_async<sizeof(V)>(sv + 128 + lane, upY + gz);
+                if (box_coord(z, P.xs[1], g.Fb[1], ny, g.periodic[1]) >= 0 && (bxe >= 0 || bxo >= 0)) {
+                    cp_async<sizeof(V)>(sv + 160 + lane, ucX + gz);
+                    cp_async<sizeof(V)>(sv + 192 + lane, ucY + gz);
+                }
+            }
         }
-        fc = vmk(fe, fo);
+        cp_async_commit();
     };
-    V pA, xA, yA, fA, pB, xB, yB, fB;
-    load(y0 - 2, pA, xA, yA, fA);
-    load(y0 - 1, pB, xB, yB, fB);
-    // output row z: u_{n-1}, and u_n on footprint rows (for the records); two rows ahead of use
-    auto load_u = [&](int z, V& u0, V& u1, V& c0, V& c1) {
-        const bool ok = lane_out && z < ny;
-        const int gz = ok ? z * half + (xe >> 1) : 0;
-        u0 = upX[gz];
-        u1 = upY[gz];
-        if (ok && box_coord(z, P.xs[1], g.Fb[1], ny, g.periodic[1]) >= 0 && (bxe >= 0 || bxo >= 0)) {
-            c0 = ucX[gz];
-            c1 = ucY[gz];
-        }
-    };
-    const V zero = vsplat<T>(0.0);
-    V uxA, uyA, cxA = zero, cyA = zero, uxB, uyB, cxB = zero, cyB = zero;
-    load_u(y0, uxA, uyA, cxA, cyA);
-    load_u(y0 + 1, uxB, uyB, cxB, cyB);
-    // raw lam_u of the source rows r-1 and r-2 (the output row's footprint record)
-    V rx1 = zero, ry1 = zero, rx2 = zero, ry2 = zero;
+#pragma unroll
+    for (int t = 0; t < DEPTH - 1; ++t) issue(t);
+
     // moment accumulators as (even, odd) pairs: rows r-1 (0), r (1), r+1 (2); completed rows r-2 (c), r-3 (p)
+    const V zero = vsplat<T>(0.0);
     V m00 = zero, mx0 = zero, my0 = zero, xx0 = zero, xy0 = zero, yy0 = zero;
     V m01 = zero, mx1 = zero, my1 = zero, xx1 = zero, xy1 = zero, yy1 = zero;
     V m02 = zero, mx2 = zero, my2 = zero, xx2 = zero, xy2 = zero, yy2 = zero;
     V m0c = zero, mxc = zero, myc = zero, xxc = zero, xyc = zero, yyc = zero;
     V xyp = zero, yyp = zero;
     const V c3 = vsplat<T>(3.0), c9 = vsplat<T>(9.0), cm3 = vsplat<T>(-3.0), vA = vmk(A, A);
+    // raw lam_u of the source rows r-1 and r-2 (the output row's footprint record); the ring slot of row r-2 is
+    // being refilled by then
+    V rx1 = zero, ry1 = zero, rx2 = zero, ry2 = zero;
 
 #pragma unroll 1
-    for (int r = y0 - 2; r <= y0 + R + 1; ++r) {
-        const V lp = pA, lxv = xA, lyv = yA, fac = fA;
-        pA = pB; xA = xB; yA = yB; fA = fB;
-        if (r + 2 <= y0 + R + 1) load(r + 2, pB, xB, yB, fB);
-        // source row r: p-bar*/3 = lam_p / 3, u-bar* = lam_u * factor
+    for (int t = 0; t < NRW; ++t) {
+        issue(t + DEPTH - 1);  // into the slot of row t - 1, read in the previous iteration
+        cp_async_wait<DEPTH - 1>();  // this lane's copies of row t have landed
+        const int r = y0 - 2 + t;
+        const V* sv = rv + (t % DEPTH) * RG::ROW_V;
+        const T* st = rt + (t % DEPTH) * RG::ROW_T;
+        const V lp = sv[lane], lxv = sv[32 + lane], lyv = sv[64 + lane];
+        // source row r: p-bar*/3 = lam_p / 3, u-bar* = lam_u * factor (1/(1 + kappa) off the walls, 0 on them)
+        V fac;
+        {
+            const int yw = wrap(r, ny);
+            T fe = one, fo = one;
+            if (wall_side(yw, ny, g.periodic[1]) >= 0) {
+                fe = fo = zr;
+            } else {
+                const int by = box_coord(yw, P.xs[1], g.Fb[1], ny, g.periodic[1]);
+                if (by >= 0) {
+                    if (a.fac != nullptr) {
+                        if (sbxe >= 0) fe = st[lane];
+                        if (sbxo >= 0) fo = st[32 + lane];
+                    } else {
+                        if (sbxe >= 0) {
+                            const int b[2] = {sbxe, by};
+                            fe = adj_inv<T, 2, HW>(g, P, a.kref, nullptr, b);
+                        }
+                        if (sbxo >= 0) {
+                            const int b[2] = {sbxo, by};
+                            fo = adj_inv<T, 2, HW>(g, P, a.kref, nullptr, b);
+                        }
+                    }
+                }
+                if (swxe) fe = zr;
+                if (swxo) fo = zr;
+            }
+            fac = vmk(fe, fo);
+        }
         const V P3 = vmul(vsplat<T>(1.0 / 3.0), lp), U = vmul(lxv, fac), W = vmul(lyv, fac);
         // sources x-1 of the pair (previous lane's odd, even) and x+1 (odd, next lane's even)
         const V P3L = vmk(shfl_u(P3.y), P3.x), P3R = vmk(P3.y, shfl_d(P3.x));
@@ -352,12 +387,10 @@ __global__ void __launch_bounds__(128, 4) adj2v_kernel(Geom g, AdjArgs<T> a) {
         // lambda_{n-1} of row z = r - 2 from moment rows z-1 (p), z (c), z+1 (0)
         const int z = r - 2;
         if (z >= y0) {
-            const V u0 = uxA, u1 = uyA, c0 = cxA, c1 = cyA;
-            uxA = uxB; uyA = uyB; cxA = cxB; cyA = cyB;
-            if (z + 2 <= y0 + R - 1) load_u(z + 2, uxB, uyB, cxB, cyB);
             const V xxL = vmk(shfl_u(xxc.y), xxc.x), xxR = vmk(xxc.y, shfl_d(xxc.x));
             const V xyL = vmk(shfl_u(xyc.y), xyc.x), xyR = vmk(xyc.y, shfl_d(xyc.x));
             if (lane_out && z < ny) {
+                const V u0 = sv[96 + lane], u1 = sv[128 + lane];
                 const int go = z * half + (xe >> 1);
                 // lam_u' = 3 M1 - 3 u M0 + 9 M2 u + A sum_a [M2_a.(z - e_a) - M2_a.(z + e_a)]
                 V vx = vmul(c9, vfma(xyc, u1, vmul(xxc, u0)));
@@ -387,18 +420,19 @@ __global__ void __launch_bounds__(128, 4) adj2v_kernel(Geom g, AdjArgs<T> a) {
                 oX[go] = vx;
                 oY[go] = vy;
                 const int by = box_coord(z, P.xs[1], g.Fb[1], ny, g.periodic[1]);
-                if (by >= 0) {
+                if (by >= 0 && (bxe >= 0 || bxo >= 0)) {
                     // records: raw lam_u of row z (0 on walls) and u_n
+                    const V rx = rx2, ry = ry2, c0 = sv[160 + lane], c1 = sv[192 + lane];
                     const int bl = by * Fb0;
                     if (bxe >= 0) {
-                        a.boxbuf[bl + bxe] = we ? zr : rx2.x;
-                        a.boxbuf[Fbn + bl + bxe] = we ? zr : ry2.x;
+                        a.boxbuf[bl + bxe] = we ? zr : rx.x;
+                        a.boxbuf[Fbn + bl + bxe] = we ? zr : ry.x;
                         a.boxbuf[2 * Fbn + bl + bxe] = c0.x;
                         a.boxbuf[3 * Fbn + bl + bxe] = c1.x;
                     }
                     if (bxo >= 0) {
-                        a.boxbuf[bl + bxo] = wo ? zr : rx2.y;
-                        a.boxbuf[Fbn + bl + bxo] = wo ? zr : ry2.y;
+                        a.boxbuf[bl + bxo] = wo ? zr : rx.y;
+                        a.boxbuf[Fbn + bl + bxo] = wo ? zr : ry.y;
                         a.boxbuf[2 * Fbn + bl + bxo] = c0.y;
                         a.boxbuf[3 * Fbn + bl + bxo] = c1.y;
                     }
@@ -413,6 +447,7 @@ __global__ void __launch_bounds__(128, 4) adj2v_kernel(Geom g, AdjArgs<T> a) {
         m01 = m02; mx1 = mx2; my1 = my2; xx1 = xx2; xy1 = xy2; yy1 = yy2;
         m02 = zero; mx2 = zero; my2 = zero; xx2 = zero; xy2 = zero; yy2 = zero;
     }
+    cp_async_wait<0>();
 }
 
 }  // namespace lks

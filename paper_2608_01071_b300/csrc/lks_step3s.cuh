@@ -40,18 +40,6 @@ __host__ __device__ constexpr size_t smem3s_fwd() {
     return sizeof(T) * (5 * 4 * Sep3<TY>::NS + 6 * Sep3<TY>::NM);
 }
 
-// Asynchronous global-to-shared copy of one element (cp.async, completion tracked by commit groups).
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
 // Halo-1 coordinates (i, j) of ring node r: row j = 0, row j = MY - 1, column i = 0, column i = MX - 1.
 template <int TY>
 __device__ __forceinline__ void ring_node(int r, int& i, int& j) {

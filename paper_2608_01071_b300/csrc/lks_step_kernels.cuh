@@ -76,6 +76,18 @@ __device__ __forceinline__ void pdl_wait_then_release() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Asynchronous global-to-shared copy of BYTES (4, 8 or 16; cp.async, completion tracked by commit groups).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Sum of NV values over the block in the state precision T (warp shuffles, then the warp partials in warp order on
 // thread 0); the block total is returned in FP64, in which the callers sum over blocks.  FP64 throughput is scarce
 // on this part (a few FP64 instructions per block already take a visible share of a sensitivity pass), so
