@@ -106,8 +106,8 @@ struct Engine2D : EngineCommon<T, 2, HW> {
             case 2: launch_pdl(fwd2r_kernel<T, HW, 2>, this->fgrid, this->fthreads, smem2r_fwd<T, 2>(), s, this->pdl, g, a); break;
             case 4: fwd_r<4>(g, a, s); break;
             case 8: fwd_r<8>(g, a, s); break;
-            case 32: launch_pdl(fwd2v_kernel<T, HW, 32>, this->fgrid, this->fthreads, 0, s, this->pdl, g, a); break;
-            case 64: launch_pdl(fwd2v_kernel<T, HW, 64>, this->fgrid, this->fthreads, 0, s, this->pdl, g, a); break;
+            case 32: launch_pdl(fwd2v_kernel<T, HW, 32>, this->fgrid, this->fthreads, smem2v_fwd<T>(), s, this->pdl, g, a); break;
+            case 64: launch_pdl(fwd2v_kernel<T, HW, 64>, this->fgrid, this->fthreads, smem2v_fwd<T>(), s, this->pdl, g, a); break;
             default: fwd_r<(sizeof(T) == 4 ? 16 : 8)>(g, a, s); break;
         }
     }

@@ -63,12 +63,23 @@ __device__ __forceinline__ int wall_side(int x, int n, int periodic) {
 // ------------------------------------------------------------------------------------------------
 // Forward step n-1 -> n.
 // ------------------------------------------------------------------------------------------------
+// The input rows arrive by asynchronous copies into a per-warp ring of kFwd2vDepth rows in shared memory,
+// kFwd2vDepth - 1 rows ahead of use; each lane copies and reads back only its own column pair, so the ring needs no
+// barrier, and many rows are in flight without holding them in registers.
+constexpr int kFwd2vDepth = 6;
+template <typename T>
+constexpr size_t smem2v_fwd() {
+    return sizeof(typename Vec2<T>::type) * 4 * kFwd2vDepth * 3 * 32;
+}
+
 template <typename T, int HW, int R>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (HW == 1 ? 7 : 5) : 4) fwd2v_kernel(Geom g, FwdArgs<T> a) {
     using V = typename Vec2<T>::type;
-    constexpr int WY = 4;
+    constexpr int WY = 4, DEPTH = kFwd2vDepth;
     __shared__ double red[2 * WY];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    V* ring = reinterpret_cast<V*>(smem_raw) + (size_t)warp * DEPTH * 96;  // [DEPTH][p, u_x, u_y][32]
     const int nx = g.n[0], ny = g.n[1];
     const int x0 = blockIdx.x * kVecCols;
     const int y0 = (blockIdx.y * WY + warp) * R;
@@ -89,18 +100,33 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (HW == 1 ? 7 : 5) : 4) f
     const int half = nx >> 1;
     pdl_wait_then_release();
 
-    auto load = [&](int r, V& p, V& ux, V& uy) {
-        const int gi = wrap(r, ny) * half + (xl >> 1);
-        p = inP[gi];
-        ux = inX[gi];
-        uy = inY[gi];
+    // input row t = y0 - 2 + t (t = 0 .. R + 3) into ring slot t mod DEPTH, one copy group per row
+    constexpr int NRW = R + 4;
+    auto issue = [&](int t) {
+        if (t < NRW) {
+            V* sv = ring + (t % DEPTH) * 96;
+            const int gi = wrap(y0 - 2 + t, ny) * half + (xl >> 1);
+            cp_async<sizeof(V)>(sv + lane, inP + gi);
+            cp_async<sizeof(V)>(sv + 32 + lane, inX + gi);
+            cp_async<sizeof(V)>(sv + 64 + lane, inY + gi);
+        }
+        cp_async_commit();
     };
-    // rolling window (rows r-2, r-1, r) and prefetch (rows r+1, r+2)
-    V p0, x0v, y0v, p1, x1v, y1v, p2, x2v, y2v, pA, xA, yA, pB, xB, yB;
-    load(y0 - 2, p0, x0v, y0v);
-    load(y0 - 1, p1, x1v, y1v);
-    load(y0, pA, xA, yA);
-    load(y0 + 1, pB, xB, yB);
+    // row t, once it has landed (its slot is refilled DEPTH - 1 rows later)
+    auto take = [&](int t, V& p, V& ux, V& uy) {
+        issue(t + DEPTH - 1);
+        cp_async_wait<DEPTH - 1>();
+        const V* sv = ring + (t % DEPTH) * 96;
+        p = sv[lane];
+        ux = sv[32 + lane];
+        uy = sv[64 + lane];
+    };
+#pragma unroll
+    for (int t = 0; t < DEPTH - 1; ++t) issue(t);
+    // rolling window (rows r-2, r-1, r)
+    V p0, x0v, y0v, p1, x1v, y1v, p2, x2v, y2v;
+    take(0, p0, x0v, y0v);
+    take(1, p1, x1v, y1v);
     // output accumulators of rows m-1 (0), m (1), m+1 (2) as (even, odd) pairs: sum_i f_i, u*_x, u*_y
     const V zero = vsplat<T>(0.0);
     V aP0 = zero, aX0 = zero, aY0 = zero, aP1 = zero, aX1 = zero, aY1 = zero, aP2 = zero, aX2 = zero, aY2 = zero;
@@ -110,9 +136,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (HW == 1 ? 7 : 5) : 4) f
 
 #pragma unroll 1
     for (int r = y0; r <= y0 + R + 1; ++r) {
-        p2 = pA; x2v = xA; y2v = yA;
-        pA = pB; xA = xB; yA = yB;
-        if (r + 2 <= y0 + R + 1) load(r + 2, pB, xB, yB);
+        take(r - y0 + 2, p2, x2v, y2v);
         // moment row m = r - 1 from rows r-2 (0), r-1 (1), r (2); the x-neighbours of the pair are
         // (x - 1) = (previous lane's odd, even) and (x + 1) = (odd, next lane's even)
         const V ux = x1v, uy = y1v;
@@ -185,6 +209,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (HW == 1 ? 7 : 5) : 4) f
         aP1 = aP2; aX1 = aX2; aY1 = aY2;
         aP2 = zero; aX2 = zero; aY2 = zero;
     }
+    cp_async_wait<0>();
     if (unstable) atomicOr(a.flag, 1u);
     if (a.jslot != nullptr) {
         const int bx = (int)blockIdx.x - a.jb_lo[0], by = (int)blockIdx.y - a.jb_lo[1];
