@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(128, 4) adj2v_kernel(Geom g, AdjArgs<T> a) {
     const bool pxe = xe >= g.probe_lo[0] && xe < g.probe_hi[0];
     const bool pxo = xe + 1 >= g.probe_lo[0] && xe + 1 < g.probe_hi[0];
     const T one = (T)1, zr = (T)0;
-    const int NRW = R + 4;  // source rows y0 - 2 .. y0 + R + 1; row t is source row y0 - 2 + t, output row y0 - 4 + t
+    constexpr int NRW = R + 4;  // source rows y0 - 2 .. y0 + R + 1; row t is source row y0 - 2 + t, output row y0 - 4 + t
     pdl_wait_then_release();
 
     // copy group t: source row r = y0 - 2 + t (lambda; factors on footprint rows) and output row z = r - 2 (u_{n-1};
@@ -335,20 +335,20 @@ __global__ void __launch_bounds__(128, 4) adj2v_kernel(Geom g, AdjArgs<T> a) {
 #pragma unroll
     for (int t = 0; t < DEPTH - 1; ++t) issue(t);
 
-    // moment accumulators as (even, odd) pairs: rows r-1 (0), r (1), r+1 (2); completed rows r-2 (c), r-3 (p)
+    // moment accumulators as (even, odd) pairs of four rows that take the roles r-2 (completed, output), r-1, r and
+    // r+1 in turn: the loop body is unrolled four times with the roles renamed, instead of moving the sets between
+    // registers every row; xyp, yyp keep M2_xy and M2_yy of row r-3
+    struct Mom { V m0, mx, my, xx, xy, yy; };
     const V zero = vsplat<T>(0.0);
-    V m00 = zero, mx0 = zero, my0 = zero, xx0 = zero, xy0 = zero, yy0 = zero;
-    V m01 = zero, mx1 = zero, my1 = zero, xx1 = zero, xy1 = zero, yy1 = zero;
-    V m02 = zero, mx2 = zero, my2 = zero, xx2 = zero, xy2 = zero, yy2 = zero;
-    V m0c = zero, mxc = zero, myc = zero, xxc = zero, xyc = zero, yyc = zero;
+    Mom S0{zero, zero, zero, zero, zero, zero}, S1 = S0, S2 = S0, S3 = S0;
     V xyp = zero, yyp = zero;
     const V c3 = vsplat<T>(3.0), c9 = vsplat<T>(9.0), cm3 = vsplat<T>(-3.0), vA = vmk(A, A);
     // raw lam_u of the source rows r-1 and r-2 (the output row's footprint record); the ring slot of row r-2 is
     // being refilled by then
     V rx1 = zero, ry1 = zero, rx2 = zero, ry2 = zero;
 
-#pragma unroll 1
-    for (int t = 0; t < NRW; ++t) {
+    // row t: ac = row r-2, a0 = row r-1, a1 = row r, a2 = row r+1 (r = y0 - 2 + t)
+    auto step = [&](int t, Mom& ac, Mom& a0, Mom& a1, Mom& a2) {
         issue(t + DEPTH - 1);  // into the slot of row t - 1, read in the previous iteration
         cp_async_wait<DEPTH - 1>();  // this lane's copies of row t have landed
         const int r = y0 - 2 + t;
@@ -400,30 +400,30 @@ __global__ void __launch_bounds__(128, 4) adj2v_kernel(Geom g, AdjArgs<T> a) {
             const V Sx = vmul(vsplat<T>(Wy / 6.0), vadd(FL, FR));
             const V S = vfma(vsplat<T>(Wy * 2.0 / 3.0), FC, Sx), D = vmul(vsplat<T>(Wy / 6.0), vsub(FR, FL));
             if (cy == 1) {  // moment row r-1
-                m00 = vadd(m00, S); mx0 = vadd(mx0, D); my0 = vadd(my0, S);
-                xx0 = vadd(xx0, Sx); xy0 = vadd(xy0, D); yy0 = vadd(yy0, S);
+                a0.m0 = vadd(a0.m0, S); a0.mx = vadd(a0.mx, D); a0.my = vadd(a0.my, S);
+                a0.xx = vadd(a0.xx, Sx); a0.xy = vadd(a0.xy, D); a0.yy = vadd(a0.yy, S);
             } else if (cy == 0) {  // row r
-                m01 = vadd(m01, S); mx1 = vadd(mx1, D); xx1 = vadd(xx1, Sx);
+                a1.m0 = vadd(a1.m0, S); a1.mx = vadd(a1.mx, D); a1.xx = vadd(a1.xx, Sx);
             } else {  // row r+1
-                m02 = vadd(m02, S); mx2 = vadd(mx2, D); my2 = vsub(my2, S);
-                xx2 = vadd(xx2, Sx); xy2 = vsub(xy2, D); yy2 = vadd(yy2, S);
+                a2.m0 = vadd(a2.m0, S); a2.mx = vadd(a2.mx, D); a2.my = vsub(a2.my, S);
+                a2.xx = vadd(a2.xx, Sx); a2.xy = vsub(a2.xy, D); a2.yy = vadd(a2.yy, S);
             }
         }
-        // lambda_{n-1} of row z = r - 2 from moment rows z-1 (p), z (c), z+1 (0)
+        // lambda_{n-1} of row z = r - 2 from moment rows z-1 (p), z (ac), z+1 (a0)
         const int z = r - 2;
         if (z >= y0) {
-            const V xxL = vmk(shfl_u(xxc.y), xxc.x), xxR = vmk(xxc.y, shfl_d(xxc.x));
-            const V xyL = vmk(shfl_u(xyc.y), xyc.x), xyR = vmk(xyc.y, shfl_d(xyc.x));
+            const V xxL = vmk(shfl_u(ac.xx.y), ac.xx.x), xxR = vmk(ac.xx.y, shfl_d(ac.xx.x));
+            const V xyL = vmk(shfl_u(ac.xy.y), ac.xy.x), xyR = vmk(ac.xy.y, shfl_d(ac.xy.x));
             if (lane_out && z < ny) {
                 const V u0 = sv[96 + lane], u1 = sv[128 + lane];
                 const int go = z * half + (xe >> 1);
                 // lam_u' = 3 M1 - 3 u M0 + 9 M2 u + A sum_a [M2_a.(z - e_a) - M2_a.(z + e_a)]
-                V vx = vmul(c9, vfma(xyc, u1, vmul(xxc, u0)));
-                V vy = vmul(c9, vfma(yyc, u1, vmul(xyc, u0)));
-                vx = vfma(c3, mxc, vfma(vmul(cm3, u0), m0c, vx));
-                vy = vfma(c3, myc, vfma(vmul(cm3, u1), m0c, vy));
-                vx = vfma(vA, vadd(vsub(xxL, xxR), vsub(xyp, xy0)), vx);
-                vy = vfma(vA, vadd(vsub(xyL, xyR), vsub(yyp, yy0)), vy);
+                V vx = vmul(c9, vfma(ac.xy, u1, vmul(ac.xx, u0)));
+                V vy = vmul(c9, vfma(ac.yy, u1, vmul(ac.xy, u0)));
+                vx = vfma(c3, ac.mx, vfma(vmul(cm3, u0), ac.m0, vx));
+                vy = vfma(c3, ac.my, vfma(vmul(cm3, u1), ac.m0, vy));
+                vx = vfma(vA, vadd(vsub(xxL, xxR), vsub(xyp, a0.xy)), vx);
+                vy = vfma(vA, vadd(vsub(xyL, xyR), vsub(yyp, a0.yy)), vy);
                 const bool wy = wall_side(z, ny, g.periodic[1]) >= 0;
                 const bool we = wy || wxe, wo = wy || wxo;
                 if (a.src && z >= g.probe_lo[1] && z < g.probe_hi[1]) {
@@ -441,36 +441,42 @@ __global__ void __launch_bounds__(128, 4) adj2v_kernel(Geom g, AdjArgs<T> a) {
                 V* oP = reinterpret_cast<V*>(a.lam_out);
                 V* oX = reinterpret_cast<V*>(a.lam_out + N);
                 V* oY = reinterpret_cast<V*>(a.lam_out + 2 * N);
-                oP[go] = vmul(c3, m0c);
+                oP[go] = vmul(c3, ac.m0);
                 oX[go] = vx;
                 oY[go] = vy;
                 const int by = box_coord(z, P.xs[1], g.Fb[1], ny, g.periodic[1]);
                 if (by >= 0 && (bxe >= 0 || bxo >= 0)) {
                     // records: raw lam_u of row z (0 on walls) and u_n
-                    const V rx = rx2, ry = ry2, c0 = sv[160 + lane], c1 = sv[192 + lane];
+                    const V c0 = sv[160 + lane], c1 = sv[192 + lane];
                     const int bl = by * Fb0;
                     if (bxe >= 0) {
-                        a.boxbuf[bl + bxe] = we ? zr : rx.x;
-                        a.boxbuf[Fbn + bl + bxe] = we ? zr : ry.x;
+                        a.boxbuf[bl + bxe] = we ? zr : rx2.x;
+                        a.boxbuf[Fbn + bl + bxe] = we ? zr : ry2.x;
                         a.boxbuf[2 * Fbn + bl + bxe] = c0.x;
                         a.boxbuf[3 * Fbn + bl + bxe] = c1.x;
                     }
                     if (bxo >= 0) {
-                        a.boxbuf[bl + bxo] = wo ? zr : rx.y;
-                        a.boxbuf[Fbn + bl + bxo] = wo ? zr : ry.y;
+                        a.boxbuf[bl + bxo] = wo ? zr : rx2.y;
+                        a.boxbuf[Fbn + bl + bxo] = wo ? zr : ry2.y;
                         a.boxbuf[2 * Fbn + bl + bxo] = c0.y;
                         a.boxbuf[3 * Fbn + bl + bxo] = c1.y;
                     }
                 }
             }
         }
-        // roll the raw lam_u rows and the moment rows
+        // the completed row's M2_xy, M2_yy become row r-3's for the next row; its set starts row r+2 from zero
+        xyp = ac.xy;
+        yyp = ac.yy;
+        ac = Mom{zero, zero, zero, zero, zero, zero};
         rx2 = rx1; ry2 = ry1; rx1 = lxv; ry1 = lyv;
-        xyp = xyc; yyp = yyc;
-        m0c = m00; mxc = mx0; myc = my0; xxc = xx0; xyc = xy0; yyc = yy0;
-        m00 = m01; mx0 = mx1; my0 = my1; xx0 = xx1; xy0 = xy1; yy0 = yy1;
-        m01 = m02; mx1 = mx2; my1 = my2; xx1 = xx2; xy1 = xy2; yy1 = yy2;
-        m02 = zero; mx2 = zero; my2 = zero; xx2 = zero; xy2 = zero; yy2 = zero;
+    };
+    static_assert(NRW % 4 == 0, "rows come in fours");
+#pragma unroll 1
+    for (int t = 0; t < NRW; t += 4) {
+        step(t, S0, S1, S2, S3);
+        step(t + 1, S1, S2, S3, S0);
+        step(t + 2, S2, S3, S0, S1);
+        step(t + 3, S3, S0, S1, S2);
     }
     cp_async_wait<0>();
 }
