@@ -123,30 +123,34 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (HW == 1 ? 7 : 5) : 4) f
     };
 #pragma unroll
     for (int t = 0; t < DEPTH - 1; ++t) issue(t);
-    // rolling window (rows r-2, r-1, r)
-    V p0, x0v, y0v, p1, x1v, y1v, p2, x2v, y2v;
-    take(0, p0, x0v, y0v);
-    take(1, p1, x1v, y1v);
-    // output accumulators of rows m-1 (0), m (1), m+1 (2) as (even, odd) pairs: sum_i f_i, u*_x, u*_y
+    // rolling window of input rows (r-2, r-1, r) and output accumulators of rows m-1, m, m+1 (m = r - 1) as (even,
+    // odd) pairs (sum_i f_i, u*_x, u*_y): three sets of each take those roles in turn, the loop body unrolled three
+    // times with the roles renamed instead of moving the sets between registers every row
+    struct Row { V p, x, y; };
+    struct Acc { V P, X, Y; };
+    Row Wa, Wb, Wc;
+    take(0, Wa.p, Wa.x, Wa.y);
+    take(1, Wb.p, Wb.x, Wb.y);
     const V zero = vsplat<T>(0.0);
-    V aP0 = zero, aX0 = zero, aY0 = zero, aP1 = zero, aX1 = zero, aY1 = zero, aP2 = zero, aX2 = zero, aY2 = zero;
+    Acc Aa{zero, zero, zero}, Ab = Aa, Ac = Aa;
     const V c3 = vsplat<T>(3.0), cm15 = vsplat<T>(-1.5), c45 = vsplat<T>(4.5), vA = vmk(A, A),
             vhA = vmk((T)0.5 * A, (T)0.5 * A);
     bool unstable = false;
 
-#pragma unroll 1
-    for (int r = y0; r <= y0 + R + 1; ++r) {
-        take(r - y0 + 2, p2, x2v, y2v);
-        // moment row m = r - 1 from rows r-2 (0), r-1 (1), r (2); the x-neighbours of the pair are
+    // input row r = y0 + k (loop row k); w0, w1, w2 = rows r-2, r-1, r; a0, a1, a2 = accumulators of rows r-2, r-1, r
+    auto step = [&](int k, Row& w0, Row& w1, Row& w2, Acc& a0, Acc& a1, Acc& a2) {
+        const int r = y0 + k;
+        take(k + 2, w2.p, w2.x, w2.y);
+        // moment row m = r - 1 from rows r-2, r-1, r; the x-neighbours of the pair are
         // (x - 1) = (previous lane's odd, even) and (x + 1) = (odd, next lane's even)
-        const V ux = x1v, uy = y1v;
+        const V ux = w1.x, uy = w1.y;
         const V uxL = vmk(shfl_u(ux.y), ux.x), uxR = vmk(ux.y, shfl_d(ux.x));
         const V uyL = vmk(shfl_u(uy.y), uy.x), uyR = vmk(uy.y, shfl_d(uy.x));
         const V uxx = vmul(ux, ux), uyy = vmul(uy, uy);
-        const V sig = vfma(cm15, vadd(uxx, uyy), vmul(c3, p1));
+        const V sig = vfma(cm15, vadd(uxx, uyy), vmul(c3, w1.p));
         const V Txx = vfma(c45, uxx, vmul(vA, vsub(uxR, uxL)));
-        const V Tyy = vfma(c45, uyy, vmul(vA, vsub(y2v, y0v)));
-        const V Txy = vfma(c45, vmul(ux, uy), vmul(vhA, vadd(vsub(uyR, uyL), vsub(x2v, x0v))));
+        const V Tyy = vfma(c45, uyy, vmul(vA, vsub(w2.y, w0.y)));
+        const V Txy = vfma(c45, vmul(ux, uy), vmul(vhA, vadd(vsub(uyR, uyL), vsub(w2.x, w0.x))));
         const V ux3 = vmul(c3, ux);
 #pragma unroll
         for (int cy = -1; cy <= 1; ++cy) {
@@ -160,9 +164,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (HW == 1 ? 7 : 5) : 4) f
             const double Wy = cy == 0 ? 2.0 / 3.0 : 1.0 / 6.0;
             const V S = vfma(vsplat<T>(Wy / 6.0), vadd(FL, FR), vmul(vsplat<T>(Wy * 2.0 / 3.0), b));
             const V X = vmul(vsplat<T>(Wy / 6.0), vsub(FL, FR));
-            if (cy == -1) { aP0 = vadd(aP0, S); aX0 = vadd(aX0, X); aY0 = vsub(aY0, S); }
-            if (cy == 0) { aP1 = vadd(aP1, S); aX1 = vadd(aX1, X); }
-            if (cy == 1) { aP2 = vadd(aP2, S); aX2 = vadd(aX2, X); aY2 = vadd(aY2, S); }
+            if (cy == -1) { a0.P = vadd(a0.P, S); a0.X = vadd(a0.X, X); a0.Y = vsub(a0.Y, S); }
+            if (cy == 0) { a1.P = vadd(a1.P, S); a1.X = vadd(a1.X, X); }
+            if (cy == 1) { a2.P = vadd(a2.P, S); a2.X = vadd(a2.X, X); a2.Y = vadd(a2.Y, S); }
         }
         // output row o = r - 2
         const int o = r - 2;
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (HW == 1 ? 7 : 5) : 4) f
                     if (a.u_crit2 > (T)0 && !(u0 * u0 + u1 * u1 <= a.u_crit2)) unstable = true;
                 }
             };
-            T ue0 = aX0.x, ue1 = aY0.x, uo0 = aX0.y, uo1 = aY0.y;
+            T ue0 = a0.X.x, ue1 = a0.Y.x, uo0 = a0.X.y, uo1 = a0.Y.y;
             finish(ue0, ue1, bxe, wxe);
             finish(uo0, uo1, bxo, wxo);
             const int go = o * half + (xe >> 1);
@@ -196,19 +200,25 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (HW == 1 ? 7 : 5) : 4) f
             V* outX = reinterpret_cast<V*>(a.out_u);
             V* outY = reinterpret_cast<V*>(a.out_u + g.N);
             V vp, vx, vy;
-            vp = vmul(vsplat<T>(1.0 / 3.0), aP0);
+            vp = vmul(vsplat<T>(1.0 / 3.0), a0.P);
             vx.x = ue0; vx.y = uo0;
             vy.x = ue1; vy.y = uo1;
             outP[go] = vp;
             outX[go] = vx;
             outY[go] = vy;
         }
-        p0 = p1; x0v = x1v; y0v = y1v;
-        p1 = p2; x1v = x2v; y1v = y2v;
-        aP0 = aP1; aX0 = aX1; aY0 = aY1;
-        aP1 = aP2; aX1 = aX2; aY1 = aY2;
-        aP2 = zero; aX2 = zero; aY2 = zero;
+        a0 = Acc{zero, zero, zero};  // the output row's set starts row r+1
+    };
+    constexpr int NIT = R + 2;  // rows r = y0 .. y0 + R + 1
+    int k = 0;
+#pragma unroll 1
+    for (; k + 3 <= NIT; k += 3) {
+        step(k, Wa, Wb, Wc, Aa, Ab, Ac);
+        step(k + 1, Wb, Wc, Wa, Ab, Ac, Aa);
+        step(k + 2, Wc, Wa, Wb, Ac, Aa, Ab);
     }
+    if (NIT % 3 >= 1) step(k, Wa, Wb, Wc, Aa, Ab, Ac);
+    if (NIT % 3 >= 2) step(k + 1, Wb, Wc, Wa, Ab, Ac, Aa);
     cp_async_wait<0>();
     if (unstable) atomicOr(a.flag, 1u);
     if (a.jslot != nullptr) {
