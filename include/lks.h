@@ -95,7 +95,14 @@ enum { LKS_ADJ_DISCRETE = 0, LKS_ADJ_ALKS = 1 };                /* reverse sweep
  *                 block; 32 or 64 = separable z-marching kernels with 16 or 32 planes of 32 x 8 columns; 96 =
  *                 separable forward with 16 planes of 32 x 16 columns (forward only); LKS_FP32 only: 128 or 160 =
  *                 plane-pair kernels (two planes per FP32x2 instruction) with 16 or 32 planes of 32 x 8 columns
- *                 per block, 192 = the plane-pair adjoint with 64 planes (tile_rows_adj only).
+ *                 per block, 192 = the plane-pair adjoint with 64 planes (tile_rows_adj only).  The plane-pair
+ *                 blocks whose input region lies inside the grid in x and y (n[0] a multiple of 4) fetch their
+ *                 planes by tensor (TMA) copies that complete on shared-memory barriers; each wait for them is
+ *                 bounded (one second), and an expired wait makes the block leave and the context report
+ *                 LKS_ETIMEOUT.  Environment read by lks_create: LKS_NO_TMA=1 turns the tensor copies off (every
+ *                 block copies per thread; same results bit for bit), LKS_WAIT_NS sets the bound in ns, and the
+ *                 diagnostic LKS_WAIT_PROBE=1 makes every such block first wait on a barrier that nothing
+ *                 completes (the wait expires: a test of the timeout path).
  *                 0 = autotune at lks_create: times every choice on the context's buffers, then the fastest
  *                 one-step forward/adjoint pairs launched side by side; the forward sweep takes the fastest
  *                 forward, the pipelined sqrt(N) sweep and batch instances the fastest side-by-side pair
@@ -209,7 +216,10 @@ int lks_forward_dev(lks_ctx* ctx, const double* d_gamma, const double* d_pos_kno
 /*
  * Status of the last forward: waits for it to finish, then LKS_EUNSTABLE if it saw a non-finite velocity or |u| > u_crit
  * (the check of lks_params.u_crit), LKS_OK otherwise; LKS_ESTATE before the first forward.  The _dev forward and
- * adjoint calls do not wait for the forward, so this is where their callers learn of an unstable sweep.
+ * adjoint calls do not wait for the forward, so this is where their callers learn of an unstable sweep.  It also
+ * waits for the device and returns LKS_ETIMEOUT (before LKS_EUNSTABLE) once any bounded device-side wait of the
+ * context's kernels has expired; that status stays set for the context's lifetime, and lks_forward and lks_adjoint
+ * return it too (the _dev adjoint then fills its outputs with NaN).
  */
 int lks_get_status(lks_ctx* ctx);
 

@@ -293,6 +293,9 @@ void setup_geometry(lks_ctx* c) {
     g.Fbn = (long long)g.Fb[0] * g.Fb[1] * g.Fb[2];
     g.A = 0.75 - 4.5 * p.nu;
     g.u_crit2 = p.u_crit > 0.0 ? p.u_crit * p.u_crit : 0.0;
+    // limit of the bounded device-side waits, and the diagnostic that makes them expire
+    if (const char* e = std::getenv("LKS_WAIT_NS"); e && *e) g.wait_ns = std::strtoull(e, nullptr, 10);
+    if (const char* e = std::getenv("LKS_WAIT_PROBE"); e && *e) g.wait_probe = std::atoi(e) != 0 ? 1 : 0;
     // |O| counts probe nodes off the walls
     long long cnt = 1;
     for (int a = 0; a < c->D; ++a) {
@@ -757,7 +760,9 @@ void allocate(lks_ctx* c) {
         LKS_CUDA(cudaMemset(c->d_oslot, 0, (size_t)(p.Nt + 1) * onv * 8));
         LKS_CUDA(cudaMemset(c->d_oar_guG, 0, (size_t)(p.Nt + 1) * D * 8));
     }
-    c->d_flag = (unsigned*)dalloc(c, 16);
+    c->d_flag = (unsigned*)dalloc(c, 16);  // [0] stability flag of the last forward, [1] status word (Geom::status)
+    LKS_CUDA(cudaMemset(c->d_flag, 0, 16));
+    c->g.status = c->d_flag + 1;
     // kappa-bar per step (and u^S-bar with a rotating body); per-block motion partials per step (2 D values, and
     // dJ/dtheta, dJ/domega with a rotating body)
     c->d_kbar = dalloc(c, (size_t)c->Lmax * c->g.Fbn * ts * (c->rot ? 1 + D : 1));
@@ -814,7 +819,7 @@ void allocate(lks_ctx* c) {
     c->stats.pipelined = c->pipelined ? 1 : 0;
 
     LKS_CUDA(cudaHostAlloc((void**)&c->h_flag, 16, cudaHostAllocDefault));
-    *c->h_flag = 0;
+    std::memset(c->h_flag, 0, 16);
     LKS_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
     LKS_CUDA(cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking));
     LKS_CUDA(cudaStreamCreateWithFlags(&c->cap3, cudaStreamNonBlocking));
@@ -1144,7 +1149,7 @@ void forward_body(lks_ctx* c, cudaStream_t s) {
         LKS_LAUNCHED();
         c->launches++;
     }
-    LKS_CUDA(cudaMemcpyAsync(c->h_flag, c->d_flag, 4, cudaMemcpyDeviceToHost, s));
+    LKS_CUDA(cudaMemcpyAsync(c->h_flag, c->d_flag, 8, cudaMemcpyDeviceToHost, s));
     c->launches_fwd = c->launches;
     c->spans_fwd = c->spans;
 }
@@ -1548,7 +1553,15 @@ void alks_launch(lks_ctx* c, bool init, const void* lam_in, void* lam_out, const
     }
 }
 
-// NaN gradients on the device when the last forward raised the stability flag (asynchronous adjoint variants).
+// Errors that the device reports through the context's flag words (copied to h_flag by the calls that read them):
+// an expired bounded wait (status word) first, as the cause of anything else, then the forward's stability flag.
+void check_flags(lks_ctx* c) {
+    if (c->h_flag[1] != 0u) throw LksError{LKS_ETIMEOUT, "a bounded device-side wait expired (tensor copies did not complete)"};
+    if (c->h_flag[0] != 0u) throw LksError{LKS_EUNSTABLE, "forward sweep unstable: non-finite velocity or |u| > u_crit"};
+}
+
+// NaN gradients on the device when the last forward raised the stability flag or a bounded wait expired
+// (asynchronous adjoint variants).
 void poison_if_unstable(lks_ctx* c, double* dgamma, double* dpos, cudaStream_t s) {
     const long long nk = (long long)c->prm.K * c->D;
     const long long n = std::max<long long>(c->nd, nk);
@@ -1757,7 +1770,7 @@ int lks_forward(lks_ctx* c, const double* gamma, const double* pos, double* J) {
         double j = 0.0;
         LKS_CUDA(cudaMemcpyAsync(&j, c->d_J, 8, cudaMemcpyDeviceToHost, s));
         LKS_CUDA(cudaStreamSynchronize(s));
-        if (*c->h_flag) throw LksError{LKS_EUNSTABLE, "forward sweep unstable: non-finite velocity or |u| > u_crit"};
+        check_flags(c);
         *J = j;
     });
 }
@@ -1779,8 +1792,10 @@ int lks_adjoint(lks_ctx* c, double* dgamma, double* dpos) {
         cudaStream_t s = 0;
         run_adjoint(c, s);
         finish_adjoint(c, c->d_out_g, c->d_out_k, s);
-        LKS_CUDA(cudaStreamSynchronize(s));  // the forward's flag reached the host before its sweep ended
-        if (*c->h_flag) throw LksError{LKS_EUNSTABLE, "forward sweep unstable: non-finite velocity or |u| > u_crit"};
+        // the forward's flag reached the host before its sweep ended; the status word is read after the sweep
+        LKS_CUDA(cudaMemcpyAsync(c->h_flag + 1, c->d_flag + 1, 4, cudaMemcpyDeviceToHost, s));
+        LKS_CUDA(cudaStreamSynchronize(s));
+        check_flags(c);
         LKS_CUDA(cudaMemcpyAsync(dgamma, c->d_out_g, c->nd * 8, cudaMemcpyDeviceToHost, s));
         LKS_CUDA(cudaMemcpyAsync(dpos, c->d_out_k, (size_t)c->prm.K * c->D * 8, cudaMemcpyDeviceToHost, s));
         LKS_CUDA(cudaStreamSynchronize(s));
@@ -2134,7 +2149,10 @@ int lks_get_status(lks_ctx* c) {
     return guard(c, [&] {
         if (!c->have_final) throw LksError{LKS_ESTATE, "no forward has run"};
         LKS_CUDA(cudaEventSynchronize(c->ev_flag));
-        if (*c->h_flag) throw LksError{LKS_EUNSTABLE, "forward sweep unstable: non-finite velocity or |u| > u_crit"};
+        // the status word covers every kernel queued so far on any stream
+        LKS_CUDA(cudaDeviceSynchronize());
+        LKS_CUDA(cudaMemcpy(c->h_flag + 1, c->d_flag + 1, 4, cudaMemcpyDeviceToHost));
+        check_flags(c);
     });
 }
 

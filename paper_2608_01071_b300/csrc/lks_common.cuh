@@ -79,6 +79,10 @@ struct Geom {
     int rot;            // 1: the body also rotates (theta turns x-y about an axis parallel to z); the footprint box
                         // on x and y then covers the design grid at any angle (lks_rot.cuh)
     const void* rotmap; // rotating body: kappa, u^S_0 .. u^S_D-1 of the current step on the footprint box (forward)
+    unsigned* status;   // device status word of the context (bit 1: a bounded device-side wait expired), or nullptr
+    unsigned long long wait_ns;  // limit of one bounded device-side wait in ns (0: one second)
+    int wait_probe;     // diagnostic: the plane-pair blocks with tensor copies first wait on a barrier that nothing
+                        // completes, so that the wait expires
 };
 
 // Per-step rigid-body pose (Eq. rigid_body_position with theta = 0) reduced to what the mapping needs:

@@ -6,9 +6,41 @@
 #include "lks_step3s.cuh"
 #include "lks_step3p.cuh"
 
+#include <cstdint>
+#include <cstring>
 #include <type_traits>
 
 namespace lks {
+
+// Tensor map of a state (4 fields of N floats, field a at base + a N) as the 4-D tensor (x, y, z, field) with the
+// plane-pair kernels' raw box (RX x RY x 1 x 4, i.e. one plane of all four fields).  False when the driver has no
+// encoder or the layout does not qualify (n_x not a multiple of 4, base not 16-byte aligned): the kernels then copy
+// with every thread.
+inline bool pair_tensor_map(const Geom& g, const void* base, CUtensorMap& tm) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static const Encode enc = [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            (void)cudaGetLastError();
+            return (Encode) nullptr;
+        }
+        return reinterpret_cast<Encode>(fn);
+    }();
+    static_assert(Pair3::RX == PairA3::RX && Pair3::RY == PairA3::RY, "one box for both kernels");
+    std::memset(&tm, 0, sizeof(tm));
+    if (enc == nullptr || g.n[0] % 4 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+    const cuuint64_t dim[4] = {(cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2], 4};
+    const cuuint64_t stride[3] = {(cuuint64_t)g.n[0] * 4, (cuuint64_t)g.n[0] * g.n[1] * 4, (cuuint64_t)g.N * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)Pair3::RX, (cuuint32_t)Pair3::RY, 1, 4};
+    const cuuint32_t unit[4] = {1, 1, 1, 1};
+    return enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dim, stride, box, unit,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 // D3Q15 engine: rows = 1 selects the generic shared-memory tile kernels (32 x 4 x 4 nodes per block);
 // rows = 8 or 16 the z-marching kernels with that many planes per block (32 x 8 columns); forward rows = 32,
@@ -24,6 +56,7 @@ struct Engine3D : EngineCommon<T, 3, HW> {
     static constexpr size_t smem_adj = sizeof(T) * (4 * TL::S + 10 * TL::M);
 
     explicit Engine3D(const Geom& g) {
+        if (const char* e = std::getenv("LKS_NO_TMA"); e != nullptr && *e != '\0' && std::atoi(e) != 0) tma_on = false;
         LKS_CUDA(cudaFuncSetAttribute(fwd_step_kernel<T, 3, HW, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem_fwd));
         LKS_CUDA(cudaFuncSetAttribute(adj_step_kernel<T, 3, HW, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -65,13 +98,16 @@ struct Engine3D : EngineCommon<T, 3, HW> {
         return 0;
     }
     template <int ZB>
-    static void (*fwd3p_fn(bool v4))(Geom, FwdArgs<float>) {
+    static void (*fwd3p_fn(bool v4))(Geom, FwdArgs<float>, CUtensorMap, int) {
         return v4 ? fwd3p_kernel<HW, ZB, true> : fwd3p_kernel<HW, ZB, false>;
     }
     template <int ZB>
-    static void (*adj3p_fn(bool v4))(Geom, AdjArgs<float>) {
+    static void (*adj3p_fn(bool v4))(Geom, AdjArgs<float>, CUtensorMap, int) {
         return v4 ? adj3p_kernel<HW, ZB, true> : adj3p_kernel<HW, ZB, false>;
     }
+    // tensor copies are used unless the environment of the context's creation turned them off (LKS_NO_TMA=1:
+    // every block copies per thread)
+    bool tma_on = true;
     std::vector<int> fwd_codes() const override {
         if (kPair) return {1, 8, 16, 32, 64, 96, 128, 160};
         return {1, 8, 16, 32, 64, 96};
@@ -130,9 +166,11 @@ struct Engine3D : EngineCommon<T, 3, HW> {
             launch_pdl(fwd3s_kernel<T, HW, 16, 16>, this->fgrid, this->fthreads, smem3s_fwd<T, 16>(), s, this->pdl, g, a);
         else if constexpr (kPair) {
             const bool v4 = g.n[0] % 4 == 0;
+            CUtensorMap tm;
+            const int ut = tma_on && pair_tensor_map(g, in, tm) ? 1 : 0;
             switch (pair_zb(this->rows_f, false)) {
-                case 16: launch_pdl(fwd3p_fn<16>(v4), this->fgrid, this->fthreads, smem3p_fwd(), s, this->pdl, g, a); break;
-                default: launch_pdl(fwd3p_fn<32>(v4), this->fgrid, this->fthreads, smem3p_fwd(), s, this->pdl, g, a); break;
+                case 16: launch_pdl(fwd3p_fn<16>(v4), this->fgrid, this->fthreads, smem3p_fwd(), s, this->pdl, g, a, tm, ut); break;
+                default: launch_pdl(fwd3p_fn<32>(v4), this->fgrid, this->fthreads, smem3p_fwd(), s, this->pdl, g, a, tm, ut); break;
             }
         }
     }
@@ -151,10 +189,12 @@ struct Engine3D : EngineCommon<T, 3, HW> {
             launch_pdl(adj3s_kernel<T, HW, 32, 8>, this->agrid, this->athreads, smem3s_adj<T, 8>(), s, this->pdl, g, a);
         else if constexpr (kPair) {
             const bool v4 = g.n[0] % 4 == 0;
+            CUtensorMap tm;
+            const int ut = tma_on && pair_tensor_map(g, lam_in, tm) ? 1 : 0;
             switch (pair_zb(this->rows_a, true)) {
-                case 16: launch_pdl(adj3p_fn<16>(v4), this->agrid, this->athreads, smem3p_adj(), s, this->pdl, g, a); break;
-                case 64: launch_pdl(adj3p_fn<64>(v4), this->agrid, this->athreads, smem3p_adj(), s, this->pdl, g, a); break;
-                default: launch_pdl(adj3p_fn<32>(v4), this->agrid, this->athreads, smem3p_adj(), s, this->pdl, g, a); break;
+                case 16: launch_pdl(adj3p_fn<16>(v4), this->agrid, this->athreads, smem3p_adj(), s, this->pdl, g, a, tm, ut); break;
+                case 64: launch_pdl(adj3p_fn<64>(v4), this->agrid, this->athreads, smem3p_adj(), s, this->pdl, g, a, tm, ut); break;
+                default: launch_pdl(adj3p_fn<32>(v4), this->agrid, this->athreads, smem3p_adj(), s, this->pdl, g, a, tm, ut); break;
             }
         }
     }

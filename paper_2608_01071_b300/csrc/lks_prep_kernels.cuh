@@ -387,7 +387,7 @@ __global__ void add_state_kernel(Geom g, T* __restrict__ dst, const T* __restric
 // asynchronous adjoint cannot return LKS_EUNSTABLE, so its outputs carry the failure instead.
 static __global__ void poison_unstable_kernel(const unsigned* __restrict__ flag, double* __restrict__ a, long long na,
                                               double* __restrict__ b, long long nb) {
-    if ((*flag & 1u) == 0u) return;
+    if ((flag[0] & 1u) == 0u && flag[1] == 0u) return;  // stable forward and no expired device-side wait
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (a != nullptr && i < na) a[i] = __longlong_as_double(0x7ff8000000000000LL);
     if (b != nullptr && i < nb) b[i] = __longlong_as_double(0x7ff8000000000000LL);

@@ -10,9 +10,10 @@
 // columns two planes at a time: these values for planes k and k+1 are computed together, one FP32x2 instruction for
 // both, and stored interleaved in shared memory as float2, so that one 8-byte shared load feeds the same stencil
 // position of both planes.  Only the coupling along z between the planes of a pair and the neighbouring pairs is done
-// in scalar arithmetic (a few additions per node).  Raw planes (p', u) arrive by 16-byte asynchronous copies (4-byte
-// copies when n_x is not a multiple of 4) into a ring of two plane pairs; the next pair is fetched while the
-// current one is being summed.
+// in scalar arithmetic (a few additions per node).  Raw planes (p', u) arrive in a ring of two plane pairs; the next
+// pair is fetched while the current one is being summed.  A block whose raw region lies inside the grid in x and y
+// fetches each plane with one 4-D tensor copy (all four fields) issued by one thread; a block at a periodic seam
+// (whose region wraps) by 16-byte asynchronous copies of every thread (4-byte copies when n_x is not a multiple of 4).
 //
 // Per iteration j the block holds the raw planes k-1 .. k+2 (k = z0 - 1 + 2j) and
 //   (A) evaluates the emitted values of planes k, k+1 on the halo-1 region (each thread its own column and at most
@@ -25,6 +26,7 @@
 #include "lks_common.cuh"
 #include "lks_step_kernels.cuh"
 #include "lks_step3s.cuh"
+#include "lks_tma.cuh"
 
 namespace lks {
 
@@ -126,14 +128,19 @@ struct ColumnMapHat {
 
 // Forward step n-1 -> n (Sec. 2.2 / 2.3); same result as fwd_step_kernel up to the order of FP additions.
 // VEC4: n_x is a multiple of 4, so raw rows move in aligned 16-byte chunks that never straddle the periodic seam.
+// tm: the input state as a 4-D tensor (x, y, z, field) with a box of one raw plane (RX x RY x 1 x 4), valid when
+// use_tma is set (n_x a multiple of 4).
 template <int HW, int ZB, bool VEC4>
-__global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<float> a) {
+__global__ void __launch_bounds__(Pair3::NT, 3)
+    fwd3p_kernel(Geom g, FwdArgs<float> a, const __grid_constant__ CUtensorMap tm, int use_tma) {
     using R = Pair3;
     static_assert(ZB % 2 == 0, "planes come in pairs");
+    static_assert((4 * R::RS * sizeof(float)) % 128 == 0, "tensor copies land on 128-byte boundaries");
     constexpr int NP = ZB / 2 + 1;  // iterations (field-plane pairs)
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_pair[];
     __shared__ double red[2 * (R::NT / 32)];
-    float* raw = reinterpret_cast<float*>(smem_raw);                      // [4 planes][p', u_x, u_y, u_z][RS]
+    __shared__ PairTma pt;
+    float* raw = reinterpret_cast<float*>(smem_pair);                     // [4 planes][p', u_x, u_y, u_z][RS]
     float2* fld = reinterpret_cast<float2*>(raw + 4 * 4 * R::RS);         // [NFLD][NM]
     // emitted values: hp[s] = H+ and hm[s] = H- for (sx, sy) = (+,+), (-,+), (+,-), (-,-) (s = 0 .. 3), i.e. for the
     // receivers at (x + 1, y + 1), (x - 1, y + 1), (x + 1, y - 1), (x - 1, y - 1); ex[0] = E_x+ (receiver x + 1),
@@ -150,11 +157,16 @@ __global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<flo
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + R::TX * ty;
     const float A = (float)g.A;
     const Pose& P = *a.pose;
+    // tensor copies for a raw region inside the grid (x0 - 4 .. x0 + TX + 3, y0 - 2 .. y0 + TY + 1); x0 - 4 is a
+    // multiple of 4 elements (16 bytes)
+    // (and a 128-byte aligned ring, which the declaration asks for)
+    const bool tma = VEC4 && use_tma != 0 && x0 >= 4 && x0 + R::TX + 4 <= nx && y0 >= 2 && y0 + R::TY + 2 <= ny &&
+                     (smem_addr(raw) & 127u) == 0u;
 
     // plane-invariant copy descriptors of this thread's 16-byte chunks
     int goff[VEC4 ? R::PERCH : 1];
     int soff[VEC4 ? R::PERCH : 1];
-    if (VEC4) {
+    if (VEC4 && !tma) {
 #pragma unroll
         for (int q = 0; q < R::PERCH; ++q) {
             const int e = tid + q * R::NT;
@@ -187,10 +199,19 @@ __global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<flo
             }
         }
     };
-    auto issue_pair = [&](int j) {  // raw planes z0 - 2 + 2j, z0 - 1 + 2j as one copy group
-        issue(z0 - 2 + 2 * j);
-        issue(z0 - 1 + 2 * j);
-        cp_async_commit();
+    auto issue_pair = [&](int j) {  // raw planes z0 - 2 + 2j, z0 - 1 + 2j as one copy group (one barrier phase)
+        if (tma) {
+            if (tid == 0) {
+                uint64_t* b = &pt.bar[j & 1];
+                mbar_expect_tx(b, 2 * 4 * R::RS * sizeof(float));
+                tma_load_4d(slot(z0 - 2 + 2 * j), &tm, x0 - 4, y0 - 2, wrap(z0 - 2 + 2 * j, nz), 0, b);
+                tma_load_4d(slot(z0 - 1 + 2 * j), &tm, x0 - 4, y0 - 2, wrap(z0 - 1 + 2 * j, nz), 0, b);
+            }
+        } else {
+            issue(z0 - 2 + 2 * j);
+            issue(z0 - 1 + 2 * j);
+            cp_async_commit();
+        }
     };
 
     // field nodes of this thread: 0 = own column, 1 = a node of the halo-1 ring (tid < NR)
@@ -215,6 +236,10 @@ __global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<flo
     const float2 c3 = f2s(3.f), c9 = f2s(9.f), cA = f2s(A), c45 = f2s(4.5f), cm15 = f2s(-1.5f);
     const float2 w0 = f2s(2.f / 9.f), wf = f2s(1.f / 9.f), wc = f2s(1.f / 72.f);
 
+    if (tma && tid == 0) {
+        pt.init();
+        tma_prefetch_map(&tm);
+    }
     pdl_wait_then_release();
     issue_pair(0);
     issue_pair(1);
@@ -276,8 +301,14 @@ __global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<flo
 
 #pragma unroll 1
     for (int j = 0; j < NP; ++j) {
-        cp_async_wait<0>();  // raw pair j + 1 (this thread's copies; pair j arrived one iteration earlier)
+        // raw pair j + 1 (pair j arrived one iteration earlier; both on the first)
+        if (tma) {
+            if (tid == 0) pt.wait(j == 0 ? 0 : j + 1, j + 1, g);
+        } else {
+            cp_async_wait<0>();  // this thread's copies
+        }
         __syncthreads();
+        if (tma && pt.bad) return;  // a wait expired (the whole block leaves; no copy is in flight)
         const int k = z0 - 1 + 2 * j;
         const float* pm = slot(k - 1);
         const float* p0 = slot(k);
@@ -412,8 +443,9 @@ __global__ void __launch_bounds__(Pair3::NT, 3) fwd3p_kernel(Geom g, FwdArgs<flo
 // is known: every step of the output is FP32x2 as well, with the M2 z-neighbours taken from the column itself.
 //
 // Iteration j: raw pair j (planes z0 - 2 + 2j, z0 - 1 + 2j) -> C_j (planes z0 - 3 + 2j, z0 - 2 + 2j);
-// output C_{j-1} (planes z0 - 5 + 2j, z0 - 4 + 2j) for j >= 2.  Raw lambda arrives by asynchronous copies one pair
-// ahead and is transformed into the staged pair one iteration ahead of use.
+// output C_{j-1} (planes z0 - 5 + 2j, z0 - 4 + 2j) for j >= 2.  Raw lambda arrives one pair ahead (by tensor copies
+// issued by one thread where the block's raw region lies inside the grid in x and y, else by every thread's
+// asynchronous copies) and is transformed into the staged pair one iteration ahead of use.
 // ------------------------------------------------------------------------------------------------
 struct PairA3 {
     static constexpr int TX = 32, TY = 8, NT = TX * TY;
@@ -433,14 +465,19 @@ __host__ __device__ constexpr size_t smem3p_adj() {
     return sizeof(float) * 2 * 2 * 4 * PairA3::RS + sizeof(float2) * (2 * 4 * PairA3::NS + 2 * PairA3::SLOT);
 }
 
+// tm: lambda_n as a 4-D tensor (x, y, z, field) with a box of one raw plane (RX x RY x 1 x 4), valid when use_tma
+// is set (n_x a multiple of 4).
 template <int HW, int ZB, bool VEC4>
-__global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<float> a) {
+__global__ void __launch_bounds__(PairA3::NT, 2)
+    adj3p_kernel(Geom g, AdjArgs<float> a, const __grid_constant__ CUtensorMap tm, int use_tma) {
     using R = PairA3;
     static_assert(ZB % 2 == 0, "planes come in pairs");
+    static_assert((4 * R::RS * sizeof(float)) % 128 == 0, "tensor copies land on 128-byte boundaries");
     constexpr int NRP = ZB / 2 + 2;  // raw pairs
     constexpr int NJ = ZB / 2 + 3;   // iterations: raw pairs 0 .. NRP - 1, outputs of C_1 .. C_{NRP - 1}
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* stg = reinterpret_cast<float*>(smem_raw);                  // [2 pair slots][2 planes][4 fields][RS]
+    extern __shared__ __align__(128) unsigned char smem_pair[];
+    __shared__ PairTma pt;
+    float* stg = reinterpret_cast<float*>(smem_pair);                 // [2 pair slots][2 planes][4 fields][RS]
     float2* tl = reinterpret_cast<float2*>(stg + 2 * 2 * 4 * R::RS);  // [2 slots][P, X, Y, Z][NS]
     float2* mom = tl + 2 * 4 * R::NS;                                 // [2 slots][SLOT]
 
@@ -452,11 +489,15 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
     const Pose& P = *a.pose;
     const int xs2 = P.xs[2];
     const bool zper = g.periodic[2] != 0;
+    // tensor copies for a raw region inside the grid (x0 - 4 .. x0 + TX + 3, y0 - 2 .. y0 + TY + 1) and a 128-byte
+    // aligned staging area
+    const bool tma = VEC4 && use_tma != 0 && x0 >= 4 && x0 + R::TX + 4 <= nx && y0 >= 2 && y0 + R::TY + 2 <= ny &&
+                     (smem_addr(stg) & 127u) == 0u;
 
     // raw copies: plane-invariant descriptors of this thread's 16-byte chunks
     int goff[VEC4 ? R::PERCH : 1];
     int soff[VEC4 ? R::PERCH : 1];
-    if (VEC4) {
+    if (VEC4 && !tma) {
 #pragma unroll
         for (int q = 0; q < R::PERCH; ++q) {
             const int e = tid + q * R::NT;
@@ -486,11 +527,20 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
             }
         }
     };
-    auto issue_pair = [&](int jj) {  // raw pair jj into staging slot jj % 2
+    auto issue_pair = [&](int jj) {  // raw pair jj into staging slot jj % 2 (one barrier phase)
         float* dst = stg + (jj & 1) * 2 * 4 * R::RS;
-        issue_plane(dst, z0 - 2 + 2 * jj);
-        issue_plane(dst + 4 * R::RS, z0 - 1 + 2 * jj);
-        cp_async_commit();
+        if (tma) {
+            if (tid == 0) {
+                uint64_t* b = &pt.bar[jj & 1];
+                mbar_expect_tx(b, 2 * 4 * R::RS * sizeof(float));
+                tma_load_4d(dst, &tm, x0 - 4, y0 - 2, wrap(z0 - 2 + 2 * jj, nz), 0, b);
+                tma_load_4d(dst + 4 * R::RS, &tm, x0 - 4, y0 - 2, wrap(z0 - 1 + 2 * jj, nz), 0, b);
+            }
+        } else {
+            issue_plane(dst, z0 - 2 + 2 * jj);
+            issue_plane(dst + 4 * R::RS, z0 - 1 + 2 * jj);
+            cp_async_commit();
+        }
     };
 
     // staged elements of this thread (halo-2 region): wall and footprint coordinates, and whether the element is one
@@ -586,12 +636,21 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
     const float2 w0 = f2s(2.f / 9.f), wf = f2s(1.f / 9.f), wc = f2s(1.f / 72.f), c3 = f2s(3.f), c9 = f2s(9.f);
     const float2 cA = f2s((float)g.A), cm3 = f2s(-3.f);
 
+    if (tma && tid == 0) {
+        pt.init();
+        tma_prefetch_map(&tm);
+    }
     pdl_wait_then_release();
     float fcur[R::PERT][2], fnext[R::PERT][2];
     issue_pair(0);
     load_fac(0, fcur);
-    cp_async_wait<0>();
+    if (tma) {
+        if (tid == 0) pt.wait(0, 0, g);
+    } else {
+        cp_async_wait<0>();
+    }
     __syncthreads();
+    if (tma && pt.bad) return;  // a wait expired (the whole block leaves; no copy is in flight)
     transform(0, fcur);
     issue_pair(1);
     load_fac(1, fnext);
@@ -649,8 +708,14 @@ __global__ void __launch_bounds__(PairA3::NT, 2) adj3p_kernel(Geom g, AdjArgs<fl
                 uc[2].y = uq[2 * N + plane];
             }
         }
-        cp_async_wait<0>();  // raw pair j + 1 (this thread's copies)
+        // raw pair j + 1
+        if (tma) {
+            if (tid == 0 && j + 1 < NRP) pt.wait(j + 1, j + 1, g);
+        } else {
+            cp_async_wait<0>();  // this thread's copies
+        }
         __syncthreads();
+        if (tma && pt.bad) return;
 #pragma unroll
         for (int q = 0; q < R::PERT; ++q) {
             fcur[q][0] = fnext[q][0];
