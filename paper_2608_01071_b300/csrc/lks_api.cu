@@ -141,6 +141,7 @@ struct lks_ctx {
     int S = 1;             // boundary spacing (segment length)
     int M = 1;             // number of segments
     int Lmax = 1;          // longest segment (sensitivity buffer depth)
+    int fac_written[2] = {0, 0};  // per history buffer: leading steps whose 1 / (1 + kappa) the recompute wrote
     int free_slots = 0;    // REVOLVE: slots besides boundary 0
     // the reverse sweep pipelines recomputation, adjoint and sensitivities on three streams with two history buffers:
     // SQRT, and REVOLVE when the slots hold every segment boundary (the binomial schedule is then the sqrt one)
@@ -990,7 +991,9 @@ int njb_of(const lks_ctx* c) {
     return cnt[0] * cnt[1] * cnt[2];
 }
 
-void fwd_step(lks_ctx* c, int n, const void* in, void* out, bool objective, cudaStream_t s) {
+// fac: where the forward kernel also writes 1 / (1 + kappa) of step n on the footprint box (nullptr: not wanted,
+// or the kernel cannot)
+void fwd_step(lks_ctx* c, int n, const void* in, void* out, bool objective, cudaStream_t s, void* fac = nullptr) {
     if (c->rot) {  // kappa and u^S of step n on the footprint box, read by the step kernel
         c->eng->rot_box_map(c->g, c->d_pose + n, c->d_kref, c->d_rotmap, s);
         c->launches++;
@@ -998,8 +1001,10 @@ void fwd_step(lks_ctx* c, int n, const void* in, void* out, bool objective, cuda
     int lo[3], cnt[3];
     probe_blocks(c, lo, cnt);
     const int njb = cnt[0] * cnt[1] * cnt[2];
+    c->eng->fac_out = fac;
     c->eng->fwd(c->g, in, out, c->d_kref, c->d_pose + n,
                 objective ? c->d_jslot + (long long)n * njb : nullptr, c->d_flag, lo, cnt, s);
+    c->eng->fac_out = nullptr;
     c->launches++;
 }
 
@@ -1026,9 +1031,12 @@ void oar_partial(lks_ctx* c, int n, const void* st, cudaStream_t s) {
 }
 
 // Steps n0+1 .. n1 from the state at `in`; dst(n) names the buffer of state n (distinct from the state it is
-// computed from).  Pairs of steps go to one fused launch when the forward kernel supports it.
+// computed from).  Pairs of steps go to one fused launch when the forward kernel supports it.  fac_base: when set
+// and the forward kernel writes them (Engine::fwd_writes_fac), the footprint-box factors 1 / (1 + kappa) of step n go
+// to fac_base + (n - n0 - 1) Fbn elements.
 template <typename Dst>
-const void* run_steps(lks_ctx* c, int n0, int n1, const void* in, Dst&& dst, bool objective, cudaStream_t s) {
+const void* run_steps(lks_ctx* c, int n0, int n1, const void* in, Dst&& dst, bool objective, cudaStream_t s,
+                      void* fac_base = nullptr) {
     const void* cur = in;
     int n = n0 + 1;
     while (n <= n1) {
@@ -1045,7 +1053,8 @@ const void* run_steps(lks_ctx* c, int n0, int n1, const void* in, Dst&& dst, boo
             n += two ? 2 : 1;
         } else {
             void* o = dst(n);
-            fwd_step(c, n, cur, o, objective, s);
+            fwd_step(c, n, cur, o, objective, s,
+                     fac_base != nullptr ? c->tptr(fac_base, (long long)(n - n0 - 1) * c->g.Fbn) : nullptr);
             if (objective && c->oar) oar_partial(c, n, o, s);
             cur = o;
             ++n;
@@ -1172,6 +1181,7 @@ void recompute_segment(lks_ctx* c, int a, int b, const void* start, const void* 
     st.assign(L + 1, nullptr);
     st[0] = start;
     const bool full = c->prm.ckpt == LKS_CKPT_FULL;
+    c->fac_written[buf] = 0;
     cudaEvent_t er = full ? nullptr : span_begin(c, s);
     if (full) {
         for (int j = 1; j <= L; ++j) {
@@ -1185,7 +1195,12 @@ void recompute_segment(lks_ctx* c, int a, int b, const void* start, const void* 
         if (end != nullptr) st[L] = end;
         if (last >= 1) {
             auto dst = [&](int n) -> void* { return c->hist[buf][n - a]; };
-            run_steps(c, a, a + last, start, dst, false, s);
+            // the recompute also writes the adjoint's factors of its steps when its kernel can (the rest come from
+            // box_fac in adjoint_segment)
+            const bool fac = c->eng->fwd_writes_fac() && !c->rot && !c->alks && !c->eng->fused2();
+            run_steps(c, a, a + last, start, dst, false, s,
+                      fac ? c->tptr(c->d_fac, (long long)buf * c->Lmax * c->g.Fbn) : nullptr);
+            if (fac) c->fac_written[buf] = last;
             c->stats.recompute_steps += last;
         }
     }
@@ -1211,14 +1226,18 @@ void adjoint_segment(lks_ctx* c, int a, int b, int buf, cudaStream_t s) {
         span_end(c, 2, ea, s);
         return;
     }
-    // 1 / (1 + kappa) on the footprint box for every step of the segment, in one launch
-    if (c->rot)
+    // 1 / (1 + kappa) on the footprint box for the steps of the segment that the recompute did not write (all of
+    // them unless its kernel writes them), in one launch
+    const int fw = c->fac_written[buf];
+    if (c->rot) {
         c->eng->rot_box_fac(c->g, c->d_pose, c->d_kref, a + 1, b - a,
                             c->tptr(c->d_fac, (long long)buf * c->Lmax * c->g.Fbn), s);
-    else
-        c->eng->box_fac(c->g, c->d_pose, c->d_kref, a + 1, b - a,
-                        c->tptr(c->d_fac, (long long)buf * c->Lmax * c->g.Fbn), s);
-    c->launches++;
+        c->launches++;
+    } else if (fw < b - a) {
+        c->eng->box_fac(c->g, c->d_pose, c->d_kref, a + 1 + fw, b - a - fw,
+                        c->tptr(c->d_fac, ((long long)buf * c->Lmax + fw) * c->g.Fbn), s);
+        c->launches++;
+    }
     for (int n = b; n > a;) {
         const int j = n - a - 1;  // box-buffer slot of step n
         void* bb = c->tptr(c->d_boxbuf, ((long long)buf * c->Lmax + j) * c->box_step);

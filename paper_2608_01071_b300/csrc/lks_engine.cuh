@@ -74,6 +74,10 @@ struct Engine {
     virtual void fwd(const Geom& g, const void* in, void* out, const void* kref, const Pose* pose, double* jslot,
                      unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) = 0;
     // two-step forward launches (steps n and n+1 in one kernel); out2 == nullptr takes step n only
+    // 1 / (1 + kappa) of the step on the footprint box, written by the forward kernel for the adjoint when it can
+    // (fwd_writes_fac) and this is set (for one fwd call)
+    void* fac_out = nullptr;
+    virtual bool fwd_writes_fac() const { return false; }
     virtual bool fused2() const { return false; }
     virtual void fwd2(const Geom& g, const void* in, void* out1, void* out2, const void* kref, const Pose* pose1,
                       double* jslot1, double* jslot2, unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) {}
@@ -148,6 +152,7 @@ FwdArgs<T> make_fwd_args(const Geom& g, const void* in, void* out, const void* k
     a.jslot = jslot;
     a.jsq = jslot != nullptr && g.jsq_off != 0 ? jslot + g.jsq_off : nullptr;
     a.flag = flag;
+    a.fac_out = nullptr;
     a.u_crit2 = (T)g.u_crit2;
     return a;
 }

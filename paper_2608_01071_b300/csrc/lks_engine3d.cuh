@@ -108,6 +108,19 @@ struct Engine3D : EngineCommon<T, 3, HW> {
     // tensor copies are used unless the environment of the context's creation turned them off (LKS_NO_TMA=1:
     // every block copies per thread)
     bool tma_on = true;
+    // the plane-pair forward writes 1 / (1 + kappa) on the footprint box for the adjoint with the hat kernel, with
+    // the arithmetic of box_fac below
+    bool fwd_writes_fac() const override { return kPair && HW == 1 && pair_zb(this->rows_f, false) > 0; }
+    void box_fac(const Geom& g, const Pose* poses, const void* kref, int n_first, int nsteps, void* out,
+                 cudaStream_t s) override {
+        if constexpr (kPair && HW == 1) {
+            box_fac_hat3_kernel<<<dim3(nblk(g.Fbn, 256), nsteps, 1), 256, 0, s>>>(g, poses, (const float*)kref, n_first,
+                                                                                 (float*)out);
+            LKS_LAUNCHED();
+        } else {
+            EngineCommon<T, 3, HW>::box_fac(g, poses, kref, n_first, nsteps, out, s);
+        }
+    }
     std::vector<int> fwd_codes() const override {
         if (kPair) return {1, 8, 16, 32, 64, 96, 128, 160};
         return {1, 8, 16, 32, 64, 96};
@@ -166,6 +179,7 @@ struct Engine3D : EngineCommon<T, 3, HW> {
             launch_pdl(fwd3s_kernel<T, HW, 16, 16>, this->fgrid, this->fthreads, smem3s_fwd<T, 16>(), s, this->pdl, g, a);
         else if constexpr (kPair) {
             const bool v4 = g.n[0] % 4 == 0;
+            a.fac_out = (float*)this->fac_out;
             CUtensorMap tm;
             const int ut = tma_on && pair_tensor_map(g, in, tm) ? 1 : 0;
             switch (pair_zb(this->rows_f, false)) {

@@ -68,10 +68,13 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 //   K_xy(jz) = sum_{kx, ky} w_x[kx] w_y[ky] kappa^ref[jx0 + kx, jy0 + ky, jz],
 // is the same for every node of the column, and consecutive nodes share one of their two design planes: a window of
 // two K_xy values rolls upward, and each new plane adds one (four loads) instead of evaluating all eight taps.
+// Every operation is an explicitly rounded intrinsic, so that the forward step and box_fac_kernel, which both use
+// this map, give kappa (and 1 / (1 + kappa)) bit for bit alike whatever the compiler contracts around them.
 struct ColumnMapHat {
     float wxy[4];  // products of the valid x and y tap weights (0 for a tap outside the design grid)
     int off[4];    // design-grid offsets of the x-y taps (clamped into the grid where the weight is 0)
     float cxy;     // sum of the valid x weights times the sum of the valid y weights
+    float wz[2];   // z tap weights of the step
     float win[2];  // K_xy of design planes jz0, jz0 + 1
     int jz0;       // first design plane of the window (-2^30: empty)
 
@@ -86,30 +89,31 @@ struct ColumnMapHat {
             wy[k] = vy ? P.wf[1][k] : 0.f;
             ix[k] = vx ? jx : 0;
             iy[k] = vy ? jy : 0;
-            sx += wx[k];
-            sy += wy[k];
+            sx = __fadd_rn(sx, wx[k]);
+            sy = __fadd_rn(sy, wy[k]);
         }
 #pragma unroll
         for (int l = 0; l < 2; ++l)
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                wxy[k + 2 * l] = wx[k] * wy[l];
+                wxy[k + 2 * l] = __fmul_rn(wx[k], wy[l]);
                 off[k + 2 * l] = ix[k] + g.nde[0] * iy[l];
             }
-        cxy = sx * sy;
+        cxy = __fmul_rn(sx, sy);
+        wz[0] = P.wf[2][0];
+        wz[1] = P.wf[2][1];
         jz0 = -(1 << 30);
     }
     __device__ __forceinline__ float kxy(const Geom& g, const float* __restrict__ kref, int jz) const {
         if (jz < 0 || jz >= g.nde[2]) return 0.f;
         const float* kp = kref + g.nde[0] * g.nde[1] * jz;
-        float s = wxy[0] * kp[off[0]];
+        float s = __fmul_rn(wxy[0], kp[off[0]]);
 #pragma unroll
-        for (int t = 1; t < 4; ++t) s += wxy[t] * kp[off[t]];
+        for (int t = 1; t < 4; ++t) s = __fmaf_rn(wxy[t], kp[off[t]], s);
         return s;
     }
     // kappa and C at box coordinate bz of the column
-    __device__ __forceinline__ void at(const Geom& g, const Pose& P, const float* __restrict__ kref, int bz, float& kap,
-                                       float& C) {
+    __device__ __forceinline__ void at(const Geom& g, const float* __restrict__ kref, int bz, float& kap, float& C) {
         const int j0 = bz - 1;
         if (j0 == jz0 + 1) {
             win[0] = win[1];
@@ -120,11 +124,29 @@ struct ColumnMapHat {
         }
         jz0 = j0;
         const bool v0 = j0 >= 0 && j0 < g.nde[2], v1 = j0 + 1 >= 0 && j0 + 1 < g.nde[2];
-        const float wz0 = v0 ? P.wf[2][0] : 0.f, wz1 = v1 ? P.wf[2][1] : 0.f;
-        kap = wz0 * win[0] + wz1 * win[1];
-        C = cxy * (wz0 + wz1);
+        const float wz0 = v0 ? wz[0] : 0.f, wz1 = v1 ? wz[1] : 0.f;
+        kap = __fmaf_rn(wz1, win[1], __fmul_rn(wz0, win[0]));
+        C = __fmul_rn(cxy, __fadd_rn(wz0, wz1));
     }
 };
+
+// 1 / (1 + kappa) over the footprint box for steps n_first .. n_first + nsteps - 1 (box_fac_kernel) for the FP32
+// state and the hat kernel in 3D, with the column map of the plane-pair forward, which writes the same factors for
+// the steps it recomputes: both give the same bits.
+static __global__ void __launch_bounds__(256) box_fac_hat3_kernel(Geom g, const Pose* __restrict__ poses,
+                                                                  const float* __restrict__ kref, int n_first,
+                                                                  float* __restrict__ fac) {
+    const long long bl = blockIdx.x * 256LL + threadIdx.x;
+    if (bl >= g.Fbn) return;
+    const int j = blockIdx.y;
+    int b[3];
+    box_unflatten<3>(g, bl, b);
+    ColumnMapHat cm;
+    cm.init(g, poses[n_first + j], b[0], b[1]);
+    float kap, C;
+    cm.at(g, kref, b[2], kap, C);
+    fac[j * g.Fbn + bl] = __fdiv_rn(1.f, __fadd_rn(1.f, kap));
+}
 
 // Forward step n-1 -> n (Sec. 2.2 / 2.3); same result as fwd_step_kernel up to the order of FP additions.
 // VEC4: n_x is a multiple of 4, so raw rows move in aligned 16-byte chunks that never straddle the periodic seam.
@@ -266,37 +288,73 @@ __global__ void __launch_bounds__(Pair3::NT, 3)
     if (HW == 1 && colbox) cmap.init(g, P, bx, by);
     const int gcol = xg + nx * yg;
 
-    // Brinkman, walls and stores of one completed output plane
-    auto emit = [&](int zo, float mp, float mx, float my, float mz) {
-        if (zo < z0 || zo >= z0 + ZB || zo >= nz || !col) return;
-        const float pn = mp * (1.f / 3.f);
-        float un[3] = {mx, my, mz};
-        const int bz = colbox ? box_coord(zo, xs2, g.Fb[2], g.n[2], g.periodic[2]) : -1;
-        if (bz >= 0) {
-            float kap, C;
-            if (HW == 1) {
-                cmap.at(g, P, a.kref, bz, kap, C);
-            } else {
-                const int b[3] = {bx, by, bz};
-                map_node<float, 3, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
-            }
-            const float inv = 1.f / (1.f + kap);
-            un[0] = (un[0] + kap * (uG0 * C)) * inv;
-            un[1] = (un[1] + kap * (uG1 * C)) * inv;
-            un[2] = (un[2] + kap * (uG2 * C)) * inv;
+    // kappa and C (Eqs. kappa, u_s) at box coordinate bz of the column
+    auto map_at = [&](int bz, float& kap, float& C) {
+        if (HW == 1) {
+            cmap.at(g, a.kref, bz, kap, C);
+        } else {
+            const int b[3] = {bx, by, bz};
+            map_node<float, 3, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
         }
-        const int wz_side = g.periodic[2] ? -1 : (zo == 0 ? 0 : (zo == nz - 1 ? 1 : -1));
-        const bool wall = wxy_axis >= 0 || wz_side >= 0;
-        if (wall) {
-            const int ax = wz_side >= 0 ? 2 : wxy_axis, sd = wz_side >= 0 ? wz_side : wxy_side;
+    };
+    // Brinkman (Eqs. p, u), walls and stores of the completed output planes zo and zo + 1 (lanes x and y of the
+    // moments), both among the block's planes
+    auto emit2 = [&](int zo, float2 mp, float2 mx, float2 my, float2 mz) {
+        if (!col) return;
+        const float2 pn = f2mul(f2s(1.f / 3.f), mp);
+        float2 un[3] = {mx, my, mz};
+        if (colbox) {
+            const int bz0 = box_coord(zo, xs2, g.Fb[2], g.n[2], g.periodic[2]);
+            const int bz1 = box_coord(zo + 1, xs2, g.Fb[2], g.n[2], g.periodic[2]);
+            if (bz0 >= 0 || bz1 >= 0) {
+                float2 kap = f2s(0.f), C = f2s(0.f);
+                if (bz0 >= 0) map_at(bz0, kap.x, C.x);
+                if (bz1 >= 0) map_at(bz1, kap.y, C.y);
+                const float2 inv = f2(__fdiv_rn(1.f, __fadd_rn(1.f, kap.x)), __fdiv_rn(1.f, __fadd_rn(1.f, kap.y)));
+                if (a.fac_out != nullptr) {  // the adjoint's 1 / (1 + kappa) of this step (as box_fac_kernel)
+                    const int bcol = bx + g.Fb[0] * by, fbxy = g.Fb[0] * g.Fb[1];
+                    if (bz0 >= 0 && zo < nz) a.fac_out[bcol + fbxy * bz0] = inv.x;
+                    if (bz1 >= 0 && zo + 1 < nz) a.fac_out[bcol + fbxy * bz1] = inv.y;
+                }
+                const float uG[3] = {uG0, uG1, uG2};
 #pragma unroll
-            for (int c = 0; c < 3; ++c) un[c] = (float)g.wall_u[ax][sd][c];
+                for (int c = 0; c < 3; ++c) {
+                    const float2 nw = f2mul(f2fma(kap, f2mul(f2s(uG[c]), C), un[c]), inv);
+                    un[c] = f2(bz0 >= 0 ? nw.x : un[c].x, bz1 >= 0 ? nw.y : un[c].y);
+                }
+            }
+        }
+        // wall planes (zo >= 0, so plane zo + 1 is never the lower z wall)
+        const int wz0 = g.periodic[2] ? -1 : (zo == 0 ? 0 : (zo == nz - 1 ? 1 : -1));
+        const int wz1 = g.periodic[2] ? -1 : (zo + 1 == nz - 1 ? 1 : -1);
+        const bool wall0 = wxy_axis >= 0 || wz0 >= 0, wall1 = wxy_axis >= 0 || wz1 >= 0;
+        if (wall0) {
+            const int ax = wz0 >= 0 ? 2 : wxy_axis, sd = wz0 >= 0 ? wz0 : wxy_side;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) un[c].x = (float)g.wall_u[ax][sd][c];
+        }
+        if (wall1) {
+            const int ax = wz1 >= 0 ? 2 : wxy_axis, sd = wz1 >= 0 ? wz1 : wxy_side;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) un[c].y = (float)g.wall_u[ax][sd][c];
         }
         const int gi = gcol + plane * zo;
-        a.out_p[gi] = pn;
+        const bool v0 = zo < nz, v1 = zo + 1 < nz;
+        if (v0) {
+            a.out_p[gi] = pn.x;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) a.out_u[c * N + gi] = un[c];
-        if (!wall && a.u_crit2 > 0.f && !(un[0] * un[0] + un[1] * un[1] + un[2] * un[2] <= a.u_crit2)) unstable = true;
+            for (int c = 0; c < 3; ++c) a.out_u[c * N + gi] = un[c].x;
+        }
+        if (v1) {
+            a.out_p[gi + plane] = pn.y;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) a.out_u[c * N + gi + plane] = un[c].y;
+        }
+        if (a.u_crit2 > 0.f) {
+            const float2 uu = f2fma(un[2], un[2], f2fma(un[1], un[1], f2mul(un[0], un[0])));
+            if (v0 && !wall0 && !(uu.x <= a.u_crit2)) unstable = true;
+            if (v1 && !wall1 && !(uu.y <= a.u_crit2)) unstable = true;
+        }
     };
 
 #pragma unroll 1
@@ -328,7 +386,7 @@ __global__ void __launch_bounds__(Pair3::NT, 3)
                 U[c] = f2(u0, u1);
                 Gx[c] = f2sub(f2(a0[r + 1], a1[r + 1]), f2(a0[r - 1], a1[r - 1]));
                 Gy[c] = f2sub(f2(a0[r + R::RX], a1[r + R::RX]), f2(a0[r - R::RX], a1[r - R::RX]));
-                Gz[c] = f2sub(f2(u1, p2[(1 + c) * R::RS + r]), f2(pm[(1 + c) * R::RS + r], u0));
+                Gz[c] = f2(u1 - pm[(1 + c) * R::RS + r], p2[(1 + c) * R::RS + r] - u0);
             }
             const float2 Pp = f2(p0[r], p1[r]);
             const float2 uu = f2fma(U[2], U[2], f2fma(U[1], U[1], f2mul(U[0], U[0])));
@@ -403,8 +461,7 @@ __global__ void __launch_bounds__(Pair3::NT, 3)
             dnB[1] = dnX.y;
             dnB[2] = dnY.y;
             dnB[3] = dnP.y;
-            emit(k - 1, oA0, oA1, oA2, oA3);
-            emit(k, oB0, oB1, oB2, oB3);
+            if (j >= 1) emit2(k - 1, f2(oA0, oB0), f2(oA1, oB1), f2(oA2, oB2), f2(oA3, oB3));
         }
     }
     if (unstable) atomicOr(a.flag, 1u);

@@ -34,6 +34,8 @@ struct FwdArgs {
     double* jslot;      // objective partials of step n, one per probe block (nullptr: not needed)
     double* jsq;        // their twins for (n.u)^2 (set with jslot)
     unsigned* flag;     // stability flag (bit 0)
+    T* fac_out;         // 1 / (1 + kappa) of step n on the footprint box (box_fac_kernel's layout), written by the
+                        // plane-pair forward for the adjoint when set; nullptr otherwise
     int jb_lo[3];       // first block touching the probe box, per axis
     int jb_n[3];        // number of blocks touching it, per axis
     T dir[3];           // objective direction n in T
