@@ -767,7 +767,7 @@ void allocate(lks_ctx* c) {
     // kappa-bar per step (and u^S-bar with a rotating body); per-block motion partials per step (2 D values, and
     // dJ/dtheta, dJ/domega with a rotating body)
     c->d_kbar = dalloc(c, (size_t)c->Lmax * c->g.Fbn * ts * (c->rot ? 1 + D : 1));
-    c->nsb = (int)nblk(c->g.Fbn, c->rot ? 256 : 256 * kSensNPT);  // blocks per step of rot_sens / adj_sens
+    c->nsb = c->rot ? (int)nblk(c->g.Fbn, 256) : c->eng->sens_blocks(c->g, c->alks);  // blocks per step of the sensitivities
     c->d_mslot = (double*)dalloc(c, (size_t)c->Lmax * c->nsb * (2 * D + (c->rot ? 2 : 0)) * 8);
     c->d_mpart = (double*)dalloc(c, (size_t)c->Lmax * kMotionChunks * (2 * D + (c->rot ? 2 : 0)) * 8);
     if (c->rot) {

@@ -95,6 +95,8 @@ struct Engine {
                          cudaStream_t s) = 0;
     virtual void sens(const Geom& g, const Pose* poses, const void* kref, const void* boxbuf, long long bstride,
                       int n_first, int nsteps, void* kbar, double* mslot, bool alks, cudaStream_t s) = 0;
+    // blocks per step of sens (the motion partials per step in mslot)
+    virtual int sens_blocks(const Geom& g, bool alks) const { return (int)nblk(g.Fbn, 256 * kSensNPT); }
     // the ALKS reverse sweep (lks_alks.cuh): terminal state and one step; the pointers of AlksArgs are in the state
     // precision of the engine
     virtual void alks_init(const Geom& g, const Pose* pose, const void* kref, void* lam, const void* args,

@@ -121,6 +121,24 @@ struct Engine3D : EngineCommon<T, 3, HW> {
             EngineCommon<T, 3, HW>::box_fac(g, poses, kref, n_first, nsteps, out, s);
         }
     }
+    // local sensitivities: the column kernel for the FP32 state and the hat kernel (discrete adjoint)
+    void sens(const Geom& g, const Pose* poses, const void* kref, const void* boxbuf, long long bstride, int n_first,
+              int nsteps, void* kbar, double* mslot, bool alks, cudaStream_t s) override {
+        if constexpr (kPair && HW == 1) {
+            if (!alks) {
+                adj_sens_hat3_kernel<<<dim3(sens_blocks(g, alks), nsteps, 1), kSensHatNT, 0, s>>>(
+                    g, poses, (const float*)kref, (const float*)boxbuf, bstride, n_first, (float*)kbar, mslot);
+                LKS_LAUNCHED();
+                return;
+            }
+        }
+        EngineCommon<T, 3, HW>::sens(g, poses, kref, boxbuf, bstride, n_first, nsteps, kbar, mslot, alks, s);
+    }
+    int sens_blocks(const Geom& g, bool alks) const override {
+        if (kPair && HW == 1 && !alks)
+            return (int)(nblk((long long)g.Fb[0] * g.Fb[1], kSensHatNT) * nblk(g.Fb[2], kSensHatZC));
+        return EngineCommon<T, 3, HW>::sens_blocks(g, alks);
+    }
     std::vector<int> fwd_codes() const override {
         if (kPair) return {1, 8, 16, 32, 64, 96, 128, 160};
         return {1, 8, 16, 32, 64, 96};

@@ -148,6 +148,156 @@ static __global__ void __launch_bounds__(256) box_fac_hat3_kernel(Geom g, const 
     fac[j * g.Fbn + bl] = __fdiv_rn(1.f, __fadd_rn(1.f, kap));
 }
 
+// Local shape and motion sensitivities of a segment (adj_sens_kernel's quantities, Eqs. dJdgamma, dJdchi in discrete
+// form) for the FP32 state and the hat kernel in 3D: one thread per (footprint-box column, chunk of kSensHatZC
+// planes, step) marching up its chunk of the column.  The mapping and its offset derivatives factor like the column map: per design plane jz the x-y sums
+//   K(jz) = sum w_x w_y kappa^ref,   X(jz) = sum w'_x w_y kappa^ref,   Y(jz) = sum w_x w'_y kappa^ref
+// (four loads serve all three; w' = dw/d offset), and at box plane bz, whose z taps are jz = bz - 1 and bz,
+//   kappa = sum w_z K,   dkappa/ds = (sum w_z X, sum w_z Y, sum w'_z K),
+//   C = S_x S_y S_z,   dC/ds = (S'_x S_y S_z, S_x S'_y S_z, S_x S_y S'_z)
+// with S, S' the sums of the valid weights and of their derivatives (taps off the design grid have weight 0).  A
+// thread sums its motion partials over its chunk and the block over its threads in FP32, in a fixed order, as
+// adj_sens_kernel does (FP64 from the block sums on: the FP64 pipe of this part is narrow); blocks: the column blocks
+// of the first chunk, then of the next...  kappa-bar goes to kbar as in adj_sens_kernel.
+constexpr int kSensHatNT = 128, kSensHatZC = 16;
+
+static __global__ void __launch_bounds__(kSensHatNT)
+    adj_sens_hat3_kernel(Geom g, const Pose* __restrict__ poses, const float* __restrict__ kref,
+                         const float* __restrict__ boxbuf, long long bstride, int n_first, float* __restrict__ kbar,
+                         double* __restrict__ mslot) {
+    __shared__ double red[6 * (kSensHatNT / 32)];
+    const int s = blockIdx.y;
+    const Pose& P = poses[n_first + s];
+    const int fb0 = g.Fb[0], fbxy = g.Fb[0] * g.Fb[1];
+    const long long Fbn = g.Fbn;
+    const int ncb = (fbxy + kSensHatNT - 1) / kSensHatNT;  // column blocks per chunk
+    const int col = (blockIdx.x % ncb) * kSensHatNT + threadIdx.x;
+    const int bz0 = (blockIdx.x / ncb) * kSensHatZC, bz1 = min(bz0 + kSensHatZC, g.Fb[2]);
+    float mv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bool ok = col < fbxy;
+    const int bx = ok ? col % fb0 : 0, by = ok ? col / fb0 : 0;
+    // box nodes outside the grid (non-periodic axes) contribute nothing
+    if (ok && !g.periodic[0]) ok = (unsigned)(P.xs[0] + bx) < (unsigned)g.n[0];
+    if (ok && !g.periodic[1]) ok = (unsigned)(P.xs[1] + by) < (unsigned)g.n[1];
+    if (ok) {
+        float wx[2], dwx[2], wy[2], dwy[2], sx = 0.f, dsx = 0.f, sy = 0.f, dsy = 0.f;
+        int ix[2], iy[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int jx = bx - 1 + k, jy = by - 1 + k;
+            const bool vx = jx >= 0 && jx < g.nde[0], vy = jy >= 0 && jy < g.nde[1];
+            wx[k] = vx ? P.wf[0][k] : 0.f;
+            dwx[k] = vx ? P.dwf[0][k] : 0.f;
+            wy[k] = vy ? P.wf[1][k] : 0.f;
+            dwy[k] = vy ? P.dwf[1][k] : 0.f;
+            ix[k] = vx ? jx : 0;
+            iy[k] = vy ? jy : 0;
+            sx += wx[k];
+            dsx += dwx[k];
+            sy += wy[k];
+            dsy += dwy[k];
+        }
+        float wK[4], wX[4], wY[4];
+        int off[4];
+#pragma unroll
+        for (int l = 0; l < 2; ++l)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                wK[k + 2 * l] = wx[k] * wy[l];
+                wX[k + 2 * l] = dwx[k] * wy[l];
+                wY[k + 2 * l] = wx[k] * dwy[l];
+                off[k + 2 * l] = ix[k] + g.nde[0] * iy[l];
+            }
+        const float wz[2] = {P.wf[2][0], P.wf[2][1]}, dwz[2] = {P.dwf[2][0], P.dwf[2][1]};
+        const float uG[3] = {P.uGf[0], P.uGf[1], P.uGf[2]};
+        const int nde2 = g.nde[2], sxy = g.nde[0] * g.nde[1], xs2 = P.xs[2], nz = g.n[2];
+        const bool zper = g.periodic[2] != 0;
+        const float* rec = boxbuf + (long long)s * bstride + col;
+        float* kbo = kbar != nullptr ? kbar + (long long)s * Fbn + col : nullptr;
+        // the four x-y taps of design plane jz (0 off the design grid), and their x-y sums
+        auto taps = [&](int jz, float (&kr)[4]) {
+            const bool v = jz >= 0 && jz < nde2;
+            const float* kp = kref + sxy * (v ? jz : 0);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) kr[t] = v ? kp[off[t]] : 0.f;
+        };
+        auto xy_sums = [&](const float (&kr)[4], float& K, float& X, float& Y) {
+            K = X = Y = 0.f;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                K += wK[t] * kr[t];
+                X += wX[t] * kr[t];
+                Y += wY[t] * kr[t];
+            }
+        };
+        float K0, X0, Y0;  // x-y sums of design plane bz - 1
+        {
+            float kr[4];
+            taps(bz0 - 1, kr);
+            xy_sums(kr, K0, X0, Y0);
+        }
+        // four planes at a time: all their loads (design taps, records) are issued before any is used
+        constexpr int U = 4;
+#pragma unroll 1
+        for (int bq = bz0; bq < bz1; bq += U) {
+            float kr[U][4], rl[U][6];
+            bool in[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int bz = bq + u;
+                in[u] = bz < bz1 && (zper || (unsigned)(xs2 + bz) < (unsigned)nz);
+                taps(bz < bz1 ? bz : -1, kr[u]);
+                const long long o = (long long)fbxy * (in[u] ? bz : 0);
+#pragma unroll
+                for (int c = 0; c < 6; ++c) rl[u][c] = in[u] ? rec[c * Fbn + o] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int bz = bq + u;
+                float K1, X1, Y1;  // design plane bz
+                xy_sums(kr[u], K1, X1, Y1);
+                if (in[u]) {
+                    const bool v0 = bz >= 1, v1 = bz < nde2;  // z taps jz = bz - 1, bz on the design grid
+                    const float wz0 = v0 ? wz[0] : 0.f, wz1 = v1 ? wz[1] : 0.f;
+                    const float dz0 = v0 ? dwz[0] : 0.f, dz1 = v1 ? dwz[1] : 0.f;
+                    const float kap = wz0 * K0 + wz1 * K1;
+                    const float dk[3] = {wz0 * X0 + wz1 * X1, wz0 * Y0 + wz1 * Y1, dz0 * K0 + dz1 * K1};
+                    const float sz = wz0 + wz1, dsz = dz0 + dz1;
+                    const float C = sx * sy * sz;
+                    const float dC[3] = {dsx * sy * sz, sx * dsy * sz, sx * sy * dsz};
+                    const float inv = 1.f / (1.f + kap);
+                    float kb = 0.f, cbar = 0.f, usb[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float lu = rl[u][c];
+                        kb += lu * (uG[c] * C - rl[u][3 + c]);
+                        usb[c] = lu * kap * inv;
+                        cbar += usb[c] * uG[c];
+                    }
+                    kb *= inv;
+                    if (kbo != nullptr) kbo[(long long)fbxy * bz] = kb;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        mv[c] += kb * dk[c] + cbar * dC[c];
+                        mv[3 + c] += usb[c] * C;
+                    }
+                }
+                K0 = K1;
+                X0 = X1;
+                Y0 = Y1;
+            }
+        }
+    }
+    if (mslot != nullptr) {
+        double out[6];
+        block_sum<kSensHatNT, 6, float>(mv, out, red);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) mslot[((long long)s * gridDim.x + blockIdx.x) * 6 + c] = out[c];
+        }
+    }
+}
+
 // Forward step n-1 -> n (Sec. 2.2 / 2.3); same result as fwd_step_kernel up to the order of FP additions.
 // VEC4: n_x is a multiple of 4, so raw rows move in aligned 16-byte chunks that never straddle the periodic seam.
 // tm: the input state as a 4-D tensor (x, y, z, field) with a box of one raw plane (RX x RY x 1 x 4), valid when
