@@ -134,6 +134,19 @@ struct Engine3D : EngineCommon<T, 3, HW> {
         }
         EngineCommon<T, 3, HW>::sens(g, poses, kref, boxbuf, bstride, n_first, nsteps, kbar, mslot, alks, s);
     }
+    // transposed mapping: the hat kernel's gather for the FP32 state (both sensitivity kernels leave kappa-bar = 0
+    // outside the grid)
+    void gather(const Geom& g, const Pose* poses, const void* kbar, int n_first, int nsteps, long long kstride,
+                double* dkref, cudaStream_t s) override {
+        if constexpr (kPair && HW == 1) {
+            const long long nd = (long long)g.nde[0] * g.nde[1] * g.nde[2];
+            design_gather_hat3_kernel<<<nblk(nd, kGatherHatNT), kGatherHatNT, 0, s>>>(g, poses, (const float*)kbar,
+                                                                                   n_first, nsteps, kstride, dkref);
+            LKS_LAUNCHED();
+        } else {
+            EngineCommon<T, 3, HW>::gather(g, poses, kbar, n_first, nsteps, kstride, dkref, s);
+        }
+    }
     int sens_blocks(const Geom& g, bool alks) const override {
         if (kPair && HW == 1 && !alks)
             return (int)(nblk((long long)g.Fb[0] * g.Fb[1], kSensHatNT) * nblk(g.Fb[2], kSensHatZC));

@@ -158,10 +158,10 @@ static __global__ void __launch_bounds__(256) box_fac_hat3_kernel(Geom g, const 
 // with S, S' the sums of the valid weights and of their derivatives (taps off the design grid have weight 0).  A
 // thread sums its motion partials over its chunk and the block over its threads in FP32, in a fixed order, as
 // adj_sens_kernel does (FP64 from the block sums on: the FP64 pipe of this part is narrow); blocks: the column blocks
-// of the first chunk, then of the next...  kappa-bar goes to kbar as in adj_sens_kernel.
+// of the first chunk, then of the next...  kappa-bar goes to kbar as in adj_sens_kernel (0 outside the grid).
 constexpr int kSensHatNT = 128, kSensHatZC = 16;
 
-static __global__ void __launch_bounds__(kSensHatNT)
+static __global__ void __launch_bounds__(kSensHatNT, 5)
     adj_sens_hat3_kernel(Geom g, const Pose* __restrict__ poses, const float* __restrict__ kref,
                          const float* __restrict__ boxbuf, long long bstride, int n_first, float* __restrict__ kbar,
                          double* __restrict__ mslot) {
@@ -174,11 +174,16 @@ static __global__ void __launch_bounds__(kSensHatNT)
     const int col = (blockIdx.x % ncb) * kSensHatNT + threadIdx.x;
     const int bz0 = (blockIdx.x / ncb) * kSensHatZC, bz1 = min(bz0 + kSensHatZC, g.Fb[2]);
     float mv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    bool ok = col < fbxy;
+    const bool colin = col < fbxy;
+    bool ok = colin;
     const int bx = ok ? col % fb0 : 0, by = ok ? col / fb0 : 0;
-    // box nodes outside the grid (non-periodic axes) contribute nothing
+    // box nodes outside the grid (non-periodic axes) contribute nothing and get kappa-bar = 0
     if (ok && !g.periodic[0]) ok = (unsigned)(P.xs[0] + bx) < (unsigned)g.n[0];
     if (ok && !g.periodic[1]) ok = (unsigned)(P.xs[1] + by) < (unsigned)g.n[1];
+    float* kbo = colin && kbar != nullptr ? kbar + (long long)s * Fbn + col : nullptr;
+    if (!ok && kbo != nullptr) {
+        for (int bz = bz0; bz < bz1; ++bz) kbo[(long long)fbxy * bz] = 0.f;
+    }
     if (ok) {
         float wx[2], dwx[2], wy[2], dwy[2], sx = 0.f, dsx = 0.f, sy = 0.f, dsy = 0.f;
         int ix[2], iy[2];
@@ -213,7 +218,6 @@ static __global__ void __launch_bounds__(kSensHatNT)
         const int nde2 = g.nde[2], sxy = g.nde[0] * g.nde[1], xs2 = P.xs[2], nz = g.n[2];
         const bool zper = g.periodic[2] != 0;
         const float* rec = boxbuf + (long long)s * bstride + col;
-        float* kbo = kbar != nullptr ? kbar + (long long)s * Fbn + col : nullptr;
         // the four x-y taps of design plane jz (0 off the design grid), and their x-y sums
         auto taps = [&](int jz, float (&kr)[4]) {
             const bool v = jz >= 0 && jz < nde2;
@@ -281,6 +285,8 @@ static __global__ void __launch_bounds__(kSensHatNT)
                         mv[c] += kb * dk[c] + cbar * dC[c];
                         mv[3 + c] += usb[c] * C;
                     }
+                } else if (bz < bz1 && kbo != nullptr) {
+                    kbo[(long long)fbxy * bz] = 0.f;
                 }
                 K0 = K1;
                 X0 = X1;
@@ -296,6 +302,54 @@ static __global__ void __launch_bounds__(kSensHatNT)
             for (int c = 0; c < 6; ++c) mslot[((long long)s * gridDim.x + blockIdx.x) * 6 + c] = out[c];
         }
     }
+}
+
+// Transposed mapping onto the design grid (design_gather_kernel, Eq. dJdgamma in discrete form) for the FP32 state
+// and the hat kernel in 3D.  kappa-bar is 0 at footprint-box nodes outside the grid (both sensitivity kernels write
+// it so), so a tap needs no grid test, only to lie in the box: its validity and offset are fixed per design node.
+// The eight tap-weight products of each step are formed once per block in shared memory; a thread sums its eight
+// taps per step and adds the step's sum to its FP64 running sum in strict step order n = Nt..1 (across calls too).
+constexpr int kGatherHatNT = 128, kGatherHatSC = 64;  // threads per block; steps whose weights are staged at once
+
+static __global__ void __launch_bounds__(kGatherHatNT)
+    design_gather_hat3_kernel(Geom g, const Pose* __restrict__ poses, const float* __restrict__ kbar, int n_first,
+                              int nsteps, long long kstride, double* __restrict__ dkref) {
+    __shared__ float wp[kGatherHatSC][8];
+    const int nd = g.nde[0] * g.nde[1] * g.nde[2];  // fewer than 2^31 (checked at context creation)
+    const int jl = blockIdx.x * kGatherHatNT + threadIdx.x;
+    const bool act = jl < nd;
+    const int jx = jl % g.nde[0], jy = (jl / g.nde[0]) % g.nde[1], jz = jl / (g.nde[0] * g.nde[1]);
+    // tap t = kx + 2 ky + 4 kz reads box node (j + 1 - k) per axis
+    int off[8];
+    bool val[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int bx = jx + 1 - (t & 1), by = jy + 1 - ((t >> 1) & 1), bz = jz + 1 - (t >> 2);
+        val[t] = act && bx >= 0 && bx < g.Fb[0] && by >= 0 && by < g.Fb[1] && bz >= 0 && bz < g.Fb[2];
+        off[t] = val[t] ? bx + g.Fb[0] * (by + g.Fb[1] * bz) : 0;
+    }
+    double acc = act ? dkref[jl] : 0.0;
+    for (int c0 = nsteps - 1; c0 >= 0; c0 -= kGatherHatSC) {
+        const int cn = min(kGatherHatSC, c0 + 1);  // steps c0, c0 - 1, .., c0 - cn + 1
+        __syncthreads();
+        for (int i = threadIdx.x; i < cn * 8; i += kGatherHatNT) {
+            const int u = i >> 3, t = i & 7;
+            const Pose& P = poses[n_first + c0 - u];
+            wp[u][t] = P.wf[0][t & 1] * P.wf[1][(t >> 1) & 1] * P.wf[2][t >> 2];
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll 2
+            for (int u = 0; u < cn; ++u) {
+                const float* kb = kbar + (long long)(c0 - u) * kstride;
+                float sum = 0.f;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) sum = fmaf(wp[u][t], val[t] ? kb[off[t]] : 0.f, sum);
+                acc += (double)sum;
+            }
+        }
+    }
+    if (act) dkref[jl] = acc;
 }
 
 // Forward step n-1 -> n (Sec. 2.2 / 2.3); same result as fwd_step_kernel up to the order of FP additions.

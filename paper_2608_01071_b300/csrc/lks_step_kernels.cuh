@@ -628,7 +628,8 @@ __global__ void __launch_bounds__(TX * TY * TZ) adj_step_kernel(Geom g, AdjArgs<
 // adjoint's critical path: one thread per (footprint-box node, step).
 //   kappa-bar = lam_u . (u^S - u_n) / (1 + kappa),   u^S-bar = lam_u kappa / (1 + kappa)
 //   dJ/ds_a  += kappa-bar dkappa/ds_a + (u^S-bar . u^G) dC/ds_a,   dJ/du^G_a += u^S-bar_a C
-// kappa-bar goes to kbar[s][box node] (for design_gather_kernel); the motion terms are summed per block
+// kappa-bar goes to kbar[s][box node] (for design_gather_kernel; 0 at box nodes outside the grid); the motion terms
+// are summed per block
 // (FP32 within a warp, FP64 across warps) into mslot[s][block][2D].
 // ------------------------------------------------------------------------------------------------
 // With ALKS set the records hold the ALKS adjoint velocity u~ (lks_alks.cuh) and the sensitivities are its forms
@@ -661,6 +662,7 @@ __global__ void __launch_bounds__(256) adj_sens_kernel(Geom g, const Pose* __res
                 ingrid = ingrid && x >= 0 && x < g.n[c];
             }
         }
+        if (!ingrid && kbar != nullptr) kbar[(long long)s * g.Fbn + bl] = 0;
         if (ingrid) {
             const T* bb = boxbuf + (long long)s * bstride;
             T kap, C, dk[D], dC[D];
