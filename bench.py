@@ -129,7 +129,7 @@ COMMON_SOURCES = ["lks_common.cuh", "lks_step_kernels.cuh"]
 
 
 def kernel_variant(lattice, rows, kind):
-    """(name, source file, steps per launch) of the step kernel that a tile_rows code selects.
+    """(name, source files, steps per launch) of the step kernel that a tile_rows code selects.
 
     kind is "fwd" or "adj".  D2Q9: 1/2 row tiles, 3 two steps per launch on row tiles, 4/8/16 warp columns,
     32/64 vectorised warp columns.  D3Q15: 1 the generic shared-memory kernel, 8/16 z-marching, 32/64/96
@@ -140,7 +140,7 @@ def kernel_variant(lattice, rows, kind):
             return f"{kind}_step_kernel", "lks_step_kernels.cuh", 1
         if rows >= 128:
             zb = {128: 16, 160: 32, 192: 64}[rows]
-            return f"{kind}3p_kernel<ZB={zb}>", "lks_step3p.cuh", 1
+            return f"{kind}3p_kernel<ZB={zb}>", ["lks_step3s.cuh", "lks_tma.cuh", "lks_step3p.cuh"], 1
         if rows >= 32:
             zb, ty = {32: (16, 8), 64: (32, 8), 96: (16, 16)}[rows]
             return f"{kind}3s_kernel<ZB={zb},TY={ty}>", "lks_step3s.cuh", 1
@@ -174,7 +174,7 @@ def captured_traffic(workload_name, kernel, source):
     path = os.path.join(ROOT, "profiles", f"step_kernels_{workload_name}.md")
     if not os.path.exists(path):
         return None
-    sha = source_sha(COMMON_SOURCES + [source])
+    sha = source_sha(COMMON_SOURCES + (list(source) if isinstance(source, (list, tuple)) else [source]))
     for m in re.finditer(r"traffic_bytes_per_launch (\S+) (\d+) src ([0-9a-f]+)", open(path).read()):
         if m.group(1) == kernel and sha.startswith(m.group(3)):
             return int(m.group(2))
