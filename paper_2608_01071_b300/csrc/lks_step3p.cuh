@@ -49,6 +49,11 @@ __host__ __device__ constexpr size_t smem3p_fwd() {
     return sizeof(float) * 4 * 4 * Pair3::RS + sizeof(float2) * Pair3::NFLD * Pair3::NM;
 }
 
+// The thread that issues and waits for a block's tensor copies: the last one, in a warp without a halo-ring node
+// (the ring nodes go to the first threads), so that the copy duty does not fall on a warp that already does more.
+constexpr int kTmaThread = 255;
+static_assert(Pair3::NT == 256, "kTmaThread is the last thread of a plane-pair block");
+
 // Packed FP32x2 arithmetic (one instruction for both planes; rounding as the scalar instructions; a - b = fma(b, -1, a)).
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
@@ -427,7 +432,7 @@ __global__ void __launch_bounds__(Pair3::NT, 3)
     };
     auto issue_pair = [&](int j) {  // raw planes z0 - 2 + 2j, z0 - 1 + 2j as one copy group (one barrier phase)
         if (tma) {
-            if (tid == 0) {
+            if (tid == kTmaThread) {
                 uint64_t* b = &pt.bar[j & 1];
                 mbar_expect_tx(b, 2 * 4 * R::RS * sizeof(float));
                 tma_load_4d(slot(z0 - 2 + 2 * j), &tm, x0 - 4, y0 - 2, wrap(z0 - 2 + 2 * j, nz), 0, b);
@@ -462,7 +467,7 @@ __global__ void __launch_bounds__(Pair3::NT, 3)
     const float2 c3 = f2s(3.f), c9 = f2s(9.f), cA = f2s(A), c45 = f2s(4.5f), cm15 = f2s(-1.5f);
     const float2 w0 = f2s(2.f / 9.f), wf = f2s(1.f / 9.f), wc = f2s(1.f / 72.f);
 
-    if (tma && tid == 0) {
+    if (tma && tid == kTmaThread) {
         pt.init();
         tma_prefetch_map(&tm);
     }
@@ -565,7 +570,7 @@ __global__ void __launch_bounds__(Pair3::NT, 3)
     for (int j = 0; j < NP; ++j) {
         // raw pair j + 1 (pair j arrived one iteration earlier; both on the first)
         if (tma) {
-            if (tid == 0) pt.wait(j == 0 ? 0 : j + 1, j + 1, g);
+            if (tid == kTmaThread) pt.wait(j == 0 ? 0 : j + 1, j + 1, g);
         } else {
             cp_async_wait<0>();  // this thread's copies
         }
@@ -791,7 +796,7 @@ __global__ void __launch_bounds__(PairA3::NT, 2)
     auto issue_pair = [&](int jj) {  // raw pair jj into staging slot jj % 2 (one barrier phase)
         float* dst = stg + (jj & 1) * 2 * 4 * R::RS;
         if (tma) {
-            if (tid == 0) {
+            if (tid == kTmaThread) {
                 uint64_t* b = &pt.bar[jj & 1];
                 mbar_expect_tx(b, 2 * 4 * R::RS * sizeof(float));
                 tma_load_4d(dst, &tm, x0 - 4, y0 - 2, wrap(z0 - 2 + 2 * jj, nz), 0, b);
@@ -897,7 +902,7 @@ __global__ void __launch_bounds__(PairA3::NT, 2)
     const float2 w0 = f2s(2.f / 9.f), wf = f2s(1.f / 9.f), wc = f2s(1.f / 72.f), c3 = f2s(3.f), c9 = f2s(9.f);
     const float2 cA = f2s((float)g.A), cm3 = f2s(-3.f);
 
-    if (tma && tid == 0) {
+    if (tma && tid == kTmaThread) {
         pt.init();
         tma_prefetch_map(&tm);
     }
@@ -906,7 +911,7 @@ __global__ void __launch_bounds__(PairA3::NT, 2)
     issue_pair(0);
     load_fac(0, fcur);
     if (tma) {
-        if (tid == 0) pt.wait(0, 0, g);
+        if (tid == kTmaThread) pt.wait(0, 0, g);
     } else {
         cp_async_wait<0>();
     }
@@ -971,7 +976,7 @@ __global__ void __launch_bounds__(PairA3::NT, 2)
         }
         // raw pair j + 1
         if (tma) {
-            if (tid == 0 && j + 1 < NRP) pt.wait(j + 1, j + 1, g);
+            if (tid == kTmaThread && j + 1 < NRP) pt.wait(j + 1, j + 1, g);
         } else {
             cp_async_wait<0>();  // this thread's copies
         }

@@ -77,7 +77,7 @@ __device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* tm) {
 }
 
 // Pipeline of raw plane pairs fetched by tensor copies: pair jj completes on barrier jj mod 2 (phase jj / 2).
-// Thread 0 alone issues and waits; a barrier of the block then publishes the data to the other threads.
+// One thread of the block issues and waits; a barrier of the block then publishes the data to the other threads.
 struct PairTma {
     uint64_t bar[3];  // two pair slots, and one that nothing completes (the diagnostic wait)
     int bad;          // a wait expired: the block leaves
@@ -89,7 +89,7 @@ struct PairTma {
         bad = 0;
         mbar_init_fence();
     }
-    // thread 0: wait for pairs first .. last; on a timeout, wait (kDrainNs at most) for the copies still in flight,
+    // the issuing thread: wait for pairs first .. last; on a timeout, wait (kDrainNs at most) for the copies still in flight,
     // record the timeout and mark the block
     __device__ __forceinline__ void wait(int first, int last, const Geom& g) {
         const unsigned long long lim = g.wait_ns ? g.wait_ns : kWaitNsDefault;
