@@ -71,6 +71,47 @@ struct Engine2D : EngineCommon<T, 2, HW> {
         launch_pdl(fwd2d_kernel<T, HW, R, WY>, this->fgrid, this->fthreads, 0, s, this->pdl, g, a);
     }
     bool fused2() const override { return this->rows_f == 3; }
+    // FP32 state, hat kernel: the vectorised forward writes the footprint factors for the adjoint (map_hat2, the
+    // arithmetic of box_fac below); the sensitivities and the design gather run as column kernels
+    static constexpr bool kHat = kHat2f<T, HW>;
+    bool fwd_writes_fac() const override { return kHat && (this->rows_f == 32 || this->rows_f == 64); }
+    void box_fac(const Geom& g, const Pose* poses, const void* kref, int n_first, int nsteps, void* out,
+                 cudaStream_t s) override {
+        if constexpr (kHat) {
+            box_fac_hat2_kernel<<<dim3(nblk(g.Fbn, 256), nsteps, 1), 256, 0, s>>>(g, poses, (const float*)kref, n_first,
+                                                                                 (float*)out);
+            LKS_LAUNCHED();
+        } else {
+            EngineCommon<T, 2, HW>::box_fac(g, poses, kref, n_first, nsteps, out, s);
+        }
+    }
+    void sens(const Geom& g, const Pose* poses, const void* kref, const void* boxbuf, long long bstride, int n_first,
+              int nsteps, void* kbar, double* mslot, bool alks, cudaStream_t s) override {
+        if constexpr (kHat) {
+            if (!alks) {
+                adj_sens_hat2_kernel<<<dim3(sens_blocks(g, alks), nsteps, 1), kSensHat2NT, 0, s>>>(
+                    g, poses, (const float*)kref, (const float*)boxbuf, bstride, n_first, (float*)kbar, mslot);
+                LKS_LAUNCHED();
+                return;
+            }
+        }
+        EngineCommon<T, 2, HW>::sens(g, poses, kref, boxbuf, bstride, n_first, nsteps, kbar, mslot, alks, s);
+    }
+    int sens_blocks(const Geom& g, bool alks) const override {
+        if (kHat && !alks) return (int)(nblk(g.Fb[0], kSensHat2NT) * nblk(g.Fb[1], kSensHat2YC));
+        return EngineCommon<T, 2, HW>::sens_blocks(g, alks);
+    }
+    void gather(const Geom& g, const Pose* poses, const void* kbar, int n_first, int nsteps, long long kstride,
+                double* dkref, cudaStream_t s) override {
+        if constexpr (kHat) {
+            const long long nd = (long long)g.nde[0] * g.nde[1];
+            design_gather_hat2_kernel<<<nblk(nd, kGatherHat2NT), kGatherHat2NT, 0, s>>>(g, poses, (const float*)kbar,
+                                                                                     n_first, nsteps, kstride, dkref);
+            LKS_LAUNCHED();
+        } else {
+            EngineCommon<T, 2, HW>::gather(g, poses, kbar, n_first, nsteps, kstride, dkref, s);
+        }
+    }
     bool fused_adj2() const override { return this->rows_a == 3; }
     void adj2(const Geom& g, const void* lam_in, void* lam_out, const void* prev1, const void* cur1, const void* prev2,
               const void* kref, const Pose* pose, void* boxbuf1, const void* fac1, int src1, void* boxbuf2,
@@ -98,6 +139,7 @@ struct Engine2D : EngineCommon<T, 2, HW> {
     void fwd(const Geom& g, const void* in, void* out, const void* kref, const Pose* pose, double* jslot,
              unsigned* flag, const int* jlo, const int* jn, cudaStream_t s) override {
         auto a = make_fwd_args<T>(g, in, out, kref, pose, jslot, flag, jlo, jn);
+        if (this->rows_f == 32 || this->rows_f == 64) a.fac_out = (T*)this->fac_out;  // read by fwd2v (FP32, hat)
         switch (this->rows_f) {
             case 3:
                 fwd2r2(g, a, a, 0, s);

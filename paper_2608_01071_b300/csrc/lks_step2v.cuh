@@ -12,6 +12,8 @@
 #include "lks_common.cuh"
 #include "lks_step_kernels.cuh"
 
+#include <type_traits>
+
 namespace lks {
 
 constexpr int kVecCols = 60;  // output columns per warp
@@ -60,13 +62,45 @@ __device__ __forceinline__ int wall_side(int x, int n, int periodic) {
     return periodic ? -1 : (x == 0 ? 0 : (x == n - 1 ? 1 : -1));
 }
 
+// kappa and C (Eqs. kappa, u_s) at footprint-box node (bx, by) for the FP32 state and the hat kernel: the 2 x 2 taps
+// (weight 0 off the design grid), every operation an explicitly rounded intrinsic, so that the forward step and
+// box_fac_hat2_kernel give kappa and 1 / (1 + kappa) bit for bit alike whatever the compiler contracts around them.
+__device__ __forceinline__ void map_hat2(const Geom& g, const Pose& P, const float* __restrict__ kref, int bx, int by,
+                                         float& kap, float& C) {
+    float wx[2], wy[2], sx = 0.f, sy = 0.f;
+    int ix[2], iy[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int jx = bx - 1 + k, jy = by - 1 + k;
+        const bool vx = jx >= 0 && jx < g.nde[0], vy = jy >= 0 && jy < g.nde[1];
+        wx[k] = vx ? P.wf[0][k] : 0.f;
+        wy[k] = vy ? P.wf[1][k] : 0.f;
+        ix[k] = vx ? jx : 0;
+        iy[k] = vy ? jy : 0;
+        sx = __fadd_rn(sx, wx[k]);
+        sy = __fadd_rn(sy, wy[k]);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int ky = 0; ky < 2; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 2; ++kx)
+            s = __fmaf_rn(__fmul_rn(wx[kx], wy[ky]), kref[ix[kx] + g.nde[0] * iy[ky]], s);
+    kap = s;
+    C = __fmul_rn(sx, sy);
+}
+
 // ------------------------------------------------------------------------------------------------
 // Forward step n-1 -> n.
 // ------------------------------------------------------------------------------------------------
+// With the FP32 state and the hat kernel the Brinkman step maps kappa with map_hat2 and, when a.fac_out is set (the
+// recomputation of the reverse sweep), also stores 1 / (1 + kappa) of its footprint-box nodes for the adjoint.
 // The input rows arrive by asynchronous copies into a per-warp ring of kFwd2vDepth rows in shared memory,
 // kFwd2vDepth - 1 rows ahead of use; each lane copies and reads back only its own column pair, so the ring needs no
 // barrier, and many rows are in flight without holding them in registers.
 constexpr int kFwd2vDepth = 6;
+template <typename T, int HW>
+constexpr bool kHat2f = std::is_same<T, float>::value && HW == 1;
 template <typename T>
 constexpr size_t smem2v_fwd() {
     return sizeof(typename Vec2<T>::type) * 4 * kFwd2vDepth * 3 * 32;
@@ -176,10 +210,16 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (HW == 1 ? 7 : 5) : 4) f
             // Brinkman with the mapped kappa, walls and stability for one column of the pair
             auto finish = [&](T& u0, T& u1, int bx, int wx) {
                 if (bx >= 0 && by >= 0) {
-                    const int b[2] = {bx, by};
-                    T kap, C;
-                    map_node<T, 2, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
-                    const T inv = (T)1 / ((T)1 + kap);
+                    T kap, C, inv;
+                    if constexpr (kHat2f<T, HW>) {
+                        map_hat2(g, P, a.kref, bx, by, kap, C);
+                        inv = __fdiv_rn(1.f, __fadd_rn(1.f, kap));
+                        if (a.fac_out != nullptr) a.fac_out[bx + g.Fb[0] * by] = inv;
+                    } else {
+                        const int b[2] = {bx, by};
+                        map_node<T, 2, HW, false>(g, P, a.kref, b, kap, C, nullptr, nullptr);
+                        inv = (T)1 / ((T)1 + kap);
+                    }
                     u0 = (u0 + kap * (pose_uG<T>(P, 0) * C)) * inv;
                     u1 = (u1 + kap * (pose_uG<T>(P, 1) * C)) * inv;
                 }
@@ -489,6 +529,194 @@ __global__ void __launch_bounds__(128, 4) adj2v_kernel(Geom g, AdjArgs<T> a) {
         step(t + 3, S3, S0, S1, S2);
     }
     cp_async_wait<0>();
+}
+
+// ------------------------------------------------------------------------------------------------
+// The footprint-box side of the reverse sweep for the FP32 state and the hat kernel (D2Q9).
+// ------------------------------------------------------------------------------------------------
+// 1 / (1 + kappa) over the footprint box for steps n_first .. n_first + nsteps - 1 (box_fac_kernel) with map_hat2,
+// the arithmetic of the forward step, which writes the same factors for the steps it recomputes.
+static __global__ void __launch_bounds__(256) box_fac_hat2_kernel(Geom g, const Pose* __restrict__ poses,
+                                                                  const float* __restrict__ kref, int n_first,
+                                                                  float* __restrict__ fac) {
+    const long long bl = blockIdx.x * 256LL + threadIdx.x;
+    if (bl >= g.Fbn) return;
+    const int j = blockIdx.y;
+    int b[3];
+    box_unflatten<2>(g, bl, b);
+    float kap, C;
+    map_hat2(g, poses[n_first + j], kref, b[0], b[1], kap, C);
+    fac[j * g.Fbn + bl] = __fdiv_rn(1.f, __fadd_rn(1.f, kap));
+}
+
+// Local shape and motion sensitivities of a segment (adj_sens_kernel's quantities, Eqs. dJdgamma, dJdchi in discrete
+// form): one thread per (footprint-box column bx, chunk of kSensHat2YC rows, step) marching up its chunk.  Per design
+// row jy the two x taps give K(jy) = sum w_x kappa^ref and X(jy) = sum w'_x kappa^ref (w' = dw/d offset), and at box
+// row by, whose y taps are jy = by - 1 and by,
+//   kappa = sum w_y K,   dkappa/ds = (sum w_y X, sum w'_y K),   C = S_x S_y,   dC/ds = (S'_x S_y, S_x S'_y)
+// with S, S' the sums of the valid weights and of their derivatives.  The loads of four rows are issued before they
+// are used.  Motion partials: FP32 over the chunk and the block (fixed order), FP64 from the block sums on (blocks:
+// the column blocks of the first chunk, then of the next...).  kappa-bar goes to kbar (0 outside the grid).
+constexpr int kSensHat2NT = 128, kSensHat2YC = 16;
+
+static __global__ void __launch_bounds__(kSensHat2NT)
+    adj_sens_hat2_kernel(Geom g, const Pose* __restrict__ poses, const float* __restrict__ kref,
+                         const float* __restrict__ boxbuf, long long bstride, int n_first, float* __restrict__ kbar,
+                         double* __restrict__ mslot) {
+    __shared__ double red[4 * (kSensHat2NT / 32)];
+    const int s = blockIdx.y;
+    const Pose& P = poses[n_first + s];
+    const int fb0 = g.Fb[0];
+    const long long Fbn = g.Fbn;
+    const int ncb = (fb0 + kSensHat2NT - 1) / kSensHat2NT;  // column blocks per chunk
+    const int bx = (blockIdx.x % ncb) * kSensHat2NT + threadIdx.x;
+    const int by0 = (blockIdx.x / ncb) * kSensHat2YC, by1 = min(by0 + kSensHat2YC, g.Fb[1]);
+    float mv[4] = {0.f, 0.f, 0.f, 0.f};
+    const bool colin = bx < fb0;
+    const bool ok = colin && (g.periodic[0] || (unsigned)(P.xs[0] + bx) < (unsigned)g.n[0]);
+    float* kbo = colin && kbar != nullptr ? kbar + (long long)s * Fbn + bx : nullptr;
+    if (!ok && kbo != nullptr) {
+        for (int by = by0; by < by1; ++by) kbo[(long long)fb0 * by] = 0.f;
+    }
+    if (ok) {
+        float wx[2], dwx[2], sx = 0.f, dsx = 0.f;
+        int ix[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int jx = bx - 1 + k;
+            const bool vx = jx >= 0 && jx < g.nde[0];
+            wx[k] = vx ? P.wf[0][k] : 0.f;
+            dwx[k] = vx ? P.dwf[0][k] : 0.f;
+            ix[k] = vx ? jx : 0;
+            sx += wx[k];
+            dsx += dwx[k];
+        }
+        const float wy[2] = {P.wf[1][0], P.wf[1][1]}, dwy[2] = {P.dwf[1][0], P.dwf[1][1]};
+        const float uG[2] = {P.uGf[0], P.uGf[1]};
+        const int nde0 = g.nde[0], nde1 = g.nde[1], xs1 = P.xs[1], ny = g.n[1];
+        const bool yper = g.periodic[1] != 0;
+        const float* rec = boxbuf + (long long)s * bstride + bx;
+        // the two x taps of design row jy (0 off the design grid)
+        auto taps = [&](int jy, float (&kr)[2]) {
+            const bool v = jy >= 0 && jy < nde1;
+            const float* kp = kref + (long long)nde0 * (v ? jy : 0);
+#pragma unroll
+            for (int t = 0; t < 2; ++t) kr[t] = v ? kp[ix[t]] : 0.f;
+        };
+        float K0, X0;  // x sums of design row by - 1
+        {
+            float kr[2];
+            taps(by0 - 1, kr);
+            K0 = wx[0] * kr[0] + wx[1] * kr[1];
+            X0 = dwx[0] * kr[0] + dwx[1] * kr[1];
+        }
+        constexpr int U = 4;
+#pragma unroll 1
+        for (int bq = by0; bq < by1; bq += U) {
+            float kr[U][2], rl[U][4];
+            bool in[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int by = bq + u;
+                in[u] = by < by1 && (yper || (unsigned)(xs1 + by) < (unsigned)ny);
+                taps(by < by1 ? by : -1, kr[u]);
+                const long long o = (long long)fb0 * (in[u] ? by : 0);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) rl[u][c] = in[u] ? rec[c * Fbn + o] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int by = bq + u;
+                const float K1 = wx[0] * kr[u][0] + wx[1] * kr[u][1];  // design row by
+                const float X1 = dwx[0] * kr[u][0] + dwx[1] * kr[u][1];
+                if (in[u]) {
+                    const bool v0 = by >= 1, v1 = by < nde1;  // y taps jy = by - 1, by on the design grid
+                    const float wy0 = v0 ? wy[0] : 0.f, wy1 = v1 ? wy[1] : 0.f;
+                    const float dy0 = v0 ? dwy[0] : 0.f, dy1 = v1 ? dwy[1] : 0.f;
+                    const float kap = wy0 * K0 + wy1 * K1;
+                    const float dk[2] = {wy0 * X0 + wy1 * X1, dy0 * K0 + dy1 * K1};
+                    const float sy = wy0 + wy1, dsy = dy0 + dy1;
+                    const float C = sx * sy;
+                    const float dC[2] = {dsx * sy, sx * dsy};
+                    const float inv = 1.f / (1.f + kap);
+                    float kb = 0.f, cbar = 0.f, usb[2];
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const float lu = rl[u][c];
+                        kb += lu * (uG[c] * C - rl[u][2 + c]);
+                        usb[c] = lu * kap * inv;
+                        cbar += usb[c] * uG[c];
+                    }
+                    kb *= inv;
+                    if (kbo != nullptr) kbo[(long long)fb0 * by] = kb;
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        mv[c] += kb * dk[c] + cbar * dC[c];
+                        mv[2 + c] += usb[c] * C;
+                    }
+                } else if (by < by1 && kbo != nullptr) {
+                    kbo[(long long)fb0 * by] = 0.f;
+                }
+                K0 = K1;
+                X0 = X1;
+            }
+        }
+    }
+    if (mslot != nullptr) {
+        double out[4];
+        block_sum<kSensHat2NT, 4, float>(mv, out, red);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) mslot[((long long)s * gridDim.x + blockIdx.x) * 4 + c] = out[c];
+        }
+    }
+}
+
+// Transposed mapping onto the design grid (design_gather_kernel) for the FP32 state and the hat kernel: kappa-bar is
+// 0 at footprint-box nodes outside the grid, so a tap needs no grid test, only to lie in the box (fixed per design
+// node); the four tap-weight products of each step are staged once per block in shared memory, and each thread adds
+// its steps' sums to its FP64 running sum in strict step order n = Nt..1 (across calls too).
+constexpr int kGatherHat2NT = 128, kGatherHat2SC = 64;
+
+static __global__ void __launch_bounds__(kGatherHat2NT)
+    design_gather_hat2_kernel(Geom g, const Pose* __restrict__ poses, const float* __restrict__ kbar, int n_first,
+                              int nsteps, long long kstride, double* __restrict__ dkref) {
+    __shared__ float wp[kGatherHat2SC][4];
+    const int nd = g.nde[0] * g.nde[1];
+    const int jl = blockIdx.x * kGatherHat2NT + threadIdx.x;
+    const bool act = jl < nd;
+    const int jx = jl % g.nde[0], jy = jl / g.nde[0];
+    // tap t = kx + 2 ky reads box node (j + 1 - k) per axis
+    int off[4];
+    bool val[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int bx = jx + 1 - (t & 1), by = jy + 1 - (t >> 1);
+        val[t] = act && bx >= 0 && bx < g.Fb[0] && by >= 0 && by < g.Fb[1];
+        off[t] = val[t] ? bx + g.Fb[0] * by : 0;
+    }
+    double acc = act ? dkref[jl] : 0.0;
+    for (int c0 = nsteps - 1; c0 >= 0; c0 -= kGatherHat2SC) {
+        const int cn = min(kGatherHat2SC, c0 + 1);  // steps c0, c0 - 1, .., c0 - cn + 1
+        __syncthreads();
+        for (int i = threadIdx.x; i < cn * 4; i += kGatherHat2NT) {
+            const int u = i >> 2, t = i & 3;
+            const Pose& P = poses[n_first + c0 - u];
+            wp[u][t] = P.wf[0][t & 1] * P.wf[1][t >> 1];
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll 2
+            for (int u = 0; u < cn; ++u) {
+                const float* kb = kbar + (long long)(c0 - u) * kstride;
+                float sum = 0.f;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) sum = fmaf(wp[u][t], val[t] ? kb[off[t]] : 0.f, sum);
+                acc += (double)sum;
+            }
+        }
+    }
+    if (act) dkref[jl] = acc;
 }
 
 }  // namespace lks

@@ -66,13 +66,14 @@ def test_gradient_modes(mode):
     check(tiny_workload("D2Q9", mode=mode), 1e-10, 1e-10, 1e-10)
 
 
-@pytest.mark.parametrize("lattice,rows", [("D2Q9", 1), ("D2Q9", 3), ("D3Q15", 32), ("D3Q15", 128)])
+@pytest.mark.parametrize("lattice,rows", [("D2Q9", 1), ("D2Q9", 3), ("D2Q9", 32), ("D3Q15", 32), ("D3Q15", 128)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_checkpointing_bitwise(lattice, rows, prec):
     # with the step-kernel variants fixed, every checkpoint mode gives the same bits (the tuner may pick other
     # variants for the pipelined sqrt sweep, whose results then differ at rounding level); rows = 3 pairs the
-    # two-step launches differently in every mode; rows = 128 (plane-pair kernels, FP32 only): the recomputation
-    # writes the adjoint's footprint-box factors, which box_fac computes in full storage
+    # two-step launches differently in every mode; rows = 32 (D2Q9, vectorised) and 128 (D3Q15 plane pairs, FP32
+    # only): with the FP32 state the recomputation writes the adjoint's footprint-box factors, which box_fac
+    # computes in full storage
     if rows == 3 and prec == "fp64":
         pytest.skip("covered in FP32")
     if rows == 128 and prec == "fp64":
