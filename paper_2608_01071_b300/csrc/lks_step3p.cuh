@@ -49,6 +49,9 @@ __host__ __device__ constexpr size_t smem3p_fwd() {
     return sizeof(float) * 4 * 4 * Pair3::RS + sizeof(float2) * Pair3::NFLD * Pair3::NM;
 }
 
+// Prefetch the line holding p into L2 (no register is written).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // The thread that issues and waits for a block's tensor copies: the last one, in a warp without a halo-ring node
 // (the ring nodes go to the first threads), so that the copy duty does not fall on a warp that already does more.
 constexpr int kTmaThread = 255;
@@ -939,39 +942,23 @@ __global__ void __launch_bounds__(PairA3::NT, 2)
 #pragma unroll 1
     for (int j = 0; j < NJ; ++j) {
         // u_{n-1} of this iteration's output pair (planes z0 - 5 + 2j, + 1), and u_n there on the footprint box (for
-        // its records), read ahead of the moments
+        // its records): prefetched into L2 here, ahead of the moments, and loaded for the output stage (no registers
+        // held across the moments)
         const int o0 = z0 - 5 + 2 * j;
         bool ok[2];
         int bzo[2];
-        float2 u[3] = {f2s(0.f), f2s(0.f), f2s(0.f)}, uc[3] = {f2s(0.f), f2s(0.f), f2s(0.f)};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             ok[h] = j >= 2 && col && o0 + h >= z0 && o0 + h < z0 + ZB && o0 + h < nz;
             bzo[h] = (ok[h] && colbox) ? box_coord(o0 + h, xs2, g.Fb[2], g.n[2], g.periodic[2]) : -1;
         }
-        {
-            const int gi0 = gcol + plane * o0;
-            const float* up = a.u_prev + gi0;
-            const float* uq = a.u_cur + gi0;
-            if (ok[0]) {
-                u[0].x = up[0];
-                u[1].x = up[N];
-                u[2].x = up[2 * N];
-            }
-            if (ok[1]) {
-                u[0].y = up[plane];
-                u[1].y = up[N + plane];
-                u[2].y = up[2 * N + plane];
-            }
-            if (bzo[0] >= 0) {
-                uc[0].x = uq[0];
-                uc[1].x = uq[N];
-                uc[2].x = uq[2 * N];
-            }
-            if (bzo[1] >= 0) {
-                uc[0].y = uq[plane];
-                uc[1].y = uq[N + plane];
-                uc[2].y = uq[2 * N + plane];
+        const int gi0 = gcol + plane * o0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (ok[h]) prefetch_l2(a.u_prev + gi0 + h * plane + c * N);
+                if (bzo[h] >= 0) prefetch_l2(a.u_cur + gi0 + h * plane + c * N);
             }
         }
         // raw pair j + 1
@@ -1110,6 +1097,31 @@ __global__ void __launch_bounds__(PairA3::NT, 2)
         }
         __syncthreads();
         if (j >= 2) {
+            float2 u[3] = {f2s(0.f), f2s(0.f), f2s(0.f)}, uc[3] = {f2s(0.f), f2s(0.f), f2s(0.f)};
+            {
+                const float* up = a.u_prev + gi0;
+                const float* uq = a.u_cur + gi0;
+                if (ok[0]) {
+                    u[0].x = up[0];
+                    u[1].x = up[N];
+                    u[2].x = up[2 * N];
+                }
+                if (ok[1]) {
+                    u[0].y = up[plane];
+                    u[1].y = up[N + plane];
+                    u[2].y = up[2 * N + plane];
+                }
+                if (bzo[0] >= 0) {
+                    uc[0].x = uq[0];
+                    uc[1].x = uq[N];
+                    uc[2].x = uq[2 * N];
+                }
+                if (bzo[1] >= 0) {
+                    uc[0].y = uq[plane];
+                    uc[1].y = uq[N + plane];
+                    uc[2].y = uq[2 * N + plane];
+                }
+            }
             // (O) lambda_{n-1} of the pair C_{j-1} = planes (o0, o0 + 1) at the own column
             const float2* ms = mom + ((j - 1) & 1) * R::SLOT;  // C_{j-1}
             const float2* mn = mom + (j & 1) * R::SLOT;        // C_j (its first plane is above the pair)
