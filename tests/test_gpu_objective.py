@@ -70,6 +70,16 @@ def test_variance_d3q15_kernel_variants(rows):
     assert g["stats"]["tile_rows_fwd"] == rows
 
 
+@pytest.mark.parametrize("fwd,adj", [(128, 128), (160, 192)])
+def test_variance_d3q15_plane_pair_fp32(fwd, adj):
+    # the objective partials and the variance source in the plane-pair kernels (FP32 only), on a grid with a
+    # tensor-copy tile (x0 = 32, y0 = 8)
+    w = var_workload("D3Q15", precision="fp32", tile_rows=fwd, tile_rows_adj=adj, shape=(72, 20, 24),
+                     probe_lo=(40, 4, 6), probe_hi=(50, 16, 18), ckpt="sqrt", Nt=16)
+    g, _ = check(w, *TOL["fp32"])
+    assert g["stats"]["tile_rows_fwd"] == fwd and g["stats"]["tile_rows_adj"] == adj
+
+
 @pytest.mark.parametrize("ckpt", ["revolve", "sqrt"])
 def test_variance_graph_replay_new_inputs(ckpt):
     # the source constant 1 + 2 phi E is read on the device by the captured adjoint: replays with other inputs
