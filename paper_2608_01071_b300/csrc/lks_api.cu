@@ -502,7 +502,7 @@ void autotune_rows(lks_ctx* c) {
         auto it = cache.find(key);
         std::array<int, 4> v;
         if (it == cache.end() && tune_file_read(fpath, fkey, v)) {
-            // choices of an earlier process, kept only if this build still offers them on this grid
+            // choices of an earlier process, kept only if this version of the library still offers them on this grid
             const int rf0 = c->eng->rows_f, ra0 = c->eng->rows_a;
             if (c->eng->set_rows(v[0], v[2], c->g) && c->eng->set_rows(v[1], v[3], c->g)) it = cache.emplace(key, v).first;
             c->eng->set_rows(rf0, ra0, c->g);
